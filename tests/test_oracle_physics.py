@@ -1,0 +1,449 @@
+"""Pins of the oracle's transport, temperature and ray-tracing results against
+closed forms, conservation laws, brute force and independent quadrature
+(CPU only)."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+SIGMA = 5.670374419e-5          # CODATA Stefan-Boltzmann constant, CGS
+H, K = 6.62607015e-27, 1.380649e-16
+
+
+def gray_fine_model(n=4, tau_cell=1e-3, nf=400, albedo=0.0, side_au=1.0, src=None):
+    """Uniform gray cube with a fine frequency grid (0.01 um - 1 cm), so that
+    sum_j B(nu_j, T) dnu_j matches sigma T^4 / pi closely."""
+    m = W.uniform_cube(n=n, tau_cell=tau_cell, nf=8, albedo=albedo, side_au=side_au,
+                       source_pos=src)
+    nu, dnu = W.log_frequency_grid(nf, 0.01, 1.0e4)
+    m.nu, m.dnu = nu, dnu
+    m.kabs = np.full((1, nf), 1.0 - albedo)
+    m.ksca = np.full((1, nf), albedo)
+    m.g = np.zeros((1, nf))
+    m.rho = np.full_like(m.rho, tau_cell / m.cell)
+    return m
+
+
+# ---------------------------------------------------------------- Planck / Eq. 4
+def test_planck_sum_matches_stefan_boltzmann(O):
+    m = gray_fine_model()
+    for T in (20.0, 300.0, 2500.0, 5800.0):
+        s = sum(O.planck_B(nu, T) * d for nu, d in zip(m.nu, m.dnu))
+        assert s == pytest.approx(SIGMA * T ** 4 / math.pi, rel=2e-4)
+
+
+def test_planck_peak_and_derivative(O):
+    T = 5000.0
+    nus = np.geomspace(1e13, 1e16, 20001)
+    B = np.array([O.planck_B(v, T) for v in nus])
+    # Wien displacement in frequency: x_peak = 3 + W0(-3 e^-3) = 2.82143937212
+    assert nus[np.argmax(B)] == pytest.approx(2.82143937212 * K * T / H, rel=5e-4)
+    for nu in (1e12, 3e13, 6e14, 3e15):
+        for T in (30.0, 800.0, 6000.0):
+            h = 1e-4 * T
+            fd = (O.planck_B(nu, T + h) - O.planck_B(nu, T - h)) / (2 * h)
+            assert O.planck_dBdT(nu, T) == pytest.approx(fd, rel=1e-6)
+
+
+def test_temperature_solve_gray_closed_form(O):
+    m = gray_fine_model()
+    # 4 pi kappa sigma T^4 / pi = E / (rho V)  =>  T = (target / (4 kappa sigma))^(1/4)
+    for T0 in (15.0, 150.0, 1500.0):
+        target = 4.0 * SIGMA * T0 ** 4
+        T = O.solve_temperature(m, 0, target)
+        assert T == pytest.approx(T0, rel=1e-4)
+    assert O.solve_temperature(m, 0, 0.0) == 0.0
+
+
+def test_temperature_solve_inverts_planck_mean(O):
+    m = W.r2_shell(n=8, nf=64)
+    for T0 in (3.0, 47.0, 812.0, 1.6e4):
+        target = 4 * math.pi * O.planck_mean(m, 0, T0)
+        assert O.solve_temperature(m, 0, target) == pytest.approx(T0, rel=1e-10)
+
+
+# ---------------------------------------------------------------- emission
+def test_empty_grid_emission_spectrum_and_isotropy(O):
+    m = W.r2_shell(n=8, nf=24)
+    m.rho[:] = 0.0
+    N = 40000
+    r = O.transport(m, N, seed=3, mode=O.MODE_BW, traj_cap=2 * N)
+    assert r["stats"]["escaped"] == N and r["stats"]["interactions"] == 0
+    assert r["sed_esc"].sum() == pytest.approx(m.luminosity, rel=1e-12)
+    # frequency histogram vs L_nu dnu / L (chi^2); the weights are the
+    # blackbody written out here from Planck's law, independent of the oracle
+    x = H * m.nu / (K * 2500.0)
+    w = m.nu ** 3 / np.expm1(x) * m.dnu
+    p = w / w.sum()
+    cnt = r["sed_cnt"].sum(0).astype(float)
+    keep = p * N > 20
+    chi2 = ((cnt[keep] - N * p[keep]) ** 2 / (N * p[keep])).sum()
+    assert chi2 < keep.sum() + 6 * math.sqrt(2 * keep.sum())
+    # isotropy: emission directions from the trajectory log
+    tr = r["traj"]
+    k = tr["k"][tr["type"] == O.T_EMIT]
+    assert np.abs(k.mean(0)).max() < 4 / math.sqrt(3 * N)
+    kk = (k[:, :, None] * k[:, None, :]).mean(0)
+    assert np.abs(kk - np.eye(3) / 3).max() < 4 * math.sqrt(0.1 / N)
+    # cos(theta) bins are equally populated
+    h = r["sed_cnt"].sum(1)
+    assert ((h - N / 10) ** 2 / (N / 10)).sum() < 30
+
+
+# ---------------------------------------------------------------- pure absorber
+def _fib_sphere(n):
+    i = np.arange(n) + 0.5
+    mu = 1 - 2 * i / n
+    ph = math.pi * (1 + 5 ** 0.5) * i
+    st = np.sqrt(1 - mu * mu)
+    return np.stack([st * np.cos(ph), st * np.sin(ph), mu], 1)
+
+
+def test_pure_absorber_escape_fraction_closed_form(O):
+    """Uniform gray cube, source at the centre, no scattering, no re-emission:
+    the escaped fraction is (1/4 pi) int exp(-chi d(Omega)) dOmega with the
+    distance to the cube face d = (L/2) / max|k_a|; the integral is done here
+    by quadrature of that closed form."""
+    n, tau_cell = 6, 0.4
+    m = W.uniform_cube(n=n, tau_cell=tau_cell, nf=6, albedo=0.0)
+    N = 60000
+    r = O.transport(m, N, seed=5, mode=O.MODE_NOREEMIT, lucy_mode=O.LUCY_OFF)
+    k = _fib_sphere(400000)
+    d = (n / 2) / np.abs(k).max(1)           # in cells
+    f = np.exp(-tau_cell * d).mean()
+    fe = r["stats"]["escaped"] / N
+    assert abs(fe - f) < 4 * math.sqrt(f * (1 - f) / N)
+    # energy: L = escaped + absorbed (count estimator), exactly
+    xi = m.luminosity / N
+    assert r["sed_esc"].sum() + r["count"].sum() * xi == pytest.approx(m.luminosity, rel=1e-12)
+    assert r["E_abs"].sum() == pytest.approx(r["count"].sum() * xi, rel=1e-12)
+
+
+def _absorbed_fraction_quadrature(O, m, ndir=60000):
+    """(1/4 pi) int exp(-tau_before) (1 - exp(-tau_cell)) dOmega per cell for a
+    gray pure absorber, from the oracle's DDA along a Fibonacci sphere."""
+    chi = m.rho[0].reshape(-1).astype(np.float64) * (m.kabs[0, 0] + m.ksca[0, 0])
+    frac = np.zeros(chi.size)
+    src = np.array(m.sources[0].pos)
+    for k in _fib_sphere(ndir):
+        cells, lens = O.dda_segments(m, src, k)
+        t = chi[cells] * lens
+        before = np.concatenate([[0.0], np.cumsum(t)[:-1]])
+        frac[cells] += np.exp(-before) * (-np.expm1(-t))
+    return frac / ndir
+
+
+def test_pure_absorber_cell_energies_match_quadrature(O):
+    """Per-cell absorbed energy of both estimators (absorption counts and the
+    Lucy path-length form) equals the deterministic quadrature on a small
+    irregular grid."""
+    m = W.random_grid(n=(4, 4, 4), seed=7, tau_scale=0.6, albedo=(0.0, 0.0))
+    m.kabs[:] = 1.0
+    m.ksca[:] = 0.0
+    m.rho = (m.rho * (0.6 / (m.cell * m.rho.mean()))).astype(np.float32)
+    N = 200000
+    f = _absorbed_fraction_quadrature(O, m) * m.luminosity
+    xi = m.luminosity / N
+    rc = O.transport(m, N, seed=9, mode=O.MODE_NOREEMIT, lucy_mode=O.LUCY_OFF)
+    Ec = rc["E_abs"][0]
+    sig = xi * np.sqrt(np.maximum(rc["count"][0], 1))
+    assert np.all(np.abs(Ec - f) < 4.5 * sig + 1e-9 * m.luminosity)
+    rl = O.transport(m, N, seed=10, mode=O.MODE_NOREEMIT, lucy_mode=O.LUCY_ALL)
+    El = rl["E_abs"][0]
+    sl = np.sqrt(rl["esq"][0]) + 1e-12
+    assert np.all(np.abs(El - f) < 4.5 * np.maximum(sl, 0.02 * f) + 1e-9 * m.luminosity)
+    # the path-length estimator has the smaller variance in thin cells
+    thin = (m.rho[0].reshape(-1) * m.cell < 0.1) & (f > 0)
+    assert (sl[thin] < sig[thin]).mean() > 0.8
+
+
+# ---------------------------------------------------------------- conservation
+def test_bw_conserves_energy_exactly(O):
+    m = W.homogeneous_sphere(n=12, tau_v=3.0)
+    N = 4000
+    r = O.transport(m, N, seed=2, mode=O.MODE_BW)
+    assert r["stats"]["escaped"] == N
+    assert r["sed_esc"].sum() == pytest.approx(m.luminosity, rel=1e-12)
+
+
+def test_pah_packets_are_stored_and_counted(O):
+    m = W.clumpy_torus(n=16, n_clump=60, seed=3, nf=24)
+    N = 3000
+    r = O.transport(m, N, seed=4, mode=O.MODE_BW, pah_cap=N)
+    st = r["stats"]
+    assert st["pah"] > 0 and st["escaped"] + st["pah"] == N
+    xi = m.luminosity / N
+    assert r["sed_esc"].sum() + st["pah"] * xi == pytest.approx(m.luminosity, rel=1e-12)
+    assert len(r["pah"]) == st["pah"]
+
+
+def test_event_cap_terminates_packets(O):
+    m = W.uniform_cube(n=4, tau_cell=5.0, albedo=0.9)
+    r = O.transport(m, 500, seed=1, mode=O.MODE_BW, max_events=3)
+    st = r["stats"]
+    assert st["stuck"] > 0 and st["escaped"] + st["stuck"] == 500
+
+
+def test_scattering_only_matches_brute_force_walk(O):
+    """Albedo 1, isotropic scattering in a uniform gray cube with the source at
+    the centre: the mean number of scatterings per packet equals that of a
+    brute-force random walk (exponential steps, isotropic turns) in a cube of
+    the same optical half-width, written here independently."""
+    n, tau_cell = 4, 2.5
+    m = W.uniform_cube(n=n, tau_cell=tau_cell, nf=4, albedo=1.0, g=0.0)
+    N = 6000
+    r = O.transport(m, N, seed=6, mode=O.MODE_BW)
+    assert r["stats"]["escaped"] == N and r["stats"]["absorptions"] == 0
+    assert r["sed_esc"].sum() == pytest.approx(m.luminosity, rel=1e-12)
+    mc = r["stats"]["scatters"] / N
+    rng = np.random.default_rng(1)
+    half = n * tau_cell / 2
+    nw = 20000
+    pos = np.zeros((nw, 3))
+    cnt = np.zeros(nw)
+    alive = np.ones(nw, bool)
+
+    def iso(k):
+        mu = rng.uniform(-1, 1, k)
+        ph = rng.uniform(0, 2 * math.pi, k)
+        st = np.sqrt(1 - mu * mu)
+        return np.stack([st * np.cos(ph), st * np.sin(ph), mu], 1)
+
+    d = iso(nw)
+    while alive.any():
+        idx = np.nonzero(alive)[0]
+        s = rng.exponential(1.0, idx.size)
+        p = pos[idx] + d[idx] * s[:, None]
+        out = np.abs(p).max(1) > half
+        alive[idx[out]] = False
+        keep = idx[~out]
+        pos[keep] = p[~out]
+        cnt[keep] += 1
+        d[keep] = iso(keep.size)
+    bf = cnt.mean()
+    err = math.sqrt(cnt.var() / nw + (r["stats"]["scatters"] / N) / N * 4)
+    assert abs(mc - bf) < 4 * err + 0.01 * bf, (mc, bf)
+
+
+def test_optically_thin_equilibrium_temperature(O):
+    """Gray optically thin dust around a point source: T^4 = L <1/r^2> /
+    (16 pi sigma) cell by cell, with <1/r^2> averaged over the cell volume by
+    quadrature (Lucy estimator, frozen temperatures, no re-emission needed at
+    tau ~ 1e-3)."""
+    n = 8
+    m = gray_fine_model(n=n, tau_cell=2e-4, nf=160)
+    N = 60000
+    r = O.transport(m, N, seed=8, mode=O.MODE_NOREEMIT, lucy_mode=O.LUCY_ALL)
+    T = O.temperatures(m, r["E_abs"])[0].reshape(n, n, n)
+    sub = (np.arange(6) + 0.5) / 6
+    Tref = np.zeros((n, n, n))
+    for iz in range(n):
+        for iy in range(n):
+            for ix in range(n):
+                pts = m.box_min + m.cell * (np.array([ix, iy, iz])[None, :] +
+                                            np.stack(np.meshgrid(sub, sub, sub), -1).reshape(-1, 3))
+                inv = (1.0 / (pts ** 2).sum(1)).mean()
+                Tref[iz, iy, ix] = (m.luminosity * inv / (16 * math.pi * SIGMA)) ** 0.25
+    E = r["E_abs"][0].reshape(n, n, n)
+    relE = np.sqrt(r["esq"][0].reshape(n, n, n)) / E
+    c = (np.arange(n) + 0.5 - n / 2)
+    R = np.sqrt(c[:, None, None] ** 2 + c[None, :, None] ** 2 + c[None, None, :] ** 2)
+    sel = R > 2.0
+    err = np.abs(T[sel] / Tref[sel] - 1)
+    # Sigma e^2 per deposit underestimates the per-packet variance; 6 sigma
+    assert np.all(err < 6 * relE[sel] / 4 + 2e-3), err.max()
+
+
+def test_bw_and_iterative_reach_the_same_temperatures(O):
+    """Bjorkman & Wood (Eq. 10) and the iterative scheme (Eq. 5 with frozen
+    temperatures, Eq. 4 between iterations) converge to the same equilibrium
+    (Sect. 3.3)."""
+    m = W.homogeneous_sphere(n=6, tau_v=2.0, nf=20)
+    N = 80000
+    rb = O.transport(m, N, seed=21, mode=O.MODE_BW, n_threads=1)
+    Tb = O.temperatures(m, rb["E_abs"])
+    Tp = O.temperature_guess(m)
+    for it in range(4):
+        ri = O.transport(m, N, seed=100 + it, mode=O.MODE_FROZEN_T, T_prev=Tp, n_threads=4)
+        Tp = O.temperatures(m, ri["E_abs"])
+    E = rb["E_abs"][0]
+    good = (rb["count"][0] > 200) & (ri["count"][0] > 200)
+    assert good.sum() >= 16
+    rel_sig = 1 / np.sqrt(np.minimum(rb["count"][0][good], ri["count"][0][good]))
+    d = np.abs(Tb[0][good] / Tp[0][good] - 1)
+    assert np.all(d < 3 * rel_sig / 2 + 0.02), d.max()
+
+
+def test_mrw_on_and_off_agree(O):
+    """A uniform gray cube with tau_cell = 14: the modified random walk
+    (Sect. 3.2) reproduces the escaped spectrum and absorbed energy of plain
+    transport."""
+    m = W.uniform_cube(n=3, tau_cell=14.0, nf=4, albedo=0.5)
+    T0 = np.full((1, m.ncell), 300.0)
+    N = 3000
+    ron = O.transport(m, N, seed=31, mode=O.MODE_FROZEN_T, T_prev=T0, mrw=True, n_threads=4)
+    roff = O.transport(m, N, seed=32, mode=O.MODE_FROZEN_T, T_prev=T0, mrw=False, n_threads=4)
+    assert ron["stats"]["mrw_steps"] > 0 and roff["stats"]["mrw_steps"] == 0
+    assert ron["stats"]["escaped"] == N and roff["stats"]["escaped"] == N
+    a, b = ron["E_abs"].sum(), roff["E_abs"].sum()
+    assert abs(a / b - 1) < 0.06
+    sa, sb = ron["sed_esc"].sum(0), roff["sed_esc"].sum(0)
+    sig = np.sqrt(ron["sed_cnt"].sum(0) + roff["sed_cnt"].sum(0)) * m.luminosity / N
+    assert np.all(np.abs(sa - sb) <= 4 * sig + 0.05 * sb)
+    assert ron["stats"]["interactions"] < 0.7 * roff["stats"]["interactions"]
+
+
+def test_packet_range_sharding_is_exact(O):
+    m = W.random_grid(n=(5, 4, 3), ns=2, seed=11, tau_scale=2.0)
+    T0 = np.full((2, m.ncell), 200.0)
+    N = 2000
+    kw = dict(seed=4, mode=O.MODE_FROZEN_T, T_prev=T0, record_events=True, event_cap=20 * N)
+    full = O.transport(m, N, **kw)
+    a = O.transport(m, N, pid_begin=0, pid_end=700, **kw)
+    b = O.transport(m, N, pid_begin=700, pid_end=N, **kw)
+    thr = O.transport(m, N, n_threads=3, **kw)
+    np.testing.assert_array_equal(a["count"] + b["count"], full["count"])
+    np.testing.assert_allclose(a["E_abs"] + b["E_abs"], full["E_abs"], rtol=1e-12, atol=0)
+    np.testing.assert_array_equal(np.concatenate([a["events"], b["events"]]), full["events"])
+    np.testing.assert_array_equal(thr["events"], full["events"])
+    np.testing.assert_allclose(thr["E_abs"], full["E_abs"], rtol=1e-12, atol=0)
+
+
+# ---------------------------------------------------------------- ray tracer
+def test_raytrace_axis_view_of_uniform_cube(O):
+    """Uniform cube viewed along +z with pixels equal to cells: every pixel
+    sees I = S (1 - exp(-tau)) with S = eta / chi (Eqs. 12-14, R9)."""
+    n = 4
+    m = W.uniform_cube(n=n, tau_cell=0.3, nf=6, albedo=0.0)
+    T = np.full((1, m.ncell), 300.0)
+    cam = W.Camera(0.0, 0.0, n, 1e20, m.cell)
+    fidx = [1, 4]
+    img, sed = O.raytrace(m, T, None, 0.0, [cam], fidx)
+    chi = m.rho[0, 0, 0, 0] * (m.kabs[0] + m.ksca[0])
+    for f, j in enumerate(fidx):
+        x = H * m.nu[j] / (K * 300.0)
+        B = 2 * H * m.nu[j] ** 3 / 2.99792458e10 ** 2 / math.expm1(x)
+        S = m.rho[0, 0, 0, 0] * m.kabs[0, j] * B / chi[j]
+        I = S * (1 - math.exp(-chi[j] * n * m.cell))
+        np.testing.assert_allclose(img[0, f], I, rtol=1e-10)
+
+
+def test_raytrace_optically_thin_flux_and_star(O):
+    n = 4
+    m = W.uniform_cube(n=n, tau_cell=1e-9, nf=6, albedo=0.0)
+    T = np.full((1, m.ncell), 500.0)
+    D = 1e20
+    cam = W.Camera(0.0, 0.0, n, D, m.cell)
+    fidx = [0, 3, 5]
+    _, sed = O.raytrace(m, T, None, 0.0, [cam], fidx)
+    lnu = O.source_lnu(m)
+    V = m.cell ** 3
+    for f, j in enumerate(fidx):
+        x = H * m.nu[j] / (K * 500.0)
+        B = 2 * H * m.nu[j] ** 3 / 2.99792458e10 ** 2 / math.expm1(x)
+        eta = m.rho[0, 0, 0, 0] * m.kabs[0, j] * B
+        star = lnu[j] / (4 * math.pi * D * D)
+        assert sed[0, f] == pytest.approx(m.ncell * eta * V / D ** 2 + star, rel=1e-6)
+    # dark screen: cold dust, only the attenuated star; tau along +z from the
+    # centre to the face is chi * (n/2) cells
+    m2 = W.uniform_cube(n=n, tau_cell=0.7, nf=6, albedo=0.0)
+    T0 = np.zeros((1, m2.ncell))
+    for th, ph, dist in [(0.0, 0.0, n / 2), (math.pi / 2, 0.0, n / 2),
+                         (math.acos(1 / math.sqrt(3)), math.pi / 4, n / 2 * math.sqrt(3))]:
+        _, sd = O.raytrace(m2, T0, None, 0.0, [W.Camera(th, ph, 4, D)], fidx)
+        for f, j in enumerate(fidx):
+            tau = m2.rho[0, 0, 0, 0] * (m2.kabs[0, j] + m2.ksca[0, j]) * dist * m2.cell
+            assert sd[0, f] == pytest.approx(lnu[j] * math.exp(-tau) / (4 * math.pi * D * D),
+                                             rel=1e-9)
+
+
+def test_scattering_source_normalisation(O):
+    """Eq. 16 with the HG phase function normalised per steradian: the same
+    scattering event in every cell of an optically thin cube, seen from many
+    directions, integrates to N xi / dnu; with g = 0 every direction sees
+    N xi / (4 pi dnu D^2) (thermal emission and direct light off)."""
+    n = 3
+    m = W.uniform_cube(n=n, tau_cell=1e-10, nf=5, albedo=1.0, g=0.6)
+    T0 = np.zeros((1, m.ncell))
+    ev = np.zeros(m.ncell, dtype=O.EVENT_DTYPE)
+    ev["cell"] = np.arange(m.ncell)
+    ev["nu"] = 2
+    ev["k"] = [0.0, 0.6, 0.8]
+    m.sources[0].L = 1e-300            # no direct light
+    xi, D = 3.0e20, 1e18
+    npix = 48
+    dirs = _fib_sphere(300)
+    tot = 0.0
+    for k in dirs:
+        th, ph = math.acos(np.clip(k[2], -1, 1)), math.atan2(k[1], k[0])
+        _, sd = O.raytrace(m, T0, ev, xi, [W.Camera(th, ph, npix, D)], [2])
+        tot += sd[0, 0]
+    integral = tot / len(dirs) * 4 * math.pi * D * D     # int F D^2 dOmega
+    assert integral == pytest.approx(m.ncell * xi / m.dnu[2], rel=1e-2)
+    m.g[:] = 0.0
+    for k in dirs[:6]:
+        th, ph = math.acos(np.clip(k[2], -1, 1)), math.atan2(k[1], k[0])
+        _, sd = O.raytrace(m, T0, ev, xi, [W.Camera(th, ph, npix, D)], [2])
+        assert sd[0, 0] == pytest.approx(m.ncell * xi / (4 * math.pi * m.dnu[2] * D * D), rel=3e-3)
+    # axis view with pixels equal to cells: the pixel sum is exact
+    _, sd = O.raytrace(m, T0, ev, xi, [W.Camera(0.0, 0.0, n, D, m.cell)], [2])
+    assert sd[0, 0] == pytest.approx(m.ncell * xi / (4 * math.pi * m.dnu[2] * D * D), rel=1e-8)
+
+
+def _loss(O, m, T, ev, xi, cams, fidx, wi, ws):
+    img, sed = O.raytrace(m, T, ev, xi, cams, fidx)
+    return float((wi * img).sum() + (ws * sed).sum())
+
+
+def test_adjoint_matches_central_differences(O):
+    m = W.random_grid(n=(5, 4, 3), ns=2, nf=6, seed=3, tau_scale=1.5, albedo=(0.2, 0.6))
+    rng = np.random.default_rng(0)
+    T = rng.uniform(50, 900, size=(2, m.ncell))
+    ev = np.zeros(40, dtype=O.EVENT_DTYPE)
+    ev["cell"] = rng.integers(0, m.ncell, 40)
+    ev["nu"] = rng.choice([1, 4], 40)
+    ev["species"] = rng.integers(0, 2, 40)
+    kk = rng.normal(size=(40, 3))
+    ev["k"] = kk / np.linalg.norm(kk, axis=1, keepdims=True)
+    cams = [W.Camera(0.7, 0.3, 5, 3e16), W.Camera(2.0, -1.1, 5, 3e16)]
+    fidx = [1, 4]
+    wi = rng.normal(size=(2, 2, 5, 5))
+    ws = rng.normal(size=(2, 2)) * 1e32
+    xi = 1e28
+    g, gs = O.raytrace_backward(m, T, ev, xi, cams, fidx, wi, ws)
+    base = m.rho.copy()
+    for s, c in [(0, 0), (1, 7), (0, 23), (1, 31), (0, 44), (1, 59)]:
+        flat = base.reshape(2, -1)
+        if flat[s, c] == 0:
+            continue
+        rp, rm = flat.copy(), flat.copy()
+        rp[s, c] = np.float32(flat[s, c] * (1 + 1e-3))
+        rm[s, c] = np.float32(flat[s, c] * (1 - 1e-3))
+        m.rho = rp.reshape(base.shape)
+        Lp = _loss(O, m, T, ev, xi, cams, fidx, wi, ws)
+        m.rho = rm.reshape(base.shape)
+        Lm = _loss(O, m, T, ev, xi, cams, fidx, wi, ws)
+        m.rho = base
+        fd = (Lp - Lm) / (float(rp[s, c]) - float(rm[s, c]))
+        assert g[s, c] == pytest.approx(fd, rel=2e-5, abs=1e-9 * np.abs(g).max())
+    # global scale: dL/dscale from FD on rho * (1 +- h)
+    h = 1e-3
+    m.rho = (base.astype(np.float64) * (1 + h)).astype(np.float32)
+    Lp = _loss(O, m, T, ev, xi, cams, fidx, wi, ws)
+    m.rho = (base.astype(np.float64) * (1 - h)).astype(np.float32)
+    Lm = _loss(O, m, T, ev, xi, cams, fidx, wi, ws)
+    m.rho = base
+    assert gs == pytest.approx((Lp - Lm) / (2 * h), rel=1e-3)
+    assert gs == pytest.approx(float((base.reshape(2, -1).astype(np.float64) * g).sum()), rel=1e-12)
+
+
+def test_adjoint_zero_where_no_ray_passes(O):
+    m = W.uniform_cube(n=6, tau_cell=0.5, nf=4)
+    T = np.full((1, m.ncell), 400.0)
+    cam = W.Camera(0.0, 0.0, 2, 1e20, 0.5 * m.cell)    # tiny image on the axis
+    g, _ = O.raytrace_backward(m, T, None, 0.0, [cam], [1], np.ones((1, 1, 2, 2)), np.zeros((1, 1)))
+    g = g.reshape(6, 6, 6)
+    assert np.all(g[:, 0, :] == 0) and np.all(g[:, :, 0] == 0)
+    assert np.abs(g[:, 2:4, 2:4]).sum() > 0
