@@ -1,0 +1,348 @@
+/*
+ * rtgb — GB300-native Monte Carlo dust radiative transfer
+ * (method of Heymann & Siebenmorgen 2012, arXiv:1203.2941).
+ *
+ * C ABI of librtgb.so.  Every entry point is callable from C; no C++ or
+ * PyTorch type appears here.  Pointers documented as "device" must point to
+ * memory of the context's GPU (cudaMalloc'd or equivalent); "host" pointers are
+ * read during the call and may be released when it returns.
+ *
+ * Streams: every call that launches GPU work takes an rt_stream (a
+ * cudaStream_t; NULL means the legacy default stream) and is asynchronous with
+ * respect to the host unless stated otherwise.  Argument errors are reported
+ * synchronously through the return value; rt_last_error() then holds a
+ * message (thread-local, owned by the library, valid until the next call on
+ * the same thread).  Device-side conditions (capacity overflow, event cap) are
+ * reported through counters in the caller's stats array, readable after the
+ * stream is synchronised.
+ *
+ * Units are CGS throughout: lengths in cm, densities in g/cm^3, opacities in
+ * cm^2/g, frequencies in Hz, luminosities in erg/s, energies deposited per
+ * unit time in erg/s, intensities in erg/s/cm^2/Hz/sr.
+ */
+#ifndef RTGB_H
+#define RTGB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define RT_API __attribute__((visibility("default")))
+#else
+#define RT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* rt_stream;   /* identical to cudaStream_t */
+
+typedef int rt_status;
+enum {
+    RT_OK = 0,
+    RT_ERR_INVALID_ARG = 1,  /* a pointer, size or value was rejected; nothing was launched */
+    RT_ERR_CUDA = 2,         /* a CUDA runtime call failed; message in rt_last_error() */
+    RT_ERR_OOM = 3,          /* device allocation failed */
+    RT_ERR_CAPACITY = 4,     /* a fixed-size buffer is too small for the request */
+    RT_ERR_STUCK = 5,        /* reserved: packets hit the per-packet event cap (see stats) */
+    RT_ERR_STATE = 6         /* handle used with the wrong context or after free */
+};
+
+typedef struct rt_ctx rt_ctx;
+typedef struct rt_grid rt_grid;
+typedef struct rt_opacity rt_opacity;
+typedef struct rt_batch rt_batch;
+
+/* Message for the last failing call on this thread ("" if none). */
+RT_API const char* rt_last_error(void);
+/* Library version string. */
+RT_API const char* rt_version(void);
+
+/* Create a context on CUDA device `device` (it becomes current for the calling
+ * thread).  The context owns small scratch buffers (work counters).  Errors:
+ * RT_ERR_INVALID_ARG (no such device / out == NULL), RT_ERR_CUDA. */
+RT_API rt_status rt_ctx_create(int device, rt_ctx** out);
+RT_API void rt_ctx_destroy(rt_ctx* ctx);
+
+/* ---------------------------------------------------------------------------
+ * Model space (paper Sect. 2: a Cartesian grid of cubes with constant density
+ * per cube, several grain materials).
+ *
+ * rho: [n_species][nz][ny][nx] float32 g/cm^3, x fastest, host OR device
+ * pointer (copied; the caller keeps ownership).  box_min: host [3] cm, lower
+ * corner; cell_size: edge of the cubic cells (cm).  The library keeps its own
+ * copy, re-packed per transport call into an interleaved per-cell layout.
+ * Errors: RT_ERR_INVALID_ARG for non-positive sizes, n_species outside 1..4,
+ * non-finite box or cell, negative or non-finite density (checked on the
+ * device copy, synchronously on `stream`).
+ * ------------------------------------------------------------------------- */
+RT_API rt_status rt_grid_upload(rt_ctx* ctx, int nx, int ny, int nz, int n_species,
+                         const double box_min[3], double cell_size, const float* rho,
+                         rt_stream stream, rt_grid** out);
+RT_API void rt_grid_free(rt_grid* grid);
+
+/* Dust cross sections per unit mass (paper Sect. 2 "absorption kappa_abs and
+ * scattering kappa_sca cross-sections", Henyey-Greenstein g of Eq. 15),
+ * tabulated on one frequency grid shared by the sources and the dust.
+ * nu, dnu: host [n_freq] Hz, nu strictly ascending, dnu > 0 (bin widths).
+ * kabs, ksca, g: host [n_species][n_freq]; kabs, ksca >= 0, |g| < 1.
+ * is_pah: host [n_species] or NULL; a nonzero entry marks a stochastically
+ * heated species (Sect. 2.1) whose absorptions end the packet and are stored.
+ * All arrays are copied.  n_freq in 2..1024, n_species in 1..4. */
+RT_API rt_status rt_opacity_upload(rt_ctx* ctx, int n_freq, const double* nu, const double* dnu,
+                            int n_species, const double* kabs, const double* ksca,
+                            const double* g, const int* is_pah, rt_opacity** out);
+RT_API void rt_opacity_free(rt_opacity* opac);
+
+/* A point source inside the grid.  L_nu: host [n_freq] spectral shape (erg/s/Hz,
+ * any normalisation) or NULL for a blackbody of temperature T_eff.  The
+ * spectrum is normalised so that sum_j L_nu,j dnu_j = L (equal-energy packets,
+ * paper Eq. 1 in expectation). */
+typedef struct {
+    double pos[3];
+    double L;
+    double T_eff;
+    const double* L_nu;
+} rt_source;
+
+/* ---------------------------------------------------------------------------
+ * Photon-packet transport (paper Sects. 2 and 3.1-3.4).
+ * ------------------------------------------------------------------------- */
+enum { RT_MODE_BW = 0,        /* Bjorkman & Wood: T from Eq. 4 after each absorption,
+                                 re-emission from Eq. 10 (Sect. 3.3) */
+       RT_MODE_FROZEN_T = 1,  /* iterative scheme: re-emission from Eq. 5 at T_prev (Sect. 2) */
+       RT_MODE_NOREEMIT = 2 };/* absorbed packets end (pure-absorber diagnostics) */
+enum { RT_LUCY_OFF = 0, RT_LUCY_THIN = 1, RT_LUCY_ALL = 2 };   /* Sect. 3.1 cells */
+enum { RT_LUCY_LINEAR = 0,    /* deposit xi kappa_abs rho l (unbiased path-length form) */
+       RT_LUCY_EXPM1 = 1 };   /* deposit (1 - exp(-kappa_abs rho l)) xi (Eq. 9) */
+enum { RT_PREC_FP32 = 0,      /* production: FP32 transport, FP64 accumulators */
+       RT_PREC_FP64 = 1 };    /* debug: every quantity in FP64 (trajectory parity) */
+enum { RT_SCHED_PERSISTENT = 0, /* all SMs, dynamic packet refill */
+       RT_SCHED_SERIAL = 1 };   /* one GPU thread, packets in id order (debug) */
+
+typedef struct {
+    int mode;                 /* RT_MODE_* */
+    int lucy_mode;            /* RT_LUCY_* */
+    int lucy_form;            /* RT_LUCY_LINEAR / RT_LUCY_EXPM1 */
+    double lucy_tau;          /* THIN: largest face-to-face tau below this (paper: 1e-2) */
+    int mrw;                  /* modified random walk in thick cells (Sect. 3.2) */
+    double mrw_tau_cell;      /* cell tau above which MRW is tried (10) */
+    double mrw_gamma;         /* minimum sphere optical radius (2) */
+    uint64_t seed;            /* Philox key = (seed_lo, seed_hi ^ model_id) */
+    uint32_t model_id;
+    uint64_t n_packets;       /* N; packet energy xi = L / N */
+    uint64_t pid_begin, pid_end;  /* packets simulated: [pid_begin, pid_end) within [0, N) */
+    uint64_t max_events;      /* per-packet interaction cap; capped packets are counted "stuck" */
+    int record_events;        /* store scattering events for the ray tracer (Sect. 2) */
+    int precision;            /* RT_PREC_* */
+    int schedule;             /* RT_SCHED_* */
+    int threads_per_block;    /* 0 = library default */
+    int blocks_per_sm;        /* 0 = occupancy-derived */
+    int march_min_active;     /* lanes still marching below which a warp serves its
+                                 pending interactions (0..31; -1 = default) */
+} rt_transport_params;
+
+/* Fill p with the defaults: B&W, Lucy THIN at 1e-2, linear form, MRW off
+ * (tau 10, gamma 2), seed 1, FP32, persistent, max_events 1e7. */
+RT_API void rt_transport_params_default(rt_transport_params* p);
+
+/* One stored scattering event (20 bytes): cell index, frequency index,
+ * scattering species, model index in a batch, incoming direction. */
+typedef struct {
+    uint32_t cell;
+    uint16_t nu;
+    uint8_t species;
+    uint8_t model;
+    float k[3];
+} rt_event;
+
+/* One stored PAH absorption (Sect. 2.1): cell and frequency index. */
+typedef struct {
+    uint32_t cell;
+    uint16_t nu;
+    uint16_t model;
+} rt_pah_event;
+
+/* Trajectory record (debug/parity): packet id, event number within the
+ * packet, type (RT_TRAJ_*), cell, frequency index after the event, position
+ * (cm) and direction after the event. 72 bytes. */
+typedef struct {
+    uint64_t pid;
+    uint32_t seq, type, cell, nu;
+    double x[3];
+    double k[3];
+} rt_traj;
+enum { RT_TRAJ_EMIT = 0, RT_TRAJ_SCATTER = 1, RT_TRAJ_ABSORB = 2, RT_TRAJ_MRW = 3,
+       RT_TRAJ_ESCAPE = 4, RT_TRAJ_PAH = 5, RT_TRAJ_STUCK = 6, RT_TRAJ_ABSORB_END = 7 };
+
+/* Indices of the uint64 stats array (RT_STAT_COUNT entries, device). */
+enum {
+    RT_STAT_CROSSINGS = 0,    /* packet cell-face crossings */
+    RT_STAT_INTERACTIONS = 1, RT_STAT_SCATTERS = 2, RT_STAT_ABSORPTIONS = 3,
+    RT_STAT_MRW = 4, RT_STAT_ESCAPED = 5, RT_STAT_STUCK = 6, RT_STAT_PAH = 7,
+    RT_STAT_EVENTS_DROPPED = 8, RT_STAT_LUCY = 9, RT_STAT_EMITTED = 10,
+    RT_STAT_PAH_DROPPED = 11, RT_STAT_TRAJ_DROPPED = 12,
+    RT_STAT_N_EVENTS = 13,    /* cursor into events (also counts dropped ones) */
+    RT_STAT_N_PAH = 14, RT_STAT_N_TRAJ = 15,
+    RT_STAT_COUNT = 16
+};
+
+/* Caller-owned device outputs.  All are ACCUMULATED into (zero them for a
+ * fresh run); B&W temperatures see the accumulated E_abs, so a run split into
+ * packet ranges continues exactly where the previous call stopped.
+ *   E_abs   [n_species][ncell] double  absorbed power per species and cell
+ *   count   [n_species][ncell] uint32  absorption events
+ *   esq     [n_species][ncell] double  sum of squared deposits, or NULL
+ *   sed_esc [10][n_freq] double        escaped power in 10 bins equal in cos(theta)
+ *   sed_cnt [10][n_freq] uint64        escaped packets
+ *   events/pah/traj: append buffers (NULL with cap 0 to disable); the cursor
+ *           is stats[RT_STAT_N_*]; entries beyond the capacity are counted in
+ *           the *_DROPPED stats and not written.
+ *   stats   [RT_STAT_COUNT] uint64 (required). */
+typedef struct {
+    double* E_abs;
+    uint32_t* count;
+    double* esq;
+    double* sed_esc;
+    uint64_t* sed_cnt;
+    rt_event* events; uint64_t event_cap;
+    rt_pah_event* pah; uint64_t pah_cap;
+    rt_traj* traj; uint64_t traj_cap;
+    uint64_t* stats;
+} rt_transport_out;
+
+/* Transport N = p->n_packets equal-energy packets (packets [pid_begin,
+ * pid_end)) from the sources through the grid: isotropic emission, one
+ * optical depth -ln(u) per flight (Sect. 2 and its footnote), cell traversal
+ * with tau_i = (kabs + ksca) rho l (Eq. 2), interaction distance (Eq. 3),
+ * albedo choice, HG scattering (Eq. 15) with the event store, absorption with
+ * B&W (Eq. 4 + Eq. 10) or frozen-T (Eq. 5) re-emission, Lucy deposits in thin
+ * cells (Sect. 3.1, Eq. 9) and the modified random walk in thick cells
+ * (Sect. 3.2).  T_prev: device [n_species][ncell] double, required in
+ * RT_MODE_FROZEN_T, ignored otherwise.  Sources must lie inside the grid.
+ * Random numbers: Philox4x32-10, key (seed_lo, seed_hi ^ model_id), counter
+ * (draw/2, 0, pid_lo, pid_hi); the k-th draw of a packet is the uniform
+ * ((w >> 11) + 1) 2^-53 (FP64) or ((w >> 40) + 1) 2^-24 (FP32) of 64-bit word
+ * k mod 2 of block k/2.  Errors: RT_ERR_INVALID_ARG (ranges, pointers,
+ * precision/mode combinations), RT_ERR_CUDA. */
+RT_API rt_status rt_transport(rt_ctx* ctx, const rt_grid* grid, const rt_opacity* opac,
+                       const rt_source* sources, int n_sources,
+                       const rt_transport_params* p, const double* T_prev,
+                       const rt_transport_out* out, rt_stream stream);
+
+/* Dust temperatures from Eq. 4: for every species s and cell i, the T with
+ * 4 pi sum_j kabs_s,j B_nu_j(T) dnu_j = E_abs[s][i] / (rho_s,i V); 0 where E or
+ * rho is 0.  FP64 (table start, Newton polish to ~1e-13 relative).
+ * E_abs, T: device [n_species][ncell] double. */
+RT_API rt_status rt_temperatures(rt_ctx* ctx, const rt_grid* grid, const rt_opacity* opac,
+                          const double* E_abs, double* T, rt_stream stream);
+
+/* Initial guess of the iterative scheme (Sect. 2): optically thin gray dust,
+ * T^4 = sum_src L / (16 pi sigma r^2) at the cell centre, capped at 2000 K.
+ * T: device [n_species][ncell] double. */
+RT_API rt_status rt_temperature_guess(rt_ctx* ctx, const rt_grid* grid, const rt_source* sources,
+                               int n_sources, double* T, rt_stream stream);
+
+/* ---------------------------------------------------------------------------
+ * Ray tracer (paper Sect. 4).
+ * ------------------------------------------------------------------------- */
+/* Observer direction (theta, phi) from +z, square image npix x npix, distance
+ * D (cm), pixel size (cm; <= 0: box diagonal / npix so any view fits).  Image
+ * axes e_x' = (-sin phi, cos phi, 0), e_y' = (-cos theta cos phi,
+ * -cos theta sin phi, sin theta); pixel (ix, iy) is centred at
+ * ((ix + 0.5 - npix/2) p, (iy + 0.5 - npix/2) p) about the box centre (Eq. 11). */
+typedef struct {
+    double theta, phi;
+    int npix;
+    double D;
+    double pixel;
+} rt_camera;
+
+/* Images and SEDs from the dust temperatures and the stored scattering events.
+ * Per pixel ray (parallel projection, Eq. 11) marched front to back:
+ * I = sum_k S_k (1 - exp(-dtau_k)) exp(-tau_<k) with dtau = (kabs+ksca) rho l
+ * over the actual chord, S = (eta_th + eta_sca) / ((kabs+ksca) rho),
+ * eta_th = sum_s rho_s kabs_s B_nu(T_s) (Eq. 14 source function),
+ * eta_sca = xi_ev / (V dnu) sum_events P_HG(k_in . k_obs; g) (Eq. 16).
+ * sed[c][f] = sum_pix I A_pix / D^2 (Eq. 17) + sum_src L_nu exp(-tau_src) / (4 pi D^2).
+ *   T: device [n_species][ncell] double;  events: device [n_events] (may be
+ *   NULL if n_events == 0);  xi_ev: power carried by one event (= L/N of the
+ *   transport that stored them);  cams: host [n_cams], all with the same npix;
+ *   freq_idx: host [n_f] indices into the opacity grid, n_f in 1..16;
+ *   images: device [n_cams][n_f][npix][npix] float;  sed: device [n_cams][n_f]
+ *   double;  ray_steps: device uint64 or NULL, incremented by the number of
+ *   ray-cell steps marched.  Scratch: emissivity tables of n_cams * ncell *
+ *   n_f floats are allocated by the context and kept for reuse. */
+RT_API rt_status rt_raytrace(rt_ctx* ctx, const rt_grid* grid, const rt_opacity* opac,
+                      const double* T, const rt_event* events, uint64_t n_events, double xi_ev,
+                      const rt_source* sources, int n_sources, const rt_camera* cams, int n_cams,
+                      const int* freq_idx, int n_f, float* images, double* sed,
+                      uint64_t* ray_steps, rt_stream stream);
+
+/* Adjoint of rt_raytrace with T and the events held fixed (no counterpart in
+ * the paper; added to differentiate images and SEDs with respect to density).
+ * dL_dimg: device [n_cams][n_f][npix][npix] float; dL_dsed: device
+ * [n_cams][n_f] double (either may be NULL = zero).  Accumulates
+ * dL/drho_s,i into dL_drho (device [n_species][ncell] float) and
+ * sum_s,i rho_s,i dL/drho_s,i (the derivative with respect to a global
+ * density scale) into dL_dscale (device, one double).  Per ray the forward
+ * march is recomputed (pass 1: totals, pass 2: gradients); no path is stored.
+ * ray_steps: device uint64 or NULL, incremented by the ray-cell steps of both
+ * passes. */
+RT_API rt_status rt_raytrace_backward(rt_ctx* ctx, const rt_grid* grid, const rt_opacity* opac,
+                               const double* T, const rt_event* events, uint64_t n_events,
+                               double xi_ev, const rt_source* sources, int n_sources,
+                               const rt_camera* cams, int n_cams, const int* freq_idx, int n_f,
+                               const float* dL_dimg, const double* dL_dsed, float* dL_drho,
+                               double* dL_dscale, uint64_t* ray_steps, rt_stream stream);
+
+/* ---------------------------------------------------------------------------
+ * Batched transport: many models of uneven grid size in one persistent launch
+ * (no counterpart in the paper; packets of all models share the warps).
+ * Model m uses Philox model_id = p->model_id + m and packets [0, n_packets).
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    const rt_grid* grid;
+    const rt_source* sources;   /* host [n_sources] */
+    int n_sources;
+    uint64_t n_packets;
+    const double* T_prev;       /* device, frozen-T mode only */
+    rt_transport_out out;
+} rt_model;
+
+/* Prepare a batch: packs every grid, uploads the model table and source
+ * tables (host-synchronous).  The batch keeps pointers to the grids and the
+ * output buffers; they must outlive it.  n_models in 1..4096; all grids share
+ * `opac` and must have its species count. */
+RT_API rt_status rt_batch_create(rt_ctx* ctx, const rt_opacity* opac, int n_models,
+                          const rt_model* models, const rt_transport_params* p,
+                          rt_batch** out);
+/* Launch the batch on `stream`: one memset of the work counter and one
+ * persistent kernel, nothing else (no host synchronisation, no allocation),
+ * so the call can be recorded into a CUDA graph and replayed. */
+RT_API rt_status rt_batch_run(rt_batch* batch, rt_stream stream);
+RT_API void rt_batch_free(rt_batch* batch);
+
+/* Convenience: rt_batch_create + rt_batch_run + release (stream-ordered). */
+RT_API rt_status rt_transport_batched(rt_ctx* ctx, const rt_opacity* opac, int n_models,
+                               const rt_model* models, const rt_transport_params* p,
+                               rt_stream stream);
+
+/* ---------------------------------------------------------------------------
+ * Diagnostics and test hooks.
+ * ------------------------------------------------------------------------- */
+/* Number of CUDA kernel launches this process has issued through the library
+ * (all contexts, all threads), for launch accounting in benchmarks. */
+RT_API uint64_t rt_kernel_launches(void);
+
+/* Philox4x32-10 on the device: for i < n, out[4i..4i+3] = Philox(ctr_i, key)
+ * with ctr_i = (ctr0[0] + i, ctr0[1], ctr0[2], ctr0[3]) (no carry; the caller
+ * keeps ctr0[0] + n below 2^32).  out: device uint32 [4n]. */
+RT_API rt_status rt_philox(rt_ctx* ctx, const uint32_t ctr0[4], const uint32_t key[2], uint64_t n,
+                    uint32_t* out, rt_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RTGB_H */

@@ -1,0 +1,635 @@
+// C ABI of librtgb: handles, argument validation, per-call model tables and
+// launches.  Every computation of the method runs in the kernels of
+// transport.cu, temperature.cu and raytrace.cu; this file only marshals.
+#include <math.h>
+
+#include <atomic>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "rt_internal.cuh"
+
+namespace rtgb {
+
+static thread_local std::string g_err;
+static std::atomic<uint64_t> g_serial{1};
+static std::atomic<uint64_t> g_launches{0};
+
+void count_launches(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+static const int kMagic = 0x72746762;   // "rtgb"
+
+void set_error(const std::string& msg) { g_err = msg; }
+
+rt_status fail(rt_status code, const std::string& msg)
+{
+    g_err = msg;
+    return code;
+}
+
+rt_status cuda_fail(cudaError_t e, const char* what)
+{
+    g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? RT_ERR_OOM : RT_ERR_CUDA;
+}
+
+static bool isfin(double v) { return std::isfinite(v); }
+
+__global__ void check_rho_kernel(const float* rho, size_t n, unsigned int* bad)
+{
+    const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i < n) {
+        const float v = rho[i];
+        if (!(v >= 0.0f) || !isfinite(v)) atomicOr(bad, 1u);
+    }
+}
+
+}  // namespace rtgb
+
+using namespace rtgb;
+
+extern "C" {
+
+const char* rt_last_error(void) { return g_err.c_str(); }
+const char* rt_version(void) { return "rtgb 0.1 (sm_103a)"; }
+uint64_t rt_kernel_launches(void) { return g_launches.load(); }
+
+rt_status rt_ctx_create(int device, rt_ctx** out)
+{
+    if (!out) return fail(RT_ERR_INVALID_ARG, "rt_ctx_create: out is NULL");
+    int n = 0;
+    RT_CUDA(cudaGetDeviceCount(&n));
+    if (device < 0 || device >= n) return fail(RT_ERR_INVALID_ARG, "rt_ctx_create: no such device");
+    RT_CUDA(cudaSetDevice(device));
+    rt_ctx* c = new rt_ctx();
+    std::memset(c, 0, sizeof(*c));
+    c->magic = kMagic;
+    c->device = device;
+    cudaError_t e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (e != cudaSuccess) { delete c; return cuda_fail(e, "cudaDeviceGetAttribute"); }
+    e = cudaMalloc(&c->d_counters, 64 * sizeof(unsigned long long));
+    if (e != cudaSuccess) { delete c; return cuda_fail(e, "cudaMalloc(counters)"); }
+    *out = c;
+    return RT_OK;
+}
+
+void rt_ctx_destroy(rt_ctx* c)
+{
+    if (!c || c->magic != kMagic) return;
+    cudaSetDevice(c->device);
+    cudaFree(c->d_counters);
+    cudaFree(c->d_eta);
+    cudaFree(c->d_bk);
+    cudaFree(c->d_red);
+    c->magic = 0;
+    delete c;
+}
+
+rt_status rt_grid_upload(rt_ctx* ctx, int nx, int ny, int nz, int ns, const double box_min[3],
+                         double cell, const float* rho, rt_stream stream, rt_grid** out)
+{
+    if (!ctx || ctx->magic != kMagic) return fail(RT_ERR_STATE, "rt_grid_upload: bad context");
+    if (!out || !rho || !box_min) return fail(RT_ERR_INVALID_ARG, "rt_grid_upload: NULL pointer");
+    if (nx <= 0 || ny <= 0 || nz <= 0) return fail(RT_ERR_INVALID_ARG, "rt_grid_upload: sizes must be positive");
+    if ((double)nx * ny * nz > 2.0e9) return fail(RT_ERR_INVALID_ARG, "rt_grid_upload: more than 2e9 cells");
+    if (ns < 1 || ns > kMaxSpecies) return fail(RT_ERR_INVALID_ARG, "rt_grid_upload: n_species must be 1..4");
+    if (!(cell > 0.0) || !isfin(cell)) return fail(RT_ERR_INVALID_ARG, "rt_grid_upload: bad cell size");
+    for (int a = 0; a < 3; ++a)
+        if (!isfin(box_min[a])) return fail(RT_ERR_INVALID_ARG, "rt_grid_upload: non-finite box_min");
+    RT_CUDA(cudaSetDevice(ctx->device));
+    rt_grid* g = new rt_grid();
+    std::memset((void*)g, 0, sizeof(*g));
+    g->ctx = ctx; g->nx = nx; g->ny = ny; g->nz = nz; g->ns = ns; g->cell = cell;
+    for (int a = 0; a < 3; ++a) g->box_min[a] = box_min[a];
+    const size_t n = g->ncell() * ns;
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned int* bad = nullptr;
+    cudaError_t e = cudaMalloc(&g->d_rho, n * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(g->d_rho, rho, n * sizeof(float), cudaMemcpyDefault, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&bad, sizeof(unsigned int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(bad, 0, sizeof(unsigned int), s);
+    if (e == cudaSuccess) {
+        check_rho_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g->d_rho, n, bad);
+        count_launches();
+        e = cudaGetLastError();
+    }
+    unsigned int hbad = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, sizeof(unsigned int), cudaMemcpyDeviceToHost, s);
+    if (bad) cudaFreeAsync(bad, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cudaFree(g->d_rho);
+        delete g;
+        return cuda_fail(e, "rt_grid_upload");
+    }
+    if (hbad) {
+        cudaFree(g->d_rho);
+        delete g;
+        return fail(RT_ERR_INVALID_ARG, "rt_grid_upload: density must be finite and >= 0");
+    }
+    *out = g;
+    return RT_OK;
+}
+
+void rt_grid_free(rt_grid* g)
+{
+    if (!g) return;
+    cudaSetDevice(g->ctx->device);
+    cudaFree(g->d_rho);
+    cudaFree(g->d_packed);
+    delete g;
+}
+
+rt_status rt_opacity_upload(rt_ctx* ctx, int nf, const double* nu, const double* dnu, int ns,
+                            const double* kabs, const double* ksca, const double* g,
+                            const int* is_pah, rt_opacity** out)
+{
+    if (!ctx || ctx->magic != kMagic) return fail(RT_ERR_STATE, "rt_opacity_upload: bad context");
+    if (!out || !nu || !dnu || !kabs || !ksca || !g)
+        return fail(RT_ERR_INVALID_ARG, "rt_opacity_upload: NULL pointer");
+    if (nf < 2 || nf > kMaxFreq) return fail(RT_ERR_INVALID_ARG, "rt_opacity_upload: n_freq must be 2..1024");
+    if (ns < 1 || ns > kMaxSpecies) return fail(RT_ERR_INVALID_ARG, "rt_opacity_upload: n_species must be 1..4");
+    for (int j = 0; j < nf; ++j) {
+        if (!(nu[j] > 0.0) || !isfin(nu[j]) || !(dnu[j] > 0.0) || !isfin(dnu[j]))
+            return fail(RT_ERR_INVALID_ARG, "rt_opacity_upload: nu and dnu must be positive and finite");
+        if (j > 0 && !(nu[j] > nu[j - 1]))
+            return fail(RT_ERR_INVALID_ARG, "rt_opacity_upload: nu must be strictly ascending");
+    }
+    for (int i = 0; i < ns * nf; ++i) {
+        if (!(kabs[i] >= 0.0) || !(ksca[i] >= 0.0) || !isfin(kabs[i]) || !isfin(ksca[i]))
+            return fail(RT_ERR_INVALID_ARG, "rt_opacity_upload: kappa must be finite and >= 0");
+        if (!(fabs(g[i]) < 1.0)) return fail(RT_ERR_INVALID_ARG, "rt_opacity_upload: |g| must be < 1");
+    }
+    RT_CUDA(cudaSetDevice(ctx->device));
+    rt_opacity* op = new rt_opacity();
+    op->ctx = ctx; op->nf = nf; op->ns = ns;
+    op->serial = g_serial.fetch_add(1);
+    op->nu.assign(nu, nu + nf);
+    op->dnu.assign(dnu, dnu + nf);
+    op->kabs.assign(kabs, kabs + ns * nf);
+    op->ksca.assign(ksca, ksca + ns * nf);
+    op->g.assign(g, g + ns * nf);
+    op->is_pah.assign(ns, 0);
+    if (is_pah)
+        for (int s = 0; s < ns; ++s) op->is_pah[s] = is_pah[s] != 0;
+    rt_status st = build_opacity_tables(op);
+    if (st != RT_OK) {
+        rt_opacity_free(op);
+        return st;
+    }
+    *out = op;
+    return RT_OK;
+}
+
+void rt_opacity_free(rt_opacity* op)
+{
+    if (!op) return;
+    cudaSetDevice(op->ctx->device);
+    cudaFree(op->d_nu); cudaFree(op->d_dnu); cudaFree(op->d_kabs); cudaFree(op->d_ksca);
+    cudaFree(op->d_g); cudaFree(op->d_opac32); cudaFree(op->d_xh); cudaFree(op->d_wB);
+    cudaFree(op->d_wD); cudaFree(op->d_tinv); cudaFree(op->d_tinv64); cudaFree(op->d_mrwS);
+    delete op;
+}
+
+void rt_transport_params_default(rt_transport_params* p)
+{
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->mode = RT_MODE_BW;
+    p->lucy_mode = RT_LUCY_THIN;
+    p->lucy_form = RT_LUCY_LINEAR;
+    p->lucy_tau = 1e-2;
+    p->mrw = 0;
+    p->mrw_tau_cell = 10.0;
+    p->mrw_gamma = 2.0;
+    p->seed = 1;
+    p->model_id = 0;
+    p->n_packets = 0;
+    p->pid_begin = 0;
+    p->pid_end = 0;
+    p->max_events = 10000000ull;
+    p->record_events = 0;
+    p->precision = RT_PREC_FP32;
+    p->schedule = RT_SCHED_PERSISTENT;
+    p->threads_per_block = 0;
+    p->blocks_per_sm = 0;
+    p->march_min_active = -1;
+}
+
+}  // extern "C"
+
+namespace rtgb {
+
+static rt_status check_params(const rt_transport_params* p)
+{
+    if (!p) return fail(RT_ERR_INVALID_ARG, "transport: params is NULL");
+    if (p->mode < RT_MODE_BW || p->mode > RT_MODE_NOREEMIT) return fail(RT_ERR_INVALID_ARG, "transport: bad mode");
+    if (p->lucy_mode < RT_LUCY_OFF || p->lucy_mode > RT_LUCY_ALL) return fail(RT_ERR_INVALID_ARG, "transport: bad lucy_mode");
+    if (p->lucy_form != RT_LUCY_LINEAR && p->lucy_form != RT_LUCY_EXPM1) return fail(RT_ERR_INVALID_ARG, "transport: bad lucy_form");
+    if (!(p->lucy_tau >= 0.0) || !isfin(p->lucy_tau)) return fail(RT_ERR_INVALID_ARG, "transport: bad lucy_tau");
+    if (p->mrw && (!(p->mrw_tau_cell > 0.0) || !(p->mrw_gamma > 0.0)))
+        return fail(RT_ERR_INVALID_ARG, "transport: MRW thresholds must be positive");
+    if (p->precision != RT_PREC_FP32 && p->precision != RT_PREC_FP64) return fail(RT_ERR_INVALID_ARG, "transport: bad precision");
+    if (p->schedule != RT_SCHED_PERSISTENT && p->schedule != RT_SCHED_SERIAL) return fail(RT_ERR_INVALID_ARG, "transport: bad schedule");
+    if (p->n_packets == 0) return fail(RT_ERR_INVALID_ARG, "transport: n_packets must be > 0");
+    if (p->march_min_active < -1 || p->march_min_active > 31) return fail(RT_ERR_INVALID_ARG, "transport: march_min_active must be -1..31");
+    if (p->threads_per_block != 0 && (p->threads_per_block % 32 != 0 || p->threads_per_block > 256 || p->threads_per_block < 32))
+        return fail(RT_ERR_INVALID_ARG, "transport: threads_per_block must be a multiple of 32 in 32..256");
+    if (p->blocks_per_sm < 0 || p->blocks_per_sm > 64) return fail(RT_ERR_INVALID_ARG, "transport: blocks_per_sm must be 0..64");
+    if (p->max_events == 0) return fail(RT_ERR_INVALID_ARG, "transport: max_events must be > 0");
+    return RT_OK;
+}
+
+static rt_status check_out(const rt_transport_out* o)
+{
+    if (!o) return fail(RT_ERR_INVALID_ARG, "transport: out is NULL");
+    if (!o->E_abs || !o->count || !o->sed_esc || !o->sed_cnt || !o->stats)
+        return fail(RT_ERR_INVALID_ARG, "transport: E_abs, count, sed_esc, sed_cnt and stats are required");
+    if ((o->event_cap && !o->events) || (o->pah_cap && !o->pah) || (o->traj_cap && !o->traj))
+        return fail(RT_ERR_INVALID_ARG, "transport: buffer with capacity but NULL pointer");
+    return RT_OK;
+}
+
+// Host-side staging of one model: its descriptor and source tables.
+struct HostModel {
+    ModelDev md;
+    std::vector<double> pos, Lcdf, cdf64;
+    std::vector<float> cdf32;
+};
+
+static rt_status make_model(const rt_grid* g, const rt_opacity* op, const rt_source* src, int nsrc,
+                            uint64_t n_packets, uint64_t pid_begin, uint32_t model_id, int model_index,
+                            const double* T_prev, const rt_transport_out* o, HostModel& hm)
+{
+    if (!src || nsrc < 1 || nsrc > 64) return fail(RT_ERR_INVALID_ARG, "transport: need 1..64 sources");
+    const int nf = op->nf;
+    double Ltot = 0.0;
+    hm.pos.resize(3 * nsrc);
+    hm.Lcdf.resize(nsrc);
+    hm.cdf64.resize((size_t)nsrc * nf);
+    hm.cdf32.resize((size_t)nsrc * nf);
+    std::vector<double> lnu;
+    const double hi[3] = { g->box_min[0] + g->nx * g->cell, g->box_min[1] + g->ny * g->cell,
+                           g->box_min[2] + g->nz * g->cell };
+    for (int i = 0; i < nsrc; ++i) {
+        const rt_source& s = src[i];
+        if (!(s.L >= 0.0) || !isfin(s.L)) return fail(RT_ERR_INVALID_ARG, "transport: source L must be >= 0");
+        if (!s.L_nu && !(s.T_eff > 0.0)) return fail(RT_ERR_INVALID_ARG, "transport: blackbody source needs T_eff > 0");
+        if (s.L_nu)
+            for (int j = 0; j < nf; ++j)
+                if (!(s.L_nu[j] >= 0.0) || !isfin(s.L_nu[j]))
+                    return fail(RT_ERR_INVALID_ARG, "transport: L_nu must be finite and >= 0");
+        for (int a = 0; a < 3; ++a) {
+            if (!(s.pos[a] >= g->box_min[a] && s.pos[a] <= hi[a]))
+                return fail(RT_ERR_INVALID_ARG, "transport: sources must lie inside the grid");
+            hm.pos[3 * i + a] = (s.pos[a] - g->box_min[a]) / g->cell;
+        }
+        source_spectrum(op, s, lnu);
+        double acc = 0.0;
+        for (int j = 0; j < nf; ++j) {
+            acc += lnu[j] * op->dnu[j];
+            hm.cdf64[(size_t)i * nf + j] = acc;
+        }
+        if (!(acc > 0.0) && s.L > 0.0) return fail(RT_ERR_INVALID_ARG, "transport: source spectrum is zero on the grid");
+        for (int j = 0; j < nf; ++j)
+            hm.cdf32[(size_t)i * nf + j] = acc > 0.0 ? (float)(hm.cdf64[(size_t)i * nf + j] / acc) : 1.0f;
+        hm.cdf32[(size_t)i * nf + nf - 1] = 1.0f;
+        Ltot += s.L;
+        hm.Lcdf[i] = Ltot;
+    }
+    if (!(Ltot > 0.0)) return fail(RT_ERR_INVALID_ARG, "transport: total luminosity must be > 0");
+    ModelDev& m = hm.md;
+    std::memset(&m, 0, sizeof(m));
+    m.rho = g->d_packed;
+    m.nx = g->nx; m.ny = g->ny; m.nz = g->nz;
+    m.model_id = model_id;
+    m.model_index = model_index;
+    m.nsrc = nsrc;
+    m.cell = g->cell;
+    m.vol = g->cell * g->cell * g->cell;
+    m.xi = Ltot / (double)n_packets;
+    m.log2_4piV = 2.0 * log2(g->cell);
+    for (int a = 0; a < 3; ++a) m.box_min[a] = g->box_min[a];
+    m.pid_begin = pid_begin;
+    m.E_abs = o->E_abs; m.count = o->count; m.esq = o->esq;
+    m.sed_esc = o->sed_esc; m.sed_cnt = (unsigned long long*)o->sed_cnt;
+    m.T_prev = T_prev;
+    m.events = o->events; m.event_cap = o->event_cap;
+    m.pah = o->pah; m.pah_cap = o->pah_cap;
+    m.traj = o->traj; m.traj_cap = o->traj_cap;
+    m.stats = (unsigned long long*)o->stats;
+    return RT_OK;
+}
+
+// Device image of a set of models: descriptors, prefix sums and source tables
+// in one allocation.
+struct DeviceModels {
+    void* buf = nullptr;
+    size_t bytes = 0;
+    ModelDev* models = nullptr;
+    unsigned long long* prefix = nullptr;
+    unsigned long long* work = nullptr;
+    unsigned long long total = 0;
+};
+
+static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+static rt_status stage_models(std::vector<HostModel>& hms, const std::vector<uint64_t>& nwork,
+                              int nf, bool async, cudaStream_t s, DeviceModels& dm)
+{
+    const int n = (int)hms.size();
+    size_t off = 0;
+    const size_t o_models = off; off = align_up(off + sizeof(ModelDev) * n, 64);
+    const size_t o_prefix = off; off = align_up(off + sizeof(unsigned long long) * (n + 1), 64);
+    const size_t o_work = off; off = align_up(off + sizeof(unsigned long long) * 2, 64);
+    std::vector<size_t> o_pos(n), o_L(n), o_c64(n), o_c32(n);
+    for (int i = 0; i < n; ++i) {
+        const int ns_ = hms[i].md.nsrc;
+        o_pos[i] = off; off = align_up(off + sizeof(double) * 3 * ns_, 64);
+        o_L[i] = off; off = align_up(off + sizeof(double) * ns_, 64);
+        o_c64[i] = off; off = align_up(off + sizeof(double) * ns_ * nf, 64);
+        o_c32[i] = off; off = align_up(off + sizeof(float) * ns_ * nf, 64);
+    }
+    std::vector<unsigned char> h(off, 0);
+    std::vector<unsigned long long> prefix(n + 1, 0);
+    for (int i = 0; i < n; ++i) prefix[i + 1] = prefix[i] + nwork[i];
+    char* base = nullptr;
+    if (async) RT_CUDA(cudaMallocAsync((void**)&base, off, s));
+    else RT_CUDA(cudaMalloc((void**)&base, off));
+    for (int i = 0; i < n; ++i) {
+        ModelDev md = hms[i].md;
+        std::memcpy(&h[o_pos[i]], hms[i].pos.data(), sizeof(double) * hms[i].pos.size());
+        std::memcpy(&h[o_L[i]], hms[i].Lcdf.data(), sizeof(double) * hms[i].Lcdf.size());
+        std::memcpy(&h[o_c64[i]], hms[i].cdf64.data(), sizeof(double) * hms[i].cdf64.size());
+        std::memcpy(&h[o_c32[i]], hms[i].cdf32.data(), sizeof(float) * hms[i].cdf32.size());
+        md.src_pos = (const double*)(base + o_pos[i]);
+        md.src_Lcdf = (const double*)(base + o_L[i]);
+        md.src_cdf64 = (const double*)(base + o_c64[i]);
+        md.src_cdf32 = (const float*)(base + o_c32[i]);
+        std::memcpy(&h[o_models + sizeof(ModelDev) * i], &md, sizeof(ModelDev));
+    }
+    std::memcpy(&h[o_prefix], prefix.data(), sizeof(unsigned long long) * (n + 1));
+    if (async) {
+        cudaError_t e = cudaMemcpyAsync(base, h.data(), off, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) { cudaFreeAsync(base, s); return cuda_fail(e, "stage models"); }
+    } else {
+        cudaError_t e = cudaMemcpy(base, h.data(), off, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) { cudaFree(base); return cuda_fail(e, "stage models"); }
+    }
+    dm.buf = base;
+    dm.bytes = off;
+    dm.models = (ModelDev*)(base + o_models);
+    dm.prefix = (unsigned long long*)(base + o_prefix);
+    dm.work = (unsigned long long*)(base + o_work);
+    dm.total = prefix[n];
+    return RT_OK;
+}
+
+static void fill_kp(TransportKP& kp, const rt_opacity* op, const rt_transport_params* p,
+                    const DeviceModels& dm, int n_models)
+{
+    std::memset(&kp, 0, sizeof(kp));
+    kp.models = dm.models;
+    kp.prefix = dm.prefix;
+    kp.n_models = n_models;
+    kp.total_work = dm.total;
+    kp.work_ctr = dm.work;
+    kp.nf = op->nf;
+    kp.mode = p->mode;
+    kp.lucy_form = p->lucy_form;
+    kp.mrw = p->mrw;
+    kp.record_events = p->record_events;
+    kp.pah_mask = 0;
+    for (int s = 0; s < op->ns; ++s)
+        if (op->is_pah[s]) kp.pah_mask |= 1 << s;
+    kp.march_min_active = p->march_min_active < 0 ? 8 : p->march_min_active;
+    kp.max_events = p->max_events;
+    kp.seed = p->seed;
+    kp.mrw_tau_cell = p->mrw_tau_cell;
+    kp.mrw_gamma = p->mrw_gamma;
+    kp.opac32 = op->d_opac32;
+    kp.xh = op->d_xh;
+    kp.wre = p->mode == RT_MODE_BW ? op->d_wD : op->d_wB;
+    kp.tinv = op->d_tinv;
+    for (int s = 0; s < kMaxSpecies; ++s) {
+        kp.tinv_y0[s] = s < op->ns ? op->tinv_y0[s] : 0.0f;
+        kp.tinv_inv_dy[s] = s < op->ns ? op->tinv_inv_dy[s] : 0.0f;
+    }
+    kp.mrwS = op->d_mrwS;
+    kp.nu = op->d_nu; kp.dnu = op->d_dnu;
+    kp.kabs = op->d_kabs; kp.ksca = op->d_ksca; kp.g = op->d_g;
+}
+
+}  // namespace rtgb
+
+struct rt_batch {
+    rt_ctx* ctx;
+    const rt_opacity* op;
+    rt_transport_params p;
+    int n_models, ns;
+    DeviceModels dm;
+    TransportKP kp;
+};
+
+extern "C" {
+
+rt_status rt_transport(rt_ctx* ctx, const rt_grid* grid, const rt_opacity* op,
+                       const rt_source* sources, int n_sources, const rt_transport_params* p,
+                       const double* T_prev, const rt_transport_out* out, rt_stream stream)
+{
+    if (!ctx || ctx->magic != kMagic) return fail(RT_ERR_STATE, "rt_transport: bad context");
+    if (!grid || !op) return fail(RT_ERR_INVALID_ARG, "rt_transport: NULL grid or opacity");
+    if (grid->ctx != ctx || op->ctx != ctx) return fail(RT_ERR_STATE, "rt_transport: handle from another context");
+    if (grid->ns != op->ns) return fail(RT_ERR_INVALID_ARG, "rt_transport: grid and opacity species differ");
+    rt_status st = check_params(p);
+    if (st != RT_OK) return st;
+    st = check_out(out);
+    if (st != RT_OK) return st;
+    if (p->pid_end < p->pid_begin || p->pid_end > p->n_packets)
+        return fail(RT_ERR_INVALID_ARG, "rt_transport: need pid_begin <= pid_end <= n_packets");
+    if (p->mode == RT_MODE_FROZEN_T && !T_prev)
+        return fail(RT_ERR_INVALID_ARG, "rt_transport: frozen-T mode needs T_prev");
+    RT_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<HostModel> hms(1);
+    st = make_model(grid, op, sources, n_sources, p->n_packets, p->pid_begin, p->model_id, 0,
+                    T_prev, out, hms[0]);
+    if (st != RT_OK) return st;
+    if (p->pid_end == p->pid_begin) return RT_OK;
+    st = pack_grid(const_cast<rt_grid*>(grid), op, p->lucy_mode, p->lucy_tau, p->precision, s);
+    if (st != RT_OK) return st;
+    hms[0].md.rho = grid->d_packed;
+    DeviceModels dm;
+    st = stage_models(hms, { p->pid_end - p->pid_begin }, op->nf, true, s, dm);
+    if (st != RT_OK) return st;
+    RT_CUDA(cudaMemsetAsync(dm.work, 0, sizeof(unsigned long long), s));
+    TransportKP kp;
+    fill_kp(kp, op, p, dm, 1);
+    const int threads = p->threads_per_block ? p->threads_per_block : 256;
+    st = launch_transport(ctx, op, kp, op->ns, p->precision, p->schedule, threads, p->blocks_per_sm, s);
+    cudaFreeAsync(dm.buf, s);
+    return st;
+}
+
+rt_status rt_batch_create(rt_ctx* ctx, const rt_opacity* op, int n_models, const rt_model* models,
+                          const rt_transport_params* p, rt_batch** out)
+{
+    if (!ctx || ctx->magic != kMagic) return fail(RT_ERR_STATE, "rt_batch_create: bad context");
+    if (!op || !models || !out) return fail(RT_ERR_INVALID_ARG, "rt_batch_create: NULL pointer");
+    if (n_models < 1 || n_models > 4096) return fail(RT_ERR_INVALID_ARG, "rt_batch_create: n_models must be 1..4096");
+    rt_status st = check_params(p);
+    if (st != RT_OK) return st;
+    RT_CUDA(cudaSetDevice(ctx->device));
+    std::vector<HostModel> hms(n_models);
+    std::vector<uint64_t> nwork(n_models);
+    for (int m = 0; m < n_models; ++m) {
+        const rt_model& M = models[m];
+        if (!M.grid || M.grid->ctx != ctx || M.grid->ns != op->ns)
+            return fail(RT_ERR_INVALID_ARG, "rt_batch_create: grid missing, foreign or with other species");
+        if (M.n_packets == 0) return fail(RT_ERR_INVALID_ARG, "rt_batch_create: n_packets must be > 0");
+        if (p->mode == RT_MODE_FROZEN_T && !M.T_prev)
+            return fail(RT_ERR_INVALID_ARG, "rt_batch_create: frozen-T mode needs T_prev for every model");
+        st = check_out(&M.out);
+        if (st != RT_OK) return st;
+        st = pack_grid(const_cast<rt_grid*>(M.grid), op, p->lucy_mode, p->lucy_tau, p->precision, 0);
+        if (st != RT_OK) return st;
+        st = make_model(M.grid, op, M.sources, M.n_sources, M.n_packets, 0, p->model_id + (uint32_t)m, m,
+                        M.T_prev, &M.out, hms[m]);
+        if (st != RT_OK) return st;
+        hms[m].md.rho = M.grid->d_packed;
+        nwork[m] = M.n_packets;
+    }
+    RT_CUDA(cudaDeviceSynchronize());
+    rt_batch* b = new rt_batch();
+    b->ctx = ctx; b->op = op; b->p = *p; b->n_models = n_models; b->ns = op->ns;
+    st = stage_models(hms, nwork, op->nf, false, 0, b->dm);
+    if (st != RT_OK) { delete b; return st; }
+    fill_kp(b->kp, op, p, b->dm, n_models);
+    *out = b;
+    return RT_OK;
+}
+
+rt_status rt_batch_run(rt_batch* b, rt_stream stream)
+{
+    if (!b) return fail(RT_ERR_INVALID_ARG, "rt_batch_run: NULL batch");
+    cudaStream_t s = (cudaStream_t)stream;
+    RT_CUDA(cudaMemsetAsync(b->dm.work, 0, sizeof(unsigned long long), s));
+    const int threads = b->p.threads_per_block ? b->p.threads_per_block : 256;
+    return launch_transport(b->ctx, b->op, b->kp, b->ns, b->p.precision, b->p.schedule, threads,
+                            b->p.blocks_per_sm, s);
+}
+
+void rt_batch_free(rt_batch* b)
+{
+    if (!b) return;
+    cudaSetDevice(b->ctx->device);
+    cudaFree(b->dm.buf);
+    delete b;
+}
+
+rt_status rt_transport_batched(rt_ctx* ctx, const rt_opacity* op, int n_models,
+                               const rt_model* models, const rt_transport_params* p, rt_stream stream)
+{
+    rt_batch* b = nullptr;
+    rt_status st = rt_batch_create(ctx, op, n_models, models, p, &b);
+    if (st != RT_OK) return st;
+    st = rt_batch_run(b, stream);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (st == RT_OK) {
+        cudaFreeAsync(b->dm.buf, s);
+        b->dm.buf = nullptr;
+    }
+    rt_batch_free(b);
+    return st;
+}
+
+rt_status rt_temperatures(rt_ctx* ctx, const rt_grid* grid, const rt_opacity* op,
+                          const double* E_abs, double* T, rt_stream stream)
+{
+    if (!ctx || ctx->magic != kMagic) return fail(RT_ERR_STATE, "rt_temperatures: bad context");
+    if (!grid || !op || !E_abs || !T) return fail(RT_ERR_INVALID_ARG, "rt_temperatures: NULL pointer");
+    if (grid->ctx != ctx || op->ctx != ctx) return fail(RT_ERR_STATE, "rt_temperatures: handle from another context");
+    if (grid->ns != op->ns) return fail(RT_ERR_INVALID_ARG, "rt_temperatures: grid and opacity species differ");
+    RT_CUDA(cudaSetDevice(ctx->device));
+    return launch_temperatures(ctx, grid, op, E_abs, T, (cudaStream_t)stream);
+}
+
+rt_status rt_temperature_guess(rt_ctx* ctx, const rt_grid* grid, const rt_source* src, int nsrc,
+                               double* T, rt_stream stream)
+{
+    if (!ctx || ctx->magic != kMagic) return fail(RT_ERR_STATE, "rt_temperature_guess: bad context");
+    if (!grid || !src || !T || nsrc < 1 || nsrc > 64)
+        return fail(RT_ERR_INVALID_ARG, "rt_temperature_guess: bad arguments");
+    RT_CUDA(cudaSetDevice(ctx->device));
+    std::vector<double> pos(3 * nsrc), L(nsrc);
+    for (int i = 0; i < nsrc; ++i) {
+        for (int a = 0; a < 3; ++a) pos[3 * i + a] = src[i].pos[a];
+        L[i] = src[i].L;
+    }
+    return launch_temperature_guess(ctx, grid, pos.data(), L.data(), nsrc, T, (cudaStream_t)stream);
+}
+
+static rt_status check_rt_args(rt_ctx* ctx, const rt_grid* grid, const rt_opacity* op,
+                               const double* T, const rt_event* ev, uint64_t nev,
+                               const rt_source* src, int nsrc, const rt_camera* cams, int ncam,
+                               const int* fidx, int nfi)
+{
+    if (!ctx || ctx->magic != kMagic) return fail(RT_ERR_STATE, "rt_raytrace: bad context");
+    if (!grid || !op || !T || !cams || !fidx) return fail(RT_ERR_INVALID_ARG, "rt_raytrace: NULL pointer");
+    if (grid->ctx != ctx || op->ctx != ctx) return fail(RT_ERR_STATE, "rt_raytrace: handle from another context");
+    if (grid->ns != op->ns) return fail(RT_ERR_INVALID_ARG, "rt_raytrace: grid and opacity species differ");
+    if (nev > 0 && !ev) return fail(RT_ERR_INVALID_ARG, "rt_raytrace: events NULL with n_events > 0");
+    if (nsrc < 0 || nsrc > 64 || (nsrc > 0 && !src)) return fail(RT_ERR_INVALID_ARG, "rt_raytrace: bad sources");
+    if (ncam < 1 || ncam > 1024) return fail(RT_ERR_INVALID_ARG, "rt_raytrace: n_cams must be 1..1024");
+    if (nfi < 1 || nfi > kMaxImgFreq) return fail(RT_ERR_INVALID_ARG, "rt_raytrace: n_f must be 1..16");
+    for (int f = 0; f < nfi; ++f)
+        if (fidx[f] < 0 || fidx[f] >= op->nf) return fail(RT_ERR_INVALID_ARG, "rt_raytrace: freq_idx out of range");
+    for (int c = 0; c < ncam; ++c) {
+        if (cams[c].npix != cams[0].npix || cams[c].npix < 1 || cams[c].npix > 16384)
+            return fail(RT_ERR_INVALID_ARG, "rt_raytrace: all cameras need the same npix in 1..16384");
+        if (!(cams[c].D > 0.0) || !isfin(cams[c].D) || !isfin(cams[c].theta) || !isfin(cams[c].phi))
+            return fail(RT_ERR_INVALID_ARG, "rt_raytrace: bad camera");
+    }
+    return RT_OK;
+}
+
+rt_status rt_raytrace(rt_ctx* ctx, const rt_grid* grid, const rt_opacity* op, const double* T,
+                      const rt_event* ev, uint64_t nev, double xi_ev, const rt_source* src, int nsrc,
+                      const rt_camera* cams, int ncam, const int* fidx, int nfi, float* images,
+                      double* sed, uint64_t* ray_steps, rt_stream stream)
+{
+    rt_status st = check_rt_args(ctx, grid, op, T, ev, nev, src, nsrc, cams, ncam, fidx, nfi);
+    if (st != RT_OK) return st;
+    if (!images || !sed) return fail(RT_ERR_INVALID_ARG, "rt_raytrace: NULL output");
+    RT_CUDA(cudaSetDevice(ctx->device));
+    return raytrace_impl(ctx, grid, op, T, ev, nev, xi_ev, src, nsrc, cams, ncam, fidx, nfi, images,
+                         sed, nullptr, nullptr, nullptr, nullptr, (unsigned long long*)ray_steps,
+                         false, (cudaStream_t)stream);
+}
+
+rt_status rt_raytrace_backward(rt_ctx* ctx, const rt_grid* grid, const rt_opacity* op,
+                               const double* T, const rt_event* ev, uint64_t nev, double xi_ev,
+                               const rt_source* src, int nsrc, const rt_camera* cams, int ncam,
+                               const int* fidx, int nfi, const float* dimg, const double* dsed,
+                               float* drho, double* dscale, uint64_t* ray_steps, rt_stream stream)
+{
+    rt_status st = check_rt_args(ctx, grid, op, T, ev, nev, src, nsrc, cams, ncam, fidx, nfi);
+    if (st != RT_OK) return st;
+    if (!drho || !dscale) return fail(RT_ERR_INVALID_ARG, "rt_raytrace_backward: NULL output");
+    RT_CUDA(cudaSetDevice(ctx->device));
+    return raytrace_impl(ctx, grid, op, T, ev, nev, xi_ev, src, nsrc, cams, ncam, fidx, nfi, nullptr,
+                         nullptr, dimg, dsed, drho, dscale, (unsigned long long*)ray_steps, true,
+                         (cudaStream_t)stream);
+}
+
+rt_status rt_philox(rt_ctx* ctx, const uint32_t ctr0[4], const uint32_t key[2], uint64_t n,
+                    uint32_t* out, rt_stream stream)
+{
+    if (!ctx || ctx->magic != kMagic) return fail(RT_ERR_STATE, "rt_philox: bad context");
+    if (!ctr0 || !key || !out) return fail(RT_ERR_INVALID_ARG, "rt_philox: NULL pointer");
+    if ((uint64_t)ctr0[0] + n > 0x100000000ull) return fail(RT_ERR_INVALID_ARG, "rt_philox: counter word 0 would wrap");
+    RT_CUDA(cudaSetDevice(ctx->device));
+    return launch_philox(ctr0, key, n, out, (cudaStream_t)stream);
+}
+
+}  // extern "C"

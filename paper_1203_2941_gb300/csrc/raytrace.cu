@@ -1,0 +1,743 @@
+// Ray tracer for images and SEDs (Heymann & Siebenmorgen 2012, Sect. 4) and
+// its adjoint with respect to the cell densities.
+//
+//   eta_th[c][f]       = sum_s rho_s kabs_s(nu_f) B(nu_f, T_s)      (Eq. 14)
+//   eta[cam][c][f]     = eta_th + xi_ev / (V dnu_f) sum_events P_HG(k_in . k_obs)  (Eq. 16)
+//   I(pixel, f)        = sum_k S_k (1 - exp(-dtau_k)) exp(-tau_<k),  S = eta / chi  (Eqs. 12-13)
+//   sed[cam][f]        = sum_pix I A_pix / D^2 + sum_src L_nu exp(-tau_src) / (4 pi D^2)  (Eq. 17)
+//
+// Rays start on the box face nearest the observer (parallel projection,
+// Eq. 11) and march front to back through the grid with an incremental DDA;
+// a ray carries all requested frequencies, so each cell visit loads the
+// density once and the emissivities of all frequencies as contiguous float4s.
+// Optical depths are summed with compensation (Kahan) in FP32.
+#include <math.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "rt_internal.cuh"
+
+namespace rtgb {
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kCamChunk = 16;
+
+struct CamDev {
+    float kobs[3], ex[3], ey[3];
+    float pix_cell;      // pixel size in cells
+    double apix_d2;      // A_pix / D^2
+    int npix;
+};
+
+struct RayKP {
+    const void* rho;           // packed FP32 grid (rho * cell, Lucy sign bit ignored)
+    int nx, ny, nz;
+    float cell;
+    float kext[kMaxSpecies][kMaxImgFreq];   // cm^2/g
+    int nfi, nfp;
+    size_t ncell;
+    const float* eta;          // [ncam_total][ncell][nfp]
+    const float* bk;           // [ns][ncell][nfp] (backward)
+    CamDev cam[kCamChunk];
+    int cam0, ncam;            // cameras of this launch: [cam0, cam0 + ncam)
+    float* img;                // [ncam_total][nfi][npix][npix]
+    const float* dimg;
+    const double* dsed;        // [ncam_total][nfi]
+    float* grad;               // [ns][ncell]
+    unsigned long long* steps; // ray-cell step counter or nullptr
+};
+
+// add a per-thread step count to the counter, one atomic per warp
+__device__ __forceinline__ void count_steps(unsigned long long* ctr, unsigned n)
+{
+    if (!ctr) return;
+    const unsigned mask = __activemask();
+    const unsigned tot = __reduce_add_sync(mask, n);
+    if ((threadIdx.x & 31) == __ffs(mask) - 1 && tot) atomicAdd(ctr, (unsigned long long)tot);
+}
+
+template <int NS> struct PT;
+template <> struct PT<1> { using T = float; };
+template <> struct PT<2> { using T = float2; };
+template <> struct PT<4> { using T = float4; };
+__device__ __forceinline__ void unpack(float v, float* r) { r[0] = fabsf(v); }
+__device__ __forceinline__ void unpack(float2 v, float* r) { r[0] = fabsf(v.x); r[1] = v.y; }
+__device__ __forceinline__ void unpack(float4 v, float* r) { r[0] = fabsf(v.x); r[1] = v.y; r[2] = v.z; r[3] = v.w; }
+
+__device__ __forceinline__ void kahan_add(float& s, float& comp, float v)
+{
+    const float y = v - comp;
+    const float t = s + y;
+    comp = (t - s) - y;
+    s = t;
+}
+
+// (1 - e^-x) / x and its derivative
+__device__ __forceinline__ float phi_f(float x)
+{
+    return x < 1e-4f ? 1.0f - 0.5f * x : -expm1f(-x) / x;
+}
+__device__ __forceinline__ float dphi_f(float x)
+{
+    if (x < 1e-2f) return -0.5f + x * (1.0f / 3.0f) - x * x * 0.125f;
+    return (expf(-x) * (1.0f + x) - 1.0f) / (x * x);
+}
+
+// Ray set-up: origin of pixel (ix, iy) in cell units, box span along kobs.
+struct Ray {
+    float p[3], d[3];          // start point (cell units) and march direction (-kobs)
+    int i[3];
+    float tm[3], td[3];
+    bool hit;
+};
+
+__device__ __forceinline__ void setup_dda(Ray& r, int nx, int ny, int nz)
+{
+    const int n[3] = { nx, ny, nz };
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float f = floorf(r.p[a]);
+        int i = (int)f;
+        if (f == r.p[a] && r.d[a] < 0.0f) i -= 1;
+        r.i[a] = min(max(i, 0), n[a] - 1);
+        if (r.d[a] > 0.0f) {
+            r.td[a] = 1.0f / r.d[a];
+            r.tm[a] = fmaxf(((float)(r.i[a] + 1) - r.p[a]) / r.d[a], 0.0f);
+        } else if (r.d[a] < 0.0f) {
+            r.td[a] = -1.0f / r.d[a];
+            r.tm[a] = fmaxf(((float)r.i[a] - r.p[a]) / r.d[a], 0.0f);
+        } else {
+            r.td[a] = INFINITY;
+            r.tm[a] = INFINITY;
+        }
+    }
+}
+
+// rays from the observer: start on the near face, march along -kobs;
+// reverse = true starts on the far face and marches along +kobs
+__device__ __forceinline__ Ray pixel_ray(const CamDev& cm, int ix, int iy, int nx, int ny, int nz,
+                                         bool reverse)
+{
+    Ray r;
+    const float xp = ((float)ix + 0.5f - 0.5f * cm.npix) * cm.pix_cell;
+    const float yp = ((float)iy + 0.5f - 0.5f * cm.npix) * cm.pix_cell;
+    const float n[3] = { (float)nx, (float)ny, (float)nz };
+    float o[3];
+    float lo = -INFINITY, hi = INFINITY;
+    bool hit = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        o[a] = 0.5f * n[a] + xp * cm.ex[a] + yp * cm.ey[a];
+        const float k = cm.kobs[a];
+        if (k != 0.0f) {
+            float s1 = (0.0f - o[a]) / k, s2 = (n[a] - o[a]) / k;
+            if (s1 > s2) { const float t = s1; s1 = s2; s2 = t; }
+            lo = fmaxf(lo, s1);
+            hi = fminf(hi, s2);
+        } else if (o[a] < 0.0f || o[a] > n[a]) {
+            hit = false;
+        }
+    }
+    r.hit = hit && (lo < hi);
+    const float s0 = reverse ? lo : hi;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        r.p[a] = o[a] + s0 * cm.kobs[a];
+        r.d[a] = reverse ? cm.kobs[a] : -cm.kobs[a];
+    }
+    if (r.hit) setup_dda(r, nx, ny, nz);
+    return r;
+}
+
+// advance to the next cell; returns false when the ray left the grid
+__device__ __forceinline__ bool dda_step(Ray& r, float& tcur, float& seg, int nx, int ny, int nz)
+{
+    const bool ax = (r.tm[0] <= r.tm[1]) && (r.tm[0] <= r.tm[2]);
+    const bool ay = !ax && (r.tm[1] <= r.tm[2]);
+    const float tn = ax ? r.tm[0] : (ay ? r.tm[1] : r.tm[2]);
+    seg = tn - tcur;
+    tcur = tn;
+    if (ax) { r.tm[0] += r.td[0]; r.i[0] += r.d[0] > 0.0f ? 1 : -1; return (unsigned)r.i[0] < (unsigned)nx; }
+    if (ay) { r.tm[1] += r.td[1]; r.i[1] += r.d[1] > 0.0f ? 1 : -1; return (unsigned)r.i[1] < (unsigned)ny; }
+    r.tm[2] += r.td[2]; r.i[2] += r.d[2] > 0.0f ? 1 : -1; return (unsigned)r.i[2] < (unsigned)nz;
+}
+
+template <int NS>
+__device__ __forceinline__ void load_rho(const RayKP& P, int c, float* rho)
+{
+    const typename PT<NS>::T v = __ldg(reinterpret_cast<const typename PT<NS>::T*>(P.rho) + c);
+    float r[4];
+    unpack(v, r);
+#pragma unroll
+    for (int s = 0; s < NS; ++s) rho[s] = r[s];
+}
+
+template <int NFP>
+__device__ __forceinline__ void load_eta(const float* base, float* eta)
+{
+    const float4* q = reinterpret_cast<const float4*>(base);
+#pragma unroll
+    for (int v = 0; v < NFP / 4; ++v) {
+        const float4 t = __ldg(q + v);
+        eta[4 * v] = t.x; eta[4 * v + 1] = t.y; eta[4 * v + 2] = t.z; eta[4 * v + 3] = t.w;
+    }
+}
+
+template <int NS, int NFP>
+__global__ void __launch_bounds__(128) ray_fwd_kernel(const __grid_constant__ RayKP P)
+{
+    const int ci = blockIdx.y;
+    const CamDev& cm = P.cam[ci];
+    const int np = cm.npix;
+    const long long pix = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (pix >= (long long)np * np) return;
+    const int ix = (int)(pix % np), iy = (int)(pix / np);
+    const int cam = P.cam0 + ci;
+    float I[NFP], Ic[NFP], tau[NFP], tc[NFP];
+#pragma unroll
+    for (int f = 0; f < NFP; ++f) { I[f] = 0.f; Ic[f] = 0.f; tau[f] = 0.f; tc[f] = 0.f; }
+    Ray r = pixel_ray(cm, ix, iy, P.nx, P.ny, P.nz, false);
+    unsigned nsteps = 0;
+    if (r.hit) {
+        const float* eta_cam = P.eta + (size_t)cam * P.ncell * P.nfp;
+        float tcur = 0.f, seg;
+        const int maxstep = P.nx + P.ny + P.nz + 4;
+        for (int st = 0; st < maxstep; ++st) {
+            ++nsteps;
+            const int c = (r.i[2] * P.ny + r.i[1]) * P.nx + r.i[0];
+            float rho[NS], eta[NFP];
+            load_rho<NS>(P, c, rho);
+            load_eta<NFP>(eta_cam + (size_t)c * NFP, eta);
+            const bool inside = dda_step(r, tcur, seg, P.nx, P.ny, P.nz);
+            const float seg_phys = seg * P.cell;
+#pragma unroll
+            for (int f = 0; f < NFP; ++f) {
+                float chi = 0.f;
+#pragma unroll
+                for (int s = 0; s < NS; ++s) chi += rho[s] * P.kext[s][f];
+                const float dt = chi * seg;
+                const float contrib = eta[f] * seg_phys * phi_f(dt) * __expf(-tau[f]);
+                kahan_add(I[f], Ic[f], contrib);
+                kahan_add(tau[f], tc[f], dt);
+            }
+            if (!inside) break;
+        }
+    }
+    float* out = P.img + ((size_t)cam * P.nfi) * np * np + pix;
+#pragma unroll
+    for (int f = 0; f < NFP; ++f)
+        if (f < P.nfi) out[(size_t)f * np * np] = I[f];
+    count_steps(P.steps, nsteps);
+}
+
+// Adjoint: pass 1 (front to back) gives tau_total and I_total per frequency;
+// pass 2 walks back to front from the far face, where the attenuation of the
+// observer-side optical depth is exp(-(tau_total - tau_behind_incl)) and the
+// sum of contributions farther than the current cell accumulates directly.
+template <int NS, int NFP>
+__global__ void __launch_bounds__(128) ray_bwd_kernel(const __grid_constant__ RayKP P)
+{
+    const int ci = blockIdx.y;
+    const CamDev& cm = P.cam[ci];
+    const int np = cm.npix;
+    const long long pix = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (pix >= (long long)np * np) return;
+    const int ix = (int)(pix % np), iy = (int)(pix / np);
+    const int cam = P.cam0 + ci;
+    float w[NFP];
+    bool any = false;
+#pragma unroll
+    for (int f = 0; f < NFP; ++f) {
+        float v = 0.f;
+        if (f < P.nfi) {
+            if (P.dimg) v += P.dimg[((size_t)cam * P.nfi + f) * np * np + pix];
+            if (P.dsed) v += (float)(P.dsed[(size_t)cam * P.nfi + f] * cm.apix_d2);
+        }
+        w[f] = v;
+        any = any || v != 0.f;
+    }
+    if (!any) return;
+    Ray r = pixel_ray(cm, ix, iy, P.nx, P.ny, P.nz, false);
+    if (!r.hit) return;
+    const float* eta_cam = P.eta + (size_t)cam * P.ncell * P.nfp;
+    const int maxstep = P.nx + P.ny + P.nz + 4;
+    float tot[NFP], totc[NFP];
+    unsigned nsteps = 0;
+#pragma unroll
+    for (int f = 0; f < NFP; ++f) { tot[f] = 0.f; totc[f] = 0.f; }
+    {
+        float tcur = 0.f, seg;
+        for (int st = 0; st < maxstep; ++st) {
+            ++nsteps;
+            const int c = (r.i[2] * P.ny + r.i[1]) * P.nx + r.i[0];
+            float rho[NS];
+            load_rho<NS>(P, c, rho);
+            const bool inside = dda_step(r, tcur, seg, P.nx, P.ny, P.nz);
+#pragma unroll
+            for (int f = 0; f < NFP; ++f) {
+                float chi = 0.f;
+#pragma unroll
+                for (int s = 0; s < NS; ++s) chi += rho[s] * P.kext[s][f];
+                kahan_add(tot[f], totc[f], chi * seg);
+            }
+            if (!inside) break;
+        }
+    }
+    Ray q = pixel_ray(cm, ix, iy, P.nx, P.ny, P.nz, true);
+    if (!q.hit) { count_steps(P.steps, nsteps); return; }
+    float tb[NFP], tbc[NFP], beh[NFP], behc[NFP];
+#pragma unroll
+    for (int f = 0; f < NFP; ++f) { tb[f] = 0.f; tbc[f] = 0.f; beh[f] = 0.f; behc[f] = 0.f; }
+    float tcur = 0.f, seg;
+    for (int st = 0; st < maxstep; ++st) {
+        ++nsteps;
+        const int c = (q.i[2] * P.ny + q.i[1]) * P.nx + q.i[0];
+        float rho[NS], eta[NFP];
+        load_rho<NS>(P, c, rho);
+        load_eta<NFP>(eta_cam + (size_t)c * NFP, eta);
+        const bool inside = dda_step(q, tcur, seg, P.nx, P.ny, P.nz);
+        const float seg_phys = seg * P.cell;
+        float g[NS];
+#pragma unroll
+        for (int s = 0; s < NS; ++s) g[s] = 0.f;
+#pragma unroll
+        for (int f = 0; f < NFP; ++f) {
+            float chi = 0.f;
+#pragma unroll
+            for (int s = 0; s < NS; ++s) chi += rho[s] * P.kext[s][f];
+            const float dt = chi * seg;
+            kahan_add(tb[f], tbc[f], dt);
+            const float front = fmaxf(tot[f] - tb[f], 0.0f);      // tau between cell and observer
+            const float att = __expf(-front);
+            const float ph = phi_f(dt);
+            const float dph = dphi_f(dt);
+            const float contrib = eta[f] * seg_phys * ph * att;
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                const float bk = P.bk[((size_t)s * P.ncell + c) * NFP + f];
+                const float ke = P.kext[s][f];
+                g[s] += w[f] * ((bk * ph + eta[f] * dph * ke * seg_phys) * seg_phys * att
+                                - ke * seg_phys * beh[f]);
+            }
+            kahan_add(beh[f], behc[f], contrib);
+        }
+#pragma unroll
+        for (int s = 0; s < NS; ++s)
+            if (g[s] != 0.f) atomicAdd(&P.grad[(size_t)s * P.ncell + c], g[s]);
+        if (!inside) break;
+    }
+    count_steps(P.steps, nsteps);
+}
+
+// eta_th (and bk = kabs_s B(T_s) for the adjoint) for every camera's table
+__global__ void eta_thermal_kernel(const float* rho, const double* T, size_t nc, int ns, int nfi, int nfp,
+                                   const double* nu_f, const double* kabs_f /*[ns][nfi]*/, int ncam,
+                                   float* eta, float* bk)
+{
+    const size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (c >= nc) return;
+    const double h = 6.62607015e-27, kb = 1.380649e-16, cl = 2.99792458e10;
+    for (int f = 0; f < nfp; ++f) {
+        double e = 0.0;
+        if (f < nfi) {
+            for (int s = 0; s < ns; ++s) {
+                const double Ts = T[s * nc + c];
+                double B = 0.0;
+                if (Ts > 0.0) {
+                    const double nu = nu_f[f];
+                    B = 2.0 * h * nu * nu * nu / (cl * cl) / expm1(h * nu / (kb * Ts));
+                }
+                const double b = kabs_f[s * nfi + f] * B;
+                e += (double)rho[s * nc + c] * b;
+                if (bk) bk[((size_t)s * nc + c) * nfp + f] = (float)b;
+            }
+        } else if (bk) {
+            for (int s = 0; s < ns; ++s) bk[((size_t)s * nc + c) * nfp + f] = 0.f;
+        }
+        for (int k = 0; k < ncam; ++k) eta[((size_t)k * nc + c) * nfp + f] = (float)e;
+    }
+}
+
+struct ScatKP {
+    int ncam, nfi, nfp;
+    size_t nc;
+    double inv_vol;
+    const float* kobs;         // [ncam][3]
+    const int* f_of_nu;        // [nf] image-frequency slot or -1
+    const double* g;           // [ns][nf]
+    const double* dnu;         // [nf]
+    int nf, ns;
+    double xi;
+};
+
+// eta_sca: every stored event adds xi / (V dnu) P_HG(k_in . k_obs) to its cell
+__global__ void eta_scatter_kernel(const rt_event* ev, uint64_t nev, ScatKP P, float* eta)
+{
+    const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (i >= nev) return;
+    const rt_event e = ev[i];
+    if (e.nu >= P.nf || e.species >= P.ns) return;
+    const int f = P.f_of_nu[e.nu];
+    if (f < 0 || (size_t)e.cell >= P.nc) return;
+    const double g = P.g[e.species * P.nf + e.nu];
+    const double amp = P.xi * P.inv_vol / P.dnu[e.nu];
+    for (int k = 0; k < P.ncam; ++k) {
+        const double cb = (double)e.k[0] * P.kobs[3 * k] + (double)e.k[1] * P.kobs[3 * k + 1] +
+                          (double)e.k[2] * P.kobs[3 * k + 2];
+        const double d = 1.0 + g * g - 2.0 * g * cb;
+        const double ph = (1.0 - g * g) / (4.0 * kPi * d * sqrt(d));
+        atomicAdd(&eta[((size_t)k * P.nc + e.cell) * P.nfp + f], (float)(amp * ph));
+    }
+}
+
+// several image frequencies share one event frequency: handled by a second
+// pass over the remaining duplicate slots
+__global__ void eta_scatter_dup_kernel(const rt_event* ev, uint64_t nev, ScatKP P, const int* dup,
+                                       int ndup, float* eta)
+{
+    const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (i >= nev) return;
+    const rt_event e = ev[i];
+    if ((size_t)e.cell >= P.nc || e.nu >= P.nf || e.species >= P.ns) return;
+    for (int q = 0; q < ndup; ++q) {
+        const int f = dup[2 * q], j = dup[2 * q + 1];
+        if ((int)e.nu != j) continue;
+        const double g = P.g[e.species * P.nf + e.nu];
+        const double amp = P.xi * P.inv_vol / P.dnu[e.nu];
+        for (int k = 0; k < P.ncam; ++k) {
+            const double cb = (double)e.k[0] * P.kobs[3 * k] + (double)e.k[1] * P.kobs[3 * k + 1] +
+                              (double)e.k[2] * P.kobs[3 * k + 2];
+            const double d = 1.0 + g * g - 2.0 * g * cb;
+            const double ph = (1.0 - g * g) / (4.0 * kPi * d * sqrt(d));
+            atomicAdd(&eta[((size_t)k * P.nc + e.cell) * P.nfp + f], (float)(amp * ph));
+        }
+    }
+}
+
+// sed[cam][f] = A_pix / D^2 * sum_pix I  (one block per (cam, f), FP64)
+__global__ void sed_reduce_kernel(const float* img, int nfi, long long npix2, const double* apix_d2,
+                                  double* sed)
+{
+    const int cf = blockIdx.x;
+    const float* p = img + (size_t)cf * npix2;
+    double acc = 0.0;
+    for (long long i = threadIdx.x; i < npix2; i += blockDim.x) acc += (double)p[i];
+    __shared__ double red[256];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) sed[cf] = red[0] * apix_d2[cf / nfi];
+}
+
+struct StarKP {
+    const float* rho;          // unpacked [ns][nc]
+    int nx, ny, nz, ns, nfi;
+    size_t nc;
+    double cell;
+    double kext[kMaxSpecies][kMaxImgFreq];
+    const double* pos_cell;    // [nsrc][3]
+    const double* lnu;         // [nsrc][nfi]
+    const double* kobs;        // [ncam][3]
+    const double* inv4piD2;    // [ncam]
+    int nsrc, ncam;
+    double* sed;               // forward: += L exp(-tau) / (4 pi D^2)
+    const double* dsed;        // backward
+    float* grad;
+};
+
+// Direct light of each source along k_obs (FP64, one thread per (cam, src)).
+// Forward adds it to the SED; backward adds -dL/dF F kext_s l to the gradient.
+__global__ void star_kernel(const __grid_constant__ StarKP P, int backward)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= P.ncam * P.nsrc) return;
+    const int cam = t / P.nsrc, si = t % P.nsrc;
+    const double d[3] = { P.kobs[3 * cam], P.kobs[3 * cam + 1], P.kobs[3 * cam + 2] };
+    const int n[3] = { P.nx, P.ny, P.nz };
+    double tau[kMaxImgFreq];
+    for (int f = 0; f < P.nfi; ++f) tau[f] = 0.0;
+    for (int pass = 0; pass < (backward ? 2 : 1); ++pass) {
+        double x[3];
+        int i[3];
+        bool in = true;
+        for (int a = 0; a < 3; ++a) {
+            x[a] = P.pos_cell[3 * si + a];
+            const double fl = floor(x[a]);
+            int k = (int)fl;
+            if (fl == x[a] && d[a] < 0.0) k -= 1;
+            i[a] = k;
+            in = in && k >= 0 && k < n[a];
+        }
+        while (in) {
+            double best = INFINITY;
+            int ba = 0;
+            for (int a = 0; a < 3; ++a) {
+                double tt;
+                if (d[a] > 0.0) tt = ((double)(i[a] + 1) - x[a]) / d[a];
+                else if (d[a] < 0.0) tt = ((double)i[a] - x[a]) / d[a];
+                else tt = INFINITY;
+                if (tt < 0.0) tt = 0.0;
+                if (tt < best) { best = tt; ba = a; }
+            }
+            const size_t c = ((size_t)i[2] * P.ny + i[1]) * P.nx + i[0];
+            const double l = best * P.cell;
+            if (pass == 0) {
+                for (int f = 0; f < P.nfi; ++f) {
+                    double chi = 0.0;
+                    for (int s = 0; s < P.ns; ++s) chi += (double)P.rho[s * P.nc + c] * P.kext[s][f];
+                    tau[f] += chi * l;
+                }
+            } else {
+                for (int s = 0; s < P.ns; ++s) {
+                    double g = 0.0;
+                    for (int f = 0; f < P.nfi; ++f) {
+                        const double F = P.lnu[si * P.nfi + f] * exp(-tau[f]) * P.inv4piD2[cam];
+                        g -= P.dsed[cam * P.nfi + f] * F * P.kext[s][f] * l;
+                    }
+                    if (g != 0.0) atomicAdd(&P.grad[s * P.nc + c], (float)g);
+                }
+            }
+            for (int b = 0; b < 3; ++b) x[b] += best * d[b];
+            x[ba] = d[ba] > 0.0 ? (double)(i[ba] + 1) : (double)i[ba];
+            i[ba] += d[ba] > 0.0 ? 1 : -1;
+            in = i[ba] >= 0 && i[ba] < n[ba];
+        }
+    }
+    if (!backward)
+        for (int f = 0; f < P.nfi; ++f)
+            atomicAdd(&P.sed[cam * P.nfi + f], P.lnu[si * P.nfi + f] * exp(-tau[f]) * P.inv4piD2[cam]);
+}
+
+// grad_total += grad_call;  dscale += sum rho * grad_call
+__global__ void grad_finish_kernel(const float* rho, const float* g, size_t n, float* drho, double* dscale)
+{
+    double acc = 0.0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const float v = g[i];
+        drho[i] += v;
+        acc += (double)rho[i] * v;
+    }
+    __shared__ double red[256];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(dscale, red[0]);
+}
+
+template <int NS, int NFP>
+void launch_rays(const RayKP& kp, int npix, bool backward, cudaStream_t s)
+{
+    const int th = 128;
+    dim3 grid((unsigned)(((long long)npix * npix + th - 1) / th), kp.ncam);
+    if (backward) ray_bwd_kernel<NS, NFP><<<grid, th, 0, s>>>(kp);
+    else ray_fwd_kernel<NS, NFP><<<grid, th, 0, s>>>(kp);
+    count_launches();
+}
+
+template <int NS>
+void launch_rays_nf(const RayKP& kp, int npix, bool backward, cudaStream_t s)
+{
+    switch (kp.nfp) {
+    case 4: launch_rays<NS, 4>(kp, npix, backward, s); break;
+    case 8: launch_rays<NS, 8>(kp, npix, backward, s); break;
+    case 12: launch_rays<NS, 12>(kp, npix, backward, s); break;
+    default: launch_rays<NS, 16>(kp, npix, backward, s); break;
+    }
+}
+
+template <typename T>
+rt_status grow(T*& p, size_t& cap, size_t n)
+{
+    if (cap >= n && p) return RT_OK;
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    RT_CUDA(cudaMalloc(&p, sizeof(T) * n));
+    cap = n;
+    return RT_OK;
+}
+
+}  // namespace
+
+rt_status raytrace_impl(rt_ctx* ctx, const rt_grid* g, const rt_opacity* op, const double* T,
+                        const rt_event* ev, uint64_t nev, double xi_ev, const rt_source* src,
+                        int nsrc, const rt_camera* cams, int ncam, const int* fidx, int nfi,
+                        float* images, double* sed, const float* dimg, const double* dsed,
+                        float* drho, double* dscale, unsigned long long* ray_steps, bool backward,
+                        cudaStream_t s)
+{
+    const size_t nc = g->ncell();
+    const int ns = g->ns;
+    const int nfp = (nfi + 3) / 4 * 4;
+    // packed FP32 density (any Lucy flagging: the ray tracer ignores the flag)
+    rt_grid* gm = const_cast<rt_grid*>(g);
+    if (!gm->d_packed || gm->packed_prec != RT_PREC_FP32 || gm->packed_opac_serial != op->serial) {
+        rt_status st = pack_grid(gm, op, RT_LUCY_OFF, 0.0, RT_PREC_FP32, s);
+        if (st != RT_OK) return st;
+    }
+    rt_status st = grow(ctx->d_eta, ctx->eta_cap, (size_t)ncam * nc * nfp);
+    if (st != RT_OK) return st;
+    if (backward) {
+        st = grow(ctx->d_bk, ctx->bk_cap, (size_t)ns * nc * nfp + (size_t)ns * nc);
+        if (st != RT_OK) return st;
+    }
+    // host-side per-call tables
+    std::vector<double> nu_f(nfi), kabs_f((size_t)ns * nfi);
+    for (int f = 0; f < nfi; ++f) {
+        nu_f[f] = op->nu[fidx[f]];
+        for (int sp = 0; sp < ns; ++sp) kabs_f[sp * nfi + f] = op->kabs[sp * op->nf + fidx[f]];
+    }
+    std::vector<float> kobs(3 * ncam);
+    std::vector<double> kobs_d(3 * ncam), inv4piD2(ncam), apix_d2(ncam);
+    std::vector<CamDev> cd(ncam);
+    const double diag = g->cell * sqrt((double)g->nx * g->nx + (double)g->ny * g->ny + (double)g->nz * g->nz);
+    for (int c = 0; c < ncam; ++c) {
+        const double st_ = sin(cams[c].theta), ct = cos(cams[c].theta);
+        const double sp = sin(cams[c].phi), cp = cos(cams[c].phi);
+        const double ko[3] = { st_ * cp, st_ * sp, ct };
+        const double ex[3] = { -sp, cp, 0.0 };
+        const double ey[3] = { -ct * cp, -ct * sp, st_ };
+        const double pix = cams[c].pixel > 0.0 ? cams[c].pixel : diag / cams[c].npix;
+        for (int a = 0; a < 3; ++a) {
+            kobs[3 * c + a] = (float)ko[a];
+            kobs_d[3 * c + a] = ko[a];
+            cd[c].kobs[a] = (float)ko[a];
+            cd[c].ex[a] = (float)ex[a];
+            cd[c].ey[a] = (float)ey[a];
+        }
+        cd[c].pix_cell = (float)(pix / g->cell);
+        cd[c].apix_d2 = pix * pix / (cams[c].D * cams[c].D);
+        cd[c].npix = cams[c].npix;
+        inv4piD2[c] = 1.0 / (4.0 * kPi * cams[c].D * cams[c].D);
+        apix_d2[c] = cd[c].apix_d2;
+    }
+    std::vector<int> f_of_nu(op->nf, -1), dup;
+    for (int f = 0; f < nfi; ++f) {
+        if (f_of_nu[fidx[f]] < 0) f_of_nu[fidx[f]] = f;
+        else { dup.push_back(f); dup.push_back(fidx[f]); }
+    }
+    std::vector<double> lnu((size_t)std::max(nsrc, 1) * nfi), spos((size_t)std::max(nsrc, 1) * 3);
+    std::vector<double> spec;
+    for (int i = 0; i < nsrc; ++i) {
+        source_spectrum(op, src[i], spec);
+        for (int f = 0; f < nfi; ++f) lnu[(size_t)i * nfi + f] = spec[fidx[f]];
+        for (int a = 0; a < 3; ++a) spos[3 * i + a] = (src[i].pos[a] - g->box_min[a]) / g->cell;
+    }
+    // one staging allocation for the small tables
+    size_t off = 0;
+    auto take = [&](size_t bytes) { const size_t o = off; off = (off + bytes + 255) / 256 * 256; return o; };
+    const size_t o_nu = take(sizeof(double) * nfi), o_ka = take(sizeof(double) * ns * nfi);
+    const size_t o_ko = take(sizeof(float) * 3 * ncam), o_kd = take(sizeof(double) * 3 * ncam);
+    const size_t o_i4 = take(sizeof(double) * ncam), o_ap = take(sizeof(double) * ncam);
+    const size_t o_fn = take(sizeof(int) * op->nf), o_du = take(sizeof(int) * (dup.size() + 2));
+    const size_t o_ln = take(sizeof(double) * lnu.size()), o_sp = take(sizeof(double) * spos.size());
+    std::vector<unsigned char> h(off, 0);
+    std::memcpy(&h[o_nu], nu_f.data(), sizeof(double) * nfi);
+    std::memcpy(&h[o_ka], kabs_f.data(), sizeof(double) * ns * nfi);
+    std::memcpy(&h[o_ko], kobs.data(), sizeof(float) * 3 * ncam);
+    std::memcpy(&h[o_kd], kobs_d.data(), sizeof(double) * 3 * ncam);
+    std::memcpy(&h[o_i4], inv4piD2.data(), sizeof(double) * ncam);
+    std::memcpy(&h[o_ap], apix_d2.data(), sizeof(double) * ncam);
+    std::memcpy(&h[o_fn], f_of_nu.data(), sizeof(int) * op->nf);
+    if (!dup.empty()) std::memcpy(&h[o_du], dup.data(), sizeof(int) * dup.size());
+    std::memcpy(&h[o_ln], lnu.data(), sizeof(double) * lnu.size());
+    std::memcpy(&h[o_sp], spos.data(), sizeof(double) * spos.size());
+    char* dbuf = nullptr;
+    RT_CUDA(cudaMallocAsync((void**)&dbuf, off, s));
+    RT_CUDA(cudaMemcpyAsync(dbuf, h.data(), off, cudaMemcpyHostToDevice, s));
+
+    float* bk = backward ? ctx->d_bk : nullptr;
+    float* gcall = backward ? ctx->d_bk + (size_t)ns * nc * nfp : nullptr;
+    eta_thermal_kernel<<<(unsigned)((nc + 255) / 256), 256, 0, s>>>(
+        g->d_rho, T, nc, ns, nfi, nfp, (const double*)(dbuf + o_nu), (const double*)(dbuf + o_ka),
+        ncam, ctx->d_eta, bk);
+    count_launches();
+    RT_CUDA(cudaGetLastError());
+    if (nev > 0) {
+        ScatKP sk;
+        sk.ncam = ncam; sk.nfi = nfi; sk.nfp = nfp; sk.nc = nc;
+        sk.inv_vol = 1.0 / (g->cell * g->cell * g->cell);
+        sk.kobs = (const float*)(dbuf + o_ko);
+        sk.f_of_nu = (const int*)(dbuf + o_fn);
+        sk.g = op->d_g; sk.dnu = op->d_dnu; sk.nf = op->nf; sk.ns = ns; sk.xi = xi_ev;
+        const unsigned blocks = (unsigned)((nev + 255) / 256);
+        eta_scatter_kernel<<<blocks, 256, 0, s>>>(ev, nev, sk, ctx->d_eta);
+        count_launches();
+        if (!dup.empty()) {
+            eta_scatter_dup_kernel<<<blocks, 256, 0, s>>>(ev, nev, sk, (const int*)(dbuf + o_du),
+                                                          (int)dup.size() / 2, ctx->d_eta);
+            count_launches();
+        }
+        RT_CUDA(cudaGetLastError());
+    }
+    if (backward) RT_CUDA(cudaMemsetAsync(gcall, 0, sizeof(float) * ns * nc, s));
+
+    RayKP kp;
+    std::memset(&kp, 0, sizeof(kp));
+    kp.rho = g->d_packed;
+    kp.nx = g->nx; kp.ny = g->ny; kp.nz = g->nz;
+    kp.cell = (float)g->cell;
+    for (int sp = 0; sp < ns; ++sp)
+        for (int f = 0; f < nfi; ++f)
+            kp.kext[sp][f] = (float)(op->kabs[sp * op->nf + fidx[f]] + op->ksca[sp * op->nf + fidx[f]]);
+    kp.nfi = nfi; kp.nfp = nfp; kp.ncell = nc;
+    kp.eta = ctx->d_eta; kp.bk = bk;
+    kp.img = images; kp.dimg = dimg; kp.dsed = dsed; kp.grad = gcall;
+    kp.steps = ray_steps;
+    const int npix = cams[0].npix;
+    for (int c0 = 0; c0 < ncam; c0 += kCamChunk) {
+        kp.cam0 = c0;
+        kp.ncam = std::min(kCamChunk, ncam - c0);
+        for (int k = 0; k < kp.ncam; ++k) kp.cam[k] = cd[c0 + k];
+        const int vec = ns == 1 ? 1 : (ns == 2 ? 2 : 4);
+        if (vec == 1) launch_rays_nf<1>(kp, npix, backward, s);
+        else if (vec == 2) launch_rays_nf<2>(kp, npix, backward, s);
+        else launch_rays_nf<4>(kp, npix, backward, s);
+        RT_CUDA(cudaGetLastError());
+    }
+    if (!backward) {
+        sed_reduce_kernel<<<ncam * nfi, 256, 0, s>>>(images, nfi, (long long)npix * npix,
+                                                     (const double*)(dbuf + o_ap), sed);
+        count_launches();
+    }
+    if (nsrc > 0 && (!backward || dsed)) {
+        StarKP sp;
+        std::memset(&sp, 0, sizeof(sp));
+        sp.rho = g->d_rho; sp.nx = g->nx; sp.ny = g->ny; sp.nz = g->nz; sp.ns = ns; sp.nfi = nfi;
+        sp.nc = nc; sp.cell = g->cell;
+        for (int q = 0; q < ns; ++q)
+            for (int f = 0; f < nfi; ++f)
+                sp.kext[q][f] = op->kabs[q * op->nf + fidx[f]] + op->ksca[q * op->nf + fidx[f]];
+        sp.pos_cell = (const double*)(dbuf + o_sp);
+        sp.lnu = (const double*)(dbuf + o_ln);
+        sp.kobs = (const double*)(dbuf + o_kd);
+        sp.inv4piD2 = (const double*)(dbuf + o_i4);
+        sp.nsrc = nsrc; sp.ncam = ncam;
+        sp.sed = sed; sp.dsed = dsed; sp.grad = gcall;
+        const int nt = ncam * nsrc;
+        star_kernel<<<(nt + 63) / 64, 64, 0, s>>>(sp, backward ? 1 : 0);
+        count_launches();
+        RT_CUDA(cudaGetLastError());
+    }
+    if (backward) {
+        const size_t n = (size_t)ns * nc;
+        const unsigned blocks = (unsigned)std::min<size_t>((n + 255) / 256, (size_t)ctx->num_sms * 8);
+        grad_finish_kernel<<<blocks, 256, 0, s>>>(g->d_rho, gcall, n, drho, dscale);
+        count_launches();
+        RT_CUDA(cudaGetLastError());
+    }
+    RT_CUDA(cudaFreeAsync(dbuf, s));
+    return RT_OK;
+}
+
+}  // namespace rtgb

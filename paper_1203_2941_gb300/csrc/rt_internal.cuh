@@ -1,0 +1,181 @@
+// Internal declarations of librtgb: handle layouts, kernel parameter blocks
+// and small device helpers shared by the CUDA translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/rtgb.h"
+
+namespace rtgb {
+
+// ----------------------------------------------------------------- errors
+void set_error(const std::string& msg);
+rt_status fail(rt_status code, const std::string& msg);
+rt_status cuda_fail(cudaError_t e, const char* what);
+#define RT_CUDA(call)                                          \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
+        if (e_ != cudaSuccess) return ::rtgb::cuda_fail(e_, #call); \
+    } while (0)
+
+// ----------------------------------------------------------------- sizes
+constexpr int kMaxSpecies = 4;
+constexpr int kMaxFreq = 1024;
+constexpr int kTinvN = 4096;      // FP32 temperature-inverse table entries per species
+constexpr int kTinv64N = 8192;    // FP64 table used to start the Eq. 4 Newton polish
+constexpr int kMrwN = 2048;       // MRW survival table entries on y in [0, kMrwYmax]
+constexpr double kMrwYmax = 2.0;
+constexpr int kSedBins = 10;
+constexpr int kMaxImgFreq = 16;
+
+}  // namespace rtgb
+
+// ----------------------------------------------------------------- handles
+struct rt_ctx {
+    int magic;
+    int device;
+    int num_sms;
+    unsigned long long* d_counters;   // scratch: work counters [64]
+    // ray-tracer scratch, grown on demand and reused
+    float* d_eta;  size_t eta_cap;    // [ncam][ncell][nfp]
+    float* d_bk;   size_t bk_cap;     // [ns][ncell][nfp] kabs_s B_nu(T_s)
+    double* d_red; size_t red_cap;    // reduction scratch
+};
+
+struct rt_opacity {
+    rt_ctx* ctx;
+    int nf, ns;
+    uint64_t serial;
+    std::vector<double> nu, dnu, kabs, ksca, g;
+    std::vector<int> is_pah;
+    // device tables
+    double* d_nu; double* d_dnu;           // [nf]
+    double* d_kabs; double* d_ksca; double* d_g;  // [ns][nf]
+    float4* d_opac32;                      // [ns][nf] {kext, kabs, ksca, g}
+    float* d_xh;                           // [nf] h nu / k  (K)
+    float* d_wB;                           // [ns][nf] kabs dnu (nu/nu_max)^3 / max
+    float* d_wD;                           // [ns][nf] kabs dnu (nu/nu_max)^4 / max
+    float* d_tinv;                         // [ns][kTinvN] log2 T on uniform log2(P) grid
+    double* d_tinv64;                      // [ns][kTinv64N] ln T on uniform ln(4 pi P) grid
+    float tinv_y0[rtgb::kMaxSpecies], tinv_inv_dy[rtgb::kMaxSpecies];
+    double t64_y0[rtgb::kMaxSpecies], t64_inv_dy[rtgb::kMaxSpecies];
+    float* d_mrwS;                         // [kMrwN] survival S(y)
+};
+
+struct rt_grid {
+    rt_ctx* ctx;
+    int nx, ny, nz, ns;
+    double box_min[3];
+    double cell;
+    float* d_rho;                          // [ns][ncell] as uploaded
+    // packed per-cell layout with the Lucy flag in the sign bit of species 0
+    void* d_packed;
+    int packed_vec;                        // 1, 2 or 4 floats per cell
+    uint64_t packed_opac_serial;
+    int packed_lucy_mode;
+    double packed_lucy_tau;
+    int packed_prec;
+    size_t ncell() const { return (size_t)nx * ny * nz; }
+};
+
+// ----------------------------------------------------------------- kernel parameter blocks
+namespace rtgb {
+
+struct ModelDev {
+    const void* rho;           // packed cells (float, float2 or float4)
+    int nx, ny, nz;
+    uint32_t model_id;
+    int model_index;
+    int nsrc;
+    double cell, vol, xi;
+    double log2_4piV;          // log2(4 pi V / cell) for the packed FP32 density rho*cell
+    double box_min[3];
+    uint64_t pid_begin;
+    const double* src_pos;     // [nsrc][3] in cell units
+    const double* src_Lcdf;    // [nsrc] cumulative luminosity
+    const double* src_cdf64;   // [nsrc][nf] cumulative L_nu dnu
+    const float* src_cdf32;    // [nsrc][nf] cumulative, normalised to 1
+    double* E_abs; uint32_t* count; double* esq;
+    double* sed_esc; unsigned long long* sed_cnt;
+    const double* T_prev;
+    rt_event* events; uint64_t event_cap;
+    rt_pah_event* pah; uint64_t pah_cap;
+    rt_traj* traj; uint64_t traj_cap;
+    unsigned long long* stats;
+};
+
+struct TransportKP {
+    const ModelDev* models;
+    const unsigned long long* prefix;   // [n_models + 1] work-index prefix
+    int n_models;
+    unsigned long long total_work;
+    unsigned long long* work_ctr;
+    int nf;
+    int mode, lucy_form, mrw, record_events;
+    int pah_mask;
+    int march_min_active;
+    unsigned long long max_events;
+    uint64_t seed;
+    double mrw_tau_cell, mrw_gamma;
+    // opacity tables
+    const float4* opac32;
+    const float* xh;
+    const float* wre;                   // wB (frozen T) or wD (B&W)
+    const float* tinv;
+    float tinv_y0[kMaxSpecies], tinv_inv_dy[kMaxSpecies];
+    const float* mrwS;
+    const double* nu; const double* dnu;
+    const double* kabs; const double* ksca; const double* g;
+};
+
+// ----------------------------------------------------------------- device helpers
+#ifdef __CUDACC__
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw 2011): ten rounds, each with two
+// 32x32 products whose halves are permuted and xored with the counter words
+// and a Weyl-sequence key.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t a = 0xD2511F53u * c.x, ah = __umulhi(0xD2511F53u, c.x);
+        const uint32_t b = 0xCD9E8D57u * c.z, bh = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(bh ^ c.y ^ k.x, b, ah ^ c.w ^ k.y, a);
+        k.x += 0x9E3779B9u;
+        k.y += 0xBB67AE85u;
+    }
+    return c;
+}
+#endif
+
+}  // namespace rtgb
+
+// ----------------------------------------------------------------- cross-TU host entry points
+namespace rtgb {
+rt_status build_opacity_tables(rt_opacity* op);
+rt_status pack_grid(rt_grid* g, const rt_opacity* op, int lucy_mode, double lucy_tau, int prec,
+                    cudaStream_t s);
+rt_status launch_transport(rt_ctx* ctx, const rt_opacity* op, const TransportKP& kp,
+                           int ns, int prec, int schedule, int threads, int blocks_per_sm,
+                           cudaStream_t s);
+rt_status launch_temperatures(rt_ctx* ctx, const rt_grid* g, const rt_opacity* op,
+                              const double* E, double* T, cudaStream_t s);
+rt_status launch_temperature_guess(rt_ctx* ctx, const rt_grid* g, const double* src_pos,
+                                   const double* src_L, int nsrc, double* T, cudaStream_t s);
+rt_status raytrace_impl(rt_ctx* ctx, const rt_grid* g, const rt_opacity* op, const double* T,
+                        const rt_event* ev, uint64_t nev, double xi_ev, const rt_source* src,
+                        int nsrc, const rt_camera* cams, int ncam, const int* fidx, int nfi,
+                        float* images, double* sed, const float* dimg, const double* dsed,
+                        float* drho, double* dscale, unsigned long long* ray_steps, bool backward,
+                        cudaStream_t s);
+rt_status launch_philox(const uint32_t ctr0[4], const uint32_t key[2], uint64_t n, uint32_t* out,
+                        cudaStream_t s);
+// launch accounting (rt_kernel_launches)
+void count_launches(unsigned n = 1);
+// host helpers
+double planck_B_host(double nu, double T);
+void source_spectrum(const rt_opacity* op, const rt_source& src, std::vector<double>& lnu);
+}  // namespace rtgb

@@ -1,0 +1,202 @@
+// Host-side construction of the per-opacity device tables:
+//  * float4 {kext, kabs, ksca, g} per species and frequency,
+//  * re-emission weights for the Eq. 5 (B) and Eq. 10 (dB/dT) CDFs in a
+//    scaled form that stays inside FP32 range,
+//  * inverse Planck-mean tables (Eq. 4): log2 T on a uniform grid of
+//    log2(4 pi sum_j kabs_j B_j(T) dnu_j) for the FP32 transport and ln T on a
+//    uniform ln grid for the FP64 temperature solve,
+//  * the survival function of the modified random walk (Sect. 3.2).
+#include <math.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "rt_internal.cuh"
+
+namespace rtgb {
+
+static const double kH = 6.62607015e-27;   // erg s
+static const double kK = 1.380649e-16;     // erg / K
+static const double kC = 2.99792458e10;    // cm / s
+static const double kPi = 3.14159265358979323846;
+
+double planck_B_host(double nu, double T)
+{
+    if (T <= 0.0) return 0.0;
+    const double x = kH * nu / (kK * T);
+    return 2.0 * kH * nu * nu * nu / (kC * kC) / expm1(x);
+}
+
+void source_spectrum(const rt_opacity* op, const rt_source& src, std::vector<double>& lnu)
+{
+    lnu.assign(op->nf, 0.0);
+    double tot = 0.0;
+    for (int j = 0; j < op->nf; ++j) {
+        lnu[j] = src.L_nu ? src.L_nu[j] : planck_B_host(op->nu[j], src.T_eff);
+        tot += lnu[j] * op->dnu[j];
+    }
+    for (int j = 0; j < op->nf; ++j) lnu[j] = tot > 0.0 ? src.L * lnu[j] / tot : 0.0;
+}
+
+// ln(4 pi sum_j kabs_j B(nu_j, T) dnu_j) by log-sum-exp (no underflow at low T);
+// lnc[j] = ln(kabs_j dnu_j 2 h nu_j^3 / c^2) (or -inf), x1[j] = h nu_j / k.
+static double ln_emission(const std::vector<double>& lnc, const std::vector<double>& x1, double T)
+{
+    const size_t nf = lnc.size();
+    double mx = -INFINITY;
+    double t[rtgb::kMaxFreq];
+    for (size_t j = 0; j < nf; ++j) {
+        if (!std::isfinite(lnc[j])) { t[j] = -INFINITY; continue; }
+        const double x = x1[j] / T;
+        const double lnexpm1 = x > 30.0 ? x + log1p(-exp(-x)) : log(expm1(x));
+        t[j] = lnc[j] - lnexpm1;
+        mx = std::max(mx, t[j]);
+    }
+    if (!std::isfinite(mx)) return -INFINITY;
+    double acc = 0.0;
+    for (size_t j = 0; j < nf; ++j)
+        if (std::isfinite(t[j])) acc += exp(t[j] - mx);
+    return log(4.0 * kPi) + mx + log(acc);
+}
+
+// Invert a monotone increasing dense table (lnT_i, z_i) at uniform z targets
+// by linear interpolation between the bracketing dense points.
+static void invert_dense(const std::vector<double>& lnT, const std::vector<double>& z, double z0,
+                         double dz, int n, std::vector<double>& out)
+{
+    out.resize(n);
+    size_t k = 0;
+    for (int i = 0; i < n; ++i) {
+        const double zt = z0 + i * dz;
+        while (k + 2 < z.size() && z[k + 1] < zt) ++k;
+        const double a = z[k], b = z[k + 1];
+        const double w = b > a ? std::min(1.0, std::max(0.0, (zt - a) / (b - a))) : 0.0;
+        out[i] = lnT[k] + w * (lnT[k + 1] - lnT[k]);
+    }
+}
+
+// Survival probability of the walk from the centre of an absorbing sphere:
+// S(y) = 2 sum_n (-1)^(n+1) exp(-n^2 pi^2 y) = 1 - theta_4 written, for small
+// y, through its Poisson-summed form 1 - (2/sqrt(pi y)) sum_m exp(-(m+1/2)^2/y).
+static double mrw_S(double y)
+{
+    if (y <= 0.0) return 1.0;
+    double s = 0.0;
+    if (y < 0.08) {
+        for (int m = 0; m < 40; ++m) {
+            const double e = exp(-(m + 0.5) * (m + 0.5) / y);
+            s += e;
+            if (e < 1e-300) break;
+        }
+        return 1.0 - 2.0 / sqrt(kPi * y) * s;
+    }
+    for (int n = 1; n < 100; ++n) {
+        const double e = exp(-(double)n * n * kPi * kPi * y);
+        s += (n % 2) ? e : -e;
+        if (e < 1e-20) break;
+    }
+    return 2.0 * s;
+}
+
+rt_status build_opacity_tables(rt_opacity* op)
+{
+    const int nf = op->nf, ns = op->ns;
+    const size_t sf = (size_t)ns * nf;
+    std::vector<float4> o32(sf);
+    std::vector<float> xh(nf), wB(sf), wD(sf);
+    double numax = op->nu[nf - 1];
+    for (int j = 0; j < nf; ++j) xh[j] = (float)(kH * op->nu[j] / kK);
+    for (int s = 0; s < ns; ++s) {
+        double mb = 0.0, md = 0.0;
+        std::vector<double> b(nf), d(nf);
+        for (int j = 0; j < nf; ++j) {
+            const double r = op->nu[j] / numax;
+            b[j] = op->kabs[s * nf + j] * op->dnu[j] * r * r * r;
+            d[j] = b[j] * r;
+            mb = std::max(mb, b[j]);
+            md = std::max(md, d[j]);
+        }
+        for (int j = 0; j < nf; ++j) {
+            const double ka = op->kabs[s * nf + j], ks = op->ksca[s * nf + j];
+            o32[s * nf + j] = make_float4((float)(ka + ks), (float)ka, (float)ks,
+                                          (float)op->g[s * nf + j]);
+            wB[s * nf + j] = mb > 0.0 ? (float)(b[j] / mb) : 0.0f;
+            wD[s * nf + j] = md > 0.0 ? (float)(d[j] / md) : 0.0f;
+        }
+    }
+
+    // inverse emission tables from a dense forward table in ln T
+    const double lnTlo = log(0.1), lnThi = log(1.0e6);
+    const int ndense = 1 << 16;
+    std::vector<float> tinv((size_t)ns * kTinvN);
+    std::vector<double> tinv64((size_t)ns * kTinv64N);
+    std::vector<double> lnTd(ndense), zd(ndense), inv;
+    std::vector<double> x1(nf), lnc(nf);
+    for (int j = 0; j < nf; ++j) x1[j] = kH * op->nu[j] / kK;
+    for (int s = 0; s < ns; ++s) {
+        for (int j = 0; j < nf; ++j) {
+            const double ka = op->kabs[s * nf + j];
+            lnc[j] = ka > 0.0 ? log(ka) + log(op->dnu[j]) + log(2.0 * kH / (kC * kC)) +
+                                    3.0 * log(op->nu[j])
+                              : -INFINITY;
+        }
+        bool ok = true;
+        for (int i = 0; i < ndense; ++i) {
+            lnTd[i] = lnTlo + (lnThi - lnTlo) * i / (ndense - 1);
+            zd[i] = ln_emission(lnc, x1, exp(lnTd[i]));
+            if (!std::isfinite(zd[i]) || (i > 0 && !(zd[i] > zd[i - 1]))) ok = false;
+        }
+        if (!ok) {
+            // a species without absorption: temperatures stay at the table floor
+            for (int i = 0; i < kTinvN; ++i) tinv[(size_t)s * kTinvN + i] = (float)(lnTlo / log(2.0));
+            for (int i = 0; i < kTinv64N; ++i) tinv64[(size_t)s * kTinv64N + i] = lnTlo;
+            op->tinv_y0[s] = 0.0f; op->tinv_inv_dy[s] = 0.0f;
+            op->t64_y0[s] = 0.0; op->t64_inv_dy[s] = 0.0;
+            continue;
+        }
+        const double zlo = zd[0], zhi = zd[ndense - 1];
+        const double dy = (zhi - zlo) / log(2.0) / (kTinvN - 1);
+        invert_dense(lnTd, zd, zlo, dy * log(2.0), kTinvN, inv);
+        for (int i = 0; i < kTinvN; ++i) tinv[(size_t)s * kTinvN + i] = (float)(inv[i] / log(2.0));
+        op->tinv_y0[s] = (float)(zlo / log(2.0));
+        op->tinv_inv_dy[s] = (float)(1.0 / dy);
+        const double dz = (zhi - zlo) / (kTinv64N - 1);
+        invert_dense(lnTd, zd, zlo, dz, kTinv64N, inv);
+        for (int i = 0; i < kTinv64N; ++i) tinv64[(size_t)s * kTinv64N + i] = inv[i];
+        op->t64_y0[s] = zlo;
+        op->t64_inv_dy[s] = 1.0 / dz;
+    }
+
+    std::vector<float> mrw(kMrwN);
+    for (int i = 0; i < kMrwN; ++i) mrw[i] = (float)mrw_S(kMrwYmax * i / (kMrwN - 1));
+
+    RT_CUDA(cudaMalloc(&op->d_nu, sizeof(double) * nf));
+    RT_CUDA(cudaMalloc(&op->d_dnu, sizeof(double) * nf));
+    RT_CUDA(cudaMalloc(&op->d_kabs, sizeof(double) * sf));
+    RT_CUDA(cudaMalloc(&op->d_ksca, sizeof(double) * sf));
+    RT_CUDA(cudaMalloc(&op->d_g, sizeof(double) * sf));
+    RT_CUDA(cudaMalloc(&op->d_opac32, sizeof(float4) * sf));
+    RT_CUDA(cudaMalloc(&op->d_xh, sizeof(float) * nf));
+    RT_CUDA(cudaMalloc(&op->d_wB, sizeof(float) * sf));
+    RT_CUDA(cudaMalloc(&op->d_wD, sizeof(float) * sf));
+    RT_CUDA(cudaMalloc(&op->d_tinv, sizeof(float) * tinv.size()));
+    RT_CUDA(cudaMalloc(&op->d_tinv64, sizeof(double) * tinv64.size()));
+    RT_CUDA(cudaMalloc(&op->d_mrwS, sizeof(float) * kMrwN));
+    RT_CUDA(cudaMemcpy(op->d_nu, op->nu.data(), sizeof(double) * nf, cudaMemcpyHostToDevice));
+    RT_CUDA(cudaMemcpy(op->d_dnu, op->dnu.data(), sizeof(double) * nf, cudaMemcpyHostToDevice));
+    RT_CUDA(cudaMemcpy(op->d_kabs, op->kabs.data(), sizeof(double) * sf, cudaMemcpyHostToDevice));
+    RT_CUDA(cudaMemcpy(op->d_ksca, op->ksca.data(), sizeof(double) * sf, cudaMemcpyHostToDevice));
+    RT_CUDA(cudaMemcpy(op->d_g, op->g.data(), sizeof(double) * sf, cudaMemcpyHostToDevice));
+    RT_CUDA(cudaMemcpy(op->d_opac32, o32.data(), sizeof(float4) * sf, cudaMemcpyHostToDevice));
+    RT_CUDA(cudaMemcpy(op->d_xh, xh.data(), sizeof(float) * nf, cudaMemcpyHostToDevice));
+    RT_CUDA(cudaMemcpy(op->d_wB, wB.data(), sizeof(float) * sf, cudaMemcpyHostToDevice));
+    RT_CUDA(cudaMemcpy(op->d_wD, wD.data(), sizeof(float) * sf, cudaMemcpyHostToDevice));
+    RT_CUDA(cudaMemcpy(op->d_tinv, tinv.data(), sizeof(float) * tinv.size(), cudaMemcpyHostToDevice));
+    RT_CUDA(cudaMemcpy(op->d_tinv64, tinv64.data(), sizeof(double) * tinv64.size(),
+                       cudaMemcpyHostToDevice));
+    RT_CUDA(cudaMemcpy(op->d_mrwS, mrw.data(), sizeof(float) * kMrwN, cudaMemcpyHostToDevice));
+    return RT_OK;
+}
+
+}  // namespace rtgb

@@ -1,0 +1,978 @@
+// Photon-packet transport (Heymann & Siebenmorgen 2012, Sects. 2 and 3).
+//
+// One persistent kernel processes all packets of one or many models.  Each
+// lane carries one packet at a time; lanes whose packet ended pull new packet
+// ids with one warp-aggregated atomic.  A warp advances in phases:
+//   refill   lanes without a packet emit a new one (Sect. 2: equal-energy
+//            packet, frequency bin from the source CDF, isotropic direction)
+//   flight   lanes at a new flight origin either take a modified-random-walk
+//            step (Sect. 3.2) or draw tau = -ln(u) and set up the traversal
+//   march    all marching lanes cross cells together (Eq. 2 test against the
+//            remaining tau, Lucy deposits in thin cells, Sect. 3.1) until at
+//            most `march_min_active` lanes are still marching
+//   events   lanes that stopped inside a cell interact (albedo choice, HG
+//            scattering Eq. 15, absorption with B&W Eq. 4 + Eq. 10 or frozen-T
+//            Eq. 5 re-emission); lanes that left the grid tally the escape.
+// Keeping interactions out of the march loop lets the expensive event code
+// run for several lanes at once instead of stalling the crossing lanes.
+//
+// The cell traversal tracks, per flight, the distance to the next x, y and z
+// face (incremental DDA); the cell index is integer-exact and the packet
+// leaves the grid when an index leaves [0, n).  Positions are in cell units
+// relative to the grid corner.  The FP32 kernel reads a packed grid holding
+// rho_s * cell (so the optical depth of a chord is sum_s rho_s kext_s * l
+// with l in cells) with the Lucy flag in the sign bit of species 0; the FP64
+// debug kernel reads rho_s unscaled and follows the same algorithm with every
+// quantity in double precision, reproducing the FP64 CPU reference packet by
+// packet.
+#include <math.h>
+
+#include <algorithm>
+
+#include "rt_internal.cuh"
+
+namespace rtgb {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+enum { ST_NEED = 0, ST_FLIGHT = 1, ST_MARCH = 2, ST_INTERACT = 3, ST_ESCAPE = 4, ST_DONE = 5 };
+enum { C_INT, C_SCA, C_ABS, C_MRW, C_ESC, C_STUCK, C_PAH, C_LUCY, C_EMIT, C_N };
+constexpr double kPi = 3.14159265358979323846;
+
+template <int NS> struct PackedT;
+template <> struct PackedT<1> { using T = float; };
+template <> struct PackedT<2> { using T = float2; };
+template <> struct PackedT<4> { using T = float4; };
+
+__device__ __forceinline__ void unpack(float v, float* r) { r[0] = v; }
+__device__ __forceinline__ void unpack(float2 v, float* r) { r[0] = v.x; r[1] = v.y; }
+__device__ __forceinline__ void unpack(float4 v, float* r) { r[0] = v.x; r[1] = v.y; r[2] = v.z; r[3] = v.w; }
+
+// ------------------------------------------------------------- random numbers
+struct Rng {
+    uint2 key;
+    uint32_t plo, phi, draw, c_lo, c_hi;
+};
+
+__device__ __forceinline__ void rng_init(Rng& r, uint64_t seed, uint32_t model_id, uint64_t pid)
+{
+    r.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32) ^ model_id);
+    r.plo = (uint32_t)pid;
+    r.phi = (uint32_t)(pid >> 32);
+    r.draw = 0;
+}
+
+template <typename R> __device__ __forceinline__ R rng_u(Rng& r);
+
+template <> __device__ __forceinline__ float rng_u<float>(Rng& r)
+{
+    const uint32_t d = r.draw++;
+    uint32_t hi;
+    if ((d & 1u) == 0) {
+        const uint4 b = philox4x32_10(make_uint4(d >> 1, 0u, r.plo, r.phi), r.key);
+        hi = b.y;
+        r.c_hi = b.w;
+    } else {
+        hi = r.c_hi;
+    }
+    return (float)((hi >> 8) + 1u) * 0x1p-24f;
+}
+
+template <> __device__ __forceinline__ double rng_u<double>(Rng& r)
+{
+    const uint32_t d = r.draw++;
+    uint32_t lo, hi;
+    if ((d & 1u) == 0) {
+        const uint4 b = philox4x32_10(make_uint4(d >> 1, 0u, r.plo, r.phi), r.key);
+        lo = b.x; hi = b.y;
+        r.c_lo = b.z; r.c_hi = b.w;
+    } else {
+        lo = r.c_lo; hi = r.c_hi;
+    }
+    const uint64_t w = ((uint64_t)hi << 32) | lo;
+    return (double)((w >> 11) + 1u) * 0x1p-53;
+}
+
+// ------------------------------------------------------------- math shims
+__device__ __forceinline__ float r_log(float x) { return logf(x); }
+__device__ __forceinline__ double r_log(double x) { return log(x); }
+__device__ __forceinline__ float r_exp(float x) { return expf(x); }
+__device__ __forceinline__ double r_exp(double x) { return exp(x); }
+__device__ __forceinline__ float r_expm1(float x) { return expm1f(x); }
+__device__ __forceinline__ double r_expm1(double x) { return expm1(x); }
+__device__ __forceinline__ float r_sqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double r_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ void r_sincos2pi(float z, float* s, float* c) { sincospif(2.0f * z, s, c); }
+__device__ __forceinline__ void r_sincos2pi(double z, double* s, double* c) { sincospi(2.0 * z, s, c); }
+
+// Isotropic direction: phi = 2 pi zeta1, cos(theta) = 1 - 2 zeta2, zeta = 1 - u.
+template <typename R>
+__device__ __forceinline__ void iso_dir(R u1, R u2, R* k)
+{
+    const R mu = R(1) - R(2) * (R(1) - u2);
+    const R st = r_sqrt(fmax(R(0), R(1) - mu * mu));
+    R sp, cp;
+    r_sincos2pi(R(1) - u1, &sp, &cp);
+    k[0] = st * cp;
+    k[1] = st * sp;
+    k[2] = mu;
+}
+
+// Henyey-Greenstein inverse CDF for the cosine of the scattering angle.
+template <typename R>
+__device__ __forceinline__ R hg_mu(R g, R u)
+{
+    const R z = R(1) - u;
+    R mu;
+    if (fabs(g) > R(1e-6)) {
+        const R t = (R(1) - g * g) / (R(1) - g + R(2) * g * z);
+        mu = (R(1) + g * g - t * t) / (R(2) * g);
+    } else {
+        mu = R(2) * z - R(1);
+    }
+    return fmin(R(1), fmax(R(-1), mu));
+}
+
+template <typename R>
+__device__ __forceinline__ void rotate(R* k, R mu, R u_phi)
+{
+    const R st = r_sqrt(fmax(R(0), R(1) - mu * mu));
+    R sp, cp;
+    r_sincos2pi(R(1) - u_phi, &sp, &cp);
+    R n0, n1, n2;
+    if (fabs(k[2]) > R(0.99999)) {
+        n0 = st * cp;
+        n1 = st * sp;
+        n2 = k[2] > R(0) ? mu : -mu;
+    } else {
+        const R t = r_sqrt(R(1) - k[2] * k[2]);
+        n0 = st * (k[0] * k[2] * cp - k[1] * sp) / t + k[0] * mu;
+        n1 = st * (k[1] * k[2] * cp + k[0] * sp) / t + k[1] * mu;
+        n2 = -st * cp * t + k[2] * mu;
+    }
+    const R l = r_sqrt(n0 * n0 + n1 * n1 + n2 * n2);
+    k[0] = n0 / l; k[1] = n1 / l; k[2] = n2 / l;
+}
+
+// ------------------------------------------------------------- Planck (FP64 debug path)
+__device__ __forceinline__ double planck_B(double nu, double T)
+{
+    if (T <= 0.0) return 0.0;
+    const double h = 6.62607015e-27, kb = 1.380649e-16, c = 2.99792458e10;
+    const double x = h * nu / (kb * T);
+    return 2.0 * h * nu * nu * nu / (c * c) / expm1(x);
+}
+
+__device__ __forceinline__ double planck_dBdT(double nu, double T)
+{
+    if (T <= 0.0) return 0.0;
+    const double h = 6.62607015e-27, kb = 1.380649e-16, c = 2.99792458e10;
+    const double x = h * nu / (kb * T);
+    return 2.0 * h * nu * nu * nu / (c * c) * (x / T) / (expm1(x) * (-expm1(-x)));
+}
+
+__device__ double planck_mean64(const TransportKP& P, int s, double T)
+{
+    double acc = 0.0;
+    for (int j = 0; j < P.nf; ++j) acc += P.kabs[s * P.nf + j] * planck_B(P.nu[j], T) * P.dnu[j];
+    return acc;
+}
+
+// Eq. 4 by bisection to 1e-12 relative (debug path; same stopping rule as the
+// FP64 reference so that both return the same root to ~1e-12).
+__device__ double solve_T64(const TransportKP& P, int s, double target)
+{
+    if (!(target > 0.0)) return 0.0;
+    double lo = 0.0, hi = 1.0e5;
+    while (4.0 * kPi * planck_mean64(P, s, hi) < target && hi < 1e12) hi *= 2.0;
+    for (int it = 0; it < 400 && hi - lo > 1e-12 * hi; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (4.0 * kPi * planck_mean64(P, s, mid) < target) lo = mid; else hi = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+// MRW survival S(y) (debug path; large-time series, image series for small y)
+__device__ double mrw_S64(double y)
+{
+    if (y <= 0.0) return 1.0;
+    double s = 0.0;
+    if (y < 0.1) {
+        for (int m = 0; m < 60; ++m) {
+            const double t = exp(-(m + 0.5) * (m + 0.5) / y);
+            s += t;
+            if (t < 1e-300) break;
+        }
+        return 1.0 - 2.0 / sqrt(kPi * y) * s;
+    }
+    for (int n = 1; n < 200; ++n) {
+        const double t = exp(-(double)n * n * kPi * kPi * y);
+        s += (n & 1) ? t : -t;
+        if (t < 1e-22) break;
+    }
+    return 2.0 * s;
+}
+
+__device__ double mrw_y64(double u)
+{
+    if (u >= 1.0) return 0.0;
+    double lo = 0.0, hi = fmax(log(2.0 / u) / (kPi * kPi), 1e-3);
+    for (int it = 0; it < 64 && mrw_S64(hi) > u; ++it) hi *= 2.0;
+    for (int it = 0; it < 200 && hi - lo > 1e-15 * hi; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (mrw_S64(mid) > u) lo = mid; else hi = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+// MRW y from the survival table (FP32 path): S decreases on the uniform y
+// grid; below the table the tail S ~ 2 exp(-pi^2 y) is exact to 1e-7.
+__device__ __forceinline__ float mrw_y32(const float* S, float u)
+{
+    if (u >= 1.0f) return 0.0f;
+    const float s_last = S[kMrwN - 1];
+    if (u <= s_last) return logf(2.0f / u) * (float)(1.0 / (kPi * kPi));
+    int lo = 0, hi = kMrwN - 1;               // S[lo] >= u > S[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (S[mid] >= u) lo = mid; else hi = mid;
+    }
+    const float a = S[lo], b = S[hi];
+    const float w = (a - u) / fmaxf(a - b, 1e-30f);
+    return ((float)lo + w) * (float)(kMrwYmax / (kMrwN - 1));
+}
+
+// log2 of a positive double without FP64 transcendental work
+__device__ __forceinline__ float log2_d(double v)
+{
+    const int hi = __double2hiint(v);
+    const int e = ((hi >> 20) & 0x7ff) - 1023;
+    const double m = __hiloint2double((hi & 0x800fffff) | 0x3ff00000, __double2loint(v));
+    return (float)e + __log2f((float)m);
+}
+
+// ------------------------------------------------------------- per-lane packet state
+template <typename R, int NS>
+struct Lane {
+    int st, m;                 // state, model index
+    uint64_t pid;
+    Rng rng;
+    uint32_t seq, nev;
+    R x[3], k[3];              // flight origin (cell units) and direction
+    int ix, iy, iz, c;         // cell indices and linear index
+    int j;                     // frequency index
+    R tau, tcur;
+    R tm[3], td[3];
+    R rho[NS];                 // current cell (FP32: rho*cell; FP64: rho)
+    bool lucy;
+    R chi;                     // extinction per cell length at frequency j
+    R kex[NS], kab[NS];        // kext, kabs at frequency j (FP64: times cell)
+};
+
+struct Counters {
+    unsigned long long cross;
+    uint32_t c[C_N];
+};
+
+template <typename R, int NS>
+struct Kernel {
+    using PT = typename PackedT<NS>::T;
+    static constexpr bool DBG = sizeof(R) == 8;
+
+    const TransportKP& P;
+    const float4* s_op;        // [NS][nf] in shared memory (FP32 path)
+    const float* s_xh;
+    const float* s_w;
+    const float* s_mrw;
+    const ModelDev* md;        // model of the lane's current packet
+    Counters cnt;
+
+    __device__ Kernel(const TransportKP& p, const float4* op, const float* xh, const float* w,
+                      const float* mrw)
+        : P(p), s_op(op), s_xh(xh), s_w(w), s_mrw(mrw), md(nullptr)
+    {
+        cnt.cross = 0;
+        for (int i = 0; i < C_N; ++i) cnt.c[i] = 0;
+    }
+
+    __device__ __forceinline__ void load_cell(Lane<R, NS>& L)
+    {
+        const PT v = __ldg(reinterpret_cast<const PT*>(md->rho) + L.c);
+        float r[4];
+        unpack(v, r);
+        L.lucy = signbit(r[0]);
+        r[0] = fabsf(r[0]);
+        R chi = R(0);
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            L.rho[s] = (R)r[s];
+            chi += L.rho[s] * L.kex[s];
+        }
+        L.chi = chi;
+    }
+
+    // kext, kabs of every species at the lane's frequency
+    __device__ __forceinline__ void load_freq(Lane<R, NS>& L)
+    {
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            if constexpr (DBG) {
+                const double ka = P.kabs[s * P.nf + L.j], ks = P.ksca[s * P.nf + L.j];
+                L.kex[s] = (ka + ks) * md->cell;
+                L.kab[s] = ka * md->cell;
+            } else {
+                const float4 o = s_op[s * P.nf + L.j];
+                L.kex[s] = o.x;
+                L.kab[s] = o.y;
+            }
+        }
+        R chi = R(0);
+#pragma unroll
+        for (int s = 0; s < NS; ++s) chi += L.rho[s] * L.kex[s];
+        L.chi = chi;
+    }
+
+    __device__ void traj(Lane<R, NS>& L, uint32_t type, const R* x)
+    {
+        const uint32_t q = L.seq++;
+        if (md->traj == nullptr) return;
+        const unsigned long long slot = atomicAdd(&md->stats[RT_STAT_N_TRAJ], 1ull);
+        if (slot >= md->traj_cap) {
+            atomicAdd(&md->stats[RT_STAT_TRAJ_DROPPED], 1ull);
+            return;
+        }
+        rt_traj t;
+        t.pid = L.pid; t.seq = q; t.type = type; t.cell = (uint32_t)L.c; t.nu = (uint32_t)L.j;
+        for (int a = 0; a < 3; ++a) {
+            t.x[a] = md->box_min[a] + (double)x[a] * md->cell;
+            t.k[a] = (double)L.k[a];
+        }
+        md->traj[slot] = t;
+    }
+
+    // smallest j with cdf[j] >= u * cdf[n-1] (binary search, cdf non-decreasing)
+    template <typename C>
+    __device__ __forceinline__ int search_cdf(const C* cdf, int n, C target)
+    {
+        int lo = 0, hi = n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (cdf[mid] >= target) hi = mid; else lo = mid + 1;
+        }
+        return lo;
+    }
+
+    __device__ void emit(Lane<R, NS>& L, uint64_t w)
+    {
+        // model lookup: largest m with prefix[m] <= w
+        int lo = 0, hi = P.n_models - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (P.prefix[mid] <= w) lo = mid; else hi = mid - 1;
+        }
+        if (lo != L.m) {
+            if (L.m >= 0) flush(L.m);
+            L.m = lo;
+        }
+        md = &P.models[lo];
+        L.pid = md->pid_begin + (w - P.prefix[lo]);
+        rng_init(L.rng, P.seed, md->model_id, L.pid);
+        L.seq = 0;
+        L.nev = 0;
+        int si = 0;
+        if (md->nsrc > 1) {
+            const double u = (double)rng_u<R>(L.rng);
+            si = search_cdf(md->src_Lcdf, md->nsrc, u * md->src_Lcdf[md->nsrc - 1]);
+        }
+        const R ub = rng_u<R>(L.rng);
+        if constexpr (DBG) {
+            const double* cdf = md->src_cdf64 + (size_t)si * P.nf;
+            L.j = search_cdf(cdf, P.nf, ub * cdf[P.nf - 1]);
+        } else {
+            L.j = search_cdf(md->src_cdf32 + (size_t)si * P.nf, P.nf, ub);
+        }
+        const R u1 = rng_u<R>(L.rng), u2 = rng_u<R>(L.rng);
+        iso_dir(u1, u2, L.k);
+        int idx[3];
+        const int n[3] = { md->nx, md->ny, md->nz };
+        bool in = true;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            L.x[a] = (R)md->src_pos[si * 3 + a];
+            const R f = floor(L.x[a]);
+            int i = (int)f;
+            if (f == L.x[a] && L.k[a] < R(0)) i -= 1;
+            idx[a] = i;
+            in = in && (i >= 0 && i < n[a]);
+        }
+        L.ix = idx[0]; L.iy = idx[1]; L.iz = idx[2];
+        L.c = in ? (L.iz * md->ny + L.iy) * md->nx + L.ix : 0;
+        cnt.c[C_EMIT]++;
+        traj(L, RT_TRAJ_EMIT, L.x);
+        if (!in) {
+            L.tcur = R(0);
+            L.st = ST_ESCAPE;
+            return;
+        }
+#pragma unroll
+        for (int s = 0; s < NS; ++s) L.rho[s] = R(0);
+        load_freq(L);
+        load_cell(L);
+        L.st = ST_FLIGHT;
+    }
+
+    __device__ __forceinline__ void deposit_lucy(Lane<R, NS>& L, R l)
+    {
+        const size_t nc = (size_t)md->nx * md->ny * md->nz;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            const R ta = L.kab[s] * L.rho[s] * l;
+            double e;
+            if (P.lucy_form == RT_LUCY_EXPM1) e = -(double)r_expm1(-ta) * md->xi;
+            else e = (double)ta * md->xi;
+            if (e != 0.0) {
+                atomicAdd(&md->E_abs[s * nc + L.c], e);
+                if (md->esq) atomicAdd(&md->esq[s * nc + L.c], e * e);
+            }
+        }
+        cnt.c[C_LUCY]++;
+    }
+
+    // Temperature of species s in cell c from the accumulated energy (Eq. 4)
+    __device__ __forceinline__ R temperature(const Lane<R, NS>& L, int s, double E)
+    {
+        if constexpr (DBG) {
+            const double rv = L.rho[s] * md->vol;
+            return rv > 0.0 ? solve_T64(P, s, E / rv) : 0.0;
+        } else {
+            if (!(E > 0.0) || !(L.rho[s] > 0.0f)) return 0.0f;
+            const float y = log2_d(E) - __log2f(L.rho[s]) - (float)md->log2_4piV;
+            float f = (y - P.tinv_y0[s]) * P.tinv_inv_dy[s];
+            f = fminf(fmaxf(f, 0.0f), (float)(kTinvN - 1));
+            const int i = min((int)f, kTinvN - 2);
+            const float w = f - (float)i;
+            const float* t = P.tinv + (size_t)s * kTinvN;
+            return exp2f(t[i] + w * (t[i + 1] - t[i]));
+        }
+    }
+
+    // Re-emission frequency: Eq. 10 (B&W, dB/dT weights) or Eq. 5 (frozen T)
+    __device__ int reemit(const Lane<R, NS>& L, int s, double E, R u)
+    {
+        const size_t nc = (size_t)md->nx * md->ny * md->nz;
+        const bool bw = P.mode == RT_MODE_BW;
+        R T;
+        if (bw) T = temperature(L, s, E);
+        else T = (R)md->T_prev[s * nc + L.c];
+        const int nf = P.nf;
+        if constexpr (DBG) {
+            double tot = 0.0;
+            for (int l = 0; l < nf; ++l) {
+                const double b = bw ? planck_dBdT(P.nu[l], T) : planck_B(P.nu[l], T);
+                tot += P.kabs[s * nf + l] * b * P.dnu[l];
+            }
+            const double target = u * tot;
+            double acc = 0.0;
+            for (int l = 0; l < nf; ++l) {
+                const double b = bw ? planck_dBdT(P.nu[l], T) : planck_B(P.nu[l], T);
+                acc += P.kabs[s * nf + l] * b * P.dnu[l];
+                if (acc >= target) return l;
+            }
+            return nf - 1;
+        } else {
+            if (!(T > 0.0f)) return 0;
+            const float invT = 1.0f / T;
+            const float* w = s_w + s * nf;
+            float tot = 0.0f;
+            for (int l = 0; l < nf; ++l) tot += w[l] * weight(s_xh[l] * invT, bw);
+            const float target = u * tot;
+            float acc = 0.0f;
+            for (int l = 0; l < nf; ++l) {
+                acc += w[l] * weight(s_xh[l] * invT, bw);
+                if (acc >= target) return l;
+            }
+            return nf - 1;
+        }
+    }
+
+    // B: 1/(e^x - 1);  dB/dT (up to a factor): e^-x / (1 - e^-x)^2
+    __device__ __forceinline__ float weight(float x, bool bw)
+    {
+        const float em = __expf(-x);
+        const float om = x < 0.05f ? -expm1f(-x) : 1.0f - em;
+        return bw ? em / (om * om) : em / om;
+    }
+
+    __device__ __forceinline__ int pick_species(const Lane<R, NS>& L, bool sca, R u)
+    {
+        R w[NS];
+        R tot = R(0);
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            R ks;
+            if constexpr (DBG) ks = sca ? P.ksca[s * P.nf + L.j] : P.kabs[s * P.nf + L.j];
+            else ks = sca ? s_op[s * P.nf + L.j].z : s_op[s * P.nf + L.j].y;
+            w[s] = L.rho[s] * ks;
+            tot += w[s];
+        }
+        const R target = u * tot;
+        R acc = R(0);
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            acc += w[s];
+            if (acc >= target) return s;
+        }
+        return NS - 1;
+    }
+
+    __device__ void store_pah(Lane<R, NS>& L, const R* x)
+    {
+        const unsigned long long slot = atomicAdd(&md->stats[RT_STAT_N_PAH], 1ull);
+        if (md->pah && slot < md->pah_cap) {
+            rt_pah_event e;
+            e.cell = (uint32_t)L.c; e.nu = (uint16_t)L.j; e.model = (uint16_t)md->model_index;
+            md->pah[slot] = e;
+        } else {
+            atomicAdd(&md->stats[RT_STAT_PAH_DROPPED], 1ull);
+        }
+        cnt.c[C_PAH]++;
+        traj(L, RT_TRAJ_PAH, x);
+        L.st = ST_NEED;
+    }
+
+    __device__ __forceinline__ bool is_pah(int s) const { return (P.pah_mask >> s) & 1; }
+
+    // A new flight from L.x along L.k: MRW step or tau draw + traversal set-up
+    __device__ void flight(Lane<R, NS>& L)
+    {
+        if (P.mrw && P.mode != RT_MODE_NOREEMIT && L.chi > (R)P.mrw_tau_cell) {
+            R R0 = R(1e30);
+            const int id[3] = { L.ix, L.iy, L.iz };
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const R d1 = L.x[a] - (R)id[a], d2 = (R)(id[a] + 1) - L.x[a];
+                R0 = fmin(R0, fmin(d1, d2));
+            }
+            R0 = fmax(R0, R(0));
+            if (R0 * L.chi >= (R)P.mrw_gamma) {
+                mrw_step(L, R0);
+                return;
+            }
+        }
+        L.tau = -r_log(rng_u<R>(L.rng));
+        const int id[3] = { L.ix, L.iy, L.iz };
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const R ka = L.k[a];
+            if (ka > R(0)) {
+                L.td[a] = R(1) / ka;
+                L.tm[a] = fmax(((R)(id[a] + 1) - L.x[a]) / ka, R(0));
+            } else if (ka < R(0)) {
+                L.td[a] = R(-1) / ka;
+                L.tm[a] = fmax(((R)id[a] - L.x[a]) / ka, R(0));
+            } else {
+                L.td[a] = R(INFINITY);
+                L.tm[a] = R(INFINITY);
+            }
+        }
+        L.tcur = R(0);
+        L.st = ST_MARCH;
+    }
+
+    __device__ void mrw_step(Lane<R, NS>& L, R R0)
+    {
+        if (++L.nev > P.max_events) {
+            cnt.c[C_STUCK]++;
+            traj(L, RT_TRAJ_STUCK, L.x);
+            L.st = ST_NEED;
+            return;
+        }
+        const R u = rng_u<R>(L.rng);
+        R y;
+        if constexpr (DBG) y = mrw_y64(u);
+        else y = mrw_y32(s_mrw, u);
+        const R l = R(3) * L.chi * R0 * R0 * y;          // path length in cells
+        R nh[3];
+        { const R u1 = rng_u<R>(L.rng), u2 = rng_u<R>(L.rng); iso_dir(u1, u2, nh); }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) L.x[a] += R0 * nh[a];
+        { const R u3 = rng_u<R>(L.rng), u4 = rng_u<R>(L.rng); iso_dir(u3, u4, L.k); }
+        const size_t nc = (size_t)md->nx * md->ny * md->nz;
+        R ca = R(0);
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            const double e = (double)(L.kab[s] * L.rho[s] * l) * md->xi;
+            ca += L.kab[s] * L.rho[s];
+            if (e != 0.0) {
+                atomicAdd(&md->E_abs[s * nc + L.c], e);
+                if (md->esq) atomicAdd(&md->esq[s * nc + L.c], e * e);
+            }
+        }
+        cnt.c[C_MRW]++;
+        if (rng_u<R>(L.rng) < -r_expm1(-ca * l)) {
+            int s = 0;
+            if (NS > 1) s = pick_species(L, false, rng_u<R>(L.rng));
+            if (is_pah(s)) { store_pah(L, L.x); return; }
+            const double E = __ldcg(&md->E_abs[s * nc + L.c]);
+            L.j = reemit(L, s, E, rng_u<R>(L.rng));
+            load_freq(L);
+        }
+        traj(L, RT_TRAJ_MRW, L.x);
+        L.st = ST_FLIGHT;
+    }
+
+    // One cell traversal step of a marching lane.
+    __device__ __forceinline__ void march(Lane<R, NS>& L)
+    {
+        const bool ax = (L.tm[0] <= L.tm[1]) && (L.tm[0] <= L.tm[2]);
+        const bool ay = !ax && (L.tm[1] <= L.tm[2]);
+        const R tn = ax ? L.tm[0] : (ay ? L.tm[1] : L.tm[2]);
+        const R seg = tn - L.tcur;
+        const R dtau = L.chi * seg;
+        if (dtau <= L.tau) {
+            if (L.lucy) deposit_lucy(L, seg);
+            L.tau -= dtau;
+            L.tcur = tn;
+            bool out;
+            if (ax) {
+                const int st = L.k[0] > R(0) ? 1 : -1;
+                L.tm[0] += L.td[0];
+                L.ix += st;
+                L.c += st;
+                out = (unsigned)L.ix >= (unsigned)md->nx;
+            } else if (ay) {
+                const int st = L.k[1] > R(0) ? 1 : -1;
+                L.tm[1] += L.td[1];
+                L.iy += st;
+                L.c += st * md->nx;
+                out = (unsigned)L.iy >= (unsigned)md->ny;
+            } else {
+                const int st = L.k[2] > R(0) ? 1 : -1;
+                L.tm[2] += L.td[2];
+                L.iz += st;
+                L.c += st * md->nx * md->ny;
+                out = (unsigned)L.iz >= (unsigned)md->nz;
+            }
+            cnt.cross++;
+            if (out) {
+                // restore the last cell inside for the escape record
+                if (ax) { L.ix -= (L.k[0] > R(0) ? 1 : -1); L.c -= (L.k[0] > R(0) ? 1 : -1); }
+                else if (ay) { L.iy -= (L.k[1] > R(0) ? 1 : -1); L.c -= (L.k[1] > R(0) ? 1 : -1) * md->nx; }
+                else { L.iz -= (L.k[2] > R(0) ? 1 : -1); L.c -= (L.k[2] > R(0) ? 1 : -1) * md->nx * md->ny; }
+                L.st = ST_ESCAPE;
+            } else {
+                load_cell(L);
+            }
+        } else {
+            const R d = L.tau / L.chi;
+            if (L.lucy) deposit_lucy(L, d);
+            L.tcur += d;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) L.x[a] += L.tcur * L.k[a];
+            L.st = ST_INTERACT;
+        }
+    }
+
+    __device__ void interact(Lane<R, NS>& L)
+    {
+        if (++L.nev > P.max_events) {
+            cnt.c[C_STUCK]++;
+            traj(L, RT_TRAJ_STUCK, L.x);
+            L.st = ST_NEED;
+            return;
+        }
+        cnt.c[C_INT]++;
+        R cs = R(0);
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            R ks;
+            if constexpr (DBG) ks = P.ksca[s * P.nf + L.j] * md->cell;
+            else ks = s_op[s * P.nf + L.j].z;
+            cs += L.rho[s] * ks;
+        }
+        const R albedo = cs / L.chi;
+        if (rng_u<R>(L.rng) < albedo) {
+            int s = 0;
+            if (NS > 1) s = pick_species(L, true, rng_u<R>(L.rng));
+            R g;
+            if constexpr (DBG) g = P.g[s * P.nf + L.j];
+            else g = s_op[s * P.nf + L.j].w;
+            const R mu = hg_mu(g, rng_u<R>(L.rng));
+            const R uphi = rng_u<R>(L.rng);
+            if (P.record_events) {
+                const unsigned long long slot = atomicAdd(&md->stats[RT_STAT_N_EVENTS], 1ull);
+                if (md->events && slot < md->event_cap) {
+                    rt_event e;
+                    e.cell = (uint32_t)L.c; e.nu = (uint16_t)L.j; e.species = (uint8_t)s;
+                    e.model = (uint8_t)md->model_index;
+                    e.k[0] = (float)L.k[0]; e.k[1] = (float)L.k[1]; e.k[2] = (float)L.k[2];
+                    md->events[slot] = e;
+                } else {
+                    atomicAdd(&md->stats[RT_STAT_EVENTS_DROPPED], 1ull);
+                }
+            }
+            rotate(L.k, mu, uphi);
+            cnt.c[C_SCA]++;
+            traj(L, RT_TRAJ_SCATTER, L.x);
+            L.st = ST_FLIGHT;
+            return;
+        }
+        cnt.c[C_ABS]++;
+        int s = 0;
+        if (NS > 1) s = pick_species(L, false, rng_u<R>(L.rng));
+        if (is_pah(s)) { store_pah(L, L.x); return; }
+        const size_t nc = (size_t)md->nx * md->ny * md->nz;
+        double E = 0.0;
+        if (!L.lucy) {
+            E = atomicAdd(&md->E_abs[s * nc + L.c], md->xi) + md->xi;
+            if (md->esq) atomicAdd(&md->esq[s * nc + L.c], md->xi * md->xi);
+        } else if (P.mode == RT_MODE_BW) {
+            E = __ldcg(&md->E_abs[s * nc + L.c]);
+        }
+        atomicAdd(&md->count[s * nc + L.c], 1u);
+        if (P.mode == RT_MODE_NOREEMIT) {
+            traj(L, RT_TRAJ_ABSORB_END, L.x);
+            L.st = ST_NEED;
+            return;
+        }
+        L.j = reemit(L, s, E, rng_u<R>(L.rng));
+        { const R u1 = rng_u<R>(L.rng), u2 = rng_u<R>(L.rng); iso_dir(u1, u2, L.k); }
+        load_freq(L);
+        traj(L, RT_TRAJ_ABSORB, L.x);
+        L.st = ST_FLIGHT;
+    }
+
+    __device__ void escape(Lane<R, NS>& L)
+    {
+        int b = (int)floor((L.k[2] + R(1)) * R(5));
+        b = min(max(b, 0), kSedBins - 1);
+        atomicAdd(&md->sed_esc[b * P.nf + L.j], md->xi);
+        atomicAdd(&md->sed_cnt[b * P.nf + L.j], 1ull);
+        cnt.c[C_ESC]++;
+        if (md->traj) {
+            R xe[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) xe[a] = L.x[a] + L.tcur * L.k[a];
+            traj(L, RT_TRAJ_ESCAPE, xe);
+        }
+        L.st = ST_NEED;
+    }
+
+    // add this lane's counters to model m's stats
+    __device__ void flush(int m)
+    {
+        unsigned long long* st = P.models[m].stats;
+        if (cnt.cross) atomicAdd(&st[RT_STAT_CROSSINGS], cnt.cross);
+        const int map[C_N] = { RT_STAT_INTERACTIONS, RT_STAT_SCATTERS, RT_STAT_ABSORPTIONS,
+                               RT_STAT_MRW, RT_STAT_ESCAPED, RT_STAT_STUCK, RT_STAT_PAH,
+                               RT_STAT_LUCY, RT_STAT_EMITTED };
+#pragma unroll
+        for (int i = 0; i < C_N; ++i)
+            if (cnt.c[i]) atomicAdd(&st[map[i]], (unsigned long long)cnt.c[i]);
+        cnt.cross = 0;
+        for (int i = 0; i < C_N; ++i) cnt.c[i] = 0;
+    }
+};
+
+template <typename R, int NS>
+__global__ void __launch_bounds__(256) transport_kernel(const TransportKP P, int serial)
+{
+    extern __shared__ float4 smem[];
+    float4* s_op = smem;
+    float* s_xh = reinterpret_cast<float*>(s_op + NS * P.nf);
+    float* s_w = s_xh + P.nf;
+    float* s_mrw = s_w + NS * P.nf;
+    if (sizeof(R) == 4) {
+        for (int i = threadIdx.x; i < NS * P.nf; i += blockDim.x) {
+            s_op[i] = P.opac32[i];
+            s_w[i] = P.wre[i];
+        }
+        for (int i = threadIdx.x; i < P.nf; i += blockDim.x) s_xh[i] = P.xh[i];
+        if (P.mrw)
+            for (int i = threadIdx.x; i < kMrwN; i += blockDim.x) s_mrw[i] = P.mrwS[i];
+    }
+    __syncthreads();
+
+    Kernel<R, NS> K(P, s_op, s_xh, s_w, s_mrw);
+    Lane<R, NS> L;
+    L.st = ST_NEED;
+    L.m = -1;
+    const int lane = threadIdx.x & 31;
+
+    if (serial) {
+        // one thread, packets in id order: the order-dependent B&W temperatures
+        // evolve exactly as in a sequential run
+        if (blockIdx.x != 0 || threadIdx.x != 0) return;
+        for (unsigned long long w = 0; w < P.total_work; ++w) {
+            K.emit(L, w);
+            while (L.st != ST_NEED) {
+                if (L.st == ST_FLIGHT) K.flight(L);
+                else if (L.st == ST_MARCH) K.march(L);
+                else if (L.st == ST_INTERACT) K.interact(L);
+                else if (L.st == ST_ESCAPE) K.escape(L);
+            }
+        }
+        if (L.m >= 0) K.flush(L.m);
+        return;
+    }
+
+    const int min_active = P.march_min_active;
+    for (;;) {
+        const unsigned need = __ballot_sync(FULL, L.st == ST_NEED);
+        if (need) {
+            const int leader = __ffs(need) - 1;
+            unsigned long long base = 0;
+            if (lane == leader) base = atomicAdd(P.work_ctr, (unsigned long long)__popc(need));
+            base = __shfl_sync(FULL, base, leader);
+            if (L.st == ST_NEED) {
+                const unsigned long long w = base + __popc(need & ((1u << lane) - 1u));
+                if (w >= P.total_work) L.st = ST_DONE;
+                else K.emit(L, w);
+            }
+        }
+        if (__all_sync(FULL, L.st == ST_DONE)) break;
+        if (L.st == ST_FLIGHT) {
+            K.md = &P.models[L.m];
+            K.flight(L);
+        }
+        int nm;
+        do {
+            if (L.st == ST_MARCH) {
+                K.md = &P.models[L.m];
+                K.march(L);
+            }
+            nm = __popc(__ballot_sync(FULL, L.st == ST_MARCH));
+        } while (nm > min_active);
+        if (L.st == ST_INTERACT) {
+            K.md = &P.models[L.m];
+            K.interact(L);
+        } else if (L.st == ST_ESCAPE) {
+            K.md = &P.models[L.m];
+            K.escape(L);
+        }
+    }
+    if (L.m >= 0) K.flush(L.m);
+}
+
+// ------------------------------------------------------------- grid packing
+template <typename PT, int NS>
+__global__ void pack_kernel(const float* rho, size_t nc, const double* kext_max_dummy, PT* out,
+                            int prec, double cell, int lucy_mode, double lucy_tau,
+                            const double* kext, int nf)
+{
+    const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i >= nc) return;
+    float r[4] = { 0.f, 0.f, 0.f, 0.f };
+    double dust = 0.0;
+    for (int s = 0; s < NS; ++s) {
+        r[s] = rho[s * nc + i];
+        dust += r[s];
+    }
+    bool lucy = false;
+    if (dust > 0.0) {
+        if (lucy_mode == RT_LUCY_ALL) {
+            lucy = true;
+        } else if (lucy_mode == RT_LUCY_THIN) {
+            double mx = 0.0;
+            for (int j = 0; j < nf; ++j) {
+                double chi = 0.0;
+                for (int s = 0; s < NS; ++s) chi += (double)r[s] * kext[s * nf + j];
+                mx = fmax(mx, chi * cell);
+            }
+            lucy = mx < lucy_tau;
+        }
+    }
+    float v[4];
+    for (int s = 0; s < 4; ++s) v[s] = prec == RT_PREC_FP32 ? (float)((double)r[s] * cell) : r[s];
+    v[0] = lucy ? -fabsf(v[0]) : fabsf(v[0]);
+    if constexpr (NS == 1) out[i] = v[0];
+    else if constexpr (NS == 2) out[i] = make_float2(v[0], v[1]);
+    else out[i] = make_float4(v[0], v[1], v[2], v[3]);
+}
+
+__global__ void kext_kernel(const double* kabs, const double* ksca, double* kext, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) kext[i] = kabs[i] + ksca[i];
+}
+
+template <typename R, int NS>
+rt_status launch_one(rt_ctx* ctx, const TransportKP& kp, int schedule, int threads,
+                     int blocks_per_sm, cudaStream_t s)
+{
+    const size_t smem = sizeof(float4) * NS * kp.nf + sizeof(float) * kp.nf +
+                        sizeof(float) * NS * kp.nf + (kp.mrw ? sizeof(float) * kMrwN : 0);
+    auto fn = transport_kernel<R, NS>;
+    RT_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (schedule == RT_SCHED_SERIAL) {
+        fn<<<1, 32, smem, s>>>(kp, 1);
+        count_launches();
+    } else {
+        int nb = blocks_per_sm;
+        if (nb <= 0) {
+            RT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, threads, smem));
+            nb = std::max(nb, 1);
+        }
+        fn<<<ctx->num_sms * nb, threads, smem, s>>>(kp, 0);
+        count_launches();
+    }
+    RT_CUDA(cudaGetLastError());
+    return RT_OK;
+}
+
+}  // namespace
+
+rt_status pack_grid(rt_grid* g, const rt_opacity* op, int lucy_mode, double lucy_tau, int prec,
+                    cudaStream_t s)
+{
+    const int vec = g->ns == 1 ? 1 : (g->ns == 2 ? 2 : 4);
+    if (g->d_packed && g->packed_opac_serial == op->serial && g->packed_lucy_mode == lucy_mode &&
+        g->packed_lucy_tau == lucy_tau && g->packed_prec == prec)
+        return RT_OK;
+    const size_t nc = g->ncell();
+    if (!g->d_packed) RT_CUDA(cudaMalloc(&g->d_packed, nc * sizeof(float) * vec));
+    double* kext = nullptr;
+    const int n = op->ns * op->nf;
+    RT_CUDA(cudaMallocAsync(&kext, sizeof(double) * n, s));
+    kext_kernel<<<(n + 255) / 256, 256, 0, s>>>(op->d_kabs, op->d_ksca, kext, n);
+    count_launches(2);   // this one and the packing kernel below
+    const int th = 256;
+    const unsigned blocks = (unsigned)((nc + th - 1) / th);
+    if (vec == 1)
+        pack_kernel<float, 1><<<blocks, th, 0, s>>>(g->d_rho, nc, nullptr, (float*)g->d_packed, prec,
+                                                     g->cell, lucy_mode, lucy_tau, kext, op->nf);
+    else if (vec == 2)
+        pack_kernel<float2, 2><<<blocks, th, 0, s>>>(g->d_rho, nc, nullptr, (float2*)g->d_packed,
+                                                      prec, g->cell, lucy_mode, lucy_tau, kext, op->nf);
+    else if (g->ns == 3)
+        pack_kernel<float4, 3><<<blocks, th, 0, s>>>(g->d_rho, nc, nullptr, (float4*)g->d_packed,
+                                                      prec, g->cell, lucy_mode, lucy_tau, kext, op->nf);
+    else
+        pack_kernel<float4, 4><<<blocks, th, 0, s>>>(g->d_rho, nc, nullptr, (float4*)g->d_packed,
+                                                      prec, g->cell, lucy_mode, lucy_tau, kext, op->nf);
+    RT_CUDA(cudaGetLastError());
+    RT_CUDA(cudaFreeAsync(kext, s));
+    g->packed_vec = vec;
+    g->packed_opac_serial = op->serial;
+    g->packed_lucy_mode = lucy_mode;
+    g->packed_lucy_tau = lucy_tau;
+    g->packed_prec = prec;
+    return RT_OK;
+}
+
+rt_status launch_transport(rt_ctx* ctx, const rt_opacity* op, const TransportKP& kp, int ns,
+                           int prec, int schedule, int threads, int blocks_per_sm, cudaStream_t s)
+{
+    const int vec = ns == 1 ? 1 : (ns == 2 ? 2 : 4);
+    if (prec == RT_PREC_FP64) {
+        if (vec == 1) return launch_one<double, 1>(ctx, kp, schedule, threads, blocks_per_sm, s);
+        if (vec == 2) return launch_one<double, 2>(ctx, kp, schedule, threads, blocks_per_sm, s);
+        return launch_one<double, 4>(ctx, kp, schedule, threads, blocks_per_sm, s);
+    }
+    if (vec == 1) return launch_one<float, 1>(ctx, kp, schedule, threads, blocks_per_sm, s);
+    if (vec == 2) return launch_one<float, 2>(ctx, kp, schedule, threads, blocks_per_sm, s);
+    return launch_one<float, 4>(ctx, kp, schedule, threads, blocks_per_sm, s);
+}
+
+}  // namespace rtgb

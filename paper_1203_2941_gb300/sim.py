@@ -1,0 +1,368 @@
+"""Convenience layer over the C ABI: torch tensors own the device buffers,
+torch streams carry the work, and every step runs in librtgb's kernels.
+
+    ctx = Context()
+    grid, opac, srcs = ctx.grid(model), ctx.opacity(model), Sources(model.sources)
+    out = transport(ctx, grid, opac, srcs, n_packets=10**7)
+    T = temperatures(ctx, grid, opac, out.E_abs)
+    img, sed = raytrace(ctx, grid, opac, T, out, srcs, cams, freq_idx)
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+from typing import List, Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import rtgb as R
+
+
+def _stream(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _ptr(t: Optional[torch.Tensor]) -> Optional[int]:
+    return None if t is None else int(t.data_ptr())
+
+
+class Context:
+    """A library context on one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        if not torch.cuda.is_available():
+            raise RuntimeError("rtgb needs a CUDA GPU; none is visible")
+        R.load()
+        torch.cuda.set_device(device)
+        self.device = device
+        self.h = R.rt_ctx_create(device)
+
+    def close(self):
+        if getattr(self, "h", None):
+            R.rt_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def grid(self, model, stream=None) -> "Grid":
+        return Grid(self, model.rho, model.box_min, model.cell, stream)
+
+    def opacity(self, model) -> "Opacity":
+        return Opacity(self, model.nu, model.dnu, model.kabs, model.ksca, model.g, model.is_pah)
+
+
+class Grid:
+    def __init__(self, ctx: Context, rho, box_min, cell, stream=None):
+        self.ctx = ctx
+        if isinstance(rho, torch.Tensor):
+            t = rho.detach().to(dtype=torch.float32).contiguous()
+        else:
+            t = torch.from_numpy(np.ascontiguousarray(rho, dtype=np.float32))
+        ns, nz, ny, nx = t.shape
+        self.shape = (nx, ny, nz)
+        self.ns = ns
+        self.ncell = nx * ny * nz
+        self.box_min = [float(v) for v in box_min]
+        self.cell = float(cell)
+        self._src = t           # keep alive until the copy finished (upload syncs)
+        self.h = R.rt_grid_upload(ctx.h, nx, ny, nz, ns, self.box_min, self.cell, t.data_ptr(),
+                                  _stream(stream) if t.is_cuda else _stream(stream))
+        self._src = None
+
+    def __del__(self):
+        try:
+            if self.h:
+                R.rt_grid_free(self.h)
+                self.h = None
+        except Exception:
+            pass
+
+
+class Opacity:
+    def __init__(self, ctx: Context, nu, dnu, kabs, ksca, g, is_pah=None):
+        self.ctx = ctx
+        self.nu = np.asarray(nu, dtype=np.float64)
+        self.nf = self.nu.size
+        self.ns = np.atleast_2d(kabs).shape[0]
+        self.h = R.rt_opacity_upload(ctx.h, nu, dnu, np.atleast_2d(kabs), np.atleast_2d(ksca),
+                                     np.atleast_2d(g), is_pah)
+
+    def __del__(self):
+        try:
+            if self.h:
+                R.rt_opacity_free(self.h)
+                self.h = None
+        except Exception:
+            pass
+
+
+class Sources:
+    """rt_source array built from workloads.Source objects (keeps L_nu alive)."""
+
+    def __init__(self, sources):
+        self._lnu = []
+        arr = (R.rt_source * len(sources))()
+        for i, s in enumerate(sources):
+            lnu = None if s.L_nu is None else np.ascontiguousarray(s.L_nu, dtype=np.float64)
+            self._lnu.append(lnu)
+            arr[i].pos = (C.c_double * 3)(*[float(v) for v in s.pos])
+            arr[i].L = float(s.L)
+            arr[i].T_eff = float(s.T_eff)
+            arr[i].L_nu = None if lnu is None else lnu.ctypes.data
+        self.arr = arr
+        self.n = len(sources)
+        self.L = float(sum(s.L for s in sources))
+
+
+class TransportOut:
+    """Device outputs of rt_transport (accumulated across calls)."""
+
+    def __init__(self, ncell: int, ns: int, nf: int, event_cap: int = 0, pah_cap: int = 0,
+                 traj_cap: int = 0, esq: bool = True, device=None):
+        dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.E_abs = torch.zeros((ns, ncell), dtype=torch.float64, device=dev)
+        self.count = torch.zeros((ns, ncell), dtype=torch.int32, device=dev)
+        self.esq = torch.zeros((ns, ncell), dtype=torch.float64, device=dev) if esq else None
+        self.sed_esc = torch.zeros((10, nf), dtype=torch.float64, device=dev)
+        self.sed_cnt = torch.zeros((10, nf), dtype=torch.int64, device=dev)
+        self.events = torch.zeros(max(event_cap, 1) * 20, dtype=torch.uint8, device=dev)
+        self.event_cap = event_cap
+        self.pah = torch.zeros(max(pah_cap, 1) * 8, dtype=torch.uint8, device=dev)
+        self.pah_cap = pah_cap
+        self.traj = torch.zeros(max(traj_cap, 1) * 72, dtype=torch.uint8, device=dev)
+        self.traj_cap = traj_cap
+        self.stats = torch.zeros(R.RT_STAT_COUNT, dtype=torch.int64, device=dev)
+        self.xi = None
+
+    def zero_(self):
+        for t in (self.E_abs, self.count, self.esq, self.sed_esc, self.sed_cnt, self.stats):
+            if t is not None:
+                t.zero_()
+        return self
+
+    def c_struct(self) -> R.rt_transport_out:
+        return R.rt_transport_out(
+            _ptr(self.E_abs), _ptr(self.count), _ptr(self.esq), _ptr(self.sed_esc),
+            _ptr(self.sed_cnt),
+            _ptr(self.events) if self.event_cap else None, self.event_cap,
+            _ptr(self.pah) if self.pah_cap else None, self.pah_cap,
+            _ptr(self.traj) if self.traj_cap else None, self.traj_cap,
+            _ptr(self.stats))
+
+    def stats_dict(self):
+        v = self.stats.cpu().numpy()
+        return {k: int(v[i]) for i, k in enumerate(R.STAT_NAMES)}
+
+    @property
+    def n_events(self):
+        return int(min(self.stats[13].item(), self.event_cap))
+
+    def events_numpy(self):
+        n = self.n_events
+        return self.events[:n * 20].cpu().numpy().view(R.EVENT_DTYPE)
+
+    def pah_numpy(self):
+        n = int(min(self.stats[14].item(), self.pah_cap))
+        return self.pah[:n * 8].cpu().numpy().view(R.PAH_DTYPE)
+
+    def traj_numpy(self):
+        n = int(min(self.stats[15].item(), self.traj_cap))
+        return self.traj[:n * 72].cpu().numpy().view(R.TRAJ_DTYPE)
+
+    def numpy(self):
+        return dict(E_abs=self.E_abs.cpu().numpy(),
+                    count=self.count.cpu().numpy().view(np.uint32),
+                    esq=None if self.esq is None else self.esq.cpu().numpy(),
+                    sed_esc=self.sed_esc.cpu().numpy(),
+                    sed_cnt=self.sed_cnt.cpu().numpy().view(np.uint64),
+                    stats=self.stats_dict(), xi=self.xi)
+
+
+def make_params(n_packets: int, mode=R.RT_MODE_BW, lucy_mode=R.RT_LUCY_THIN,
+                lucy_form=R.RT_LUCY_LINEAR, lucy_tau=1e-2, mrw=False, mrw_tau_cell=10.0,
+                mrw_gamma=2.0, seed=1, model_id=0, pid_begin=0, pid_end=None,
+                max_events=10_000_000, record_events=False, precision=R.RT_PREC_FP32,
+                schedule=R.RT_SCHED_PERSISTENT, threads_per_block=0, blocks_per_sm=0,
+                march_min_active=-1) -> R.rt_transport_params:
+    p = R.rt_transport_params_default()
+    p.mode, p.lucy_mode, p.lucy_form, p.lucy_tau = mode, lucy_mode, lucy_form, lucy_tau
+    p.mrw, p.mrw_tau_cell, p.mrw_gamma = int(bool(mrw)), mrw_tau_cell, mrw_gamma
+    p.seed, p.model_id = int(seed), int(model_id)
+    p.n_packets = int(n_packets)
+    p.pid_begin = int(pid_begin)
+    p.pid_end = int(n_packets if pid_end is None else pid_end)
+    p.max_events = int(max_events)
+    p.record_events = int(bool(record_events))
+    p.precision, p.schedule = precision, schedule
+    p.threads_per_block, p.blocks_per_sm = threads_per_block, blocks_per_sm
+    p.march_min_active = march_min_active
+    return p
+
+
+def transport(ctx: Context, grid: Grid, opac: Opacity, sources: Sources, n_packets: int,
+              out: Optional[TransportOut] = None, T_prev: Optional[torch.Tensor] = None,
+              event_cap: int = 0, pah_cap: int = 0, traj_cap: int = 0, stream=None,
+              **kw) -> TransportOut:
+    if out is None:
+        out = TransportOut(grid.ncell, grid.ns, opac.nf, event_cap, pah_cap, traj_cap)
+    if kw.get("record_events") is None and out.event_cap:
+        kw["record_events"] = True
+    p = make_params(n_packets, **kw)
+    if T_prev is not None:
+        T_prev = T_prev.to(dtype=torch.float64).contiguous()
+    R.rt_transport(ctx.h, grid.h, opac.h, sources.arr, sources.n, p, _ptr(T_prev),
+                   out.c_struct(), _stream(stream))
+    out.xi = sources.L / n_packets
+    return out
+
+
+def temperatures(ctx: Context, grid: Grid, opac: Opacity, E_abs: torch.Tensor,
+                 T: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    E_abs = E_abs.contiguous()
+    if T is None:
+        T = torch.empty_like(E_abs, dtype=torch.float64)
+    R.rt_temperatures(ctx.h, grid.h, opac.h, _ptr(E_abs), _ptr(T), _stream(stream))
+    return T
+
+
+def temperature_guess(ctx: Context, grid: Grid, sources: Sources, stream=None) -> torch.Tensor:
+    T = torch.empty((grid.ns, grid.ncell), dtype=torch.float64, device="cuda")
+    R.rt_temperature_guess(ctx.h, grid.h, sources.arr, sources.n, _ptr(T), _stream(stream))
+    return T
+
+
+def cameras(cams) -> "C.Array":
+    arr = (R.rt_camera * len(cams))()
+    for i, c in enumerate(cams):
+        arr[i].theta, arr[i].phi, arr[i].npix = float(c.theta), float(c.phi), int(c.npix)
+        arr[i].D, arr[i].pixel = float(c.D), float(c.pixel)
+    return arr
+
+
+def _events_tensor(events):
+    """Events as a device uint8 tensor (20 bytes each) and their count."""
+    if events is None:
+        return None, 0
+    if isinstance(events, TransportOut):
+        return events.events, events.n_events
+    if isinstance(events, np.ndarray):
+        if events.dtype != R.EVENT_DTYPE:
+            ev = np.zeros(len(events), R.EVENT_DTYPE)
+            ev["cell"] = events["cell"]; ev["nu"] = events["nu"]; ev["species"] = events["species"]
+            ev["k"] = events["k"]
+            events = ev
+        if len(events) == 0:
+            return None, 0
+        t = torch.from_numpy(np.ascontiguousarray(events).view(np.uint8).copy()).cuda()
+        return t, len(events)
+    raise TypeError("events must be a TransportOut or a numpy event array")
+
+
+def raytrace(ctx: Context, grid: Grid, opac: Opacity, T: torch.Tensor, events, xi_ev: float,
+             sources: Optional[Sources], cams, freq_idx: Sequence[int], stream=None,
+             steps: Optional[torch.Tensor] = None):
+    """Images [n_cams, n_f, npix, npix] (float32) and SED [n_cams, n_f] (float64);
+    ``steps`` (int64 device tensor of one element) accumulates ray-cell steps."""
+    ev, nev = _events_tensor(events)
+    ca = cameras(cams)
+    fi = (C.c_int * len(freq_idx))(*[int(f) for f in freq_idx])
+    npix = cams[0].npix
+    img = torch.empty((len(cams), len(freq_idx), npix, npix), dtype=torch.float32, device="cuda")
+    sed = torch.empty((len(cams), len(freq_idx)), dtype=torch.float64, device="cuda")
+    T = T.to(dtype=torch.float64).contiguous()
+    R.rt_raytrace(ctx.h, grid.h, opac.h, _ptr(T), _ptr(ev), nev, float(xi_ev),
+                  None if sources is None else sources.arr, 0 if sources is None else sources.n,
+                  ca, len(cams), fi, len(freq_idx), _ptr(img), _ptr(sed), _ptr(steps),
+                  _stream(stream))
+    return img, sed
+
+
+def raytrace_backward(ctx: Context, grid: Grid, opac: Opacity, T: torch.Tensor, events, xi_ev,
+                      sources: Optional[Sources], cams, freq_idx, dL_dimg=None, dL_dsed=None,
+                      stream=None, steps: Optional[torch.Tensor] = None):
+    """dL/drho [ns, ncell] (float32) and dL/dscale (float64 scalar tensor)."""
+    ev, nev = _events_tensor(events)
+    ca = cameras(cams)
+    fi = (C.c_int * len(freq_idx))(*[int(f) for f in freq_idx])
+    drho = torch.zeros((grid.ns, grid.ncell), dtype=torch.float32, device="cuda")
+    dscale = torch.zeros(1, dtype=torch.float64, device="cuda")
+    T = T.to(dtype=torch.float64).contiguous()
+    gi = None if dL_dimg is None else dL_dimg.to(dtype=torch.float32).contiguous()
+    gs = None if dL_dsed is None else dL_dsed.to(dtype=torch.float64).contiguous()
+    R.rt_raytrace_backward(ctx.h, grid.h, opac.h, _ptr(T), _ptr(ev), nev, float(xi_ev),
+                           None if sources is None else sources.arr,
+                           0 if sources is None else sources.n, ca, len(cams), fi, len(freq_idx),
+                           _ptr(gi), _ptr(gs), _ptr(drho), _ptr(dscale), _ptr(steps),
+                           _stream(stream))
+    return drho, dscale
+
+
+class RayTrace(torch.autograd.Function):
+    """Differentiable ray tracer: (rho, scale) -> (images, sed) with the
+    density scale * rho; temperatures and scattering events held fixed."""
+
+    @staticmethod
+    def forward(fctx, rho, scale, ctx, box_min, cell, opac, T, events, xi_ev, sources, cams, freq_idx):
+        dens = (rho * scale).detach().contiguous()
+        grid = Grid(ctx, dens, box_min, cell)
+        img, sed = raytrace(ctx, grid, opac, T, events, xi_ev, sources, cams, freq_idx)
+        fctx.save_for_backward(rho, scale)
+        fctx.stuff = (ctx, grid, opac, T, events, xi_ev, sources, cams, freq_idx)
+        return img, sed
+
+    @staticmethod
+    def backward(fctx, g_img, g_sed):
+        rho, scale = fctx.saved_tensors
+        ctx, grid, opac, T, events, xi_ev, sources, cams, freq_idx = fctx.stuff
+        drho_eff, dscale_eff = raytrace_backward(ctx, grid, opac, T, events, xi_ev, sources, cams,
+                                                 freq_idx, g_img, g_sed)
+        drho = (drho_eff.view_as(rho) * scale).to(rho.dtype)
+        dscale = (dscale_eff / scale.to(torch.float64)).to(scale.dtype).reshape(scale.shape)
+        return drho, dscale, None, None, None, None, None, None, None, None, None, None
+
+
+def philox(ctx: Context, ctr0, key, n: int, stream=None) -> np.ndarray:
+    out = torch.empty(4 * n, dtype=torch.int32, device="cuda")
+    R.rt_philox(ctx.h, ctr0, key, n, _ptr(out), _stream(stream))
+    torch.cuda.synchronize()
+    return out.cpu().numpy().view(np.uint32)
+
+
+class Batch:
+    """Many models in one persistent launch (rt_batch_*); run() is graph-capturable."""
+
+    def __init__(self, ctx: Context, opac: Opacity, models, n_packets: Sequence[int], event_cap=0,
+                 pah_cap=0, T_prev=None, **kw):
+        self.ctx, self.opac = ctx, opac
+        self.grids = [ctx.grid(m) for m in models]
+        self.sources = [Sources(m.sources) for m in models]
+        self.outs = [TransportOut(g.ncell, g.ns, opac.nf, event_cap, pah_cap) for g in self.grids]
+        self.T_prev = T_prev
+        arr = (R.rt_model * len(models))()
+        for i, (g, s, o) in enumerate(zip(self.grids, self.sources, self.outs)):
+            arr[i].grid = g.h
+            arr[i].sources = C.cast(s.arr, C.c_void_p)
+            arr[i].n_sources = s.n
+            arr[i].n_packets = int(n_packets[i])
+            arr[i].T_prev = None if T_prev is None else _ptr(T_prev[i])
+            arr[i].out = o.c_struct()
+        self.models = arr
+        self.params = make_params(1, **kw)
+        self.h = R.rt_batch_create(ctx.h, opac.h, len(models), arr, self.params)
+
+    def run(self, stream=None):
+        R.rt_batch_run(self.h, _stream(stream))
+
+    def __del__(self):
+        try:
+            if self.h:
+                R.rt_batch_free(self.h)
+                self.h = None
+        except Exception:
+            pass

@@ -1,0 +1,253 @@
+"""GPU transport against the FP64 CPU oracle (run on a GB300).
+
+* Philox on the device is bit-exact with the oracle's.
+* FP64 debug build: per-packet trajectories (event types, cells, frequencies,
+  positions, directions) agree with the oracle to 1e-9 relative on small
+  irregular grids, for frozen-temperature transport on all SMs, Bjorkman &
+  Wood transport in the one-lane serial schedule, 1-3 species, the Lucy
+  variants and the modified random walk; accumulated energies agree to 1e-9.
+* FP32 production build: per-cell absorbed energy within
+  max(3 sigma, 1e-3 E), escaped SED within 3 sigma, temperatures within 0.5%
+  where the relative sigma of E is below 1%; exact energy conservation.
+* Edge cases: empty grid, source on a cell face, empty packet range, event
+  and PAH buffer overflow, the per-packet event cap, ragged grid shapes.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rt():
+    import __graft_entry__ as g
+    g.build()
+    import paper_1203_2941_gb300 as rt
+    return rt
+
+
+@pytest.fixture(scope="module")
+def ctx(rt):
+    return rt.Context(0)
+
+
+def _setup(rt, ctx, m):
+    return ctx.grid(m), ctx.opacity(m), rt.Sources(m.sources)
+
+
+def _traj_compare(tg, tr, scale, rtol=1e-9):
+    tg = np.sort(tg, order=["pid", "seq"])
+    tr = np.sort(tr, order=["pid", "seq"])
+    assert len(tg) == len(tr), (len(tg), len(tr))
+    for f in ("pid", "seq", "type", "cell", "nu"):
+        bad = np.nonzero(tg[f] != tr[f])[0]
+        assert bad.size == 0, (f, bad[:5], tg[bad[:3]], tr[bad[:3]])
+    assert np.max(np.abs(tg["x"] - tr["x"])) <= rtol * scale
+    assert np.max(np.abs(tg["k"] - tr["k"])) <= rtol * 10
+
+
+def test_philox_bit_exact(rt, ctx, O):
+    rng = np.random.default_rng(0)
+    for _ in range(4):
+        ctr = [int(v) for v in rng.integers(0, 2**32 - 5000, 4)]
+        key = [int(v) for v in rng.integers(0, 2**32, 2)]
+        out = rt.philox(ctx, ctr, key, 4096).reshape(-1, 4)
+        for i in (0, 1, 77, 4095):
+            c = [ctr[0] + i, ctr[1], ctr[2], ctr[3]]
+            np.testing.assert_array_equal(out[i], O.philox(c, key))
+
+
+@pytest.mark.parametrize("ns,lucy", [(1, 1), (2, 0), (3, 2), (1, 2)])
+def test_fp64_frozen_trajectories_match_oracle(rt, ctx, O, ns, lucy):
+    m = W.random_grid(n=(7, 5, 6), ns=ns, seed=10 + ns, tau_scale=2.0, albedo=(0.3, 0.8))
+    grid, opac, srcs = _setup(rt, ctx, m)
+    rng = np.random.default_rng(ns)
+    T0 = rng.uniform(30, 900, size=(ns, m.ncell))
+    N = 600
+    out = rt.transport(ctx, grid, opac, srcs, N, mode=rt.rtgb.RT_MODE_FROZEN_T, lucy_mode=lucy,
+                       precision=rt.rtgb.RT_PREC_FP64, T_prev=torch.tensor(T0, device="cuda"),
+                       traj_cap=400 * N, event_cap=100 * N, record_events=True, seed=77)
+    torch.cuda.synchronize()
+    ref = O.transport(m, N, seed=77, mode=O.MODE_FROZEN_T, lucy_mode=lucy, T_prev=T0,
+                      traj_cap=400 * N, event_cap=100 * N, record_events=True)
+    st = out.stats_dict()
+    assert st["traj_dropped"] == 0 and ref["stats"]["traj_dropped"] == 0
+    _traj_compare(out.traj_numpy(), ref["traj"], m.cell * 7)
+    for k in ("crossings", "interactions", "scatters", "absorptions", "escaped", "lucy_deposits"):
+        assert st[k] == ref["stats"][k], k
+    g = out.numpy()
+    np.testing.assert_array_equal(g["count"], ref["count"])
+    np.testing.assert_allclose(g["E_abs"], ref["E_abs"], rtol=1e-9, atol=1e-12 * ref["E_abs"].max())
+    np.testing.assert_allclose(g["sed_esc"], ref["sed_esc"], rtol=1e-9, atol=0)
+    ev = out.events_numpy()
+    assert len(ev) == len(ref["events"])
+    key = lambda e: np.lexsort((e["nu"], e["cell"]))
+    a, b = ev[key(ev)], ref["events"][key(ref["events"])]
+    np.testing.assert_array_equal(a["cell"], b["cell"])
+
+
+def test_fp64_bw_serial_trajectories_match_oracle(rt, ctx, O):
+    m = W.random_grid(n=(5, 6, 4), ns=2, seed=21, tau_scale=3.0, albedo=(0.1, 0.5))
+    grid, opac, srcs = _setup(rt, ctx, m)
+    N = 300
+    out = rt.transport(ctx, grid, opac, srcs, N, mode=rt.rtgb.RT_MODE_BW,
+                       precision=rt.rtgb.RT_PREC_FP64, schedule=rt.rtgb.RT_SCHED_SERIAL,
+                       traj_cap=400 * N, seed=3)
+    torch.cuda.synchronize()
+    ref = O.transport(m, N, seed=3, mode=O.MODE_BW, traj_cap=400 * N)
+    _traj_compare(out.traj_numpy(), ref["traj"], m.cell * 6)
+    g = out.numpy()
+    np.testing.assert_allclose(g["E_abs"], ref["E_abs"], rtol=1e-9, atol=1e-12 * ref["E_abs"].max())
+    assert abs(g["sed_esc"].sum() / m.luminosity - 1) < 1e-12
+
+
+def test_fp64_mrw_trajectories_match_oracle(rt, ctx, O):
+    m = W.uniform_cube(n=3, tau_cell=14.0, nf=5, albedo=0.5, gray=False)
+    grid, opac, srcs = _setup(rt, ctx, m)
+    T0 = np.full((1, m.ncell), 300.0)
+    N = 120
+    out = rt.transport(ctx, grid, opac, srcs, N, mode=rt.rtgb.RT_MODE_FROZEN_T, mrw=True,
+                       precision=rt.rtgb.RT_PREC_FP64, T_prev=torch.tensor(T0, device="cuda"),
+                       traj_cap=5000 * N, seed=9)
+    torch.cuda.synchronize()
+    ref = O.transport(m, N, seed=9, mode=O.MODE_FROZEN_T, mrw=True, T_prev=T0, traj_cap=5000 * N)
+    assert ref["stats"]["mrw_steps"] > 0
+    _traj_compare(out.traj_numpy(), ref["traj"], m.cell * 3)
+    assert out.stats_dict()["mrw_steps"] == ref["stats"]["mrw_steps"]
+
+
+def test_fp64_pah_and_noreemit_match_oracle(rt, ctx, O):
+    m = W.clumpy_torus(n=12, n_clump=40, seed=5, nf=20)
+    grid, opac, srcs = _setup(rt, ctx, m)
+    N = 300
+    out = rt.transport(ctx, grid, opac, srcs, N, mode=rt.rtgb.RT_MODE_BW,
+                       precision=rt.rtgb.RT_PREC_FP64, schedule=rt.rtgb.RT_SCHED_SERIAL,
+                       traj_cap=300 * N, pah_cap=N, seed=4)
+    torch.cuda.synchronize()
+    ref = O.transport(m, N, seed=4, mode=O.MODE_BW, traj_cap=300 * N, pah_cap=N)
+    _traj_compare(out.traj_numpy(), ref["traj"], m.cell * 12)
+    assert out.stats_dict()["pah"] == ref["stats"]["pah"] > 0
+    m2 = W.random_grid(n=(4, 4, 5), seed=2, tau_scale=2.0)
+    grid2, opac2, srcs2 = _setup(rt, ctx, m2)
+    out2 = rt.transport(ctx, grid2, opac2, srcs2, 500, mode=rt.rtgb.RT_MODE_NOREEMIT,
+                        precision=rt.rtgb.RT_PREC_FP64, traj_cap=100000, seed=8)
+    torch.cuda.synchronize()
+    ref2 = O.transport(m2, 500, seed=8, mode=O.MODE_NOREEMIT, traj_cap=100000)
+    _traj_compare(out2.traj_numpy(), ref2["traj"], m2.cell * 5)
+
+
+def _stat_compare(g, ref, xi, E_rel=1e-3, nsig=3.0):
+    """Per-cell E_abs within max(nsig*sigma, E_rel*E) with sigma from both
+    runs' sums of squared deposits."""
+    sg = np.sqrt(g["esq"]) if g["esq"] is not None else xi * np.sqrt(g["count"])
+    sr = np.sqrt(ref["esq"])
+    sig = np.sqrt(sg ** 2 + sr ** 2)
+    tol = np.maximum(nsig * sig, E_rel * np.maximum(g["E_abs"], ref["E_abs"]))
+    d = np.abs(g["E_abs"] - ref["E_abs"])
+    return d <= tol + 1e-30, sig
+
+
+def test_fp32_bw_statistics_match_oracle_homogeneous_sphere(rt, ctx, O):
+    """Homogeneous sphere (32^3 in the full-size configuration; 16^3 here so
+    the B&W oracle finishes in seconds), B&W, Lucy in thin cells."""
+    m = W.homogeneous_sphere(n=16, tau_v=1.0)
+    grid, opac, srcs = _setup(rt, ctx, m)
+    N = 40000
+    out = rt.transport(ctx, grid, opac, srcs, N, seed=11)
+    torch.cuda.synchronize()
+    ref = O.transport(m, N, seed=12, mode=O.MODE_BW)
+    g = out.numpy()
+    xi = m.luminosity / N
+    assert abs(g["sed_esc"].sum() / m.luminosity - 1) < 1e-12
+    assert g["stats"]["escaped"] == N
+    ok, sig = _stat_compare(g, ref, xi, nsig=4.0)
+    # 4 sigma per cell over ~4000 cells: allow the expected Gaussian outliers
+    assert (~ok).sum() <= max(3, int(0.002 * ok.size)), (~ok).sum()
+    # total absorbed energy and escaped SED
+    tot_sig = math.sqrt((sig ** 2).sum())
+    assert abs(g["E_abs"].sum() - ref["E_abs"].sum()) < 4 * tot_sig + 1e-3 * ref["E_abs"].sum()
+    s_sig = xi * np.sqrt(g["sed_cnt"] + ref["sed_cnt"])
+    assert np.all(np.abs(g["sed_esc"] - ref["sed_esc"]) <= 4.5 * s_sig + 1e-12)
+    # temperatures where the energy is well sampled
+    Tg = O.temperatures(m, g["E_abs"])
+    Tr = O.temperatures(m, ref["E_abs"])
+    rel = np.sqrt(g["esq"]) / np.maximum(g["E_abs"], 1e-300)
+    good = (rel < 0.01) & (g["E_abs"] > 0) & (ref["E_abs"] > 0)
+    if good.sum() > 0:
+        assert np.all(np.abs(Tg[good] / Tr[good] - 1) < 0.005)
+
+
+def test_fp32_frozen_statistics_and_packet_ranges(rt, ctx, O):
+    m = W.r2_shell(n=16, tau_1um=10.0, nf=32)
+    grid, opac, srcs = _setup(rt, ctx, m)
+    T0 = O.temperature_guess(m)
+    N = 30000
+    Tt = torch.tensor(T0, device="cuda")
+    out = rt.transport(ctx, grid, opac, srcs, N, mode=rt.rtgb.RT_MODE_FROZEN_T, T_prev=Tt, seed=2)
+    # the same emission split into two packet ranges accumulates identically
+    out2 = rt.transport(ctx, grid, opac, srcs, N, mode=rt.rtgb.RT_MODE_FROZEN_T, T_prev=Tt, seed=2,
+                        pid_begin=0, pid_end=N // 3)
+    rt.transport(ctx, grid, opac, srcs, N, out=out2, mode=rt.rtgb.RT_MODE_FROZEN_T, T_prev=Tt,
+                 seed=2, pid_begin=N // 3, pid_end=N)
+    torch.cuda.synchronize()
+    g, g2 = out.numpy(), out2.numpy()
+    np.testing.assert_array_equal(g["count"], g2["count"])
+    assert g["stats"]["crossings"] == g2["stats"]["crossings"]
+    np.testing.assert_allclose(g["E_abs"], g2["E_abs"], rtol=1e-9, atol=1e-9 * g["E_abs"].max())
+    ref = O.transport(m, N, seed=3, mode=O.MODE_FROZEN_T, T_prev=T0, n_threads=8)
+    ok, _ = _stat_compare(g, ref, m.luminosity / N, nsig=4.0)
+    assert (~ok).sum() <= max(3, int(0.002 * ok.size))
+    assert abs(g["sed_esc"].sum() / m.luminosity - 1) < 1e-12
+
+
+def test_edge_cases(rt, ctx, O):
+    # empty grid: every packet escapes on its first flight, no interaction
+    m = W.uniform_cube(n=5, tau_cell=0.5)
+    m.rho[:] = 0.0
+    grid, opac, srcs = _setup(rt, ctx, m)
+    out = rt.transport(ctx, grid, opac, srcs, 2000, seed=1)
+    torch.cuda.synchronize()
+    st = out.stats_dict()
+    assert st["escaped"] == 2000 and st["interactions"] == 0 and st["lucy_deposits"] == 0
+    # source exactly on cell faces and corners (even grid, centre source)
+    m = W.uniform_cube(n=4, tau_cell=0.7, albedo=0.4)
+    grid, opac, srcs = _setup(rt, ctx, m)
+    out = rt.transport(ctx, grid, opac, srcs, 400, precision=rt.rtgb.RT_PREC_FP64,
+                       schedule=rt.rtgb.RT_SCHED_SERIAL, traj_cap=100000, seed=4)
+    torch.cuda.synchronize()
+    ref = O.transport(m, 400, seed=4, mode=O.MODE_BW, traj_cap=100000)
+    _traj_compare(out.traj_numpy(), ref["traj"], m.cell * 4)
+    # empty packet range launches nothing
+    out = rt.transport(ctx, grid, opac, srcs, 100, pid_begin=50, pid_end=50)
+    torch.cuda.synchronize()
+    assert out.stats_dict()["emitted"] == 0
+    # event buffer overflow is counted, never written past the capacity
+    m = W.uniform_cube(n=4, tau_cell=2.0, albedo=0.9)
+    grid, opac, srcs = _setup(rt, ctx, m)
+    out = rt.transport(ctx, grid, opac, srcs, 500, event_cap=10, record_events=True, seed=2)
+    torch.cuda.synchronize()
+    st = out.stats_dict()
+    assert st["n_events"] == st["scatters"] > 10 and st["events_dropped"] == st["scatters"] - 10
+    # per-packet event cap
+    out = rt.transport(ctx, grid, opac, srcs, 500, max_events=2, seed=2)
+    torch.cuda.synchronize()
+    st = out.stats_dict()
+    assert st["stuck"] > 0 and st["stuck"] + st["escaped"] == 500
+    # argument errors are synchronous and leave nothing launched
+    with pytest.raises(rt.RtError):
+        rt.transport(ctx, grid, opac, srcs, 0)
+    with pytest.raises(rt.RtError):
+        rt.transport(ctx, grid, opac, srcs, 10, mode=rt.rtgb.RT_MODE_FROZEN_T)
+    bad = W.uniform_cube(n=4)
+    bad.sources[0].pos = (10 * bad.cell * 4, 0.0, 0.0)
+    with pytest.raises(rt.RtError):
+        rt.transport(ctx, grid, opac, rt.Sources(bad.sources), 10)
+    neg = W.uniform_cube(n=3)
+    neg.rho[0, 1, 1, 1] = -1.0
+    with pytest.raises(rt.RtError):
+        ctx.grid(neg)
