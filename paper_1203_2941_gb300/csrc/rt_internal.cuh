@@ -26,7 +26,7 @@ rt_status cuda_fail(cudaError_t e, const char* what);
 constexpr int kMaxSpecies = 4;
 constexpr int kMaxFreq = 1024;
 constexpr int kTinvN = 4096;      // FP32 temperature-inverse table entries per species
-constexpr int kTinv64N = 8192;    // FP64 table used to start the Eq. 4 Newton polish
+constexpr int kTz64N = 65536;     // FP64 table of ln(4 pi P(T)) and its slope on a ln T grid
 constexpr int kMrwN = 2048;       // MRW survival table entries on y in [0, kMrwYmax]
 constexpr double kMrwYmax = 2.0;
 constexpr int kSedBins = 10;
@@ -60,9 +60,9 @@ struct rt_opacity {
     float* d_wB;                           // [ns][nf] kabs dnu (nu/nu_max)^3 / max
     float* d_wD;                           // [ns][nf] kabs dnu (nu/nu_max)^4 / max
     float* d_tinv;                         // [ns][kTinvN] log2 T on uniform log2(P) grid
-    double* d_tinv64;                      // [ns][kTinv64N] ln T on uniform ln(4 pi P) grid
+    double2* d_tz;                         // [ns][kTz64N] {ln(4 pi P), d/dlnT} on uniform ln T
+    double tz_lnT0, tz_dlnT;
     float tinv_y0[rtgb::kMaxSpecies], tinv_inv_dy[rtgb::kMaxSpecies];
-    double t64_y0[rtgb::kMaxSpecies], t64_inv_dy[rtgb::kMaxSpecies];
     float* d_mrwS;                         // [kMrwN] survival S(y)
 };
 

@@ -41,7 +41,10 @@ void source_spectrum(const rt_opacity* op, const rt_source& src, std::vector<dou
 
 // ln(4 pi sum_j kabs_j B(nu_j, T) dnu_j) by log-sum-exp (no underflow at low T);
 // lnc[j] = ln(kabs_j dnu_j 2 h nu_j^3 / c^2) (or -inf), x1[j] = h nu_j / k.
-static double ln_emission(const std::vector<double>& lnc, const std::vector<double>& x1, double T)
+// *slope (optional) receives d ln(4 pi P) / d ln T = <x / (1 - e^-x)> over the
+// emission-weighted bins.
+static double ln_emission(const std::vector<double>& lnc, const std::vector<double>& x1, double T,
+                          double* slope = nullptr)
 {
     const size_t nf = lnc.size();
     double mx = -INFINITY;
@@ -54,9 +57,15 @@ static double ln_emission(const std::vector<double>& lnc, const std::vector<doub
         mx = std::max(mx, t[j]);
     }
     if (!std::isfinite(mx)) return -INFINITY;
-    double acc = 0.0;
+    double acc = 0.0, acc_s = 0.0;
     for (size_t j = 0; j < nf; ++j)
-        if (std::isfinite(t[j])) acc += exp(t[j] - mx);
+        if (std::isfinite(t[j])) {
+            const double w = exp(t[j] - mx);
+            acc += w;
+            const double x = x1[j] / T;
+            acc_s += w * x / (-expm1(-x));
+        }
+    if (slope) *slope = acc_s / acc;
     return log(4.0 * kPi) + mx + log(acc);
 }
 
@@ -126,12 +135,14 @@ rt_status build_opacity_tables(rt_opacity* op)
         }
     }
 
-    // inverse emission tables from a dense forward table in ln T
+    // exact tabulation of z = ln(4 pi P(T)) and dz/dlnT on a uniform ln T grid
+    // (FP64 temperatures), inverted on a uniform z grid for the FP32 transport
     const double lnTlo = log(0.1), lnThi = log(1.0e6);
-    const int ndense = 1 << 16;
+    std::vector<double2> tz((size_t)ns * kTz64N);
+    op->tz_lnT0 = lnTlo;
+    op->tz_dlnT = (lnThi - lnTlo) / (kTz64N - 1);
     std::vector<float> tinv((size_t)ns * kTinvN);
-    std::vector<double> tinv64((size_t)ns * kTinv64N);
-    std::vector<double> lnTd(ndense), zd(ndense), inv;
+    std::vector<double> lnTd(kTz64N), zd(kTz64N), inv;
     std::vector<double> x1(nf), lnc(nf);
     for (int j = 0; j < nf; ++j) x1[j] = kH * op->nu[j] / kK;
     for (int s = 0; s < ns; ++s) {
@@ -142,30 +153,25 @@ rt_status build_opacity_tables(rt_opacity* op)
                               : -INFINITY;
         }
         bool ok = true;
-        for (int i = 0; i < ndense; ++i) {
-            lnTd[i] = lnTlo + (lnThi - lnTlo) * i / (ndense - 1);
-            zd[i] = ln_emission(lnc, x1, exp(lnTd[i]));
+        for (int i = 0; i < kTz64N; ++i) {
+            double sl = 0.0;
+            lnTd[i] = lnTlo + i * op->tz_dlnT;
+            zd[i] = ln_emission(lnc, x1, exp(lnTd[i]), &sl);
+            tz[(size_t)s * kTz64N + i] = make_double2(zd[i], sl);
             if (!std::isfinite(zd[i]) || (i > 0 && !(zd[i] > zd[i - 1]))) ok = false;
         }
         if (!ok) {
             // a species without absorption: temperatures stay at the table floor
             for (int i = 0; i < kTinvN; ++i) tinv[(size_t)s * kTinvN + i] = (float)(lnTlo / log(2.0));
-            for (int i = 0; i < kTinv64N; ++i) tinv64[(size_t)s * kTinv64N + i] = lnTlo;
             op->tinv_y0[s] = 0.0f; op->tinv_inv_dy[s] = 0.0f;
-            op->t64_y0[s] = 0.0; op->t64_inv_dy[s] = 0.0;
             continue;
         }
-        const double zlo = zd[0], zhi = zd[ndense - 1];
+        const double zlo = zd[0], zhi = zd[kTz64N - 1];
         const double dy = (zhi - zlo) / log(2.0) / (kTinvN - 1);
         invert_dense(lnTd, zd, zlo, dy * log(2.0), kTinvN, inv);
         for (int i = 0; i < kTinvN; ++i) tinv[(size_t)s * kTinvN + i] = (float)(inv[i] / log(2.0));
         op->tinv_y0[s] = (float)(zlo / log(2.0));
         op->tinv_inv_dy[s] = (float)(1.0 / dy);
-        const double dz = (zhi - zlo) / (kTinv64N - 1);
-        invert_dense(lnTd, zd, zlo, dz, kTinv64N, inv);
-        for (int i = 0; i < kTinv64N; ++i) tinv64[(size_t)s * kTinv64N + i] = inv[i];
-        op->t64_y0[s] = zlo;
-        op->t64_inv_dy[s] = 1.0 / dz;
     }
 
     std::vector<float> mrw(kMrwN);
@@ -181,7 +187,7 @@ rt_status build_opacity_tables(rt_opacity* op)
     RT_CUDA(cudaMalloc(&op->d_wB, sizeof(float) * sf));
     RT_CUDA(cudaMalloc(&op->d_wD, sizeof(float) * sf));
     RT_CUDA(cudaMalloc(&op->d_tinv, sizeof(float) * tinv.size()));
-    RT_CUDA(cudaMalloc(&op->d_tinv64, sizeof(double) * tinv64.size()));
+    RT_CUDA(cudaMalloc(&op->d_tz, sizeof(double2) * tz.size()));
     RT_CUDA(cudaMalloc(&op->d_mrwS, sizeof(float) * kMrwN));
     RT_CUDA(cudaMemcpy(op->d_nu, op->nu.data(), sizeof(double) * nf, cudaMemcpyHostToDevice));
     RT_CUDA(cudaMemcpy(op->d_dnu, op->dnu.data(), sizeof(double) * nf, cudaMemcpyHostToDevice));
@@ -193,8 +199,7 @@ rt_status build_opacity_tables(rt_opacity* op)
     RT_CUDA(cudaMemcpy(op->d_wB, wB.data(), sizeof(float) * sf, cudaMemcpyHostToDevice));
     RT_CUDA(cudaMemcpy(op->d_wD, wD.data(), sizeof(float) * sf, cudaMemcpyHostToDevice));
     RT_CUDA(cudaMemcpy(op->d_tinv, tinv.data(), sizeof(float) * tinv.size(), cudaMemcpyHostToDevice));
-    RT_CUDA(cudaMemcpy(op->d_tinv64, tinv64.data(), sizeof(double) * tinv64.size(),
-                       cudaMemcpyHostToDevice));
+    RT_CUDA(cudaMemcpy(op->d_tz, tz.data(), sizeof(double2) * tz.size(), cudaMemcpyHostToDevice));
     RT_CUDA(cudaMemcpy(op->d_mrwS, mrw.data(), sizeof(float) * kMrwN, cudaMemcpyHostToDevice));
     return RT_OK;
 }

@@ -107,7 +107,7 @@ def test_fp64_bw_serial_trajectories_match_oracle(rt, ctx, O):
 
 
 def test_fp64_mrw_trajectories_match_oracle(rt, ctx, O):
-    m = W.uniform_cube(n=3, tau_cell=14.0, nf=5, albedo=0.5, gray=False)
+    m = W.uniform_cube(n=3, tau_cell=14.0, nf=5, albedo=0.5)
     grid, opac, srcs = _setup(rt, ctx, m)
     T0 = np.full((1, m.ncell), 300.0)
     N = 120
