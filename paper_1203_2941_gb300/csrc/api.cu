@@ -429,6 +429,10 @@ struct rt_batch {
     int n_models, ns;
     DeviceModels dm;
     TransportKP kp;
+    double* acc;                       // FP32 build scratch for all models
+    size_t acc_bytes;
+    std::vector<rtgb::ModelDev> host;  // per-model descriptors (finalize arguments)
+    std::vector<size_t> n_acc;
 };
 
 extern "C" {
@@ -459,15 +463,28 @@ rt_status rt_transport(rt_ctx* ctx, const rt_grid* grid, const rt_opacity* op,
     st = pack_grid(const_cast<rt_grid*>(grid), op, p->lucy_mode, p->lucy_tau, p->precision, s);
     if (st != RT_OK) return st;
     hms[0].md.rho = grid->d_packed;
+    // FP32 build: this call's deposits go to FP64 scratch in units of xi
+    const size_t n_acc = (size_t)op->ns * grid->ncell();
+    double* acc = nullptr;
+    if (p->precision == RT_PREC_FP32) {
+        const size_t bytes = sizeof(double) * n_acc * (out->esq ? 2 : 1);
+        RT_CUDA(cudaMallocAsync((void**)&acc, bytes, s));
+        RT_CUDA(cudaMemsetAsync(acc, 0, bytes, s));
+        hms[0].md.accE = acc;
+        hms[0].md.accQ = out->esq ? acc + n_acc : nullptr;
+    }
     DeviceModels dm;
     st = stage_models(hms, { p->pid_end - p->pid_begin }, op->nf, true, s, dm);
-    if (st != RT_OK) return st;
+    if (st != RT_OK) { if (acc) cudaFreeAsync(acc, s); return st; }
     RT_CUDA(cudaMemsetAsync(dm.work, 0, sizeof(unsigned long long), s));
     TransportKP kp;
     fill_kp(kp, op, p, dm, 1);
     const int threads = p->threads_per_block ? p->threads_per_block : 256;
     st = launch_transport(ctx, op, kp, op->ns, p->precision, p->schedule, threads, p->blocks_per_sm, s);
+    if (st == RT_OK && acc)
+        st = launch_finalize(acc, hms[0].md.accQ, n_acc, hms[0].md.xi, out->E_abs, out->esq, s);
     cudaFreeAsync(dm.buf, s);
+    if (acc) cudaFreeAsync(acc, s);
     return st;
 }
 
@@ -502,8 +519,32 @@ rt_status rt_batch_create(rt_ctx* ctx, const rt_opacity* op, int n_models, const
     RT_CUDA(cudaDeviceSynchronize());
     rt_batch* b = new rt_batch();
     b->ctx = ctx; b->op = op; b->p = *p; b->n_models = n_models; b->ns = op->ns;
+    b->acc = nullptr;
+    b->acc_bytes = 0;
+    if (p->precision == RT_PREC_FP32) {
+        size_t tot = 0;
+        for (int m = 0; m < n_models; ++m) {
+            const size_t n = (size_t)op->ns * models[m].grid->ncell();
+            tot += n * (models[m].out.esq ? 2 : 1);
+        }
+        b->acc_bytes = tot * sizeof(double);
+        cudaError_t e = cudaMalloc((void**)&b->acc, b->acc_bytes);
+        if (e != cudaSuccess) { delete b; return cuda_fail(e, "rt_batch_create scratch"); }
+        size_t off = 0;
+        for (int m = 0; m < n_models; ++m) {
+            const size_t n = (size_t)op->ns * models[m].grid->ncell();
+            hms[m].md.accE = b->acc + off;
+            off += n;
+            hms[m].md.accQ = models[m].out.esq ? b->acc + off : nullptr;
+            if (models[m].out.esq) off += n;
+        }
+    }
+    for (int m = 0; m < n_models; ++m) {
+        b->host.push_back(hms[m].md);
+        b->n_acc.push_back((size_t)op->ns * models[m].grid->ncell());
+    }
     st = stage_models(hms, nwork, op->nf, false, 0, b->dm);
-    if (st != RT_OK) { delete b; return st; }
+    if (st != RT_OK) { cudaFree(b->acc); delete b; return st; }
     fill_kp(b->kp, op, p, b->dm, n_models);
     *out = b;
     return RT_OK;
@@ -514,9 +555,17 @@ rt_status rt_batch_run(rt_batch* b, rt_stream stream)
     if (!b) return fail(RT_ERR_INVALID_ARG, "rt_batch_run: NULL batch");
     cudaStream_t s = (cudaStream_t)stream;
     RT_CUDA(cudaMemsetAsync(b->dm.work, 0, sizeof(unsigned long long), s));
+    if (b->acc) RT_CUDA(cudaMemsetAsync(b->acc, 0, b->acc_bytes, s));
     const int threads = b->p.threads_per_block ? b->p.threads_per_block : 256;
-    return launch_transport(b->ctx, b->op, b->kp, b->ns, b->p.precision, b->p.schedule, threads,
-                            b->p.blocks_per_sm, s);
+    rt_status st = launch_transport(b->ctx, b->op, b->kp, b->ns, b->p.precision, b->p.schedule,
+                                    threads, b->p.blocks_per_sm, s);
+    if (st != RT_OK || !b->acc) return st;
+    for (int m = 0; m < b->n_models; ++m) {
+        const ModelDev& md = b->host[m];
+        st = launch_finalize(md.accE, md.accQ, b->n_acc[m], md.xi, md.E_abs, md.esq, s);
+        if (st != RT_OK) return st;
+    }
+    return RT_OK;
 }
 
 void rt_batch_free(rt_batch* b)
@@ -524,6 +573,7 @@ void rt_batch_free(rt_batch* b)
     if (!b) return;
     cudaSetDevice(b->ctx->device);
     cudaFree(b->dm.buf);
+    cudaFree(b->acc);
     delete b;
 }
 

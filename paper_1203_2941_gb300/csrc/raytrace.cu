@@ -3,6 +3,7 @@
 //
 //   eta_th[c][f]       = sum_s rho_s kabs_s(nu_f) B(nu_f, T_s)      (Eq. 14)
 //   eta[cam][c][f]     = eta_th + xi_ev / (V dnu_f) sum_events P_HG(k_in . k_obs)  (Eq. 16)
+// (tables hold eta times the cell size, so FP32 stays far from underflow)
 //   I(pixel, f)        = sum_k S_k (1 - exp(-dtau_k)) exp(-tau_<k),  S = eta / chi  (Eqs. 12-13)
 //   sed[cam][f]        = sum_pix I A_pix / D^2 + sum_src L_nu exp(-tau_src) / (4 pi D^2)  (Eq. 17)
 //
@@ -37,11 +38,12 @@ struct RayKP {
     const void* rho;           // packed FP32 grid (rho * cell, Lucy sign bit ignored)
     int nx, ny, nz;
     float cell;
-    float kext[kMaxSpecies][kMaxImgFreq];   // cm^2/g
+    float kext[kMaxSpecies][kMaxImgFreq];   // cm^2/g (packed density is rho * cell)
+    float kext_cell[kMaxSpecies][kMaxImgFreq];  // kext * cell
     int nfi, nfp;
     size_t ncell;
-    const float* eta;          // [ncam_total][ncell][nfp]
-    const float* bk;           // [ns][ncell][nfp] (backward)
+    const float* eta;          // [ncam_total][ncell][nfp] eta * cell
+    const float* bk;           // [ns][ncell][nfp] kabs_s B(T_s) * cell (backward)
     CamDev cam[kCamChunk];
     int cam0, ncam;            // cameras of this launch: [cam0, cam0 + ncam)
     float* img;                // [ncam_total][nfi][npix][npix]
@@ -213,14 +215,13 @@ __global__ void __launch_bounds__(128) ray_fwd_kernel(const __grid_constant__ Ra
             load_rho<NS>(P, c, rho);
             load_eta<NFP>(eta_cam + (size_t)c * NFP, eta);
             const bool inside = dda_step(r, tcur, seg, P.nx, P.ny, P.nz);
-            const float seg_phys = seg * P.cell;
 #pragma unroll
             for (int f = 0; f < NFP; ++f) {
                 float chi = 0.f;
 #pragma unroll
                 for (int s = 0; s < NS; ++s) chi += rho[s] * P.kext[s][f];
                 const float dt = chi * seg;
-                const float contrib = eta[f] * seg_phys * phi_f(dt) * __expf(-tau[f]);
+                const float contrib = eta[f] * seg * phi_f(dt) * __expf(-tau[f]);
                 kahan_add(I[f], Ic[f], contrib);
                 kahan_add(tau[f], tc[f], dt);
             }
@@ -300,7 +301,6 @@ __global__ void __launch_bounds__(128) ray_bwd_kernel(const __grid_constant__ Ra
         load_rho<NS>(P, c, rho);
         load_eta<NFP>(eta_cam + (size_t)c * NFP, eta);
         const bool inside = dda_step(q, tcur, seg, P.nx, P.ny, P.nz);
-        const float seg_phys = seg * P.cell;
         float g[NS];
 #pragma unroll
         for (int s = 0; s < NS; ++s) g[s] = 0.f;
@@ -315,13 +315,14 @@ __global__ void __launch_bounds__(128) ray_bwd_kernel(const __grid_constant__ Ra
             const float att = __expf(-front);
             const float ph = phi_f(dt);
             const float dph = dphi_f(dt);
-            const float contrib = eta[f] * seg_phys * ph * att;
+            const float contrib = eta[f] * seg * ph * att;
 #pragma unroll
             for (int s = 0; s < NS; ++s) {
+                // per-cell-length quantities: bk and eta carry a factor cell,
+                // ke = kext_s cell converts d(dtau)/d(rho_s) = kext_s l_phys
                 const float bk = P.bk[((size_t)s * P.ncell + c) * NFP + f];
-                const float ke = P.kext[s][f];
-                g[s] += w[f] * ((bk * ph + eta[f] * dph * ke * seg_phys) * seg_phys * att
-                                - ke * seg_phys * beh[f]);
+                const float ke = P.kext_cell[s][f];
+                g[s] += w[f] * ((bk * ph + eta[f] * dph * ke * seg) * seg * att - ke * seg * beh[f]);
             }
             kahan_add(beh[f], behc[f], contrib);
         }
@@ -333,33 +334,54 @@ __global__ void __launch_bounds__(128) ray_bwd_kernel(const __grid_constant__ Ra
     count_steps(P.steps, nsteps);
 }
 
-// eta_th (and bk = kabs_s B(T_s) for the adjoint) for every camera's table
-__global__ void eta_thermal_kernel(const float* rho, const double* T, size_t nc, int ns, int nfi, int nfp,
-                                   const double* nu_f, const double* kabs_f /*[ns][nfi]*/, int ncam,
-                                   float* eta, float* bk)
+// eta_th * cell (and bk = kabs_s B(T_s) * cell for the adjoint) for every
+// camera's table, in FP32: B = a_f / expm1(h nu_f / k T) with a_f = 2 h nu^3/c^2.
+struct EtaKP {
+    const void* rho;           // packed FP32 grid: rho_s * cell
+    const double* T;           // [ns][nc]
+    size_t nc;
+    int ns, nfi, nfp, ncam;
+    float a[kMaxImgFreq], xh[kMaxImgFreq];
+    float kabs[kMaxSpecies][kMaxImgFreq];
+    float* eta;
+    float* bk;
+};
+
+template <int NS>
+__global__ void eta_thermal_kernel(const __grid_constant__ EtaKP P)
 {
     const size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-    if (c >= nc) return;
-    const double h = 6.62607015e-27, kb = 1.380649e-16, cl = 2.99792458e10;
-    for (int f = 0; f < nfp; ++f) {
-        double e = 0.0;
-        if (f < nfi) {
-            for (int s = 0; s < ns; ++s) {
-                const double Ts = T[s * nc + c];
-                double B = 0.0;
-                if (Ts > 0.0) {
-                    const double nu = nu_f[f];
-                    B = 2.0 * h * nu * nu * nu / (cl * cl) / expm1(h * nu / (kb * Ts));
-                }
-                const double b = kabs_f[s * nfi + f] * B;
-                e += (double)rho[s * nc + c] * b;
-                if (bk) bk[((size_t)s * nc + c) * nfp + f] = (float)b;
-            }
-        } else if (bk) {
-            for (int s = 0; s < ns; ++s) bk[((size_t)s * nc + c) * nfp + f] = 0.f;
+    if (c >= P.nc) return;
+    float rho[NS], invT[NS];
+    {
+        const typename PT<NS>::T v = __ldg(reinterpret_cast<const typename PT<NS>::T*>(P.rho) + c);
+        float r[4];
+        unpack(v, r);
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            rho[s] = r[s];
+            const float T = s < P.ns ? (float)P.T[s * P.nc + c] : 0.0f;
+            invT[s] = T > 0.0f ? 1.0f / T : 0.0f;
         }
-        for (int k = 0; k < ncam; ++k) eta[((size_t)k * nc + c) * nfp + f] = (float)e;
     }
+    for (int f = 0; f < P.nfp; ++f) {
+        float e = 0.0f;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            float b = 0.0f;
+            if (f < P.nfi && invT[s] > 0.0f) b = P.kabs[s][f] * P.a[f] / expm1f(P.xh[f] * invT[s]);
+            e += rho[s] * b;                                   // rho * cell * kabs * B
+            if (P.bk && s < P.ns) P.bk[((size_t)s * P.nc + c) * P.nfp + f] = b;   // times cell below
+        }
+        for (int k = 0; k < P.ncam; ++k) P.eta[((size_t)k * P.nc + c) * P.nfp + f] = e;
+    }
+}
+
+// bk was written as kabs B; scale it by the cell size
+__global__ void scale_kernel(float* v, size_t n, float a)
+{
+    const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i < n) v[i] *= a;
 }
 
 struct ScatKP {
@@ -374,7 +396,7 @@ struct ScatKP {
     double xi;
 };
 
-// eta_sca: every stored event adds xi / (V dnu) P_HG(k_in . k_obs) to its cell
+// eta_sca * cell: every stored event adds xi cell / (V dnu) P_HG(k_in . k_obs)
 __global__ void eta_scatter_kernel(const rt_event* ev, uint64_t nev, ScatKP P, float* eta)
 {
     const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
@@ -452,18 +474,24 @@ struct StarKP {
     float* grad;
 };
 
-// Direct light of each source along k_obs (FP64, one thread per (cam, src)).
-// Forward adds it to the SED; backward adds -dL/dF F kext_s l to the gradient.
+// Direct light of each source along k_obs (FP64, one thread per (camera,
+// source, frequency)).  Forward adds L_nu exp(-tau) / (4 pi D^2) to the SED;
+// backward adds -dL/dF F kext_s l to the density gradient.
 __global__ void star_kernel(const __grid_constant__ StarKP P, int backward)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= P.ncam * P.nsrc) return;
-    const int cam = t / P.nsrc, si = t % P.nsrc;
+    if (t >= P.ncam * P.nsrc * P.nfi) return;
+    const int f = t % P.nfi, si = (t / P.nfi) % P.nsrc, cam = t / (P.nfi * P.nsrc);
     const double d[3] = { P.kobs[3 * cam], P.kobs[3 * cam + 1], P.kobs[3 * cam + 2] };
     const int n[3] = { P.nx, P.ny, P.nz };
-    double tau[kMaxImgFreq];
-    for (int f = 0; f < P.nfi; ++f) tau[f] = 0.0;
+    double tau = 0.0;
+    double F = 0.0, wsed = 0.0;
     for (int pass = 0; pass < (backward ? 2 : 1); ++pass) {
+        if (pass == 1) {
+            F = P.lnu[si * P.nfi + f] * exp(-tau) * P.inv4piD2[cam];
+            wsed = P.dsed[cam * P.nfi + f];
+            if (wsed == 0.0 || F == 0.0) return;
+        }
         double x[3];
         int i[3];
         bool in = true;
@@ -475,7 +503,7 @@ __global__ void star_kernel(const __grid_constant__ StarKP P, int backward)
             i[a] = k;
             in = in && k >= 0 && k < n[a];
         }
-        while (in) {
+        for (int steps = 0; in && steps < P.nx + P.ny + P.nz + 4; ++steps) {
             double best = INFINITY;
             int ba = 0;
             for (int a = 0; a < 3; ++a) {
@@ -489,18 +517,12 @@ __global__ void star_kernel(const __grid_constant__ StarKP P, int backward)
             const size_t c = ((size_t)i[2] * P.ny + i[1]) * P.nx + i[0];
             const double l = best * P.cell;
             if (pass == 0) {
-                for (int f = 0; f < P.nfi; ++f) {
-                    double chi = 0.0;
-                    for (int s = 0; s < P.ns; ++s) chi += (double)P.rho[s * P.nc + c] * P.kext[s][f];
-                    tau[f] += chi * l;
-                }
+                double chi = 0.0;
+                for (int s = 0; s < P.ns; ++s) chi += (double)P.rho[s * P.nc + c] * P.kext[s][f];
+                tau += chi * l;
             } else {
                 for (int s = 0; s < P.ns; ++s) {
-                    double g = 0.0;
-                    for (int f = 0; f < P.nfi; ++f) {
-                        const double F = P.lnu[si * P.nfi + f] * exp(-tau[f]) * P.inv4piD2[cam];
-                        g -= P.dsed[cam * P.nfi + f] * F * P.kext[s][f] * l;
-                    }
+                    const double g = -wsed * F * P.kext[s][f] * l;
                     if (g != 0.0) atomicAdd(&P.grad[s * P.nc + c], (float)g);
                 }
             }
@@ -511,8 +533,7 @@ __global__ void star_kernel(const __grid_constant__ StarKP P, int backward)
         }
     }
     if (!backward)
-        for (int f = 0; f < P.nfi; ++f)
-            atomicAdd(&P.sed[cam * P.nfi + f], P.lnu[si * P.nfi + f] * exp(-tau[f]) * P.inv4piD2[cam]);
+        atomicAdd(&P.sed[cam * P.nfi + f], P.lnu[si * P.nfi + f] * exp(-tau) * P.inv4piD2[cam]);
 }
 
 // grad_total += grad_call;  dscale += sum rho * grad_call
@@ -658,15 +679,36 @@ rt_status raytrace_impl(rt_ctx* ctx, const rt_grid* g, const rt_opacity* op, con
 
     float* bk = backward ? ctx->d_bk : nullptr;
     float* gcall = backward ? ctx->d_bk + (size_t)ns * nc * nfp : nullptr;
-    eta_thermal_kernel<<<(unsigned)((nc + 255) / 256), 256, 0, s>>>(
-        g->d_rho, T, nc, ns, nfi, nfp, (const double*)(dbuf + o_nu), (const double*)(dbuf + o_ka),
-        ncam, ctx->d_eta, bk);
-    count_launches();
-    RT_CUDA(cudaGetLastError());
+    {
+        EtaKP ek;
+        std::memset(&ek, 0, sizeof(ek));
+        ek.rho = g->d_packed; ek.T = T; ek.nc = nc; ek.ns = ns; ek.nfi = nfi; ek.nfp = nfp;
+        ek.ncam = ncam; ek.eta = ctx->d_eta; ek.bk = bk;
+        const double hP = 6.62607015e-27, kB = 1.380649e-16, cl = 2.99792458e10;
+        for (int f = 0; f < nfi; ++f) {
+            const double nu = op->nu[fidx[f]];
+            ek.a[f] = (float)(2.0 * hP * nu * nu * nu / (cl * cl));
+            ek.xh[f] = (float)(hP * nu / kB);
+            for (int sp = 0; sp < ns; ++sp) ek.kabs[sp][f] = (float)op->kabs[sp * op->nf + fidx[f]];
+        }
+        const unsigned blocks = (unsigned)((nc + 255) / 256);
+        const int vec = ns == 1 ? 1 : (ns == 2 ? 2 : 4);
+        if (vec == 1) eta_thermal_kernel<1><<<blocks, 256, 0, s>>>(ek);
+        else if (vec == 2) eta_thermal_kernel<2><<<blocks, 256, 0, s>>>(ek);
+        else eta_thermal_kernel<4><<<blocks, 256, 0, s>>>(ek);
+        count_launches();
+        RT_CUDA(cudaGetLastError());
+        if (bk) {
+            const size_t nb = (size_t)ns * nc * nfp;
+            scale_kernel<<<(unsigned)((nb + 255) / 256), 256, 0, s>>>(bk, nb, (float)g->cell);
+            count_launches();
+            RT_CUDA(cudaGetLastError());
+        }
+    }
     if (nev > 0) {
         ScatKP sk;
         sk.ncam = ncam; sk.nfi = nfi; sk.nfp = nfp; sk.nc = nc;
-        sk.inv_vol = 1.0 / (g->cell * g->cell * g->cell);
+        sk.inv_vol = 1.0 / (g->cell * g->cell);   // eta * cell: xi cell / V
         sk.kobs = (const float*)(dbuf + o_ko);
         sk.f_of_nu = (const int*)(dbuf + o_fn);
         sk.g = op->d_g; sk.dnu = op->d_dnu; sk.nf = op->nf; sk.ns = ns; sk.xi = xi_ev;
@@ -688,8 +730,11 @@ rt_status raytrace_impl(rt_ctx* ctx, const rt_grid* g, const rt_opacity* op, con
     kp.nx = g->nx; kp.ny = g->ny; kp.nz = g->nz;
     kp.cell = (float)g->cell;
     for (int sp = 0; sp < ns; ++sp)
-        for (int f = 0; f < nfi; ++f)
-            kp.kext[sp][f] = (float)(op->kabs[sp * op->nf + fidx[f]] + op->ksca[sp * op->nf + fidx[f]]);
+        for (int f = 0; f < nfi; ++f) {
+            const double ke = op->kabs[sp * op->nf + fidx[f]] + op->ksca[sp * op->nf + fidx[f]];
+            kp.kext[sp][f] = (float)ke;
+            kp.kext_cell[sp][f] = (float)(ke * g->cell);
+        }
     kp.nfi = nfi; kp.nfp = nfp; kp.ncell = nc;
     kp.eta = ctx->d_eta; kp.bk = bk;
     kp.img = images; kp.dimg = dimg; kp.dsed = dsed; kp.grad = gcall;
@@ -724,7 +769,7 @@ rt_status raytrace_impl(rt_ctx* ctx, const rt_grid* g, const rt_opacity* op, con
         sp.inv4piD2 = (const double*)(dbuf + o_i4);
         sp.nsrc = nsrc; sp.ncam = ncam;
         sp.sed = sed; sp.dsed = dsed; sp.grad = gcall;
-        const int nt = ncam * nsrc;
+        const int nt = ncam * nsrc * nfi;
         star_kernel<<<(nt + 63) / 64, 64, 0, s>>>(sp, backward ? 1 : 0);
         count_launches();
         RT_CUDA(cudaGetLastError());

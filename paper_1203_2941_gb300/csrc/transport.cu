@@ -243,13 +243,26 @@ __device__ __forceinline__ float mrw_y32(const float* S, float u)
     return ((float)lo + w) * (float)(kMrwYmax / (kMrwN - 1));
 }
 
-// log2 of a positive double without FP64 transcendental work
+// log2 of a positive double using only integer work and an FP32 log2 of the
+// top 23 mantissa bits (GB300 has little FP64 throughput)
 __device__ __forceinline__ float log2_d(double v)
 {
-    const int hi = __double2hiint(v);
-    const int e = ((hi >> 20) & 0x7ff) - 1023;
-    const double m = __hiloint2double((hi & 0x800fffff) | 0x3ff00000, __double2loint(v));
-    return (float)e + __log2f((float)m);
+    const unsigned hi = (unsigned)__double2hiint(v);
+    const unsigned lo = (unsigned)__double2loint(v);
+    const int e = (int)((hi >> 20) & 0x7ffu) - 1023;
+    const float m = __uint_as_float(0x3f800000u | ((hi & 0xfffffu) << 3) | (lo >> 29));
+    return (float)e + __log2f(m);
+}
+
+// Exact float -> double by re-biasing the exponent with integer operations
+// (no FP64 pipe); zero and denormal inputs give 0.
+__device__ __forceinline__ double f2d(float f)
+{
+    const unsigned b = __float_as_uint(f);
+    const unsigned e = (b >> 23) & 0xffu;
+    if (e == 0u) return 0.0;
+    const unsigned hi = (b & 0x80000000u) | ((e + (1023u - 127u)) << 20) | ((b & 0x7fffffu) >> 3);
+    return __hiloint2double((int)hi, (int)((b & 7u) << 29));
 }
 
 // ------------------------------------------------------------- per-lane packet state
@@ -266,9 +279,22 @@ struct Lane {
     R tm[3], td[3];
     R rho[NS];                 // current cell (FP32: rho*cell; FP64: rho)
     bool lucy;
+    int sx, sy, sz;            // step direction per axis (+1 / -1)
+    const void* grid;          // packed cells of the packet's model
+    int nx, ny, nz;
     R chi;                     // extinction per cell length at frequency j
     R kex[NS], kab[NS];        // kext, kabs at frequency j (FP64: times cell)
 };
+
+// a[s] for a register array and a run-time index, without local memory
+template <typename R, int NS>
+__device__ __forceinline__ R sel(const R (&a)[NS], int s)
+{
+    R v = a[0];
+#pragma unroll
+    for (int q = 1; q < NS; ++q) v = (s == q) ? a[q] : v;
+    return v;
+}
 
 struct Counters {
     unsigned long long cross;
@@ -293,12 +319,13 @@ struct Kernel {
         : P(p), s_op(op), s_xh(xh), s_w(w), s_mrw(mrw), md(nullptr)
     {
         cnt.cross = 0;
+#pragma unroll
         for (int i = 0; i < C_N; ++i) cnt.c[i] = 0;
     }
 
     __device__ __forceinline__ void load_cell(Lane<R, NS>& L)
     {
-        const PT v = __ldg(reinterpret_cast<const PT*>(md->rho) + L.c);
+        const PT v = __ldg(reinterpret_cast<const PT*>(L.grid) + L.c);
         float r[4];
         unpack(v, r);
         L.lucy = signbit(r[0]);
@@ -333,7 +360,7 @@ struct Kernel {
         L.chi = chi;
     }
 
-    __device__ void traj(Lane<R, NS>& L, uint32_t type, const R* x)
+    __device__ __forceinline__ void traj(Lane<R, NS>& L, uint32_t type, const R* x)
     {
         const uint32_t q = L.seq++;
         if (md->traj == nullptr) return;
@@ -344,6 +371,7 @@ struct Kernel {
         }
         rt_traj t;
         t.pid = L.pid; t.seq = q; t.type = type; t.cell = (uint32_t)L.c; t.nu = (uint32_t)L.j;
+#pragma unroll
         for (int a = 0; a < 3; ++a) {
             t.x[a] = md->box_min[a] + (double)x[a] * md->cell;
             t.k[a] = (double)L.k[a];
@@ -363,7 +391,7 @@ struct Kernel {
         return lo;
     }
 
-    __device__ void emit(Lane<R, NS>& L, uint64_t w)
+    __device__ __forceinline__ void emit(Lane<R, NS>& L, uint64_t w)
     {
         // model lookup: largest m with prefix[m] <= w
         int lo = 0, hi = P.n_models - 1;
@@ -376,6 +404,8 @@ struct Kernel {
             L.m = lo;
         }
         md = &P.models[lo];
+        L.grid = md->rho;
+        L.nx = md->nx; L.ny = md->ny; L.nz = md->nz;
         L.pid = md->pid_begin + (w - P.prefix[lo]);
         rng_init(L.rng, P.seed, md->model_id, L.pid);
         L.seq = 0;
@@ -422,32 +452,57 @@ struct Kernel {
         L.st = ST_FLIGHT;
     }
 
+    // Energy deposited along a path of l cells in a Lucy cell (Sect. 3.1).
+    // FP64 build: straight into E_abs.  FP32 build: into the call's FP64
+    // scratch in units of xi, converted with integer work and added by L2
+    // atomics, so the crossing loop issues no FP64 arithmetic.
     __device__ __forceinline__ void deposit_lucy(Lane<R, NS>& L, R l)
     {
-        const size_t nc = (size_t)md->nx * md->ny * md->nz;
+        const size_t nc = (size_t)L.nx * L.ny * L.nz;
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
-            const R ta = L.kab[s] * L.rho[s] * l;
-            double e;
-            if (P.lucy_form == RT_LUCY_EXPM1) e = -(double)r_expm1(-ta) * md->xi;
-            else e = (double)ta * md->xi;
-            if (e != 0.0) {
-                atomicAdd(&md->E_abs[s * nc + L.c], e);
-                if (md->esq) atomicAdd(&md->esq[s * nc + L.c], e * e);
+            const R ta0 = L.kab[s] * L.rho[s] * l;
+            const R ta = P.lucy_form == RT_LUCY_EXPM1 ? -r_expm1(-ta0) : ta0;
+            if constexpr (DBG) {
+                const double e = ta * md->xi;
+                if (e != 0.0) {
+                    atomicAdd(&md->E_abs[s * nc + L.c], e);
+                    if (md->esq) atomicAdd(&md->esq[s * nc + L.c], e * e);
+                }
+            } else {
+                if (ta > 0.0f) {
+                    atomicAdd(&md->accE[s * nc + L.c], f2d(ta));
+                    if (md->accQ) atomicAdd(&md->accQ[s * nc + L.c], f2d(ta * ta));
+                }
             }
         }
         cnt.c[C_LUCY]++;
+    }
+
+    // Accumulated absorbed power (erg/s) of species s in the lane's cell,
+    // including this call's FP32-build scratch; `old` is the value an atomic
+    // add just returned (then the packet's own xi is added).
+    __device__ __forceinline__ double energy(const Lane<R, NS>& L, int s, double old, bool have_old)
+    {
+        const size_t i = (size_t)s * L.nx * L.ny * L.nz + L.c;
+        if constexpr (DBG) {
+            return have_old ? old + md->xi : __ldcg(&md->E_abs[i]);
+        } else {
+            const double acc = have_old ? old + 1.0 : __ldcg(&md->accE[i]);
+            return __ldcg(&md->E_abs[i]) + acc * md->xi;
+        }
     }
 
     // Temperature of species s in cell c from the accumulated energy (Eq. 4)
     __device__ __forceinline__ R temperature(const Lane<R, NS>& L, int s, double E)
     {
         if constexpr (DBG) {
-            const double rv = L.rho[s] * md->vol;
+            const double rv = sel(L.rho, s) * md->vol;
             return rv > 0.0 ? solve_T64(P, s, E / rv) : 0.0;
         } else {
-            if (!(E > 0.0) || !(L.rho[s] > 0.0f)) return 0.0f;
-            const float y = log2_d(E) - __log2f(L.rho[s]) - (float)md->log2_4piV;
+            const float rs = sel(L.rho, s);
+            if (!(E > 0.0) || !(rs > 0.0f)) return 0.0f;
+            const float y = log2_d(E) - __log2f(rs) - (float)md->log2_4piV;
             float f = (y - P.tinv_y0[s]) * P.tinv_inv_dy[s];
             f = fminf(fmaxf(f, 0.0f), (float)(kTinvN - 1));
             const int i = min((int)f, kTinvN - 2);
@@ -458,9 +513,9 @@ struct Kernel {
     }
 
     // Re-emission frequency: Eq. 10 (B&W, dB/dT weights) or Eq. 5 (frozen T)
-    __device__ int reemit(const Lane<R, NS>& L, int s, double E, R u)
+    __device__ __forceinline__ int reemit(const Lane<R, NS>& L, int s, double E, R u)
     {
-        const size_t nc = (size_t)md->nx * md->ny * md->nz;
+        const size_t nc = (size_t)L.nx * L.ny * L.nz;
         const bool bw = P.mode == RT_MODE_BW;
         R T;
         if (bw) T = temperature(L, s, E);
@@ -526,7 +581,7 @@ struct Kernel {
         return NS - 1;
     }
 
-    __device__ void store_pah(Lane<R, NS>& L, const R* x)
+    __device__ __forceinline__ void store_pah(Lane<R, NS>& L, const R* x)
     {
         const unsigned long long slot = atomicAdd(&md->stats[RT_STAT_N_PAH], 1ull);
         if (md->pah && slot < md->pah_cap) {
@@ -544,7 +599,7 @@ struct Kernel {
     __device__ __forceinline__ bool is_pah(int s) const { return (P.pah_mask >> s) & 1; }
 
     // A new flight from L.x along L.k: MRW step or tau draw + traversal set-up
-    __device__ void flight(Lane<R, NS>& L)
+    __device__ __forceinline__ void flight(Lane<R, NS>& L)
     {
         if (P.mrw && P.mode != RT_MODE_NOREEMIT && L.chi > (R)P.mrw_tau_cell) {
             R R0 = R(1e30);
@@ -576,11 +631,14 @@ struct Kernel {
                 L.tm[a] = R(INFINITY);
             }
         }
+        L.sx = L.k[0] > R(0) ? 1 : -1;
+        L.sy = L.k[1] > R(0) ? 1 : -1;
+        L.sz = L.k[2] > R(0) ? 1 : -1;
         L.tcur = R(0);
         L.st = ST_MARCH;
     }
 
-    __device__ void mrw_step(Lane<R, NS>& L, R R0)
+    __device__ __forceinline__ void mrw_step(Lane<R, NS>& L, R R0)
     {
         if (++L.nev > P.max_events) {
             cnt.c[C_STUCK]++;
@@ -598,15 +656,21 @@ struct Kernel {
 #pragma unroll
         for (int a = 0; a < 3; ++a) L.x[a] += R0 * nh[a];
         { const R u3 = rng_u<R>(L.rng), u4 = rng_u<R>(L.rng); iso_dir(u3, u4, L.k); }
-        const size_t nc = (size_t)md->nx * md->ny * md->nz;
+        const size_t nc = (size_t)L.nx * L.ny * L.nz;
         R ca = R(0);
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
-            const double e = (double)(L.kab[s] * L.rho[s] * l) * md->xi;
+            const R ta = L.kab[s] * L.rho[s] * l;
             ca += L.kab[s] * L.rho[s];
-            if (e != 0.0) {
-                atomicAdd(&md->E_abs[s * nc + L.c], e);
-                if (md->esq) atomicAdd(&md->esq[s * nc + L.c], e * e);
+            if constexpr (DBG) {
+                const double e = ta * md->xi;
+                if (e != 0.0) {
+                    atomicAdd(&md->E_abs[s * nc + L.c], e);
+                    if (md->esq) atomicAdd(&md->esq[s * nc + L.c], e * e);
+                }
+            } else if (ta > 0.0f) {
+                atomicAdd(&md->accE[s * nc + L.c], f2d(ta));
+                if (md->accQ) atomicAdd(&md->accQ[s * nc + L.c], f2d(ta * ta));
             }
         }
         cnt.c[C_MRW]++;
@@ -614,7 +678,7 @@ struct Kernel {
             int s = 0;
             if (NS > 1) s = pick_species(L, false, rng_u<R>(L.rng));
             if (is_pah(s)) { store_pah(L, L.x); return; }
-            const double E = __ldcg(&md->E_abs[s * nc + L.c]);
+            const double E = energy(L, s, 0.0, false);
             L.j = reemit(L, s, E, rng_u<R>(L.rng));
             load_freq(L);
         }
@@ -622,11 +686,14 @@ struct Kernel {
         L.st = ST_FLIGHT;
     }
 
-    // One cell traversal step of a marching lane.
+    // One cell traversal step of a marching lane: the nearest of the three
+    // face distances decides the axis (ties to the lowest axis); the update is
+    // branch-free so lanes stepping along different axes stay converged.
     __device__ __forceinline__ void march(Lane<R, NS>& L)
     {
         const bool ax = (L.tm[0] <= L.tm[1]) && (L.tm[0] <= L.tm[2]);
         const bool ay = !ax && (L.tm[1] <= L.tm[2]);
+        const bool az = !ax && !ay;
         const R tn = ax ? L.tm[0] : (ay ? L.tm[1] : L.tm[2]);
         const R seg = tn - L.tcur;
         const R dtau = L.chi * seg;
@@ -634,34 +701,20 @@ struct Kernel {
             if (L.lucy) deposit_lucy(L, seg);
             L.tau -= dtau;
             L.tcur = tn;
-            bool out;
-            if (ax) {
-                const int st = L.k[0] > R(0) ? 1 : -1;
-                L.tm[0] += L.td[0];
-                L.ix += st;
-                L.c += st;
-                out = (unsigned)L.ix >= (unsigned)md->nx;
-            } else if (ay) {
-                const int st = L.k[1] > R(0) ? 1 : -1;
-                L.tm[1] += L.td[1];
-                L.iy += st;
-                L.c += st * md->nx;
-                out = (unsigned)L.iy >= (unsigned)md->ny;
-            } else {
-                const int st = L.k[2] > R(0) ? 1 : -1;
-                L.tm[2] += L.td[2];
-                L.iz += st;
-                L.c += st * md->nx * md->ny;
-                out = (unsigned)L.iz >= (unsigned)md->nz;
-            }
+            L.tm[0] = ax ? L.tm[0] + L.td[0] : L.tm[0];
+            L.tm[1] = ay ? L.tm[1] + L.td[1] : L.tm[1];
+            L.tm[2] = az ? L.tm[2] + L.td[2] : L.tm[2];
+            const int nix = L.ix + (ax ? L.sx : 0);
+            const int niy = L.iy + (ay ? L.sy : 0);
+            const int niz = L.iz + (az ? L.sz : 0);
+            const bool out = ((unsigned)nix >= (unsigned)L.nx) | ((unsigned)niy >= (unsigned)L.ny) |
+                             ((unsigned)niz >= (unsigned)L.nz);
             cnt.cross++;
             if (out) {
-                // restore the last cell inside for the escape record
-                if (ax) { L.ix -= (L.k[0] > R(0) ? 1 : -1); L.c -= (L.k[0] > R(0) ? 1 : -1); }
-                else if (ay) { L.iy -= (L.k[1] > R(0) ? 1 : -1); L.c -= (L.k[1] > R(0) ? 1 : -1) * md->nx; }
-                else { L.iz -= (L.k[2] > R(0) ? 1 : -1); L.c -= (L.k[2] > R(0) ? 1 : -1) * md->nx * md->ny; }
-                L.st = ST_ESCAPE;
+                L.st = ST_ESCAPE;          // ix, iy, iz, c keep the last cell inside
             } else {
+                L.c += ax ? L.sx : (ay ? L.sy * L.nx : L.sz * L.nx * L.ny);
+                L.ix = nix; L.iy = niy; L.iz = niz;
                 load_cell(L);
             }
         } else {
@@ -674,7 +727,7 @@ struct Kernel {
         }
     }
 
-    __device__ void interact(Lane<R, NS>& L)
+    __device__ __forceinline__ void interact(Lane<R, NS>& L)
     {
         if (++L.nev > P.max_events) {
             cnt.c[C_STUCK]++;
@@ -722,13 +775,20 @@ struct Kernel {
         int s = 0;
         if (NS > 1) s = pick_species(L, false, rng_u<R>(L.rng));
         if (is_pah(s)) { store_pah(L, L.x); return; }
-        const size_t nc = (size_t)md->nx * md->ny * md->nz;
+        const size_t nc = (size_t)L.nx * L.ny * L.nz;
         double E = 0.0;
         if (!L.lucy) {
-            E = atomicAdd(&md->E_abs[s * nc + L.c], md->xi) + md->xi;
-            if (md->esq) atomicAdd(&md->esq[s * nc + L.c], md->xi * md->xi);
+            double old;
+            if constexpr (DBG) {
+                old = atomicAdd(&md->E_abs[s * nc + L.c], md->xi);
+                if (md->esq) atomicAdd(&md->esq[s * nc + L.c], md->xi * md->xi);
+            } else {
+                old = atomicAdd(&md->accE[s * nc + L.c], 1.0);
+                if (md->accQ) atomicAdd(&md->accQ[s * nc + L.c], 1.0);
+            }
+            if (P.mode == RT_MODE_BW) E = energy(L, s, old, true);
         } else if (P.mode == RT_MODE_BW) {
-            E = __ldcg(&md->E_abs[s * nc + L.c]);
+            E = energy(L, s, 0.0, false);
         }
         atomicAdd(&md->count[s * nc + L.c], 1u);
         if (P.mode == RT_MODE_NOREEMIT) {
@@ -743,7 +803,7 @@ struct Kernel {
         L.st = ST_FLIGHT;
     }
 
-    __device__ void escape(Lane<R, NS>& L)
+    __device__ __forceinline__ void escape(Lane<R, NS>& L)
     {
         int b = (int)floor((L.k[2] + R(1)) * R(5));
         b = min(max(b, 0), kSedBins - 1);
@@ -760,7 +820,7 @@ struct Kernel {
     }
 
     // add this lane's counters to model m's stats
-    __device__ void flush(int m)
+    __device__ __forceinline__ void flush(int m)
     {
         unsigned long long* st = P.models[m].stats;
         if (cnt.cross) atomicAdd(&st[RT_STAT_CROSSINGS], cnt.cross);
@@ -771,12 +831,14 @@ struct Kernel {
         for (int i = 0; i < C_N; ++i)
             if (cnt.c[i]) atomicAdd(&st[map[i]], (unsigned long long)cnt.c[i]);
         cnt.cross = 0;
+#pragma unroll
         for (int i = 0; i < C_N; ++i) cnt.c[i] = 0;
     }
 };
 
 template <typename R, int NS>
-__global__ void __launch_bounds__(256) transport_kernel(const TransportKP P, int serial)
+__global__ void __launch_bounds__(256, 3) transport_kernel(const __grid_constant__ TransportKP P,
+                                                           int serial)
 {
     extern __shared__ float4 smem[];
     float4* s_op = smem;
@@ -891,6 +953,19 @@ __global__ void pack_kernel(const float* rho, size_t nc, const double* kext_max_
     else out[i] = make_float4(v[0], v[1], v[2], v[3]);
 }
 
+// E_abs += accE * xi and esq += accQ * xi^2 for one model (FP32 build)
+__global__ void finalize_kernel(const double* accE, const double* accQ, size_t n, double xi,
+                                double* E_abs, double* esq)
+{
+    const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double a = accE[i];
+    if (a != 0.0) {
+        E_abs[i] += a * xi;
+        if (esq && accQ) esq[i] += accQ[i] * xi * xi;
+    }
+}
+
 __global__ void kext_kernel(const double* kabs, const double* ksca, double* kext, int n)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -958,6 +1033,16 @@ rt_status pack_grid(rt_grid* g, const rt_opacity* op, int lucy_mode, double lucy
     g->packed_lucy_mode = lucy_mode;
     g->packed_lucy_tau = lucy_tau;
     g->packed_prec = prec;
+    return RT_OK;
+}
+
+rt_status launch_finalize(const double* accE, const double* accQ, size_t n, double xi,
+                          double* E_abs, double* esq, cudaStream_t s)
+{
+    if (n == 0) return RT_OK;
+    finalize_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(accE, accQ, n, xi, E_abs, esq);
+    count_launches();
+    RT_CUDA(cudaGetLastError());
     return RT_OK;
 }
 
