@@ -85,7 +85,7 @@ class ClockSampler:
              "clocks_event_reasons.sw_power_cap")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
-                                          "-i", str(self.index), "-lms", "200"],
+                                          "-i", str(self.index), "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -320,7 +320,7 @@ def main():
                               "raytrace": sum(t_ray) / K},
                 "raytrace": {"metric": "ray-cell steps/s", "value": rsteps / (sum(t_ray) / 1e3),
                              "ray_cell_steps_per_step": rsteps // K},
-                "stats_per_step": {k: v // K for k, v in S.items()},
+                "stats_per_step": {k: v // K for k, v in S.items() if not k.startswith("n_")},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
                 "gpu_launches": launches}
         print(json.dumps(line), flush=True)

@@ -36,7 +36,8 @@ namespace rtgb {
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
-enum { ST_NEED = 0, ST_FLIGHT = 1, ST_MARCH = 2, ST_INTERACT = 3, ST_ESCAPE = 4, ST_DONE = 5 };
+enum { ST_NEED = 0, ST_FLIGHT = 1, ST_MARCH = 2, ST_INTERACT = 3, ST_ESCAPE = 4, ST_DONE = 5,
+       ST_REEMIT = 6, ST_REEMITTED = 7 };
 enum { C_INT, C_SCA, C_ABS, C_MRW, C_ESC, C_STUCK, C_PAH, C_LUCY, C_EMIT, C_N };
 constexpr double kPi = 3.14159265358979323846;
 
@@ -284,6 +285,8 @@ struct Lane {
     int nx, ny, nz;
     R chi;                     // extinction per cell length at frequency j
     R kex[NS], kab[NS];        // kext, kabs at frequency j (FP64: times cell)
+    int rs;                    // species of a pending re-emission (ST_REEMIT);
+                               // its temperature and uniform ride in tau and tcur
 };
 
 // a[s] for a register array and a run-time index, without local memory
@@ -513,13 +516,23 @@ struct Kernel {
     }
 
     // Re-emission frequency: Eq. 10 (B&W, dB/dT weights) or Eq. 5 (frozen T)
+    // Temperature that sets the re-emission spectrum: Eq. 4 at the updated
+    // energy (B&W) or the previous iteration's value (frozen T)
+    __device__ __forceinline__ R emission_T(const Lane<R, NS>& L, int s, double E)
+    {
+        if (P.mode == RT_MODE_BW) return temperature(L, s, E);
+        const size_t nc = (size_t)L.nx * L.ny * L.nz;
+        return (R)md->T_prev[s * nc + L.c];
+    }
+
     __device__ __forceinline__ int reemit(const Lane<R, NS>& L, int s, double E, R u)
     {
-        const size_t nc = (size_t)L.nx * L.ny * L.nz;
+        return reemit_T(s, emission_T(L, s, E), u);
+    }
+
+    __device__ __forceinline__ int reemit_T(int s, R T, R u)
+    {
         const bool bw = P.mode == RT_MODE_BW;
-        R T;
-        if (bw) T = temperature(L, s, E);
-        else T = (R)md->T_prev[s * nc + L.c];
         const int nf = P.nf;
         if constexpr (DBG) {
             double tot = 0.0;
@@ -555,8 +568,69 @@ struct Kernel {
     __device__ __forceinline__ float weight(float x, bool bw)
     {
         const float em = __expf(-x);
-        const float om = x < 0.05f ? -expm1f(-x) : 1.0f - em;
-        return bw ? em / (om * om) : em / om;
+        const float om = x < 0.05f ? x * (1.0f - x * (0.5f - x * (1.0f / 6.0f))) : 1.0f - em;
+        return bw ? __fdividef(em, om * om) : __fdividef(em, om);
+    }
+
+    // Re-emission bins for every lane waiting in ST_REEMIT, served one lane at
+    // a time by the whole warp: each lane weighs a slice of the frequency bins
+    // (Eq. 10 or Eq. 5 weights at that lane's temperature), a warp sum gives
+    // the total, and a chunked inclusive warp scan with a ballot finds the
+    // smallest bin whose running sum reaches u times the total.  All 32 lanes
+    // must call this (FP32 build, persistent schedule).
+    __device__ __forceinline__ void reemit_warp(Lane<R, NS>& L, int lane)
+    {
+        unsigned m = __ballot_sync(FULL, L.st == ST_REEMIT);
+        const bool bw = P.mode == RT_MODE_BW;
+        const int nf = P.nf;
+        while (m) {
+            const int src = __ffs(m) - 1;
+            const float T = __shfl_sync(FULL, (float)L.tau, src);
+            const float u = __shfl_sync(FULL, (float)L.tcur, src);
+            const int s = __shfl_sync(FULL, L.rs, src);
+            int bin = 0;
+            if (T > 0.0f) {
+                const float invT = 1.0f / T;
+                const float* w = s_w + s * nf;
+                float tot = 0.0f;
+                for (int b = lane; b < nf; b += 32) tot += w[b] * weight(s_xh[b] * invT, bw);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(FULL, tot, o);
+                const float target = u * tot;
+                float carry = 0.0f;
+                bin = nf - 1;
+                for (int b0 = 0; b0 < nf; b0 += 32) {
+                    const int b = b0 + lane;
+                    float v = b < nf ? w[b] * weight(s_xh[b] * invT, bw) : 0.0f;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const float t = __shfl_up_sync(FULL, v, o);
+                        if (lane >= o) v += t;
+                    }
+                    v += carry;
+                    const unsigned hit = __ballot_sync(FULL, b < nf && v >= target);
+                    if (hit) {
+                        bin = b0 + __ffs(hit) - 1;
+                        break;
+                    }
+                    carry = __shfl_sync(FULL, v, 31);
+                }
+            }
+            if (lane == src) {
+                L.j = bin;
+                L.st = ST_REEMITTED;
+            }
+            m &= m - 1;
+        }
+    }
+
+    // after the re-emission bin is known: isotropic direction, new flight
+    __device__ __forceinline__ void finish_absorb(Lane<R, NS>& L)
+    {
+        { const R u1 = rng_u<R>(L.rng), u2 = rng_u<R>(L.rng); iso_dir(u1, u2, L.k); }
+        load_freq(L);
+        traj(L, RT_TRAJ_ABSORB, L.x);
+        L.st = ST_FLIGHT;
     }
 
     __device__ __forceinline__ int pick_species(const Lane<R, NS>& L, bool sca, R u)
@@ -727,7 +801,8 @@ struct Kernel {
         }
     }
 
-    __device__ __forceinline__ void interact(Lane<R, NS>& L)
+    // coop: defer the re-emission CDF to reemit_warp (FP32, persistent)
+    __device__ __forceinline__ void interact(Lane<R, NS>& L, bool coop = false)
     {
         if (++L.nev > P.max_events) {
             cnt.c[C_STUCK]++;
@@ -796,11 +871,16 @@ struct Kernel {
             L.st = ST_NEED;
             return;
         }
-        L.j = reemit(L, s, E, rng_u<R>(L.rng));
-        { const R u1 = rng_u<R>(L.rng), u2 = rng_u<R>(L.rng); iso_dir(u1, u2, L.k); }
-        load_freq(L);
-        traj(L, RT_TRAJ_ABSORB, L.x);
-        L.st = ST_FLIGHT;
+        const R u = rng_u<R>(L.rng);
+        if (coop) {
+            L.tau = emission_T(L, s, E);
+            L.tcur = u;
+            L.rs = s;
+            L.st = ST_REEMIT;
+            return;
+        }
+        L.j = reemit(L, s, E, u);
+        finish_absorb(L);
     }
 
     __device__ __forceinline__ void escape(Lane<R, NS>& L)
@@ -906,12 +986,20 @@ __global__ void __launch_bounds__(256, 3) transport_kernel(const __grid_constant
             }
             nm = __popc(__ballot_sync(FULL, L.st == ST_MARCH));
         } while (nm > min_active);
+        constexpr bool COOP = sizeof(R) == 4;
         if (L.st == ST_INTERACT) {
             K.md = &P.models[L.m];
-            K.interact(L);
+            K.interact(L, COOP);
         } else if (L.st == ST_ESCAPE) {
             K.md = &P.models[L.m];
             K.escape(L);
+        }
+        if constexpr (COOP) {
+            K.reemit_warp(L, lane);
+            if (L.st == ST_REEMITTED) {
+                K.md = &P.models[L.m];
+                K.finish_absorb(L);
+            }
         }
     }
     if (L.m >= 0) K.flush(L.m);
