@@ -471,7 +471,7 @@ rt_status rt_transport(rt_ctx* ctx, const rt_grid* grid, const rt_opacity* op,
         RT_CUDA(cudaMallocAsync((void**)&acc, bytes, s));
         RT_CUDA(cudaMemsetAsync(acc, 0, bytes, s));
         hms[0].md.accE = acc;
-        hms[0].md.accQ = out->esq ? acc + n_acc : nullptr;
+        hms[0].md.acc_q = out->esq ? 1 : 0;
     }
     DeviceModels dm;
     st = stage_models(hms, { p->pid_end - p->pid_begin }, op->nf, true, s, dm);
@@ -482,7 +482,7 @@ rt_status rt_transport(rt_ctx* ctx, const rt_grid* grid, const rt_opacity* op,
     const int threads = p->threads_per_block ? p->threads_per_block : 256;
     st = launch_transport(ctx, op, kp, op->ns, p->precision, p->schedule, threads, p->blocks_per_sm, s);
     if (st == RT_OK && acc)
-        st = launch_finalize(acc, hms[0].md.accQ, n_acc, hms[0].md.xi, out->E_abs, out->esq, s);
+        st = launch_finalize(acc, hms[0].md.acc_q, n_acc, hms[0].md.xi, out->E_abs, out->esq, s);
     cudaFreeAsync(dm.buf, s);
     if (acc) cudaFreeAsync(acc, s);
     return st;
@@ -534,9 +534,8 @@ rt_status rt_batch_create(rt_ctx* ctx, const rt_opacity* op, int n_models, const
         for (int m = 0; m < n_models; ++m) {
             const size_t n = (size_t)op->ns * models[m].grid->ncell();
             hms[m].md.accE = b->acc + off;
-            off += n;
-            hms[m].md.accQ = models[m].out.esq ? b->acc + off : nullptr;
-            if (models[m].out.esq) off += n;
+            hms[m].md.acc_q = models[m].out.esq ? 1 : 0;
+            off += n * (models[m].out.esq ? 2 : 1);
         }
     }
     for (int m = 0; m < n_models; ++m) {
@@ -562,7 +561,7 @@ rt_status rt_batch_run(rt_batch* b, rt_stream stream)
     if (st != RT_OK || !b->acc) return st;
     for (int m = 0; m < b->n_models; ++m) {
         const ModelDev& md = b->host[m];
-        st = launch_finalize(md.accE, md.accQ, b->n_acc[m], md.xi, md.E_abs, md.esq, s);
+        st = launch_finalize(md.accE, md.acc_q, b->n_acc[m], md.xi, md.E_abs, md.esq, s);
         if (st != RT_OK) return st;
     }
     return RT_OK;

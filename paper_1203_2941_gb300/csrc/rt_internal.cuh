@@ -100,7 +100,8 @@ struct ModelDev {
     const double* src_cdf64;   // [nsrc][nf] cumulative L_nu dnu
     const float* src_cdf32;    // [nsrc][nf] cumulative, normalised to 1
     double* E_abs; uint32_t* count; double* esq;
-    double* accE; double* accQ;  // FP32 build: this call's deposits in units of xi (xi^2)
+    double* accE;              // FP32 build: this call's deposits in units of xi; with
+    int acc_q;                 // acc_q = 1 each cell holds {sum, sum of squares} (xi, xi^2)
     double* sed_esc; unsigned long long* sed_cnt;
     const double* T_prev;
     rt_event* events; uint64_t event_cap;
@@ -162,8 +163,8 @@ rt_status pack_grid(rt_grid* g, const rt_opacity* op, int lucy_mode, double lucy
 rt_status launch_transport(rt_ctx* ctx, const rt_opacity* op, const TransportKP& kp,
                            int ns, int prec, int schedule, int threads, int blocks_per_sm,
                            cudaStream_t s);
-rt_status launch_finalize(const double* accE, const double* accQ, size_t n, double xi,
-                          double* E_abs, double* esq, cudaStream_t s);
+rt_status launch_finalize(const double* acc, int acc_q, size_t n, double xi, double* E_abs,
+                          double* esq, cudaStream_t s);
 rt_status launch_temperatures(rt_ctx* ctx, const rt_grid* g, const rt_opacity* op,
                               const double* E, double* T, cudaStream_t s);
 rt_status launch_temperature_guess(rt_ctx* ctx, const rt_grid* g, const double* src_pos,

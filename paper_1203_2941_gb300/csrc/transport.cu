@@ -285,6 +285,9 @@ struct Lane {
     int nx, ny, nz;
     R chi;                     // extinction per cell length at frequency j
     R kex[NS], kab[NS];        // kext, kabs at frequency j (FP64: times cell)
+    typename PackedT<NS>::T pf;  // prefetched packed density of the next cell
+    int cn, nax;               // next cell's linear index, axis of the next face
+    bool outn;                 // the next face is the grid boundary
     int rs;                    // species of a pending re-emission (ST_REEMIT);
                                // its temperature and uniform ride in tau and tcur
 };
@@ -328,7 +331,26 @@ struct Kernel {
 
     __device__ __forceinline__ void load_cell(Lane<R, NS>& L)
     {
-        const PT v = __ldg(reinterpret_cast<const PT*>(L.grid) + L.c);
+        use_cell(L, __ldg(reinterpret_cast<const PT*>(L.grid) + L.c));
+    }
+
+    // Next cell of the traversal (nearest face, ties to the lowest axis); its
+    // density load is issued now and consumed one crossing later.
+    __device__ __forceinline__ void prefetch_next(Lane<R, NS>& L)
+    {
+        const int a = (L.tm[0] <= L.tm[1] && L.tm[0] <= L.tm[2]) ? 0 : (L.tm[1] <= L.tm[2] ? 1 : 2);
+        L.nax = a;
+        const int nix = L.ix + (a == 0 ? L.sx : 0);
+        const int niy = L.iy + (a == 1 ? L.sy : 0);
+        const int niz = L.iz + (a == 2 ? L.sz : 0);
+        L.outn = ((unsigned)nix >= (unsigned)L.nx) | ((unsigned)niy >= (unsigned)L.ny) |
+                 ((unsigned)niz >= (unsigned)L.nz);
+        L.cn = L.c + (a == 0 ? L.sx : (a == 1 ? L.sy * L.nx : L.sz * L.nx * L.ny));
+        if (!L.outn) L.pf = __ldg(reinterpret_cast<const PT*>(L.grid) + L.cn);
+    }
+
+    __device__ __forceinline__ void use_cell(Lane<R, NS>& L, const PT v)
+    {
         float r[4];
         unpack(v, r);
         L.lucy = signbit(r[0]);
@@ -474,8 +496,9 @@ struct Kernel {
                 }
             } else {
                 if (ta > 0.0f) {
-                    atomicAdd(&md->accE[s * nc + L.c], f2d(ta));
-                    if (md->accQ) atomicAdd(&md->accQ[s * nc + L.c], f2d(ta * ta));
+                    double* e = md->accE + ((s * nc + L.c) << md->acc_q);
+                    atomicAdd(e, f2d(ta));
+                    if (md->acc_q) atomicAdd(e + 1, f2d(ta * ta));
                 }
             }
         }
@@ -491,7 +514,7 @@ struct Kernel {
         if constexpr (DBG) {
             return have_old ? old + md->xi : __ldcg(&md->E_abs[i]);
         } else {
-            const double acc = have_old ? old + 1.0 : __ldcg(&md->accE[i]);
+            const double acc = have_old ? old + 1.0 : __ldcg(&md->accE[i << md->acc_q]);
             return __ldcg(&md->E_abs[i]) + acc * md->xi;
         }
     }
@@ -709,6 +732,7 @@ struct Kernel {
         L.sy = L.k[1] > R(0) ? 1 : -1;
         L.sz = L.k[2] > R(0) ? 1 : -1;
         L.tcur = R(0);
+        prefetch_next(L);
         L.st = ST_MARCH;
     }
 
@@ -743,8 +767,9 @@ struct Kernel {
                     if (md->esq) atomicAdd(&md->esq[s * nc + L.c], e * e);
                 }
             } else if (ta > 0.0f) {
-                atomicAdd(&md->accE[s * nc + L.c], f2d(ta));
-                if (md->accQ) atomicAdd(&md->accQ[s * nc + L.c], f2d(ta * ta));
+                double* e = md->accE + ((s * nc + L.c) << md->acc_q);
+                atomicAdd(e, f2d(ta));
+                if (md->acc_q) atomicAdd(e + 1, f2d(ta * ta));
             }
         }
         cnt.c[C_MRW]++;
@@ -760,43 +785,40 @@ struct Kernel {
         L.st = ST_FLIGHT;
     }
 
-    // One cell traversal step of a marching lane: the nearest of the three
-    // face distances decides the axis (ties to the lowest axis); the update is
-    // branch-free so lanes stepping along different axes stay converged.
+    // One cell traversal step of a marching lane.  The exit face and the
+    // next cell were found (and the next density requested) one step earlier;
+    // updates are branch-free so lanes stepping along different axes stay
+    // converged.
     __device__ __forceinline__ void march(Lane<R, NS>& L)
     {
-        const bool ax = (L.tm[0] <= L.tm[1]) && (L.tm[0] <= L.tm[2]);
-        const bool ay = !ax && (L.tm[1] <= L.tm[2]);
-        const bool az = !ax && !ay;
-        const R tn = ax ? L.tm[0] : (ay ? L.tm[1] : L.tm[2]);
+        const int a = L.nax;
+        const R tn = a == 0 ? L.tm[0] : (a == 1 ? L.tm[1] : L.tm[2]);
         const R seg = tn - L.tcur;
         const R dtau = L.chi * seg;
         if (dtau <= L.tau) {
             if (L.lucy) deposit_lucy(L, seg);
             L.tau -= dtau;
             L.tcur = tn;
-            L.tm[0] = ax ? L.tm[0] + L.td[0] : L.tm[0];
-            L.tm[1] = ay ? L.tm[1] + L.td[1] : L.tm[1];
-            L.tm[2] = az ? L.tm[2] + L.td[2] : L.tm[2];
-            const int nix = L.ix + (ax ? L.sx : 0);
-            const int niy = L.iy + (ay ? L.sy : 0);
-            const int niz = L.iz + (az ? L.sz : 0);
-            const bool out = ((unsigned)nix >= (unsigned)L.nx) | ((unsigned)niy >= (unsigned)L.ny) |
-                             ((unsigned)niz >= (unsigned)L.nz);
             cnt.cross++;
-            if (out) {
+            if (L.outn) {
                 L.st = ST_ESCAPE;          // ix, iy, iz, c keep the last cell inside
             } else {
-                L.c += ax ? L.sx : (ay ? L.sy * L.nx : L.sz * L.nx * L.ny);
-                L.ix = nix; L.iy = niy; L.iz = niz;
-                load_cell(L);
+                L.tm[0] = a == 0 ? L.tm[0] + L.td[0] : L.tm[0];
+                L.tm[1] = a == 1 ? L.tm[1] + L.td[1] : L.tm[1];
+                L.tm[2] = a == 2 ? L.tm[2] + L.td[2] : L.tm[2];
+                L.ix += a == 0 ? L.sx : 0;
+                L.iy += a == 1 ? L.sy : 0;
+                L.iz += a == 2 ? L.sz : 0;
+                L.c = L.cn;
+                use_cell(L, L.pf);
+                prefetch_next(L);
             }
         } else {
             const R d = L.tau / L.chi;
             if (L.lucy) deposit_lucy(L, d);
             L.tcur += d;
 #pragma unroll
-            for (int a = 0; a < 3; ++a) L.x[a] += L.tcur * L.k[a];
+            for (int a2 = 0; a2 < 3; ++a2) L.x[a2] += L.tcur * L.k[a2];
             L.st = ST_INTERACT;
         }
     }
@@ -858,8 +880,9 @@ struct Kernel {
                 old = atomicAdd(&md->E_abs[s * nc + L.c], md->xi);
                 if (md->esq) atomicAdd(&md->esq[s * nc + L.c], md->xi * md->xi);
             } else {
-                old = atomicAdd(&md->accE[s * nc + L.c], 1.0);
-                if (md->accQ) atomicAdd(&md->accQ[s * nc + L.c], 1.0);
+                double* e = md->accE + ((s * nc + L.c) << md->acc_q);
+                old = atomicAdd(e, 1.0);
+                if (md->acc_q) atomicAdd(e + 1, 1.0);
             }
             if (P.mode == RT_MODE_BW) E = energy(L, s, old, true);
         } else if (P.mode == RT_MODE_BW) {
@@ -983,6 +1006,7 @@ __global__ void __launch_bounds__(256, 3) transport_kernel(const __grid_constant
             if (L.st == ST_MARCH) {
                 K.md = &P.models[L.m];
                 K.march(L);
+                if (L.st == ST_MARCH) K.march(L);
             }
             nm = __popc(__ballot_sync(FULL, L.st == ST_MARCH));
         } while (nm > min_active);
@@ -1041,16 +1065,17 @@ __global__ void pack_kernel(const float* rho, size_t nc, const double* kext_max_
     else out[i] = make_float4(v[0], v[1], v[2], v[3]);
 }
 
-// E_abs += accE * xi and esq += accQ * xi^2 for one model (FP32 build)
-__global__ void finalize_kernel(const double* accE, const double* accQ, size_t n, double xi,
-                                double* E_abs, double* esq)
+// E_abs += acc * xi and esq += acc_sq * xi^2 for one model (FP32 build);
+// with acc_q = 1 the scratch interleaves the two sums per cell
+__global__ void finalize_kernel(const double* acc, int acc_q, size_t n, double xi, double* E_abs,
+                                double* esq)
 {
     const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const double a = accE[i];
+    const double a = acc[i << acc_q];
     if (a != 0.0) {
         E_abs[i] += a * xi;
-        if (esq && accQ) esq[i] += accQ[i] * xi * xi;
+        if (acc_q && esq) esq[i] += acc[2 * i + 1] * xi * xi;
     }
 }
 
@@ -1124,11 +1149,11 @@ rt_status pack_grid(rt_grid* g, const rt_opacity* op, int lucy_mode, double lucy
     return RT_OK;
 }
 
-rt_status launch_finalize(const double* accE, const double* accQ, size_t n, double xi,
-                          double* E_abs, double* esq, cudaStream_t s)
+rt_status launch_finalize(const double* acc, int acc_q, size_t n, double xi, double* E_abs,
+                          double* esq, cudaStream_t s)
 {
     if (n == 0) return RT_OK;
-    finalize_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(accE, accQ, n, xi, E_abs, esq);
+    finalize_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(acc, acc_q, n, xi, E_abs, esq);
     count_launches();
     RT_CUDA(cudaGetLastError());
     return RT_OK;
