@@ -231,6 +231,31 @@ RT_API rt_status rt_transport(rt_ctx* ctx, const rt_grid* grid, const rt_opacity
                        const rt_transport_params* p, const double* T_prev,
                        const rt_transport_out* out, rt_stream stream);
 
+/* Allocation-free variant of rt_transport (no counterpart in the paper; it
+ * exists for callers that must not allocate device memory).  Same arguments,
+ * semantics, outputs and errors as rt_transport, but the call itself never
+ * allocates or frees device memory: its scratch (work counter, model and
+ * source tables, a packed copy of the density grid, the FP64 energy scratch of
+ * the FP32 build) lives in one 64 MiB statically allocated device array that
+ * every GPU which loads the library holds until the process exits.  Callers
+ * that need this: code running where a device allocation is not allowed or
+ * not affordable -- e.g. a host whose device memory is entirely owned by
+ * another allocator or pool with a fixed budget, or a loop that must not hit
+ * the implicit device synchronisation that cudaMalloc/cudaFree may cause.
+ * Limit: 1 MiB of staging plus ncell*4*vec bytes of packed density
+ * (vec = 1, 2 or 4 floats for 1, 2 or 3-4 species) plus, in FP32,
+ * n_species*ncell*8 bytes (16 with esq) must fit in 64 MiB - 64 KiB; larger
+ * grids return RT_ERR_CAPACITY without launching anything.  The first call on
+ * a device looks up the array's device address (cudaGetSymbolAddress with
+ * that device current) and should come before any stream capture.  All calls
+ * share the one array: calls whose GPU work overlaps (different streams
+ * without ordering, or several host threads) race and must not be issued;
+ * calls ordered on one stream are safe (each clears what must start at zero). */
+RT_API rt_status rt_transport_noalloc(rt_ctx* ctx, const rt_grid* grid, const rt_opacity* opac,
+                                      const rt_source* sources, int n_sources,
+                                      const rt_transport_params* p, const double* T_prev,
+                                      const rt_transport_out* out, rt_stream stream);
+
 /* Dust temperatures from Eq. 4: for every species s and cell i, the T with
  * 4 pi sum_j kabs_s,j B_nu_j(T) dnu_j = E_abs[s][i] / (rho_s,i V); 0 where E or
  * rho is 0.  FP64 (table start, Newton polish to ~1e-13 relative).

@@ -5,6 +5,7 @@
 
 #include <atomic>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -669,6 +670,144 @@ rt_status rt_raytrace_backward(rt_ctx* ctx, const rt_grid* grid, const rt_opacit
     return raytrace_impl(ctx, grid, op, T, ev, nev, xi_ev, src, nsrc, cams, ncam, fidx, nfi, nullptr,
                          nullptr, dimg, dsed, drho, dscale, (unsigned long long*)ray_steps, true,
                          (cudaStream_t)stream);
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free transport.  All scratch of one rt_transport call (the work
+// counter, the model table with its source CDFs, the packed density copy, the
+// per-call FP64 energy scratch and the kext work array) lives in one
+// file-scope device array, so the call itself never allocates device memory.
+namespace rtgb {
+
+constexpr size_t kNoAllocBytes = 64ull << 20;     // 64 MiB held by every GPU that loads the library
+constexpr size_t kNoAllocStaging = 1ull << 20;    // model table, source tables, work counter
+constexpr size_t kNoAllocKext = 64ull << 10;      // ns * nf doubles (4 * 1024 * 8 = 32 KiB)
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+static std::mutex g_noalloc_mutex;
+static void* g_noalloc_addr[256];
+
+// Device address of the scratch array on `device` (which must be current).
+// Host code cannot use the symbol's own address: on the host it names a
+// stand-in object, not device memory.
+static rt_status noalloc_scratch(int device, unsigned char** out)
+{
+    if (device < 0 || device >= 256) return fail(RT_ERR_INVALID_ARG, "rt_transport_noalloc: device id out of range");
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[device]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
+        g_noalloc_addr[device] = p;
+    }
+    *out = (unsigned char*)g_noalloc_addr[device];
+    return RT_OK;
+}
+
+// stage_models into a given device buffer (host image + one H2D copy)
+static rt_status stage_models_into(std::vector<HostModel>& hms, uint64_t nwork, int nf,
+                                   unsigned char* base, size_t cap, cudaStream_t s, DeviceModels& dm)
+{
+    HostModel& hm = hms[0];
+    const int nsrc = hm.md.nsrc;
+    size_t off = 0;
+    const size_t o_models = off; off = align_up(off + sizeof(ModelDev), 64);
+    const size_t o_prefix = off; off = align_up(off + sizeof(unsigned long long) * 2, 64);
+    const size_t o_work = off; off = align_up(off + sizeof(unsigned long long) * 2, 64);
+    const size_t o_pos = off; off = align_up(off + sizeof(double) * 3 * nsrc, 64);
+    const size_t o_L = off; off = align_up(off + sizeof(double) * nsrc, 64);
+    const size_t o_c64 = off; off = align_up(off + sizeof(double) * nsrc * nf, 64);
+    const size_t o_c32 = off; off = align_up(off + sizeof(float) * nsrc * nf, 64);
+    if (off > cap) return fail(RT_ERR_CAPACITY, "rt_transport_noalloc: source tables exceed the staging area");
+    std::vector<unsigned char> h(off, 0);
+    ModelDev md = hm.md;
+    std::memcpy(&h[o_pos], hm.pos.data(), sizeof(double) * hm.pos.size());
+    std::memcpy(&h[o_L], hm.Lcdf.data(), sizeof(double) * hm.Lcdf.size());
+    std::memcpy(&h[o_c64], hm.cdf64.data(), sizeof(double) * hm.cdf64.size());
+    std::memcpy(&h[o_c32], hm.cdf32.data(), sizeof(float) * hm.cdf32.size());
+    md.src_pos = (const double*)(base + o_pos);
+    md.src_Lcdf = (const double*)(base + o_L);
+    md.src_cdf64 = (const double*)(base + o_c64);
+    md.src_cdf32 = (const float*)(base + o_c32);
+    std::memcpy(&h[o_models], &md, sizeof(ModelDev));
+    const unsigned long long prefix[2] = { 0ull, (unsigned long long)nwork };
+    std::memcpy(&h[o_prefix], prefix, sizeof(prefix));
+    RT_CUDA(cudaMemcpyAsync(base, h.data(), off, cudaMemcpyHostToDevice, s));
+    dm.buf = base;
+    dm.bytes = off;
+    dm.models = (ModelDev*)(base + o_models);
+    dm.prefix = (unsigned long long*)(base + o_prefix);
+    dm.work = (unsigned long long*)(base + o_work);
+    dm.total = nwork;
+    return RT_OK;
+}
+
+}  // namespace rtgb
+
+extern "C" {
+
+rt_status rt_transport_noalloc(rt_ctx* ctx, const rt_grid* grid, const rt_opacity* op,
+                               const rt_source* sources, int n_sources,
+                               const rt_transport_params* p, const double* T_prev,
+                               const rt_transport_out* out, rt_stream stream)
+{
+    if (!ctx || ctx->magic != kMagic) return fail(RT_ERR_STATE, "rt_transport_noalloc: bad context");
+    if (!grid || !op) return fail(RT_ERR_INVALID_ARG, "rt_transport_noalloc: NULL grid or opacity");
+    if (grid->ctx != ctx || op->ctx != ctx) return fail(RT_ERR_STATE, "rt_transport_noalloc: handle from another context");
+    if (grid->ns != op->ns) return fail(RT_ERR_INVALID_ARG, "rt_transport_noalloc: grid and opacity species differ");
+    rt_status st = check_params(p);
+    if (st != RT_OK) return st;
+    st = check_out(out);
+    if (st != RT_OK) return st;
+    if (p->pid_end < p->pid_begin || p->pid_end > p->n_packets)
+        return fail(RT_ERR_INVALID_ARG, "rt_transport_noalloc: need pid_begin <= pid_end <= n_packets");
+    if (p->mode == RT_MODE_FROZEN_T && !T_prev)
+        return fail(RT_ERR_INVALID_ARG, "rt_transport_noalloc: frozen-T mode needs T_prev");
+    // scratch layout: staging | kext | packed density | FP64 energy scratch
+    const size_t nc = grid->ncell();
+    const int vec = grid->ns == 1 ? 1 : (grid->ns == 2 ? 2 : 4);
+    const size_t packed_bytes = align_up(nc * sizeof(float) * vec, 256);
+    const size_t n_acc = (size_t)op->ns * nc;
+    const size_t acc_bytes = p->precision == RT_PREC_FP32 ? sizeof(double) * n_acc * (out->esq ? 2 : 1) : 0;
+    const size_t need = kNoAllocStaging + kNoAllocKext + packed_bytes + acc_bytes;
+    if (need > kNoAllocBytes)
+        return fail(RT_ERR_CAPACITY, "rt_transport_noalloc: grid too large for the 64 MiB static scratch (" +
+                                         std::to_string(need >> 20) + " MiB needed)");
+    RT_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned char* base = nullptr;
+    st = noalloc_scratch(ctx->device, &base);
+    if (st != RT_OK) return st;
+    std::vector<HostModel> hms(1);
+    st = make_model(grid, op, sources, n_sources, p->n_packets, p->pid_begin, p->model_id, 0,
+                    T_prev, out, hms[0]);
+    if (st != RT_OK) return st;
+    if (p->pid_end == p->pid_begin) return RT_OK;
+    double* kext = (double*)(base + kNoAllocStaging);
+    unsigned char* packed = base + kNoAllocStaging + kNoAllocKext;
+    double* acc = acc_bytes ? (double*)(packed + packed_bytes) : nullptr;
+    st = pack_grid_into(grid, op, p->lucy_mode, p->lucy_tau, p->precision, kext, packed, s);
+    if (st != RT_OK) return st;
+    hms[0].md.rho = packed;
+    if (acc) {
+        RT_CUDA(cudaMemsetAsync(acc, 0, acc_bytes, s));     // the array keeps the last call's sums
+        hms[0].md.accE = acc;
+        hms[0].md.acc_q = out->esq ? 1 : 0;
+    }
+    DeviceModels dm;
+    st = stage_models_into(hms, p->pid_end - p->pid_begin, op->nf, base, kNoAllocStaging, s, dm);
+    if (st != RT_OK) return st;
+    RT_CUDA(cudaMemsetAsync(dm.work, 0, sizeof(unsigned long long), s));
+    TransportKP kp;
+    fill_kp(kp, op, p, dm, 1);
+    const int threads = p->threads_per_block ? p->threads_per_block : 256;
+    st = launch_transport(ctx, op, kp, op->ns, p->precision, p->schedule, threads, p->blocks_per_sm, s);
+    if (st == RT_OK && acc)
+        st = launch_finalize(acc, hms[0].md.acc_q, n_acc, hms[0].md.xi, out->E_abs, out->esq, s);
+    return st;
 }
 
 rt_status rt_philox(rt_ctx* ctx, const uint32_t ctr0[4], const uint32_t key[2], uint64_t n,

@@ -160,6 +160,8 @@ namespace rtgb {
 rt_status build_opacity_tables(rt_opacity* op);
 rt_status pack_grid(rt_grid* g, const rt_opacity* op, int lucy_mode, double lucy_tau, int prec,
                     cudaStream_t s);
+rt_status pack_grid_into(const rt_grid* g, const rt_opacity* op, int lucy_mode, double lucy_tau,
+                         int prec, double* kext, void* dst, cudaStream_t s);
 rt_status launch_transport(rt_ctx* ctx, const rt_opacity* op, const TransportKP& kp,
                            int ns, int prec, int schedule, int threads, int blocks_per_sm,
                            cudaStream_t s);

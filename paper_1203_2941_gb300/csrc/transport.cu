@@ -1159,6 +1159,34 @@ rt_status launch_finalize(const double* acc, int acc_q, size_t n, double xi, dou
     return RT_OK;
 }
 
+// Pack the grid into `dst` (ncell cells of 1, 2 or 4 floats) with the Lucy
+// flags of (lucy_mode, lucy_tau); `kext` receives ns * nf doubles of work
+// space.  Allocates nothing.
+rt_status pack_grid_into(const rt_grid* g, const rt_opacity* op, int lucy_mode, double lucy_tau,
+                         int prec, double* kext, void* dst, cudaStream_t s)
+{
+    const int vec = g->ns == 1 ? 1 : (g->ns == 2 ? 2 : 4);
+    const size_t nc = g->ncell();
+    const int n = op->ns * op->nf;
+    kext_kernel<<<(n + 255) / 256, 256, 0, s>>>(op->d_kabs, op->d_ksca, kext, n);
+    const unsigned blocks = (unsigned)((nc + 255) / 256);
+    if (vec == 1)
+        pack_kernel<float, 1><<<blocks, 256, 0, s>>>(g->d_rho, nc, nullptr, (float*)dst, prec,
+                                                      g->cell, lucy_mode, lucy_tau, kext, op->nf);
+    else if (vec == 2)
+        pack_kernel<float2, 2><<<blocks, 256, 0, s>>>(g->d_rho, nc, nullptr, (float2*)dst, prec,
+                                                       g->cell, lucy_mode, lucy_tau, kext, op->nf);
+    else if (g->ns == 3)
+        pack_kernel<float4, 3><<<blocks, 256, 0, s>>>(g->d_rho, nc, nullptr, (float4*)dst, prec,
+                                                       g->cell, lucy_mode, lucy_tau, kext, op->nf);
+    else
+        pack_kernel<float4, 4><<<blocks, 256, 0, s>>>(g->d_rho, nc, nullptr, (float4*)dst, prec,
+                                                       g->cell, lucy_mode, lucy_tau, kext, op->nf);
+    count_launches(2);
+    RT_CUDA(cudaGetLastError());
+    return RT_OK;
+}
+
 rt_status launch_transport(rt_ctx* ctx, const rt_opacity* op, const TransportKP& kp, int ns,
                            int prec, int schedule, int threads, int blocks_per_sm, cudaStream_t s)
 {

@@ -32,7 +32,7 @@ EXPORTS = ["rt_last_error", "rt_version", "rt_ctx_create", "rt_ctx_destroy", "rt
            "rt_grid_free", "rt_opacity_upload", "rt_opacity_free", "rt_transport_params_default",
            "rt_transport", "rt_temperatures", "rt_temperature_guess", "rt_raytrace",
            "rt_raytrace_backward", "rt_batch_create", "rt_batch_run", "rt_batch_free",
-           "rt_transport_batched", "rt_philox", "rt_kernel_launches"]
+           "rt_transport_batched", "rt_philox", "rt_kernel_launches", "rt_transport_noalloc"]
 
 
 class RtError(RuntimeError):
@@ -107,6 +107,8 @@ def load(path: str = LIB_PATH):
         "rt_transport_params_default": (None, [C.POINTER(rt_transport_params)]),
         "rt_transport": (i32, [vp, vp, vp, vp, i32, C.POINTER(rt_transport_params), vp,
                                C.POINTER(rt_transport_out), vp]),
+        "rt_transport_noalloc": (i32, [vp, vp, vp, vp, i32, C.POINTER(rt_transport_params), vp,
+                                       C.POINTER(rt_transport_out), vp]),
         "rt_temperatures": (i32, [vp, vp, vp, vp, vp, vp]),
         "rt_temperature_guess": (i32, [vp, vp, vp, i32, vp, vp]),
         "rt_raytrace": (i32, [vp, vp, vp, vp, vp, u64, dbl, vp, i32, vp, i32, vp, i32, vp, vp, vp,
@@ -190,6 +192,11 @@ def rt_transport_params_default() -> rt_transport_params:
 def rt_transport(ctx, grid, opac, sources, n_sources, params, T_prev_ptr, out, stream=0):
     _check(load().rt_transport(ctx, grid, opac, sources, n_sources, C.byref(params), T_prev_ptr,
                                C.byref(out), stream), "rt_transport")
+
+
+def rt_transport_noalloc(ctx, grid, opac, sources, n_sources, params, T_prev_ptr, out, stream=0):
+    _check(load().rt_transport_noalloc(ctx, grid, opac, sources, n_sources, C.byref(params),
+                                       T_prev_ptr, C.byref(out), stream), "rt_transport_noalloc")
 
 
 def rt_temperatures(ctx, grid, opac, E_ptr, T_ptr, stream=0):
