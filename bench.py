@@ -235,6 +235,10 @@ def main():
     if dist:
         dist.barrier()
     launches = R.rt_kernel_launches() - launches0
+    if dist:
+        # replicas of the B&W solve: average the accumulated outputs (untimed)
+        from paper_1203_2941_gb300.shard import allreduce_mean
+        allreduce_mean([out.E_abs, out.sed_esc])
     t_step = [e[0].elapsed_time(e[3]) for e in evs]
     t_tr = [e[0].elapsed_time(e[1]) for e in evs]
     t_T = [e[1].elapsed_time(e[2]) for e in evs]
