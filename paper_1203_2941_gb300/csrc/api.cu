@@ -404,6 +404,9 @@ static void fill_kp(TransportKP& kp, const rt_opacity* op, const rt_transport_pa
     for (int s = 0; s < op->ns; ++s)
         if (op->is_pah[s]) kp.pah_mask |= 1 << s;
     kp.march_min_active = p->march_min_active < 0 ? 8 : p->march_min_active;
+    kp.want_traj = 0;
+    kp.smem_sed = 0;
+    kp.smem_cdf = 0;
     kp.max_events = p->max_events;
     kp.seed = p->seed;
     kp.mrw_tau_cell = p->mrw_tau_cell;
@@ -419,6 +422,19 @@ static void fill_kp(TransportKP& kp, const rt_opacity* op, const rt_transport_pa
     kp.mrwS = op->d_mrwS;
     kp.nu = op->d_nu; kp.dnu = op->d_dnu;
     kp.kabs = op->d_kabs; kp.ksca = op->d_ksca; kp.g = op->d_g;
+}
+
+// Shared-memory options of a single-model launch: per-block escape SED (the
+// 10 x nf tallies otherwise take heavily contended global atomics) and the
+// source CDFs; trajectory logging selects the kernel variant that has it.
+static void single_model_options(TransportKP& kp, const rt_opacity* op,
+                                 const rt_transport_params* p, const rt_transport_out* out,
+                                 int n_sources)
+{
+    kp.want_traj = out->traj != nullptr && out->traj_cap > 0;
+    const bool persistent = p->schedule == RT_SCHED_PERSISTENT && p->precision == RT_PREC_FP32;
+    kp.smem_sed = persistent && op->nf <= 256 ? 1 : 0;
+    kp.smem_cdf = persistent && n_sources * op->nf <= 4096 ? n_sources * op->nf : 0;
 }
 
 }  // namespace rtgb
@@ -480,6 +496,7 @@ rt_status rt_transport(rt_ctx* ctx, const rt_grid* grid, const rt_opacity* op,
     RT_CUDA(cudaMemsetAsync(dm.work, 0, sizeof(unsigned long long), s));
     TransportKP kp;
     fill_kp(kp, op, p, dm, 1);
+    single_model_options(kp, op, p, out, n_sources);
     const int threads = p->threads_per_block ? p->threads_per_block : 256;
     st = launch_transport(ctx, op, kp, op->ns, p->precision, p->schedule, threads, p->blocks_per_sm, s);
     if (st == RT_OK && acc)
@@ -546,6 +563,8 @@ rt_status rt_batch_create(rt_ctx* ctx, const rt_opacity* op, int n_models, const
     st = stage_models(hms, nwork, op->nf, false, 0, b->dm);
     if (st != RT_OK) { cudaFree(b->acc); delete b; return st; }
     fill_kp(b->kp, op, p, b->dm, n_models);
+    for (int m = 0; m < n_models; ++m)
+        if (models[m].out.traj && models[m].out.traj_cap) b->kp.want_traj = 1;
     *out = b;
     return RT_OK;
 }
@@ -803,6 +822,7 @@ rt_status rt_transport_noalloc(rt_ctx* ctx, const rt_grid* grid, const rt_opacit
     RT_CUDA(cudaMemsetAsync(dm.work, 0, sizeof(unsigned long long), s));
     TransportKP kp;
     fill_kp(kp, op, p, dm, 1);
+    single_model_options(kp, op, p, out, n_sources);
     const int threads = p->threads_per_block ? p->threads_per_block : 256;
     st = launch_transport(ctx, op, kp, op->ns, p->precision, p->schedule, threads, p->blocks_per_sm, s);
     if (st == RT_OK && acc)

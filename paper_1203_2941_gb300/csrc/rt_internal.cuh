@@ -120,6 +120,9 @@ struct TransportKP {
     int mode, lucy_form, mrw, record_events;
     int pah_mask;
     int march_min_active;
+    int want_traj;                      // some model logs trajectories
+    int smem_sed;                       // single-model persistent launch: SED tallied per block
+    int smem_cdf;                       // floats of model 0's source CDFs kept in shared memory
     unsigned long long max_events;
     uint64_t seed;
     double mrw_tau_cell, mrw_gamma;

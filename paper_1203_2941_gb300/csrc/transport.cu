@@ -307,22 +307,30 @@ struct Counters {
     uint32_t c[C_N];
 };
 
-template <typename R, int NS>
+// FEAT bits: 1 = modified random walk compiled in, 2 = trajectory logging
+// compiled in (production launches leave unused paths out of the hot code)
+template <typename R, int NS, int FEAT>
 struct Kernel {
     using PT = typename PackedT<NS>::T;
     static constexpr bool DBG = sizeof(R) == 8;
+    static constexpr bool HAS_MRW = (FEAT & 1) != 0;
+    static constexpr bool HAS_TRAJ = (FEAT & 2) != 0;
 
     const TransportKP& P;
     const float4* s_op;        // [NS][nf] in shared memory (FP32 path)
     const float* s_xh;
     const float* s_w;
     const float* s_mrw;
+    const float* s_cdf;        // source CDFs of a single-model launch (or null)
+    double* s_sed;             // per-block escape SED of a single-model launch (or null)
+    unsigned* s_cnt;
     const ModelDev* md;        // model of the lane's current packet
     Counters cnt;
 
     __device__ Kernel(const TransportKP& p, const float4* op, const float* xh, const float* w,
-                      const float* mrw)
-        : P(p), s_op(op), s_xh(xh), s_w(w), s_mrw(mrw), md(nullptr)
+                      const float* mrw, const float* cdf, double* sed, unsigned* cnt_)
+        : P(p), s_op(op), s_xh(xh), s_w(w), s_mrw(mrw), s_cdf(cdf), s_sed(sed), s_cnt(cnt_),
+          md(nullptr)
     {
         cnt.cross = 0;
 #pragma unroll
@@ -387,6 +395,7 @@ struct Kernel {
 
     __device__ __forceinline__ void traj(Lane<R, NS>& L, uint32_t type, const R* x)
     {
+        if constexpr (!HAS_TRAJ) return;
         const uint32_t q = L.seq++;
         if (md->traj == nullptr) return;
         const unsigned long long slot = atomicAdd(&md->stats[RT_STAT_N_TRAJ], 1ull);
@@ -445,7 +454,7 @@ struct Kernel {
             const double* cdf = md->src_cdf64 + (size_t)si * P.nf;
             L.j = search_cdf(cdf, P.nf, ub * cdf[P.nf - 1]);
         } else {
-            L.j = search_cdf(md->src_cdf32 + (size_t)si * P.nf, P.nf, ub);
+            L.j = search_cdf((s_cdf ? s_cdf : md->src_cdf32) + (size_t)si * P.nf, P.nf, ub);
         }
         const R u1 = rng_u<R>(L.rng), u2 = rng_u<R>(L.rng);
         iso_dir(u1, u2, L.k);
@@ -698,7 +707,7 @@ struct Kernel {
     // A new flight from L.x along L.k: MRW step or tau draw + traversal set-up
     __device__ __forceinline__ void flight(Lane<R, NS>& L)
     {
-        if (P.mrw && P.mode != RT_MODE_NOREEMIT && L.chi > (R)P.mrw_tau_cell) {
+        if (HAS_MRW && P.mrw && P.mode != RT_MODE_NOREEMIT && L.chi > (R)P.mrw_tau_cell) {
             R R0 = R(1e30);
             const int id[3] = { L.ix, L.iy, L.iz };
 #pragma unroll
@@ -719,10 +728,10 @@ struct Kernel {
             const R ka = L.k[a];
             if (ka > R(0)) {
                 L.td[a] = R(1) / ka;
-                L.tm[a] = fmax(((R)(id[a] + 1) - L.x[a]) / ka, R(0));
+                L.tm[a] = fmax(((R)(id[a] + 1) - L.x[a]) * L.td[a], R(0));
             } else if (ka < R(0)) {
                 L.td[a] = R(-1) / ka;
-                L.tm[a] = fmax(((R)id[a] - L.x[a]) / ka, R(0));
+                L.tm[a] = fmax((L.x[a] - (R)id[a]) * L.td[a], R(0));
             } else {
                 L.td[a] = R(INFINITY);
                 L.tm[a] = R(INFINITY);
@@ -910,8 +919,13 @@ struct Kernel {
     {
         int b = (int)floor((L.k[2] + R(1)) * R(5));
         b = min(max(b, 0), kSedBins - 1);
-        atomicAdd(&md->sed_esc[b * P.nf + L.j], md->xi);
-        atomicAdd(&md->sed_cnt[b * P.nf + L.j], 1ull);
+        if (s_sed) {
+            atomicAdd(&s_sed[b * P.nf + L.j], md->xi);
+            atomicAdd(&s_cnt[b * P.nf + L.j], 1u);
+        } else {
+            atomicAdd(&md->sed_esc[b * P.nf + L.j], md->xi);
+            atomicAdd(&md->sed_cnt[b * P.nf + L.j], 1ull);
+        }
         cnt.c[C_ESC]++;
         if (md->traj) {
             R xe[3];
@@ -939,27 +953,37 @@ struct Kernel {
     }
 };
 
-template <typename R, int NS>
+// Shared memory: [escape SED doubles][escape counts][opacity float4]
+// [h nu / k][re-emission weights][MRW survival][source CDFs]; the SED and CDF
+// parts exist only for single-model, persistent launches (smem_sed, smem_cdf).
+template <typename R, int NS, int FEAT>
 __global__ void __launch_bounds__(256, 3) transport_kernel(const __grid_constant__ TransportKP P,
                                                            int serial)
 {
     extern __shared__ float4 smem[];
-    float4* s_op = smem;
+    const int nsed = P.smem_sed ? kSedBins * P.nf : 0;
+    double* s_sed = reinterpret_cast<double*>(smem);
+    unsigned* s_cnt = reinterpret_cast<unsigned*>(s_sed + nsed);
+    float4* s_op = smem + (nsed * 12 + 15) / 16;
     float* s_xh = reinterpret_cast<float*>(s_op + NS * P.nf);
     float* s_w = s_xh + P.nf;
     float* s_mrw = s_w + NS * P.nf;
+    float* s_cdf = s_mrw + ((FEAT & 1) && P.mrw ? kMrwN : 0);
     if (sizeof(R) == 4) {
         for (int i = threadIdx.x; i < NS * P.nf; i += blockDim.x) {
             s_op[i] = P.opac32[i];
             s_w[i] = P.wre[i];
         }
         for (int i = threadIdx.x; i < P.nf; i += blockDim.x) s_xh[i] = P.xh[i];
-        if (P.mrw)
+        if ((FEAT & 1) && P.mrw)
             for (int i = threadIdx.x; i < kMrwN; i += blockDim.x) s_mrw[i] = P.mrwS[i];
+        for (int i = threadIdx.x; i < P.smem_cdf; i += blockDim.x) s_cdf[i] = P.models[0].src_cdf32[i];
+        for (int i = threadIdx.x; i < nsed; i += blockDim.x) { s_sed[i] = 0.0; s_cnt[i] = 0u; }
     }
     __syncthreads();
 
-    Kernel<R, NS> K(P, s_op, s_xh, s_w, s_mrw);
+    Kernel<R, NS, FEAT> K(P, s_op, s_xh, s_w, s_mrw, (sizeof(R) == 4 && P.smem_cdf) ? s_cdf : nullptr,
+                          (sizeof(R) == 4 && nsed && !serial) ? s_sed : nullptr, s_cnt);
     Lane<R, NS> L;
     L.st = ST_NEED;
     L.m = -1;
@@ -1027,6 +1051,15 @@ __global__ void __launch_bounds__(256, 3) transport_kernel(const __grid_constant
         }
     }
     if (L.m >= 0) K.flush(L.m);
+    if (K.s_sed) {
+        __syncthreads();
+        const ModelDev& m0 = P.models[0];
+        for (int i = threadIdx.x; i < nsed; i += blockDim.x)
+            if (s_cnt[i]) {
+                atomicAdd(&m0.sed_esc[i], s_sed[i]);
+                atomicAdd(&m0.sed_cnt[i], (unsigned long long)s_cnt[i]);
+            }
+    }
 }
 
 // ------------------------------------------------------------- grid packing
@@ -1085,13 +1118,16 @@ __global__ void kext_kernel(const double* kabs, const double* ksca, double* kext
     if (i < n) kext[i] = kabs[i] + ksca[i];
 }
 
-template <typename R, int NS>
+template <typename R, int NS, int FEAT>
 rt_status launch_one(rt_ctx* ctx, const TransportKP& kp, int schedule, int threads,
                      int blocks_per_sm, cudaStream_t s)
 {
-    const size_t smem = sizeof(float4) * NS * kp.nf + sizeof(float) * kp.nf +
-                        sizeof(float) * NS * kp.nf + (kp.mrw ? sizeof(float) * kMrwN : 0);
-    auto fn = transport_kernel<R, NS>;
+    const size_t nsed = kp.smem_sed ? (size_t)kSedBins * kp.nf : 0;
+    const size_t smem = (nsed * 12 + 15) / 16 * 16 + sizeof(float4) * NS * kp.nf +
+                        sizeof(float) * kp.nf + sizeof(float) * NS * kp.nf +
+                        ((FEAT & 1) && kp.mrw ? sizeof(float) * kMrwN : 0) +
+                        sizeof(float) * kp.smem_cdf;
+    auto fn = transport_kernel<R, NS, FEAT>;
     RT_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     if (schedule == RT_SCHED_SERIAL) {
         fn<<<1, 32, smem, s>>>(kp, 1);
@@ -1107,6 +1143,24 @@ rt_status launch_one(rt_ctx* ctx, const TransportKP& kp, int schedule, int threa
     }
     RT_CUDA(cudaGetLastError());
     return RT_OK;
+}
+
+// FP32: instantiate only the feature set a launch needs; FP64 debug: all
+template <typename R, int NS>
+rt_status launch_feat(rt_ctx* ctx, const TransportKP& kp, int schedule, int threads,
+                      int blocks_per_sm, cudaStream_t s)
+{
+    if constexpr (sizeof(R) == 8) {
+        return launch_one<R, NS, 3>(ctx, kp, schedule, threads, blocks_per_sm, s);
+    } else {
+        const int feat = (kp.mrw ? 1 : 0) | (kp.want_traj ? 2 : 0);
+        switch (feat) {
+        case 0: return launch_one<R, NS, 0>(ctx, kp, schedule, threads, blocks_per_sm, s);
+        case 1: return launch_one<R, NS, 1>(ctx, kp, schedule, threads, blocks_per_sm, s);
+        case 2: return launch_one<R, NS, 2>(ctx, kp, schedule, threads, blocks_per_sm, s);
+        default: return launch_one<R, NS, 3>(ctx, kp, schedule, threads, blocks_per_sm, s);
+        }
+    }
 }
 
 }  // namespace
@@ -1192,13 +1246,13 @@ rt_status launch_transport(rt_ctx* ctx, const rt_opacity* op, const TransportKP&
 {
     const int vec = ns == 1 ? 1 : (ns == 2 ? 2 : 4);
     if (prec == RT_PREC_FP64) {
-        if (vec == 1) return launch_one<double, 1>(ctx, kp, schedule, threads, blocks_per_sm, s);
-        if (vec == 2) return launch_one<double, 2>(ctx, kp, schedule, threads, blocks_per_sm, s);
-        return launch_one<double, 4>(ctx, kp, schedule, threads, blocks_per_sm, s);
+        if (vec == 1) return launch_feat<double, 1>(ctx, kp, schedule, threads, blocks_per_sm, s);
+        if (vec == 2) return launch_feat<double, 2>(ctx, kp, schedule, threads, blocks_per_sm, s);
+        return launch_feat<double, 4>(ctx, kp, schedule, threads, blocks_per_sm, s);
     }
-    if (vec == 1) return launch_one<float, 1>(ctx, kp, schedule, threads, blocks_per_sm, s);
-    if (vec == 2) return launch_one<float, 2>(ctx, kp, schedule, threads, blocks_per_sm, s);
-    return launch_one<float, 4>(ctx, kp, schedule, threads, blocks_per_sm, s);
+    if (vec == 1) return launch_feat<float, 1>(ctx, kp, schedule, threads, blocks_per_sm, s);
+    if (vec == 2) return launch_feat<float, 2>(ctx, kp, schedule, threads, blocks_per_sm, s);
+    return launch_feat<float, 4>(ctx, kp, schedule, threads, blocks_per_sm, s);
 }
 
 }  // namespace rtgb
