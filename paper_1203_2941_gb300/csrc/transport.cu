@@ -1007,18 +1007,37 @@ __global__ void __launch_bounds__(256, 3) transport_kernel(const __grid_constant
     }
 
     const int min_active = P.march_min_active;
+    // Packet ids are claimed per warp in chunks (one global atomic per chunk);
+    // the chunk shrinks from 256 to 32 ids as the work runs out, which keeps
+    // the tail balanced.  [w_next, w_end) is the warp's unclaimed range.
+    unsigned long long w_next = 0, w_end = 0;
+    bool exhausted = false;
+    const unsigned long long n_warps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
     for (;;) {
         const unsigned need = __ballot_sync(FULL, L.st == ST_NEED);
         if (need) {
-            const int leader = __ffs(need) - 1;
-            unsigned long long base = 0;
-            if (lane == leader) base = atomicAdd(P.work_ctr, (unsigned long long)__popc(need));
-            base = __shfl_sync(FULL, base, leader);
-            if (L.st == ST_NEED) {
-                const unsigned long long w = base + __popc(need & ((1u << lane) - 1u));
-                if (w >= P.total_work) L.st = ST_DONE;
-                else K.emit(L, w);
+            if (w_next == w_end && !exhausted) {
+                unsigned long long base = 0;
+                const unsigned long long left = P.total_work > w_end ? P.total_work - w_end : 0;
+                unsigned long long chunk = left / (4ull * n_warps);
+                chunk = chunk < 32ull ? 32ull : (chunk > 256ull ? 256ull : chunk);
+                if (lane == 0) base = atomicAdd(P.work_ctr, chunk);
+                base = __shfl_sync(FULL, base, 0);
+                if (base >= P.total_work) {
+                    exhausted = true;
+                    w_next = w_end = P.total_work;
+                } else {
+                    w_next = base;
+                    w_end = base + chunk < P.total_work ? base + chunk : P.total_work;
+                }
             }
+            const unsigned avail = (unsigned)(w_end - w_next);
+            const unsigned rank = __popc(need & ((1u << lane) - 1u));
+            if (L.st == ST_NEED) {
+                if (rank < avail) K.emit(L, w_next + rank);
+                else if (exhausted) L.st = ST_DONE;
+            }
+            w_next += __popc(need) < avail ? __popc(need) : avail;
         }
         if (__all_sync(FULL, L.st == ST_DONE)) break;
         if (L.st == ST_FLIGHT) {
