@@ -883,21 +883,45 @@ struct Kernel {
         if (is_pah(s)) { store_pah(L, L.x); return; }
         const size_t nc = (size_t)L.nx * L.ny * L.nz;
         double E = 0.0;
-        if (!L.lucy) {
-            double old;
-            if constexpr (DBG) {
-                old = atomicAdd(&md->E_abs[s * nc + L.c], md->xi);
+        if constexpr (DBG) {
+            if (!L.lucy) {
+                const double old = atomicAdd(&md->E_abs[s * nc + L.c], md->xi);
                 if (md->esq) atomicAdd(&md->esq[s * nc + L.c], md->xi * md->xi);
-            } else {
-                double* e = md->accE + ((s * nc + L.c) << md->acc_q);
-                old = atomicAdd(e, 1.0);
-                if (md->acc_q) atomicAdd(e + 1, 1.0);
+                if (P.mode == RT_MODE_BW) E = energy(L, s, old, true);
+            } else if (P.mode == RT_MODE_BW) {
+                E = energy(L, s, 0.0, false);
             }
-            if (P.mode == RT_MODE_BW) E = energy(L, s, old, true);
-        } else if (P.mode == RT_MODE_BW) {
-            E = energy(L, s, 0.0, false);
+            atomicAdd(&md->count[s * nc + L.c], 1u);
+        } else {
+            // Lanes absorbing in the same cell and species combine into one
+            // atomic: the group leader adds the group size, and lane r of the
+            // group sees the old value plus r (as if the lanes absorbed one
+            // after another in lane order).  Optically thick cells next to a
+            // source receive most absorptions; per-lane atomics on them
+            // serialise in L2.
+            const size_t idx = s * nc + L.c;
+            const unsigned grp = __match_any_sync(__activemask(), (unsigned long long)idx * 2u + (L.lucy ? 1u : 0u));
+            const int leader = __ffs(grp) - 1;
+            const unsigned rank = __popc(grp & ((1u << (threadIdx.x & 31)) - 1u));
+            const unsigned n = __popc(grp);
+            const bool lead = (int)(threadIdx.x & 31) == leader;
+            double old = 0.0;
+            if (!L.lucy) {
+                double* e = md->accE + (idx << md->acc_q);
+                if (lead) {
+                    if (P.mode == RT_MODE_BW) old = atomicAdd(e, (double)n);
+                    else atomicAdd(e, (double)n);
+                    if (md->acc_q) atomicAdd(e + 1, (double)n);
+                }
+                if (P.mode == RT_MODE_BW) {
+                    old = __shfl_sync(grp, old, leader) + (double)rank;
+                    E = energy(L, s, old, true);
+                }
+            } else if (P.mode == RT_MODE_BW) {
+                E = energy(L, s, 0.0, false);
+            }
+            if (lead) atomicAdd(&md->count[idx], n);
         }
-        atomicAdd(&md->count[s * nc + L.c], 1u);
         if (P.mode == RT_MODE_NOREEMIT) {
             traj(L, RT_TRAJ_ABSORB_END, L.x);
             L.st = ST_NEED;
