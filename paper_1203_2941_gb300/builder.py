@@ -16,7 +16,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-BUILD = os.path.join(HERE, "_build")
+BUILD = os.environ.get("RTGB_BUILD_DIR") or os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "librtgb.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
@@ -50,7 +50,7 @@ def build(force: bool = False, verbose: bool = False, extra=None) -> str:
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
-    extra = list(extra or [])
+    extra = list(extra or []) + os.environ.get("RTGB_NVCC_FLAGS", "").split()
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")

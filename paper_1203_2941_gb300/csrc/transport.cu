@@ -980,9 +980,12 @@ struct Kernel {
 // Shared memory: [escape SED doubles][escape counts][opacity float4]
 // [h nu / k][re-emission weights][MRW survival][source CDFs]; the SED and CDF
 // parts exist only for single-model, persistent launches (smem_sed, smem_cdf).
+#ifndef RT_TRANSPORT_MIN_BLOCKS
+#define RT_TRANSPORT_MIN_BLOCKS 3
+#endif
 template <typename R, int NS, int FEAT>
-__global__ void __launch_bounds__(256, 3) transport_kernel(const __grid_constant__ TransportKP P,
-                                                           int serial)
+__global__ void __launch_bounds__(256, RT_TRANSPORT_MIN_BLOCKS)
+    transport_kernel(const __grid_constant__ TransportKP P, int serial)
 {
     extern __shared__ float4 smem[];
     const int nsed = P.smem_sed ? kSedBins * P.nf : 0;

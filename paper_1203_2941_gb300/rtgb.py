@@ -16,7 +16,7 @@ from typing import Optional, Sequence
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_build", "librtgb.so")
+LIB_PATH = os.path.join(os.environ.get("RTGB_BUILD_DIR") or os.path.join(HERE, "_build"), "librtgb.so")
 
 RT_OK, RT_ERR_INVALID_ARG, RT_ERR_CUDA, RT_ERR_OOM, RT_ERR_CAPACITY, RT_ERR_STUCK, RT_ERR_STATE = range(7)
 RT_MODE_BW, RT_MODE_FROZEN_T, RT_MODE_NOREEMIT = 0, 1, 2
