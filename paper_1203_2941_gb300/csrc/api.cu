@@ -303,6 +303,7 @@ static rt_status make_model(const rt_grid* g, const rt_opacity* op, const rt_sou
     std::memset(&m, 0, sizeof(m));
     m.rho = g->d_packed;
     m.nx = g->nx; m.ny = g->ny; m.nz = g->nz;
+    m.ncell = (int)g->ncell();
     m.model_id = model_id;
     m.model_index = model_index;
     m.nsrc = nsrc;

@@ -88,6 +88,7 @@ namespace rtgb {
 struct ModelDev {
     const void* rho;           // packed cells (float, float2 or float4)
     int nx, ny, nz;
+    int ncell;                 // nx * ny * nz
     uint32_t model_id;
     int model_index;
     int nsrc;
@@ -123,6 +124,8 @@ struct TransportKP {
     int want_traj;                      // some model logs trajectories
     int smem_sed;                       // single-model persistent launch: SED tallied per block
     int smem_cdf;                       // floats of model 0's source CDFs kept in shared memory
+    // dynamic shared-memory layout (byte offsets, set by the launcher)
+    int so_sed, so_cnt, so_op, so_xh, so_w, so_mrw, so_cdf, so_ctr;
     unsigned long long max_events;
     uint64_t seed;
     double mrw_tau_cell, mrw_gamma;

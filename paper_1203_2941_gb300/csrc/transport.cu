@@ -38,8 +38,8 @@ namespace {
 constexpr unsigned FULL = 0xffffffffu;
 enum { ST_NEED = 0, ST_FLIGHT = 1, ST_MARCH = 2, ST_INTERACT = 3, ST_ESCAPE = 4, ST_DONE = 5,
        ST_REEMIT = 6, ST_REEMITTED = 7 };
-enum { C_INT, C_SCA, C_ABS, C_MRW, C_ESC, C_STUCK, C_PAH, C_LUCY, C_EMIT, C_N };
 constexpr double kPi = 3.14159265358979323846;
+constexpr int kLaneStats = RT_STAT_EMITTED + 1;   // stats counted per thread (the rest are cursors)
 
 template <int NS> struct PackedT;
 template <> struct PackedT<1> { using T = float; };
@@ -51,27 +51,29 @@ __device__ __forceinline__ void unpack(float2 v, float* r) { r[0] = v.x; r[1] = 
 __device__ __forceinline__ void unpack(float4 v, float* r) { r[0] = v.x; r[1] = v.y; r[2] = v.z; r[3] = v.w; }
 
 // ------------------------------------------------------------- random numbers
+// Per-packet Philox stream: key = (seed_lo, seed_hi ^ model_id), counter =
+// (draw/2, 0, pid_lo, pid_hi).  The key's first word is the launch seed and is
+// passed in, so a lane keeps five words (six in the FP64 build).
 struct Rng {
-    uint2 key;
-    uint32_t plo, phi, draw, c_lo, c_hi;
+    uint32_t ky, plo, phi, draw, c_lo, c_hi;
 };
 
 __device__ __forceinline__ void rng_init(Rng& r, uint64_t seed, uint32_t model_id, uint64_t pid)
 {
-    r.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32) ^ model_id);
+    r.ky = (uint32_t)(seed >> 32) ^ model_id;
     r.plo = (uint32_t)pid;
     r.phi = (uint32_t)(pid >> 32);
     r.draw = 0;
 }
 
-template <typename R> __device__ __forceinline__ R rng_u(Rng& r);
+template <typename R> __device__ __forceinline__ R rng_u(Rng& r, uint32_t kx);
 
-template <> __device__ __forceinline__ float rng_u<float>(Rng& r)
+template <> __device__ __forceinline__ float rng_u<float>(Rng& r, uint32_t kx)
 {
     const uint32_t d = r.draw++;
     uint32_t hi;
     if ((d & 1u) == 0) {
-        const uint4 b = philox4x32_10(make_uint4(d >> 1, 0u, r.plo, r.phi), r.key);
+        const uint4 b = philox4x32_10(make_uint4(d >> 1, 0u, r.plo, r.phi), make_uint2(kx, r.ky));
         hi = b.y;
         r.c_hi = b.w;
     } else {
@@ -80,12 +82,12 @@ template <> __device__ __forceinline__ float rng_u<float>(Rng& r)
     return (float)((hi >> 8) + 1u) * 0x1p-24f;
 }
 
-template <> __device__ __forceinline__ double rng_u<double>(Rng& r)
+template <> __device__ __forceinline__ double rng_u<double>(Rng& r, uint32_t kx)
 {
     const uint32_t d = r.draw++;
     uint32_t lo, hi;
     if ((d & 1u) == 0) {
-        const uint4 b = philox4x32_10(make_uint4(d >> 1, 0u, r.plo, r.phi), r.key);
+        const uint4 b = philox4x32_10(make_uint4(d >> 1, 0u, r.plo, r.phi), make_uint2(kx, r.ky));
         lo = b.x; hi = b.y;
         r.c_lo = b.z; r.c_hi = b.w;
     } else {
@@ -267,22 +269,23 @@ __device__ __forceinline__ double f2d(float f)
 }
 
 // ------------------------------------------------------------- per-lane packet state
+// Registers decide occupancy for this latency-bound kernel, so the state is
+// kept lean: the cell is one linear index, and per flight each axis keeps its
+// signed linear stride and the number of steps left before the grid boundary
+// (indices are recovered from the linear index at a flight start).
 template <typename R, int NS>
 struct Lane {
     int st, m;                 // state, model index
-    uint64_t pid;
     Rng rng;
-    uint32_t seq, nev;
+    uint32_t seq, nev;         // trajectory record number, events of this packet
     R x[3], k[3];              // flight origin (cell units) and direction
-    int ix, iy, iz, c;         // cell indices and linear index
+    int c;                     // linear cell index
+    int rem[3], dc[3];         // per axis: steps left inside the grid, signed stride
     int j;                     // frequency index
     R tau, tcur;
     R tm[3], td[3];
     R rho[NS];                 // current cell (FP32: rho*cell; FP64: rho)
     bool lucy;
-    int sx, sy, sz;            // step direction per axis (+1 / -1)
-    const void* grid;          // packed cells of the packet's model
-    int nx, ny, nz;
     R chi;                     // extinction per cell length at frequency j
     R kex[NS], kab[NS];        // kext, kabs at frequency j (FP64: times cell)
     typename PackedT<NS>::T pf;  // prefetched packed density of the next cell
@@ -290,6 +293,8 @@ struct Lane {
     bool outn;                 // the next face is the grid boundary
     int rs;                    // species of a pending re-emission (ST_REEMIT);
                                // its temperature and uniform ride in tau and tcur
+    const void* grid;          // packed cells of the packet's model
+    uint32_t ncross, nlucy;    // crossings and Lucy deposits of the current packet
 };
 
 // a[s] for a register array and a run-time index, without local memory
@@ -302,10 +307,16 @@ __device__ __forceinline__ R sel(const R (&a)[NS], int s)
     return v;
 }
 
-struct Counters {
-    unsigned long long cross;
-    uint32_t c[C_N];
-};
+__device__ __forceinline__ int sel3(const int (&a)[3], int i)
+{
+    return i == 0 ? a[0] : (i == 1 ? a[1] : a[2]);
+}
+
+__device__ __forceinline__ unsigned char* smem_raw()
+{
+    extern __shared__ __align__(16) unsigned char smem_bytes[];
+    return smem_bytes;
+}
 
 // FEAT bits: 1 = modified random walk compiled in, 2 = trajectory logging
 // compiled in (production launches leave unused paths out of the hot code)
@@ -317,24 +328,51 @@ struct Kernel {
     static constexpr bool HAS_TRAJ = (FEAT & 2) != 0;
 
     const TransportKP& P;
-    const float4* s_op;        // [NS][nf] in shared memory (FP32 path)
-    const float* s_xh;
-    const float* s_w;
-    const float* s_mrw;
-    const float* s_cdf;        // source CDFs of a single-model launch (or null)
-    double* s_sed;             // per-block escape SED of a single-model launch (or null)
-    unsigned* s_cnt;
     const ModelDev* md;        // model of the lane's current packet
-    Counters cnt;
 
-    __device__ Kernel(const TransportKP& p, const float4* op, const float* xh, const float* w,
-                      const float* mrw, const float* cdf, double* sed, unsigned* cnt_)
-        : P(p), s_op(op), s_xh(xh), s_w(w), s_mrw(mrw), s_cdf(cdf), s_sed(sed), s_cnt(cnt_),
-          md(nullptr)
+    __device__ explicit Kernel(const TransportKP& p) : P(p), md(nullptr) {}
+
+    // shared-memory tables (offsets set by the host launcher)
+    __device__ __forceinline__ const float4* s_op() const { return reinterpret_cast<const float4*>(smem_raw() + P.so_op); }
+    __device__ __forceinline__ const float* s_xh() const { return reinterpret_cast<const float*>(smem_raw() + P.so_xh); }
+    __device__ __forceinline__ const float* s_w() const { return reinterpret_cast<const float*>(smem_raw() + P.so_w); }
+    __device__ __forceinline__ const float* s_mrw() const { return reinterpret_cast<const float*>(smem_raw() + P.so_mrw); }
+    __device__ __forceinline__ const float* s_cdf() const { return reinterpret_cast<const float*>(smem_raw() + P.so_cdf); }
+    __device__ __forceinline__ double* s_sed() const { return reinterpret_cast<double*>(smem_raw() + P.so_sed); }
+    __device__ __forceinline__ unsigned* s_cnt() const { return reinterpret_cast<unsigned*>(smem_raw() + P.so_cnt); }
+    __device__ __forceinline__ unsigned long long* s_ctr() const { return reinterpret_cast<unsigned long long*>(smem_raw() + P.so_ctr); }
+
+    __device__ __forceinline__ R U(Lane<R, NS>& L) const { return rng_u<R>(L.rng, (uint32_t)P.seed); }
+
+    // Event counters of the lane's current model: per thread in shared memory
+    // (plain adds, no atomics), handed to the model's stats when the lane
+    // moves to another model and at the end of the kernel.
+    __device__ __forceinline__ unsigned long long& slot(int stat) const
     {
-        cnt.cross = 0;
+        return s_ctr()[stat * blockDim.x + threadIdx.x];
+    }
+
+    __device__ __forceinline__ void count(int stat, unsigned v) const { slot(stat) += v; }
+
+    __device__ __forceinline__ void flush_lane(int m) const
+    {
+        unsigned long long* st = P.models[m].stats;
 #pragma unroll
-        for (int i = 0; i < C_N; ++i) cnt.c[i] = 0;
+        for (int i = 0; i < kLaneStats; ++i) {
+            unsigned long long& c = slot(i);
+            if (c) atomicAdd(&st[i], c);
+            c = 0;
+        }
+    }
+
+    // the packet ends: its crossings and Lucy deposits go to the counters
+    __device__ __forceinline__ void end_packet(Lane<R, NS>& L)
+    {
+        count(RT_STAT_CROSSINGS, L.ncross);
+        count(RT_STAT_LUCY, L.nlucy);
+        L.ncross = 0;
+        L.nlucy = 0;
+        L.st = ST_NEED;
     }
 
     __device__ __forceinline__ void load_cell(Lane<R, NS>& L)
@@ -348,12 +386,8 @@ struct Kernel {
     {
         const int a = (L.tm[0] <= L.tm[1] && L.tm[0] <= L.tm[2]) ? 0 : (L.tm[1] <= L.tm[2] ? 1 : 2);
         L.nax = a;
-        const int nix = L.ix + (a == 0 ? L.sx : 0);
-        const int niy = L.iy + (a == 1 ? L.sy : 0);
-        const int niz = L.iz + (a == 2 ? L.sz : 0);
-        L.outn = ((unsigned)nix >= (unsigned)L.nx) | ((unsigned)niy >= (unsigned)L.ny) |
-                 ((unsigned)niz >= (unsigned)L.nz);
-        L.cn = L.c + (a == 0 ? L.sx : (a == 1 ? L.sy * L.nx : L.sz * L.nx * L.ny));
+        L.outn = sel3(L.rem, a) == 0;
+        L.cn = L.c + sel3(L.dc, a);
         if (!L.outn) L.pf = __ldg(reinterpret_cast<const PT*>(L.grid) + L.cn);
     }
 
@@ -382,7 +416,7 @@ struct Kernel {
                 L.kex[s] = (ka + ks) * md->cell;
                 L.kab[s] = ka * md->cell;
             } else {
-                const float4 o = s_op[s * P.nf + L.j];
+                const float4 o = s_op()[s * P.nf + L.j];
                 L.kex[s] = o.x;
                 L.kab[s] = o.y;
             }
@@ -404,7 +438,8 @@ struct Kernel {
             return;
         }
         rt_traj t;
-        t.pid = L.pid; t.seq = q; t.type = type; t.cell = (uint32_t)L.c; t.nu = (uint32_t)L.j;
+        t.pid = ((uint64_t)L.rng.phi << 32) | L.rng.plo;
+        t.seq = q; t.type = type; t.cell = (uint32_t)L.c; t.nu = (uint32_t)L.j;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             t.x[a] = md->box_min[a] + (double)x[a] * md->cell;
@@ -434,29 +469,29 @@ struct Kernel {
             if (P.prefix[mid] <= w) lo = mid; else hi = mid - 1;
         }
         if (lo != L.m) {
-            if (L.m >= 0) flush(L.m);
+            if (L.m >= 0) flush_lane(L.m);
             L.m = lo;
         }
         md = &P.models[lo];
         L.grid = md->rho;
-        L.nx = md->nx; L.ny = md->ny; L.nz = md->nz;
-        L.pid = md->pid_begin + (w - P.prefix[lo]);
-        rng_init(L.rng, P.seed, md->model_id, L.pid);
+        rng_init(L.rng, P.seed, md->model_id, md->pid_begin + (w - P.prefix[lo]));
         L.seq = 0;
         L.nev = 0;
+        L.ncross = 0;
+        L.nlucy = 0;
         int si = 0;
         if (md->nsrc > 1) {
-            const double u = (double)rng_u<R>(L.rng);
+            const double u = (double)U(L);
             si = search_cdf(md->src_Lcdf, md->nsrc, u * md->src_Lcdf[md->nsrc - 1]);
         }
-        const R ub = rng_u<R>(L.rng);
+        const R ub = U(L);
         if constexpr (DBG) {
             const double* cdf = md->src_cdf64 + (size_t)si * P.nf;
             L.j = search_cdf(cdf, P.nf, ub * cdf[P.nf - 1]);
         } else {
-            L.j = search_cdf((s_cdf ? s_cdf : md->src_cdf32) + (size_t)si * P.nf, P.nf, ub);
+            L.j = search_cdf((P.smem_cdf ? s_cdf() : md->src_cdf32) + (size_t)si * P.nf, P.nf, ub);
         }
-        const R u1 = rng_u<R>(L.rng), u2 = rng_u<R>(L.rng);
+        const R u1 = U(L), u2 = U(L);
         iso_dir(u1, u2, L.k);
         int idx[3];
         const int n[3] = { md->nx, md->ny, md->nz };
@@ -470,9 +505,8 @@ struct Kernel {
             idx[a] = i;
             in = in && (i >= 0 && i < n[a]);
         }
-        L.ix = idx[0]; L.iy = idx[1]; L.iz = idx[2];
-        L.c = in ? (L.iz * md->ny + L.iy) * md->nx + L.ix : 0;
-        cnt.c[C_EMIT]++;
+        L.c = in ? (idx[2] * n[1] + idx[1]) * n[0] + idx[0] : 0;
+        count(RT_STAT_EMITTED, 1);
         traj(L, RT_TRAJ_EMIT, L.x);
         if (!in) {
             L.tcur = R(0);
@@ -492,26 +526,26 @@ struct Kernel {
     // atomics, so the crossing loop issues no FP64 arithmetic.
     __device__ __forceinline__ void deposit_lucy(Lane<R, NS>& L, R l)
     {
-        const size_t nc = (size_t)L.nx * L.ny * L.nz;
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
-            const R ta0 = L.kab[s] * L.rho[s] * l;
-            const R ta = P.lucy_form == RT_LUCY_EXPM1 ? -r_expm1(-ta0) : ta0;
+            const size_t idx = (size_t)s * md->ncell + L.c;
+            R ta = L.kab[s] * L.rho[s] * l;
+            if (P.lucy_form == RT_LUCY_EXPM1) ta = -r_expm1(-ta);
             if constexpr (DBG) {
                 const double e = ta * md->xi;
                 if (e != 0.0) {
-                    atomicAdd(&md->E_abs[s * nc + L.c], e);
-                    if (md->esq) atomicAdd(&md->esq[s * nc + L.c], e * e);
+                    atomicAdd(&md->E_abs[idx], e);
+                    if (md->esq) atomicAdd(&md->esq[idx], e * e);
                 }
             } else {
                 if (ta > 0.0f) {
-                    double* e = md->accE + ((s * nc + L.c) << md->acc_q);
+                    double* e = md->accE + (idx << md->acc_q);
                     atomicAdd(e, f2d(ta));
                     if (md->acc_q) atomicAdd(e + 1, f2d(ta * ta));
                 }
             }
         }
-        cnt.c[C_LUCY]++;
+        L.nlucy++;
     }
 
     // Accumulated absorbed power (erg/s) of species s in the lane's cell,
@@ -519,7 +553,7 @@ struct Kernel {
     // add just returned (then the packet's own xi is added).
     __device__ __forceinline__ double energy(const Lane<R, NS>& L, int s, double old, bool have_old)
     {
-        const size_t i = (size_t)s * L.nx * L.ny * L.nz + L.c;
+        const size_t i = (size_t)s * md->ncell + L.c;
         if constexpr (DBG) {
             return have_old ? old + md->xi : __ldcg(&md->E_abs[i]);
         } else {
@@ -547,14 +581,12 @@ struct Kernel {
         }
     }
 
-    // Re-emission frequency: Eq. 10 (B&W, dB/dT weights) or Eq. 5 (frozen T)
     // Temperature that sets the re-emission spectrum: Eq. 4 at the updated
     // energy (B&W) or the previous iteration's value (frozen T)
     __device__ __forceinline__ R emission_T(const Lane<R, NS>& L, int s, double E)
     {
         if (P.mode == RT_MODE_BW) return temperature(L, s, E);
-        const size_t nc = (size_t)L.nx * L.ny * L.nz;
-        return (R)md->T_prev[s * nc + L.c];
+        return (R)md->T_prev[(size_t)s * md->ncell + L.c];
     }
 
     __device__ __forceinline__ int reemit(const Lane<R, NS>& L, int s, double E, R u)
@@ -562,6 +594,7 @@ struct Kernel {
         return reemit_T(s, emission_T(L, s, E), u);
     }
 
+    // Re-emission frequency: Eq. 10 (B&W, dB/dT weights) or Eq. 5 (frozen T)
     __device__ __forceinline__ int reemit_T(int s, R T, R u)
     {
         const bool bw = P.mode == RT_MODE_BW;
@@ -583,13 +616,14 @@ struct Kernel {
         } else {
             if (!(T > 0.0f)) return 0;
             const float invT = 1.0f / T;
-            const float* w = s_w + s * nf;
+            const float* w = s_w() + s * nf;
+            const float* xh = s_xh();
             float tot = 0.0f;
-            for (int l = 0; l < nf; ++l) tot += w[l] * weight(s_xh[l] * invT, bw);
+            for (int l = 0; l < nf; ++l) tot += w[l] * weight(xh[l] * invT, bw);
             const float target = u * tot;
             float acc = 0.0f;
             for (int l = 0; l < nf; ++l) {
-                acc += w[l] * weight(s_xh[l] * invT, bw);
+                acc += w[l] * weight(xh[l] * invT, bw);
                 if (acc >= target) return l;
             }
             return nf - 1;
@@ -623,9 +657,10 @@ struct Kernel {
             int bin = 0;
             if (T > 0.0f) {
                 const float invT = 1.0f / T;
-                const float* w = s_w + s * nf;
+                const float* w = s_w() + s * nf;
+                const float* xh = s_xh();
                 float tot = 0.0f;
-                for (int b = lane; b < nf; b += 32) tot += w[b] * weight(s_xh[b] * invT, bw);
+                for (int b = lane; b < nf; b += 32) tot += w[b] * weight(xh[b] * invT, bw);
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(FULL, tot, o);
                 const float target = u * tot;
@@ -633,7 +668,7 @@ struct Kernel {
                 bin = nf - 1;
                 for (int b0 = 0; b0 < nf; b0 += 32) {
                     const int b = b0 + lane;
-                    float v = b < nf ? w[b] * weight(s_xh[b] * invT, bw) : 0.0f;
+                    float v = b < nf ? w[b] * weight(xh[b] * invT, bw) : 0.0f;
 #pragma unroll
                     for (int o = 1; o < 32; o <<= 1) {
                         const float t = __shfl_up_sync(FULL, v, o);
@@ -659,7 +694,7 @@ struct Kernel {
     // after the re-emission bin is known: isotropic direction, new flight
     __device__ __forceinline__ void finish_absorb(Lane<R, NS>& L)
     {
-        { const R u1 = rng_u<R>(L.rng), u2 = rng_u<R>(L.rng); iso_dir(u1, u2, L.k); }
+        { const R u1 = U(L), u2 = U(L); iso_dir(u1, u2, L.k); }
         load_freq(L);
         traj(L, RT_TRAJ_ABSORB, L.x);
         L.st = ST_FLIGHT;
@@ -673,7 +708,7 @@ struct Kernel {
         for (int s = 0; s < NS; ++s) {
             R ks;
             if constexpr (DBG) ks = sca ? P.ksca[s * P.nf + L.j] : P.kabs[s * P.nf + L.j];
-            else ks = sca ? s_op[s * P.nf + L.j].z : s_op[s * P.nf + L.j].y;
+            else ks = sca ? s_op()[s * P.nf + L.j].z : s_op()[s * P.nf + L.j].y;
             w[s] = L.rho[s] * ks;
             tot += w[s];
         }
@@ -697,9 +732,9 @@ struct Kernel {
         } else {
             atomicAdd(&md->stats[RT_STAT_PAH_DROPPED], 1ull);
         }
-        cnt.c[C_PAH]++;
+        count(RT_STAT_PAH, 1);
         traj(L, RT_TRAJ_PAH, x);
-        L.st = ST_NEED;
+        end_packet(L);
     }
 
     __device__ __forceinline__ bool is_pah(int s) const { return (P.pah_mask >> s) & 1; }
@@ -707,39 +742,50 @@ struct Kernel {
     // A new flight from L.x along L.k: MRW step or tau draw + traversal set-up
     __device__ __forceinline__ void flight(Lane<R, NS>& L)
     {
-        if (HAS_MRW && P.mrw && P.mode != RT_MODE_NOREEMIT && L.chi > (R)P.mrw_tau_cell) {
-            R R0 = R(1e30);
-            const int id[3] = { L.ix, L.iy, L.iz };
+        const int nx = md->nx, ny = md->ny, nz = md->nz;
+        const int iz = L.c / (nx * ny);
+        const int r = L.c - iz * nx * ny;
+        const int iy = r / nx;
+        const int ix = r - iy * nx;
+        const int id[3] = { ix, iy, iz };
+        if constexpr (HAS_MRW) {
+            if (P.mrw && P.mode != RT_MODE_NOREEMIT && L.chi > (R)P.mrw_tau_cell) {
+                R R0 = R(1e30);
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const R d1 = L.x[a] - (R)id[a], d2 = (R)(id[a] + 1) - L.x[a];
-                R0 = fmin(R0, fmin(d1, d2));
-            }
-            R0 = fmax(R0, R(0));
-            if (R0 * L.chi >= (R)P.mrw_gamma) {
-                mrw_step(L, R0);
-                return;
+                for (int a = 0; a < 3; ++a) {
+                    const R d1 = L.x[a] - (R)id[a], d2 = (R)(id[a] + 1) - L.x[a];
+                    R0 = fmin(R0, fmin(d1, d2));
+                }
+                R0 = fmax(R0, R(0));
+                if (R0 * L.chi >= (R)P.mrw_gamma) {
+                    mrw_step(L, R0);
+                    return;
+                }
             }
         }
-        L.tau = -r_log(rng_u<R>(L.rng));
-        const int id[3] = { L.ix, L.iy, L.iz };
+        L.tau = -r_log(U(L));
+        const int n[3] = { nx, ny, nz };
+        const int stride[3] = { 1, nx, nx * ny };
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             const R ka = L.k[a];
             if (ka > R(0)) {
                 L.td[a] = R(1) / ka;
                 L.tm[a] = fmax(((R)(id[a] + 1) - L.x[a]) * L.td[a], R(0));
+                L.rem[a] = n[a] - 1 - id[a];
+                L.dc[a] = stride[a];
             } else if (ka < R(0)) {
                 L.td[a] = R(-1) / ka;
                 L.tm[a] = fmax((L.x[a] - (R)id[a]) * L.td[a], R(0));
+                L.rem[a] = id[a];
+                L.dc[a] = -stride[a];
             } else {
                 L.td[a] = R(INFINITY);
                 L.tm[a] = R(INFINITY);
+                L.rem[a] = 1;
+                L.dc[a] = 0;
             }
         }
-        L.sx = L.k[0] > R(0) ? 1 : -1;
-        L.sy = L.k[1] > R(0) ? 1 : -1;
-        L.sz = L.k[2] > R(0) ? 1 : -1;
         L.tcur = R(0);
         prefetch_next(L);
         L.st = ST_MARCH;
@@ -748,46 +794,46 @@ struct Kernel {
     __device__ __forceinline__ void mrw_step(Lane<R, NS>& L, R R0)
     {
         if (++L.nev > P.max_events) {
-            cnt.c[C_STUCK]++;
+            count(RT_STAT_STUCK, 1);
             traj(L, RT_TRAJ_STUCK, L.x);
-            L.st = ST_NEED;
+            end_packet(L);
             return;
         }
-        const R u = rng_u<R>(L.rng);
+        const R u = U(L);
         R y;
         if constexpr (DBG) y = mrw_y64(u);
-        else y = mrw_y32(s_mrw, u);
+        else y = mrw_y32(s_mrw(), u);
         const R l = R(3) * L.chi * R0 * R0 * y;          // path length in cells
         R nh[3];
-        { const R u1 = rng_u<R>(L.rng), u2 = rng_u<R>(L.rng); iso_dir(u1, u2, nh); }
+        { const R u1 = U(L), u2 = U(L); iso_dir(u1, u2, nh); }
 #pragma unroll
         for (int a = 0; a < 3; ++a) L.x[a] += R0 * nh[a];
-        { const R u3 = rng_u<R>(L.rng), u4 = rng_u<R>(L.rng); iso_dir(u3, u4, L.k); }
-        const size_t nc = (size_t)L.nx * L.ny * L.nz;
+        { const R u3 = U(L), u4 = U(L); iso_dir(u3, u4, L.k); }
         R ca = R(0);
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
+            const size_t idx = (size_t)s * md->ncell + L.c;
             const R ta = L.kab[s] * L.rho[s] * l;
             ca += L.kab[s] * L.rho[s];
             if constexpr (DBG) {
                 const double e = ta * md->xi;
                 if (e != 0.0) {
-                    atomicAdd(&md->E_abs[s * nc + L.c], e);
-                    if (md->esq) atomicAdd(&md->esq[s * nc + L.c], e * e);
+                    atomicAdd(&md->E_abs[idx], e);
+                    if (md->esq) atomicAdd(&md->esq[idx], e * e);
                 }
             } else if (ta > 0.0f) {
-                double* e = md->accE + ((s * nc + L.c) << md->acc_q);
+                double* e = md->accE + (idx << md->acc_q);
                 atomicAdd(e, f2d(ta));
                 if (md->acc_q) atomicAdd(e + 1, f2d(ta * ta));
             }
         }
-        cnt.c[C_MRW]++;
-        if (rng_u<R>(L.rng) < -r_expm1(-ca * l)) {
+        count(RT_STAT_MRW, 1);
+        if (U(L) < -r_expm1(-ca * l)) {
             int s = 0;
-            if (NS > 1) s = pick_species(L, false, rng_u<R>(L.rng));
+            if (NS > 1) s = pick_species(L, false, U(L));
             if (is_pah(s)) { store_pah(L, L.x); return; }
             const double E = energy(L, s, 0.0, false);
-            L.j = reemit(L, s, E, rng_u<R>(L.rng));
+            L.j = reemit(L, s, E, U(L));
             load_freq(L);
         }
         traj(L, RT_TRAJ_MRW, L.x);
@@ -808,16 +854,16 @@ struct Kernel {
             if (L.lucy) deposit_lucy(L, seg);
             L.tau -= dtau;
             L.tcur = tn;
-            cnt.cross++;
+            L.ncross++;
             if (L.outn) {
-                L.st = ST_ESCAPE;          // ix, iy, iz, c keep the last cell inside
+                L.st = ST_ESCAPE;          // c keeps the last cell inside
             } else {
                 L.tm[0] = a == 0 ? L.tm[0] + L.td[0] : L.tm[0];
                 L.tm[1] = a == 1 ? L.tm[1] + L.td[1] : L.tm[1];
                 L.tm[2] = a == 2 ? L.tm[2] + L.td[2] : L.tm[2];
-                L.ix += a == 0 ? L.sx : 0;
-                L.iy += a == 1 ? L.sy : 0;
-                L.iz += a == 2 ? L.sz : 0;
+                L.rem[0] -= a == 0;
+                L.rem[1] -= a == 1;
+                L.rem[2] -= a == 2;
                 L.c = L.cn;
                 use_cell(L, L.pf);
                 prefetch_next(L);
@@ -836,29 +882,29 @@ struct Kernel {
     __device__ __forceinline__ void interact(Lane<R, NS>& L, bool coop = false)
     {
         if (++L.nev > P.max_events) {
-            cnt.c[C_STUCK]++;
+            count(RT_STAT_STUCK, 1);
             traj(L, RT_TRAJ_STUCK, L.x);
-            L.st = ST_NEED;
+            end_packet(L);
             return;
         }
-        cnt.c[C_INT]++;
+        count(RT_STAT_INTERACTIONS, 1);
         R cs = R(0);
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
             R ks;
             if constexpr (DBG) ks = P.ksca[s * P.nf + L.j] * md->cell;
-            else ks = s_op[s * P.nf + L.j].z;
+            else ks = s_op()[s * P.nf + L.j].z;
             cs += L.rho[s] * ks;
         }
         const R albedo = cs / L.chi;
-        if (rng_u<R>(L.rng) < albedo) {
+        if (U(L) < albedo) {
             int s = 0;
-            if (NS > 1) s = pick_species(L, true, rng_u<R>(L.rng));
+            if (NS > 1) s = pick_species(L, true, U(L));
             R g;
             if constexpr (DBG) g = P.g[s * P.nf + L.j];
-            else g = s_op[s * P.nf + L.j].w;
-            const R mu = hg_mu(g, rng_u<R>(L.rng));
-            const R uphi = rng_u<R>(L.rng);
+            else g = s_op()[s * P.nf + L.j].w;
+            const R mu = hg_mu(g, U(L));
+            const R uphi = U(L);
             if (P.record_events) {
                 const unsigned long long slot = atomicAdd(&md->stats[RT_STAT_N_EVENTS], 1ull);
                 if (md->events && slot < md->event_cap) {
@@ -872,26 +918,26 @@ struct Kernel {
                 }
             }
             rotate(L.k, mu, uphi);
-            cnt.c[C_SCA]++;
+            count(RT_STAT_SCATTERS, 1);
             traj(L, RT_TRAJ_SCATTER, L.x);
             L.st = ST_FLIGHT;
             return;
         }
-        cnt.c[C_ABS]++;
+        count(RT_STAT_ABSORPTIONS, 1);
         int s = 0;
-        if (NS > 1) s = pick_species(L, false, rng_u<R>(L.rng));
+        if (NS > 1) s = pick_species(L, false, U(L));
         if (is_pah(s)) { store_pah(L, L.x); return; }
-        const size_t nc = (size_t)L.nx * L.ny * L.nz;
+        const size_t idx = (size_t)s * md->ncell + L.c;
         double E = 0.0;
         if constexpr (DBG) {
             if (!L.lucy) {
-                const double old = atomicAdd(&md->E_abs[s * nc + L.c], md->xi);
-                if (md->esq) atomicAdd(&md->esq[s * nc + L.c], md->xi * md->xi);
+                const double old = atomicAdd(&md->E_abs[idx], md->xi);
+                if (md->esq) atomicAdd(&md->esq[idx], md->xi * md->xi);
                 if (P.mode == RT_MODE_BW) E = energy(L, s, old, true);
             } else if (P.mode == RT_MODE_BW) {
                 E = energy(L, s, 0.0, false);
             }
-            atomicAdd(&md->count[s * nc + L.c], 1u);
+            atomicAdd(&md->count[idx], 1u);
         } else {
             // Lanes absorbing in the same cell and species combine into one
             // atomic: the group leader adds the group size, and lane r of the
@@ -899,7 +945,6 @@ struct Kernel {
             // after another in lane order).  Optically thick cells next to a
             // source receive most absorptions; per-lane atomics on them
             // serialise in L2.
-            const size_t idx = s * nc + L.c;
             const unsigned grp = __match_any_sync(__activemask(), (unsigned long long)idx * 2u + (L.lucy ? 1u : 0u));
             const int leader = __ffs(grp) - 1;
             const unsigned rank = __popc(grp & ((1u << (threadIdx.x & 31)) - 1u));
@@ -924,10 +969,10 @@ struct Kernel {
         }
         if (P.mode == RT_MODE_NOREEMIT) {
             traj(L, RT_TRAJ_ABSORB_END, L.x);
-            L.st = ST_NEED;
+            end_packet(L);
             return;
         }
-        const R u = rng_u<R>(L.rng);
+        const R u = U(L);
         if (coop) {
             L.tau = emission_T(L, s, E);
             L.tcur = u;
@@ -943,74 +988,95 @@ struct Kernel {
     {
         int b = (int)floor((L.k[2] + R(1)) * R(5));
         b = min(max(b, 0), kSedBins - 1);
-        if (s_sed) {
-            atomicAdd(&s_sed[b * P.nf + L.j], md->xi);
-            atomicAdd(&s_cnt[b * P.nf + L.j], 1u);
+        if (P.smem_sed && !DBG) {
+            atomicAdd(&s_sed()[b * P.nf + L.j], md->xi);
+            atomicAdd(&s_cnt()[b * P.nf + L.j], 1u);
         } else {
             atomicAdd(&md->sed_esc[b * P.nf + L.j], md->xi);
             atomicAdd(&md->sed_cnt[b * P.nf + L.j], 1ull);
         }
-        cnt.c[C_ESC]++;
-        if (md->traj) {
-            R xe[3];
+        count(RT_STAT_ESCAPED, 1);
+        if constexpr (HAS_TRAJ) {
+            if (md->traj) {
+                R xe[3];
 #pragma unroll
-            for (int a = 0; a < 3; ++a) xe[a] = L.x[a] + L.tcur * L.k[a];
-            traj(L, RT_TRAJ_ESCAPE, xe);
+                for (int a = 0; a < 3; ++a) xe[a] = L.x[a] + L.tcur * L.k[a];
+                traj(L, RT_TRAJ_ESCAPE, xe);
+            }
         }
-        L.st = ST_NEED;
+        end_packet(L);
     }
 
-    // add this lane's counters to model m's stats
-    __device__ __forceinline__ void flush(int m)
+    // End of the persistent loop (all lanes converged): counters of warps
+    // whose lanes share one model are summed with shuffles first.
+    __device__ __forceinline__ void flush_warp(int m) const
     {
-        unsigned long long* st = P.models[m].stats;
-        if (cnt.cross) atomicAdd(&st[RT_STAT_CROSSINGS], cnt.cross);
-        const int map[C_N] = { RT_STAT_INTERACTIONS, RT_STAT_SCATTERS, RT_STAT_ABSORPTIONS,
-                               RT_STAT_MRW, RT_STAT_ESCAPED, RT_STAT_STUCK, RT_STAT_PAH,
-                               RT_STAT_LUCY, RT_STAT_EMITTED };
+        const int m0 = __shfl_sync(FULL, m, 0);
+        if (__all_sync(FULL, m == m0)) {
+            if (m0 < 0) return;
+            unsigned long long* st = P.models[m0].stats;
 #pragma unroll
-        for (int i = 0; i < C_N; ++i)
-            if (cnt.c[i]) atomicAdd(&st[map[i]], (unsigned long long)cnt.c[i]);
-        cnt.cross = 0;
+            for (int i = 0; i < kLaneStats; ++i) {
+                unsigned long long v = slot(i);
 #pragma unroll
-        for (int i = 0; i < C_N; ++i) cnt.c[i] = 0;
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+                if ((threadIdx.x & 31) == 0 && v) atomicAdd(&st[i], v);
+            }
+        } else if (m >= 0) {
+            flush_lane(m);
+        }
+    }
+
+    // block SED tallies to global memory (thread-strided, after a barrier)
+    __device__ __forceinline__ void flush_sed(int t, int nt) const
+    {
+        if (P.smem_sed && !DBG) {
+            const ModelDev& m0 = P.models[0];
+            const double* sed = s_sed();
+            const unsigned* cnt = s_cnt();
+            for (int i = t; i < kSedBins * P.nf; i += nt)
+                if (cnt[i]) {
+                    atomicAdd(&m0.sed_esc[i], sed[i]);
+                    atomicAdd(&m0.sed_cnt[i], (unsigned long long)cnt[i]);
+                }
+        }
     }
 };
 
-// Shared memory: [escape SED doubles][escape counts][opacity float4]
-// [h nu / k][re-emission weights][MRW survival][source CDFs]; the SED and CDF
-// parts exist only for single-model, persistent launches (smem_sed, smem_cdf).
 #ifndef RT_TRANSPORT_MIN_BLOCKS
-#define RT_TRANSPORT_MIN_BLOCKS 3
+#define RT_TRANSPORT_MIN_BLOCKS 4
 #endif
 template <typename R, int NS, int FEAT>
-__global__ void __launch_bounds__(256, RT_TRANSPORT_MIN_BLOCKS)
+__global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : RT_TRANSPORT_MIN_BLOCKS)
     transport_kernel(const __grid_constant__ TransportKP P, int serial)
 {
-    extern __shared__ float4 smem[];
-    const int nsed = P.smem_sed ? kSedBins * P.nf : 0;
-    double* s_sed = reinterpret_cast<double*>(smem);
-    unsigned* s_cnt = reinterpret_cast<unsigned*>(s_sed + nsed);
-    float4* s_op = smem + (nsed * 12 + 15) / 16;
-    float* s_xh = reinterpret_cast<float*>(s_op + NS * P.nf);
-    float* s_w = s_xh + P.nf;
-    float* s_mrw = s_w + NS * P.nf;
-    float* s_cdf = s_mrw + ((FEAT & 1) && P.mrw ? kMrwN : 0);
-    if (sizeof(R) == 4) {
+    unsigned char* sm = smem_raw();
+    {
+        float4* s_op = reinterpret_cast<float4*>(sm + P.so_op);
+        float* s_xh = reinterpret_cast<float*>(sm + P.so_xh);
+        float* s_w = reinterpret_cast<float*>(sm + P.so_w);
         for (int i = threadIdx.x; i < NS * P.nf; i += blockDim.x) {
             s_op[i] = P.opac32[i];
             s_w[i] = P.wre[i];
         }
         for (int i = threadIdx.x; i < P.nf; i += blockDim.x) s_xh[i] = P.xh[i];
-        if ((FEAT & 1) && P.mrw)
+        if ((FEAT & 1) && P.mrw) {
+            float* s_mrw = reinterpret_cast<float*>(sm + P.so_mrw);
             for (int i = threadIdx.x; i < kMrwN; i += blockDim.x) s_mrw[i] = P.mrwS[i];
+        }
+        float* s_cdf = reinterpret_cast<float*>(sm + P.so_cdf);
         for (int i = threadIdx.x; i < P.smem_cdf; i += blockDim.x) s_cdf[i] = P.models[0].src_cdf32[i];
-        for (int i = threadIdx.x; i < nsed; i += blockDim.x) { s_sed[i] = 0.0; s_cnt[i] = 0u; }
+        if (P.smem_sed) {
+            double* s_sed = reinterpret_cast<double*>(sm + P.so_sed);
+            unsigned* s_cnt = reinterpret_cast<unsigned*>(sm + P.so_cnt);
+            for (int i = threadIdx.x; i < kSedBins * P.nf; i += blockDim.x) { s_sed[i] = 0.0; s_cnt[i] = 0u; }
+        }
+        unsigned long long* s_ctr = reinterpret_cast<unsigned long long*>(sm + P.so_ctr);
+        for (int i = threadIdx.x; i < kLaneStats * (int)blockDim.x; i += blockDim.x) s_ctr[i] = 0ull;
     }
     __syncthreads();
 
-    Kernel<R, NS, FEAT> K(P, s_op, s_xh, s_w, s_mrw, (sizeof(R) == 4 && P.smem_cdf) ? s_cdf : nullptr,
-                          (sizeof(R) == 4 && nsed && !serial) ? s_sed : nullptr, s_cnt);
+    Kernel<R, NS, FEAT> K(P);
     Lane<R, NS> L;
     L.st = ST_NEED;
     L.m = -1;
@@ -1029,7 +1095,8 @@ __global__ void __launch_bounds__(256, RT_TRANSPORT_MIN_BLOCKS)
                 else if (L.st == ST_ESCAPE) K.escape(L);
             }
         }
-        if (L.m >= 0) K.flush(L.m);
+        if (L.m >= 0) K.flush_lane(L.m);
+        K.flush_sed(0, 1);
         return;
     }
 
@@ -1096,15 +1163,10 @@ __global__ void __launch_bounds__(256, RT_TRANSPORT_MIN_BLOCKS)
             }
         }
     }
-    if (L.m >= 0) K.flush(L.m);
-    if (K.s_sed) {
+    K.flush_warp(L.m);
+    if (P.smem_sed) {
         __syncthreads();
-        const ModelDev& m0 = P.models[0];
-        for (int i = threadIdx.x; i < nsed; i += blockDim.x)
-            if (s_cnt[i]) {
-                atomicAdd(&m0.sed_esc[i], s_sed[i]);
-                atomicAdd(&m0.sed_cnt[i], (unsigned long long)s_cnt[i]);
-            }
+        K.flush_sed(threadIdx.x, blockDim.x);
     }
 }
 
@@ -1168,15 +1230,28 @@ template <typename R, int NS, int FEAT>
 rt_status launch_one(rt_ctx* ctx, const TransportKP& kp, int schedule, int threads,
                      int blocks_per_sm, cudaStream_t s)
 {
+    TransportKP k = kp;
     const size_t nsed = kp.smem_sed ? (size_t)kSedBins * kp.nf : 0;
-    const size_t smem = (nsed * 12 + 15) / 16 * 16 + sizeof(float4) * NS * kp.nf +
-                        sizeof(float) * kp.nf + sizeof(float) * NS * kp.nf +
-                        ((FEAT & 1) && kp.mrw ? sizeof(float) * kMrwN : 0) +
-                        sizeof(float) * kp.smem_cdf;
+    size_t off = 0;
+    auto place = [&](size_t bytes, size_t align) {
+        off = (off + align - 1) / align * align;
+        const int o = (int)off;
+        off += bytes;
+        return o;
+    };
+    k.so_ctr = place(sizeof(unsigned long long) * kLaneStats * (schedule == RT_SCHED_SERIAL ? 32 : threads), 16);
+    k.so_sed = place(sizeof(double) * nsed, 16);
+    k.so_op = place(sizeof(float4) * NS * kp.nf, 16);
+    k.so_cnt = place(sizeof(unsigned) * nsed, 16);
+    k.so_xh = place(sizeof(float) * kp.nf, 16);
+    k.so_w = place(sizeof(float) * NS * kp.nf, 16);
+    k.so_mrw = place((FEAT & 1) && kp.mrw ? sizeof(float) * kMrwN : 0, 16);
+    k.so_cdf = place(sizeof(float) * kp.smem_cdf, 16);
+    const size_t smem = (off + 15) / 16 * 16;
     auto fn = transport_kernel<R, NS, FEAT>;
     RT_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     if (schedule == RT_SCHED_SERIAL) {
-        fn<<<1, 32, smem, s>>>(kp, 1);
+        fn<<<1, 32, smem, s>>>(k, 1);
         count_launches();
     } else {
         int nb = blocks_per_sm;
@@ -1184,7 +1259,7 @@ rt_status launch_one(rt_ctx* ctx, const TransportKP& kp, int schedule, int threa
             RT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, threads, smem));
             nb = std::max(nb, 1);
         }
-        fn<<<ctx->num_sms * nb, threads, smem, s>>>(kp, 0);
+        fn<<<ctx->num_sms * nb, threads, smem, s>>>(k, 0);
         count_launches();
     }
     RT_CUDA(cudaGetLastError());
