@@ -369,6 +369,7 @@ static rt_status stage_models(std::vector<HostModel>& hms, const std::vector<uin
         md.src_cdf64 = (const double*)(base + o_c64[i]);
         md.src_cdf32 = (const float*)(base + o_c32[i]);
         std::memcpy(&h[o_models + sizeof(ModelDev) * i], &md, sizeof(ModelDev));
+        hms[i].md = md;                // the host copy now matches the device one
     }
     std::memcpy(&h[o_prefix], prefix.data(), sizeof(unsigned long long) * (n + 1));
     if (async) {
@@ -406,6 +407,8 @@ static void fill_kp(TransportKP& kp, const rt_opacity* op, const rt_transport_pa
         if (op->is_pah[s]) kp.pah_mask |= 1 << s;
     kp.march_min_active = p->march_min_active < 0 ? 8 : p->march_min_active;
     kp.want_traj = 0;
+    kp.single = 0;
+    kp.rho0 = nullptr;
     kp.smem_sed = 0;
     kp.smem_cdf = 0;
     kp.max_events = p->max_events;
@@ -428,14 +431,22 @@ static void fill_kp(TransportKP& kp, const rt_opacity* op, const rt_transport_pa
 // Shared-memory options of a single-model launch: per-block escape SED (the
 // 10 x nf tallies otherwise take heavily contended global atomics) and the
 // source CDFs; trajectory logging selects the kernel variant that has it.
-static void single_model_options(TransportKP& kp, const rt_opacity* op,
-                                 const rt_transport_params* p, const rt_transport_out* out,
-                                 int n_sources)
+static rt_status single_model_options(TransportKP& kp, const rt_opacity* op,
+                                      const rt_transport_params* p, const rt_transport_out* out,
+                                      int n_sources, const ModelDev& m0)
 {
+    // the kernel reads this descriptor from its launch parameters: it must
+    // be the staged one, with every device table in place
+    if (!m0.rho || !m0.src_pos || !m0.src_Lcdf || !m0.src_cdf64 || !m0.src_cdf32 || !m0.stats)
+        return fail(RT_ERR_STATE, "transport: model descriptor not staged");
     kp.want_traj = out->traj != nullptr && out->traj_cap > 0;
+    kp.single = 1;
+    kp.rho0 = m0.rho;
+    kp.m0 = m0;
     const bool persistent = p->schedule == RT_SCHED_PERSISTENT && p->precision == RT_PREC_FP32;
     kp.smem_sed = persistent && op->nf <= 256 ? 1 : 0;
     kp.smem_cdf = persistent && n_sources * op->nf <= 4096 ? n_sources * op->nf : 0;
+    return RT_OK;
 }
 
 }  // namespace rtgb
@@ -497,7 +508,8 @@ rt_status rt_transport(rt_ctx* ctx, const rt_grid* grid, const rt_opacity* op,
     RT_CUDA(cudaMemsetAsync(dm.work, 0, sizeof(unsigned long long), s));
     TransportKP kp;
     fill_kp(kp, op, p, dm, 1);
-    single_model_options(kp, op, p, out, n_sources);
+    st = single_model_options(kp, op, p, out, n_sources, hms[0].md);
+    if (st != RT_OK) { cudaFreeAsync(dm.buf, s); if (acc) cudaFreeAsync(acc, s); return st; }
     const int threads = p->threads_per_block ? p->threads_per_block : 256;
     st = launch_transport(ctx, op, kp, op->ns, p->precision, p->schedule, threads, p->blocks_per_sm, s);
     if (st == RT_OK && acc)
@@ -753,6 +765,7 @@ static rt_status stage_models_into(std::vector<HostModel>& hms, uint64_t nwork, 
     md.src_cdf64 = (const double*)(base + o_c64);
     md.src_cdf32 = (const float*)(base + o_c32);
     std::memcpy(&h[o_models], &md, sizeof(ModelDev));
+    hm.md = md;                        // the host copy now matches the device one
     const unsigned long long prefix[2] = { 0ull, (unsigned long long)nwork };
     std::memcpy(&h[o_prefix], prefix, sizeof(prefix));
     RT_CUDA(cudaMemcpyAsync(base, h.data(), off, cudaMemcpyHostToDevice, s));
@@ -823,7 +836,8 @@ rt_status rt_transport_noalloc(rt_ctx* ctx, const rt_grid* grid, const rt_opacit
     RT_CUDA(cudaMemsetAsync(dm.work, 0, sizeof(unsigned long long), s));
     TransportKP kp;
     fill_kp(kp, op, p, dm, 1);
-    single_model_options(kp, op, p, out, n_sources);
+    st = single_model_options(kp, op, p, out, n_sources, hms[0].md);
+    if (st != RT_OK) return st;
     const int threads = p->threads_per_block ? p->threads_per_block : 256;
     st = launch_transport(ctx, op, kp, op->ns, p->precision, p->schedule, threads, p->blocks_per_sm, s);
     if (st == RT_OK && acc)

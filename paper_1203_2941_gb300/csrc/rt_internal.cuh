@@ -122,10 +122,13 @@ struct TransportKP {
     int pah_mask;
     int march_min_active;
     int want_traj;                      // some model logs trajectories
+    int single;                         // one model, whose descriptor is m0 (read from the
+    const void* rho0;                   // launch parameters) and packed grid rho0
+    ModelDev m0;
     int smem_sed;                       // single-model persistent launch: SED tallied per block
     int smem_cdf;                       // floats of model 0's source CDFs kept in shared memory
     // dynamic shared-memory layout (byte offsets, set by the launcher)
-    int so_sed, so_cnt, so_op, so_xh, so_w, so_mrw, so_cdf, so_ctr;
+    int so_sed, so_cnt, so_op, so_xh, so_w, so_mrw, so_cdf, so_ctr, so_claim;
     unsigned long long max_events;
     uint64_t seed;
     double mrw_tau_cell, mrw_gamma;

@@ -281,7 +281,9 @@ struct Lane {
     R x[3], k[3];              // flight origin (cell units) and direction
     int c;                     // linear cell index
     int rem[3], dc[3];         // per axis: steps left inside the grid, signed stride
-    int j;                     // frequency index
+    int j;                     // frequency index; in ST_REEMIT the species of the
+                               // pending re-emission (its temperature and uniform
+                               // ride in tau and tcur)
     R tau, tcur;
     R tm[3], td[3];
     R rho[NS];                 // current cell (FP32: rho*cell; FP64: rho)
@@ -291,8 +293,6 @@ struct Lane {
     typename PackedT<NS>::T pf;  // prefetched packed density of the next cell
     int cn, nax;               // next cell's linear index, axis of the next face
     bool outn;                 // the next face is the grid boundary
-    int rs;                    // species of a pending re-emission (ST_REEMIT);
-                               // its temperature and uniform ride in tau and tcur
     const void* grid;          // packed cells of the packet's model
     uint32_t ncross, nlucy;    // crossings and Lucy deposits of the current packet
 };
@@ -319,18 +319,33 @@ __device__ __forceinline__ unsigned char* smem_raw()
 }
 
 // FEAT bits: 1 = modified random walk compiled in, 2 = trajectory logging
-// compiled in (production launches leave unused paths out of the hot code)
+// compiled in, 4 = a single model (its index, descriptor and grid come from
+// the launch parameters instead of lane registers); production launches leave
+// unused paths out of the hot code.
 template <typename R, int NS, int FEAT>
 struct Kernel {
     using PT = typename PackedT<NS>::T;
     static constexpr bool DBG = sizeof(R) == 8;
     static constexpr bool HAS_MRW = (FEAT & 1) != 0;
     static constexpr bool HAS_TRAJ = (FEAT & 2) != 0;
+    static constexpr bool SINGLE = (FEAT & 4) != 0;
 
     const TransportKP& P;
     const ModelDev* md;        // model of the lane's current packet
 
-    __device__ explicit Kernel(const TransportKP& p) : P(p), md(nullptr) {}
+    __device__ explicit Kernel(const TransportKP& p) : P(p), md(SINGLE ? &p.m0 : p.models) {}
+
+    // descriptor of the lane's model, before a call that uses md
+    __device__ __forceinline__ void bind(const Lane<R, NS>& L)
+    {
+        if constexpr (!SINGLE) md = &P.models[L.m];
+    }
+
+    __device__ __forceinline__ const PT* cells(const Lane<R, NS>& L) const
+    {
+        if constexpr (SINGLE) return reinterpret_cast<const PT*>(P.rho0);
+        else return reinterpret_cast<const PT*>(L.grid);
+    }
 
     // shared-memory tables (offsets set by the host launcher)
     __device__ __forceinline__ const float4* s_op() const { return reinterpret_cast<const float4*>(smem_raw() + P.so_op); }
@@ -377,7 +392,7 @@ struct Kernel {
 
     __device__ __forceinline__ void load_cell(Lane<R, NS>& L)
     {
-        use_cell(L, __ldg(reinterpret_cast<const PT*>(L.grid) + L.c));
+        use_cell(L, __ldg(cells(L) + L.c));
     }
 
     // Next cell of the traversal (nearest face, ties to the lowest axis); its
@@ -388,7 +403,7 @@ struct Kernel {
         L.nax = a;
         L.outn = sel3(L.rem, a) == 0;
         L.cn = L.c + sel3(L.dc, a);
-        if (!L.outn) L.pf = __ldg(reinterpret_cast<const PT*>(L.grid) + L.cn);
+        if (!L.outn) L.pf = __ldg(cells(L) + L.cn);
     }
 
     __device__ __forceinline__ void use_cell(Lane<R, NS>& L, const PT v)
@@ -462,18 +477,23 @@ struct Kernel {
 
     __device__ __forceinline__ void emit(Lane<R, NS>& L, uint64_t w)
     {
-        // model lookup: largest m with prefix[m] <= w
-        int lo = 0, hi = P.n_models - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (P.prefix[mid] <= w) lo = mid; else hi = mid - 1;
+        int lo = 0;
+        if constexpr (!SINGLE) {
+            // model lookup: largest m with prefix[m] <= w
+            int hi = P.n_models - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (P.prefix[mid] <= w) lo = mid; else hi = mid - 1;
+            }
+            if (lo != L.m) {
+                if (L.m >= 0) flush_lane(L.m);
+                L.m = lo;
+            }
+            md = &P.models[lo];
+            L.grid = md->rho;
+        } else {
+            L.m = 0;
         }
-        if (lo != L.m) {
-            if (L.m >= 0) flush_lane(L.m);
-            L.m = lo;
-        }
-        md = &P.models[lo];
-        L.grid = md->rho;
         rng_init(L.rng, P.seed, md->model_id, md->pid_begin + (w - P.prefix[lo]));
         L.seq = 0;
         L.nev = 0;
@@ -653,7 +673,7 @@ struct Kernel {
             const int src = __ffs(m) - 1;
             const float T = __shfl_sync(FULL, (float)L.tau, src);
             const float u = __shfl_sync(FULL, (float)L.tcur, src);
-            const int s = __shfl_sync(FULL, L.rs, src);
+            const int s = __shfl_sync(FULL, L.j, src);
             int bin = 0;
             if (T > 0.0f) {
                 const float invT = 1.0f / T;
@@ -976,7 +996,7 @@ struct Kernel {
         if (coop) {
             L.tau = emission_T(L, s, E);
             L.tcur = u;
-            L.rs = s;
+            L.j = s;
             L.st = ST_REEMIT;
             return;
         }
@@ -1103,22 +1123,24 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : RT_TRANSPORT_MIN_BLO
     const int min_active = P.march_min_active;
     // Packet ids are claimed per warp in chunks (one global atomic per chunk);
     // the chunk shrinks from 256 to 32 ids as the work runs out, which keeps
-    // the tail balanced.  [w_next, w_end) is the warp's unclaimed range.
-    unsigned long long w_next = 0, w_end = 0;
-    bool exhausted = false;
-    const unsigned long long n_warps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
+    // the tail balanced.  The warp's unclaimed range [claim[0], claim[1]) is
+    // kept in shared memory, off the registers of the crossing loop; once a
+    // range ends at total_work every id has been claimed.
+    unsigned long long* claim = reinterpret_cast<unsigned long long*>(sm + P.so_claim) + 2 * (threadIdx.x >> 5);
+    if (lane == 0) { claim[0] = 0; claim[1] = 0; }
+    __syncwarp();
     for (;;) {
         const unsigned need = __ballot_sync(FULL, L.st == ST_NEED);
         if (need) {
-            if (w_next == w_end && !exhausted) {
+            unsigned long long w_next = claim[0], w_end = claim[1];
+            if (w_next == w_end && w_end < P.total_work) {
                 unsigned long long base = 0;
-                const unsigned long long left = P.total_work > w_end ? P.total_work - w_end : 0;
-                unsigned long long chunk = left / (4ull * n_warps);
+                const unsigned long long n_warps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
+                unsigned long long chunk = (P.total_work - w_end) / (4ull * n_warps);
                 chunk = chunk < 32ull ? 32ull : (chunk > 256ull ? 256ull : chunk);
                 if (lane == 0) base = atomicAdd(P.work_ctr, chunk);
                 base = __shfl_sync(FULL, base, 0);
                 if (base >= P.total_work) {
-                    exhausted = true;
                     w_next = w_end = P.total_work;
                 } else {
                     w_next = base;
@@ -1129,19 +1151,22 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : RT_TRANSPORT_MIN_BLO
             const unsigned rank = __popc(need & ((1u << lane) - 1u));
             if (L.st == ST_NEED) {
                 if (rank < avail) K.emit(L, w_next + rank);
-                else if (exhausted) L.st = ST_DONE;
+                else if (w_end >= P.total_work) L.st = ST_DONE;
             }
             w_next += __popc(need) < avail ? __popc(need) : avail;
+            __syncwarp();
+            if (lane == 0) { claim[0] = w_next; claim[1] = w_end; }
+            __syncwarp();
         }
         if (__all_sync(FULL, L.st == ST_DONE)) break;
         if (L.st == ST_FLIGHT) {
-            K.md = &P.models[L.m];
+            K.bind(L);
             K.flight(L);
         }
         int nm;
         do {
             if (L.st == ST_MARCH) {
-                K.md = &P.models[L.m];
+                K.bind(L);
                 K.march(L);
                 if (L.st == ST_MARCH) K.march(L);
             }
@@ -1149,21 +1174,21 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : RT_TRANSPORT_MIN_BLO
         } while (nm > min_active);
         constexpr bool COOP = sizeof(R) == 4;
         if (L.st == ST_INTERACT) {
-            K.md = &P.models[L.m];
+            K.bind(L);
             K.interact(L, COOP);
         } else if (L.st == ST_ESCAPE) {
-            K.md = &P.models[L.m];
+            K.bind(L);
             K.escape(L);
         }
         if constexpr (COOP) {
             K.reemit_warp(L, lane);
             if (L.st == ST_REEMITTED) {
-                K.md = &P.models[L.m];
+                K.bind(L);
                 K.finish_absorb(L);
             }
         }
     }
-    K.flush_warp(L.m);
+    K.flush_warp(Kernel<R, NS, FEAT>::SINGLE ? 0 : L.m);
     if (P.smem_sed) {
         __syncthreads();
         K.flush_sed(threadIdx.x, blockDim.x);
@@ -1239,6 +1264,7 @@ rt_status launch_one(rt_ctx* ctx, const TransportKP& kp, int schedule, int threa
         off += bytes;
         return o;
     };
+    k.so_claim = place(16 * (threads / 32 + 1), 16);
     k.so_ctr = place(sizeof(unsigned long long) * kLaneStats * (schedule == RT_SCHED_SERIAL ? 32 : threads), 16);
     k.so_sed = place(sizeof(double) * nsed, 16);
     k.so_op = place(sizeof(float4) * NS * kp.nf, 16);
@@ -1274,12 +1300,14 @@ rt_status launch_feat(rt_ctx* ctx, const TransportKP& kp, int schedule, int thre
     if constexpr (sizeof(R) == 8) {
         return launch_one<R, NS, 3>(ctx, kp, schedule, threads, blocks_per_sm, s);
     } else {
-        const int feat = (kp.mrw ? 1 : 0) | (kp.want_traj ? 2 : 0);
+        const int feat = (kp.mrw ? 1 : 0) | (kp.want_traj ? 2 : (kp.single ? 4 : 0));
         switch (feat) {
         case 0: return launch_one<R, NS, 0>(ctx, kp, schedule, threads, blocks_per_sm, s);
         case 1: return launch_one<R, NS, 1>(ctx, kp, schedule, threads, blocks_per_sm, s);
         case 2: return launch_one<R, NS, 2>(ctx, kp, schedule, threads, blocks_per_sm, s);
-        default: return launch_one<R, NS, 3>(ctx, kp, schedule, threads, blocks_per_sm, s);
+        case 3: return launch_one<R, NS, 3>(ctx, kp, schedule, threads, blocks_per_sm, s);
+        case 4: return launch_one<R, NS, 4>(ctx, kp, schedule, threads, blocks_per_sm, s);
+        default: return launch_one<R, NS, 5>(ctx, kp, schedule, threads, blocks_per_sm, s);
         }
     }
 }
