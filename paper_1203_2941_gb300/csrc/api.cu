@@ -188,7 +188,7 @@ void rt_opacity_free(rt_opacity* op)
     cudaSetDevice(op->ctx->device);
     cudaFree(op->d_nu); cudaFree(op->d_dnu); cudaFree(op->d_kabs); cudaFree(op->d_ksca);
     cudaFree(op->d_g); cudaFree(op->d_opac32); cudaFree(op->d_xh); cudaFree(op->d_wB);
-    cudaFree(op->d_wD); cudaFree(op->d_tinv); cudaFree(op->d_tz); cudaFree(op->d_mrwS);
+    cudaFree(op->d_wD); cudaFree(op->d_tinv); cudaFree(op->d_tz); cudaFree(op->d_tw); cudaFree(op->d_zinv); cudaFree(op->d_mrwS);
     delete op;
 }
 

@@ -27,10 +27,18 @@ constexpr int kMaxSpecies = 4;
 constexpr int kMaxFreq = 1024;
 constexpr int kTinvN = 4096;      // FP32 temperature-inverse table entries per species
 constexpr int kTz64N = 65536;     // FP64 table of ln(4 pi P(T)) and its slope on a ln T grid
+constexpr int kZinvN = 16384;     // FP32 table: ln T grid position on a uniform ln(4 pi P) grid
 constexpr int kMrwN = 2048;       // MRW survival table entries on y in [0, kMrwYmax]
 constexpr double kMrwYmax = 2.0;
 constexpr int kSedBins = 10;
 constexpr int kMaxImgFreq = 16;
+
+// Node j of the linear-space temperature table on the uniform ln T grid:
+// W = 4 pi P(T_j), m = dW/du (u = position within the interval, in units of
+// the grid step h), T = T_j, g = 1 / (d ln W / du).
+struct alignas(32) TwNode {
+    double W, m, T, g;
+};
 
 }  // namespace rtgb
 
@@ -62,6 +70,10 @@ struct rt_opacity {
     float* d_tinv;                         // [ns][kTinvN] log2 T on uniform log2(P) grid
     double2* d_tz;                         // [ns][kTz64N] {ln(4 pi P), d/dlnT} on uniform ln T
     double tz_lnT0, tz_dlnT;
+    rtgb::TwNode* d_tw;                    // [ns][kTz64N] linear-space nodes (same ln T grid)
+    float* d_zinv;                         // [ns][kZinvN] grid position (lnT - lnT0) / dlnT
+    float zinv_z0[rtgb::kMaxSpecies], zinv_idz[rtgb::kMaxSpecies];
+    int tw_ok[rtgb::kMaxSpecies];          // species has a finite, increasing table
     float tinv_y0[rtgb::kMaxSpecies], tinv_inv_dy[rtgb::kMaxSpecies];
     float* d_mrwS;                         // [kMrwN] survival S(y)
 };
@@ -159,6 +171,36 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
         k.y += 0xBB67AE85u;
     }
     return c;
+}
+
+// log2 of a positive double using only integer work and an FP32 log2 of the
+// top 23 mantissa bits (GB300 has little FP64 throughput)
+__device__ __forceinline__ float log2_d(double v)
+{
+    const unsigned hi = (unsigned)__double2hiint(v);
+    const unsigned lo = (unsigned)__double2loint(v);
+    const int e = (int)((hi >> 20) & 0x7ffu) - 1023;
+    const float m = __uint_as_float(0x3f800000u | ((hi & 0xfffffu) << 3) | (lo >> 29));
+    return (float)e + __log2f(m);
+}
+
+// Exact float -> double by re-biasing the exponent with integer operations
+// (no FP64 pipe); zero and denormal inputs give 0.
+__device__ __forceinline__ double f2d(float f)
+{
+    const unsigned b = __float_as_uint(f);
+    const unsigned e = (b >> 23) & 0xffu;
+    if (e == 0u) return 0.0;
+    const unsigned hi = (b & 0x80000000u) | ((e + (1023u - 127u)) << 20) | ((b & 0x7fffffu) >> 3);
+    return __hiloint2double((int)hi, (int)((b & 7u) << 29));
+}
+
+// Hardware reciprocal estimate of a double (a Newton step needs no more)
+__device__ __forceinline__ double rcp_approx(double x)
+{
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+    return r;
 }
 #endif
 

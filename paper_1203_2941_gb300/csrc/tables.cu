@@ -142,6 +142,8 @@ rt_status build_opacity_tables(rt_opacity* op)
     op->tz_lnT0 = lnTlo;
     op->tz_dlnT = (lnThi - lnTlo) / (kTz64N - 1);
     std::vector<float> tinv((size_t)ns * kTinvN);
+    std::vector<TwNode> tw((size_t)ns * kTz64N);
+    std::vector<float> zinv((size_t)ns * kZinvN);
     std::vector<double> lnTd(kTz64N), zd(kTz64N), inv;
     std::vector<double> x1(nf), lnc(nf);
     for (int j = 0; j < nf; ++j) x1[j] = kH * op->nu[j] / kK;
@@ -159,8 +161,16 @@ rt_status build_opacity_tables(rt_opacity* op)
             zd[i] = ln_emission(lnc, x1, exp(lnTd[i]), &sl);
             tz[(size_t)s * kTz64N + i] = make_double2(zd[i], sl);
             if (!std::isfinite(zd[i]) || (i > 0 && !(zd[i] > zd[i - 1]))) ok = false;
+            TwNode& n = tw[(size_t)s * kTz64N + i];
+            n.W = exp(zd[i]);                            // 0 where 4 pi P underflows
+            n.m = n.W * sl * op->tz_dlnT;
+            n.T = exp(lnTd[i]);
+            n.g = sl > 0.0 ? 1.0 / (sl * op->tz_dlnT) : 0.0;
         }
+        op->tw_ok[s] = ok ? 1 : 0;
         if (!ok) {
+            for (int i = 0; i < kZinvN; ++i) zinv[(size_t)s * kZinvN + i] = 0.0f;
+            op->zinv_z0[s] = 0.0f; op->zinv_idz[s] = 0.0f;
             // a species without absorption: temperatures stay at the table floor
             for (int i = 0; i < kTinvN; ++i) tinv[(size_t)s * kTinvN + i] = (float)(lnTlo / log(2.0));
             op->tinv_y0[s] = 0.0f; op->tinv_inv_dy[s] = 0.0f;
@@ -172,6 +182,14 @@ rt_status build_opacity_tables(rt_opacity* op)
         for (int i = 0; i < kTinvN; ++i) tinv[(size_t)s * kTinvN + i] = (float)(inv[i] / log(2.0));
         op->tinv_y0[s] = (float)(zlo / log(2.0));
         op->tinv_inv_dy[s] = (float)(1.0 / dy);
+        // grid position (lnT - lnT0) / h on a uniform z grid: the FP32 start
+        // of the FP64 temperature solve
+        const double dzi = (zhi - zlo) / (kZinvN - 1);
+        invert_dense(lnTd, zd, zlo, dzi, kZinvN, inv);
+        for (int i = 0; i < kZinvN; ++i)
+            zinv[(size_t)s * kZinvN + i] = (float)((inv[i] - lnTlo) / op->tz_dlnT);
+        op->zinv_z0[s] = (float)zlo;
+        op->zinv_idz[s] = (float)(1.0 / dzi);
     }
 
     std::vector<float> mrw(kMrwN);
@@ -188,6 +206,8 @@ rt_status build_opacity_tables(rt_opacity* op)
     RT_CUDA(cudaMalloc(&op->d_wD, sizeof(float) * sf));
     RT_CUDA(cudaMalloc(&op->d_tinv, sizeof(float) * tinv.size()));
     RT_CUDA(cudaMalloc(&op->d_tz, sizeof(double2) * tz.size()));
+    RT_CUDA(cudaMalloc(&op->d_tw, sizeof(TwNode) * tw.size()));
+    RT_CUDA(cudaMalloc(&op->d_zinv, sizeof(float) * zinv.size()));
     RT_CUDA(cudaMalloc(&op->d_mrwS, sizeof(float) * kMrwN));
     RT_CUDA(cudaMemcpy(op->d_nu, op->nu.data(), sizeof(double) * nf, cudaMemcpyHostToDevice));
     RT_CUDA(cudaMemcpy(op->d_dnu, op->dnu.data(), sizeof(double) * nf, cudaMemcpyHostToDevice));
@@ -200,6 +220,8 @@ rt_status build_opacity_tables(rt_opacity* op)
     RT_CUDA(cudaMemcpy(op->d_wD, wD.data(), sizeof(float) * sf, cudaMemcpyHostToDevice));
     RT_CUDA(cudaMemcpy(op->d_tinv, tinv.data(), sizeof(float) * tinv.size(), cudaMemcpyHostToDevice));
     RT_CUDA(cudaMemcpy(op->d_tz, tz.data(), sizeof(double2) * tz.size(), cudaMemcpyHostToDevice));
+    RT_CUDA(cudaMemcpy(op->d_tw, tw.data(), sizeof(TwNode) * tw.size(), cudaMemcpyHostToDevice));
+    RT_CUDA(cudaMemcpy(op->d_zinv, zinv.data(), sizeof(float) * zinv.size(), cudaMemcpyHostToDevice));
     RT_CUDA(cudaMemcpy(op->d_mrwS, mrw.data(), sizeof(float) * kMrwN, cudaMemcpyHostToDevice));
     return RT_OK;
 }

@@ -11,26 +11,24 @@ namespace {
 
 constexpr double kPi = 3.14159265358979323846;
 
-// One thread per (species, cell).  The left-hand side of Eq. 4 in log form,
-// z(T) = ln(4 pi sum_j kabs_j B_j(T) dnu_j), is tabulated exactly (value and
-// slope dz/dlnT, FP64) on a fine uniform ln T grid from 0.1 K to 1e6 K.  A cell
-// solves z(T) = ln(E / (rho V)) by binary search for the bracketing table
-// interval and Newton iterations on that interval's cubic Hermite interpolant,
-// whose error (h^4/384 times the fourth derivative, h = 2.5e-4) is below double
-// rounding.  Targets outside the table fall back to bisection on the Planck sum.
-__global__ void temperatures_kernel(const float* rho, const double* E, double* T, size_t nc, int ns,
-                                    double vol, const double2* tz, double lnT0, double dlnT, int nf,
-                                    const double* nu, const double* dnu, const double* kabs)
+struct TempKP {
+    const float* rho; const double* E; double* T;
+    size_t nc; int ns; double vol;
+    const double2* tz; const TwNode* tw; const float* zinv;
+    float zinv_z0[kMaxSpecies], zinv_idz[kMaxSpecies];
+    int tw_ok[kMaxSpecies];
+    double lnT0, dlnT;
+    int nf; const double* nu; const double* dnu; const double* kabs;
+};
+
+// z(T) = ln(4 pi sum_j kabs_j B_j(T) dnu_j) solved by binary search for the
+// bracketing table interval and Newton iterations on its cubic Hermite
+// interpolant; targets outside the table fall back to bisection on the
+// Planck sum.
+__device__ double solve_z(const TempKP& P, int s, double e, double rv)
 {
-    const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-    if (i >= nc * ns) return;
-    const int s = (int)(i / nc);
-    const double rv = (double)rho[i] * vol;
-    const double e = E[i];
-    if (!(rv > 0.0) || !(e > 0.0)) { T[i] = 0.0; return; }
-    const double target = e / rv;
-    const double z = log(target);
-    const double2* t = tz + (size_t)s * kTz64N;
+    const double z = log(e / rv);
+    const double2* t = P.tz + (size_t)s * kTz64N;
     if (z >= t[0].x && z <= t[kTz64N - 1].x) {
         int lo = 0, hi = kTz64N - 1;
         while (hi - lo > 1) {
@@ -38,7 +36,7 @@ __global__ void temperatures_kernel(const float* rho, const double* E, double* T
             if (t[mid].x <= z) lo = mid; else hi = mid;
         }
         const double2 a = t[lo], b = t[hi];
-        const double m0 = a.y * dlnT, m1 = b.y * dlnT;
+        const double m0 = a.y * P.dlnT, m1 = b.y * P.dlnT;
         double u = (b.x > a.x) ? (z - a.x) / (b.x - a.x) : 0.0;
         for (int it = 0; it < 6; ++it) {
             const double u2 = u * u, u3 = u2 * u;
@@ -49,17 +47,16 @@ __global__ void temperatures_kernel(const float* rho, const double* E, double* T
             if (!(dH > 0.0)) break;
             u = fmin(1.0, fmax(0.0, u - (H - z) / dH));
         }
-        T[i] = exp(lnT0 + ((double)lo + u) * dlnT);
-        return;
+        return exp(P.lnT0 + ((double)lo + u) * P.dlnT);
     }
-    // outside 0.1 K .. 1e6 K: bisection on 4 pi sum_j kabs B dnu = target
+    const double target = e / rv;
     const double h = 6.62607015e-27, kb = 1.380649e-16, c = 2.99792458e10;
     auto em4pi = [&](double Tc) {
-        double P = 0.0;
-        for (int j = 0; j < nf; ++j)
-            P += 4.0 * kPi * kabs[s * nf + j] * dnu[j] * 2.0 * h * nu[j] * nu[j] * nu[j] /
-                 (c * c) / expm1(h * nu[j] / (kb * Tc));
-        return P;
+        double Ps = 0.0;
+        for (int j = 0; j < P.nf; ++j)
+            Ps += 4.0 * kPi * P.kabs[s * P.nf + j] * P.dnu[j] * 2.0 * h * P.nu[j] * P.nu[j] * P.nu[j] /
+                  (c * c) / expm1(h * P.nu[j] / (kb * Tc));
+        return Ps;
     };
     double lo = 0.0, hi = 1.0e5;
     for (int it = 0; it < 64 && em4pi(hi) < target; ++it) hi *= 2.0;
@@ -67,7 +64,62 @@ __global__ void temperatures_kernel(const float* rho, const double* E, double* T
         const double mid = 0.5 * (lo + hi);
         if (em4pi(mid) < target) lo = mid; else hi = mid;
     }
-    T[i] = 0.5 * (lo + hi);
+    return 0.5 * (lo + hi);
+}
+
+// One thread per (species, cell): Eq. 4, 4 pi P(T) = E / (rho V).  GB300 has
+// little FP64 throughput, so the solve avoids FP64 logarithms, divisions and
+// searches.  An FP32 estimate of z = ln(E / (rho V)) (integer exponent split,
+// FP32 log2) indexes a uniform-z table that returns the position t on the
+// fine ln T grid.  Two Newton steps on the cubic Hermite interpolant of
+// W(u) = 4 pi P in linear space (interval j = floor t, u = t - j; W and dW/du
+// at the nodes are exact) solve W(u) rho V = E: the step is the relative
+// residual 1 - E / (W rho V) (hardware reciprocal estimate) times
+// 1 / (d ln W / du) at the node.  From a start within 0.02 of an interval the
+// second step leaves an error far below double rounding of ln T.  The
+// interpolant's own error, h^4/384 times the fourth derivative of W
+// (h = 2.5e-4), is about 1e-17 (d ln W / d ln T)^3 relative in T; nodes where
+// that slope exceeds 20 (the Wien side, T of order 1 K and below) take
+// solve_z, as do underflowing nodes and targets off the table.
+// T = T_j exp(u h) with a five-term series (u h < 2.5e-4).
+__global__ void temperatures_kernel(const __grid_constant__ TempKP P)
+{
+    const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i >= P.nc * P.ns) return;
+    const int s = (int)(i / P.nc);
+    const double rv = (double)P.rho[i] * P.vol;
+    const double e = P.E[i];
+    if (!(rv > 0.0) || !(e > 0.0)) { P.T[i] = 0.0; return; }
+    if (P.tw_ok[s]) {
+        const float z = (log2_d(e) - log2_d(rv)) * 0.693147180559945309f;
+        const float f = (z - P.zinv_z0[s]) * P.zinv_idz[s];
+        if (f >= 0.0f && f <= (float)(kZinvN - 1)) {
+            const float* zi = P.zinv + (size_t)s * kZinvN;
+            const int k = min((int)f, kZinvN - 2);
+            const float t = zi[k] + (f - (float)k) * (zi[k + 1] - zi[k]);
+            const int j = min(max((int)t, 0), kTz64N - 2);
+            const TwNode a = P.tw[(size_t)s * kTz64N + j];
+            const TwNode b = P.tw[(size_t)s * kTz64N + j + 1];
+            if (a.W > 0.0 && a.g * P.dlnT > 0.05) {
+                double u = f2d(t - (float)j);
+#pragma unroll
+                for (int it = 0; it < 2; ++it) {
+                    const double u2 = u * u, u3 = u2 * u;
+                    const double h01 = 3.0 * u2 - 2.0 * u3;
+                    const double W = (1.0 - h01) * a.W + (u3 - 2.0 * u2 + u) * a.m + h01 * b.W +
+                                     (u3 - u2) * b.m;
+                    const double p = W * rv;
+                    u -= (p - e) * rcp_approx(p) * a.g;
+                }
+                if (u > -0.5 && u < 1.5) {
+                    const double d = u * P.dlnT;
+                    P.T[i] = a.T * (1.0 + d * (1.0 + d * (0.5 + d * (1.0 / 6.0 + d * (1.0 / 24.0)))));
+                    return;
+                }
+            }
+        }
+    }
+    P.T[i] = solve_z(P, s, e, rv);
 }
 
 __global__ void guess_kernel(int nx, int ny, int nz, int ns, double bx, double by, double bz,
@@ -108,10 +160,19 @@ rt_status launch_temperatures(rt_ctx* ctx, const rt_grid* g, const rt_opacity* o
     (void)ctx;
     const size_t nc = g->ncell();
     const size_t n = nc * g->ns;
+    TempKP kp;
+    kp.rho = g->d_rho; kp.E = E; kp.T = T;
+    kp.nc = nc; kp.ns = g->ns; kp.vol = g->cell * g->cell * g->cell;
+    kp.tz = op->d_tz; kp.tw = op->d_tw; kp.zinv = op->d_zinv;
+    for (int q = 0; q < kMaxSpecies; ++q) {
+        kp.zinv_z0[q] = q < g->ns ? op->zinv_z0[q] : 0.0f;
+        kp.zinv_idz[q] = q < g->ns ? op->zinv_idz[q] : 0.0f;
+        kp.tw_ok[q] = q < g->ns ? op->tw_ok[q] : 0;
+    }
+    kp.lnT0 = op->tz_lnT0; kp.dlnT = op->tz_dlnT;
+    kp.nf = op->nf; kp.nu = op->d_nu; kp.dnu = op->d_dnu; kp.kabs = op->d_kabs;
     const int th = 256;
-    temperatures_kernel<<<(unsigned)((n + th - 1) / th), th, 0, s>>>(
-        g->d_rho, E, T, nc, g->ns, g->cell * g->cell * g->cell, op->d_tz, op->tz_lnT0, op->tz_dlnT,
-        op->nf, op->d_nu, op->d_dnu, op->d_kabs);
+    temperatures_kernel<<<(unsigned)((n + th - 1) / th), th, 0, s>>>(kp);
     count_launches();
     RT_CUDA(cudaGetLastError());
     return RT_OK;

@@ -246,28 +246,6 @@ __device__ __forceinline__ float mrw_y32(const float* S, float u)
     return ((float)lo + w) * (float)(kMrwYmax / (kMrwN - 1));
 }
 
-// log2 of a positive double using only integer work and an FP32 log2 of the
-// top 23 mantissa bits (GB300 has little FP64 throughput)
-__device__ __forceinline__ float log2_d(double v)
-{
-    const unsigned hi = (unsigned)__double2hiint(v);
-    const unsigned lo = (unsigned)__double2loint(v);
-    const int e = (int)((hi >> 20) & 0x7ffu) - 1023;
-    const float m = __uint_as_float(0x3f800000u | ((hi & 0xfffffu) << 3) | (lo >> 29));
-    return (float)e + __log2f(m);
-}
-
-// Exact float -> double by re-biasing the exponent with integer operations
-// (no FP64 pipe); zero and denormal inputs give 0.
-__device__ __forceinline__ double f2d(float f)
-{
-    const unsigned b = __float_as_uint(f);
-    const unsigned e = (b >> 23) & 0xffu;
-    if (e == 0u) return 0.0;
-    const unsigned hi = (b & 0x80000000u) | ((e + (1023u - 127u)) << 20) | ((b & 0x7fffffu) >> 3);
-    return __hiloint2double((int)hi, (int)((b & 7u) << 29));
-}
-
 // ------------------------------------------------------------- per-lane packet state
 // Registers decide occupancy for this latency-bound kernel, so the state is
 // kept lean: the cell is one linear index, and per flight each axis keeps its

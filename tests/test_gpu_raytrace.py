@@ -38,14 +38,27 @@ def test_temperatures_match_oracle(rt, ctx, O):
     for m in (W.r2_shell(n=12, nf=64), W.clumpy_torus(n=12, n_clump=30, nf=40, seed=2)):
         grid, opac = ctx.grid(m), ctx.opacity(m)
         rng = np.random.default_rng(1)
-        ref_scale = 4 * np.pi * np.array([O.planck_mean(m, s, 300.0) for s in range(m.ns)])
         rv = m.rho.reshape(m.ns, -1).astype(np.float64) * m.cell ** 3
-        E = rv * ref_scale[:, None] * np.exp(rng.uniform(-12, 12, size=rv.shape))
+        # temperatures log-uniform over 0.2 K .. 5e5 K (the whole fine table,
+        # including its steep Wien end); every 11th cell off the 0.1 K .. 1e6 K
+        # table (0.02 .. 0.1 K or 1e6 .. 1e10 K: bisection fallback); every 7th
+        # cell empty
+        Tset = np.exp(rng.uniform(np.log(0.2), np.log(5e5), size=rv.shape))
+        off = Tset[:, 3::11]
+        lowside = rng.random(off.shape) < 0.5
+        Tset[:, 3::11] = np.where(lowside, np.exp(rng.uniform(np.log(0.02), np.log(0.1), off.shape)),
+                                  np.exp(rng.uniform(np.log(1e6), np.log(1e10), off.shape)))
+        E = np.zeros_like(rv)
+        for s_ in range(m.ns):
+            for c in range(rv.shape[1]):
+                E[s_, c] = rv[s_, c] * 4 * np.pi * O.planck_mean(m, s_, Tset[s_, c])
         E[:, ::7] = 0.0
         T = rt.temperatures(ctx, grid, opac, torch.tensor(E, device="cuda"))
         torch.cuda.synchronize()
         Tr = O.temperatures(m, E)
         np.testing.assert_allclose(T.cpu().numpy(), Tr, rtol=1e-10, atol=0)
+        on = (E > 0) & (Tset > 0.1) & (Tset < 1e6)
+        np.testing.assert_allclose(T.cpu().numpy()[on], Tset[on], rtol=1e-9)
     # the optically thin starting guess
     m = W.r2_shell(n=10, nf=16)
     grid = ctx.grid(m)
