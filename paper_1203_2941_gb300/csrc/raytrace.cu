@@ -336,18 +336,21 @@ __global__ void __launch_bounds__(128) ray_bwd_kernel(const __grid_constant__ Ra
 
 // eta_th * cell (and bk = kabs_s B(T_s) * cell for the adjoint) for every
 // camera's table, in FP32: B = a_f / expm1(h nu_f / k T) with a_f = 2 h nu^3/c^2.
+// A thread owns one cell: its NFP values are contiguous, so every camera's
+// copy (and each species' bk row) is written as whole float4s.
 struct EtaKP {
     const void* rho;           // packed FP32 grid: rho_s * cell
     const double* T;           // [ns][nc]
     size_t nc;
-    int ns, nfi, nfp, ncam;
+    int ns, nfi, ncam;
+    float cell;
     float a[kMaxImgFreq], xh[kMaxImgFreq];
     float kabs[kMaxSpecies][kMaxImgFreq];
     float* eta;
     float* bk;
 };
 
-template <int NS>
+template <int NS, int NFP>
 __global__ void eta_thermal_kernel(const __grid_constant__ EtaKP P)
 {
     const size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
@@ -364,37 +367,52 @@ __global__ void eta_thermal_kernel(const __grid_constant__ EtaKP P)
             invT[s] = T > 0.0f ? 1.0f / T : 0.0f;
         }
     }
-    for (int f = 0; f < P.nfp; ++f) {
-        float e = 0.0f;
+    float e[NFP];
 #pragma unroll
-        for (int s = 0; s < NS; ++s) {
-            float b = 0.0f;
-            if (f < P.nfi && invT[s] > 0.0f) b = P.kabs[s][f] * P.a[f] / expm1f(P.xh[f] * invT[s]);
-            e += rho[s] * b;                                   // rho * cell * kabs * B
-            if (P.bk && s < P.ns) P.bk[((size_t)s * P.nc + c) * P.nfp + f] = b;   // times cell below
+    for (int f = 0; f < NFP; ++f) e[f] = 0.0f;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        float b[NFP];
+#pragma unroll
+        for (int f = 0; f < NFP; ++f) {
+            b[f] = 0.0f;
+            if (f < P.nfi && invT[s] > 0.0f) b[f] = P.kabs[s][f] * P.a[f] / expm1f(P.xh[f] * invT[s]);
+            e[f] += rho[s] * b[f];                             // rho * cell * kabs * B
         }
-        for (int k = 0; k < P.ncam; ++k) P.eta[((size_t)k * P.nc + c) * P.nfp + f] = e;
+        if (P.bk && s < P.ns) {
+            float4* q = reinterpret_cast<float4*>(P.bk + ((size_t)s * P.nc + c) * NFP);
+#pragma unroll
+            for (int v = 0; v < NFP / 4; ++v)
+                q[v] = make_float4(b[4 * v] * P.cell, b[4 * v + 1] * P.cell, b[4 * v + 2] * P.cell,
+                                   b[4 * v + 3] * P.cell);
+        }
     }
-}
-
-// bk was written as kabs B; scale it by the cell size
-__global__ void scale_kernel(float* v, size_t n, float a)
-{
-    const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-    if (i < n) v[i] *= a;
+    for (int k = 0; k < P.ncam; ++k) {
+        float4* q = reinterpret_cast<float4*>(P.eta + ((size_t)k * P.nc + c) * NFP);
+#pragma unroll
+        for (int v = 0; v < NFP / 4; ++v) q[v] = make_float4(e[4 * v], e[4 * v + 1], e[4 * v + 2], e[4 * v + 3]);
+    }
 }
 
 struct ScatKP {
     int ncam, nfi, nfp;
     size_t nc;
-    double inv_vol;
     const float* kobs;         // [ncam][3]
     const int* f_of_nu;        // [nf] image-frequency slot or -1
-    const double* g;           // [ns][nf]
-    const double* dnu;         // [nf]
+    const float2* ag;          // [ns][nf] {xi cell / (V dnu) (1 - g^2) / (4 pi), g}
     int nf, ns;
-    double xi;
 };
+
+// Henyey-Greenstein weight towards camera k, FP32: the denominator
+// 1 + g^2 - 2 g cos = (1 - g)^2 + 2 g (1 - cos) keeps its precision at
+// forward-peaked g and cos near 1.
+__device__ __forceinline__ float hg_toward(const rt_event& e, const float* ko, float2 ag)
+{
+    const float cb = e.k[0] * ko[0] + e.k[1] * ko[1] + e.k[2] * ko[2];
+    const float g = ag.y;
+    const float d = (1.0f - g) * (1.0f - g) + 2.0f * g * (1.0f - cb);
+    return ag.x / (d * sqrtf(d));
+}
 
 // eta_sca * cell: every stored event adds xi cell / (V dnu) P_HG(k_in . k_obs)
 __global__ void eta_scatter_kernel(const rt_event* ev, uint64_t nev, ScatKP P, float* eta)
@@ -405,15 +423,9 @@ __global__ void eta_scatter_kernel(const rt_event* ev, uint64_t nev, ScatKP P, f
     if (e.nu >= P.nf || e.species >= P.ns) return;
     const int f = P.f_of_nu[e.nu];
     if (f < 0 || (size_t)e.cell >= P.nc) return;
-    const double g = P.g[e.species * P.nf + e.nu];
-    const double amp = P.xi * P.inv_vol / P.dnu[e.nu];
-    for (int k = 0; k < P.ncam; ++k) {
-        const double cb = (double)e.k[0] * P.kobs[3 * k] + (double)e.k[1] * P.kobs[3 * k + 1] +
-                          (double)e.k[2] * P.kobs[3 * k + 2];
-        const double d = 1.0 + g * g - 2.0 * g * cb;
-        const double ph = (1.0 - g * g) / (4.0 * kPi * d * sqrt(d));
-        atomicAdd(&eta[((size_t)k * P.nc + e.cell) * P.nfp + f], (float)(amp * ph));
-    }
+    const float2 ag = P.ag[e.species * P.nf + e.nu];
+    for (int k = 0; k < P.ncam; ++k)
+        atomicAdd(&eta[((size_t)k * P.nc + e.cell) * P.nfp + f], hg_toward(e, P.kobs + 3 * k, ag));
 }
 
 // several image frequencies share one event frequency: handled by a second
@@ -428,34 +440,40 @@ __global__ void eta_scatter_dup_kernel(const rt_event* ev, uint64_t nev, ScatKP 
     for (int q = 0; q < ndup; ++q) {
         const int f = dup[2 * q], j = dup[2 * q + 1];
         if ((int)e.nu != j) continue;
-        const double g = P.g[e.species * P.nf + e.nu];
-        const double amp = P.xi * P.inv_vol / P.dnu[e.nu];
-        for (int k = 0; k < P.ncam; ++k) {
-            const double cb = (double)e.k[0] * P.kobs[3 * k] + (double)e.k[1] * P.kobs[3 * k + 1] +
-                              (double)e.k[2] * P.kobs[3 * k + 2];
-            const double d = 1.0 + g * g - 2.0 * g * cb;
-            const double ph = (1.0 - g * g) / (4.0 * kPi * d * sqrt(d));
-            atomicAdd(&eta[((size_t)k * P.nc + e.cell) * P.nfp + f], (float)(amp * ph));
-        }
+        const float2 ag = P.ag[e.species * P.nf + e.nu];
+        for (int k = 0; k < P.ncam; ++k)
+            atomicAdd(&eta[((size_t)k * P.nc + e.cell) * P.nfp + f], hg_toward(e, P.kobs + 3 * k, ag));
     }
 }
 
-// sed[cam][f] = A_pix / D^2 * sum_pix I  (one block per (cam, f), FP64)
-__global__ void sed_reduce_kernel(const float* img, int nfi, long long npix2, const double* apix_d2,
-                                  double* sed)
+// sed[cam][f] = A_pix / D^2 * sum_pix I  (one block of 1024 threads per
+// (cam, f), float4 loads when the image size allows, FP64 sums)
+__global__ void __launch_bounds__(1024) sed_reduce_kernel(const float* img, int nfi, long long npix2,
+                                                          const double* apix_d2, double* sed, int vec4)
 {
     const int cf = blockIdx.x;
     const float* p = img + (size_t)cf * npix2;
     double acc = 0.0;
-    for (long long i = threadIdx.x; i < npix2; i += blockDim.x) acc += (double)p[i];
-    __shared__ double red[256];
-    red[threadIdx.x] = acc;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-        __syncthreads();
+    if (vec4) {
+        const float4* q = reinterpret_cast<const float4*>(p);
+        for (long long i = threadIdx.x; i < npix2 / 4; i += blockDim.x) {
+            const float4 v = q[i];
+            acc += ((double)v.x + (double)v.y) + ((double)v.z + (double)v.w);
+        }
+    } else {
+        for (long long i = threadIdx.x; i < npix2; i += blockDim.x) acc += (double)p[i];
     }
-    if (threadIdx.x == 0) sed[cf] = red[0] * apix_d2[cf / nfi];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    __shared__ double red[32];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) sed[cf] = v * apix_d2[cf / nfi];
+    }
 }
 
 struct StarKP {
@@ -474,66 +492,83 @@ struct StarKP {
     float* grad;
 };
 
-// Direct light of each source along k_obs (FP64, one thread per (camera,
-// source, frequency)).  Forward adds L_nu exp(-tau) / (4 pi D^2) to the SED;
-// backward adds -dL/dF F kext_s l to the density gradient.
-__global__ void star_kernel(const __grid_constant__ StarKP P, int backward)
+// Direct light of each source along k_obs (FP64).  One warp per (camera,
+// source), one lane per image frequency: the lanes walk the same path (an
+// incremental DDA: per-axis face distances advanced by fixed steps, ties to
+// the lowest axis) and each adds its own frequency's optical depth, so the
+// FP64 work per cell visit is a handful of warp instructions.  Forward adds
+// L_nu exp(-tau) / (4 pi D^2) to the SED; backward walks the path again and
+// adds -sum_f dL/dF_f F_f kext_s,f l (a warp sum) to the density gradient.
+__global__ void __launch_bounds__(32) star_kernel(const __grid_constant__ StarKP P, int backward)
 {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= P.ncam * P.nsrc * P.nfi) return;
-    const int f = t % P.nfi, si = (t / P.nfi) % P.nsrc, cam = t / (P.nfi * P.nsrc);
+    const int t = blockIdx.x;
+    if (t >= P.ncam * P.nsrc) return;
+    const int si = t % P.nsrc, cam = t / P.nsrc;
+    const int f = threadIdx.x;
+    const bool act = f < P.nfi;
+    const int fc = act ? f : 0;
+    double ke[kMaxSpecies];
+#pragma unroll
+    for (int s = 0; s < kMaxSpecies; ++s) ke[s] = act ? P.kext[s][fc] : 0.0;
     const double d[3] = { P.kobs[3 * cam], P.kobs[3 * cam + 1], P.kobs[3 * cam + 2] };
     const int n[3] = { P.nx, P.ny, P.nz };
-    double tau = 0.0;
-    double F = 0.0, wsed = 0.0;
+    double tau = 0.0, coef = 0.0;
     for (int pass = 0; pass < (backward ? 2 : 1); ++pass) {
         if (pass == 1) {
-            F = P.lnu[si * P.nfi + f] * exp(-tau) * P.inv4piD2[cam];
-            wsed = P.dsed[cam * P.nfi + f];
-            if (wsed == 0.0 || F == 0.0) return;
+            if (act) {
+                const double F = P.lnu[si * P.nfi + fc] * exp(-tau) * P.inv4piD2[cam];
+                coef = -P.dsed[cam * P.nfi + fc] * F;
+            }
+            if (!__any_sync(0xffffffffu, coef != 0.0)) return;
         }
-        double x[3];
         int i[3];
+        double tm[3], td[3];
         bool in = true;
         for (int a = 0; a < 3; ++a) {
-            x[a] = P.pos_cell[3 * si + a];
-            const double fl = floor(x[a]);
+            const double x = P.pos_cell[3 * si + a];
+            const double fl = floor(x);
             int k = (int)fl;
-            if (fl == x[a] && d[a] < 0.0) k -= 1;
+            if (fl == x && d[a] < 0.0) k -= 1;
             i[a] = k;
             in = in && k >= 0 && k < n[a];
-        }
-        for (int steps = 0; in && steps < P.nx + P.ny + P.nz + 4; ++steps) {
-            double best = INFINITY;
-            int ba = 0;
-            for (int a = 0; a < 3; ++a) {
-                double tt;
-                if (d[a] > 0.0) tt = ((double)(i[a] + 1) - x[a]) / d[a];
-                else if (d[a] < 0.0) tt = ((double)i[a] - x[a]) / d[a];
-                else tt = INFINITY;
-                if (tt < 0.0) tt = 0.0;
-                if (tt < best) { best = tt; ba = a; }
+            if (d[a] > 0.0) {
+                td[a] = 1.0 / d[a];
+                tm[a] = fmax(((double)(k + 1) - x) * td[a], 0.0);
+            } else if (d[a] < 0.0) {
+                td[a] = -1.0 / d[a];
+                tm[a] = fmax((x - (double)k) * td[a], 0.0);
+            } else {
+                td[a] = INFINITY;
+                tm[a] = INFINITY;
             }
+        }
+        double tcur = 0.0;
+        for (int steps = 0; in && steps < P.nx + P.ny + P.nz + 4; ++steps) {
+            const int ba = (tm[0] <= tm[1] && tm[0] <= tm[2]) ? 0 : (tm[1] <= tm[2] ? 1 : 2);
+            const double tn = ba == 0 ? tm[0] : (ba == 1 ? tm[1] : tm[2]);
+            const double l = (tn - tcur) * P.cell;
             const size_t c = ((size_t)i[2] * P.ny + i[1]) * P.nx + i[0];
-            const double l = best * P.cell;
             if (pass == 0) {
                 double chi = 0.0;
-                for (int s = 0; s < P.ns; ++s) chi += (double)P.rho[s * P.nc + c] * P.kext[s][f];
+                for (int s = 0; s < P.ns; ++s) chi += (double)__ldg(&P.rho[s * P.nc + c]) * ke[s];
                 tau += chi * l;
             } else {
                 for (int s = 0; s < P.ns; ++s) {
-                    const double g = -wsed * F * P.kext[s][f] * l;
-                    if (g != 0.0) atomicAdd(&P.grad[s * P.nc + c], (float)g);
+                    double g = coef * ke[s];
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
+                    g *= l;
+                    if (f == 0 && g != 0.0) atomicAdd(&P.grad[s * P.nc + c], (float)g);
                 }
             }
-            for (int b = 0; b < 3; ++b) x[b] += best * d[b];
-            x[ba] = d[ba] > 0.0 ? (double)(i[ba] + 1) : (double)i[ba];
-            i[ba] += d[ba] > 0.0 ? 1 : -1;
-            in = i[ba] >= 0 && i[ba] < n[ba];
+            tcur = tn;
+            if (ba == 0) { tm[0] += td[0]; i[0] += d[0] > 0.0 ? 1 : -1; in = i[0] >= 0 && i[0] < n[0]; }
+            else if (ba == 1) { tm[1] += td[1]; i[1] += d[1] > 0.0 ? 1 : -1; in = i[1] >= 0 && i[1] < n[1]; }
+            else { tm[2] += td[2]; i[2] += d[2] > 0.0 ? 1 : -1; in = i[2] >= 0 && i[2] < n[2]; }
         }
     }
-    if (!backward)
-        atomicAdd(&P.sed[cam * P.nfi + f], P.lnu[si * P.nfi + f] * exp(-tau) * P.inv4piD2[cam]);
+    if (!backward && act)
+        atomicAdd(&P.sed[cam * P.nfi + fc], P.lnu[si * P.nfi + fc] * exp(-tau) * P.inv4piD2[cam]);
 }
 
 // grad_total += grad_call;  dscale += sum rho * grad_call
@@ -573,6 +608,17 @@ void launch_rays_nf(const RayKP& kp, int npix, bool backward, cudaStream_t s)
     case 8: launch_rays<NS, 8>(kp, npix, backward, s); break;
     case 12: launch_rays<NS, 12>(kp, npix, backward, s); break;
     default: launch_rays<NS, 16>(kp, npix, backward, s); break;
+    }
+}
+
+template <int NS>
+void launch_eta(const EtaKP& ek, int nfp, unsigned blocks, cudaStream_t s)
+{
+    switch (nfp) {
+    case 4: eta_thermal_kernel<NS, 4><<<blocks, 256, 0, s>>>(ek); break;
+    case 8: eta_thermal_kernel<NS, 8><<<blocks, 256, 0, s>>>(ek); break;
+    case 12: eta_thermal_kernel<NS, 12><<<blocks, 256, 0, s>>>(ek); break;
+    default: eta_thermal_kernel<NS, 16><<<blocks, 256, 0, s>>>(ek); break;
     }
 }
 
@@ -662,6 +708,16 @@ rt_status raytrace_impl(rt_ctx* ctx, const rt_grid* g, const rt_opacity* op, con
     const size_t o_i4 = take(sizeof(double) * ncam), o_ap = take(sizeof(double) * ncam);
     const size_t o_fn = take(sizeof(int) * op->nf), o_du = take(sizeof(int) * (dup.size() + 2));
     const size_t o_ln = take(sizeof(double) * lnu.size()), o_sp = take(sizeof(double) * spos.size());
+    // scattering emissivity per event (tables hold eta * cell): xi cell / (V dnu)
+    // times the Henyey-Greenstein numerator (1 - g^2) / (4 pi); g alongside
+    std::vector<float2> ag((size_t)ns * op->nf);
+    for (int sp = 0; sp < ns; ++sp)
+        for (int j = 0; j < op->nf; ++j) {
+            const double gg = op->g[sp * op->nf + j];
+            const double amp = xi_ev / (g->cell * g->cell) / op->dnu[j];
+            ag[(size_t)sp * op->nf + j] = make_float2((float)(amp * (1.0 - gg * gg) / (4.0 * kPi)), (float)gg);
+        }
+    const size_t o_ag = take(sizeof(float2) * ag.size());
     std::vector<unsigned char> h(off, 0);
     std::memcpy(&h[o_nu], nu_f.data(), sizeof(double) * nfi);
     std::memcpy(&h[o_ka], kabs_f.data(), sizeof(double) * ns * nfi);
@@ -673,6 +729,7 @@ rt_status raytrace_impl(rt_ctx* ctx, const rt_grid* g, const rt_opacity* op, con
     if (!dup.empty()) std::memcpy(&h[o_du], dup.data(), sizeof(int) * dup.size());
     std::memcpy(&h[o_ln], lnu.data(), sizeof(double) * lnu.size());
     std::memcpy(&h[o_sp], spos.data(), sizeof(double) * spos.size());
+    std::memcpy(&h[o_ag], ag.data(), sizeof(float2) * ag.size());
     char* dbuf = nullptr;
     RT_CUDA(cudaMallocAsync((void**)&dbuf, off, s));
     RT_CUDA(cudaMemcpyAsync(dbuf, h.data(), off, cudaMemcpyHostToDevice, s));
@@ -682,7 +739,8 @@ rt_status raytrace_impl(rt_ctx* ctx, const rt_grid* g, const rt_opacity* op, con
     {
         EtaKP ek;
         std::memset(&ek, 0, sizeof(ek));
-        ek.rho = g->d_packed; ek.T = T; ek.nc = nc; ek.ns = ns; ek.nfi = nfi; ek.nfp = nfp;
+        ek.rho = g->d_packed; ek.T = T; ek.nc = nc; ek.ns = ns; ek.nfi = nfi;
+        ek.cell = (float)g->cell;
         ek.ncam = ncam; ek.eta = ctx->d_eta; ek.bk = bk;
         const double hP = 6.62607015e-27, kB = 1.380649e-16, cl = 2.99792458e10;
         for (int f = 0; f < nfi; ++f) {
@@ -693,25 +751,19 @@ rt_status raytrace_impl(rt_ctx* ctx, const rt_grid* g, const rt_opacity* op, con
         }
         const unsigned blocks = (unsigned)((nc + 255) / 256);
         const int vec = ns == 1 ? 1 : (ns == 2 ? 2 : 4);
-        if (vec == 1) eta_thermal_kernel<1><<<blocks, 256, 0, s>>>(ek);
-        else if (vec == 2) eta_thermal_kernel<2><<<blocks, 256, 0, s>>>(ek);
-        else eta_thermal_kernel<4><<<blocks, 256, 0, s>>>(ek);
+        if (vec == 1) launch_eta<1>(ek, nfp, blocks, s);
+        else if (vec == 2) launch_eta<2>(ek, nfp, blocks, s);
+        else launch_eta<4>(ek, nfp, blocks, s);
         count_launches();
         RT_CUDA(cudaGetLastError());
-        if (bk) {
-            const size_t nb = (size_t)ns * nc * nfp;
-            scale_kernel<<<(unsigned)((nb + 255) / 256), 256, 0, s>>>(bk, nb, (float)g->cell);
-            count_launches();
-            RT_CUDA(cudaGetLastError());
-        }
     }
     if (nev > 0) {
         ScatKP sk;
         sk.ncam = ncam; sk.nfi = nfi; sk.nfp = nfp; sk.nc = nc;
-        sk.inv_vol = 1.0 / (g->cell * g->cell);   // eta * cell: xi cell / V
+        sk.ag = (const float2*)(dbuf + o_ag);
         sk.kobs = (const float*)(dbuf + o_ko);
         sk.f_of_nu = (const int*)(dbuf + o_fn);
-        sk.g = op->d_g; sk.dnu = op->d_dnu; sk.nf = op->nf; sk.ns = ns; sk.xi = xi_ev;
+        sk.nf = op->nf; sk.ns = ns;
         const unsigned blocks = (unsigned)((nev + 255) / 256);
         eta_scatter_kernel<<<blocks, 256, 0, s>>>(ev, nev, sk, ctx->d_eta);
         count_launches();
@@ -751,8 +803,10 @@ rt_status raytrace_impl(rt_ctx* ctx, const rt_grid* g, const rt_opacity* op, con
         RT_CUDA(cudaGetLastError());
     }
     if (!backward) {
-        sed_reduce_kernel<<<ncam * nfi, 256, 0, s>>>(images, nfi, (long long)npix * npix,
-                                                     (const double*)(dbuf + o_ap), sed);
+        const long long npix2 = (long long)npix * npix;
+        const int vec4 = (npix2 % 4 == 0) && (reinterpret_cast<uintptr_t>(images) % 16 == 0);
+        sed_reduce_kernel<<<ncam * nfi, 1024, 0, s>>>(images, nfi, npix2, (const double*)(dbuf + o_ap),
+                                                      sed, vec4);
         count_launches();
     }
     if (nsrc > 0 && (!backward || dsed)) {
@@ -769,8 +823,7 @@ rt_status raytrace_impl(rt_ctx* ctx, const rt_grid* g, const rt_opacity* op, con
         sp.inv4piD2 = (const double*)(dbuf + o_i4);
         sp.nsrc = nsrc; sp.ncam = ncam;
         sp.sed = sed; sp.dsed = dsed; sp.grad = gcall;
-        const int nt = ncam * nsrc * nfi;
-        star_kernel<<<(nt + 63) / 64, 64, 0, s>>>(sp, backward ? 1 : 0);
+        star_kernel<<<ncam * nsrc, 32, 0, s>>>(sp, backward ? 1 : 0);
         count_launches();
         RT_CUDA(cudaGetLastError());
     }

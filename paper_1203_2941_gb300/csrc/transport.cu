@@ -100,8 +100,6 @@ template <> __device__ __forceinline__ double rng_u<double>(Rng& r, uint32_t kx)
 // ------------------------------------------------------------- math shims
 __device__ __forceinline__ float r_log(float x) { return logf(x); }
 __device__ __forceinline__ double r_log(double x) { return log(x); }
-__device__ __forceinline__ float r_exp(float x) { return expf(x); }
-__device__ __forceinline__ double r_exp(double x) { return exp(x); }
 __device__ __forceinline__ float r_expm1(float x) { return expm1f(x); }
 __device__ __forceinline__ double r_expm1(double x) { return expm1(x); }
 __device__ __forceinline__ float r_sqrt(float x) { return sqrtf(x); }
