@@ -140,7 +140,7 @@ typedef struct {
     int threads_per_block;    /* 0 = library default */
     int blocks_per_sm;        /* 0 = occupancy-derived */
     int march_min_active;     /* lanes still marching below which a warp serves its
-                                 pending interactions (0..31; -1 = default) */
+                                 pending interactions (0..31; -1 = default, 16) */
 } rt_transport_params;
 
 /* Fill p with the defaults: B&W, Lucy THIN at 1e-2, linear form, MRW off

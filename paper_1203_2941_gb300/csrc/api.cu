@@ -405,7 +405,7 @@ static void fill_kp(TransportKP& kp, const rt_opacity* op, const rt_transport_pa
     kp.pah_mask = 0;
     for (int s = 0; s < op->ns; ++s)
         if (op->is_pah[s]) kp.pah_mask |= 1 << s;
-    kp.march_min_active = p->march_min_active < 0 ? 8 : p->march_min_active;
+    kp.march_min_active = p->march_min_active < 0 ? 16 : p->march_min_active;
     kp.want_traj = 0;
     kp.single = 0;
     kp.rho0 = nullptr;

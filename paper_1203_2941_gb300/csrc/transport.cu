@@ -7,9 +7,10 @@
 //            packet, frequency bin from the source CDF, isotropic direction)
 //   flight   lanes at a new flight origin either take a modified-random-walk
 //            step (Sect. 3.2) or draw tau = -ln(u) and set up the traversal
-//   march    all marching lanes cross cells together (Eq. 2 test against the
-//            remaining tau, Lucy deposits in thin cells, Sect. 3.1) until at
-//            most `march_min_active` lanes are still marching
+//   march    all marching lanes cross cells together, one crossing per warp
+//            vote (Eq. 2 test against the remaining tau, Lucy deposits in
+//            thin cells, Sect. 3.1) until at most `march_min_active` lanes
+//            are still marching
 //   events   lanes that stopped inside a cell interact (albedo choice, HG
 //            scattering Eq. 15, absorption with B&W Eq. 4 + Eq. 10 or frozen-T
 //            Eq. 5 re-emission); lanes that left the grid tally the escape.
@@ -1144,7 +1145,6 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : RT_TRANSPORT_MIN_BLO
             if (L.st == ST_MARCH) {
                 K.bind(L);
                 K.march(L);
-                if (L.st == ST_MARCH) K.march(L);
             }
             nm = __popc(__ballot_sync(FULL, L.st == ST_MARCH));
         } while (nm > min_active);
