@@ -28,6 +28,7 @@ constexpr int kMaxFreq = 1024;
 constexpr int kTinvN = 4096;      // FP32 temperature-inverse table entries per species
 constexpr int kTz64N = 65536;     // FP64 table of ln(4 pi P(T)) and its slope on a ln T grid
 constexpr int kZinvN = 16384;     // FP32 table: ln T grid position on a uniform ln(4 pi P) grid
+constexpr int kReT = 4096;        // FP32 re-emission CDF rows on a uniform log2 T grid, 0.1 K .. 1e6 K
 constexpr int kMrwN = 2048;       // MRW survival table entries on y in [0, kMrwYmax]
 constexpr double kMrwYmax = 2.0;
 constexpr int kSedBins = 10;
@@ -64,9 +65,9 @@ struct rt_opacity {
     double* d_nu; double* d_dnu;           // [nf]
     double* d_kabs; double* d_ksca; double* d_g;  // [ns][nf]
     float4* d_opac32;                      // [ns][nf] {kext, kabs, ksca, g}
-    float* d_xh;                           // [nf] h nu / k  (K)
-    float* d_wB;                           // [ns][nf] kabs dnu (nu/nu_max)^3 / max
-    float* d_wD;                           // [ns][nf] kabs dnu (nu/nu_max)^4 / max
+    float* d_recdf;                        // [2][ns][kReT][nf] normalised re-emission CDFs:
+                                           // [0] Eq. 5 (kabs B dnu), [1] Eq. 10 (kabs dB/dT dnu)
+    float re_lg0, re_inv_dlg;              // row k at log2 T = re_lg0 + k / re_inv_dlg
     float* d_tinv;                         // [ns][kTinvN] log2 T on uniform log2(P) grid
     double2* d_tz;                         // [ns][kTz64N] {ln(4 pi P), d/dlnT} on uniform ln T
     double tz_lnT0, tz_dlnT;
@@ -140,14 +141,14 @@ struct TransportKP {
     int smem_sed;                       // single-model persistent launch: SED tallied per block
     int smem_cdf;                       // floats of model 0's source CDFs kept in shared memory
     // dynamic shared-memory layout (byte offsets, set by the launcher)
-    int so_sed, so_cnt, so_op, so_xh, so_w, so_mrw, so_cdf, so_ctr, so_claim;
+    int so_sed, so_cnt, so_op, so_mrw, so_cdf, so_ctr, so_claim;
     unsigned long long max_events;
     uint64_t seed;
     double mrw_tau_cell, mrw_gamma;
     // opacity tables
     const float4* opac32;
-    const float* xh;
-    const float* wre;                   // wB (frozen T) or wD (B&W)
+    const float* recdf;                 // [ns][kReT][nf] re-emission CDFs of the call's mode
+    float re_lg0, re_inv_dlg;
     const float* tinv;
     float tinv_y0[kMaxSpecies], tinv_inv_dy[kMaxSpecies];
     const float* mrwS;

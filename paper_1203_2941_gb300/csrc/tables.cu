@@ -113,26 +113,53 @@ rt_status build_opacity_tables(rt_opacity* op)
     const int nf = op->nf, ns = op->ns;
     const size_t sf = (size_t)ns * nf;
     std::vector<float4> o32(sf);
-    std::vector<float> xh(nf), wB(sf), wD(sf);
-    double numax = op->nu[nf - 1];
-    for (int j = 0; j < nf; ++j) xh[j] = (float)(kH * op->nu[j] / kK);
-    for (int s = 0; s < ns; ++s) {
-        double mb = 0.0, md = 0.0;
-        std::vector<double> b(nf), d(nf);
-        for (int j = 0; j < nf; ++j) {
-            const double r = op->nu[j] / numax;
-            b[j] = op->kabs[s * nf + j] * op->dnu[j] * r * r * r;
-            d[j] = b[j] * r;
-            mb = std::max(mb, b[j]);
-            md = std::max(md, d[j]);
-        }
+    for (int s = 0; s < ns; ++s)
         for (int j = 0; j < nf; ++j) {
             const double ka = op->kabs[s * nf + j], ks = op->ksca[s * nf + j];
-            o32[s * nf + j] = make_float4((float)(ka + ks), (float)ka, (float)ks,
-                                          (float)op->g[s * nf + j]);
-            wB[s * nf + j] = mb > 0.0 ? (float)(b[j] / mb) : 0.0f;
-            wD[s * nf + j] = md > 0.0 ? (float)(d[j] / md) : 0.0f;
+            o32[s * nf + j] = make_float4((float)(ka + ks), (float)ka, (float)ks, (float)op->g[s * nf + j]);
         }
+
+    // Re-emission CDFs for the FP32 transport: for each species and each
+    // temperature of a uniform log2 T grid (0.1 K .. 1e6 K), the normalised
+    // cumulative sum over bins of kabs B(T) dnu (Eq. 5) and kabs dB/dT dnu
+    // (Eq. 10), built in log form in FP64 (no underflow at 0.1 K).
+    const double lg_lo = log2(0.1), lg_hi = log2(1.0e6);
+    const double dlg = (lg_hi - lg_lo) / (kReT - 1);
+    op->re_lg0 = (float)lg_lo;
+    op->re_inv_dlg = (float)(1.0 / dlg);
+    std::vector<float> recdf((size_t)2 * ns * kReT * nf);
+    {
+        std::vector<double> lw(nf);
+        for (int mode = 0; mode < 2; ++mode)
+            for (int s = 0; s < ns; ++s)
+                for (int k = 0; k < kReT; ++k) {
+                    const double T = exp2(lg_lo + k * dlg);
+                    double mx = -INFINITY;
+                    for (int j = 0; j < nf; ++j) {
+                        const double ka = op->kabs[s * nf + j];
+                        const double x = kH * op->nu[j] / (kK * T);
+                        const double l1m = log(-expm1(-x));          // ln(1 - e^-x)
+                        double v = ka > 0.0 ? log(ka) + log(op->dnu[j]) + 3.0 * log(op->nu[j]) - x - l1m
+                                            : -INFINITY;
+                        if (mode == 1 && ka > 0.0) v += log(op->nu[j]) - l1m;   // dB/dT: one more nu / (1 - e^-x)
+                        lw[j] = v;
+                        mx = std::max(mx, v);
+                    }
+                    float* row = &recdf[(((size_t)mode * ns + s) * kReT + k) * nf];
+                    double acc = 0.0;
+                    for (int j = 0; j < nf; ++j) {
+                        acc += std::isfinite(mx) && std::isfinite(lw[j]) ? exp(lw[j] - mx) : 0.0;
+                        lw[j] = acc;
+                    }
+                    float prev = 0.0f;
+                    for (int j = 0; j < nf; ++j) {
+                        float c = acc > 0.0 ? (float)(lw[j] / acc) : (float)(j + 1) / nf;
+                        c = std::max(c, prev);
+                        row[j] = c;
+                        prev = c;
+                    }
+                    row[nf - 1] = 1.0f;
+                }
     }
 
     // exact tabulation of z = ln(4 pi P(T)) and dz/dlnT on a uniform ln T grid
@@ -201,9 +228,7 @@ rt_status build_opacity_tables(rt_opacity* op)
     RT_CUDA(cudaMalloc(&op->d_ksca, sizeof(double) * sf));
     RT_CUDA(cudaMalloc(&op->d_g, sizeof(double) * sf));
     RT_CUDA(cudaMalloc(&op->d_opac32, sizeof(float4) * sf));
-    RT_CUDA(cudaMalloc(&op->d_xh, sizeof(float) * nf));
-    RT_CUDA(cudaMalloc(&op->d_wB, sizeof(float) * sf));
-    RT_CUDA(cudaMalloc(&op->d_wD, sizeof(float) * sf));
+    RT_CUDA(cudaMalloc(&op->d_recdf, sizeof(float) * recdf.size()));
     RT_CUDA(cudaMalloc(&op->d_tinv, sizeof(float) * tinv.size()));
     RT_CUDA(cudaMalloc(&op->d_tz, sizeof(double2) * tz.size()));
     RT_CUDA(cudaMalloc(&op->d_tw, sizeof(TwNode) * tw.size()));
@@ -215,9 +240,7 @@ rt_status build_opacity_tables(rt_opacity* op)
     RT_CUDA(cudaMemcpy(op->d_ksca, op->ksca.data(), sizeof(double) * sf, cudaMemcpyHostToDevice));
     RT_CUDA(cudaMemcpy(op->d_g, op->g.data(), sizeof(double) * sf, cudaMemcpyHostToDevice));
     RT_CUDA(cudaMemcpy(op->d_opac32, o32.data(), sizeof(float4) * sf, cudaMemcpyHostToDevice));
-    RT_CUDA(cudaMemcpy(op->d_xh, xh.data(), sizeof(float) * nf, cudaMemcpyHostToDevice));
-    RT_CUDA(cudaMemcpy(op->d_wB, wB.data(), sizeof(float) * sf, cudaMemcpyHostToDevice));
-    RT_CUDA(cudaMemcpy(op->d_wD, wD.data(), sizeof(float) * sf, cudaMemcpyHostToDevice));
+    RT_CUDA(cudaMemcpy(op->d_recdf, recdf.data(), sizeof(float) * recdf.size(), cudaMemcpyHostToDevice));
     RT_CUDA(cudaMemcpy(op->d_tinv, tinv.data(), sizeof(float) * tinv.size(), cudaMemcpyHostToDevice));
     RT_CUDA(cudaMemcpy(op->d_tz, tz.data(), sizeof(double2) * tz.size(), cudaMemcpyHostToDevice));
     RT_CUDA(cudaMemcpy(op->d_tw, tw.data(), sizeof(TwNode) * tw.size(), cudaMemcpyHostToDevice));

@@ -37,8 +37,7 @@ namespace rtgb {
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
-enum { ST_NEED = 0, ST_FLIGHT = 1, ST_MARCH = 2, ST_INTERACT = 3, ST_ESCAPE = 4, ST_DONE = 5,
-       ST_REEMIT = 6, ST_REEMITTED = 7 };
+enum { ST_NEED = 0, ST_FLIGHT = 1, ST_MARCH = 2, ST_INTERACT = 3, ST_ESCAPE = 4, ST_DONE = 5 };
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kLaneStats = RT_STAT_EMITTED + 1;   // stats counted per thread (the rest are cursors)
 
@@ -258,9 +257,7 @@ struct Lane {
     R x[3], k[3];              // flight origin (cell units) and direction
     int c;                     // linear cell index
     int rem[3], dc[3];         // per axis: steps left inside the grid, signed stride
-    int j;                     // frequency index; in ST_REEMIT the species of the
-                               // pending re-emission (its temperature and uniform
-                               // ride in tau and tcur)
+    int j;                     // frequency index
     R tau, tcur;
     R tm[3], td[3];
     R rho[NS];                 // current cell (FP32: rho*cell; FP64: rho)
@@ -326,8 +323,6 @@ struct Kernel {
 
     // shared-memory tables (offsets set by the host launcher)
     __device__ __forceinline__ const float4* s_op() const { return reinterpret_cast<const float4*>(smem_raw() + P.so_op); }
-    __device__ __forceinline__ const float* s_xh() const { return reinterpret_cast<const float*>(smem_raw() + P.so_xh); }
-    __device__ __forceinline__ const float* s_w() const { return reinterpret_cast<const float*>(smem_raw() + P.so_w); }
     __device__ __forceinline__ const float* s_mrw() const { return reinterpret_cast<const float*>(smem_raw() + P.so_mrw); }
     __device__ __forceinline__ const float* s_cdf() const { return reinterpret_cast<const float*>(smem_raw() + P.so_cdf); }
     __device__ __forceinline__ double* s_sed() const { return reinterpret_cast<double*>(smem_raw() + P.so_sed); }
@@ -559,44 +554,47 @@ struct Kernel {
         }
     }
 
-    // Temperature of species s in cell c from the accumulated energy (Eq. 4)
-    __device__ __forceinline__ R temperature(const Lane<R, NS>& L, int s, double E)
+    // Temperature of species s in cell c from the accumulated energy (Eq. 4),
+    // FP64 build
+    __device__ __forceinline__ double temperature64(const Lane<R, NS>& L, int s, double E)
     {
-        if constexpr (DBG) {
-            const double rv = sel(L.rho, s) * md->vol;
-            return rv > 0.0 ? solve_T64(P, s, E / rv) : 0.0;
-        } else {
+        const double rv = sel(L.rho, s) * md->vol;
+        return rv > 0.0 ? solve_T64(P, s, E / rv) : 0.0;
+    }
+
+    // FP32 build: log2 of the temperature that sets the re-emission spectrum,
+    // Eq. 4 at the updated energy (B&W; FP32 inverse table of 4 pi P) or the
+    // previous iteration's value (frozen T); -inf when there is none
+    __device__ __forceinline__ float emission_log2T(const Lane<R, NS>& L, int s, double E)
+    {
+        if (P.mode == RT_MODE_BW) {
             const float rs = sel(L.rho, s);
-            if (!(E > 0.0) || !(rs > 0.0f)) return 0.0f;
+            if (!(E > 0.0) || !(rs > 0.0f)) return -INFINITY;
             const float y = log2_d(E) - __log2f(rs) - (float)md->log2_4piV;
             float f = (y - P.tinv_y0[s]) * P.tinv_inv_dy[s];
             f = fminf(fmaxf(f, 0.0f), (float)(kTinvN - 1));
             const int i = min((int)f, kTinvN - 2);
             const float w = f - (float)i;
             const float* t = P.tinv + (size_t)s * kTinvN;
-            return exp2f(t[i] + w * (t[i + 1] - t[i]));
+            return t[i] + w * (t[i + 1] - t[i]);
         }
+        const double T = md->T_prev[(size_t)s * md->ncell + L.c];
+        return T > 0.0 ? log2_d(T) : -INFINITY;
     }
 
-    // Temperature that sets the re-emission spectrum: Eq. 4 at the updated
-    // energy (B&W) or the previous iteration's value (frozen T)
-    __device__ __forceinline__ R emission_T(const Lane<R, NS>& L, int s, double E)
+    // Re-emission frequency bin: Eq. 10 (B&W, dB/dT weights) or Eq. 5 (frozen
+    // T).  FP64 build: the exact cumulative sum over bins.  FP32 build: the
+    // normalised CDF tabulated on a uniform log2 T grid; between the two
+    // bracketing rows the upper one is taken with probability equal to the
+    // interpolation weight (a draw from the linearly interpolated spectrum),
+    // then a binary search finds the smallest bin whose CDF reaches u.
+    __device__ __forceinline__ int reemit(Lane<R, NS>& L, int s, double E, R u)
     {
-        if (P.mode == RT_MODE_BW) return temperature(L, s, E);
-        return (R)md->T_prev[(size_t)s * md->ncell + L.c];
-    }
-
-    __device__ __forceinline__ int reemit(const Lane<R, NS>& L, int s, double E, R u)
-    {
-        return reemit_T(s, emission_T(L, s, E), u);
-    }
-
-    // Re-emission frequency: Eq. 10 (B&W, dB/dT weights) or Eq. 5 (frozen T)
-    __device__ __forceinline__ int reemit_T(int s, R T, R u)
-    {
-        const bool bw = P.mode == RT_MODE_BW;
-        const int nf = P.nf;
         if constexpr (DBG) {
+            const double T = P.mode == RT_MODE_BW ? temperature64(L, s, E)
+                                                  : md->T_prev[(size_t)s * md->ncell + L.c];
+            const bool bw = P.mode == RT_MODE_BW;
+            const int nf = P.nf;
             double tot = 0.0;
             for (int l = 0; l < nf; ++l) {
                 const double b = bw ? planck_dBdT(P.nu[l], T) : planck_B(P.nu[l], T);
@@ -611,80 +609,20 @@ struct Kernel {
             }
             return nf - 1;
         } else {
-            if (!(T > 0.0f)) return 0;
-            const float invT = 1.0f / T;
-            const float* w = s_w() + s * nf;
-            const float* xh = s_xh();
-            float tot = 0.0f;
-            for (int l = 0; l < nf; ++l) tot += w[l] * weight(xh[l] * invT, bw);
-            const float target = u * tot;
-            float acc = 0.0f;
-            for (int l = 0; l < nf; ++l) {
-                acc += w[l] * weight(xh[l] * invT, bw);
-                if (acc >= target) return l;
+            const float lg = emission_log2T(L, s, E);
+            const float u_row = U(L);
+            if (!(lg > -1.0e30f)) return 0;
+            float f = (lg - P.re_lg0) * P.re_inv_dlg;
+            f = fminf(fmaxf(f, 0.0f), (float)(kReT - 1));
+            int k = min((int)f, kReT - 2);
+            if (u_row < f - (float)k) ++k;
+            const float* cdf = P.recdf + ((size_t)s * kReT + k) * P.nf;
+            int lo = 0, hi = P.nf - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (__ldg(cdf + mid) >= u) hi = mid; else lo = mid + 1;
             }
-            return nf - 1;
-        }
-    }
-
-    // B: 1/(e^x - 1);  dB/dT (up to a factor): e^-x / (1 - e^-x)^2
-    __device__ __forceinline__ float weight(float x, bool bw)
-    {
-        const float em = __expf(-x);
-        const float om = x < 0.05f ? x * (1.0f - x * (0.5f - x * (1.0f / 6.0f))) : 1.0f - em;
-        return bw ? __fdividef(em, om * om) : __fdividef(em, om);
-    }
-
-    // Re-emission bins for every lane waiting in ST_REEMIT, served one lane at
-    // a time by the whole warp: each lane weighs a slice of the frequency bins
-    // (Eq. 10 or Eq. 5 weights at that lane's temperature), a warp sum gives
-    // the total, and a chunked inclusive warp scan with a ballot finds the
-    // smallest bin whose running sum reaches u times the total.  All 32 lanes
-    // must call this (FP32 build, persistent schedule).
-    __device__ __forceinline__ void reemit_warp(Lane<R, NS>& L, int lane)
-    {
-        unsigned m = __ballot_sync(FULL, L.st == ST_REEMIT);
-        const bool bw = P.mode == RT_MODE_BW;
-        const int nf = P.nf;
-        while (m) {
-            const int src = __ffs(m) - 1;
-            const float T = __shfl_sync(FULL, (float)L.tau, src);
-            const float u = __shfl_sync(FULL, (float)L.tcur, src);
-            const int s = __shfl_sync(FULL, L.j, src);
-            int bin = 0;
-            if (T > 0.0f) {
-                const float invT = 1.0f / T;
-                const float* w = s_w() + s * nf;
-                const float* xh = s_xh();
-                float tot = 0.0f;
-                for (int b = lane; b < nf; b += 32) tot += w[b] * weight(xh[b] * invT, bw);
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(FULL, tot, o);
-                const float target = u * tot;
-                float carry = 0.0f;
-                bin = nf - 1;
-                for (int b0 = 0; b0 < nf; b0 += 32) {
-                    const int b = b0 + lane;
-                    float v = b < nf ? w[b] * weight(xh[b] * invT, bw) : 0.0f;
-#pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const float t = __shfl_up_sync(FULL, v, o);
-                        if (lane >= o) v += t;
-                    }
-                    v += carry;
-                    const unsigned hit = __ballot_sync(FULL, b < nf && v >= target);
-                    if (hit) {
-                        bin = b0 + __ffs(hit) - 1;
-                        break;
-                    }
-                    carry = __shfl_sync(FULL, v, 31);
-                }
-            }
-            if (lane == src) {
-                L.j = bin;
-                L.st = ST_REEMITTED;
-            }
-            m &= m - 1;
+            return lo;
         }
     }
 
@@ -875,8 +813,7 @@ struct Kernel {
         }
     }
 
-    // coop: defer the re-emission CDF to reemit_warp (FP32, persistent)
-    __device__ __forceinline__ void interact(Lane<R, NS>& L, bool coop = false)
+    __device__ __forceinline__ void interact(Lane<R, NS>& L)
     {
         if (++L.nev > P.max_events) {
             count(RT_STAT_STUCK, 1);
@@ -970,13 +907,6 @@ struct Kernel {
             return;
         }
         const R u = U(L);
-        if (coop) {
-            L.tau = emission_T(L, s, E);
-            L.tcur = u;
-            L.j = s;
-            L.st = ST_REEMIT;
-            return;
-        }
         L.j = reemit(L, s, E, u);
         finish_absorb(L);
     }
@@ -1050,13 +980,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : RT_TRANSPORT_MIN_BLO
     unsigned char* sm = smem_raw();
     {
         float4* s_op = reinterpret_cast<float4*>(sm + P.so_op);
-        float* s_xh = reinterpret_cast<float*>(sm + P.so_xh);
-        float* s_w = reinterpret_cast<float*>(sm + P.so_w);
-        for (int i = threadIdx.x; i < NS * P.nf; i += blockDim.x) {
-            s_op[i] = P.opac32[i];
-            s_w[i] = P.wre[i];
-        }
-        for (int i = threadIdx.x; i < P.nf; i += blockDim.x) s_xh[i] = P.xh[i];
+        for (int i = threadIdx.x; i < NS * P.nf; i += blockDim.x) s_op[i] = P.opac32[i];
         if ((FEAT & 1) && P.mrw) {
             float* s_mrw = reinterpret_cast<float*>(sm + P.so_mrw);
             for (int i = threadIdx.x; i < kMrwN; i += blockDim.x) s_mrw[i] = P.mrwS[i];
@@ -1148,20 +1072,12 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : RT_TRANSPORT_MIN_BLO
             }
             nm = __popc(__ballot_sync(FULL, L.st == ST_MARCH));
         } while (nm > min_active);
-        constexpr bool COOP = sizeof(R) == 4;
         if (L.st == ST_INTERACT) {
             K.bind(L);
-            K.interact(L, COOP);
+            K.interact(L);
         } else if (L.st == ST_ESCAPE) {
             K.bind(L);
             K.escape(L);
-        }
-        if constexpr (COOP) {
-            K.reemit_warp(L, lane);
-            if (L.st == ST_REEMITTED) {
-                K.bind(L);
-                K.finish_absorb(L);
-            }
         }
     }
     K.flush_warp(Kernel<R, NS, FEAT>::SINGLE ? 0 : L.m);
@@ -1245,8 +1161,6 @@ rt_status launch_one(rt_ctx* ctx, const TransportKP& kp, int schedule, int threa
     k.so_sed = place(sizeof(double) * nsed, 16);
     k.so_op = place(sizeof(float4) * NS * kp.nf, 16);
     k.so_cnt = place(sizeof(unsigned) * nsed, 16);
-    k.so_xh = place(sizeof(float) * kp.nf, 16);
-    k.so_w = place(sizeof(float) * NS * kp.nf, 16);
     k.so_mrw = place((FEAT & 1) && kp.mrw ? sizeof(float) * kMrwN : 0, 16);
     k.so_cdf = place(sizeof(float) * kp.smem_cdf, 16);
     const size_t smem = (off + 15) / 16 * 16;
