@@ -292,7 +292,11 @@ typedef struct {
  * eta_sca = xi_ev / (V dnu) sum_events P_HG(k_in . k_obs; g) (Eq. 16).
  * sed[c][f] = sum_pix I A_pix / D^2 (Eq. 17) + sum_src L_nu exp(-tau_src) / (4 pi D^2).
  *   T: device [n_species][ncell] double;  events: device [n_events] (may be
- *   NULL if n_events == 0);  xi_ev: power carried by one event (= L/N of the
+ *   NULL if n_events == 0);  n_events_dev: device uint64 or NULL; when given,
+ *   the number of events used is min(*n_events_dev, n_events), read on the
+ *   device, so n_events is the buffer's capacity and the call needs no host
+ *   copy of a count that the transport writes (stats[RT_STAT_N_EVENTS]);
+ *   xi_ev: power carried by one event (= L/N of the
  *   transport that stored them);  cams: host [n_cams], all with the same npix;
  *   freq_idx: host [n_f] indices into the opacity grid, n_f in 1..16;
  *   images: device [n_cams][n_f][npix][npix] float;  sed: device [n_cams][n_f]
@@ -300,7 +304,8 @@ typedef struct {
  *   ray-cell steps marched.  Scratch: emissivity tables of n_cams * ncell *
  *   n_f floats are allocated by the context and kept for reuse. */
 RT_API rt_status rt_raytrace(rt_ctx* ctx, const rt_grid* grid, const rt_opacity* opac,
-                      const double* T, const rt_event* events, uint64_t n_events, double xi_ev,
+                      const double* T, const rt_event* events, uint64_t n_events,
+                      const uint64_t* n_events_dev, double xi_ev,
                       const rt_source* sources, int n_sources, const rt_camera* cams, int n_cams,
                       const int* freq_idx, int n_f, float* images, double* sed,
                       uint64_t* ray_steps, rt_stream stream);
@@ -313,11 +318,11 @@ RT_API rt_status rt_raytrace(rt_ctx* ctx, const rt_grid* grid, const rt_opacity*
  * sum_s,i rho_s,i dL/drho_s,i (the derivative with respect to a global
  * density scale) into dL_dscale (device, one double).  Per ray the forward
  * march is recomputed (pass 1: totals, pass 2: gradients); no path is stored.
- * ray_steps: device uint64 or NULL, incremented by the ray-cell steps of both
- * passes. */
+ * events, n_events and n_events_dev as for rt_raytrace.  ray_steps: device
+ * uint64 or NULL, incremented by the ray-cell steps of both passes. */
 RT_API rt_status rt_raytrace_backward(rt_ctx* ctx, const rt_grid* grid, const rt_opacity* opac,
                                const double* T, const rt_event* events, uint64_t n_events,
-                               double xi_ev, const rt_source* sources, int n_sources,
+                               const uint64_t* n_events_dev, double xi_ev, const rt_source* sources, int n_sources,
                                const rt_camera* cams, int n_cams, const int* freq_idx, int n_f,
                                const float* dL_dimg, const double* dL_dsed, float* dL_drho,
                                double* dL_dscale, uint64_t* ray_steps, rt_stream stream);

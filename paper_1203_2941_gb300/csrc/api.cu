@@ -677,7 +677,8 @@ static rt_status check_rt_args(rt_ctx* ctx, const rt_grid* grid, const rt_opacit
 }
 
 rt_status rt_raytrace(rt_ctx* ctx, const rt_grid* grid, const rt_opacity* op, const double* T,
-                      const rt_event* ev, uint64_t nev, double xi_ev, const rt_source* src, int nsrc,
+                      const rt_event* ev, uint64_t nev, const uint64_t* nev_dev, double xi_ev,
+                      const rt_source* src, int nsrc,
                       const rt_camera* cams, int ncam, const int* fidx, int nfi, float* images,
                       double* sed, uint64_t* ray_steps, rt_stream stream)
 {
@@ -685,13 +686,14 @@ rt_status rt_raytrace(rt_ctx* ctx, const rt_grid* grid, const rt_opacity* op, co
     if (st != RT_OK) return st;
     if (!images || !sed) return fail(RT_ERR_INVALID_ARG, "rt_raytrace: NULL output");
     RT_CUDA(cudaSetDevice(ctx->device));
-    return raytrace_impl(ctx, grid, op, T, ev, nev, xi_ev, src, nsrc, cams, ncam, fidx, nfi, images,
-                         sed, nullptr, nullptr, nullptr, nullptr, (unsigned long long*)ray_steps,
+    return raytrace_impl(ctx, grid, op, T, ev, nev, nev_dev, xi_ev, src, nsrc, cams, ncam, fidx, nfi,
+                         images, sed, nullptr, nullptr, nullptr, nullptr, (unsigned long long*)ray_steps,
                          false, (cudaStream_t)stream);
 }
 
 rt_status rt_raytrace_backward(rt_ctx* ctx, const rt_grid* grid, const rt_opacity* op,
-                               const double* T, const rt_event* ev, uint64_t nev, double xi_ev,
+                               const double* T, const rt_event* ev, uint64_t nev,
+                               const uint64_t* nev_dev, double xi_ev,
                                const rt_source* src, int nsrc, const rt_camera* cams, int ncam,
                                const int* fidx, int nfi, const float* dimg, const double* dsed,
                                float* drho, double* dscale, uint64_t* ray_steps, rt_stream stream)
@@ -700,8 +702,8 @@ rt_status rt_raytrace_backward(rt_ctx* ctx, const rt_grid* grid, const rt_opacit
     if (st != RT_OK) return st;
     if (!drho || !dscale) return fail(RT_ERR_INVALID_ARG, "rt_raytrace_backward: NULL output");
     RT_CUDA(cudaSetDevice(ctx->device));
-    return raytrace_impl(ctx, grid, op, T, ev, nev, xi_ev, src, nsrc, cams, ncam, fidx, nfi, nullptr,
-                         nullptr, dimg, dsed, drho, dscale, (unsigned long long*)ray_steps, true,
+    return raytrace_impl(ctx, grid, op, T, ev, nev, nev_dev, xi_ev, src, nsrc, cams, ncam, fidx, nfi,
+                         nullptr, nullptr, dimg, dsed, drho, dscale, (unsigned long long*)ray_steps, true,
                          (cudaStream_t)stream);
 }
 

@@ -414,35 +414,49 @@ __device__ __forceinline__ float hg_toward(const rt_event& e, const float* ko, f
     return ag.x / (d * sqrtf(d));
 }
 
-// eta_sca * cell: every stored event adds xi cell / (V dnu) P_HG(k_in . k_obs)
-__global__ void eta_scatter_kernel(const rt_event* ev, uint64_t nev, ScatKP P, float* eta)
+// number of events to use: min(*nev_dev, cap) when the count lives on the device
+__device__ __forceinline__ uint64_t event_count(uint64_t cap, const uint64_t* nev_dev)
 {
-    const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-    if (i >= nev) return;
-    const rt_event e = ev[i];
-    if (e.nu >= P.nf || e.species >= P.ns) return;
-    const int f = P.f_of_nu[e.nu];
-    if (f < 0 || (size_t)e.cell >= P.nc) return;
-    const float2 ag = P.ag[e.species * P.nf + e.nu];
-    for (int k = 0; k < P.ncam; ++k)
-        atomicAdd(&eta[((size_t)k * P.nc + e.cell) * P.nfp + f], hg_toward(e, P.kobs + 3 * k, ag));
+    if (!nev_dev) return cap;
+    const uint64_t n = *nev_dev;
+    return n < cap ? n : cap;
+}
+
+// eta_sca * cell: every stored event adds xi cell / (V dnu) P_HG(k_in . k_obs)
+// (grid-stride over the events)
+__global__ void eta_scatter_kernel(const rt_event* ev, uint64_t cap, const uint64_t* nev_dev, ScatKP P,
+                                   float* eta)
+{
+    const uint64_t nev = event_count(cap, nev_dev);
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < nev;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const rt_event e = ev[i];
+        if (e.nu >= P.nf || e.species >= P.ns) continue;
+        const int f = P.f_of_nu[e.nu];
+        if (f < 0 || (size_t)e.cell >= P.nc) continue;
+        const float2 ag = P.ag[e.species * P.nf + e.nu];
+        for (int k = 0; k < P.ncam; ++k)
+            atomicAdd(&eta[((size_t)k * P.nc + e.cell) * P.nfp + f], hg_toward(e, P.kobs + 3 * k, ag));
+    }
 }
 
 // several image frequencies share one event frequency: handled by a second
 // pass over the remaining duplicate slots
-__global__ void eta_scatter_dup_kernel(const rt_event* ev, uint64_t nev, ScatKP P, const int* dup,
-                                       int ndup, float* eta)
+__global__ void eta_scatter_dup_kernel(const rt_event* ev, uint64_t cap, const uint64_t* nev_dev, ScatKP P,
+                                       const int* dup, int ndup, float* eta)
 {
-    const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-    if (i >= nev) return;
-    const rt_event e = ev[i];
-    if ((size_t)e.cell >= P.nc || e.nu >= P.nf || e.species >= P.ns) return;
-    for (int q = 0; q < ndup; ++q) {
-        const int f = dup[2 * q], j = dup[2 * q + 1];
-        if ((int)e.nu != j) continue;
-        const float2 ag = P.ag[e.species * P.nf + e.nu];
-        for (int k = 0; k < P.ncam; ++k)
-            atomicAdd(&eta[((size_t)k * P.nc + e.cell) * P.nfp + f], hg_toward(e, P.kobs + 3 * k, ag));
+    const uint64_t nev = event_count(cap, nev_dev);
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < nev;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const rt_event e = ev[i];
+        if ((size_t)e.cell >= P.nc || e.nu >= P.nf || e.species >= P.ns) continue;
+        for (int q = 0; q < ndup; ++q) {
+            const int f = dup[2 * q], j = dup[2 * q + 1];
+            if ((int)e.nu != j) continue;
+            const float2 ag = P.ag[e.species * P.nf + e.nu];
+            for (int k = 0; k < P.ncam; ++k)
+                atomicAdd(&eta[((size_t)k * P.nc + e.cell) * P.nfp + f], hg_toward(e, P.kobs + 3 * k, ag));
+        }
     }
 }
 
@@ -637,8 +651,8 @@ rt_status grow(T*& p, size_t& cap, size_t n)
 }  // namespace
 
 rt_status raytrace_impl(rt_ctx* ctx, const rt_grid* g, const rt_opacity* op, const double* T,
-                        const rt_event* ev, uint64_t nev, double xi_ev, const rt_source* src,
-                        int nsrc, const rt_camera* cams, int ncam, const int* fidx, int nfi,
+                        const rt_event* ev, uint64_t nev, const uint64_t* nev_dev, double xi_ev,
+                        const rt_source* src, int nsrc, const rt_camera* cams, int ncam, const int* fidx, int nfi,
                         float* images, double* sed, const float* dimg, const double* dsed,
                         float* drho, double* dscale, unsigned long long* ray_steps, bool backward,
                         cudaStream_t s)
@@ -764,11 +778,11 @@ rt_status raytrace_impl(rt_ctx* ctx, const rt_grid* g, const rt_opacity* op, con
         sk.kobs = (const float*)(dbuf + o_ko);
         sk.f_of_nu = (const int*)(dbuf + o_fn);
         sk.nf = op->nf; sk.ns = ns;
-        const unsigned blocks = (unsigned)((nev + 255) / 256);
-        eta_scatter_kernel<<<blocks, 256, 0, s>>>(ev, nev, sk, ctx->d_eta);
+        const unsigned blocks = (unsigned)std::min<uint64_t>((nev + 255) / 256, (uint64_t)ctx->num_sms * 8);
+        eta_scatter_kernel<<<blocks, 256, 0, s>>>(ev, nev, nev_dev, sk, ctx->d_eta);
         count_launches();
         if (!dup.empty()) {
-            eta_scatter_dup_kernel<<<blocks, 256, 0, s>>>(ev, nev, sk, (const int*)(dbuf + o_du),
+            eta_scatter_dup_kernel<<<blocks, 256, 0, s>>>(ev, nev, nev_dev, sk, (const int*)(dbuf + o_du),
                                                           (int)dup.size() / 2, ctx->d_eta);
             count_launches();
         }

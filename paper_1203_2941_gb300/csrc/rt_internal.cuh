@@ -224,8 +224,8 @@ rt_status launch_temperatures(rt_ctx* ctx, const rt_grid* g, const rt_opacity* o
 rt_status launch_temperature_guess(rt_ctx* ctx, const rt_grid* g, const double* src_pos,
                                    const double* src_L, int nsrc, double* T, cudaStream_t s);
 rt_status raytrace_impl(rt_ctx* ctx, const rt_grid* g, const rt_opacity* op, const double* T,
-                        const rt_event* ev, uint64_t nev, double xi_ev, const rt_source* src,
-                        int nsrc, const rt_camera* cams, int ncam, const int* fidx, int nfi,
+                        const rt_event* ev, uint64_t nev, const uint64_t* nev_dev, double xi_ev,
+                        const rt_source* src, int nsrc, const rt_camera* cams, int ncam, const int* fidx, int nfi,
                         float* images, double* sed, const float* dimg, const double* dsed,
                         float* drho, double* dscale, unsigned long long* ray_steps, bool backward,
                         cudaStream_t s);

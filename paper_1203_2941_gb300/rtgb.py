@@ -111,9 +111,9 @@ def load(path: str = LIB_PATH):
                                        C.POINTER(rt_transport_out), vp]),
         "rt_temperatures": (i32, [vp, vp, vp, vp, vp, vp]),
         "rt_temperature_guess": (i32, [vp, vp, vp, i32, vp, vp]),
-        "rt_raytrace": (i32, [vp, vp, vp, vp, vp, u64, dbl, vp, i32, vp, i32, vp, i32, vp, vp, vp,
-                              vp]),
-        "rt_raytrace_backward": (i32, [vp, vp, vp, vp, vp, u64, dbl, vp, i32, vp, i32, vp, i32,
+        "rt_raytrace": (i32, [vp, vp, vp, vp, vp, u64, vp, dbl, vp, i32, vp, i32, vp, i32, vp, vp,
+                              vp, vp]),
+        "rt_raytrace_backward": (i32, [vp, vp, vp, vp, vp, u64, vp, dbl, vp, i32, vp, i32, vp, i32,
                                        vp, vp, vp, vp, vp, vp]),
         "rt_kernel_launches": (u64, []),
         "rt_batch_create": (i32, [vp, vp, i32, vp, C.POINTER(rt_transport_params), C.POINTER(vp)]),
@@ -208,19 +208,20 @@ def rt_temperature_guess(ctx, grid, sources, n_sources, T_ptr, stream=0):
            "rt_temperature_guess")
 
 
-def rt_raytrace(ctx, grid, opac, T_ptr, ev_ptr, n_ev, xi_ev, sources, n_sources, cams, n_cams,
-                fidx, n_f, img_ptr, sed_ptr, steps_ptr=None, stream=0):
-    _check(load().rt_raytrace(ctx, grid, opac, T_ptr, ev_ptr, n_ev, xi_ev, sources, n_sources,
-                              cams, n_cams, fidx, n_f, img_ptr, sed_ptr, steps_ptr, stream),
+def rt_raytrace(ctx, grid, opac, T_ptr, ev_ptr, n_ev, n_ev_dev, xi_ev, sources, n_sources, cams,
+                n_cams, fidx, n_f, img_ptr, sed_ptr, steps_ptr=None, stream=0):
+    _check(load().rt_raytrace(ctx, grid, opac, T_ptr, ev_ptr, n_ev, n_ev_dev, xi_ev, sources,
+                              n_sources, cams, n_cams, fidx, n_f, img_ptr, sed_ptr, steps_ptr,
+                              stream),
            "rt_raytrace")
 
 
-def rt_raytrace_backward(ctx, grid, opac, T_ptr, ev_ptr, n_ev, xi_ev, sources, n_sources, cams,
-                         n_cams, fidx, n_f, dimg_ptr, dsed_ptr, drho_ptr, dscale_ptr,
-                         steps_ptr=None, stream=0):
-    _check(load().rt_raytrace_backward(ctx, grid, opac, T_ptr, ev_ptr, n_ev, xi_ev, sources,
-                                       n_sources, cams, n_cams, fidx, n_f, dimg_ptr, dsed_ptr,
-                                       drho_ptr, dscale_ptr, steps_ptr, stream),
+def rt_raytrace_backward(ctx, grid, opac, T_ptr, ev_ptr, n_ev, n_ev_dev, xi_ev, sources,
+                         n_sources, cams, n_cams, fidx, n_f, dimg_ptr, dsed_ptr, drho_ptr,
+                         dscale_ptr, steps_ptr=None, stream=0):
+    _check(load().rt_raytrace_backward(ctx, grid, opac, T_ptr, ev_ptr, n_ev, n_ev_dev, xi_ev,
+                                       sources, n_sources, cams, n_cams, fidx, n_f, dimg_ptr,
+                                       dsed_ptr, drho_ptr, dscale_ptr, steps_ptr, stream),
            "rt_raytrace_backward")
 
 

@@ -246,11 +246,14 @@ def cameras(cams) -> "C.Array":
 
 
 def _events_tensor(events):
-    """Events as a device uint8 tensor (20 bytes each) and their count."""
+    """Events as a device uint8 tensor (20 bytes each), their count (or the
+    buffer capacity) and the address of a device-side count (or None).  A
+    TransportOut passes its event cursor in device memory, so no host copy of
+    the count (and no stream synchronisation) is needed."""
     if events is None:
-        return None, 0
+        return None, 0, None
     if isinstance(events, TransportOut):
-        return events.events, events.n_events
+        return events.events, events.event_cap, events.stats.data_ptr() + 8 * 13
     if isinstance(events, np.ndarray):
         if events.dtype != R.EVENT_DTYPE:
             ev = np.zeros(len(events), R.EVENT_DTYPE)
@@ -258,9 +261,9 @@ def _events_tensor(events):
             ev["k"] = events["k"]
             events = ev
         if len(events) == 0:
-            return None, 0
+            return None, 0, None
         t = torch.from_numpy(np.ascontiguousarray(events).view(np.uint8).copy()).cuda()
-        return t, len(events)
+        return t, len(events), None
     raise TypeError("events must be a TransportOut or a numpy event array")
 
 
@@ -269,14 +272,14 @@ def raytrace(ctx: Context, grid: Grid, opac: Opacity, T: torch.Tensor, events, x
              steps: Optional[torch.Tensor] = None):
     """Images [n_cams, n_f, npix, npix] (float32) and SED [n_cams, n_f] (float64);
     ``steps`` (int64 device tensor of one element) accumulates ray-cell steps."""
-    ev, nev = _events_tensor(events)
+    ev, nev, nev_dev = _events_tensor(events)
     ca = cameras(cams)
     fi = (C.c_int * len(freq_idx))(*[int(f) for f in freq_idx])
     npix = cams[0].npix
     img = torch.empty((len(cams), len(freq_idx), npix, npix), dtype=torch.float32, device="cuda")
     sed = torch.empty((len(cams), len(freq_idx)), dtype=torch.float64, device="cuda")
     T = T.to(dtype=torch.float64).contiguous()
-    R.rt_raytrace(ctx.h, grid.h, opac.h, _ptr(T), _ptr(ev), nev, float(xi_ev),
+    R.rt_raytrace(ctx.h, grid.h, opac.h, _ptr(T), _ptr(ev), nev, nev_dev, float(xi_ev),
                   None if sources is None else sources.arr, 0 if sources is None else sources.n,
                   ca, len(cams), fi, len(freq_idx), _ptr(img), _ptr(sed), _ptr(steps),
                   _stream(stream))
@@ -287,7 +290,7 @@ def raytrace_backward(ctx: Context, grid: Grid, opac: Opacity, T: torch.Tensor, 
                       sources: Optional[Sources], cams, freq_idx, dL_dimg=None, dL_dsed=None,
                       stream=None, steps: Optional[torch.Tensor] = None):
     """dL/drho [ns, ncell] (float32) and dL/dscale (float64 scalar tensor)."""
-    ev, nev = _events_tensor(events)
+    ev, nev, nev_dev = _events_tensor(events)
     ca = cameras(cams)
     fi = (C.c_int * len(freq_idx))(*[int(f) for f in freq_idx])
     drho = torch.zeros((grid.ns, grid.ncell), dtype=torch.float32, device="cuda")
@@ -295,7 +298,7 @@ def raytrace_backward(ctx: Context, grid: Grid, opac: Opacity, T: torch.Tensor, 
     T = T.to(dtype=torch.float64).contiguous()
     gi = None if dL_dimg is None else dL_dimg.to(dtype=torch.float32).contiguous()
     gs = None if dL_dsed is None else dL_dsed.to(dtype=torch.float64).contiguous()
-    R.rt_raytrace_backward(ctx.h, grid.h, opac.h, _ptr(T), _ptr(ev), nev, float(xi_ev),
+    R.rt_raytrace_backward(ctx.h, grid.h, opac.h, _ptr(T), _ptr(ev), nev, nev_dev, float(xi_ev),
                            None if sources is None else sources.arr,
                            0 if sources is None else sources.n, ca, len(cams), fi, len(freq_idx),
                            _ptr(gi), _ptr(gs), _ptr(drho), _ptr(dscale), _ptr(steps),

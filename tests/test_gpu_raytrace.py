@@ -116,6 +116,34 @@ def test_raytrace_matches_oracle(rt, ctx, O, case):
     np.testing.assert_allclose(sed.cpu().numpy(), sr, rtol=1e-5)
 
 
+def test_raytrace_reads_event_count_on_device(rt, ctx, O):
+    """Events straight from a transport output: the count is read on the
+    device (capacity above and below the number stored) and the images equal
+    those from the same events passed with a host count, and the oracle's."""
+    m = W.r2_shell(n=12, nf=24, tau_1um=5.0)
+    grid, opac, srcs = ctx.grid(m), ctx.opacity(m), rt.Sources(m.sources)
+    cams = [W.Camera(np.radians(30.0), 0.2, 16, 3e19), W.Camera(np.radians(80.0), 1.1, 16, 3e19)]
+    fidx = [2, 9, 15]
+    T = torch.full((m.ns, m.ncell), 300.0, dtype=torch.float64, device="cuda")
+    for cap in (200000, 500):
+        out = rt.transport(ctx, grid, opac, srcs, 20000, event_cap=cap, seed=7, record_events=True)
+        torch.cuda.synchronize()
+        stored = int(out.stats[13].item())
+        assert stored > 0 and (cap > stored or cap == 500)
+        xi = m.luminosity / 20000
+        img_d, sed_d = rt.raytrace(ctx, grid, opac, T, out, xi, srcs, cams, fidx)
+        ev = out.events_numpy()
+        assert len(ev) == min(stored, cap)
+        img_h, sed_h = rt.raytrace(ctx, grid, opac, T, ev, xi, srcs, cams, fidx)
+        torch.cuda.synchronize()
+        np.testing.assert_allclose(img_d.cpu().numpy(), img_h.cpu().numpy(), rtol=1e-6,
+                                   atol=1e-6 * float(img_h.abs().max()))
+        np.testing.assert_allclose(sed_d.cpu().numpy(), sed_h.cpu().numpy(), rtol=1e-6)
+        ir, sr = O.raytrace(m, T.cpu().numpy(), ev, xi, cams, fidx)
+        _compare_images(img_d.cpu().numpy(), ir)
+        np.testing.assert_allclose(sed_d.cpu().numpy(), sr, rtol=1e-5)
+
+
 def test_raytrace_adjoint_matches_oracle(rt, ctx, O):
     m = W.random_grid(n=(8, 7, 6), ns=2, nf=10, seed=6, tau_scale=1.5, albedo=(0.2, 0.7))
     grid, opac, srcs = ctx.grid(m), ctx.opacity(m), rt.Sources(m.sources)
