@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--npix", type=int, default=256)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--forms", default="", help="measure other forms instead of the step: "
+                    "all or a comma list of fp64_debug, mrw_disk, adjoint, batched")
     return ap.parse_args()
 
 
@@ -136,6 +138,237 @@ def cpu_baseline(m, a, budget_s=12.0):
                       f"{r['stats']['crossings']} crossings in {dt:.1f} s"}
 
 
+# ---------------------------------------------------------------------------
+# Other forms of the hot path (opt-in, --forms): each on its own workload,
+# timed with CUDA events after warm-up, reported with its roofline fraction.
+
+def _peak_hbm():
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def _timed(fn, reps, warm, flush=None):
+    import torch
+    for _ in range(warm):
+        fn(-1)
+    torch.cuda.synchronize()
+    ts = []
+    for r in range(reps):
+        if flush is not None:
+            flush.fill_(float(r))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn(r)
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1) / 1e3)
+    return ts
+
+
+def _transport_bytes(S, ns):
+    return (4 * ns * S["crossings"] + 32 * ns * S["lucy_deposits"] + 40 * S["absorptions"]
+            + 20 * S["scatters"] + 32 * S["escaped"] + 64 * S["mrw_steps"])
+
+
+def _roof(bytes_, secs):
+    peak, src = _peak_hbm()
+    gbs = bytes_ / secs / 1e9
+    return {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+            "peak_source": src}
+
+
+def _stats_delta(out, s0):
+    from paper_1203_2941_gb300 import rtgb as R
+    st = (out.stats - s0).cpu().numpy()
+    return {k: int(st[i]) for i, k in enumerate(R.STAT_NAMES)}
+
+
+def form_fp64_debug(rt, ctx, flush):
+    """Homogeneous sphere 32^3 (tau_V = 1, 30 frequencies, 1e5 packets):
+    the FP64 debug build against the FP32 production build, same packets."""
+    import torch
+    import workloads as W
+    from paper_1203_2941_gb300 import rtgb as R
+    m = W.homogeneous_sphere(n=32, tau_v=1.0, nf=30)
+    grid, opac, srcs = ctx.grid(m), ctx.opacity(m), rt.Sources(m.sources)
+    N = 100000
+    res = {}
+    for name, prec in (("fp64_debug", R.RT_PREC_FP64), ("fp32_fp64acc", R.RT_PREC_FP32)):
+        out = rt.TransportOut(grid.ncell, 1, opac.nf)
+        s0 = [None]
+
+        def run(r):
+            out.zero_()
+            rt.transport(ctx, grid, opac, srcs, N, out=out, seed=3 + max(r, 0), precision=prec)
+        ts = _timed(run, 5, 2, flush)
+        S = _stats_delta(out, torch.zeros_like(out.stats))
+        t = statistics.median(ts)
+        res[name] = {"value": S["crossings"] / t, "unit": UNIT, "ms": 1e3 * t,
+                     "roofline": _roof(_transport_bytes(S, 1), t)}
+    res["ratio_fp64_over_fp32"] = res["fp64_debug"]["value"] / res["fp32_fp64acc"]["value"]
+    res["workload"] = "homogeneous sphere 32^3, tau_V=1, 30 freq, 1e5 packets, B&W, Lucy thin"
+    return res
+
+
+def form_mrw_disk(rt, ctx, flush, packets=1e7, npix=512):
+    """Flared disk 256^3 (midplane tau_V = 1e4, 100 frequencies) with the
+    modified random walk in cells of tau > 10; then Eq. 4 temperatures and
+    images at 12 frequencies x 5 inclinations."""
+    import math as _m
+    import torch
+    import workloads as W
+    m = W.flared_disk(n=256, tau_v=1e4, nf=100)
+    grid, opac, srcs = ctx.grid(m), ctx.opacity(m), rt.Sources(m.sources)
+    N = int(packets)
+    out = rt.TransportOut(grid.ncell, 1, opac.nf, event_cap=4 * N)
+    state = {}
+
+    def run(r):
+        out.zero_()
+        out.stats[13:].zero_()
+        rt.transport(ctx, grid, opac, srcs, N, out=out, record_events=True, mrw=True,
+                     seed=11 + max(r, 0))
+    ts = _timed(run, 3, 1, flush)
+    S = _stats_delta(out, torch.zeros_like(out.stats))
+    t = statistics.median(ts)
+    res = {"transport": {"value": S["crossings"] / t, "unit": UNIT, "ms": 1e3 * t,
+                         "mrw_steps": S["mrw_steps"], "crossings": S["crossings"],
+                         "interactions": S["interactions"], "absorptions": S["absorptions"],
+                         "lucy_deposits": S["lucy_deposits"], "stuck": S["stuck"],
+                         "roofline": _roof(_transport_bytes(S, 1), t)}}
+    T = rt.temperatures(ctx, grid, opac, out.E_abs)
+    fidx = W.nearest_freq_indices(m.nu, W.image_wavelengths_um())
+    cams = [W.Camera(_m.radians(th), 0.0, npix, 140 * W.PC) for th in W.inclinations_deg()]
+    steps = torch.zeros(1, dtype=torch.int64, device="cuda")
+
+    def ray(r):
+        steps.zero_()
+        rt.raytrace(ctx, grid, opac, T, out, out.xi, srcs, cams, fidx, steps=steps)
+    ts = _timed(ray, 3, 1, flush)
+    t = statistics.median(ts)
+    n = int(steps.item())
+    nfp = (len(fidx) + 3) // 4 * 4
+    res["raytrace"] = {"value": n / t, "unit": "ray-cell steps/s", "ms": 1e3 * t, "steps": n,
+                       "roofline": _roof(n * (4 + 4 * nfp), t)}
+    res["workload"] = (f"flared disk 256^3, midplane tau_V=1e4, 100 freq, {N:.0e} packets, B&W, "
+                       f"MRW tau_cell>10, Lucy thin, events; images {len(cams)} incl x {len(fidx)} freq "
+                       f"x {npix}^2")
+    return res
+
+
+def form_batched(rt, ctx, flush, per_model=1e6, n_models=64):
+    """64 clumpy tori of uneven size (64^3 .. 192^3, silicate + carbon + PAH,
+    100 frequencies) in one persistent launch replayed from a CUDA graph,
+    against the same models run one after another through the single-model
+    path."""
+    import torch
+    import workloads as W
+    models = W.batched_tori(n_models=n_models)
+    opac = ctx.opacity(models[0])
+    N = [int(per_model)] * n_models
+    b = rt.Batch(ctx, opac, models, N, seed=21, pah_cap=int(per_model))
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        b.run(s)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    gr = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(gr):
+        b.run(torch.cuda.current_stream())
+    s0 = [o.stats.clone() for o in b.outs]
+
+    def run(r):
+        gr.replay()
+    reps = 3
+    ts = _timed(run, reps, 1, flush)
+    S = {}
+    for o, z in zip(b.outs, s0):
+        for k, v in _stats_delta(o, z).items():
+            S[k] = S.get(k, 0) + v
+    S = {k: v // (reps + 1) for k, v in S.items()}
+    t = statistics.median(ts)
+    res = {"batched_graph": {"value": S["crossings"] / t, "unit": UNIT, "ms": 1e3 * t,
+                             "crossings": S["crossings"], "roofline": _roof(_transport_bytes(S, 3), t)}}
+    grids, srcs = b.grids, b.sources
+    outs = [rt.TransportOut(g.ncell, g.ns, opac.nf, pah_cap=int(per_model)) for g in grids]
+
+    def single(r):
+        for i in range(n_models):
+            outs[i].zero_()
+            rt.transport(ctx, grids[i], opac, srcs[i], N[i], out=outs[i], seed=21, model_id=i)
+    ts = _timed(single, 2, 1, flush)
+    t1 = statistics.median(ts)
+    c1 = sum(int(o.stats[0].item()) for o in outs)
+    res["single_model_loop"] = {"value": c1 / t1, "unit": UNIT, "ms": 1e3 * t1, "crossings": c1}
+    res["ratio_batched_over_single"] = res["batched_graph"]["value"] / res["single_model_loop"]["value"]
+    sizes = [m_.rho.shape[-1] for m_ in models]
+    res["workload"] = (f"{n_models} clumpy tori {min(sizes)}^3..{max(sizes)}^3 "
+                       f"(3 species incl. PAH, 100 freq), {per_model:.0e} packets each, B&W, Lucy thin")
+    return res
+
+
+def form_adjoint(rt, ctx, flush, npix=256):
+    """Ray-tracer adjoint on a 128^3 clumpy torus (1000 clumps, temperatures
+    fixed from a prior transport): 8 views at 10 um plus the SED at 16 of
+    the model frequencies, d(loss)/d(rho) and d/d(scale)."""
+    import math as _m
+    import torch
+    import workloads as W
+    m = W.clumpy_torus(n=128, n_clump=1000, seed=77, nf=40)
+    grid, opac, srcs = ctx.grid(m), ctx.opacity(m), rt.Sources(m.sources)
+    out = rt.transport(ctx, grid, opac, srcs, 1000000, event_cap=4000000, seed=31)
+    T = rt.temperatures(ctx, grid, opac, out.E_abs)
+    fidx = W.nearest_freq_indices(m.nu, [10.0])
+    cams = [W.Camera(_m.radians(th), _m.radians(45.0 * k), npix, 14e6 * W.PC)
+            for k, th in enumerate((10, 30, 50, 70, 90, 110, 130, 150))]
+    g = torch.Generator(device="cuda").manual_seed(5)
+    dimg = torch.randn((len(cams), len(fidx), npix, npix), device="cuda", generator=g)
+    dsed = torch.randn((len(cams), len(fidx)), device="cuda", dtype=torch.float64, generator=g)
+    steps = torch.zeros(1, dtype=torch.int64, device="cuda")
+
+    def fwd(r):
+        steps.zero_()
+        rt.raytrace(ctx, grid, opac, T, out, out.xi, srcs, cams, fidx, steps=steps)
+    tf = statistics.median(_timed(fwd, 3, 1, flush))
+    nf_ = int(steps.item())
+
+    def bwd(r):
+        steps.zero_()
+        rt.raytrace_backward(ctx, grid, opac, T, out, out.xi, srcs, cams, fidx, dL_dimg=dimg,
+                             dL_dsed=dsed, steps=steps)
+    tb = statistics.median(_timed(bwd, 3, 1, flush))
+    nb = int(steps.item())
+    nfp = (len(fidx) + 3) // 4 * 4
+    br = 4 * 4 + 4 * nfp
+    res = {"forward": {"value": nf_ / tf, "unit": "ray-cell steps/s", "ms": 1e3 * tf,
+                       "roofline": _roof(nf_ * br, tf)},
+           "adjoint": {"value": nb / tb, "unit": "ray-cell steps/s", "ms": 1e3 * tb,
+                       "roofline": _roof(nb * (2 * br + 4), tb)}}
+    res["workload"] = f"clumpy torus 128^3, 1000 clumps, 3 species, 8 views x 10 um x {npix}^2 + SED"
+    return res
+
+
+def run_forms(a):
+    import torch
+    import paper_1203_2941_gb300 as rt
+    rt.build()
+    ctx = rt.Context(0)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    forms = {}
+    for name, fn in (("fp64_debug", form_fp64_debug), ("mrw_disk", form_mrw_disk),
+                     ("adjoint", form_adjoint), ("batched", form_batched)):
+        if a.forms != "all" and name not in a.forms.split(","):
+            continue
+        t0 = time.perf_counter()
+        forms[name] = fn(rt, ctx, flush)
+        forms[name]["wall_s"] = time.perf_counter() - t0
+        print(json.dumps({"form": name, **forms[name]}), flush=True)
+    return forms
+
+
 def run_reference(a):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -172,6 +405,9 @@ def main():
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+        return
+    if a.forms:
+        run_forms(a)
         return
     import numpy as np
     import torch

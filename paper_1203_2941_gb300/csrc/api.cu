@@ -415,6 +415,7 @@ static void fill_kp(TransportKP& kp, const rt_opacity* op, const rt_transport_pa
     kp.seed = p->seed;
     kp.mrw_tau_cell = p->mrw_tau_cell;
     kp.mrw_gamma = p->mrw_gamma;
+    kp.ns = op->ns;
     kp.opac32 = op->d_opac32;
     kp.recdf = op->d_recdf + (p->mode == RT_MODE_BW ? (size_t)op->ns * kReT * op->nf : 0);
     kp.re_lg0 = op->re_lg0;

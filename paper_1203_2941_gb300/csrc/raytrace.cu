@@ -37,6 +37,7 @@ struct CamDev {
 struct RayKP {
     const void* rho;           // packed FP32 grid (rho * cell, Lucy sign bit ignored)
     int nx, ny, nz;
+    int ns;                    // species (<= NS, the packed width)
     float cell;
     float kext[kMaxSpecies][kMaxImgFreq];   // cm^2/g (packed density is rho * cell)
     float kext_cell[kMaxSpecies][kMaxImgFreq];  // kext * cell
@@ -318,6 +319,7 @@ __global__ void __launch_bounds__(128) ray_bwd_kernel(const __grid_constant__ Ra
             const float contrib = eta[f] * seg * ph * att;
 #pragma unroll
             for (int s = 0; s < NS; ++s) {
+                if (s >= P.ns) break;            // float4 padding of a 3-species grid
                 // per-cell-length quantities: bk and eta carry a factor cell,
                 // ke = kext_s cell converts d(dtau)/d(rho_s) = kext_s l_phys
                 const float bk = P.bk[((size_t)s * P.ncell + c) * NFP + f];
@@ -328,7 +330,7 @@ __global__ void __launch_bounds__(128) ray_bwd_kernel(const __grid_constant__ Ra
         }
 #pragma unroll
         for (int s = 0; s < NS; ++s)
-            if (g[s] != 0.f) atomicAdd(&P.grad[(size_t)s * P.ncell + c], g[s]);
+            if (s < P.ns && g[s] != 0.f) atomicAdd(&P.grad[(size_t)s * P.ncell + c], g[s]);
         if (!inside) break;
     }
     count_steps(P.steps, nsteps);
@@ -794,6 +796,7 @@ rt_status raytrace_impl(rt_ctx* ctx, const rt_grid* g, const rt_opacity* op, con
     std::memset(&kp, 0, sizeof(kp));
     kp.rho = g->d_packed;
     kp.nx = g->nx; kp.ny = g->ny; kp.nz = g->nz;
+    kp.ns = ns;
     kp.cell = (float)g->cell;
     for (int sp = 0; sp < ns; ++sp)
         for (int f = 0; f < nfi; ++f) {

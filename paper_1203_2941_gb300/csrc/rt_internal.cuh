@@ -131,6 +131,7 @@ struct TransportKP {
     unsigned long long total_work;
     unsigned long long* work_ctr;
     int nf;
+    int ns;                             // species of the opacity (<= the kernel's padded NS)
     int mode, lucy_form, mrw, record_events;
     int pah_mask;
     int march_min_active;

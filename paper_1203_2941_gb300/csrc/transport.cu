@@ -399,7 +399,8 @@ struct Kernel {
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
             if constexpr (DBG) {
-                const double ka = P.kabs[s * P.nf + L.j], ks = P.ksca[s * P.nf + L.j];
+                const double ka = s < P.ns ? P.kabs[s * P.nf + L.j] : 0.0;
+                const double ks = s < P.ns ? P.ksca[s * P.nf + L.j] : 0.0;
                 L.kex[s] = (ka + ks) * md->cell;
                 L.kab[s] = ka * md->cell;
             } else {
@@ -642,7 +643,7 @@ struct Kernel {
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
             R ks;
-            if constexpr (DBG) ks = sca ? P.ksca[s * P.nf + L.j] : P.kabs[s * P.nf + L.j];
+            if constexpr (DBG) ks = s >= P.ns ? 0.0 : (sca ? P.ksca[s * P.nf + L.j] : P.kabs[s * P.nf + L.j]);
             else ks = sca ? s_op()[s * P.nf + L.j].z : s_op()[s * P.nf + L.j].y;
             w[s] = L.rho[s] * ks;
             tot += w[s];
@@ -654,7 +655,7 @@ struct Kernel {
             acc += w[s];
             if (acc >= target) return s;
         }
-        return NS - 1;
+        return P.ns - 1;
     }
 
     __device__ __forceinline__ void store_pah(Lane<R, NS>& L, const R* x)
@@ -826,7 +827,7 @@ struct Kernel {
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
             R ks;
-            if constexpr (DBG) ks = P.ksca[s * P.nf + L.j] * md->cell;
+            if constexpr (DBG) ks = s < P.ns ? P.ksca[s * P.nf + L.j] * md->cell : 0.0;
             else ks = s_op()[s * P.nf + L.j].z;
             cs += L.rho[s] * ks;
         }
@@ -980,7 +981,9 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : RT_TRANSPORT_MIN_BLO
     unsigned char* sm = smem_raw();
     {
         float4* s_op = reinterpret_cast<float4*>(sm + P.so_op);
-        for (int i = threadIdx.x; i < NS * P.nf; i += blockDim.x) s_op[i] = P.opac32[i];
+        // species beyond the opacity's (padding of a 3-species float4 grid) get zeros
+        for (int i = threadIdx.x; i < NS * P.nf; i += blockDim.x)
+            s_op[i] = i < P.ns * P.nf ? P.opac32[i] : make_float4(0.f, 0.f, 0.f, 0.f);
         if ((FEAT & 1) && P.mrw) {
             float* s_mrw = reinterpret_cast<float*>(sm + P.so_mrw);
             for (int i = threadIdx.x; i < kMrwN; i += blockDim.x) s_mrw[i] = P.mrwS[i];

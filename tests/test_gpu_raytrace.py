@@ -144,8 +144,10 @@ def test_raytrace_reads_event_count_on_device(rt, ctx, O):
         np.testing.assert_allclose(sed_d.cpu().numpy(), sr, rtol=1e-5)
 
 
-def test_raytrace_adjoint_matches_oracle(rt, ctx, O):
-    m = W.random_grid(n=(8, 7, 6), ns=2, nf=10, seed=6, tau_scale=1.5, albedo=(0.2, 0.7))
+@pytest.mark.parametrize("ns", [2, 3])
+def test_raytrace_adjoint_matches_oracle(rt, ctx, O, ns):
+    # ns = 3 runs the float4-padded kernels (a fourth, empty species slot)
+    m = W.random_grid(n=(8, 7, 6), ns=ns, nf=10, seed=6, tau_scale=1.5, albedo=(0.2, 0.7))
     grid, opac, srcs = ctx.grid(m), ctx.opacity(m), rt.Sources(m.sources)
     rng = np.random.default_rng(2)
     T = rng.uniform(50, 900, size=(m.ns, m.ncell))
@@ -171,7 +173,7 @@ def test_raytrace_adjoint_matches_oracle(rt, ctx, O):
     L = (img * torch.tensor(wi, device="cuda", dtype=torch.float32)).sum() + \
         (sed * torch.tensor(ws, device="cuda")).sum()
     L.backward()
-    ga = rho.grad.cpu().numpy().reshape(2, -1).astype(np.float64)
+    ga = rho.grad.cpu().numpy().reshape(ns, -1).astype(np.float64)
     assert np.all(np.abs(ga - gr) <= 1e-2 * np.abs(gr) + 1e-4 * scale)
     assert sc.grad.item() == pytest.approx(gsr, rel=1e-3)
 
