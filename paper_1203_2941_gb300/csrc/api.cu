@@ -409,6 +409,7 @@ static void fill_kp(TransportKP& kp, const rt_opacity* op, const rt_transport_pa
     kp.want_traj = 0;
     kp.single = 0;
     kp.rho0 = nullptr;
+    kp.param_models = 0;
     kp.smem_sed = 0;
     kp.smem_cdf = 0;
     kp.max_events = p->max_events;
@@ -444,7 +445,8 @@ static rt_status single_model_options(TransportKP& kp, const rt_opacity* op,
     kp.want_traj = out->traj != nullptr && out->traj_cap > 0;
     kp.single = 1;
     kp.rho0 = m0.rho;
-    kp.m0 = m0;
+    kp.param_models = 1;
+    kp.mp[0] = m0;
     const bool persistent = p->schedule == RT_SCHED_PERSISTENT && p->precision == RT_PREC_FP32;
     kp.smem_sed = persistent && op->nf <= 256 ? 1 : 0;
     kp.smem_cdf = persistent && n_sources * op->nf <= 4096 ? n_sources * op->nf : 0;
@@ -580,6 +582,11 @@ rt_status rt_batch_create(rt_ctx* ctx, const rt_opacity* op, int n_models, const
     fill_kp(b->kp, op, p, b->dm, n_models);
     for (int m = 0; m < n_models; ++m)
         if (models[m].out.traj && models[m].out.traj_cap) b->kp.want_traj = 1;
+    if (n_models <= kParamModels) {
+        // the staged descriptors also travel in the launch parameters
+        for (int m = 0; m < n_models; ++m) b->kp.mp[m] = hms[m].md;
+        b->kp.param_models = n_models;
+    }
     *out = b;
     return RT_OK;
 }

@@ -32,6 +32,7 @@ constexpr int kReT = 4096;        // FP32 re-emission CDF rows on a uniform log2
 constexpr int kMrwN = 2048;       // MRW survival table entries on y in [0, kMrwYmax]
 constexpr double kMrwYmax = 2.0;
 constexpr int kSedBins = 10;
+constexpr int kParamModels = 64;  // model descriptors carried in the transport launch parameters
 constexpr int kMaxImgFreq = 16;
 
 // Node j of the linear-space temperature table on the uniform ln T grid:
@@ -136,9 +137,10 @@ struct TransportKP {
     int pah_mask;
     int march_min_active;
     int want_traj;                      // some model logs trajectories
-    int single;                         // one model, whose descriptor is m0 (read from the
-    const void* rho0;                   // launch parameters) and packed grid rho0
-    ModelDev m0;
+    int single;                         // one model, with packed grid rho0
+    const void* rho0;
+    int param_models;                   // models whose descriptors are in mp (0: only in models)
+    ModelDev mp[kParamModels];          // descriptors read from the launch parameters
     int smem_sed;                       // single-model persistent launch: SED tallied per block
     int smem_cdf;                       // floats of model 0's source CDFs kept in shared memory
     // dynamic shared-memory layout (byte offsets, set by the launcher)

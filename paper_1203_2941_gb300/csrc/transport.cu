@@ -293,8 +293,9 @@ __device__ __forceinline__ unsigned char* smem_raw()
 }
 
 // FEAT bits: 1 = modified random walk compiled in, 2 = trajectory logging
-// compiled in, 4 = a single model (its index, descriptor and grid come from
-// the launch parameters instead of lane registers); production launches leave
+// compiled in, 4 = model descriptors read from the launch parameters (constant
+// bank) instead of global memory, 8 = a single model (its index and grid
+// pointer are constants, not lane registers); production launches leave
 // unused paths out of the hot code.
 template <typename R, int NS, int FEAT>
 struct Kernel {
@@ -302,17 +303,24 @@ struct Kernel {
     static constexpr bool DBG = sizeof(R) == 8;
     static constexpr bool HAS_MRW = (FEAT & 1) != 0;
     static constexpr bool HAS_TRAJ = (FEAT & 2) != 0;
-    static constexpr bool SINGLE = (FEAT & 4) != 0;
+    static constexpr bool PARAM = (FEAT & 4) != 0;
+    static constexpr bool SINGLE = (FEAT & 8) != 0;
 
     const TransportKP& P;
     const ModelDev* md;        // model of the lane's current packet
 
-    __device__ explicit Kernel(const TransportKP& p) : P(p), md(SINGLE ? &p.m0 : p.models) {}
+    __device__ explicit Kernel(const TransportKP& p) : P(p), md(PARAM ? &p.mp[0] : p.models) {}
+
+    __device__ __forceinline__ const ModelDev* model(int m) const
+    {
+        if constexpr (PARAM) return &P.mp[m];
+        else return &P.models[m];
+    }
 
     // descriptor of the lane's model, before a call that uses md
     __device__ __forceinline__ void bind(const Lane<R, NS>& L)
     {
-        if constexpr (!SINGLE) md = &P.models[L.m];
+        if constexpr (!SINGLE) md = model(L.m);
     }
 
     __device__ __forceinline__ const PT* cells(const Lane<R, NS>& L) const
@@ -462,7 +470,7 @@ struct Kernel {
                 if (L.m >= 0) flush_lane(L.m);
                 L.m = lo;
             }
-            md = &P.models[lo];
+            md = model(lo);
             L.grid = md->rho;
         } else {
             L.m = 0;
@@ -1193,14 +1201,20 @@ rt_status launch_feat(rt_ctx* ctx, const TransportKP& kp, int schedule, int thre
     if constexpr (sizeof(R) == 8) {
         return launch_one<R, NS, 3>(ctx, kp, schedule, threads, blocks_per_sm, s);
     } else {
-        const int feat = (kp.mrw ? 1 : 0) | (kp.want_traj ? 2 : (kp.single ? 4 : 0));
+        // trajectory logging runs the generic variants; otherwise descriptors
+        // come from the parameters when they fit, and one model is constant
+        const int feat = (kp.mrw ? 1 : 0) |
+                         (kp.want_traj ? 2 : ((kp.param_models ? 4 : 0) | (kp.single ? 8 : 0)));
         switch (feat) {
         case 0: return launch_one<R, NS, 0>(ctx, kp, schedule, threads, blocks_per_sm, s);
         case 1: return launch_one<R, NS, 1>(ctx, kp, schedule, threads, blocks_per_sm, s);
         case 2: return launch_one<R, NS, 2>(ctx, kp, schedule, threads, blocks_per_sm, s);
         case 3: return launch_one<R, NS, 3>(ctx, kp, schedule, threads, blocks_per_sm, s);
         case 4: return launch_one<R, NS, 4>(ctx, kp, schedule, threads, blocks_per_sm, s);
-        default: return launch_one<R, NS, 5>(ctx, kp, schedule, threads, blocks_per_sm, s);
+        case 5: return launch_one<R, NS, 5>(ctx, kp, schedule, threads, blocks_per_sm, s);
+        case 12: return launch_one<R, NS, 12>(ctx, kp, schedule, threads, blocks_per_sm, s);
+        case 13: return launch_one<R, NS, 13>(ctx, kp, schedule, threads, blocks_per_sm, s);
+        default: return fail(RT_ERR_STATE, "transport: no kernel variant for this feature set");
         }
     }
 }
