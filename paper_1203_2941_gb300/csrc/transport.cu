@@ -979,11 +979,14 @@ struct Kernel {
     }
 };
 
+// Occupancy target of the FP32 kernel: 4 blocks of 256 threads per SM (64
+// registers); four-species variants carry four-wide density and opacity
+// state and run at 3 blocks (80 registers), where they spill far less.
 #ifndef RT_TRANSPORT_MIN_BLOCKS
 #define RT_TRANSPORT_MIN_BLOCKS 4
 #endif
 template <typename R, int NS, int FEAT>
-__global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : RT_TRANSPORT_MIN_BLOCKS)
+__global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (NS == 4 ? 3 : RT_TRANSPORT_MIN_BLOCKS))
     transport_kernel(const __grid_constant__ TransportKP P, int serial)
 {
     unsigned char* sm = smem_raw();
