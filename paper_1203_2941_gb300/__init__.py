@@ -6,14 +6,14 @@ hand-written sm_103a CUDA kernels behind the C ABI in include/rtgb.h.
 ``rtgb`` is the one-to-one ctypes binding of that ABI; ``sim`` is a thin
 convenience layer that lets torch tensors own the device buffers.
 """
-from . import rtgb
+from . import autotune, rtgb
 from .builder import build
 from .rtgb import RtError, load, rt_version
 from .sim import (Batch, Context, Grid, Opacity, RayTrace, Sources, TransportOut, cameras,
                   make_params, philox, raytrace, raytrace_backward, temperature_guess,
                   temperatures, transport)
 
-__all__ = ["rtgb", "build", "load", "rt_version", "RtError", "Context", "Grid", "Opacity",
+__all__ = ["rtgb", "autotune", "build", "load", "rt_version", "RtError", "Context", "Grid", "Opacity",
            "Sources", "TransportOut", "transport", "temperatures", "temperature_guess",
            "raytrace", "raytrace_backward", "RayTrace", "philox", "Batch", "cameras",
            "make_params"]
