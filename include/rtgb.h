@@ -141,6 +141,12 @@ typedef struct {
     int blocks_per_sm;        /* 0 = occupancy-derived */
     int march_min_active;     /* lanes still marching below which a warp serves its
                                  pending interactions (0..31; -1 = default, 16) */
+    uint64_t defer_events;    /* 0 = off.  rt_transport only: a packet that starts a
+                                 flight after this many interactions + MRW steps is
+                                 queued (device memory, up to 2^20 packets per call)
+                                 and finished by a second pass after every other
+                                 packet, so slow packets do not hold up the warps
+                                 (a full queue leaves the packet where it is) */
 } rt_transport_params;
 
 /* Fill p with the defaults: B&W, Lucy THIN at 1e-2, linear form, MRW off
@@ -185,7 +191,8 @@ enum {
     RT_STAT_PAH_DROPPED = 11, RT_STAT_TRAJ_DROPPED = 12,
     RT_STAT_N_EVENTS = 13,    /* cursor into events (also counts dropped ones) */
     RT_STAT_N_PAH = 14, RT_STAT_N_TRAJ = 15,
-    RT_STAT_COUNT = 16
+    RT_STAT_DEFERRED = 16,    /* packets queued by defer_events (finished later) */
+    RT_STAT_COUNT = 17
 };
 
 /* Caller-owned device outputs.  All are ACCUMULATED into (zero them for a

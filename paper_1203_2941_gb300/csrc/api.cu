@@ -215,6 +215,7 @@ void rt_transport_params_default(rt_transport_params* p)
     p->threads_per_block = 0;
     p->blocks_per_sm = 0;
     p->march_min_active = -1;
+    p->defer_events = 0;
 }
 
 }  // extern "C"
@@ -413,6 +414,11 @@ static void fill_kp(TransportKP& kp, const rt_opacity* op, const rt_transport_pa
     kp.smem_sed = 0;
     kp.smem_cdf = 0;
     kp.max_events = p->max_events;
+    kp.defer_events = 0;               // set by rt_transport when it allocates a queue
+    kp.defer = nullptr;
+    kp.defer_n = nullptr;
+    kp.defer_cap = 0;
+    kp.resume = 0;
     kp.seed = p->seed;
     kp.mrw_tau_cell = p->mrw_tau_cell;
     kp.mrw_gamma = p->mrw_gamma;
@@ -514,12 +520,39 @@ rt_status rt_transport(rt_ctx* ctx, const rt_grid* grid, const rt_opacity* op,
     fill_kp(kp, op, p, dm, 1);
     st = single_model_options(kp, op, p, out, n_sources, hms[0].md);
     if (st != RT_OK) { cudaFreeAsync(dm.buf, s); if (acc) cudaFreeAsync(acc, s); return st; }
+    // deferred packets: a queue in device memory, drained by a second launch
+    char* qbuf = nullptr;
+    if (p->defer_events > 0) {
+        const uint64_t cap = std::min<uint64_t>(p->pid_end - p->pid_begin, kDeferCap);
+        const size_t qbytes = sizeof(DeferRec) * cap + 256;
+        cudaError_t e = cudaMallocAsync((void**)&qbuf, qbytes, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(qbuf + sizeof(DeferRec) * cap, 0, 256, s);
+        if (e != cudaSuccess) {
+            cudaFreeAsync(dm.buf, s);
+            if (acc) cudaFreeAsync(acc, s);
+            if (qbuf) cudaFreeAsync(qbuf, s);
+            return cuda_fail(e, "rt_transport defer queue");
+        }
+        kp.defer_events = p->defer_events;
+        kp.defer = (DeferRec*)qbuf;
+        kp.defer_n = (unsigned long long*)(qbuf + sizeof(DeferRec) * cap);
+        kp.defer_cap = cap;
+    }
     const int threads = p->threads_per_block ? p->threads_per_block : 256;
     st = launch_transport(ctx, op, kp, op->ns, p->precision, p->schedule, threads, p->blocks_per_sm, s);
+    if (st == RT_OK && qbuf) {
+        TransportKP kr = kp;
+        kr.resume = 1;
+        cudaError_t e = cudaMemsetAsync(dm.work, 0, sizeof(unsigned long long), s);
+        st = e == cudaSuccess ? launch_transport(ctx, op, kr, op->ns, p->precision, p->schedule, threads,
+                                                 p->blocks_per_sm, s)
+                              : cuda_fail(e, "rt_transport resume");
+    }
     if (st == RT_OK && acc)
         st = launch_finalize(acc, hms[0].md.acc_q, n_acc, hms[0].md.xi, out->E_abs, out->esq, s);
     cudaFreeAsync(dm.buf, s);
     if (acc) cudaFreeAsync(acc, s);
+    if (qbuf) cudaFreeAsync(qbuf, s);
     return st;
 }
 

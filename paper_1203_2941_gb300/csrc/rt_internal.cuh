@@ -125,6 +125,16 @@ struct ModelDev {
     unsigned long long* stats;
 };
 
+// A packet set aside by defer_events: enough state to restart it at the
+// start of its next flight (positions and directions in the build's
+// precision, stored as doubles).
+struct alignas(16) DeferRec {
+    double x[3], k[3];
+    uint64_t pid;
+    uint32_t cell, j, m, nev, seq, draw, c_lo, c_hi;
+};
+constexpr uint64_t kDeferCap = 1ull << 20;   // queue records per call
+
 struct TransportKP {
     const ModelDev* models;
     const unsigned long long* prefix;   // [n_models + 1] work-index prefix
@@ -146,6 +156,11 @@ struct TransportKP {
     // dynamic shared-memory layout (byte offsets, set by the launcher)
     int so_sed, so_cnt, so_op, so_mrw, so_cdf, so_ctr, so_claim;
     unsigned long long max_events;
+    unsigned long long defer_events;    // 0 = off
+    DeferRec* defer;                    // queue (main pass appends, resume pass reads)
+    unsigned long long* defer_n;        // queue cursor (device)
+    unsigned long long defer_cap;
+    int resume;                         // 1: packets come from the queue, not from emission
     uint64_t seed;
     double mrw_tau_cell, mrw_gamma;
     // opacity tables

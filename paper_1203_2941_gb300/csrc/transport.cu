@@ -64,6 +64,8 @@ __device__ __forceinline__ void rng_init(Rng& r, uint64_t seed, uint32_t model_i
     r.plo = (uint32_t)pid;
     r.phi = (uint32_t)(pid >> 32);
     r.draw = 0;
+    r.c_lo = 0;
+    r.c_hi = 0;
 }
 
 template <typename R> __device__ __forceinline__ R rng_u(Rng& r, uint32_t kx);
@@ -456,8 +458,72 @@ struct Kernel {
         return lo;
     }
 
+    // Set the packet aside at the start of a flight (defer_events): its state
+    // goes to the queue, its crossings so far to the counters, and the lane
+    // is free.  false: the queue is full and the packet carries on.
+    __device__ __forceinline__ bool defer(Lane<R, NS>& L)
+    {
+        const unsigned long long slot = atomicAdd(P.defer_n, 1ull);
+        if (slot >= P.defer_cap) return false;
+        DeferRec r;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            r.x[a] = (double)L.x[a];
+            r.k[a] = (double)L.k[a];
+        }
+        r.pid = ((uint64_t)L.rng.phi << 32) | L.rng.plo;
+        r.cell = (uint32_t)L.c; r.j = (uint32_t)L.j; r.m = (uint32_t)L.m;
+        r.nev = L.nev; r.seq = L.seq;
+        r.draw = L.rng.draw; r.c_lo = L.rng.c_lo; r.c_hi = L.rng.c_hi;
+        P.defer[slot] = r;
+        atomicAdd(&md->stats[RT_STAT_DEFERRED], 1ull);
+        end_packet(L);
+        return true;
+    }
+
+    // Resume pass: queue record w becomes the lane's packet, at the start of
+    // the flight it was set aside at (same Philox position, so the rest of
+    // its trajectory is the one it would have had)
+    __device__ __forceinline__ void resume(Lane<R, NS>& L, uint64_t w)
+    {
+        const DeferRec r = P.defer[w];
+        if constexpr (!SINGLE) {
+            const int m = (int)r.m;
+            if (m != L.m) {
+                if (L.m >= 0) flush_lane(L.m);
+                L.m = m;
+            }
+            md = model(m);
+            L.grid = md->rho;
+        } else {
+            L.m = 0;
+        }
+        rng_init(L.rng, P.seed, md->model_id, r.pid);
+        L.rng.draw = r.draw; L.rng.c_lo = r.c_lo; L.rng.c_hi = r.c_hi;
+        L.seq = r.seq;
+        L.nev = r.nev;
+        L.ncross = 0;
+        L.nlucy = 0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            L.x[a] = (R)r.x[a];
+            L.k[a] = (R)r.k[a];
+        }
+        L.c = (int)r.cell;
+        L.j = (int)r.j;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) L.rho[s] = R(0);
+        load_freq(L);
+        load_cell(L);
+        L.st = ST_FLIGHT;
+    }
+
     __device__ __forceinline__ void emit(Lane<R, NS>& L, uint64_t w)
     {
+        if (P.resume) {
+            resume(L, w);
+            return;
+        }
         int lo = 0;
         if constexpr (!SINGLE) {
             // model lookup: largest m with prefix[m] <= w
@@ -686,6 +752,7 @@ struct Kernel {
     // A new flight from L.x along L.k: MRW step or tau draw + traversal set-up
     __device__ __forceinline__ void flight(Lane<R, NS>& L)
     {
+        if (P.defer_events && !P.resume && L.nev >= P.defer_events && defer(L)) return;
         const int nx = md->nx, ny = md->ny, nz = md->nz;
         const int iz = L.c / (nx * ny);
         const int r = L.c - iz * nx * ny;
@@ -1012,6 +1079,12 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (NS == 4 ? 3 : RT_TR
     __syncthreads();
 
     Kernel<R, NS, FEAT> K(P);
+    // packets of this launch: emission ids, or the queue filled by the main pass
+    unsigned long long total_work = P.total_work;
+    if (P.resume) {
+        const unsigned long long q = *P.defer_n;
+        total_work = q < P.defer_cap ? q : P.defer_cap;
+    }
     Lane<R, NS> L;
     L.st = ST_NEED;
     L.m = -1;
@@ -1021,7 +1094,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (NS == 4 ? 3 : RT_TR
         // one thread, packets in id order: the order-dependent B&W temperatures
         // evolve exactly as in a sequential run
         if (blockIdx.x != 0 || threadIdx.x != 0) return;
-        for (unsigned long long w = 0; w < P.total_work; ++w) {
+        for (unsigned long long w = 0; w < total_work; ++w) {
             K.emit(L, w);
             while (L.st != ST_NEED) {
                 if (L.st == ST_FLIGHT) K.flight(L);
@@ -1048,25 +1121,25 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (NS == 4 ? 3 : RT_TR
         const unsigned need = __ballot_sync(FULL, L.st == ST_NEED);
         if (need) {
             unsigned long long w_next = claim[0], w_end = claim[1];
-            if (w_next == w_end && w_end < P.total_work) {
+            if (w_next == w_end && w_end < total_work) {
                 unsigned long long base = 0;
                 const unsigned long long n_warps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
-                unsigned long long chunk = (P.total_work - w_end) / (4ull * n_warps);
+                unsigned long long chunk = (total_work - w_end) / (4ull * n_warps);
                 chunk = chunk < 32ull ? 32ull : (chunk > 256ull ? 256ull : chunk);
                 if (lane == 0) base = atomicAdd(P.work_ctr, chunk);
                 base = __shfl_sync(FULL, base, 0);
-                if (base >= P.total_work) {
-                    w_next = w_end = P.total_work;
+                if (base >= total_work) {
+                    w_next = w_end = total_work;
                 } else {
                     w_next = base;
-                    w_end = base + chunk < P.total_work ? base + chunk : P.total_work;
+                    w_end = base + chunk < total_work ? base + chunk : total_work;
                 }
             }
             const unsigned avail = (unsigned)(w_end - w_next);
             const unsigned rank = __popc(need & ((1u << lane) - 1u));
             if (L.st == ST_NEED) {
                 if (rank < avail) K.emit(L, w_next + rank);
-                else if (w_end >= P.total_work) L.st = ST_DONE;
+                else if (w_end >= total_work) L.st = ST_DONE;
             }
             w_next += __popc(need) < avail ? __popc(need) : avail;
             __syncwarp();

@@ -26,8 +26,8 @@ RT_PREC_FP32, RT_PREC_FP64 = 0, 1
 RT_SCHED_PERSISTENT, RT_SCHED_SERIAL = 0, 1
 STAT_NAMES = ["crossings", "interactions", "scatters", "absorptions", "mrw_steps", "escaped",
               "stuck", "pah", "events_dropped", "lucy_deposits", "emitted", "pah_dropped",
-              "traj_dropped", "n_events", "n_pah", "n_traj"]
-RT_STAT_COUNT = 16
+              "traj_dropped", "n_events", "n_pah", "n_traj", "deferred"]
+RT_STAT_COUNT = 17
 EXPORTS = ["rt_last_error", "rt_version", "rt_ctx_create", "rt_ctx_destroy", "rt_grid_upload",
            "rt_grid_free", "rt_opacity_upload", "rt_opacity_free", "rt_transport_params_default",
            "rt_transport", "rt_temperatures", "rt_temperature_guess", "rt_raytrace",
@@ -53,7 +53,7 @@ class rt_transport_params(C.Structure):
                 ("n_packets", C.c_uint64), ("pid_begin", C.c_uint64), ("pid_end", C.c_uint64),
                 ("max_events", C.c_uint64), ("record_events", C.c_int), ("precision", C.c_int),
                 ("schedule", C.c_int), ("threads_per_block", C.c_int), ("blocks_per_sm", C.c_int),
-                ("march_min_active", C.c_int)]
+                ("march_min_active", C.c_int), ("defer_events", C.c_uint64)]
 
 
 class rt_transport_out(C.Structure):

@@ -121,6 +121,51 @@ def test_fp64_mrw_trajectories_match_oracle(rt, ctx, O):
     assert out.stats_dict()["mrw_steps"] == ref["stats"]["mrw_steps"]
 
 
+@pytest.mark.parametrize("schedule", ["persistent", "serial"])
+def test_deferred_packets_keep_their_trajectories(rt, ctx, O, schedule):
+    """defer_events sets packets aside at a flight start and finishes them in
+    a second pass: in the order-independent frozen-T mode (FP64) every
+    trajectory, count and energy still equals the oracle's, with and without
+    MRW steps; in FP32 B&W every packet still escapes exactly once."""
+    sch = rt.rtgb.RT_SCHED_PERSISTENT if schedule == "persistent" else rt.rtgb.RT_SCHED_SERIAL
+    for m, mrw, N in ((W.random_grid(n=(7, 5, 6), ns=2, seed=12, tau_scale=3.0, albedo=(0.3, 0.8)), False, 400),
+                      (W.uniform_cube(n=5, tau_cell=12.0, nf=8, albedo=0.4, gray=True), True, 200)):
+        grid, opac, srcs = _setup(rt, ctx, m)
+        T0 = np.random.default_rng(3).uniform(30, 900, size=(m.ns, m.ncell))
+        out = rt.transport(ctx, grid, opac, srcs, N, mode=rt.rtgb.RT_MODE_FROZEN_T, mrw=mrw,
+                           precision=rt.rtgb.RT_PREC_FP64, T_prev=torch.tensor(T0, device="cuda"),
+                           schedule=sch, traj_cap=1500 * N, seed=78, defer_events=2)
+        torch.cuda.synchronize()
+        ref = O.transport(m, N, seed=78, mode=O.MODE_FROZEN_T, mrw=mrw, T_prev=T0, traj_cap=1500 * N)
+        st = out.stats_dict()
+        assert st["deferred"] > 0 and st["traj_dropped"] == 0
+        # the same run without deferral: bit-identical trajectories
+        plain = rt.transport(ctx, grid, opac, srcs, N, mode=rt.rtgb.RT_MODE_FROZEN_T, mrw=mrw,
+                             precision=rt.rtgb.RT_PREC_FP64, T_prev=torch.tensor(T0, device="cuda"),
+                             schedule=sch, traj_cap=1500 * N, seed=78)
+        torch.cuda.synchronize()
+        a = np.sort(out.traj_numpy(), order=["pid", "seq"])
+        b = np.sort(plain.traj_numpy(), order=["pid", "seq"])
+        assert len(a) == len(b)
+        for f in ("pid", "seq", "type", "cell", "nu", "x", "k"):
+            np.testing.assert_array_equal(a[f], b[f])
+        # and the oracle's (long MRW walks accumulate rounding: 1e-8 of the grid)
+        _traj_compare(out.traj_numpy(), ref["traj"], m.cell * 7, rtol=1e-9 if not mrw else 1e-8)
+        for k in ("crossings", "interactions", "absorptions", "escaped", "lucy_deposits", "mrw_steps",
+                  "emitted"):
+            assert st[k] == ref["stats"][k], k
+        g = out.numpy()
+        np.testing.assert_array_equal(g["count"], ref["count"])
+        np.testing.assert_allclose(g["E_abs"], ref["E_abs"], rtol=1e-9, atol=1e-12 * ref["E_abs"].max())
+    m = W.r2_shell(n=16, tau_1um=10.0, nf=24)
+    grid, opac, srcs = _setup(rt, ctx, m)
+    out = rt.transport(ctx, grid, opac, srcs, 20000, schedule=sch, defer_events=1, seed=5)
+    torch.cuda.synchronize()
+    st = out.stats_dict()
+    assert st["deferred"] > 0 and st["escaped"] == 20000 and st["stuck"] == 0
+    assert abs(out.numpy()["sed_esc"].sum() / m.luminosity - 1) < 1e-9
+
+
 def test_fp64_pah_and_noreemit_match_oracle(rt, ctx, O):
     m = W.clumpy_torus(n=12, n_clump=40, seed=5, nf=20)
     grid, opac, srcs = _setup(rt, ctx, m)
