@@ -520,7 +520,7 @@ def main():
         T_h = torch.empty((1, grid.ncell), dtype=torch.float64).pin_memory()
         img_h = torch.empty((len(cams), len(fidx), a.npix, a.npix), dtype=torch.float32).pin_memory()
         sed_h = torch.empty((len(cams), len(fidx)), dtype=torch.float64).pin_memory()
-        st_h = torch.empty(16, dtype=torch.int64).pin_memory()
+        st_h = torch.empty(R.RT_STAT_COUNT, dtype=torch.int64).pin_memory()
         e2e_out = rt.TransportOut(grid.ncell, 1, opac.nf, event_cap=ev_cap)
         cross_e2e = 0
         torch.cuda.synchronize()

@@ -232,6 +232,9 @@ rt_status pack_grid(rt_grid* g, const rt_opacity* op, int lucy_mode, double lucy
                     cudaStream_t s);
 rt_status pack_grid_into(const rt_grid* g, const rt_opacity* op, int lucy_mode, double lucy_tau,
                          int prec, double* kext, void* dst, cudaStream_t s);
+template <int NS>
+rt_status launch_transport_ns(rt_ctx* ctx, const TransportKP& kp, int prec, int schedule, int threads,
+                              int blocks_per_sm, cudaStream_t s);
 rt_status launch_transport(rt_ctx* ctx, const rt_opacity* op, const TransportKP& kp,
                            int ns, int prec, int schedule, int threads, int blocks_per_sm,
                            cudaStream_t s);

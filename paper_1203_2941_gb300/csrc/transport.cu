@@ -297,8 +297,8 @@ __device__ __forceinline__ unsigned char* smem_raw()
 // FEAT bits: 1 = modified random walk compiled in, 2 = trajectory logging
 // compiled in, 4 = model descriptors read from the launch parameters (constant
 // bank) instead of global memory, 8 = a single model (its index and grid
-// pointer are constants, not lane registers); production launches leave
-// unused paths out of the hot code.
+// pointer are constants, not lane registers), 16 = the deferred-packet queue
+// compiled in; production launches leave unused paths out of the hot code.
 template <typename R, int NS, int FEAT>
 struct Kernel {
     using PT = typename PackedT<NS>::T;
@@ -307,6 +307,7 @@ struct Kernel {
     static constexpr bool HAS_TRAJ = (FEAT & 2) != 0;
     static constexpr bool PARAM = (FEAT & 4) != 0;
     static constexpr bool SINGLE = (FEAT & 8) != 0;
+    static constexpr bool HAS_DEFER = (FEAT & 16) != 0;
 
     const TransportKP& P;
     const ModelDev* md;        // model of the lane's current packet
@@ -520,9 +521,11 @@ struct Kernel {
 
     __device__ __forceinline__ void emit(Lane<R, NS>& L, uint64_t w)
     {
-        if (P.resume) {
-            resume(L, w);
-            return;
+        if constexpr (HAS_DEFER) {
+            if (P.resume) {
+                resume(L, w);
+                return;
+            }
         }
         int lo = 0;
         if constexpr (!SINGLE) {
@@ -752,7 +755,9 @@ struct Kernel {
     // A new flight from L.x along L.k: MRW step or tau draw + traversal set-up
     __device__ __forceinline__ void flight(Lane<R, NS>& L)
     {
-        if (P.defer_events && !P.resume && L.nev >= P.defer_events && defer(L)) return;
+        if constexpr (HAS_DEFER) {
+            if (P.defer_events && !P.resume && L.nev >= P.defer_events && defer(L)) return;
+        }
         const int nx = md->nx, ny = md->ny, nz = md->nz;
         const int iz = L.c / (nx * ny);
         const int r = L.c - iz * nx * ny;
@@ -1081,7 +1086,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (NS == 4 ? 3 : RT_TR
     Kernel<R, NS, FEAT> K(P);
     // packets of this launch: emission ids, or the queue filled by the main pass
     unsigned long long total_work = P.total_work;
-    if (P.resume) {
+    if ((FEAT & 16) && P.resume) {
         const unsigned long long q = *P.defer_n;
         total_work = q < P.defer_cap ? q : P.defer_cap;
     }
@@ -1275,12 +1280,13 @@ rt_status launch_feat(rt_ctx* ctx, const TransportKP& kp, int schedule, int thre
                       int blocks_per_sm, cudaStream_t s)
 {
     if constexpr (sizeof(R) == 8) {
-        return launch_one<R, NS, 3>(ctx, kp, schedule, threads, blocks_per_sm, s);
+        return launch_one<R, NS, 19>(ctx, kp, schedule, threads, blocks_per_sm, s);
     } else {
         // trajectory logging runs the generic variants; otherwise descriptors
         // come from the parameters when they fit, and one model is constant
         const int feat = (kp.mrw ? 1 : 0) |
-                         (kp.want_traj ? 2 : ((kp.param_models ? 4 : 0) | (kp.single ? 8 : 0)));
+                         (kp.want_traj ? 2 : ((kp.param_models ? 4 : 0) | (kp.single ? 8 : 0))) |
+                         (kp.defer_events ? 16 : 0);
         switch (feat) {
         case 0: return launch_one<R, NS, 0>(ctx, kp, schedule, threads, blocks_per_sm, s);
         case 1: return launch_one<R, NS, 1>(ctx, kp, schedule, threads, blocks_per_sm, s);
@@ -1290,6 +1296,10 @@ rt_status launch_feat(rt_ctx* ctx, const TransportKP& kp, int schedule, int thre
         case 5: return launch_one<R, NS, 5>(ctx, kp, schedule, threads, blocks_per_sm, s);
         case 12: return launch_one<R, NS, 12>(ctx, kp, schedule, threads, blocks_per_sm, s);
         case 13: return launch_one<R, NS, 13>(ctx, kp, schedule, threads, blocks_per_sm, s);
+        case 18: return launch_one<R, NS, 18>(ctx, kp, schedule, threads, blocks_per_sm, s);
+        case 19: return launch_one<R, NS, 19>(ctx, kp, schedule, threads, blocks_per_sm, s);
+        case 28: return launch_one<R, NS, 28>(ctx, kp, schedule, threads, blocks_per_sm, s);
+        case 29: return launch_one<R, NS, 29>(ctx, kp, schedule, threads, blocks_per_sm, s);
         default: return fail(RT_ERR_STATE, "transport: no kernel variant for this feature set");
         }
     }
@@ -1297,6 +1307,11 @@ rt_status launch_feat(rt_ctx* ctx, const TransportKP& kp, int schedule, int thre
 
 }  // namespace
 
+#ifndef RT_TRANSPORT_NS
+// This translation unit: grid packing, finalize and the dispatcher.  The
+// transport kernel variants are compiled in transport_ns1/2/4.cu (which
+// define RT_TRANSPORT_NS and include this file), one per packed species
+// width, so the three compile in parallel.
 rt_status pack_grid(rt_grid* g, const rt_opacity* op, int lucy_mode, double lucy_tau, int prec,
                     cudaStream_t s)
 {
@@ -1376,15 +1391,21 @@ rt_status pack_grid_into(const rt_grid* g, const rt_opacity* op, int lucy_mode, 
 rt_status launch_transport(rt_ctx* ctx, const rt_opacity* op, const TransportKP& kp, int ns,
                            int prec, int schedule, int threads, int blocks_per_sm, cudaStream_t s)
 {
+    (void)op;
     const int vec = ns == 1 ? 1 : (ns == 2 ? 2 : 4);
-    if (prec == RT_PREC_FP64) {
-        if (vec == 1) return launch_feat<double, 1>(ctx, kp, schedule, threads, blocks_per_sm, s);
-        if (vec == 2) return launch_feat<double, 2>(ctx, kp, schedule, threads, blocks_per_sm, s);
-        return launch_feat<double, 4>(ctx, kp, schedule, threads, blocks_per_sm, s);
-    }
-    if (vec == 1) return launch_feat<float, 1>(ctx, kp, schedule, threads, blocks_per_sm, s);
-    if (vec == 2) return launch_feat<float, 2>(ctx, kp, schedule, threads, blocks_per_sm, s);
-    return launch_feat<float, 4>(ctx, kp, schedule, threads, blocks_per_sm, s);
+    if (vec == 1) return launch_transport_ns<1>(ctx, kp, prec, schedule, threads, blocks_per_sm, s);
+    if (vec == 2) return launch_transport_ns<2>(ctx, kp, prec, schedule, threads, blocks_per_sm, s);
+    return launch_transport_ns<4>(ctx, kp, prec, schedule, threads, blocks_per_sm, s);
 }
+#else
+template <>
+rt_status launch_transport_ns<RT_TRANSPORT_NS>(rt_ctx* ctx, const TransportKP& kp, int prec, int schedule,
+                                                int threads, int blocks_per_sm, cudaStream_t s)
+{
+    if (prec == RT_PREC_FP64)
+        return launch_feat<double, RT_TRANSPORT_NS>(ctx, kp, schedule, threads, blocks_per_sm, s);
+    return launch_feat<float, RT_TRANSPORT_NS>(ctx, kp, schedule, threads, blocks_per_sm, s);
+}
+#endif
 
 }  // namespace rtgb
