@@ -1181,7 +1181,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (NS == 4 ? 3 : RT_TR
 
 // ------------------------------------------------------------- grid packing
 template <typename PT, int NS>
-__global__ void pack_kernel(const float* rho, size_t nc, const double* kext_max_dummy, PT* out,
+__global__ void pack_kernel(const float* rho, size_t nc, double kext_max, PT* out,
                             int prec, double cell, int lucy_mode, double lucy_tau,
                             const double* kext, int nf)
 {
@@ -1199,10 +1199,16 @@ __global__ void pack_kernel(const float* rho, size_t nc, const double* kext_max_
             lucy = true;
         } else if (lucy_mode == RT_LUCY_THIN) {
             double mx = 0.0;
-            for (int j = 0; j < nf; ++j) {
-                double chi = 0.0;
-                for (int s = 0; s < NS; ++s) chi += (double)r[s] * kext[s * nf + j];
-                mx = fmax(mx, chi * cell);
+            if constexpr (NS == 1) {
+                // one species: rounding is monotonic, so the largest of
+                // fl(fl(rho kext_j) cell) over j is the one at the largest kext
+                mx = ((double)r[0] * kext_max) * cell;
+            } else {
+                for (int j = 0; j < nf; ++j) {
+                    double chi = 0.0;
+                    for (int s = 0; s < NS; ++s) chi += (double)r[s] * kext[s * nf + j];
+                    mx = fmax(mx, chi * cell);
+                }
             }
             lucy = mx < lucy_tau;
         }
@@ -1312,6 +1318,15 @@ rt_status launch_feat(rt_ctx* ctx, const TransportKP& kp, int schedule, int thre
 // transport kernel variants are compiled in transport_ns1/2/4.cu (which
 // define RT_TRANSPORT_NS and include this file), one per packed species
 // width, so the three compile in parallel.
+// largest kabs + ksca of species 0 over the frequency grid (the one-species
+// Lucy criterion), summed as the kext kernel sums it
+static double kext_max(const rt_opacity* op)
+{
+    double mx = 0.0;
+    for (int j = 0; j < op->nf; ++j) mx = std::max(mx, op->kabs[j] + op->ksca[j]);
+    return mx;
+}
+
 rt_status pack_grid(rt_grid* g, const rt_opacity* op, int lucy_mode, double lucy_tau, int prec,
                     cudaStream_t s)
 {
@@ -1329,16 +1344,16 @@ rt_status pack_grid(rt_grid* g, const rt_opacity* op, int lucy_mode, double lucy
     const int th = 256;
     const unsigned blocks = (unsigned)((nc + th - 1) / th);
     if (vec == 1)
-        pack_kernel<float, 1><<<blocks, th, 0, s>>>(g->d_rho, nc, nullptr, (float*)g->d_packed, prec,
+        pack_kernel<float, 1><<<blocks, th, 0, s>>>(g->d_rho, nc, kext_max(op), (float*)g->d_packed, prec,
                                                      g->cell, lucy_mode, lucy_tau, kext, op->nf);
     else if (vec == 2)
-        pack_kernel<float2, 2><<<blocks, th, 0, s>>>(g->d_rho, nc, nullptr, (float2*)g->d_packed,
+        pack_kernel<float2, 2><<<blocks, th, 0, s>>>(g->d_rho, nc, kext_max(op), (float2*)g->d_packed,
                                                       prec, g->cell, lucy_mode, lucy_tau, kext, op->nf);
     else if (g->ns == 3)
-        pack_kernel<float4, 3><<<blocks, th, 0, s>>>(g->d_rho, nc, nullptr, (float4*)g->d_packed,
+        pack_kernel<float4, 3><<<blocks, th, 0, s>>>(g->d_rho, nc, kext_max(op), (float4*)g->d_packed,
                                                       prec, g->cell, lucy_mode, lucy_tau, kext, op->nf);
     else
-        pack_kernel<float4, 4><<<blocks, th, 0, s>>>(g->d_rho, nc, nullptr, (float4*)g->d_packed,
+        pack_kernel<float4, 4><<<blocks, th, 0, s>>>(g->d_rho, nc, kext_max(op), (float4*)g->d_packed,
                                                       prec, g->cell, lucy_mode, lucy_tau, kext, op->nf);
     RT_CUDA(cudaGetLastError());
     RT_CUDA(cudaFreeAsync(kext, s));
@@ -1372,16 +1387,16 @@ rt_status pack_grid_into(const rt_grid* g, const rt_opacity* op, int lucy_mode, 
     kext_kernel<<<(n + 255) / 256, 256, 0, s>>>(op->d_kabs, op->d_ksca, kext, n);
     const unsigned blocks = (unsigned)((nc + 255) / 256);
     if (vec == 1)
-        pack_kernel<float, 1><<<blocks, 256, 0, s>>>(g->d_rho, nc, nullptr, (float*)dst, prec,
+        pack_kernel<float, 1><<<blocks, 256, 0, s>>>(g->d_rho, nc, kext_max(op), (float*)dst, prec,
                                                       g->cell, lucy_mode, lucy_tau, kext, op->nf);
     else if (vec == 2)
-        pack_kernel<float2, 2><<<blocks, 256, 0, s>>>(g->d_rho, nc, nullptr, (float2*)dst, prec,
+        pack_kernel<float2, 2><<<blocks, 256, 0, s>>>(g->d_rho, nc, kext_max(op), (float2*)dst, prec,
                                                        g->cell, lucy_mode, lucy_tau, kext, op->nf);
     else if (g->ns == 3)
-        pack_kernel<float4, 3><<<blocks, 256, 0, s>>>(g->d_rho, nc, nullptr, (float4*)dst, prec,
+        pack_kernel<float4, 3><<<blocks, 256, 0, s>>>(g->d_rho, nc, kext_max(op), (float4*)dst, prec,
                                                        g->cell, lucy_mode, lucy_tau, kext, op->nf);
     else
-        pack_kernel<float4, 4><<<blocks, 256, 0, s>>>(g->d_rho, nc, nullptr, (float4*)dst, prec,
+        pack_kernel<float4, 4><<<blocks, 256, 0, s>>>(g->d_rho, nc, kext_max(op), (float4*)dst, prec,
                                                        g->cell, lucy_mode, lucy_tau, kext, op->nf);
     count_launches(2);
     RT_CUDA(cudaGetLastError());
