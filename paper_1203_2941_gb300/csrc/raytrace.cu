@@ -190,50 +190,63 @@ __device__ __forceinline__ void load_eta(const float* base, float* eta)
     }
 }
 
+// Forward march.  A ray is served by NFP / 4 consecutive threads, each
+// carrying four image frequencies (one float4 of the emissivity row): the
+// threads repeat the ray's DDA (the same arithmetic, so the same chords) and
+// share its density loads, which keeps the compensated sums of a thread in
+// few registers and the SMs well occupied.
 template <int NS, int NFP>
 __global__ void __launch_bounds__(128) ray_fwd_kernel(const __grid_constant__ RayKP P)
 {
+    constexpr int G = NFP / 4;
     const int ci = blockIdx.y;
     const CamDev& cm = P.cam[ci];
     const int np = cm.npix;
-    const long long pix = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long pix = t / G;
+    const int g = (int)(t - pix * G);
     if (pix >= (long long)np * np) return;
     const int ix = (int)(pix % np), iy = (int)(pix / np);
     const int cam = P.cam0 + ci;
-    float I[NFP], Ic[NFP], tau[NFP], tc[NFP];
+    float I[4], Ic[4], tau[4], tc[4], ke[NS][4];
 #pragma unroll
-    for (int f = 0; f < NFP; ++f) { I[f] = 0.f; Ic[f] = 0.f; tau[f] = 0.f; tc[f] = 0.f; }
+    for (int q = 0; q < 4; ++q) {
+        I[q] = 0.f; Ic[q] = 0.f; tau[q] = 0.f; tc[q] = 0.f;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) ke[s][q] = P.kext[s][4 * g + q];
+    }
     Ray r = pixel_ray(cm, ix, iy, P.nx, P.ny, P.nz, false);
     unsigned nsteps = 0;
     if (r.hit) {
-        const float* eta_cam = P.eta + (size_t)cam * P.ncell * P.nfp;
+        const float* eta_cam = P.eta + (size_t)cam * P.ncell * P.nfp + 4 * g;
         float tcur = 0.f, seg;
         const int maxstep = P.nx + P.ny + P.nz + 4;
         for (int st = 0; st < maxstep; ++st) {
             ++nsteps;
             const int c = (r.i[2] * P.ny + r.i[1]) * P.nx + r.i[0];
-            float rho[NS], eta[NFP];
+            float rho[NS];
             load_rho<NS>(P, c, rho);
-            load_eta<NFP>(eta_cam + (size_t)c * NFP, eta);
+            const float4 e4 = __ldg(reinterpret_cast<const float4*>(eta_cam + (size_t)c * NFP));
+            const float eta[4] = { e4.x, e4.y, e4.z, e4.w };
             const bool inside = dda_step(r, tcur, seg, P.nx, P.ny, P.nz);
 #pragma unroll
-            for (int f = 0; f < NFP; ++f) {
+            for (int q = 0; q < 4; ++q) {
                 float chi = 0.f;
 #pragma unroll
-                for (int s = 0; s < NS; ++s) chi += rho[s] * P.kext[s][f];
+                for (int s = 0; s < NS; ++s) chi += rho[s] * ke[s][q];
                 const float dt = chi * seg;
-                const float contrib = eta[f] * seg * phi_f(dt) * __expf(-tau[f]);
-                kahan_add(I[f], Ic[f], contrib);
-                kahan_add(tau[f], tc[f], dt);
+                const float contrib = eta[q] * seg * phi_f(dt) * __expf(-tau[q]);
+                kahan_add(I[q], Ic[q], contrib);
+                kahan_add(tau[q], tc[q], dt);
             }
             if (!inside) break;
         }
     }
     float* out = P.img + ((size_t)cam * P.nfi) * np * np + pix;
 #pragma unroll
-    for (int f = 0; f < NFP; ++f)
-        if (f < P.nfi) out[(size_t)f * np * np] = I[f];
-    count_steps(P.steps, nsteps);
+    for (int q = 0; q < 4; ++q)
+        if (4 * g + q < P.nfi) out[(size_t)(4 * g + q) * np * np] = I[q];
+    count_steps(P.steps, g == 0 ? nsteps : 0u);
 }
 
 // Adjoint: pass 1 (front to back) gives tau_total and I_total per frequency;
@@ -610,7 +623,8 @@ template <int NS, int NFP>
 void launch_rays(const RayKP& kp, int npix, bool backward, cudaStream_t s)
 {
     const int th = 128;
-    dim3 grid((unsigned)(((long long)npix * npix + th - 1) / th), kp.ncam);
+    const long long nthreads = (long long)npix * npix * (backward ? 1 : NFP / 4);
+    dim3 grid((unsigned)((nthreads + th - 1) / th), kp.ncam);
     if (backward) ray_bwd_kernel<NS, NFP><<<grid, th, 0, s>>>(kp);
     else ray_fwd_kernel<NS, NFP><<<grid, th, 0, s>>>(kp);
     count_launches();
