@@ -29,6 +29,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "photon-packet cell-crossings/s"
 UNIT = "crossings/s"
+# DRAM bytes (read + write) of one full-size transport launch of this
+# workload, from a single-pass ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum, profiles/transport_kernel_r2shell128.md); to be
+# re-measured (or set to None) whenever the transport kernel changes
+TRANSPORT_DRAM_BYTES = 31.75e6 + 30.30e6
 
 
 def parse():
@@ -508,8 +513,10 @@ def main():
     peak_src = "measured" if hbm else "fallback"
     hbm = hbm or 6800.0
     achieved = bytes_alg / t_tr_s / 1e9
+    default_work = (a.n == 128 and a.tau == 10.0 and int(a.packets) == 10**7)
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-            "traffic": None, "kernel": "transport_kernel<float,1>", "peak_source": peak_src,
+            "traffic": TRANSPORT_DRAM_BYTES if default_work else None,
+            "kernel": "transport_kernel<float,1,12>", "peak_source": peak_src,
             "bytes_per_launch": bytes_alg, "launch_ms": t_tr_s * 1e3}
 
     # end to end through the public API with host buffers
