@@ -39,7 +39,7 @@ TRANSPORT_DRAM_BYTES = 31.75e6 + 30.30e6
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--packets", type=float, default=1e7)
@@ -145,11 +145,12 @@ def cpu_baseline(m, a, budget_s=12.0):
     # packet-id ranges over all host cores
     cores = os.cpu_count() or 1
     T0 = O.temperature_guess(m)
+    n1 = 2000 * cores
     t0 = time.perf_counter()
-    O.transport(om, N, seed=98, pid_begin=0, pid_end=200 * cores, mode=O.MODE_FROZEN_T, T_prev=T0,
+    O.transport(om, N, seed=98, pid_begin=0, pid_end=n1, mode=O.MODE_FROZEN_T, T_prev=T0,
                 n_threads=cores)
     dt = time.perf_counter() - t0
-    n2 = max(200 * cores, min(int(200 * cores * 0.6 * budget_s / max(dt, 1e-3)), 2000000))
+    n2 = max(n1, min(int(n1 * 0.6 * budget_s / max(dt, 1e-3)), 4000000))
     t0 = time.perf_counter()
     r2 = O.transport(om, N, seed=98, pid_begin=0, pid_end=n2, mode=O.MODE_FROZEN_T, T_prev=T0,
                      n_threads=cores)
