@@ -147,6 +147,14 @@ typedef struct {
                                  and finished by a second pass after every other
                                  packet, so slow packets do not hold up the warps
                                  (a full queue leaves the packet where it is) */
+    uint32_t source_bins;     /* 0 = source and frequency bin drawn per packet with
+                                 probability ~ L_nu dnu.  m > 0: the source grid of
+                                 Eq. 1 -- the sources' combined luminosity is cut
+                                 into m bins of equal energy L/m and packet pid is
+                                 emitted from bin b = floor(pid m / N), at the point
+                                 (b + 1/2) / m of the cumulative luminosity (its
+                                 source, then its frequency bin); N/m packets per
+                                 bin when m divides N */
 } rt_transport_params;
 
 /* Fill p with the defaults: B&W, Lucy THIN at 1e-2, linear form, MRW off

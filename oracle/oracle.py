@@ -62,7 +62,8 @@ class _Params(C.Structure):
                 ("lucy_tau", C.c_double), ("mrw", C.c_int), ("mrw_tau_cell", C.c_double),
                 ("mrw_gamma", C.c_double), ("seed", C.c_uint64), ("model_id", C.c_uint32),
                 ("n_packets", C.c_uint64), ("pid_begin", C.c_uint64), ("pid_end", C.c_uint64),
-                ("max_events", C.c_uint64), ("record_events", C.c_int)]
+                ("max_events", C.c_uint64), ("record_events", C.c_int),
+                ("source_bins", C.c_uint32)]
 
 
 EVENT_DTYPE = np.dtype([("cell", "<u4"), ("nu", "<u4"), ("species", "<u4"), ("pad", "<u4"),
@@ -185,7 +186,7 @@ def transport(model, n_packets, seed=1, model_id=0, mode=MODE_BW, lucy_mode=LUCY
               lucy_form=LUCY_LINEAR, lucy_tau=1e-2, mrw=False, mrw_tau_cell=10.0, mrw_gamma=2.0,
               pid_begin=0, pid_end=None, max_events=10_000_000, record_events=False,
               event_cap=0, pah_cap=0, traj_cap=0, T_prev=None, n_threads=1, esq=True,
-              accumulate=None):
+              accumulate=None, source_bins=0):
     """Run packets [pid_begin, pid_end) of an N = n_packets emission and return
     a dict of numpy arrays (E_abs, count, esq, sed_esc, sed_cnt, events, pah,
     traj, stats).  ``accumulate`` may hold a previous result dict whose
@@ -194,7 +195,8 @@ def transport(model, n_packets, seed=1, model_id=0, mode=MODE_BW, lucy_mode=LUCY
     L = lib()
     pid_end = n_packets if pid_end is None else pid_end
     p = _Params(mode, lucy_mode, lucy_form, lucy_tau, int(bool(mrw)), mrw_tau_cell, mrw_gamma,
-                seed, model_id, n_packets, pid_begin, pid_end, max_events, int(bool(record_events)))
+                seed, model_id, n_packets, pid_begin, pid_end, max_events, int(bool(record_events)),
+                int(source_bins))
     nc, ns, nf = om.ncell, om.ns, om.nf
     if accumulate is not None:
         E = accumulate["E_abs"].copy(); cnt = accumulate["count"].copy()

@@ -435,9 +435,31 @@ static void run_packet(const or_ctx* C, or_out* o, uint64_t pid)
     uint32_t seq = 0;
 
     /* emission (Sect. 2): source, frequency bin, isotropic direction */
-    int si = 0;
-    if (C->nsrc > 1) si = pick_cdf(C->src_L, C->nsrc, rng_u(&r));
-    int j = pick_cdf(C->src_w + (size_t)si * m->nf, m->nf, rng_u(&r));
+    int si = 0, j = 0;
+    if (p->source_bins == 0) {
+        if (C->nsrc > 1) si = pick_cdf(C->src_L, C->nsrc, rng_u(&r));
+        j = pick_cdf(C->src_w + (size_t)si * m->nf, m->nf, rng_u(&r));
+    } else {
+        /* Eq. 1: the sources' combined luminosity is cut into m bins of equal
+         * energy L/m, and N/m packets are emitted in each: packet pid belongs
+         * to bin b = floor(pid m / N) and takes the point u = (b + 1/2) / m of
+         * the cumulative luminosity -- the source where the running sum of
+         * the L_i first reaches u L, then, by the fraction of that source's
+         * luminosity below the point, its frequency bin. */
+        const uint64_t b = (pid * (uint64_t)p->source_bins) / p->n_packets;
+        const double u = ((double)b + 0.5) / (double)p->source_bins;
+        double tot = 0.0;
+        for (int i = 0; i < C->nsrc; ++i) tot += C->src_L[i];
+        const double target = u * tot;
+        double below = 0.0, upto = 0.0;
+        for (si = 0; si < C->nsrc; ++si) {
+            upto = below + C->src_L[si];
+            if (upto >= target || si == C->nsrc - 1) break;
+            below = upto;
+        }
+        const double uf = (target - below) / (upto - below);
+        j = pick_cdf(C->src_w + (size_t)si * m->nf, m->nf, uf);
+    }
     double k[3], x[3];
     { double u1 = rng_u(&r), u2 = rng_u(&r); iso_dir(u1, u2, k); }
     for (int a = 0; a < 3; ++a) x[a] = C->src[si].pos[a];

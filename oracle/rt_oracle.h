@@ -48,6 +48,9 @@ typedef struct {
     uint32_t model_id;
     uint64_t n_packets, pid_begin, pid_end, max_events;
     int record_events;
+    uint32_t source_bins;   /* 0: source and bin drawn at random (prob. ~ L_nu dnu);
+                               m > 0: Eq. 1 equal-energy source bins, packet pid
+                               from bin floor(pid m / N) (see or_transport) */
 } or_params;
 
 typedef struct { uint32_t cell, nu, species, pad; double k[3]; } or_event;

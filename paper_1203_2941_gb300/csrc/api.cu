@@ -216,6 +216,7 @@ void rt_transport_params_default(rt_transport_params* p)
     p->blocks_per_sm = 0;
     p->march_min_active = -1;
     p->defer_events = 0;
+    p->source_bins = 0;
 }
 
 }  // extern "C"
@@ -239,6 +240,9 @@ static rt_status check_params(const rt_transport_params* p)
         return fail(RT_ERR_INVALID_ARG, "transport: threads_per_block must be a multiple of 32 in 32..256");
     if (p->blocks_per_sm < 0 || p->blocks_per_sm > 64) return fail(RT_ERR_INVALID_ARG, "transport: blocks_per_sm must be 0..64");
     if (p->max_events == 0) return fail(RT_ERR_INVALID_ARG, "transport: max_events must be > 0");
+    if (p->source_bins > 0 && ((double)p->source_bins > (double)p->n_packets ||
+                               (double)p->source_bins * (double)p->n_packets > 9.0e18))
+        return fail(RT_ERR_INVALID_ARG, "transport: source_bins must be <= n_packets with n_packets * source_bins < 9e18");
     return RT_OK;
 }
 
@@ -314,6 +318,7 @@ static rt_status make_model(const rt_grid* g, const rt_opacity* op, const rt_sou
     m.log2_4piV = 2.0 * log2(g->cell);
     for (int a = 0; a < 3; ++a) m.box_min[a] = g->box_min[a];
     m.pid_begin = pid_begin;
+    m.n_emit = n_packets;
     m.E_abs = o->E_abs; m.count = o->count; m.esq = o->esq;
     m.sed_esc = o->sed_esc; m.sed_cnt = (unsigned long long*)o->sed_cnt;
     m.T_prev = T_prev;
@@ -414,6 +419,7 @@ static void fill_kp(TransportKP& kp, const rt_opacity* op, const rt_transport_pa
     kp.smem_sed = 0;
     kp.smem_cdf = 0;
     kp.max_events = p->max_events;
+    kp.source_bins = p->source_bins;
     kp.defer_events = 0;               // set by rt_transport when it allocates a queue
     kp.defer = nullptr;
     kp.defer_n = nullptr;

@@ -110,6 +110,7 @@ struct ModelDev {
     double log2_4piV;          // log2(4 pi V / cell) for the packed FP32 density rho*cell
     double box_min[3];
     uint64_t pid_begin;
+    uint64_t n_emit;           // N of the model's emission (packet ids 0..N-1)
     const double* src_pos;     // [nsrc][3] in cell units
     const double* src_Lcdf;    // [nsrc] cumulative luminosity
     const double* src_cdf64;   // [nsrc][nf] cumulative L_nu dnu
@@ -156,6 +157,7 @@ struct TransportKP {
     // dynamic shared-memory layout (byte offsets, set by the launcher)
     int so_sed, so_cnt, so_op, so_mrw, so_cdf, so_ctr, so_claim;
     unsigned long long max_events;
+    unsigned long long source_bins;     // 0: random source bins; m: Eq. 1 equal-energy bins
     unsigned long long defer_events;    // 0 = off
     DeferRec* defer;                    // queue (main pass appends, resume pass reads)
     unsigned long long* defer_n;        // queue cursor (device)

@@ -550,11 +550,24 @@ struct Kernel {
         L.ncross = 0;
         L.nlucy = 0;
         int si = 0;
-        if (md->nsrc > 1) {
-            const double u = (double)U(L);
-            si = search_cdf(md->src_Lcdf, md->nsrc, u * md->src_Lcdf[md->nsrc - 1]);
+        R ub;
+        if (P.source_bins) {
+            // Eq. 1: equal-energy source bins, packet pid from bin floor(pid m / N)
+            // at the point (b + 1/2) / m of the cumulative luminosity: its source,
+            // then (by the fraction of that source below the point) its bin
+            const uint64_t pid = ((uint64_t)L.rng.phi << 32) | L.rng.plo;
+            const uint64_t b = (pid * P.source_bins) / md->n_emit;
+            const double target = ((double)b + 0.5) / (double)P.source_bins * md->src_Lcdf[md->nsrc - 1];
+            si = search_cdf(md->src_Lcdf, md->nsrc, target);
+            const double below = si > 0 ? md->src_Lcdf[si - 1] : 0.0;
+            ub = (R)((target - below) / (md->src_Lcdf[si] - below));
+        } else {
+            if (md->nsrc > 1) {
+                const double u = (double)U(L);
+                si = search_cdf(md->src_Lcdf, md->nsrc, u * md->src_Lcdf[md->nsrc - 1]);
+            }
+            ub = U(L);
         }
-        const R ub = U(L);
         if constexpr (DBG) {
             const double* cdf = md->src_cdf64 + (size_t)si * P.nf;
             L.j = search_cdf(cdf, P.nf, ub * cdf[P.nf - 1]);

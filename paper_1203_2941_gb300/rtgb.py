@@ -53,7 +53,8 @@ class rt_transport_params(C.Structure):
                 ("n_packets", C.c_uint64), ("pid_begin", C.c_uint64), ("pid_end", C.c_uint64),
                 ("max_events", C.c_uint64), ("record_events", C.c_int), ("precision", C.c_int),
                 ("schedule", C.c_int), ("threads_per_block", C.c_int), ("blocks_per_sm", C.c_int),
-                ("march_min_active", C.c_int), ("defer_events", C.c_uint64)]
+                ("march_min_active", C.c_int), ("defer_events", C.c_uint64),
+                ("source_bins", C.c_uint32)]
 
 
 class rt_transport_out(C.Structure):

@@ -189,7 +189,7 @@ def make_params(n_packets: int, mode=R.RT_MODE_BW, lucy_mode=R.RT_LUCY_THIN,
                 mrw_gamma=2.0, seed=1, model_id=0, pid_begin=0, pid_end=None,
                 max_events=10_000_000, record_events=False, precision=R.RT_PREC_FP32,
                 schedule=R.RT_SCHED_PERSISTENT, threads_per_block=0, blocks_per_sm=0,
-                march_min_active=-1, defer_events=0) -> R.rt_transport_params:
+                march_min_active=-1, defer_events=0, source_bins=0) -> R.rt_transport_params:
     p = R.rt_transport_params_default()
     p.mode, p.lucy_mode, p.lucy_form, p.lucy_tau = mode, lucy_mode, lucy_form, lucy_tau
     p.mrw, p.mrw_tau_cell, p.mrw_gamma = int(bool(mrw)), mrw_tau_cell, mrw_gamma
@@ -203,6 +203,7 @@ def make_params(n_packets: int, mode=R.RT_MODE_BW, lucy_mode=R.RT_LUCY_THIN,
     p.threads_per_block, p.blocks_per_sm = threads_per_block, blocks_per_sm
     p.march_min_active = march_min_active
     p.defer_events = int(defer_events)
+    p.source_bins = int(source_bins)
     return p
 
 

@@ -12,6 +12,7 @@
 * Edge cases: empty grid, source on a cell face, empty packet range, event
   and PAH buffer overflow, the per-packet event cap, ragged grid shapes.
 """
+import copy
 import math
 
 import numpy as np
@@ -164,6 +165,40 @@ def test_deferred_packets_keep_their_trajectories(rt, ctx, O, schedule):
     st = out.stats_dict()
     assert st["deferred"] > 0 and st["escaped"] == 20000 and st["stuck"] == 0
     assert abs(out.numpy()["sed_esc"].sum() / m.luminosity - 1) < 1e-9
+
+
+def test_equal_energy_source_bins_match_oracle(rt, ctx, O):
+    """Eq. 1 source grid (source_bins = m): FP64 trajectories equal the
+    oracle's; in FP32 the emission histogram (empty grid, every packet escapes
+    at its emission frequency) equals the oracle's bin by bin."""
+    m = W.random_grid(n=(6, 5, 4), ns=2, seed=15, tau_scale=1.5, albedo=(0.3, 0.7))
+    m.sources = [W.Source(m.sources[0].pos, 2.0 * W.LSUN, 5800.0),
+                 W.Source(tuple(0.5 * np.asarray(m.sources[0].pos)), 1.0 * W.LSUN, 3500.0)]
+    grid, opac, srcs = _setup(rt, ctx, m)
+    T0 = np.random.default_rng(4).uniform(50, 800, size=(m.ns, m.ncell))
+    N = 1200
+    out = rt.transport(ctx, grid, opac, srcs, N, mode=rt.rtgb.RT_MODE_FROZEN_T,
+                       precision=rt.rtgb.RT_PREC_FP64, T_prev=torch.tensor(T0, device="cuda"),
+                       traj_cap=600 * N, seed=21, source_bins=120)
+    torch.cuda.synchronize()
+    ref = O.transport(m, N, seed=21, mode=O.MODE_FROZEN_T, T_prev=T0, traj_cap=600 * N,
+                      source_bins=120)
+    _traj_compare(out.traj_numpy(), ref["traj"], m.cell * 7)
+    e = copy.deepcopy(m)
+    e.rho = np.zeros_like(m.rho)
+    g0, o0, s0 = _setup(rt, ctx, e)
+    N = 240000
+    out = rt.transport(ctx, g0, o0, s0, N, mode=rt.rtgb.RT_MODE_NOREEMIT, seed=3, source_bins=4000)
+    torch.cuda.synchronize()
+    ref = O.transport(e, N, seed=3, mode=O.MODE_NOREEMIT, source_bins=4000)
+    hg = out.numpy()["sed_cnt"].sum(axis=0)
+    hr = ref["sed_cnt"].sum(axis=0)
+    assert hg.sum() == hr.sum() == N
+    # FP32 bin searches may move a source bin across a frequency-bin edge only
+    # where its midpoint lies within FP32 rounding of the edge
+    assert np.abs(hg - hr).sum() <= 2 * (N // 4000)
+    with pytest.raises(rt.RtError):
+        rt.transport(ctx, g0, o0, s0, 100, source_bins=101)
 
 
 def test_fp64_pah_and_noreemit_match_oracle(rt, ctx, O):

@@ -447,3 +447,44 @@ def test_adjoint_zero_where_no_ray_passes(O):
     g = g.reshape(6, 6, 6)
     assert np.all(g[:, 0, :] == 0) and np.all(g[:, :, 0] == 0)
     assert np.abs(g[:, 2:4, 2:4]).sum() > 0
+
+
+def test_equal_energy_source_bins(O):
+    """Eq. 1 source grid: with the sources' luminosity cut into m bins of
+    equal energy and N/m packets per bin, the packets emitted into each model
+    frequency bin carry its energy sum_s L_nu,s dnu to within one source bin
+    (L/m) per source, and each source receives its share of L to within one
+    source bin.  An
+    empty grid with re-emission off lets every packet escape at its emission
+    frequency, so the escape tallies are the emission histogram."""
+    m = W.uniform_cube(n=3, tau_cell=0.5, nf=24, gray=False)
+    m.rho[:] = 0.0
+    m.sources = [W.Source((0.1 * m.cell, 0.2 * m.cell, 0.0), 2.0 * W.LSUN, 5800.0),
+                 W.Source((-0.3 * m.cell, 0.0, 0.1 * m.cell), 1.0 * W.LSUN, 3000.0)]
+    Ltot = 3.0 * W.LSUN
+    for mbins in (60, 600):
+        N = 30 * mbins
+        r = O.transport(m, N, seed=3, mode=O.MODE_NOREEMIT, source_bins=mbins)
+        assert r["stats"]["escaped"] == N
+        counts = r["sed_cnt"].sum(axis=0)
+        E_emit = counts * (Ltot / N)
+        E_true = np.zeros(m.nf)
+        for s in m.sources:
+            lnu = O.source_lnu(m, m.sources.index(s))
+            E_true += lnu * m.dnu
+        assert np.all(np.abs(E_emit - E_true) <= len(m.sources) * Ltot / mbins * (1 + 1e-9))
+        assert np.abs(E_emit - E_true).max() > 0                 # not trivially exact
+        # each source's packets (told apart by position at emission) carry its L
+        r_t = O.transport(m, N, seed=3, mode=O.MODE_NOREEMIT, source_bins=mbins, traj_cap=3 * N)
+        em = r_t["traj"][r_t["traj"]["type"] == O.T_EMIT]
+        n0 = int(np.sum(np.abs(em["x"][:, 0] - m.sources[0].pos[0]) < 1e-3 * m.cell))
+        assert abs(n0 * Ltot / N - m.sources[0].L) <= Ltot / mbins * (1 + 1e-9)
+    # stratification: packet ids of one source bin share one frequency bin,
+    # independent of the seed
+    r1 = O.transport(m, 600, seed=1, mode=O.MODE_NOREEMIT, source_bins=60, traj_cap=10000)
+    r2 = O.transport(m, 600, seed=9, mode=O.MODE_NOREEMIT, source_bins=60, traj_cap=10000)
+    e1 = np.sort(r1["traj"][r1["traj"]["type"] == O.T_EMIT], order="pid")
+    e2 = np.sort(r2["traj"][r2["traj"]["type"] == O.T_EMIT], order="pid")
+    np.testing.assert_array_equal(e1["nu"], e2["nu"])
+    nu = e1["nu"].reshape(60, 10)
+    assert np.all(nu == nu[:, :1])
