@@ -121,6 +121,20 @@ enum { RT_PREC_FP32 = 0,      /* production: FP32 transport, FP64 accumulators *
 enum { RT_SCHED_PERSISTENT = 0, /* all SMs, dynamic packet refill */
        RT_SCHED_SERIAL = 1 };   /* one GPU thread, packets in id order (debug) */
 
+/* A photon-counting camera (Sect. 4: photons escaping into a solid angle
+ * are counted and converted into a flux): packets that leave the grid with
+ * k . k_obs >= cos_accept add their power xi to the pixel of their exit
+ * point projected on the image plane.  Frame as in rt_raytrace: k_obs from
+ * (theta, phi), image axes e_x' = (-sin phi, cos phi, 0), e_y' = (-cos theta
+ * cos phi, -cos theta sin phi, sin theta), image centred on the box centre,
+ * npix^2 pixels of `pixel` cm (0 = box diagonal / npix). */
+typedef struct {
+    double theta, phi;
+    int npix;
+    double pixel;
+    double cos_accept;
+} rt_pc_camera;
+
 typedef struct {
     int mode;                 /* RT_MODE_* */
     int lucy_mode;            /* RT_LUCY_* */
@@ -155,6 +169,9 @@ typedef struct {
                                  (b + 1/2) / m of the cumulative luminosity (its
                                  source, then its frequency bin); N/m packets per
                                  bin when m divides N */
+    const rt_pc_camera* pc_cams;  /* host [n_pc_cams] photon-counting cameras
+                                 (rt_transport only; NULL with 0 = none) */
+    int n_pc_cams;            /* 0..16 (rt_transport only) */
 } rt_transport_params;
 
 /* Fill p with the defaults: B&W, Lucy THIN at 1e-2, linear form, MRW off
@@ -214,7 +231,11 @@ enum {
  *   events/pah/traj: append buffers (NULL with cap 0 to disable); the cursor
  *           is stats[RT_STAT_N_*]; entries beyond the capacity are counted in
  *           the *_DROPPED stats and not written.
- *   stats   [RT_STAT_COUNT] uint64 (required). */
+ *   stats   [RT_STAT_COUNT] uint64 (required).
+ *   pc_img  device double, one [n_freq][npix][npix] block per photon-counting
+ *           camera (camera c after the blocks of cameras 0..c-1): power
+ *           (erg/s) of the packets it counted, per frequency bin and pixel
+ *           (required when p->n_pc_cams > 0). */
 typedef struct {
     double* E_abs;
     uint32_t* count;
@@ -225,6 +246,7 @@ typedef struct {
     rt_pah_event* pah; uint64_t pah_cap;
     rt_traj* traj; uint64_t traj_cap;
     uint64_t* stats;
+    double* pc_img;
 } rt_transport_out;
 
 /* Transport N = p->n_packets equal-energy packets (packets [pid_begin,
@@ -239,8 +261,10 @@ typedef struct {
  * Random numbers: Philox4x32-10, key (seed_lo, seed_hi ^ model_id), counter
  * (draw/2, 0, pid_lo, pid_hi); the k-th draw of a packet is the uniform
  * ((w >> 11) + 1) 2^-53 (FP64) or ((w >> 40) + 1) 2^-24 (FP32) of 64-bit word
- * k mod 2 of block k/2.  Errors: RT_ERR_INVALID_ARG (ranges, pointers,
- * precision/mode combinations), RT_ERR_CUDA. */
+ * k mod 2 of block k/2.  Photon-counting cameras (p->pc_cams, Sect. 4) add
+ * each escaping packet's power to out->pc_img (accumulated, not cleared).
+ * Errors: RT_ERR_INVALID_ARG (ranges, pointers, precision/mode combinations),
+ * RT_ERR_CUDA. */
 RT_API rt_status rt_transport(rt_ctx* ctx, const rt_grid* grid, const rt_opacity* opac,
                        const rt_source* sources, int n_sources,
                        const rt_transport_params* p, const double* T_prev,
@@ -265,7 +289,8 @@ RT_API rt_status rt_transport(rt_ctx* ctx, const rt_grid* grid, const rt_opacity
  * that device current) and should come before any stream capture.  All calls
  * share the one array: calls whose GPU work overlaps (different streams
  * without ordering, or several host threads) race and must not be issued;
- * calls ordered on one stream are safe (each clears what must start at zero). */
+ * calls ordered on one stream are safe (each clears what must start at zero).
+ * Photon-counting cameras are not served here (n_pc_cams must be 0). */
 RT_API rt_status rt_transport_noalloc(rt_ctx* ctx, const rt_grid* grid, const rt_opacity* opac,
                                       const rt_source* sources, int n_sources,
                                       const rt_transport_params* p, const double* T_prev,
@@ -342,6 +367,24 @@ RT_API rt_status rt_raytrace_backward(rt_ctx* ctx, const rt_grid* grid, const rt
                                const float* dL_dimg, const double* dL_dsed, float* dL_drho,
                                double* dL_dscale, uint64_t* ray_steps, rt_stream stream);
 
+/* Complex visibilities of ray-traced images.  Sect. 4 names visibilities
+ * among the ray tracer's products without a formula; this is the plain
+ * definition: for image (c, f) of rt_raytrace's output,
+ *   V(u, v) = sum over pixels of I A_pix / D^2 exp(-2 pi i (u alpha + v beta)),
+ * alpha, beta = the pixel centre's offsets along the image axes (e_x', e_y')
+ * divided by D (small-angle sky coordinates, radians), so V(0, 0) is the
+ * image's part of the SED.
+ *   cams: host [n_cams], as passed to rt_raytrace for this grid (the default
+ *   pixel size comes from the grid), 1..1024 cameras with one npix <= 8192;
+ *   images: device [n_cams][n_f][npix][npix] float; n_f 1..16;
+ *   uv: host [n_uv][2] doubles, cycles per radian along e_x', e_y' (a
+ *   projected baseline divided by the wavelength), n_uv 1..65535;
+ *   vis: device [n_cams][n_f][n_uv][2] double (real, imaginary part).
+ * Errors: RT_ERR_INVALID_ARG on NULL pointers or sizes out of range. */
+RT_API rt_status rt_visibilities(rt_ctx* ctx, const rt_grid* grid, const rt_camera* cams, int n_cams,
+                                 const float* images, int n_f, const double* uv, int n_uv,
+                                 double* vis, rt_stream stream);
+
 /* ---------------------------------------------------------------------------
  * Batched transport: many models of uneven grid size in one persistent launch
  * (no counterpart in the paper; packets of all models share the warps).
@@ -359,7 +402,7 @@ typedef struct {
 /* Prepare a batch: packs every grid, uploads the model table and source
  * tables (host-synchronous).  The batch keeps pointers to the grids and the
  * output buffers; they must outlive it.  n_models in 1..4096; all grids share
- * `opac` and must have its species count. */
+ * `opac` and must have its species count; p->n_pc_cams must be 0. */
 RT_API rt_status rt_batch_create(rt_ctx* ctx, const rt_opacity* opac, int n_models,
                           const rt_model* models, const rt_transport_params* p,
                           rt_batch** out);

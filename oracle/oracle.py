@@ -63,7 +63,12 @@ class _Params(C.Structure):
                 ("mrw_gamma", C.c_double), ("seed", C.c_uint64), ("model_id", C.c_uint32),
                 ("n_packets", C.c_uint64), ("pid_begin", C.c_uint64), ("pid_end", C.c_uint64),
                 ("max_events", C.c_uint64), ("record_events", C.c_int),
-                ("source_bins", C.c_uint32)]
+                ("source_bins", C.c_uint32), ("pc", C.c_void_p), ("n_pc", C.c_int)]
+
+
+class _PcCamera(C.Structure):
+    _fields_ = [("theta", C.c_double), ("phi", C.c_double), ("npix", C.c_int),
+                ("pixel", C.c_double), ("cos_accept", C.c_double)]
 
 
 EVENT_DTYPE = np.dtype([("cell", "<u4"), ("nu", "<u4"), ("species", "<u4"), ("pad", "<u4"),
@@ -79,7 +84,7 @@ class _Out(C.Structure):
                 ("events", C.c_void_p), ("event_cap", C.c_uint64), ("n_events", C.c_uint64),
                 ("pah", C.c_void_p), ("pah_cap", C.c_uint64), ("n_pah", C.c_uint64),
                 ("traj", C.c_void_p), ("traj_cap", C.c_uint64), ("n_traj", C.c_uint64),
-                ("stats", C.c_uint64 * 16)]
+                ("stats", C.c_uint64 * 16), ("pc_img", C.c_void_p)]
 
 
 class _Camera(C.Structure):
@@ -186,11 +191,13 @@ def transport(model, n_packets, seed=1, model_id=0, mode=MODE_BW, lucy_mode=LUCY
               lucy_form=LUCY_LINEAR, lucy_tau=1e-2, mrw=False, mrw_tau_cell=10.0, mrw_gamma=2.0,
               pid_begin=0, pid_end=None, max_events=10_000_000, record_events=False,
               event_cap=0, pah_cap=0, traj_cap=0, T_prev=None, n_threads=1, esq=True,
-              accumulate=None, source_bins=0):
+              accumulate=None, source_bins=0, pc_cameras=()):
     """Run packets [pid_begin, pid_end) of an N = n_packets emission and return
     a dict of numpy arrays (E_abs, count, esq, sed_esc, sed_cnt, events, pah,
-    traj, stats).  ``accumulate`` may hold a previous result dict whose
-    accumulators are continued (the B&W temperatures then see them)."""
+    traj, stats, pc_img).  ``accumulate`` may hold a previous result dict whose
+    accumulators are continued (the B&W temperatures then see them).
+    ``pc_cameras``: (theta, phi, npix, pixel, cos_accept) tuples of
+    photon-counting cameras; pc_img is a list of [nf, npix, npix] images."""
     om = _om(model)
     L = lib()
     pid_end = n_packets if pid_end is None else pid_end
@@ -198,6 +205,14 @@ def transport(model, n_packets, seed=1, model_id=0, mode=MODE_BW, lucy_mode=LUCY
                 seed, model_id, n_packets, pid_begin, pid_end, max_events, int(bool(record_events)),
                 int(source_bins))
     nc, ns, nf = om.ncell, om.ns, om.nf
+    pcs = [tuple(c) for c in pc_cameras]
+    pc_arr = (_PcCamera * max(1, len(pcs)))(*[_PcCamera(float(c[0]), float(c[1]), int(c[2]),
+                                                         float(c[3]), float(c[4])) for c in pcs])
+    if pcs:
+        p.pc, p.n_pc = C.cast(pc_arr, C.c_void_p), len(pcs)
+    pc_img = np.zeros(sum(nf * int(c[2]) ** 2 for c in pcs))
+    if accumulate is not None and pcs:
+        pc_img = np.concatenate([a.reshape(-1) for a in accumulate["pc_img"]]).copy()
     if accumulate is not None:
         E = accumulate["E_abs"].copy(); cnt = accumulate["count"].copy()
         q = accumulate["esq"].copy() if esq else None
@@ -213,15 +228,21 @@ def transport(model, n_packets, seed=1, model_id=0, mode=MODE_BW, lucy_mode=LUCY
                _ptr(ev) if event_cap else None, event_cap, 0,
                _ptr(pah) if pah_cap else None, pah_cap, 0,
                _ptr(tr) if traj_cap else None, traj_cap, 0)
+    out.pc_img = _ptr(pc_img) if pcs else None
     Tp = None if T_prev is None else np.ascontiguousarray(T_prev, dtype=np.float64).reshape(ns, nc)
     rc = L.or_transport(C.byref(om.c), om.srcs, om.nsrc, C.byref(p), _ptr(Tp), C.byref(out),
                         int(n_threads))
     if rc != 0:
         raise ValueError("oracle transport rejected its arguments")
     stats = {k: int(out.stats[i]) for i, k in enumerate(STAT_NAMES)}
+    imgs, o = [], 0
+    for c in pcs:
+        n = int(c[2])
+        imgs.append(pc_img[o:o + nf * n * n].reshape(nf, n, n))
+        o += nf * n * n
     return dict(E_abs=E, count=cnt, esq=q, sed_esc=sed, sed_cnt=sc,
                 events=ev[:out.n_events], pah=pah[:out.n_pah], traj=tr[:out.n_traj],
-                stats=stats, xi=model_luminosity(om) / n_packets)
+                stats=stats, xi=model_luminosity(om) / n_packets, pc_img=imgs)
 
 
 def model_luminosity(om):
@@ -356,3 +377,24 @@ def raytrace_backward(model, T, events, xi_ev, cams, fidx, dL_dimg, dL_dsed):
                                om.srcs, om.nsrc, _cams(cams), len(cams), _ptr(fi), len(fi),
                                _ptr(gi), _ptr(gs), _ptr(drho), _ptr(dscale))
     return drho, float(dscale[0])
+
+
+def visibilities(model, images, cams, uv):
+    """Complex visibilities of ray-traced images by their plain definition
+    (FP64): V(u, v) = sum over pixels of I A_pix / D^2 exp(-2 pi i (u alpha +
+    v beta)), alpha and beta the pixel centre's offsets along the image axes
+    divided by D; images [n_cams][n_f][npix][npix] as or_raytrace returns
+    them, uv [n_uv][2] in cycles per radian."""
+    images = np.asarray(images, dtype=np.float64)
+    uv = np.asarray(uv, dtype=np.float64).reshape(-1, 2)
+    nx, ny, nz = model.rho.shape[3], model.rho.shape[2], model.rho.shape[1]
+    diag = model.cell * np.sqrt(float(nx * nx + ny * ny + nz * nz))
+    out = np.zeros(images.shape[:2] + (len(uv),), dtype=np.complex128)
+    for c, cam in enumerate(cams):
+        npix = images.shape[-1]
+        pix = cam.pixel if cam.pixel > 0 else diag / cam.npix
+        a = (np.arange(npix) + 0.5 - 0.5 * npix) * pix / cam.D
+        for k, (u, v) in enumerate(uv):
+            ph = np.exp(-2j * np.pi * (u * a[None, :] + v * a[:, None]))   # [y][x]
+            out[c, :, k] = (images[c] * ph[None]).sum(axis=(1, 2)) * pix * pix / (cam.D * cam.D)
+    return out

@@ -424,6 +424,52 @@ static int pick_species(const or_model* m, int64_t c, int j, int sca, double u)
     return pick_cdf(w, m->ns, u);
 }
 
+/* Observer direction k_obs (from the model towards the observer) for
+ * (theta, phi); image axes e_x' = (-sin phi, cos phi, 0) and
+ * e_y' = (-cos theta cos phi, -cos theta sin phi, sin theta), so that
+ * (e_x', e_y', k_obs) is right handed and e_y' follows +z. */
+static void obs_frame(double theta, double phi, double kobs[3], double ex[3], double ey[3])
+{
+    double st = sin(theta), ct = cos(theta), sp = sin(phi), cp = cos(phi);
+    kobs[0] = st * cp; kobs[1] = st * sp; kobs[2] = ct;
+    ex[0] = -sp; ex[1] = cp; ex[2] = 0.0;
+    ey[0] = -ct * cp; ey[1] = -ct * sp; ey[2] = st;
+}
+
+/* Photon counting (Sect. 4): an escaping packet whose direction lies in a
+ * camera's acceptance cone, k . k_obs >= cos_accept, adds its power xi to the
+ * pixel that holds its exit point x projected on the image plane,
+ * x' = (x - centre) . e_x', y' = (x - centre) . e_y', pixel
+ * (floor(x'/p + npix/2), floor(y'/p + npix/2)); points outside the image
+ * are not counted. */
+static void pc_count(const or_model* m, const or_params* p, or_out* o, const double x[3],
+                     const double k[3], int j, double xi)
+{
+    if (!p->pc || !o->pc_img) return;
+    int nn[3] = { m->nx, m->ny, m->nz };
+    double rel[3];
+    for (int a = 0; a < 3; ++a) rel[a] = x[a] - (m->box_min[a] + 0.5 * nn[a] * m->cell);
+    size_t off = 0;
+    for (int c = 0; c < p->n_pc; ++c) {
+        const or_pc_camera* cam = &p->pc[c];
+        const int n = cam->npix;
+        double kobs[3], ex[3], ey[3];
+        obs_frame(cam->theta, cam->phi, kobs, ex, ey);
+        double pix = cam->pixel;
+        if (!(pix > 0.0))
+            pix = m->cell * sqrt((double)nn[0] * nn[0] + (double)nn[1] * nn[1] + (double)nn[2] * nn[2]) / n;
+        double kd = k[0] * kobs[0] + k[1] * kobs[1] + k[2] * kobs[2];
+        if (kd >= cam->cos_accept) {
+            double xp = rel[0] * ex[0] + rel[1] * ex[1] + rel[2] * ex[2];
+            double yp = rel[0] * ey[0] + rel[1] * ey[1] + rel[2] * ey[2];
+            double fx = floor(xp / pix + 0.5 * n), fy = floor(yp / pix + 0.5 * n);
+            if (fx >= 0.0 && fx < n && fy >= 0.0 && fy < n)
+                o->pc_img[off + ((size_t)j * n + (size_t)fy) * n + (size_t)fx] += xi;
+        }
+        off += (size_t)m->nf * n * n;
+    }
+}
+
 /* One packet, from emission to escape (or termination). */
 static void run_packet(const or_ctx* C, or_out* o, uint64_t pid)
 {
@@ -478,6 +524,7 @@ static void run_packet(const or_ctx* C, or_out* o, uint64_t pid)
             if (b > 9) b = 9;
             o->sed_esc[b * m->nf + j] += C->xi;
             o->sed_cnt[b * m->nf + j] += 1;
+            pc_count(m, p, o, x, k, j, C->xi);
             o->stats[OR_S_ESCAPE]++;
             log_event(o, pid, &seq, OR_T_ESCAPE, last_cell, j, x, k);
             return;
@@ -636,6 +683,9 @@ int or_transport(const or_model* m, const or_source* src, int nsrc, const or_par
 {
     if (nsrc < 1 || m->nf < 1 || m->ns < 1 || m->ns > 64 || p->n_packets == 0) return 1;
     if (p->pid_end < p->pid_begin || p->pid_end > p->n_packets) return 1;
+    if (p->n_pc < 0 || (p->n_pc > 0 && !p->pc)) return 1;
+    for (int c = 0; c < p->n_pc; ++c)
+        if (p->pc[c].npix < 1) return 1;
     or_ctx C;
     C.m = m; C.p = p; C.T_prev = T_prev; C.nsrc = nsrc; C.src = src;
     C.vol = m->cell * m->cell * m->cell;
@@ -667,6 +717,10 @@ int or_transport(const or_model* m, const or_source* src, int nsrc, const or_par
         C.lucy[c] = mx < p->lucy_tau;
     }
 
+    size_t n_pc_px = 0;
+    if (p->pc && out->pc_img)
+        for (int c = 0; c < p->n_pc; ++c)
+            n_pc_px += (size_t)m->nf * p->pc[c].npix * p->pc[c].npix;
     int nt = n_threads < 1 ? 1 : n_threads;
     if (p->mode == OR_MODE_BW) nt = 1;      /* order-dependent: serial by definition */
     uint64_t np = p->pid_end - p->pid_begin;
@@ -682,6 +736,7 @@ int or_transport(const or_model* m, const or_source* src, int nsrc, const or_par
             parts[t].esq = out->esq ? (double*)calloc((size_t)(m->ns * nc), sizeof(double)) : NULL;
             parts[t].sed_esc = (double*)calloc((size_t)(10 * m->nf), sizeof(double));
             parts[t].sed_cnt = (uint64_t*)calloc((size_t)(10 * m->nf), sizeof(uint64_t));
+            parts[t].pc_img = n_pc_px ? (double*)calloc(n_pc_px, sizeof(double)) : NULL;
             parts[t].event_cap = out->events ? out->event_cap : 0;
             parts[t].events = parts[t].event_cap ? (or_event*)malloc(sizeof(or_event) * parts[t].event_cap) : NULL;
             parts[t].pah_cap = out->pah ? out->pah_cap : 0;
@@ -709,6 +764,7 @@ int or_transport(const or_model* m, const or_source* src, int nsrc, const or_par
                 out->sed_esc[i] += q->sed_esc[i];
                 out->sed_cnt[i] += q->sed_cnt[i];
             }
+            for (size_t i = 0; i < n_pc_px; ++i) out->pc_img[i] += q->pc_img[i];
             for (uint64_t i = 0; i < q->n_events; ++i) {
                 if (out->n_events < out->event_cap) out->events[out->n_events++] = q->events[i];
                 else out->stats[OR_S_EV_DROP]++;
@@ -723,7 +779,7 @@ int or_transport(const or_model* m, const or_source* src, int nsrc, const or_par
             }
             for (int i = 0; i < OR_S_N; ++i) out->stats[i] += q->stats[i];
             free(q->E_abs); free(q->count); free(q->esq); free(q->sed_esc); free(q->sed_cnt);
-            free(q->events); free(q->pah); free(q->traj);
+            free(q->events); free(q->pah); free(q->traj); free(q->pc_img);
         }
         free(parts);
     }
@@ -775,16 +831,10 @@ void or_temperature_guess(const or_model* m, const or_source* src, int nsrc, dou
 /* ------------------------------------------------------------------------ */
 /* Ray tracer (Sect. 4)                                                      */
 /* ------------------------------------------------------------------------ */
-/* Observer direction k_obs (from the model towards the observer) for
- * (theta, phi); image axes e_x' = (-sin phi, cos phi, 0) and
- * e_y' = (-cos theta cos phi, -cos theta sin phi, sin theta), so that
- * (e_x', e_y', k_obs) is right handed and e_y' follows +z. */
+/* camera frame of a ray-tracing camera (obs_frame) */
 static void camera_frame(const or_camera* cam, double kobs[3], double ex[3], double ey[3])
 {
-    double st = sin(cam->theta), ct = cos(cam->theta), sp = sin(cam->phi), cp = cos(cam->phi);
-    kobs[0] = st * cp; kobs[1] = st * sp; kobs[2] = ct;
-    ex[0] = -sp; ex[1] = cp; ex[2] = 0.0;
-    ey[0] = -ct * cp; ey[1] = -ct * sp; ey[2] = st;
+    obs_frame(cam->theta, cam->phi, kobs, ex, ey);
 }
 
 static double pixel_size(const or_model* m, const or_camera* cam)

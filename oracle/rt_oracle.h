@@ -39,6 +39,11 @@ enum { OR_MODE_BW = 0, OR_MODE_FROZEN_T = 1, OR_MODE_NOREEMIT = 2 };
 enum { OR_LUCY_OFF = 0, OR_LUCY_THIN = 1, OR_LUCY_ALL = 2 };
 enum { OR_LUCY_LINEAR = 0, OR_LUCY_EXPM1 = 1 };
 
+/* Photon-counting camera (Sect. 4): packets leaving the grid with
+ * k . k_obs >= cos_accept are counted in the pixel of their exit point
+ * projected on the image plane (frame and pixel size as for or_camera). */
+typedef struct { double theta, phi; int npix; double pixel; double cos_accept; } or_pc_camera;
+
 typedef struct {
     int mode, lucy_mode, lucy_form;
     double lucy_tau;
@@ -51,6 +56,8 @@ typedef struct {
     uint32_t source_bins;   /* 0: source and bin drawn at random (prob. ~ L_nu dnu);
                                m > 0: Eq. 1 equal-energy source bins, packet pid
                                from bin floor(pid m / N) (see or_transport) */
+    const or_pc_camera* pc;  /* [n_pc] photon-counting cameras (or NULL) */
+    int n_pc;
 } or_params;
 
 typedef struct { uint32_t cell, nu, species, pad; double k[3]; } or_event;
@@ -74,6 +81,7 @@ typedef struct {
     or_pah* pah; uint64_t pah_cap; uint64_t n_pah;
     or_traj* traj; uint64_t traj_cap; uint64_t n_traj;
     uint64_t stats[OR_S_N];
+    double* pc_img;              /* camera c at offset sum_{c'<c} nf npix_c'^2: [nf][npix][npix] */
 } or_out;
 
 typedef struct { double theta, phi; int npix; double D; double pixel; } or_camera;

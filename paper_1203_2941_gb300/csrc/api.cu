@@ -243,7 +243,47 @@ static rt_status check_params(const rt_transport_params* p)
     if (p->source_bins > 0 && ((double)p->source_bins > (double)p->n_packets ||
                                (double)p->source_bins * (double)p->n_packets > 9.0e18))
         return fail(RT_ERR_INVALID_ARG, "transport: source_bins must be <= n_packets with n_packets * source_bins < 9e18");
+    if (p->n_pc_cams < 0 || p->n_pc_cams > kPcMax)
+        return fail(RT_ERR_INVALID_ARG, "transport: n_pc_cams must be 0..16");
+    if (p->n_pc_cams > 0 && !p->pc_cams) return fail(RT_ERR_INVALID_ARG, "transport: pc_cams is NULL");
+    for (int c = 0; c < p->n_pc_cams; ++c) {
+        const rt_pc_camera& q = p->pc_cams[c];
+        if (q.npix < 1 || q.npix > 4096 || !isfin(q.theta) || !isfin(q.phi) || !(q.pixel >= 0.0) ||
+            !isfin(q.pixel) || !(q.cos_accept >= -1.0 && q.cos_accept <= 1.0))
+            return fail(RT_ERR_INVALID_ARG, "transport: photon-counting camera needs npix 1..4096, finite angles, "
+                                            "pixel >= 0 and cos_accept in [-1, 1]");
+    }
     return RT_OK;
+}
+
+// Photon-counting cameras of a single-model call: frames in cell units, in
+// the launch parameters.
+static void fill_pc(TransportKP& kp, const rt_grid* g, const rt_transport_params* p,
+                    const rt_transport_out* out)
+{
+    kp.n_pc = p->n_pc_cams;
+    kp.pc_img = out->pc_img;
+    const double n[3] = { (double)g->nx, (double)g->ny, (double)g->nz };
+    for (int a = 0; a < 3; ++a) kp.pc_ctr[a] = 0.5 * n[a];
+    unsigned long long off = 0;
+    for (int c = 0; c < p->n_pc_cams; ++c) {
+        const rt_pc_camera& q = p->pc_cams[c];
+        PcDev& d = kp.pc[c];
+        const double st = std::sin(q.theta), ct = std::cos(q.theta);
+        const double sp = std::sin(q.phi), cp = std::cos(q.phi);
+        d.kobs[0] = st * cp; d.kobs[1] = st * sp; d.kobs[2] = ct;
+        d.ex[0] = -sp; d.ex[1] = cp; d.ex[2] = 0.0;
+        d.ey[0] = -ct * cp; d.ey[1] = -ct * sp; d.ey[2] = st;
+        const double pix = q.pixel > 0.0
+            ? q.pixel
+            : g->cell * std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]) / q.npix;
+        d.cos_accept = q.cos_accept;
+        d.pix_per_cell = g->cell / pix;
+        d.half_npix = 0.5 * q.npix;
+        d.npix = q.npix;
+        d.off = off;
+        off += (unsigned long long)kp.nf * q.npix * q.npix;
+    }
 }
 
 static rt_status check_out(const rt_transport_out* o)
@@ -496,6 +536,8 @@ rt_status rt_transport(rt_ctx* ctx, const rt_grid* grid, const rt_opacity* op,
     if (st != RT_OK) return st;
     if (p->pid_end < p->pid_begin || p->pid_end > p->n_packets)
         return fail(RT_ERR_INVALID_ARG, "rt_transport: need pid_begin <= pid_end <= n_packets");
+    if (p->n_pc_cams > 0 && !out->pc_img)
+        return fail(RT_ERR_INVALID_ARG, "rt_transport: photon-counting cameras need out->pc_img");
     if (p->mode == RT_MODE_FROZEN_T && !T_prev)
         return fail(RT_ERR_INVALID_ARG, "rt_transport: frozen-T mode needs T_prev");
     RT_CUDA(cudaSetDevice(ctx->device));
@@ -524,6 +566,7 @@ rt_status rt_transport(rt_ctx* ctx, const rt_grid* grid, const rt_opacity* op,
     RT_CUDA(cudaMemsetAsync(dm.work, 0, sizeof(unsigned long long), s));
     TransportKP kp;
     fill_kp(kp, op, p, dm, 1);
+    fill_pc(kp, grid, p, out);
     st = single_model_options(kp, op, p, out, n_sources, hms[0].md);
     if (st != RT_OK) { cudaFreeAsync(dm.buf, s); if (acc) cudaFreeAsync(acc, s); return st; }
     // deferred packets: a queue in device memory, drained by a second launch
@@ -570,6 +613,8 @@ rt_status rt_batch_create(rt_ctx* ctx, const rt_opacity* op, int n_models, const
     if (n_models < 1 || n_models > 4096) return fail(RT_ERR_INVALID_ARG, "rt_batch_create: n_models must be 1..4096");
     rt_status st = check_params(p);
     if (st != RT_OK) return st;
+    if (p->n_pc_cams != 0)
+        return fail(RT_ERR_INVALID_ARG, "rt_batch_create: photon-counting cameras are served by rt_transport only");
     RT_CUDA(cudaSetDevice(ctx->device));
     std::vector<HostModel> hms(n_models);
     std::vector<uint64_t> nwork(n_models);
@@ -738,6 +783,27 @@ rt_status rt_raytrace(rt_ctx* ctx, const rt_grid* grid, const rt_opacity* op, co
                          false, (cudaStream_t)stream);
 }
 
+rt_status rt_visibilities(rt_ctx* ctx, const rt_grid* grid, const rt_camera* cams, int ncam,
+                          const float* images, int nf, const double* uv, int nuv, double* vis,
+                          rt_stream stream)
+{
+    if (!ctx || ctx->magic != kMagic) return fail(RT_ERR_STATE, "rt_visibilities: bad context");
+    if (!grid || !cams || !images || !uv || !vis) return fail(RT_ERR_INVALID_ARG, "rt_visibilities: NULL pointer");
+    if (grid->ctx != ctx) return fail(RT_ERR_STATE, "rt_visibilities: grid from another context");
+    if (ncam < 1 || ncam > 1024) return fail(RT_ERR_INVALID_ARG, "rt_visibilities: n_cams must be 1..1024");
+    if (nf < 1 || nf > kMaxImgFreq) return fail(RT_ERR_INVALID_ARG, "rt_visibilities: n_f must be 1..16");
+    if (nuv < 1 || nuv > 65535) return fail(RT_ERR_INVALID_ARG, "rt_visibilities: n_uv must be 1..65535");
+    for (int c = 0; c < ncam; ++c) {
+        if (cams[c].npix != cams[0].npix || cams[c].npix < 1 || cams[c].npix > 8192)
+            return fail(RT_ERR_INVALID_ARG, "rt_visibilities: all cameras need the same npix in 1..8192");
+        if (!(cams[c].D > 0.0) || !isfin(cams[c].D)) return fail(RT_ERR_INVALID_ARG, "rt_visibilities: bad camera");
+    }
+    for (int k = 0; k < 2 * nuv; ++k)
+        if (!isfin(uv[k])) return fail(RT_ERR_INVALID_ARG, "rt_visibilities: non-finite uv");
+    RT_CUDA(cudaSetDevice(ctx->device));
+    return visibilities_impl(ctx, grid, cams, ncam, images, nf, uv, nuv, vis, (cudaStream_t)stream);
+}
+
 rt_status rt_raytrace_backward(rt_ctx* ctx, const rt_grid* grid, const rt_opacity* op,
                                const double* T, const rt_event* ev, uint64_t nev,
                                const uint64_t* nev_dev, double xi_ev,
@@ -847,6 +913,8 @@ rt_status rt_transport_noalloc(rt_ctx* ctx, const rt_grid* grid, const rt_opacit
     if (st != RT_OK) return st;
     if (p->pid_end < p->pid_begin || p->pid_end > p->n_packets)
         return fail(RT_ERR_INVALID_ARG, "rt_transport_noalloc: need pid_begin <= pid_end <= n_packets");
+    if (p->n_pc_cams != 0)
+        return fail(RT_ERR_INVALID_ARG, "rt_transport_noalloc: photon-counting cameras are served by rt_transport only");
     if (p->mode == RT_MODE_FROZEN_T && !T_prev)
         return fail(RT_ERR_INVALID_ARG, "rt_transport_noalloc: frozen-T mode needs T_prev");
     // scratch layout: staging | kext | packed density | FP64 energy scratch

@@ -870,3 +870,98 @@ rt_status raytrace_impl(rt_ctx* ctx, const rt_grid* g, const rt_opacity* op, con
 }
 
 }  // namespace rtgb
+
+namespace rtgb {
+namespace {
+
+// Complex visibility of one image at one (u, v): one block per (image, uv).
+// exp(-2 pi i (u alpha + v beta)) separates into a column and a row factor,
+// tabulated in shared memory (phases reduced in FP64, then FP32 sine and
+// cosine of pi times a number in [-1, 1)); a warp takes a row at a time,
+// its lanes stride along the row (coalesced), the row sum (FP32) is reduced
+// by shuffles and multiplied by the row factor, rows accumulate in FP64.
+__global__ void visibility_kernel(const float* images, int npix, const double* alpha0,
+                                  const double* dalpha, const double* scale, int nf, const double* uv,
+                                  int nuv, double* vis)
+{
+    extern __shared__ float2 tab[];                    // [npix] columns, [npix] rows
+    const int img = blockIdx.y, k = blockIdx.x;
+    const int cam = img / nf;
+    const double u = uv[2 * k], v = uv[2 * k + 1];
+    const double a0 = alpha0[cam], da = dalpha[cam];
+    for (int i = threadIdx.x; i < 2 * npix; i += blockDim.x) {
+        const int p = i < npix ? i : i - npix;
+        const double w = i < npix ? u : v;
+        double cyc = w * (a0 + da * (double)p);        // cycles
+        cyc -= rint(cyc);                              // [-1/2, 1/2]
+        float s, c;
+        sincospif((float)(-2.0 * cyc), &s, &c);
+        tab[i] = make_float2(c, s);
+    }
+    __syncthreads();
+    const float* I = images + (size_t)img * npix * npix;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    double re = 0.0, im = 0.0;
+    for (int y = warp; y < npix; y += nw) {
+        float sr = 0.f, si = 0.f;
+        for (int x = lane; x < npix; x += 32) {
+            const float q = I[(size_t)y * npix + x];
+            sr += q * tab[x].x;
+            si += q * tab[x].y;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            sr += __shfl_xor_sync(0xffffffffu, sr, o);
+            si += __shfl_xor_sync(0xffffffffu, si, o);
+        }
+        if (lane == 0) {
+            const float2 r = tab[npix + y];
+            re += (double)sr * r.x - (double)si * r.y;
+            im += (double)sr * r.y + (double)si * r.x;
+        }
+    }
+    __shared__ double red[2][32];
+    if (lane == 0) { red[0][warp] = re; red[1][warp] = im; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double R = 0.0, M = 0.0;
+        for (int w = 0; w < nw; ++w) { R += red[0][w]; M += red[1][w]; }
+        vis[2 * ((size_t)img * nuv + k)] = R * scale[cam];
+        vis[2 * ((size_t)img * nuv + k) + 1] = M * scale[cam];
+    }
+}
+
+}  // namespace
+
+rt_status visibilities_impl(rt_ctx* ctx, const rt_grid* g, const rt_camera* cams, int ncam,
+                            const float* images, int nf, const double* uv, int nuv, double* vis,
+                            cudaStream_t s)
+{
+    (void)ctx;
+    const int npix = cams[0].npix;
+    const double diag = g->cell * sqrt((double)g->nx * g->nx + (double)g->ny * g->ny + (double)g->nz * g->nz);
+    // per camera: first pixel centre and pixel size in radians, A_pix / D^2; then uv
+    std::vector<double> h(3 * (size_t)ncam + 2 * (size_t)nuv);
+    for (int c = 0; c < ncam; ++c) {
+        const double pix = cams[c].pixel > 0.0 ? cams[c].pixel : diag / cams[c].npix;
+        h[c] = (0.5 - 0.5 * npix) * pix / cams[c].D;
+        h[ncam + c] = pix / cams[c].D;
+        h[2 * ncam + c] = pix * pix / (cams[c].D * cams[c].D);
+    }
+    std::memcpy(&h[3 * (size_t)ncam], uv, sizeof(double) * 2 * nuv);
+    double* d = nullptr;
+    RT_CUDA(cudaMallocAsync((void**)&d, sizeof(double) * h.size(), s));
+    RT_CUDA(cudaMemcpyAsync(d, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice, s));
+    const size_t smem = sizeof(float2) * 2 * npix;
+    if (smem > 48 * 1024)
+        RT_CUDA(cudaFuncSetAttribute(visibility_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid((unsigned)nuv, (unsigned)(ncam * nf));
+    visibility_kernel<<<grid, 256, smem, s>>>(images, npix, d, d + ncam, d + 2 * ncam, nf,
+                                               d + 3 * ncam, nuv, vis);
+    count_launches();
+    RT_CUDA(cudaGetLastError());
+    RT_CUDA(cudaFreeAsync(d, s));
+    return RT_OK;
+}
+
+}  // namespace rtgb

@@ -33,6 +33,7 @@ constexpr int kMrwN = 2048;       // MRW survival table entries on y in [0, kMrw
 constexpr double kMrwYmax = 2.0;
 constexpr int kSedBins = 10;
 constexpr int kParamModels = 64;  // model descriptors carried in the transport launch parameters
+constexpr int kPcMax = 16;        // photon-counting cameras of one transport call
 constexpr int kMaxImgFreq = 16;
 
 // Node j of the linear-space temperature table on the uniform ln T grid:
@@ -136,6 +137,16 @@ struct alignas(16) DeferRec {
 };
 constexpr uint64_t kDeferCap = 1ull << 20;   // queue records per call
 
+// A photon-counting camera in the grid's cell units: observer direction,
+// image axes, acceptance cosine, pixels per cell length, and the offset of
+// its [nf][npix][npix] image in the output.
+struct PcDev {
+    double kobs[3], ex[3], ey[3];
+    double cos_accept, pix_per_cell, half_npix;
+    int npix;
+    unsigned long long off;
+};
+
 struct TransportKP {
     const ModelDev* models;
     const unsigned long long* prefix;   // [n_models + 1] work-index prefix
@@ -163,6 +174,10 @@ struct TransportKP {
     unsigned long long* defer_n;        // queue cursor (device)
     unsigned long long defer_cap;
     int resume;                         // 1: packets come from the queue, not from emission
+    int n_pc;                           // photon-counting cameras (single-model calls)
+    double* pc_img;
+    double pc_ctr[3];                   // grid centre, cell units
+    PcDev pc[kPcMax];
     uint64_t seed;
     double mrw_tau_cell, mrw_gamma;
     // opacity tables
@@ -234,6 +249,9 @@ rt_status pack_grid(rt_grid* g, const rt_opacity* op, int lucy_mode, double lucy
                     cudaStream_t s);
 rt_status pack_grid_into(const rt_grid* g, const rt_opacity* op, int lucy_mode, double lucy_tau,
                          int prec, double* kext, void* dst, cudaStream_t s);
+rt_status visibilities_impl(rt_ctx* ctx, const rt_grid* g, const rt_camera* cams, int ncam,
+                            const float* images, int nf, const double* uv, int nuv, double* vis,
+                            cudaStream_t s);
 template <int NS>
 rt_status launch_transport_ns(rt_ctx* ctx, const TransportKP& kp, int prec, int schedule, int threads,
                               int blocks_per_sm, cudaStream_t s);

@@ -1005,6 +1005,31 @@ struct Kernel {
         finish_absorb(L);
     }
 
+    // Photon counting (Sect. 4): the escaping packet's power goes to the
+    // pixel of its exit point projected on each camera whose acceptance cone
+    // holds its direction; the projection runs in FP64 in cell units.
+    __device__ __forceinline__ void photon_count(const Lane<R, NS>& L) const
+    {
+        double xe[3], k[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            k[a] = (double)L.k[a];
+            xe[a] = (double)L.x[a] + (double)L.tcur * k[a] - P.pc_ctr[a];
+        }
+        for (int c = 0; c < P.n_pc; ++c) {
+            const PcDev& q = P.pc[c];
+            const double kd = k[0] * q.kobs[0] + k[1] * q.kobs[1] + k[2] * q.kobs[2];
+            if (!(kd >= q.cos_accept)) continue;
+            const double xp = xe[0] * q.ex[0] + xe[1] * q.ex[1] + xe[2] * q.ex[2];
+            const double yp = xe[0] * q.ey[0] + xe[1] * q.ey[1] + xe[2] * q.ey[2];
+            const double fx = floor(xp * q.pix_per_cell + q.half_npix);
+            const double fy = floor(yp * q.pix_per_cell + q.half_npix);
+            if (fx >= 0.0 && fx < q.npix && fy >= 0.0 && fy < q.npix)
+                atomicAdd(&P.pc_img[q.off + ((unsigned long long)L.j * q.npix + (int)fy) * q.npix + (int)fx],
+                          md->xi);
+        }
+    }
+
     __device__ __forceinline__ void escape(Lane<R, NS>& L)
     {
         int b = (int)floor((L.k[2] + R(1)) * R(5));
@@ -1017,6 +1042,7 @@ struct Kernel {
             atomicAdd(&md->sed_cnt[b * P.nf + L.j], 1ull);
         }
         count(RT_STAT_ESCAPED, 1);
+        if (P.n_pc) photon_count(L);
         if constexpr (HAS_TRAJ) {
             if (md->traj) {
                 R xe[3];

@@ -32,7 +32,7 @@ EXPORTS = ["rt_last_error", "rt_version", "rt_ctx_create", "rt_ctx_destroy", "rt
            "rt_grid_free", "rt_opacity_upload", "rt_opacity_free", "rt_transport_params_default",
            "rt_transport", "rt_temperatures", "rt_temperature_guess", "rt_raytrace",
            "rt_raytrace_backward", "rt_batch_create", "rt_batch_run", "rt_batch_free",
-           "rt_transport_batched", "rt_philox", "rt_kernel_launches", "rt_transport_noalloc"]
+           "rt_transport_batched", "rt_philox", "rt_kernel_launches", "rt_transport_noalloc", "rt_visibilities"]
 
 
 class RtError(RuntimeError):
@@ -54,7 +54,7 @@ class rt_transport_params(C.Structure):
                 ("max_events", C.c_uint64), ("record_events", C.c_int), ("precision", C.c_int),
                 ("schedule", C.c_int), ("threads_per_block", C.c_int), ("blocks_per_sm", C.c_int),
                 ("march_min_active", C.c_int), ("defer_events", C.c_uint64),
-                ("source_bins", C.c_uint32)]
+                ("source_bins", C.c_uint32), ("pc_cams", C.c_void_p), ("n_pc_cams", C.c_int)]
 
 
 class rt_transport_out(C.Structure):
@@ -63,12 +63,17 @@ class rt_transport_out(C.Structure):
                 ("events", C.c_void_p), ("event_cap", C.c_uint64),
                 ("pah", C.c_void_p), ("pah_cap", C.c_uint64),
                 ("traj", C.c_void_p), ("traj_cap", C.c_uint64),
-                ("stats", C.c_void_p)]
+                ("stats", C.c_void_p), ("pc_img", C.c_void_p)]
 
 
 class rt_camera(C.Structure):
     _fields_ = [("theta", C.c_double), ("phi", C.c_double), ("npix", C.c_int),
                 ("D", C.c_double), ("pixel", C.c_double)]
+
+
+class rt_pc_camera(C.Structure):
+    _fields_ = [("theta", C.c_double), ("phi", C.c_double), ("npix", C.c_int),
+                ("pixel", C.c_double), ("cos_accept", C.c_double)]
 
 
 class rt_model(C.Structure):
@@ -116,6 +121,7 @@ def load(path: str = LIB_PATH):
                               vp, vp]),
         "rt_raytrace_backward": (i32, [vp, vp, vp, vp, vp, u64, vp, dbl, vp, i32, vp, i32, vp, i32,
                                        vp, vp, vp, vp, vp, vp]),
+        "rt_visibilities": (i32, [vp, vp, vp, i32, vp, i32, vp, i32, vp, vp]),
         "rt_kernel_launches": (u64, []),
         "rt_batch_create": (i32, [vp, vp, i32, vp, C.POINTER(rt_transport_params), C.POINTER(vp)]),
         "rt_batch_run": (i32, [vp, vp]),
@@ -215,6 +221,11 @@ def rt_raytrace(ctx, grid, opac, T_ptr, ev_ptr, n_ev, n_ev_dev, xi_ev, sources, 
                               n_sources, cams, n_cams, fidx, n_f, img_ptr, sed_ptr, steps_ptr,
                               stream),
            "rt_raytrace")
+
+
+def rt_visibilities(ctx, grid, cams, n_cams, img_ptr, n_f, uv, n_uv, vis_ptr, stream=0):
+    _check(load().rt_visibilities(ctx, grid, cams, n_cams, img_ptr, n_f, uv, n_uv, vis_ptr, stream),
+           "rt_visibilities")
 
 
 def rt_raytrace_backward(ctx, grid, opac, T_ptr, ev_ptr, n_ev, n_ev_dev, xi_ev, sources,

@@ -11,6 +11,7 @@ from __future__ import annotations
 
 import ctypes as C
 import math
+from dataclasses import dataclass
 from typing import List, Optional, Sequence
 
 import numpy as np
@@ -139,12 +140,35 @@ class TransportOut:
         self.traj_cap = traj_cap
         self.stats = torch.zeros(R.RT_STAT_COUNT, dtype=torch.int64, device=dev)
         self.xi = None
+        self.nf = nf
+        self.pc_npix: List[int] = []
+        self.pc_img = None           # flat: one [nf, npix, npix] block per camera
 
     def zero_(self):
-        for t in (self.E_abs, self.count, self.esq, self.sed_esc, self.sed_cnt, self.stats):
+        for t in (self.E_abs, self.count, self.esq, self.sed_esc, self.sed_cnt, self.stats,
+                  self.pc_img):
             if t is not None:
                 t.zero_()
         return self
+
+    def ensure_pc(self, cams) -> None:
+        """Allocate (once) the photon-counting images of ``cams``."""
+        npix = [int(c.npix) for c in cams]
+        if self.pc_img is not None and npix == self.pc_npix:
+            return
+        if self.pc_img is not None:
+            raise ValueError("TransportOut already holds images of other photon-counting cameras")
+        self.pc_npix = npix
+        self.pc_img = torch.zeros(sum(self.nf * n * n for n in npix), dtype=torch.float64,
+                                  device=self.E_abs.device)
+
+    def pc_images(self) -> List[torch.Tensor]:
+        """Photon-counting images, one [nf, npix, npix] view per camera."""
+        out, o = [], 0
+        for n in self.pc_npix:
+            out.append(self.pc_img[o:o + self.nf * n * n].view(self.nf, n, n))
+            o += self.nf * n * n
+        return out
 
     def c_struct(self) -> R.rt_transport_out:
         return R.rt_transport_out(
@@ -153,7 +177,7 @@ class TransportOut:
             _ptr(self.events) if self.event_cap else None, self.event_cap,
             _ptr(self.pah) if self.pah_cap else None, self.pah_cap,
             _ptr(self.traj) if self.traj_cap else None, self.traj_cap,
-            _ptr(self.stats))
+            _ptr(self.stats), _ptr(self.pc_img))
 
     def stats_dict(self):
         v = self.stats.cpu().numpy()
@@ -207,15 +231,42 @@ def make_params(n_packets: int, mode=R.RT_MODE_BW, lucy_mode=R.RT_LUCY_THIN,
     return p
 
 
+@dataclass
+class PcCamera:
+    """Photon-counting camera (Sect. 4): packets leaving the grid with
+    k . k_obs >= cos_accept are counted in the pixel of their projected exit
+    point; pixel 0 means box diagonal / npix."""
+    theta: float
+    phi: float
+    npix: int
+    cos_accept: float
+    pixel: float = 0.0
+
+
+def pc_cameras(cams) -> "C.Array":
+    arr = (R.rt_pc_camera * max(1, len(cams)))()
+    for i, c in enumerate(cams):
+        arr[i].theta, arr[i].phi, arr[i].npix = float(c.theta), float(c.phi), int(c.npix)
+        arr[i].pixel, arr[i].cos_accept = float(c.pixel), float(c.cos_accept)
+    return arr
+
+
 def transport(ctx: Context, grid: Grid, opac: Opacity, sources: Sources, n_packets: int,
               out: Optional[TransportOut] = None, T_prev: Optional[torch.Tensor] = None,
               event_cap: int = 0, pah_cap: int = 0, traj_cap: int = 0, stream=None,
-              **kw) -> TransportOut:
+              pc_cams: Sequence[PcCamera] = (), **kw) -> TransportOut:
+    """One rt_transport call; ``pc_cams`` adds photon-counting images
+    (``out.pc_images()``)."""
     if out is None:
         out = TransportOut(grid.ncell, grid.ns, opac.nf, event_cap, pah_cap, traj_cap)
     if kw.get("record_events") is None and out.event_cap:
         kw["record_events"] = True
     p = make_params(n_packets, **kw)
+    pca = None
+    if pc_cams:
+        out.ensure_pc(pc_cams)
+        pca = pc_cameras(pc_cams)
+        p.pc_cams, p.n_pc_cams = C.cast(pca, C.c_void_p), len(pc_cams)
     if T_prev is not None:
         T_prev = T_prev.to(dtype=torch.float64).contiguous()
     R.rt_transport(ctx.h, grid.h, opac.h, sources.arr, sources.n, p, _ptr(T_prev),
@@ -286,6 +337,19 @@ def raytrace(ctx: Context, grid: Grid, opac: Opacity, T: torch.Tensor, events, x
                   ca, len(cams), fi, len(freq_idx), _ptr(img), _ptr(sed), _ptr(steps),
                   _stream(stream))
     return img, sed
+
+
+def visibilities(ctx: Context, grid: Grid, cams, images: torch.Tensor, uv, stream=None) -> torch.Tensor:
+    """Complex visibilities [n_cams, n_f, n_uv] (complex128) of images from
+    ``raytrace`` at ``uv`` ([n_uv, 2], cycles per radian along the image axes)."""
+    ca = cameras(cams)
+    uv = np.ascontiguousarray(np.asarray(uv, dtype=np.float64).reshape(-1, 2))
+    images = images.to(dtype=torch.float32).contiguous()
+    ncam, nf = images.shape[0], images.shape[1]
+    vis = torch.empty((ncam, nf, len(uv), 2), dtype=torch.float64, device="cuda")
+    R.rt_visibilities(ctx.h, grid.h, ca, len(cams), _ptr(images), nf,
+                      uv.ctypes.data_as(C.c_void_p), len(uv), _ptr(vis), _stream(stream))
+    return torch.view_as_complex(vis)
 
 
 def raytrace_backward(ctx: Context, grid: Grid, opac: Opacity, T: torch.Tensor, events, xi_ev,

@@ -61,6 +61,8 @@ int main(void) {
          sizeof(rt_pah_event), sizeof(rt_traj));
   printf("%zu %zu %zu\n", offsetof(rt_transport_params, march_min_active),
          offsetof(rt_transport_out, stats), offsetof(rt_model, out));
+  printf("%zu %zu %zu\n", sizeof(rt_pc_camera), offsetof(rt_transport_params, pc_cams),
+         offsetof(rt_transport_out, pc_img));
   return 0;
 }
 '''
@@ -75,5 +77,7 @@ int main(void) {
             ctypes.sizeof(R.rt_transport_out), ctypes.sizeof(R.rt_camera), ctypes.sizeof(R.rt_model),
             R.EVENT_DTYPE.itemsize, R.PAH_DTYPE.itemsize, R.TRAJ_DTYPE.itemsize,
             R.rt_transport_params.march_min_active.offset, R.rt_transport_out.stats.offset,
-            R.rt_model.out.offset]
+            R.rt_model.out.offset,
+            ctypes.sizeof(R.rt_pc_camera), R.rt_transport_params.pc_cams.offset,
+            R.rt_transport_out.pc_img.offset]
     assert [int(v) for v in got] == want

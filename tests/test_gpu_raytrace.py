@@ -12,6 +12,8 @@ the FP64 CPU oracle (run on a GB300).
   packet by packet (FP64) and conserves energy (FP32), also when replayed
   from a CUDA graph.
 """
+import math
+
 import numpy as np
 import pytest
 import torch
@@ -142,6 +144,29 @@ def test_raytrace_reads_event_count_on_device(rt, ctx, O):
         ir, sr = O.raytrace(m, T.cpu().numpy(), ev, xi, cams, fidx)
         _compare_images(img_d.cpu().numpy(), ir)
         np.testing.assert_allclose(sed_d.cpu().numpy(), sr, rtol=1e-5)
+
+
+def test_visibilities_match_oracle(rt, ctx, O):
+    """Visibilities of ray-traced images against the oracle's definition on
+    the same images; V(0, 0) equals the images' share of the SED."""
+    m = W.r2_shell(n=16, nf=24, tau_1um=5.0)
+    grid, opac, srcs = ctx.grid(m), ctx.opacity(m), rt.Sources(m.sources)
+    T = torch.tensor(np.random.default_rng(3).uniform(30, 900, size=(m.ns, m.ncell)), device="cuda")
+    cams = [W.Camera(np.radians(t), 0.4, 48, 3e19) for t in (20.0, 70.0)]
+    fidx = [4, 11, 18]
+    img, sed = rt.raytrace(ctx, grid, opac, T, None, 0.0, None, cams, fidx)
+    diag = m.cell * math.sqrt(3.0) * 16
+    lam_over_res = 1.0 / (diag / 3e19)                  # cycles per radian of one field width
+    uv = np.array([[0.0, 0.0], [0.5, 0.0], [0.0, 1.5], [3.0, -2.0], [-7.5, 4.0], [20.0, 11.0]]) * lam_over_res
+    V = rt.visibilities(ctx, grid, cams, img, uv)
+    torch.cuda.synchronize()
+    Vr = O.visibilities(m, img.cpu().numpy(), cams, uv)
+    Vg = V.cpu().numpy()
+    scale = np.abs(Vr[:, :, :1])
+    assert np.all(np.abs(Vg - Vr) <= 1e-6 * scale + 1e-300)
+    np.testing.assert_allclose(Vg[:, :, 0].real, sed.cpu().numpy(), rtol=1e-6)   # no star in sed here
+    with pytest.raises(rt.RtError):
+        rt.visibilities(ctx, grid, cams, img, np.array([[np.nan, 0.0]]))
 
 
 @pytest.mark.parametrize("ns", [2, 3])

@@ -331,3 +331,63 @@ def test_edge_cases(rt, ctx, O):
     neg.rho[0, 1, 1, 1] = -1.0
     with pytest.raises(rt.RtError):
         ctx.grid(neg)
+
+
+# ------------------------------------------------------- photon counting (Sect. 4)
+def _pc_cams(rt, m):
+    return [rt.PcCamera(0.0, 0.0, 12, 0.8), rt.PcCamera(1.1, 0.4, 9, -1.0),
+            rt.PcCamera(2.2, -0.7, 5, 0.3, pixel=0.5 * m.cell), rt.PcCamera(0.6, 2.5, 33, 0.9)]
+
+
+def test_fp64_photon_counting_matches_oracle(rt, ctx, O):
+    m = W.random_grid(n=(6, 5, 4), ns=2, seed=4, tau_scale=1.5, albedo=(0.3, 0.8))
+    grid, opac, srcs = _setup(rt, ctx, m)
+    T0 = np.random.default_rng(2).uniform(40, 600, size=(m.ns, m.ncell))
+    cams = _pc_cams(rt, m)
+    N = 3000
+    out = rt.transport(ctx, grid, opac, srcs, N, mode=rt.rtgb.RT_MODE_FROZEN_T,
+                       precision=rt.rtgb.RT_PREC_FP64, T_prev=torch.tensor(T0, device="cuda"),
+                       pc_cams=cams, seed=9)
+    torch.cuda.synchronize()
+    ref = O.transport(m, N, seed=9, mode=O.MODE_FROZEN_T, T_prev=T0, n_threads=4,
+                      pc_cameras=[(c.theta, c.phi, c.npix, c.pixel, c.cos_accept) for c in cams])
+    for g, r in zip(out.pc_images(), ref["pc_img"]):
+        g = g.cpu().numpy()
+        assert g.shape == r.shape and r.sum() > 0
+        np.testing.assert_allclose(g, r, rtol=1e-10, atol=1e-10 * r.max())
+
+
+def test_fp32_photon_counting_invariants(rt, ctx, O):
+    """FP32 B&W run: the +z camera of acceptance 0.8 holds the top bin of the
+    escape SED, the all-sky camera every escaped packet (per frequency; a
+    packet with k_z within rounding of 0.8 may fall on either side), also
+    after a second call accumulates into the same images."""
+    m = W.r2_shell(n=24, tau_1um=3.0, nf=16)
+    grid, opac, srcs = _setup(rt, ctx, m)
+    cams = [rt.PcCamera(0.0, 0.0, 32, 0.8), rt.PcCamera(0.9, 0.3, 16, -1.0)]
+    N = 200_000
+    out = rt.transport(ctx, grid, opac, srcs, N, pc_cams=cams, seed=5)
+    torch.cuda.synchronize()
+    top, full = [g.cpu().numpy() for g in out.pc_images()]
+    sed = out.sed_esc.cpu().numpy()
+    xi = out.xi
+    assert np.all(np.abs(top.sum(axis=(1, 2)) - sed[9]) <= 2 * xi)
+    np.testing.assert_allclose(full.sum(axis=(1, 2)), sed.sum(axis=0), rtol=1e-12, atol=2 * xi)
+    assert full.sum() == pytest.approx(m.luminosity, rel=1e-9)
+    rt.transport(ctx, grid, opac, srcs, N, out=out, pc_cams=cams, seed=6)
+    torch.cuda.synchronize()
+    top, full = [g.cpu().numpy() for g in out.pc_images()]
+    sed = out.sed_esc.cpu().numpy()
+    assert np.all(np.abs(top.sum(axis=(1, 2)) - sed[9]) <= 4 * xi)
+    assert full.sum() == pytest.approx(2 * m.luminosity, rel=1e-9)
+
+
+def test_photon_counting_rejections(rt, ctx):
+    m = W.uniform_cube(n=4, tau_cell=0.1)
+    grid, opac, srcs = _setup(rt, ctx, m)
+    with pytest.raises(rt.RtError):
+        rt.transport(ctx, grid, opac, srcs, 100, pc_cams=[rt.PcCamera(0.0, 0.0, 0, 0.5)])
+    with pytest.raises(rt.RtError):
+        rt.transport(ctx, grid, opac, srcs, 100, pc_cams=[rt.PcCamera(0.0, 0.0, 8, 1.5)])
+    with pytest.raises(rt.RtError):
+        rt.transport(ctx, grid, opac, srcs, 100, pc_cams=[rt.PcCamera(0.0, 0.0, 8, 0.5)] * 17)

@@ -488,3 +488,101 @@ def test_equal_energy_source_bins(O):
     np.testing.assert_array_equal(e1["nu"], e2["nu"])
     nu = e1["nu"].reshape(60, 10)
     assert np.all(nu == nu[:, :1])
+
+
+def test_visibility_definition_pins(O):
+    """Visibilities of images (oracle): a single bright pixel gives |V| = its
+    flux with the phase of its sky offset; a Gaussian image gives the
+    Gaussian transform exp(-2 pi^2 s^2 (u^2 + v^2)); real images are
+    Hermitian, V(-u, -v) = conj V(u, v); a one-pixel shift multiplies V by
+    exp(-2 pi i u dalpha)."""
+    m = W.uniform_cube(n=4, tau_cell=0.5)
+    npix, D = 64, 1e19
+    cam = W.Camera(0.3, 0.2, npix, D, 0.05 * m.cell)
+    pix = cam.pixel
+    a = (np.arange(npix) + 0.5 - 0.5 * npix) * pix / D
+    uv = np.array([[0.0, 0.0], [3e4, -1e4], [-2e5, 7e4], [5e5, 5e5]]) * (D / (npix * pix)) / 3e4
+    img = np.zeros((1, 1, npix, npix))
+    img[0, 0, 40, 13] = 2.5
+    V = O.visibilities(m, img, [cam], uv)[0, 0]
+    F = 2.5 * pix * pix / (D * D)
+    np.testing.assert_allclose(np.abs(V), F, rtol=1e-12)
+    np.testing.assert_allclose(V, F * np.exp(-2j * np.pi * (uv[:, 0] * a[13] + uv[:, 1] * a[40])),
+                               rtol=1e-12, atol=1e-12 * F)
+    # Gaussian of rms s (radians) much wider than a pixel and much narrower than the field
+    s = 5 * pix / D
+    g = np.exp(-(a[None, :] ** 2 + a[:, None] ** 2) / (2 * s * s))[None, None]
+    ug = np.array([[0.0, 0.0], [0.05 / s, 0.0], [0.1 / s, 0.05 / s], [0.0, 0.15 / s]])
+    Vg = O.visibilities(m, g, [cam], ug)[0, 0]
+    expect = np.exp(-2 * np.pi ** 2 * s * s * (ug[:, 0] ** 2 + ug[:, 1] ** 2))
+    np.testing.assert_allclose((Vg / Vg[0]).real, expect, rtol=1e-6)
+    assert np.all(np.abs((Vg / Vg[0]).imag) < 1e-9)
+    # Hermitian symmetry of a random real image, and the shift theorem
+    rnd = np.random.default_rng(4).random((1, 1, npix, npix))
+    Vp = O.visibilities(m, rnd, [cam], uv)[0, 0]
+    Vm = O.visibilities(m, rnd, [cam], -uv)[0, 0]
+    np.testing.assert_allclose(Vm, np.conj(Vp), rtol=1e-12, atol=1e-14 * abs(Vp[0]))
+    sh = np.zeros_like(rnd)
+    sh[..., 1:] = rnd[..., :-1]
+    sh[..., 0] = 0.0
+    rnd0 = rnd.copy()
+    rnd0[..., -1] = 0.0                                 # the column shifted out
+    V0 = O.visibilities(m, rnd0, [cam], uv)[0, 0]
+    Vs = O.visibilities(m, sh, [cam], uv)[0, 0]
+    np.testing.assert_allclose(Vs, V0 * np.exp(-2j * np.pi * uv[:, 0] * pix / D), rtol=1e-10,
+                               atol=1e-12 * abs(V0[0]))
+
+
+# ------------------------------------------------------- photon counting (Sect. 4)
+def test_photon_counting_geometry_closed_forms(O):
+    """Dust-free cube, point source off the centre, camera looking down +x
+    with acceptance cosine c: every accepted packet leaves through the face
+    x = h at (y0 + h ky/kx, z0 + h kz/kx).  Closed forms for isotropic
+    emission: accepted fraction (1 - c)/2; image centroid (y0, z0); per-axis
+    variance h^2 (1/c - 1)/2 plus the pixel's p^2/12."""
+    side = W.AU
+    h = side / 2
+    y0, z0, c = 0.2 * h, -0.15 * h, 0.8
+    m = W.uniform_cube(n=4, tau_cell=0.0, nf=6, source_pos=(0.0, y0, z0))
+    m.rho[:] = 0.0
+    npix = 64
+    pix = side / npix
+    N = 200_000
+    r = O.transport(m, N, seed=3, mode=O.MODE_NOREEMIT, n_threads=4,
+                    pc_cameras=[(math.pi / 2, 0.0, npix, pix, c)])
+    img = r["pc_img"][0].sum(axis=0)                 # [iy, ix]
+    xi = r["xi"]
+    L = m.luminosity
+    p = (1 - c) / 2
+    assert abs(img.sum() - L * p) <= 5 * xi * math.sqrt(N * p * (1 - p))
+    n_acc = img.sum() / xi
+    ctr = (np.arange(npix) + 0.5 - npix / 2) * pix
+    wy, wx = img.sum(axis=1), img.sum(axis=0)        # y' (rows) and x' (columns)
+    mx, my = (wx * ctr).sum() / img.sum(), (wy * ctr).sum() / img.sum()
+    sd = h * math.sqrt((1 / c - 1) / 2)
+    assert abs(mx - y0) <= 5 * sd / math.sqrt(n_acc)
+    assert abs(my - z0) <= 5 * sd / math.sqrt(n_acc)
+    for w, mu in ((wx, y0), (wy, z0)):
+        var = (w * (ctr - mu) ** 2).sum() / img.sum()
+        assert var == pytest.approx(sd ** 2 + pix ** 2 / 12, rel=0.05)
+
+
+def test_photon_counting_matches_escape_tallies(O):
+    """With dust: a camera on the +z axis with acceptance cosine 0.8 counts
+    exactly the packets of the top cos(theta) bin of the escape SED, and a
+    camera accepting every direction (c = -1, field = box diagonal) counts
+    every escaped packet, per frequency; the threaded run merges the images
+    in the same order as the serial one."""
+    m = W.random_grid(n=(6, 5, 4), ns=2, seed=4, tau_scale=1.5, albedo=(0.3, 0.8))
+    cams = [(0.0, 0.0, 12, 0.0, 0.8), (1.1, 0.4, 9, 0.0, -1.0), (2.2, -0.7, 5, 0.5 * m.cell, 0.3)]
+    T0 = np.random.default_rng(2).uniform(40, 600, size=(m.ns, m.ncell))
+    kw = dict(seed=9, mode=O.MODE_FROZEN_T, T_prev=T0, pc_cameras=cams)
+    r1 = O.transport(m, 4000, n_threads=1, **kw)
+    r4 = O.transport(m, 4000, n_threads=4, **kw)
+    top, full, part = r1["pc_img"]
+    assert r1["stats"]["escaped"] == 4000
+    np.testing.assert_allclose(top.sum(axis=(1, 2)), r1["sed_esc"][9], rtol=1e-12, atol=0)
+    np.testing.assert_allclose(full.sum(axis=(1, 2)), r1["sed_esc"].sum(axis=0), rtol=1e-12, atol=0)
+    assert 0 < part.sum() < full.sum()
+    for a, b in zip(r1["pc_img"], r4["pc_img"]):
+        np.testing.assert_allclose(a, b, rtol=1e-12, atol=0)
