@@ -270,6 +270,34 @@ RT_API rt_status rt_transport(rt_ctx* ctx, const rt_grid* grid, const rt_opacity
                        const rt_transport_params* p, const double* T_prev,
                        const rt_transport_out* out, rt_stream stream);
 
+/* PAH re-emission pass (Sect. 2.1, Eqs. 6-7).  After the large grains'
+ * temperatures are known, every cell with stored PAH absorptions becomes a
+ * source that emits as many packets as it absorbed: packet pid (of
+ * [p->pid_begin, p->pid_end), p->n_packets == n_records) starts in the cell
+ * of records[pid], at a point drawn uniformly in the cell (one draw per axis
+ * after the bin draw), in the frequency bin j of Eq. 6 -- the smallest j with
+ * sum_{l<=j} eps_n(nu_l) dnu_l >= u sum_l eps_n(nu_l) dnu_l -- with n the
+ * cell's emissivity class, in an isotropic direction, carrying energy xi
+ * (that of the pass that stored the records).  The packets are then
+ * transported exactly as by rt_transport with p (mode, Lucy, MRW, seed,
+ * model_id, precision, schedule, photon-counting cameras); PAH absorptions
+ * in this pass are stored again in out->pah for a further pass.
+ *   records: device [n_records] (the records' nu and model fields are
+ *            ignored); must not overlap out->pah.
+ *   eps: host [n_eps][n_freq] double, eps_n(nu_j) of Eq. 7 (K_PAH times the
+ *        P_n(T)-weighted Planck function, supplied by the caller), finite,
+ *        >= 0, each class nonzero on the grid; n_eps 1..65535.
+ *   eps_class: device int [ncell] class n of each cell, or NULL (class 0).
+ *   A record whose cell is outside the grid, or whose class is out of
+ *   range, emits nothing and is counted in RT_STAT_STUCK.
+ * Errors: as rt_transport; RT_ERR_INVALID_ARG for n_records = 0,
+ * n_packets != n_records, source_bins != 0, xi <= 0 or a bad eps table. */
+RT_API rt_status rt_pah_reemit(rt_ctx* ctx, const rt_grid* grid, const rt_opacity* opac,
+                               const rt_pah_event* records, uint64_t n_records, double xi,
+                               const double* eps, int n_eps, const int* eps_class,
+                               const rt_transport_params* p, const double* T_prev,
+                               const rt_transport_out* out, rt_stream stream);
+
 /* Allocation-free variant of rt_transport (no counterpart in the paper; it
  * exists for callers that must not allocate device memory).  Same arguments,
  * semantics, outputs and errors as rt_transport, but the call itself never

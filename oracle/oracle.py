@@ -87,6 +87,11 @@ class _Out(C.Structure):
                 ("stats", C.c_uint64 * 16), ("pc_img", C.c_void_p)]
 
 
+class _PahSrc(C.Structure):
+    _fields_ = [("rec", C.c_void_p), ("n_rec", C.c_uint64), ("xi", C.c_double),
+                ("eps", C.c_void_p), ("n_eps", C.c_int), ("eps_class", C.c_void_p)]
+
+
 class _Camera(C.Structure):
     _fields_ = [("theta", C.c_double), ("phi", C.c_double), ("npix", C.c_int),
                 ("D", C.c_double), ("pixel", C.c_double)]
@@ -131,6 +136,9 @@ def lib():
             L.or_transport.restype = C.c_int
             L.or_transport.argtypes = [C.POINTER(_Model), C.POINTER(_Source), C.c_int,
                                        C.POINTER(_Params), C.c_void_p, C.POINTER(_Out), C.c_int]
+            L.or_pah_reemit.restype = C.c_int
+            L.or_pah_reemit.argtypes = [C.POINTER(_Model), C.POINTER(_PahSrc), C.POINTER(_Params),
+                                        C.c_void_p, C.POINTER(_Out), C.c_int]
             L.or_temperatures.restype = None
             L.or_temperatures.argtypes = [C.POINTER(_Model), C.c_void_p, C.c_void_p]
             L.or_temperature_guess.restype = None
@@ -191,7 +199,7 @@ def transport(model, n_packets, seed=1, model_id=0, mode=MODE_BW, lucy_mode=LUCY
               lucy_form=LUCY_LINEAR, lucy_tau=1e-2, mrw=False, mrw_tau_cell=10.0, mrw_gamma=2.0,
               pid_begin=0, pid_end=None, max_events=10_000_000, record_events=False,
               event_cap=0, pah_cap=0, traj_cap=0, T_prev=None, n_threads=1, esq=True,
-              accumulate=None, source_bins=0, pc_cameras=()):
+              accumulate=None, source_bins=0, pc_cameras=(), _pah=None):
     """Run packets [pid_begin, pid_end) of an N = n_packets emission and return
     a dict of numpy arrays (E_abs, count, esq, sed_esc, sed_cnt, events, pah,
     traj, stats, pc_img).  ``accumulate`` may hold a previous result dict whose
@@ -230,8 +238,12 @@ def transport(model, n_packets, seed=1, model_id=0, mode=MODE_BW, lucy_mode=LUCY
                _ptr(tr) if traj_cap else None, traj_cap, 0)
     out.pc_img = _ptr(pc_img) if pcs else None
     Tp = None if T_prev is None else np.ascontiguousarray(T_prev, dtype=np.float64).reshape(ns, nc)
-    rc = L.or_transport(C.byref(om.c), om.srcs, om.nsrc, C.byref(p), _ptr(Tp), C.byref(out),
-                        int(n_threads))
+    if _pah is None:
+        rc = L.or_transport(C.byref(om.c), om.srcs, om.nsrc, C.byref(p), _ptr(Tp), C.byref(out),
+                            int(n_threads))
+    else:
+        rc = L.or_pah_reemit(C.byref(om.c), C.byref(_pah), C.byref(p), _ptr(Tp), C.byref(out),
+                             int(n_threads))
     if rc != 0:
         raise ValueError("oracle transport rejected its arguments")
     stats = {k: int(out.stats[i]) for i, k in enumerate(STAT_NAMES)}
@@ -242,7 +254,26 @@ def transport(model, n_packets, seed=1, model_id=0, mode=MODE_BW, lucy_mode=LUCY
         o += nf * n * n
     return dict(E_abs=E, count=cnt, esq=q, sed_esc=sed, sed_cnt=sc,
                 events=ev[:out.n_events], pah=pah[:out.n_pah], traj=tr[:out.n_traj],
-                stats=stats, xi=model_luminosity(om) / n_packets, pc_img=imgs)
+                stats=stats, xi=model_luminosity(om) / n_packets if _pah is None else _pah.xi,
+                pc_img=imgs)
+
+
+def pah_reemit(model, records, xi, eps, eps_class=None, **kw):
+    """PAH re-emission pass (Sect. 2.1, Eqs. 6-7): one packet of energy xi per
+    stored PAH absorption (``records``, PAH_DTYPE or any array with a 'cell'
+    field), emitted uniformly in the record's cell with its bin drawn from
+    eps[n] (eps [n_eps][nf], n = eps_class[cell] or 0).  Other keywords as for
+    ``transport`` (n_packets is len(records); source_bins must stay 0)."""
+    om = _om(model)
+    rec = np.zeros(len(records), PAH_DTYPE)
+    rec["cell"] = np.asarray(records["cell"])
+    eps = np.ascontiguousarray(eps, dtype=np.float64).reshape(-1, om.nf)
+    cls = None if eps_class is None else np.ascontiguousarray(eps_class, dtype=np.int32).reshape(om.ncell)
+    ps = _PahSrc(_ptr(rec), len(rec), float(xi), _ptr(eps), eps.shape[0], _ptr(cls))
+    keep = (rec, eps, cls)
+    r = transport(model, len(rec), _pah=ps, **kw)
+    del keep
+    return r
 
 
 def model_luminosity(om):

@@ -350,6 +350,8 @@ typedef struct {
     double* src_w;      /* [nsrc][nf] emission weights L_nu dnu */
     double* src_L;      /* [nsrc] */
     unsigned char* lucy;/* [ncell] */
+    const or_pah_src* ps;  /* PAH re-emission pass, or NULL */
+    double* eps_w;      /* [n_eps][nf] eps_n(nu_j) dnu_j */
 } or_ctx;
 
 static double chi_ext(const or_model* m, int64_t c, int j)
@@ -480,37 +482,52 @@ static void run_packet(const or_ctx* C, or_out* o, uint64_t pid)
     rng_init(&r, p->seed, p->model_id, pid);
     uint32_t seq = 0;
 
-    /* emission (Sect. 2): source, frequency bin, isotropic direction */
     int si = 0, j = 0;
-    if (p->source_bins == 0) {
-        if (C->nsrc > 1) si = pick_cdf(C->src_L, C->nsrc, rng_u(&r));
-        j = pick_cdf(C->src_w + (size_t)si * m->nf, m->nf, rng_u(&r));
-    } else {
-        /* Eq. 1: the sources' combined luminosity is cut into m bins of equal
-         * energy L/m, and N/m packets are emitted in each: packet pid belongs
-         * to bin b = floor(pid m / N) and takes the point u = (b + 1/2) / m of
-         * the cumulative luminosity -- the source where the running sum of
-         * the L_i first reaches u L, then, by the fraction of that source's
-         * luminosity below the point, its frequency bin. */
-        const uint64_t b = (pid * (uint64_t)p->source_bins) / p->n_packets;
-        const double u = ((double)b + 0.5) / (double)p->source_bins;
-        double tot = 0.0;
-        for (int i = 0; i < C->nsrc; ++i) tot += C->src_L[i];
-        const double target = u * tot;
-        double below = 0.0, upto = 0.0;
-        for (si = 0; si < C->nsrc; ++si) {
-            upto = below + C->src_L[si];
-            if (upto >= target || si == C->nsrc - 1) break;
-            below = upto;
-        }
-        const double uf = (target - below) / (upto - below);
-        j = pick_cdf(C->src_w + (size_t)si * m->nf, m->nf, uf);
-    }
     double k[3], x[3];
-    { double u1 = rng_u(&r), u2 = rng_u(&r); iso_dir(u1, u2, k); }
-    for (int a = 0; a < 3; ++a) x[a] = C->src[si].pos[a];
     int idx[3];
-    locate(m, x, k, idx);
+    if (C->ps) {
+        /* PAH re-emission (Sect. 2.1): the record's cell is the source; the
+         * bin follows Eq. 6 with the cell's emissivity class, the position is
+         * uniform in the cell (one draw per axis), the direction isotropic */
+        const int64_t c = (int64_t)C->ps->rec[pid].cell;
+        const int n = C->ps->eps_class ? C->ps->eps_class[c] : 0;
+        j = pick_cdf(C->eps_w + (size_t)n * m->nf, m->nf, rng_u(&r));
+        idx[0] = (int)(c % m->nx);
+        idx[1] = (int)((c / m->nx) % m->ny);
+        idx[2] = (int)(c / ((int64_t)m->nx * m->ny));
+        for (int a = 0; a < 3; ++a) x[a] = m->box_min[a] + (idx[a] + rng_u(&r)) * m->cell;
+        { double u1 = rng_u(&r), u2 = rng_u(&r); iso_dir(u1, u2, k); }
+    } else {
+        /* emission (Sect. 2): source, frequency bin, isotropic direction */
+        if (p->source_bins == 0) {
+            if (C->nsrc > 1) si = pick_cdf(C->src_L, C->nsrc, rng_u(&r));
+            j = pick_cdf(C->src_w + (size_t)si * m->nf, m->nf, rng_u(&r));
+        } else {
+            /* Eq. 1: the sources' combined luminosity is cut into m bins of
+             * equal energy L/m, and N/m packets are emitted in each: packet
+             * pid belongs to bin b = floor(pid m / N) and takes the point
+             * u = (b + 1/2) / m of the cumulative luminosity -- the source
+             * where the running sum of the L_i first reaches u L, then, by
+             * the fraction of that source's luminosity below the point, its
+             * frequency bin. */
+            const uint64_t b = (pid * (uint64_t)p->source_bins) / p->n_packets;
+            const double u = ((double)b + 0.5) / (double)p->source_bins;
+            double tot = 0.0;
+            for (int i = 0; i < C->nsrc; ++i) tot += C->src_L[i];
+            const double target = u * tot;
+            double below = 0.0, upto = 0.0;
+            for (si = 0; si < C->nsrc; ++si) {
+                upto = below + C->src_L[si];
+                if (upto >= target || si == C->nsrc - 1) break;
+                below = upto;
+            }
+            const double uf = (target - below) / (upto - below);
+            j = pick_cdf(C->src_w + (size_t)si * m->nf, m->nf, uf);
+        }
+        { double u1 = rng_u(&r), u2 = rng_u(&r); iso_dir(u1, u2, k); }
+        for (int a = 0; a < 3; ++a) x[a] = C->src[si].pos[a];
+        locate(m, x, k, idx);
+    }
     o->stats[OR_S_EMIT]++;
     log_event(o, pid, &seq, OR_T_EMIT, inside(m, idx) ? lin(m, idx) : 0, j, x, k);
     uint64_t n_ev = 0;
@@ -678,10 +695,11 @@ static void zero_out_counts(or_out* o)
     memset(o->stats, 0, sizeof(o->stats));
 }
 
-int or_transport(const or_model* m, const or_source* src, int nsrc, const or_params* p,
-                 const double* T_prev, or_out* out, int n_threads)
+static int transport_impl(const or_model* m, const or_source* src, int nsrc,
+                          const or_pah_src* ps, const or_params* p, const double* T_prev,
+                          or_out* out, int n_threads)
 {
-    if (nsrc < 1 || m->nf < 1 || m->ns < 1 || m->ns > 64 || p->n_packets == 0) return 1;
+    if (m->nf < 1 || m->ns < 1 || m->ns > 64 || p->n_packets == 0) return 1;
     if (p->pid_end < p->pid_begin || p->pid_end > p->n_packets) return 1;
     if (p->n_pc < 0 || (p->n_pc > 0 && !p->pc)) return 1;
     for (int c = 0; c < p->n_pc; ++c)
@@ -689,8 +707,10 @@ int or_transport(const or_model* m, const or_source* src, int nsrc, const or_par
     or_ctx C;
     C.m = m; C.p = p; C.T_prev = T_prev; C.nsrc = nsrc; C.src = src;
     C.vol = m->cell * m->cell * m->cell;
-    C.src_w = (double*)malloc(sizeof(double) * nsrc * m->nf);
-    C.src_L = (double*)malloc(sizeof(double) * nsrc);
+    C.ps = ps;
+    C.eps_w = NULL;
+    C.src_w = (double*)malloc(sizeof(double) * (nsrc > 0 ? nsrc : 1) * m->nf);
+    C.src_L = (double*)malloc(sizeof(double) * (nsrc > 0 ? nsrc : 1));
     double Ltot = 0.0;
     for (int i = 0; i < nsrc; ++i) {
         or_source_lnu(m, &src[i], C.src_w + (size_t)i * m->nf);
@@ -699,6 +719,14 @@ int or_transport(const or_model* m, const or_source* src, int nsrc, const or_par
         Ltot += src[i].L;
     }
     C.xi = Ltot / (double)p->n_packets;
+    if (ps) {
+        /* Eq. 6 on the model's frequency bins: weights eps_n(nu_j) dnu_j */
+        C.eps_w = (double*)malloc(sizeof(double) * (size_t)ps->n_eps * m->nf);
+        for (int n = 0; n < ps->n_eps; ++n)
+            for (int j = 0; j < m->nf; ++j)
+                C.eps_w[(size_t)n * m->nf + j] = ps->eps[(size_t)n * m->nf + j] * m->dnu[j];
+        C.xi = ps->xi;
+    }
     int64_t nc = ncell_of(m);
     C.lucy = (unsigned char*)calloc((size_t)nc, 1);
     for (int64_t c = 0; c < nc; ++c) {
@@ -783,8 +811,37 @@ int or_transport(const or_model* m, const or_source* src, int nsrc, const or_par
         }
         free(parts);
     }
-    free(C.src_w); free(C.src_L); free(C.lucy);
+    free(C.src_w); free(C.src_L); free(C.lucy); free(C.eps_w);
     return 0;
+}
+
+int or_transport(const or_model* m, const or_source* src, int nsrc, const or_params* p,
+                 const double* T_prev, or_out* out, int n_threads)
+{
+    if (nsrc < 1) return 1;
+    return transport_impl(m, src, nsrc, NULL, p, T_prev, out, n_threads);
+}
+
+int or_pah_reemit(const or_model* m, const or_pah_src* ps, const or_params* p,
+                  const double* T_prev, or_out* out, int n_threads)
+{
+    if (!ps || !ps->rec || !ps->eps || ps->n_eps < 1 || ps->n_rec != p->n_packets) return 1;
+    if (p->source_bins != 0 || !(ps->xi > 0.0)) return 1;
+    const int64_t nc = ncell_of(m);
+    for (uint64_t i = 0; i < ps->n_rec; ++i)
+        if ((int64_t)ps->rec[i].cell >= nc) return 1;
+    if (ps->eps_class)
+        for (int64_t c = 0; c < nc; ++c)
+            if (ps->eps_class[c] < 0 || ps->eps_class[c] >= ps->n_eps) return 1;
+    for (int n = 0; n < ps->n_eps; ++n) {
+        double tot = 0.0;
+        for (int j = 0; j < m->nf; ++j) {
+            if (!(ps->eps[(size_t)n * m->nf + j] >= 0.0)) return 1;
+            tot += ps->eps[(size_t)n * m->nf + j];
+        }
+        if (!(tot > 0.0)) return 1;
+    }
+    return transport_impl(m, NULL, 0, ps, p, T_prev, out, n_threads);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -86,6 +86,19 @@ typedef struct {
 
 typedef struct { double theta, phi; int npix; double D; double pixel; } or_camera;
 
+/* PAH re-emission pass (Sect. 2.1): the stored PAH absorptions become the
+ * sources, one packet of energy xi per record, emitted from a point drawn
+ * uniformly in the record's cell, in the frequency bin drawn from Eq. 6 with
+ * the emissivity eps_n(nu) of Eq. 7 supplied per class n. */
+typedef struct {
+    const or_pah* rec;           /* [n_rec] stored absorptions (cell used, nu ignored) */
+    uint64_t n_rec;
+    double xi;                   /* packet energy of the pass that stored them */
+    const double* eps;           /* [n_eps][nf] eps_n(nu_j), >= 0 */
+    int n_eps;
+    const int* eps_class;        /* [ncell] class n of each cell, or NULL (class 0) */
+} or_pah_src;
+
 /* primitives exposed for the pins */
 void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 void or_uniforms(uint64_t seed, uint32_t model_id, uint64_t pid, uint32_t n, double* out);
@@ -104,6 +117,10 @@ int or_dda_segments(const or_model* m, const double x[3], const double k[3], int
 /* the path */
 int or_transport(const or_model* m, const or_source* src, int nsrc, const or_params* p,
                  const double* T_prev, or_out* out, int n_threads);
+/* Runs packets [pid_begin, pid_end) of the pass; p->n_packets must equal
+ * ps->n_rec and p->source_bins must be 0.  Packet pid starts from rec[pid]. */
+int or_pah_reemit(const or_model* m, const or_pah_src* ps, const or_params* p,
+                  const double* T_prev, or_out* out, int n_threads);
 void or_temperatures(const or_model* m, const double* E_abs, double* T);
 void or_temperature_guess(const or_model* m, const or_source* src, int nsrc, double* T);
 void or_raytrace(const or_model* m, const double* T, const or_event* ev, uint64_t nev,

@@ -303,11 +303,15 @@ struct HostModel {
     std::vector<float> cdf32;
 };
 
+// xi_fixed > 0: a pass without sources (PAH re-emission) whose packets carry
+// that energy; otherwise xi = L / n_packets of the 1..64 sources.
 static rt_status make_model(const rt_grid* g, const rt_opacity* op, const rt_source* src, int nsrc,
                             uint64_t n_packets, uint64_t pid_begin, uint32_t model_id, int model_index,
-                            const double* T_prev, const rt_transport_out* o, HostModel& hm)
+                            const double* T_prev, const rt_transport_out* o, HostModel& hm,
+                            double xi_fixed = 0.0)
 {
-    if (!src || nsrc < 1 || nsrc > 64) return fail(RT_ERR_INVALID_ARG, "transport: need 1..64 sources");
+    if (xi_fixed > 0.0) nsrc = 0;
+    else if (!src || nsrc < 1 || nsrc > 64) return fail(RT_ERR_INVALID_ARG, "transport: need 1..64 sources");
     const int nf = op->nf;
     double Ltot = 0.0;
     hm.pos.resize(3 * nsrc);
@@ -343,7 +347,7 @@ static rt_status make_model(const rt_grid* g, const rt_opacity* op, const rt_sou
         Ltot += s.L;
         hm.Lcdf[i] = Ltot;
     }
-    if (!(Ltot > 0.0)) return fail(RT_ERR_INVALID_ARG, "transport: total luminosity must be > 0");
+    if (!(Ltot > 0.0) && !(xi_fixed > 0.0)) return fail(RT_ERR_INVALID_ARG, "transport: total luminosity must be > 0");
     ModelDev& m = hm.md;
     std::memset(&m, 0, sizeof(m));
     m.rho = g->d_packed;
@@ -354,7 +358,7 @@ static rt_status make_model(const rt_grid* g, const rt_opacity* op, const rt_sou
     m.nsrc = nsrc;
     m.cell = g->cell;
     m.vol = g->cell * g->cell * g->cell;
-    m.xi = Ltot / (double)n_packets;
+    m.xi = xi_fixed > 0.0 ? xi_fixed : Ltot / (double)n_packets;
     m.log2_4piV = 2.0 * log2(g->cell);
     for (int a = 0; a < 3; ++a) m.box_min[a] = g->box_min[a];
     m.pid_begin = pid_begin;
@@ -505,6 +509,21 @@ static rt_status single_model_options(TransportKP& kp, const rt_opacity* op,
     return RT_OK;
 }
 
+// The stored absorptions and emissivity classes of a PAH re-emission pass.
+struct PahPass {
+    const rt_pah_event* rec;
+    uint64_t n_rec;
+    double xi;
+    const double* eps;
+    int n_eps;
+    const int* eps_class;
+};
+
+static rt_status transport_one(rt_ctx* ctx, const rt_grid* grid, const rt_opacity* op,
+                               const rt_source* sources, int n_sources, const rt_transport_params* p,
+                               const double* T_prev, const rt_transport_out* out, cudaStream_t s,
+                               const PahPass* pp);
+
 }  // namespace rtgb
 
 struct rt_batch {
@@ -526,6 +545,45 @@ rt_status rt_transport(rt_ctx* ctx, const rt_grid* grid, const rt_opacity* op,
                        const rt_source* sources, int n_sources, const rt_transport_params* p,
                        const double* T_prev, const rt_transport_out* out, rt_stream stream)
 {
+    return transport_one(ctx, grid, op, sources, n_sources, p, T_prev, out, (cudaStream_t)stream, nullptr);
+}
+
+rt_status rt_pah_reemit(rt_ctx* ctx, const rt_grid* grid, const rt_opacity* op,
+                        const rt_pah_event* records, uint64_t n_records, double xi,
+                        const double* eps, int n_eps, const int* eps_class,
+                        const rt_transport_params* p, const double* T_prev,
+                        const rt_transport_out* out, rt_stream stream)
+{
+    if (!op || !ctx || ctx->magic != kMagic) return fail(RT_ERR_INVALID_ARG, "rt_pah_reemit: bad context or NULL opacity");
+    if (!records || n_records == 0) return fail(RT_ERR_INVALID_ARG, "rt_pah_reemit: need records");
+    if (!p || p->n_packets != n_records)
+        return fail(RT_ERR_INVALID_ARG, "rt_pah_reemit: p->n_packets must equal n_records");
+    if (p->source_bins != 0) return fail(RT_ERR_INVALID_ARG, "rt_pah_reemit: source_bins must be 0");
+    if (!(xi > 0.0) || !isfin(xi)) return fail(RT_ERR_INVALID_ARG, "rt_pah_reemit: xi must be finite and > 0");
+    if (!eps || n_eps < 1 || n_eps > 65535)
+        return fail(RT_ERR_INVALID_ARG, "rt_pah_reemit: need 1..65535 emissivity classes");
+    for (int n = 0; n < n_eps; ++n) {
+        double tot = 0.0;
+        for (int j = 0; j < op->nf; ++j) {
+            const double v = eps[(size_t)n * op->nf + j];
+            if (!(v >= 0.0) || !isfin(v)) return fail(RT_ERR_INVALID_ARG, "rt_pah_reemit: eps must be finite and >= 0");
+            tot += v * op->dnu[j];
+        }
+        if (!(tot > 0.0)) return fail(RT_ERR_INVALID_ARG, "rt_pah_reemit: an emissivity class is zero on the grid");
+    }
+    const PahPass pp{ records, n_records, xi, eps, n_eps, eps_class };
+    return transport_one(ctx, grid, op, nullptr, 0, p, T_prev, out, (cudaStream_t)stream, &pp);
+}
+
+}  // extern "C"
+
+namespace rtgb {
+
+static rt_status transport_one(rt_ctx* ctx, const rt_grid* grid, const rt_opacity* op,
+                               const rt_source* sources, int n_sources, const rt_transport_params* p,
+                               const double* T_prev, const rt_transport_out* out, cudaStream_t s,
+                               const PahPass* pp)
+{
     if (!ctx || ctx->magic != kMagic) return fail(RT_ERR_STATE, "rt_transport: bad context");
     if (!grid || !op) return fail(RT_ERR_INVALID_ARG, "rt_transport: NULL grid or opacity");
     if (grid->ctx != ctx || op->ctx != ctx) return fail(RT_ERR_STATE, "rt_transport: handle from another context");
@@ -541,10 +599,9 @@ rt_status rt_transport(rt_ctx* ctx, const rt_grid* grid, const rt_opacity* op,
     if (p->mode == RT_MODE_FROZEN_T && !T_prev)
         return fail(RT_ERR_INVALID_ARG, "rt_transport: frozen-T mode needs T_prev");
     RT_CUDA(cudaSetDevice(ctx->device));
-    cudaStream_t s = (cudaStream_t)stream;
     std::vector<HostModel> hms(1);
     st = make_model(grid, op, sources, n_sources, p->n_packets, p->pid_begin, p->model_id, 0,
-                    T_prev, out, hms[0]);
+                    T_prev, out, hms[0], pp ? pp->xi : 0.0);
     if (st != RT_OK) return st;
     if (p->pid_end == p->pid_begin) return RT_OK;
     st = pack_grid(const_cast<rt_grid*>(grid), op, p->lucy_mode, p->lucy_tau, p->precision, s);
@@ -569,6 +626,40 @@ rt_status rt_transport(rt_ctx* ctx, const rt_grid* grid, const rt_opacity* op,
     fill_pc(kp, grid, p, out);
     st = single_model_options(kp, op, p, out, n_sources, hms[0].md);
     if (st != RT_OK) { cudaFreeAsync(dm.buf, s); if (acc) cudaFreeAsync(acc, s); return st; }
+    // PAH pass: the emissivity classes' cumulative tables (Eq. 6), FP64 and
+    // normalised FP32
+    char* ebuf = nullptr;
+    if (pp) {
+        const int nf = op->nf;
+        const size_t n = (size_t)pp->n_eps * nf;
+        std::vector<double> c64(n);
+        std::vector<float> c32(n);
+        for (int k = 0; k < pp->n_eps; ++k) {
+            double acc_e = 0.0;
+            for (int j = 0; j < nf; ++j) {
+                acc_e += pp->eps[(size_t)k * nf + j] * op->dnu[j];
+                c64[(size_t)k * nf + j] = acc_e;
+            }
+            for (int j = 0; j < nf; ++j) c32[(size_t)k * nf + j] = (float)(c64[(size_t)k * nf + j] / acc_e);
+            c32[(size_t)k * nf + nf - 1] = 1.0f;
+        }
+        const size_t o32 = align_up(sizeof(double) * n, 256);
+        cudaError_t e = cudaMallocAsync((void**)&ebuf, o32 + sizeof(float) * n, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(ebuf, c64.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(ebuf + o32, c32.data(), sizeof(float) * n, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) {
+            cudaFreeAsync(dm.buf, s);
+            if (acc) cudaFreeAsync(acc, s);
+            if (ebuf) cudaFreeAsync(ebuf, s);
+            return cuda_fail(e, "rt_pah_reemit emissivity tables");
+        }
+        kp.pah_src = pp->rec;
+        kp.eps_cdf64 = (const double*)ebuf;
+        kp.eps_cdf32 = (const float*)(ebuf + o32);
+        kp.eps_class = pp->eps_class;
+        kp.n_eps = pp->n_eps;
+        kp.smem_cdf = 0;
+    }
     // deferred packets: a queue in device memory, drained by a second launch
     char* qbuf = nullptr;
     if (p->defer_events > 0) {
@@ -579,6 +670,7 @@ rt_status rt_transport(rt_ctx* ctx, const rt_grid* grid, const rt_opacity* op,
         if (e != cudaSuccess) {
             cudaFreeAsync(dm.buf, s);
             if (acc) cudaFreeAsync(acc, s);
+            if (ebuf) cudaFreeAsync(ebuf, s);
             if (qbuf) cudaFreeAsync(qbuf, s);
             return cuda_fail(e, "rt_transport defer queue");
         }
@@ -601,9 +693,14 @@ rt_status rt_transport(rt_ctx* ctx, const rt_grid* grid, const rt_opacity* op,
         st = launch_finalize(acc, hms[0].md.acc_q, n_acc, hms[0].md.xi, out->E_abs, out->esq, s);
     cudaFreeAsync(dm.buf, s);
     if (acc) cudaFreeAsync(acc, s);
+    if (ebuf) cudaFreeAsync(ebuf, s);
     if (qbuf) cudaFreeAsync(qbuf, s);
     return st;
 }
+
+}  // namespace rtgb
+
+extern "C" {
 
 rt_status rt_batch_create(rt_ctx* ctx, const rt_opacity* op, int n_models, const rt_model* models,
                           const rt_transport_params* p, rt_batch** out)

@@ -174,6 +174,13 @@ struct TransportKP {
     unsigned long long* defer_n;        // queue cursor (device)
     unsigned long long defer_cap;
     int resume;                         // 1: packets come from the queue, not from emission
+    // PAH re-emission pass (single-model calls): packet pid starts in the
+    // cell of record pid, its bin drawn from the cell's emissivity class
+    const rt_pah_event* pah_src;        // NULL: emission from the sources
+    const double* eps_cdf64;            // [n_eps][nf] cumulative eps dnu
+    const float* eps_cdf32;             // [n_eps][nf] cumulative, normalised to 1
+    const int* eps_class;               // [ncell] or NULL (class 0)
+    int n_eps;
     int n_pc;                           // photon-counting cameras (single-model calls)
     double* pc_img;
     double pc_ctr[3];                   // grid centre, cell units

@@ -298,7 +298,8 @@ __device__ __forceinline__ unsigned char* smem_raw()
 // compiled in, 4 = model descriptors read from the launch parameters (constant
 // bank) instead of global memory, 8 = a single model (its index and grid
 // pointer are constants, not lane registers), 16 = the deferred-packet queue
-// compiled in; production launches leave unused paths out of the hot code.
+// compiled in, 32 = PAH re-emission sources compiled in; production launches
+// leave unused paths out of the hot code.
 template <typename R, int NS, int FEAT>
 struct Kernel {
     using PT = typename PackedT<NS>::T;
@@ -308,6 +309,7 @@ struct Kernel {
     static constexpr bool PARAM = (FEAT & 4) != 0;
     static constexpr bool SINGLE = (FEAT & 8) != 0;
     static constexpr bool HAS_DEFER = (FEAT & 16) != 0;
+    static constexpr bool HAS_PAH = (FEAT & 32) != 0;
 
     const TransportKP& P;
     const ModelDev* md;        // model of the lane's current packet
@@ -549,6 +551,12 @@ struct Kernel {
         L.nev = 0;
         L.ncross = 0;
         L.nlucy = 0;
+        if constexpr (HAS_PAH) {
+            if (P.pah_src) {
+                emit_pah(L, md->pid_begin + (w - P.prefix[lo]));
+                return;
+            }
+        }
         int si = 0;
         R ub;
         if (P.source_bins) {
@@ -596,6 +604,45 @@ struct Kernel {
             L.st = ST_ESCAPE;
             return;
         }
+#pragma unroll
+        for (int s = 0; s < NS; ++s) L.rho[s] = R(0);
+        load_freq(L);
+        load_cell(L);
+        L.st = ST_FLIGHT;
+    }
+
+    // PAH re-emission (Sect. 2.1): the stored absorption's cell is the
+    // source; the bin follows Eq. 6 with the cell's emissivity class, the
+    // point is uniform in the cell (one draw per axis), the direction
+    // isotropic.  A record outside the grid, or a cell whose class is out of
+    // range, is counted as stuck and emits nothing.
+    __device__ __forceinline__ void emit_pah(Lane<R, NS>& L, uint64_t pid)
+    {
+        const int c = (int)P.pah_src[pid].cell;
+        const R ub = U(L);
+        const R ux = U(L), uy = U(L), uz = U(L);
+        const R u1 = U(L), u2 = U(L);
+        const bool in = (unsigned)c < (unsigned)md->ncell;
+        const int n = !in ? -1 : (P.eps_class ? P.eps_class[c] : 0);
+        count(RT_STAT_EMITTED, 1);
+        if ((unsigned)n >= (unsigned)P.n_eps) {
+            count(RT_STAT_STUCK, 1);
+            end_packet(L);
+            return;
+        }
+        if constexpr (DBG) {
+            const double* cdf = P.eps_cdf64 + (size_t)n * P.nf;
+            L.j = search_cdf(cdf, P.nf, ub * cdf[P.nf - 1]);
+        } else {
+            L.j = search_cdf(P.eps_cdf32 + (size_t)n * P.nf, P.nf, ub);
+        }
+        const int ix = c % md->nx, iy = (c / md->nx) % md->ny, iz = c / (md->nx * md->ny);
+        L.x[0] = (R)ix + ux;
+        L.x[1] = (R)iy + uy;
+        L.x[2] = (R)iz + uz;
+        iso_dir(u1, u2, L.k);
+        L.c = c;
+        traj(L, RT_TRAJ_EMIT, L.x);
 #pragma unroll
         for (int s = 0; s < NS; ++s) L.rho[s] = R(0);
         load_freq(L);
@@ -1325,8 +1372,16 @@ rt_status launch_feat(rt_ctx* ctx, const TransportKP& kp, int schedule, int thre
                       int blocks_per_sm, cudaStream_t s)
 {
     if constexpr (sizeof(R) == 8) {
+        if (kp.pah_src) return launch_one<R, NS, 51>(ctx, kp, schedule, threads, blocks_per_sm, s);
         return launch_one<R, NS, 19>(ctx, kp, schedule, threads, blocks_per_sm, s);
     } else {
+        // PAH re-emission pass: the single-model variant, or the generic one
+        // with every optional path compiled in
+        if (kp.pah_src) {
+            if (!kp.mrw && !kp.want_traj && !kp.defer_events && kp.single)
+                return launch_one<R, NS, 44>(ctx, kp, schedule, threads, blocks_per_sm, s);
+            return launch_one<R, NS, 51>(ctx, kp, schedule, threads, blocks_per_sm, s);
+        }
         // trajectory logging runs the generic variants; otherwise descriptors
         // come from the parameters when they fit, and one model is constant
         const int feat = (kp.mrw ? 1 : 0) |

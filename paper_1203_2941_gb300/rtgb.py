@@ -32,7 +32,8 @@ EXPORTS = ["rt_last_error", "rt_version", "rt_ctx_create", "rt_ctx_destroy", "rt
            "rt_grid_free", "rt_opacity_upload", "rt_opacity_free", "rt_transport_params_default",
            "rt_transport", "rt_temperatures", "rt_temperature_guess", "rt_raytrace",
            "rt_raytrace_backward", "rt_batch_create", "rt_batch_run", "rt_batch_free",
-           "rt_transport_batched", "rt_philox", "rt_kernel_launches", "rt_transport_noalloc", "rt_visibilities"]
+           "rt_transport_batched", "rt_philox", "rt_kernel_launches", "rt_transport_noalloc", "rt_visibilities",
+           "rt_pah_reemit"]
 
 
 class RtError(RuntimeError):
@@ -115,6 +116,8 @@ def load(path: str = LIB_PATH):
                                C.POINTER(rt_transport_out), vp]),
         "rt_transport_noalloc": (i32, [vp, vp, vp, vp, i32, C.POINTER(rt_transport_params), vp,
                                        C.POINTER(rt_transport_out), vp]),
+        "rt_pah_reemit": (i32, [vp, vp, vp, vp, u64, dbl, vp, i32, vp,
+                                C.POINTER(rt_transport_params), vp, C.POINTER(rt_transport_out), vp]),
         "rt_temperatures": (i32, [vp, vp, vp, vp, vp, vp]),
         "rt_temperature_guess": (i32, [vp, vp, vp, i32, vp, vp]),
         "rt_raytrace": (i32, [vp, vp, vp, vp, vp, u64, vp, dbl, vp, i32, vp, i32, vp, i32, vp, vp,
@@ -204,6 +207,12 @@ def rt_transport(ctx, grid, opac, sources, n_sources, params, T_prev_ptr, out, s
 def rt_transport_noalloc(ctx, grid, opac, sources, n_sources, params, T_prev_ptr, out, stream=0):
     _check(load().rt_transport_noalloc(ctx, grid, opac, sources, n_sources, C.byref(params),
                                        T_prev_ptr, C.byref(out), stream), "rt_transport_noalloc")
+
+
+def rt_pah_reemit(ctx, grid, opac, rec_ptr, n_rec, xi, eps, n_eps, cls_ptr, params, T_prev_ptr,
+                  out, stream=0):
+    _check(load().rt_pah_reemit(ctx, grid, opac, rec_ptr, n_rec, xi, eps, n_eps, cls_ptr,
+                                C.byref(params), T_prev_ptr, C.byref(out), stream), "rt_pah_reemit")
 
 
 def rt_temperatures(ctx, grid, opac, E_ptr, T_ptr, stream=0):

@@ -275,6 +275,60 @@ def transport(ctx: Context, grid: Grid, opac: Opacity, sources: Sources, n_packe
     return out
 
 
+def _pah_records(records):
+    """Stored PAH absorptions as a device uint8 tensor (8 bytes each) and
+    their count."""
+    if isinstance(records, TransportOut):
+        n = int(min(records.stats[14].item(), records.pah_cap))
+        return records.pah, n
+    if isinstance(records, np.ndarray):
+        rec = np.zeros(len(records), R.PAH_DTYPE)
+        rec["cell"] = records["cell"]
+        if len(rec) == 0:
+            return None, 0
+        return torch.from_numpy(rec.view(np.uint8).copy()).cuda(), len(rec)
+    raise TypeError("records must be a TransportOut or a numpy PAH record array")
+
+
+def pah_reemit(ctx: Context, grid: Grid, opac: Opacity, records, xi: float, eps,
+               eps_class: Optional[torch.Tensor] = None, out: Optional[TransportOut] = None,
+               T_prev: Optional[torch.Tensor] = None, event_cap: int = 0, pah_cap: int = 0,
+               traj_cap: int = 0, stream=None, pc_cams: Sequence[PcCamera] = (),
+               **kw) -> TransportOut:
+    """PAH re-emission pass (rt_pah_reemit): one packet of energy ``xi`` per
+    stored PAH absorption of ``records`` (a TransportOut of an earlier pass
+    or a numpy record array), bins drawn from ``eps`` [n_eps][nf] by the
+    cells' ``eps_class`` (device int32 [ncell] or None).  Results accumulate
+    into ``out`` (a new TransportOut by default; its PAH buffer receives this
+    pass's PAH absorptions and must not be the records' buffer)."""
+    rec, n = _pah_records(records)
+    if out is None:
+        out = TransportOut(grid.ncell, grid.ns, opac.nf, event_cap, pah_cap, traj_cap)
+    if isinstance(records, TransportOut) and records is out:
+        raise ValueError("the pass's output must not hold its own input records")
+    out.xi = float(xi)
+    if n == 0:
+        return out
+    if kw.get("record_events") is None and out.event_cap:
+        kw["record_events"] = True
+    p = make_params(n, **kw)
+    pca = None
+    if pc_cams:
+        out.ensure_pc(pc_cams)
+        pca = pc_cameras(pc_cams)
+        p.pc_cams, p.n_pc_cams = C.cast(pca, C.c_void_p), len(pc_cams)
+    e = np.ascontiguousarray(eps, dtype=np.float64).reshape(-1, opac.nf)
+    cls = None
+    if eps_class is not None:
+        cls = torch.as_tensor(eps_class, dtype=torch.int32, device="cuda").contiguous()
+    if T_prev is not None:
+        T_prev = T_prev.to(dtype=torch.float64).contiguous()
+    R.rt_pah_reemit(ctx.h, grid.h, opac.h, _ptr(rec), n, float(xi),
+                    e.ctypes.data_as(C.c_void_p), e.shape[0], _ptr(cls), p, _ptr(T_prev),
+                    out.c_struct(), _stream(stream))
+    return out
+
+
 def temperatures(ctx: Context, grid: Grid, opac: Opacity, E_abs: torch.Tensor,
                  T: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
     E_abs = E_abs.contiguous()

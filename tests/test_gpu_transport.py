@@ -391,3 +391,94 @@ def test_photon_counting_rejections(rt, ctx):
         rt.transport(ctx, grid, opac, srcs, 100, pc_cams=[rt.PcCamera(0.0, 0.0, 8, 1.5)])
     with pytest.raises(rt.RtError):
         rt.transport(ctx, grid, opac, srcs, 100, pc_cams=[rt.PcCamera(0.0, 0.0, 8, 0.5)] * 17)
+
+
+# ------------------------------------------------ PAH re-emission pass (Sect. 2.1)
+def test_fp64_pah_reemission_matches_oracle(rt, ctx, O):
+    """Records stored by the oracle's B&W pass of the torus, re-emitted on both
+    sides (frozen T): per-packet trajectories equal to 1e-9, the same
+    absorbed energies, escape tallies and re-stored PAH records."""
+    m = W.clumpy_torus(n=16, n_clump=60, seed=3, nf=24)
+    eps, cls = W.pah_emissivity(m)
+    r1 = O.transport(m, 3000, seed=4, mode=O.MODE_BW, pah_cap=3000)
+    rec, xi = r1["pah"], r1["xi"]
+    n = len(rec)
+    assert n > 20
+    grid, opac, _ = _setup(rt, ctx, m)
+    T0 = np.random.default_rng(3).uniform(30, 700, size=(m.ns, m.ncell))
+    out = rt.pah_reemit(ctx, grid, opac, rec, xi, eps, torch.tensor(cls, device="cuda"),
+                        mode=rt.rtgb.RT_MODE_FROZEN_T, precision=rt.rtgb.RT_PREC_FP64,
+                        T_prev=torch.tensor(T0, device="cuda"), traj_cap=400 * n, pah_cap=n,
+                        seed=21, model_id=1)
+    torch.cuda.synchronize()
+    ref = O.pah_reemit(m, rec, xi, eps, cls, seed=21, model_id=1, mode=O.MODE_FROZEN_T, T_prev=T0,
+                       traj_cap=400 * n, pah_cap=n, n_threads=4)
+    st = out.stats_dict()
+    assert st["traj_dropped"] == 0 and ref["stats"]["traj_dropped"] == 0
+    _traj_compare(out.traj_numpy(), ref["traj"], m.cell * 16)
+    for k in ("emitted", "escaped", "pah", "absorptions", "crossings", "scatters", "lucy_deposits"):
+        assert st[k] == ref["stats"][k], k
+    g = out.numpy()
+    np.testing.assert_allclose(g["E_abs"], ref["E_abs"], rtol=1e-9, atol=1e-9 * ref["E_abs"].max())
+    np.testing.assert_allclose(g["sed_esc"], ref["sed_esc"], rtol=1e-9, atol=1e-12 * xi)
+    assert sorted(out.pah_numpy()["cell"].tolist()) == sorted(ref["pah"]["cell"].tolist())
+
+
+def test_fp32_pah_reemission_conserves_energy(rt, ctx):
+    """FP32 B&W: the GPU's own stored PAH absorptions re-emitted with the same
+    xi; first-pass escapes + second-pass escapes + second-pass stores = L."""
+    m = W.clumpy_torus(n=32, n_clump=200, seed=5, nf=32)
+    eps, cls = W.pah_emissivity(m)
+    grid, opac, srcs = _setup(rt, ctx, m)
+    N = 400_000
+    o1 = rt.transport(ctx, grid, opac, srcs, N, pah_cap=N, seed=8)
+    torch.cuda.synchronize()
+    n1 = o1.stats_dict()["pah"]
+    assert n1 > 1000 and o1.stats_dict()["pah_dropped"] == 0
+    o2 = rt.pah_reemit(ctx, grid, opac, o1, o1.xi, eps, torch.tensor(cls, device="cuda"),
+                       pah_cap=n1, seed=8, model_id=1)
+    torch.cuda.synchronize()
+    s2 = o2.stats_dict()
+    assert s2["emitted"] == n1 and s2["escaped"] + s2["pah"] == n1 and s2["stuck"] == 0
+    e1, e2 = o1.sed_esc.sum().item(), o2.sed_esc.sum().item()
+    assert e1 + e2 + s2["pah"] * o1.xi == pytest.approx(m.luminosity, rel=1e-9)
+
+
+def test_fp32_pah_reemission_frequency_law(rt, ctx):
+    """Eq. 6 in the FP32 build: dust-free grid, records in class-0 cells; the
+    escape counts per bin are a multinomial sample of eps_0 dnu."""
+    m = W.uniform_cube(n=6, tau_cell=0.0, nf=40)
+    m.rho[:] = 0.0
+    eps, cls = W.pah_emissivity(m, n_classes=3)
+    cells = np.nonzero(cls == 0)[0]
+    rec = np.zeros(300_000, rt.rtgb.PAH_DTYPE)
+    rec["cell"] = np.resize(cells, len(rec))
+    grid, opac, _ = _setup(rt, ctx, m)
+    out = rt.pah_reemit(ctx, grid, opac, rec, 1.0, eps, torch.tensor(cls, device="cuda"),
+                        mode=rt.rtgb.RT_MODE_NOREEMIT, seed=3)
+    torch.cuda.synchronize()
+    cnt = out.sed_cnt.cpu().numpy().sum(axis=0).astype(np.float64)
+    w = eps[0] * m.dnu
+    expect = len(rec) * w / w.sum()
+    keep = expect > 0
+    c2 = ((cnt[keep] - expect[keep]) ** 2 / expect[keep]).sum()
+    dof = keep.sum() - 1
+    assert abs(c2 - dof) <= 5 * math.sqrt(2 * dof), (c2, dof)
+
+
+def test_pah_reemission_bad_inputs(rt, ctx):
+    m = W.uniform_cube(n=3, tau_cell=0.1)
+    grid, opac, _ = _setup(rt, ctx, m)
+    rec = np.zeros(8, rt.rtgb.PAH_DTYPE)
+    with pytest.raises(rt.RtError):
+        rt.pah_reemit(ctx, grid, opac, rec, 1.0, np.zeros((1, m.nf)))
+    with pytest.raises(rt.RtError):
+        rt.pah_reemit(ctx, grid, opac, rec, 0.0, np.ones((1, m.nf)))
+    rec["cell"][:3] = [m.ncell, 2 ** 31, 5]                 # outside the grid: counted as stuck
+    cls = torch.full((m.ncell,), 7, dtype=torch.int32, device="cuda")
+    cls[1:] = 0                                              # cell 0's class is out of range
+    out = rt.pah_reemit(ctx, grid, opac, rec, 1.0, np.ones((1, m.nf)), cls,
+                        mode=rt.rtgb.RT_MODE_NOREEMIT)
+    torch.cuda.synchronize()
+    st = out.stats_dict()
+    assert st["emitted"] == 8 and st["stuck"] == 2 + 5 and st["escaped"] + st["absorptions"] >= 1

@@ -586,3 +586,104 @@ def test_photon_counting_matches_escape_tallies(O):
     assert 0 < part.sum() < full.sum()
     for a, b in zip(r1["pc_img"], r4["pc_img"]):
         np.testing.assert_allclose(a, b, rtol=1e-12, atol=0)
+
+
+# ------------------------------------------------ PAH re-emission pass (Sect. 2.1)
+def _chi2_ok(counts, expect, z=5.0):
+    """chi^2 of a multinomial histogram within z sigma of its mean."""
+    keep = expect > 0
+    assert np.all(counts[~keep] == 0)
+    c2 = ((counts[keep] - expect[keep]) ** 2 / expect[keep]).sum()
+    dof = keep.sum() - 1
+    return abs(c2 - dof) <= z * math.sqrt(2 * dof), (c2, dof)
+
+
+def test_pah_reemission_frequency_law_per_class(O):
+    """Eq. 6 with the class's eps_n: in a dust-free grid every re-emitted
+    packet escapes at its emitted bin, so the escape counts per bin are a
+    multinomial sample of eps_n(nu_j) dnu_j / sum; records in class-0 and
+    class-2 cells are checked separately against their own table."""
+    m = W.uniform_cube(n=6, tau_cell=0.0, nf=40)
+    m.rho[:] = 0.0
+    eps, cls = W.pah_emissivity(m, n_classes=3)
+    for want in (0, 2):
+        cells = np.nonzero(cls == want)[0]
+        rec = np.zeros(20000, O.PAH_DTYPE)
+        rec["cell"] = np.resize(cells, len(rec))
+        r = O.pah_reemit(m, rec, 1.0, eps, cls, seed=11, mode=O.MODE_NOREEMIT, n_threads=4)
+        assert r["stats"]["escaped"] == len(rec) and r["stats"]["emitted"] == len(rec)
+        cnt = r["sed_cnt"].sum(axis=0).astype(np.float64)
+        w = eps[want] * m.dnu
+        ok, info = _chi2_ok(cnt, len(rec) * w / w.sum())
+        assert ok, info
+        other = eps[2 - want] * m.dnu
+        assert not _chi2_ok(cnt, len(rec) * other / other.sum())[0]
+        assert r["sed_esc"].sum() == pytest.approx(len(rec) * 1.0, rel=1e-12)
+
+
+def test_pah_reemission_positions_and_directions(O):
+    """Emission points lie in the record's cell, uniform per axis (mean 1/2,
+    variance 1/12 of the cell); directions isotropic (<k> = 0,
+    <k_a^2> = 1/3)."""
+    m = W.random_grid(n=(5, 4, 3), ns=1, seed=2)
+    m.rho[:] = 0.0
+    eps, _ = W.pah_emissivity(m, n_classes=1)
+    rng = np.random.default_rng(1)
+    rec = np.zeros(6000, O.PAH_DTYPE)
+    rec["cell"] = rng.integers(0, m.ncell, len(rec))
+    r = O.pah_reemit(m, rec, 2.0, eps, None, seed=5, mode=O.MODE_NOREEMIT, traj_cap=3 * len(rec))
+    t = r["traj"]
+    em = np.sort(t[t["type"] == 0], order="pid")
+    assert len(em) == len(rec)
+    c = rec["cell"][em["pid"]].astype(np.int64)
+    nx, ny = m.rho.shape[3], m.rho.shape[2]
+    idx = np.stack([c % nx, (c // nx) % ny, c // (nx * ny)], axis=1)
+    f = (em["x"] - m.box_min[None, :]) / m.cell - idx
+    assert np.all((f >= 0) & (f <= 1))
+    n = len(f)
+    assert np.all(np.abs(f.mean(axis=0) - 0.5) <= 5 * math.sqrt(1 / 12 / n))
+    assert np.all(np.abs(f.var(axis=0) - 1 / 12) <= 5 * math.sqrt(1 / 180 / n))
+    k = em["k"]
+    assert np.all(np.abs(k.mean(axis=0)) <= 5 * math.sqrt(1 / 3 / n))
+    assert np.all(np.abs((k ** 2).mean(axis=0) - 1 / 3) <= 5 * math.sqrt(4 / 45 / n))
+
+
+def test_pah_reemission_conserves_the_stored_energy(O):
+    """B&W transport of the torus stores PAH absorptions; the re-emission pass
+    sends one packet of the same xi per record: it escapes or is stored
+    again, so first-pass escapes + second-pass escapes + second-pass stores
+    add up to L exactly; frozen-T passes split across threads agree."""
+    m = W.clumpy_torus(n=16, n_clump=60, seed=3, nf=24)
+    eps, cls = W.pah_emissivity(m)
+    N = 3000
+    r1 = O.transport(m, N, seed=4, mode=O.MODE_BW, pah_cap=N)
+    xi = r1["xi"]
+    n1 = r1["stats"]["pah"]
+    assert n1 > 20 and len(r1["pah"]) == n1
+    r2 = O.pah_reemit(m, r1["pah"], xi, eps, cls, seed=4, model_id=1, mode=O.MODE_BW,
+                      pah_cap=n1, accumulate=r1)
+    st2 = r2["stats"]
+    assert st2["emitted"] == n1 and st2["escaped"] + st2["pah"] == n1
+    esc2 = r2["sed_esc"].sum() - r1["sed_esc"].sum()
+    assert r1["sed_esc"].sum() + esc2 + st2["pah"] * xi == pytest.approx(m.luminosity, rel=1e-12)
+    T0 = np.full((m.ns, m.ncell), 80.0)
+    a = O.pah_reemit(m, r1["pah"], xi, eps, cls, seed=4, mode=O.MODE_FROZEN_T, T_prev=T0,
+                     n_threads=1)
+    b = O.pah_reemit(m, r1["pah"], xi, eps, cls, seed=4, mode=O.MODE_FROZEN_T, T_prev=T0,
+                     n_threads=4)
+    np.testing.assert_allclose(a["E_abs"], b["E_abs"], rtol=1e-12, atol=0)
+    np.testing.assert_array_equal(a["sed_cnt"], b["sed_cnt"])
+
+
+def test_pah_reemission_rejects_bad_inputs(O):
+    m = W.uniform_cube(n=3, tau_cell=0.1)
+    eps = np.ones((1, m.nf))
+    rec = np.zeros(4, O.PAH_DTYPE)
+    with pytest.raises(ValueError):
+        O.pah_reemit(m, rec, 1.0, np.zeros((1, m.nf)), None)           # eps sums to 0
+    rec["cell"][0] = m.ncell
+    with pytest.raises(ValueError):
+        O.pah_reemit(m, rec, 1.0, eps, None)                           # cell out of range
+    rec["cell"][0] = 0
+    with pytest.raises(ValueError):
+        O.pah_reemit(m, rec, 1.0, eps, np.full(m.ncell, 1))            # class out of range

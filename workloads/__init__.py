@@ -437,6 +437,26 @@ def random_grid(n=(6, 5, 4), ns: int = 1, nf: int = 8, seed: int = 0, tau_scale:
                  name=f"random grid {n} ns={ns} seed={seed}")
 
 
+def pah_emissivity(model: Model, n_classes: int = 4):
+    """Synthetic PAH emissivity classes for the re-emission pass: eps_n(nu) =
+    K_PAH(nu) * s_n(nu), s_n a log-normal band in wavelength whose peak moves
+    from 5 to 40 micron with the class (standing in for the band-weighted
+    temperature distributions of cells in weaker radiation fields), and each
+    cell's class set by its distance from the box centre (inner cells class
+    0).  Returns eps [n_classes][nf] and eps_class int32 [ncell]."""
+    pah = [s for s in range(model.ns) if model.is_pah[s]]
+    kabs = model.kabs[pah[0]] if pah else model.kabs[0]
+    lam = wavelength_um(model.nu)
+    peaks = np.geomspace(5.0, 40.0, n_classes)
+    eps = np.stack([kabs * np.exp(-0.5 * (np.log(lam / p) / 0.6) ** 2) for p in peaks])
+    nz, ny, nx = model.rho.shape[1:]
+    z, y, x = np.meshgrid(np.arange(nz) + 0.5 - nz / 2, np.arange(ny) + 0.5 - ny / 2,
+                          np.arange(nx) + 0.5 - nx / 2, indexing="ij")
+    r = np.sqrt(x * x + y * y + z * z) / (0.5 * math.sqrt(nx * nx + ny * ny + nz * nz))
+    cls = np.minimum((r * n_classes).astype(np.int32), n_classes - 1)
+    return eps, cls.reshape(-1)
+
+
 def inclinations_deg():
     return [12.5, 30.0, 45.0, 60.0, 77.5]
 
