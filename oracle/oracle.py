@@ -49,7 +49,8 @@ class _Model(C.Structure):
                 ("box_min", C.c_double * 3), ("cell", C.c_double),
                 ("rho", C.c_void_p), ("nu", C.c_void_p), ("dnu", C.c_void_p),
                 ("kabs", C.c_void_p), ("ksca", C.c_void_p), ("g", C.c_void_p),
-                ("is_pah", C.c_void_p)]
+                ("is_pah", C.c_void_p), ("refine", C.c_int), ("refined", C.c_void_p),
+                ("leaf_base", C.c_void_p), ("nleaf", C.c_int64)]
 
 
 class _Source(C.Structure):
@@ -174,10 +175,22 @@ class OracleModel:
         self.ksca = np.ascontiguousarray(model.ksca, dtype=np.float64)
         self.g = np.ascontiguousarray(model.g, dtype=np.float64)
         self.is_pah = np.ascontiguousarray(model.is_pah, dtype=np.int32)
-        ns, nz, ny, nx = self.rho.shape
+        ns = self.rho.shape[0]
+        nz, ny, nx = model.shape
+        r = int(getattr(model, "refine", 0) or 0)
+        self.refined = self.leaf_base = None
+        nleaf = 0
+        if r:
+            self.refined = np.ascontiguousarray(model.refined, dtype=np.uint8).reshape(-1)
+            per = np.where(self.refined > 0, r ** 3, 1).astype(np.int64)
+            self.leaf_base = np.ascontiguousarray(np.concatenate([[0], np.cumsum(per)[:-1]]),
+                                                  dtype=np.int64)
+            nleaf = int(per.sum())
+            assert self.rho.shape == (ns, nleaf)
         self.c = _Model(nx, ny, nz, ns, self.nu.shape[0], (C.c_double * 3)(*model.box_min),
                         float(model.cell), _ptr(self.rho), _ptr(self.nu), _ptr(self.dnu),
-                        _ptr(self.kabs), _ptr(self.ksca), _ptr(self.g), _ptr(self.is_pah))
+                        _ptr(self.kabs), _ptr(self.ksca), _ptr(self.g), _ptr(self.is_pah),
+                        r, _ptr(self.refined), _ptr(self.leaf_base), nleaf)
         self._lnu = []
         srcs = []
         for s in model.sources:
@@ -186,7 +199,7 @@ class OracleModel:
             srcs.append(_Source((C.c_double * 3)(*s.pos), float(s.L), float(s.T_eff), _ptr(lnu)))
         self.srcs = (_Source * len(srcs))(*srcs)
         self.nsrc = len(srcs)
-        self.ncell = nx * ny * nz
+        self.ncell = nleaf if r else nx * ny * nz
         self.ns = ns
         self.nf = self.nu.shape[0]
 
@@ -418,7 +431,7 @@ def visibilities(model, images, cams, uv):
     them, uv [n_uv][2] in cycles per radian."""
     images = np.asarray(images, dtype=np.float64)
     uv = np.asarray(uv, dtype=np.float64).reshape(-1, 2)
-    nx, ny, nz = model.rho.shape[3], model.rho.shape[2], model.rho.shape[1]
+    nz, ny, nx = model.shape
     diag = model.cell * np.sqrt(float(nx * nx + ny * ny + nz * nz))
     out = np.zeros(images.shape[:2] + (len(uv),), dtype=np.complex128)
     for c, cam in enumerate(cams):

@@ -157,17 +157,50 @@ void or_source_lnu(const or_model* m, const or_source* src, double* lnu)
 /* ------------------------------------------------------------------------ */
 /* Grid helpers                                                              */
 /* ------------------------------------------------------------------------ */
-static int64_t ncell_of(const or_model* m) { return (int64_t)m->nx * m->ny * m->nz; }
+static int64_t ncube_of(const or_model* m) { return (int64_t)m->nx * m->ny * m->nz; }
+static int64_t ncell_of(const or_model* m) { return m->refine > 0 ? m->nleaf : ncube_of(m); }
 
-static int64_t lin(const or_model* m, const int idx[3])
+/* A cell of the grid: cube i[3]; inside a refined cube (f = 1) also its
+ * sub-cube s[3], each index in [0, r). */
+typedef struct { int i[3]; int s[3]; int f; } or_pos;
+
+static int64_t cube_lin(const or_model* m, const int i[3])
 {
-    return ((int64_t)idx[2] * m->ny + idx[1]) * m->nx + idx[0];
+    return ((int64_t)i[2] * m->ny + i[1]) * m->nx + i[0];
 }
 
-static int inside(const or_model* m, const int idx[3])
+static int inside(const or_model* m, const or_pos* p)
 {
-    return idx[0] >= 0 && idx[0] < m->nx && idx[1] >= 0 && idx[1] < m->ny &&
-           idx[2] >= 0 && idx[2] < m->nz;
+    return p->i[0] >= 0 && p->i[0] < m->nx && p->i[1] >= 0 && p->i[1] < m->ny &&
+           p->i[2] >= 0 && p->i[2] < m->nz;
+}
+
+static int cube_refined(const or_model* m, const int i[3])
+{
+    return m->refine > 0 && m->refined[cube_lin(m, i)];
+}
+
+/* cell number of p (see or_model) */
+static int64_t lin(const or_model* m, const or_pos* p)
+{
+    int64_t c = cube_lin(m, p->i);
+    if (m->refine <= 0) return c;
+    int64_t b = m->leaf_base[c];
+    if (!p->f) return b;
+    int r = m->refine;
+    return b + ((int64_t)p->s[2] * r + p->s[1]) * r + p->s[0];
+}
+
+/* edge of cell p and its lower corner along axis a */
+static double pos_size(const or_model* m, const or_pos* p)
+{
+    return p->f ? m->cell / m->refine : m->cell;
+}
+
+static double pos_lo(const or_model* m, const or_pos* p, int a)
+{
+    double lo = m->box_min[a] + p->i[a] * m->cell;
+    return p->f ? lo + p->s[a] * (m->cell / m->refine) : lo;
 }
 
 static double rho_of(const or_model* m, int s, int64_t c)
@@ -175,30 +208,51 @@ static double rho_of(const or_model* m, int s, int64_t c)
     return (double)m->rho[(int64_t)s * ncell_of(m) + c];
 }
 
+/* Sub-cube of refined cube p->i holding x (face rule of locate), clamped to
+ * the cube. */
+static void descend(const or_model* m, const double x[3], const double k[3], or_pos* p)
+{
+    int r = m->refine;
+    double h = m->cell / r;
+    for (int a = 0; a < 3; ++a) {
+        double u = (x[a] - (m->box_min[a] + p->i[a] * m->cell)) / h;
+        double f = floor(u);
+        int sa = (int)f;
+        if (f == u && k[a] < 0.0) sa -= 1;
+        if (sa < 0) sa = 0;
+        if (sa > r - 1) sa = r - 1;
+        p->s[a] = sa;
+    }
+    p->f = 1;
+}
+
 /* Cell containing x; a coordinate exactly on a face belongs to the lower cell
  * when the packet moves towards -axis, otherwise to the upper cell. */
-static void locate(const or_model* m, const double x[3], const double k[3], int idx[3])
+static void locate(const or_model* m, const double x[3], const double k[3], or_pos* p)
 {
     for (int a = 0; a < 3; ++a) {
         double u = (x[a] - m->box_min[a]) / m->cell;
         double f = floor(u);
         int i = (int)f;
         if (f == u && k[a] < 0.0) i -= 1;
-        idx[a] = i;
+        p->i[a] = i;
+        p->s[a] = 0;
     }
+    p->f = 0;
+    if (inside(m, p) && cube_refined(m, p->i)) descend(m, x, k, p);
 }
 
-/* Distance to the exit face of cell idx along k; axis of that face returned
+/* Distance to the exit face of cell p along k; axis of that face returned
  * in *axis (ties go to the lowest axis). */
 static double exit_distance(const or_model* m, const double x[3], const double k[3],
-                            const int idx[3], int* axis)
+                            const or_pos* p, int* axis)
 {
-    double best = INFINITY;
+    double best = INFINITY, h = pos_size(m, p);
     int ba = 0;
     for (int a = 0; a < 3; ++a) {
-        double t;
-        if (k[a] > 0.0) t = (m->box_min[a] + (idx[a] + 1) * m->cell - x[a]) / k[a];
-        else if (k[a] < 0.0) t = (m->box_min[a] + idx[a] * m->cell - x[a]) / k[a];
+        double t, lo = pos_lo(m, p, a);
+        if (k[a] > 0.0) t = (lo + h - x[a]) / k[a];
+        else if (k[a] < 0.0) t = (lo - x[a]) / k[a];
         else t = INFINITY;
         if (t < 0.0) t = 0.0;
         if (t < best) { best = t; ba = a; }
@@ -207,29 +261,82 @@ static double exit_distance(const or_model* m, const double x[3], const double k
     return best;
 }
 
-/* Move to the face found by exit_distance and step into the neighbour. */
-static void cross_face(const or_model* m, double x[3], const double k[3], int idx[3],
+/* Move to the face found by exit_distance and step into the neighbour: the
+ * next sub-cube of the same cube, else the next cube -- descending into its
+ * sub-cube at the entry point when it is refined. */
+static void cross_face(const or_model* m, double x[3], const double k[3], or_pos* p,
                        double t, int a)
 {
+    double lo = pos_lo(m, p, a), h = pos_size(m, p);
+    int step = k[a] > 0.0 ? 1 : -1;
     for (int b = 0; b < 3; ++b) x[b] += t * k[b];
-    if (k[a] > 0.0) { x[a] = m->box_min[a] + (idx[a] + 1) * m->cell; idx[a] += 1; }
-    else            { x[a] = m->box_min[a] + idx[a] * m->cell;       idx[a] -= 1; }
+    x[a] = step > 0 ? lo + h : lo;
+    if (p->f) {
+        p->s[a] += step;
+        if (p->s[a] >= 0 && p->s[a] < m->refine) return;
+        p->f = 0;
+    }
+    p->i[a] += step;
+    for (int b = 0; b < 3; ++b) p->s[b] = 0;
+    if (inside(m, p) && cube_refined(m, p->i)) {
+        descend(m, x, k, p);
+        p->s[a] = step > 0 ? 0 : m->refine - 1;      /* entered through face a */
+    }
+}
+
+/* Cell p of cell number c. */
+static void pos_of(const or_model* m, int64_t c, or_pos* p)
+{
+    int64_t cube = c;
+    p->f = 0;
+    p->s[0] = p->s[1] = p->s[2] = 0;
+    if (m->refine > 0) {
+        /* the last cube whose first cell is <= c */
+        int64_t lo = 0, hi = ncube_of(m) - 1;
+        while (lo < hi) {
+            int64_t mid = (lo + hi + 1) / 2;
+            if (m->leaf_base[mid] <= c) lo = mid; else hi = mid - 1;
+        }
+        cube = lo;
+        if (m->refined[cube]) {
+            int r = m->refine;
+            int64_t off = c - m->leaf_base[cube];
+            p->s[0] = (int)(off % r);
+            p->s[1] = (int)((off / r) % r);
+            p->s[2] = (int)(off / ((int64_t)r * r));
+            p->f = 1;
+        }
+    }
+    p->i[0] = (int)(cube % m->nx);
+    p->i[1] = (int)((cube / m->nx) % m->ny);
+    p->i[2] = (int)(cube / ((int64_t)m->nx * m->ny));
+}
+
+/* Edge length of every cell (cube edge, or cube edge / r in refined cubes). */
+static void cell_sizes(const or_model* m, double* h)
+{
+    int64_t nc = ncell_of(m);
+    for (int64_t c = 0; c < nc; ++c) {
+        or_pos p;
+        pos_of(m, c, &p);
+        h[c] = pos_size(m, &p);
+    }
 }
 
 int or_dda_segments(const or_model* m, const double x0[3], const double k[3], int max,
                     int64_t* cells, double* lens)
 {
     double x[3] = { x0[0], x0[1], x0[2] };
-    int idx[3];
-    locate(m, x, k, idx);
+    or_pos p;
+    locate(m, x, k, &p);
     int n = 0;
-    while (inside(m, idx) && n < max) {
+    while (inside(m, &p) && n < max) {
         int a;
-        double t = exit_distance(m, x, k, idx, &a);
-        cells[n] = lin(m, idx);
+        double t = exit_distance(m, x, k, &p, &a);
+        cells[n] = lin(m, &p);
         lens[n] = t;
         ++n;
-        cross_face(m, x, k, idx, t, a);
+        cross_face(m, x, k, &p, t, a);
     }
     return n;
 }
@@ -344,12 +451,12 @@ typedef struct {
     const or_params* p;
     const double* T_prev;
     double xi;
-    double vol;
     int nsrc;
     const or_source* src;
     double* src_w;      /* [nsrc][nf] emission weights L_nu dnu */
     double* src_L;      /* [nsrc] */
     unsigned char* lucy;/* [ncell] */
+    double* h;          /* [ncell] cell edge */
     const or_pah_src* ps;  /* PAH re-emission pass, or NULL */
     double* eps_w;      /* [n_eps][nf] eps_n(nu_j) dnu_j */
 } or_ctx;
@@ -399,7 +506,7 @@ static int reemit_bin(const or_ctx* C, const or_out* o, int s, int64_t c, double
     const or_model* m = C->m;
     double T;
     if (C->p->mode == OR_MODE_BW) {
-        double rv = rho_of(m, s, c) * C->vol;
+        double rv = rho_of(m, s, c) * C->h[c] * C->h[c] * C->h[c];
         double E = o->E_abs[s * ncell_of(m) + c];
         T = (rv > 0.0) ? or_solve_temperature(m, s, E / rv) : 0.0;
     } else {
@@ -484,7 +591,7 @@ static void run_packet(const or_ctx* C, or_out* o, uint64_t pid)
 
     int si = 0, j = 0;
     double k[3], x[3];
-    int idx[3];
+    or_pos idx;
     if (C->ps) {
         /* PAH re-emission (Sect. 2.1): the record's cell is the source; the
          * bin follows Eq. 6 with the cell's emissivity class, the position is
@@ -492,10 +599,9 @@ static void run_packet(const or_ctx* C, or_out* o, uint64_t pid)
         const int64_t c = (int64_t)C->ps->rec[pid].cell;
         const int n = C->ps->eps_class ? C->ps->eps_class[c] : 0;
         j = pick_cdf(C->eps_w + (size_t)n * m->nf, m->nf, rng_u(&r));
-        idx[0] = (int)(c % m->nx);
-        idx[1] = (int)((c / m->nx) % m->ny);
-        idx[2] = (int)(c / ((int64_t)m->nx * m->ny));
-        for (int a = 0; a < 3; ++a) x[a] = m->box_min[a] + (idx[a] + rng_u(&r)) * m->cell;
+        pos_of(m, c, &idx);
+        const double h = pos_size(m, &idx);
+        for (int a = 0; a < 3; ++a) x[a] = pos_lo(m, &idx, a) + rng_u(&r) * h;
         { double u1 = rng_u(&r), u2 = rng_u(&r); iso_dir(u1, u2, k); }
     } else {
         /* emission (Sect. 2): source, frequency bin, isotropic direction */
@@ -526,15 +632,15 @@ static void run_packet(const or_ctx* C, or_out* o, uint64_t pid)
         }
         { double u1 = rng_u(&r), u2 = rng_u(&r); iso_dir(u1, u2, k); }
         for (int a = 0; a < 3; ++a) x[a] = C->src[si].pos[a];
-        locate(m, x, k, idx);
+        locate(m, x, k, &idx);
     }
     o->stats[OR_S_EMIT]++;
-    log_event(o, pid, &seq, OR_T_EMIT, inside(m, idx) ? lin(m, idx) : 0, j, x, k);
+    log_event(o, pid, &seq, OR_T_EMIT, inside(m, &idx) ? lin(m, &idx) : 0, j, x, k);
     uint64_t n_ev = 0;
-    int64_t last_cell = inside(m, idx) ? lin(m, idx) : 0;
+    int64_t last_cell = inside(m, &idx) ? lin(m, &idx) : 0;
 
     for (;;) {
-        if (!inside(m, idx)) {
+        if (!inside(m, &idx)) {
             /* escape: tally in 10 bins equal in cos(theta) */
             int b = (int)floor((k[2] + 1.0) * 5.0);
             if (b < 0) b = 0;
@@ -546,21 +652,22 @@ static void run_packet(const or_ctx* C, or_out* o, uint64_t pid)
             log_event(o, pid, &seq, OR_T_ESCAPE, last_cell, j, x, k);
             return;
         }
-        int64_t c = lin(m, idx);
+        int64_t c = lin(m, &idx);
         last_cell = c;
 
-        /* modified random walk in very thick cells (Sect. 3.2) */
+        /* modified random walk in very thick cells (Sect. 3.2); the sphere
+         * stays inside the current cell (sub-cube in refined cubes) */
         if (p->mrw && p->mode != OR_MODE_NOREEMIT) {
             double chi = chi_ext(m, c, j);
-            double R0 = INFINITY;
+            double R0 = INFINITY, h = pos_size(m, &idx);
             for (int a = 0; a < 3; ++a) {
-                double lo = m->box_min[a] + idx[a] * m->cell;
-                double d1 = x[a] - lo, d2 = lo + m->cell - x[a];
+                double lo = pos_lo(m, &idx, a);
+                double d1 = x[a] - lo, d2 = lo + h - x[a];
                 if (d1 < R0) R0 = d1;
                 if (d2 < R0) R0 = d2;
             }
             if (R0 < 0.0) R0 = 0.0;
-            if (chi * m->cell > p->mrw_tau_cell && R0 * chi >= p->mrw_gamma) {
+            if (chi * h > p->mrw_tau_cell && R0 * chi >= p->mrw_gamma) {
                 if (++n_ev > p->max_events) {
                     o->stats[OR_S_STUCK]++;
                     log_event(o, pid, &seq, OR_T_STUCK, c, j, x, k);
@@ -604,17 +711,17 @@ static void run_packet(const or_ctx* C, or_out* o, uint64_t pid)
         /* one flight: tau = -ln(u), march cells (Eq. 2) until tau is used up */
         double tau = -log(rng_u(&r));
         int interact = 0;
-        while (inside(m, idx)) {
-            c = lin(m, idx);
+        while (inside(m, &idx)) {
+            c = lin(m, &idx);
             last_cell = c;
             int a;
-            double t = exit_distance(m, x, k, idx, &a);
+            double t = exit_distance(m, x, k, &idx, &a);
             double chi = chi_ext(m, c, j);
             double dtau = chi * t;
             if (dtau <= tau) {
                 if (C->lucy[c]) lucy_deposit(C, o, c, j, t);
                 tau -= dtau;
-                cross_face(m, x, k, idx, t, a);
+                cross_face(m, x, k, &idx, t, a);
                 o->stats[OR_S_CROSS]++;
             } else {
                 double d = tau / chi;          /* Eq. 3 */
@@ -626,7 +733,7 @@ static void run_packet(const or_ctx* C, or_out* o, uint64_t pid)
         }
         if (!interact) continue;                /* left the grid: escape next */
 
-        c = lin(m, idx);
+        c = lin(m, &idx);
         if (++n_ev > p->max_events) {
             o->stats[OR_S_STUCK]++;
             log_event(o, pid, &seq, OR_T_STUCK, c, j, x, k);
@@ -706,7 +813,8 @@ static int transport_impl(const or_model* m, const or_source* src, int nsrc,
         if (p->pc[c].npix < 1) return 1;
     or_ctx C;
     C.m = m; C.p = p; C.T_prev = T_prev; C.nsrc = nsrc; C.src = src;
-    C.vol = m->cell * m->cell * m->cell;
+    C.h = (double*)malloc(sizeof(double) * ncell_of(m));
+    cell_sizes(m, C.h);
     C.ps = ps;
     C.eps_w = NULL;
     C.src_w = (double*)malloc(sizeof(double) * (nsrc > 0 ? nsrc : 1) * m->nf);
@@ -739,7 +847,7 @@ static int transport_impl(const or_model* m, const or_source* src, int nsrc,
         if (p->lucy_mode != OR_LUCY_THIN) continue;
         double mx = 0.0;
         for (int j = 0; j < m->nf; ++j) {
-            double t = chi_ext(m, c, j) * m->cell;
+            double t = chi_ext(m, c, j) * C.h[c];
             if (t > mx) mx = t;
         }
         C.lucy[c] = mx < p->lucy_tau;
@@ -811,7 +919,7 @@ static int transport_impl(const or_model* m, const or_source* src, int nsrc,
         }
         free(parts);
     }
-    free(C.src_w); free(C.src_L); free(C.lucy); free(C.eps_w);
+    free(C.src_w); free(C.src_L); free(C.lucy); free(C.eps_w); free(C.h);
     return 0;
 }
 
@@ -850,13 +958,15 @@ int or_pah_reemit(const or_model* m, const or_pah_src* ps, const or_params* p,
 void or_temperatures(const or_model* m, const double* E_abs, double* T)
 {
     int64_t nc = ncell_of(m);
-    double vol = m->cell * m->cell * m->cell;
+    double* h = (double*)malloc(sizeof(double) * nc);
+    cell_sizes(m, h);
     for (int s = 0; s < m->ns; ++s)
         for (int64_t c = 0; c < nc; ++c) {
-            double rv = rho_of(m, s, c) * vol;
+            double rv = rho_of(m, s, c) * h[c] * h[c] * h[c];
             double E = E_abs[s * nc + c];
             T[s * nc + c] = (rv > 0.0 && E > 0.0) ? or_solve_temperature(m, s, E / rv) : 0.0;
         }
+    free(h);
 }
 
 /* Initial guess of the iterative scheme: optically thin gray dust around
@@ -866,23 +976,21 @@ void or_temperature_guess(const or_model* m, const or_source* src, int nsrc, dou
 {
     const double sigma = 2.0 * pow(OR_PI, 5) * pow(OR_K, 4) / (15.0 * pow(OR_H, 3) * OR_C * OR_C);
     int64_t nc = ncell_of(m);
-    for (int iz = 0; iz < m->nz; ++iz)
-        for (int iy = 0; iy < m->ny; ++iy)
-            for (int ix = 0; ix < m->nx; ++ix) {
-                double x = m->box_min[0] + (ix + 0.5) * m->cell;
-                double y = m->box_min[1] + (iy + 0.5) * m->cell;
-                double z = m->box_min[2] + (iz + 0.5) * m->cell;
-                double q = 0.0;
-                for (int i = 0; i < nsrc; ++i) {
-                    double dx = x - src[i].pos[0], dy = y - src[i].pos[1], dz = z - src[i].pos[2];
-                    double r2 = dx * dx + dy * dy + dz * dz;
-                    q += r2 > 0.0 ? src[i].L / (16.0 * OR_PI * sigma * r2) : INFINITY;
-                }
-                double t = pow(q, 0.25);
-                if (!(t < 2000.0)) t = 2000.0;
-                int64_t c = ((int64_t)iz * m->ny + iy) * m->nx + ix;
-                for (int s = 0; s < m->ns; ++s) T[s * nc + c] = t;
-            }
+    for (int64_t c = 0; c < nc; ++c) {
+        or_pos p;
+        pos_of(m, c, &p);
+        double h = pos_size(m, &p), ctr[3];
+        for (int a = 0; a < 3; ++a) ctr[a] = pos_lo(m, &p, a) + 0.5 * h;
+        double q = 0.0;
+        for (int i = 0; i < nsrc; ++i) {
+            double dx = ctr[0] - src[i].pos[0], dy = ctr[1] - src[i].pos[1], dz = ctr[2] - src[i].pos[2];
+            double r2 = dx * dx + dy * dy + dz * dz;
+            q += r2 > 0.0 ? src[i].L / (16.0 * OR_PI * sigma * r2) : INFINITY;
+        }
+        double t = pow(q, 0.25);
+        if (!(t < 2000.0)) t = 2000.0;
+        for (int s = 0; s < m->ns; ++s) T[s * nc + c] = t;
+    }
 }
 
 /* ------------------------------------------------------------------------ */
@@ -952,21 +1060,24 @@ static int ray_path(const or_model* m, const double o[3], const double kobs[3], 
     double d[3] = { -kobs[0], -kobs[1], -kobs[2] };
     double x[3];
     for (int a = 0; a < 3; ++a) x[a] = o[a] + s_hi * kobs[a];
-    int idx[3];
-    locate(m, x, d, idx);
+    or_pos p;
+    locate(m, x, d, &p);
     int nn[3] = { m->nx, m->ny, m->nz };
-    for (int a = 0; a < 3; ++a) {
-        if (idx[a] < 0) idx[a] = 0;
-        if (idx[a] >= nn[a]) idx[a] = nn[a] - 1;
+    for (int a = 0; a < 3; ++a) {              /* entry point on the box: clamp */
+        if (p.i[a] < 0) p.i[a] = 0;
+        if (p.i[a] >= nn[a]) p.i[a] = nn[a] - 1;
+        p.s[a] = 0;
     }
+    p.f = 0;
+    if (cube_refined(m, p.i)) descend(m, x, d, &p);
     int n = 0;
-    while (inside(m, idx) && n < max) {
+    while (inside(m, &p) && n < max) {
         int a;
-        double t = exit_distance(m, x, d, idx, &a);
-        cells[n] = lin(m, idx);
+        double t = exit_distance(m, x, d, &p, &a);
+        cells[n] = lin(m, &p);
         lens[n] = t;
         ++n;
-        cross_face(m, x, d, idx, t, a);
+        cross_face(m, x, d, &p, t, a);
     }
     return n;
 }
@@ -979,7 +1090,8 @@ static void emissivities(const or_model* m, const double* T, const or_event* ev,
                          double* eta)
 {
     int64_t nc = ncell_of(m);
-    double vol = m->cell * m->cell * m->cell;
+    double* h = (double*)malloc(sizeof(double) * nc);
+    cell_sizes(m, h);
     for (int64_t c = 0; c < nc; ++c)
         for (int f = 0; f < nfi; ++f) {
             int j = fidx[f];
@@ -996,9 +1108,11 @@ static void emissivities(const or_model* m, const double* T, const or_event* ev,
             if ((int)e->nu != fidx[f]) continue;
             double cb = e->k[0] * kobs[0] + e->k[1] * kobs[1] + e->k[2] * kobs[2];
             double gg = m->g[e->species * m->nf + e->nu];
+            double vol = h[e->cell] * h[e->cell] * h[e->cell];
             eta[(int64_t)e->cell * nfi + f] += xi_ev / (vol * m->dnu[e->nu]) * hg_phase(gg, cb);
         }
     }
+    free(h);
 }
 
 static void pixel_origin(const or_model* m, const or_camera* cam, int ix, int iy, double o[3],
@@ -1022,7 +1136,7 @@ void or_raytrace(const or_model* m, const double* T, const or_event* ev, uint64_
                  const int* fidx, int nfi, double* images, double* sed)
 {
     int64_t nc = ncell_of(m);
-    int maxp = m->nx + m->ny + m->nz + 8;
+    int maxp = (m->nx + m->ny + m->nz) * (m->refine > 0 ? m->refine : 1) + 8;
     int64_t* cells = (int64_t*)malloc(sizeof(int64_t) * maxp);
     double* lens = (double*)malloc(sizeof(double) * maxp);
     double* eta = (double*)malloc(sizeof(double) * nc * nfi);
@@ -1079,7 +1193,7 @@ void or_raytrace_backward(const or_model* m, const double* T, const or_event* ev
                           const double* dL_dsed, double* dL_drho, double* dL_dscale)
 {
     int64_t nc = ncell_of(m);
-    int maxp = m->nx + m->ny + m->nz + 8;
+    int maxp = (m->nx + m->ny + m->nz) * (m->refine > 0 ? m->refine : 1) + 8;
     int64_t* cells = (int64_t*)malloc(sizeof(int64_t) * maxp);
     double* lens = (double*)malloc(sizeof(double) * maxp);
     double* contrib = (double*)malloc(sizeof(double) * maxp);

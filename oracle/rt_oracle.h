@@ -15,17 +15,27 @@
 extern "C" {
 #endif
 
+/* The grid (Sect. 2): nx x ny x nz cubes of edge `cell`; with refine = r > 0
+ * the cubes flagged in `refined` are divided into r^3 sub-cubes (one level
+ * of refinement).  Cells ("leaves") are numbered cube by cube in z, y, x
+ * order; a refined cube's r^3 sub-cubes take consecutive numbers from
+ * leaf_base[cube], again in z, y, x order.  Per-cell arrays (rho, E_abs, T)
+ * are [ns][ncell], ncell = nleaf (refined) or nx ny nz. */
 typedef struct {
     int nx, ny, nz, ns, nf;
     double box_min[3];
     double cell;                 /* cubic cell edge, cm */
-    const float* rho;            /* [ns][nz][ny][nx] g/cm^3 */
+    const float* rho;            /* [ns][ncell] g/cm^3 */
     const double* nu;            /* [nf] Hz, ascending */
     const double* dnu;           /* [nf] Hz */
     const double* kabs;          /* [ns][nf] cm^2/g */
     const double* ksca;          /* [ns][nf] cm^2/g */
     const double* g;             /* [ns][nf] HG asymmetry */
     const int* is_pah;           /* [ns] */
+    int refine;                  /* r >= 2, or 0 for a uniform grid */
+    const unsigned char* refined;/* [nz][ny][nx] 1 = divided (refine > 0) */
+    const int64_t* leaf_base;    /* [nz][ny][nx] first cell of each cube (refine > 0) */
+    int64_t nleaf;               /* cells of a refined grid */
 } or_model;
 
 typedef struct {

@@ -636,7 +636,7 @@ def test_pah_reemission_positions_and_directions(O):
     em = np.sort(t[t["type"] == 0], order="pid")
     assert len(em) == len(rec)
     c = rec["cell"][em["pid"]].astype(np.int64)
-    nx, ny = m.rho.shape[3], m.rho.shape[2]
+    nz, ny, nx = m.shape
     idx = np.stack([c % nx, (c // nx) % ny, c // (nx * ny)], axis=1)
     f = (em["x"] - m.box_min[None, :]) / m.cell - idx
     assert np.all((f >= 0) & (f <= 1))

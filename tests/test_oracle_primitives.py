@@ -247,3 +247,108 @@ def test_dda_invariant_under_cube_isometries(O):
             k2 = P @ k
             got = np.sort(O.dda_segments(m, x2, k2)[1])
             np.testing.assert_allclose(got, ref, rtol=1e-9, atol=1e-9 * m.cell)
+
+
+# ------------------------------------------------ one level of refinement (Sect. 2)
+def _refined_grid(seed=3, r=3):
+    m = W.random_grid(n=(5, 4, 3), seed=seed)
+    mask = np.random.default_rng(seed).random(m.rho.shape[1:]) < 0.5
+    return W.refine_cubes(m, mask, r=r, jitter=0.5, seed=seed)
+
+
+def _leaf_of_points(m, pts):
+    """Cell number of each point by direct computation (numbering of the
+    model's docstring): cube by floor, sub-cube by floor within the cube."""
+    nz, ny, nx = m.shape
+    r = m.refine
+    ijk = np.floor((pts - m.box_min) / m.cell).astype(np.int64)
+    cube = (ijk[:, 2] * ny + ijk[:, 1]) * nx + ijk[:, 0]
+    base = m.leaf_base[cube]
+    fine = m.refined.reshape(-1)[cube] > 0
+    sub = np.floor((pts - m.box_min - ijk * m.cell) / (m.cell / r)).astype(np.int64)
+    sub = np.clip(sub, 0, r - 1)
+    return np.where(fine, base + (sub[:, 2] * r + sub[:, 1]) * r + sub[:, 0], base)
+
+
+def test_refined_dda_chords_match_brute_force(O):
+    """Cells and chord lengths of rays through a grid with one level of
+    refinement against dense point sampling classified cell by cell."""
+    m = _refined_grid()
+    nz, ny, nx = m.shape
+    ext = m.cell * np.array([nx, ny, nz])
+    rng = np.random.default_rng(7)
+    h = 2e-5 * m.cell
+    for _ in range(16):
+        x = m.box_min + ext * rng.uniform(0.05, 0.95, 3)
+        k = rng.normal(size=3)
+        k /= np.linalg.norm(k)
+        cells, lens = O.dda_segments(m, x, k)
+        assert lens.sum() == pytest.approx(_box_exit(x, k, m.box_min, m.box_min + ext), rel=1e-12)
+        s = (np.arange(int(lens.sum() / h)) + 0.5) * h
+        lin = _leaf_of_points(m, x[None, :] + s[:, None] * k[None, :])
+        # the sampled sequence of distinct cells is the DDA's (cells shorter
+        # than the sampling step may be missed by the samples)
+        seq = lin[np.concatenate([[True], lin[1:] != lin[:-1]])]
+        assert list(seq) == [c for c, l in zip(cells, lens) if l > 3 * h]
+        for c, l in zip(cells, lens):
+            assert (lin == c).sum() * h == pytest.approx(l, abs=3 * h)
+        assert len(set(cells.tolist())) == len(cells)      # a straight ray visits a cell once
+
+
+def test_refined_grid_with_inherited_density_changes_no_physics(O):
+    """Dividing cubes into sub-cubes of the cube's own density changes no
+    path: frozen-T trajectories (no MRW, Lucy in every dust cell, linear
+    form) are identical, and each divided cube's energy is the sum over its
+    sub-cubes."""
+    m = W.random_grid(n=(5, 4, 3), ns=2, seed=8, tau_scale=2.0, albedo=(0.3, 0.8))
+    mask = np.random.default_rng(2).random(m.rho.shape[1:]) < 0.5
+    mr = W.refine_cubes(m, mask, r=2)
+    T0 = np.random.default_rng(4).uniform(40, 500, size=(m.ns, m.ncell))
+    per = np.where(mr.refined.reshape(-1) > 0, 8, 1)
+    T0r = np.repeat(T0, per, axis=1)
+    kw = dict(seed=5, mode=O.MODE_FROZEN_T, lucy_mode=O.LUCY_ALL, traj_cap=200000, n_threads=4)
+    a = O.transport(m, 800, T_prev=T0, **kw)
+    b = O.transport(mr, 800, T_prev=T0r, **kw)
+    ta, tb = np.sort(a["traj"], order=["pid", "seq"]), np.sort(b["traj"], order=["pid", "seq"])
+    assert len(ta) == len(tb) > 0
+    for f in ("pid", "seq", "type", "nu"):
+        np.testing.assert_array_equal(ta[f], tb[f])
+    np.testing.assert_allclose(ta["x"], tb["x"], rtol=0, atol=1e-9 * m.cell)
+    np.testing.assert_allclose(ta["k"], tb["k"], rtol=0, atol=1e-9)
+    cube_of_leaf = np.repeat(np.arange(m.ncell), per)
+    Eb = np.zeros_like(a["E_abs"])
+    for s in range(m.ns):
+        np.add.at(Eb[s], cube_of_leaf, b["E_abs"][s])
+    np.testing.assert_allclose(Eb, a["E_abs"], rtol=1e-9, atol=1e-12 * a["E_abs"].max())
+    assert b["stats"]["crossings"] > a["stats"]["crossings"]
+    np.testing.assert_array_equal(a["sed_cnt"], b["sed_cnt"])
+
+
+def test_refined_temperatures_use_sub_cube_volumes(O):
+    """Eq. 4 per cell with the cell's own volume: a sub-cube holding 1/r^3 of
+    its cube's energy at the same density has the cube's temperature."""
+    m = W.random_grid(n=(3, 3, 2), seed=1)
+    mask = np.zeros(m.rho.shape[1:], bool)
+    mask[0, 1, 2] = mask[1, 0, 0] = True
+    mr = W.refine_cubes(m, mask, r=2)
+    E = np.random.default_rng(3).uniform(1e28, 1e31, size=(1, m.ncell))
+    T = O.temperatures(m, E)
+    per = np.where(mr.refined.reshape(-1) > 0, 8, 1)
+    Tr = O.temperatures(mr, np.repeat(E / per, per, axis=1))
+    np.testing.assert_allclose(Tr, np.repeat(T, per, axis=1), rtol=1e-12)
+
+
+def test_refined_images_equal_unrefined_for_inherited_fields(O):
+    """Formal solution (Eqs. 11-14, 17) over a cube split into sub-cubes of
+    the same emissivity and opacity equals the unsplit one."""
+    m = W.random_grid(n=(4, 4, 3), ns=1, seed=6, tau_scale=1.0, albedo=(0.0, 0.0))
+    mask = np.random.default_rng(9).random(m.rho.shape[1:]) < 0.5
+    mr = W.refine_cubes(m, mask, r=3)
+    per = np.where(mr.refined.reshape(-1) > 0, 27, 1)
+    T = np.random.default_rng(1).uniform(30, 900, size=(1, m.ncell))
+    cams = [W.Camera(0.7, 0.3, 12, 100 * W.AU), W.Camera(2.0, -1.1, 12, 100 * W.AU)]
+    ev = np.zeros(0, O.EVENT_DTYPE)
+    ia, sa = O.raytrace(m, T, ev, 1.0, cams, [1, 4, 6])
+    ib, sb = O.raytrace(mr, np.repeat(T, per, axis=1), ev, 1.0, cams, [1, 4, 6])
+    np.testing.assert_allclose(ib, ia, rtol=1e-9, atol=1e-12 * np.abs(ia).max())
+    np.testing.assert_allclose(sb, sa, rtol=1e-9)

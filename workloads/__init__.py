@@ -66,12 +66,18 @@ class Camera:
 
 @dataclasses.dataclass
 class Model:
-    """One dust model on a uniform Cartesian grid.
+    """One dust model on a Cartesian grid of cubes (Sect. 2).
 
-    rho      float32 [ns, nz, ny, nx]  g/cm^3 per species
+    rho      float32 [ns, nz, ny, nx]  g/cm^3 per species (uniform grid), or
+             float32 [ns, ncell]       per cell of a refined grid
     nu, dnu  float64 [nf]              Hz, ascending, bin widths
     kabs, ksca, g  float64 [ns, nf]    cm^2/g, cm^2/g, HG asymmetry
     is_pah   int32 [ns]                1 for stochastically heated species
+    refine   int                       r >= 2 for one level of refinement, else 0
+    refined  uint8 [nz, ny, nx]        1 = cube divided into r^3 sub-cubes
+
+    Cells of a refined grid are numbered cube by cube (z, y, x order), a
+    divided cube's r^3 sub-cubes consecutively, again in z, y, x order.
     """
     rho: np.ndarray
     box_min: np.ndarray
@@ -84,10 +90,13 @@ class Model:
     is_pah: np.ndarray
     sources: List[Source]
     name: str = ""
+    refine: int = 0
+    refined: Optional[np.ndarray] = None
 
     @property
     def shape(self):
-        return self.rho.shape[1:]
+        """Cube counts (nz, ny, nx)."""
+        return self.refined.shape if self.refine else self.rho.shape[1:]
 
     @property
     def ns(self):
@@ -99,7 +108,14 @@ class Model:
 
     @property
     def ncell(self):
-        return int(np.prod(self.rho.shape[1:]))
+        """Cells (leaves of a refined grid)."""
+        return int(self.rho.shape[1]) if self.refine else int(np.prod(self.rho.shape[1:]))
+
+    @property
+    def leaf_base(self):
+        """int64 [nz*ny*nx]: first cell of each cube (refined grids)."""
+        per = np.where(self.refined.reshape(-1) > 0, self.refine ** 3, 1).astype(np.int64)
+        return np.concatenate([[0], np.cumsum(per)[:-1]]).astype(np.int64)
 
     @property
     def luminosity(self):
@@ -437,6 +453,53 @@ def random_grid(n=(6, 5, 4), ns: int = 1, nf: int = 8, seed: int = 0, tau_scale:
                  name=f"random grid {n} ns={ns} seed={seed}")
 
 
+def refine_cubes(model: Model, mask: np.ndarray, r: int = 2, fine_rho=None, jitter: float = 0.0,
+                 seed: int = 0) -> Model:
+    """One level of refinement (Sect. 2) of a uniform model: the cubes where
+    ``mask`` [nz, ny, nx] is true are divided into r^3 sub-cubes.  Sub-cube
+    densities come from ``fine_rho`` [ns, r nz, r ny, r nx] (e.g. the profile
+    voxelised at r times the resolution) or inherit the cube's density;
+    ``jitter`` > 0 multiplies them by seeded log-normal factors."""
+    rng = np.random.default_rng(seed)
+    ns = model.ns
+    nz, ny, nx = model.rho.shape[1:]
+    mask = np.asarray(mask, dtype=bool).reshape(nz, ny, nx)
+    cols = []
+    for cz in range(nz):
+        for cy in range(ny):
+            for cx in range(nx):
+                if not mask[cz, cy, cx]:
+                    cols.append(model.rho[:, cz, cy, cx][:, None])
+                    continue
+                if fine_rho is not None:
+                    blk = fine_rho[:, cz * r:(cz + 1) * r, cy * r:(cy + 1) * r, cx * r:(cx + 1) * r]
+                    leaf = blk.reshape(ns, r ** 3)
+                else:
+                    leaf = np.repeat(model.rho[:, cz, cy, cx][:, None], r ** 3, axis=1)
+                if jitter > 0:
+                    leaf = leaf * np.exp(jitter * rng.standard_normal(leaf.shape))
+                cols.append(leaf)
+    rho = np.concatenate(cols, axis=1).astype(np.float32)
+    out = dataclasses.replace(model, rho=rho, refine=int(r), refined=mask.astype(np.uint8),
+                              name=f"{model.name} refined r={r} ({int(mask.sum())} cubes)")
+    return out
+
+
+def r2_shell_refined(n: int = 64, tau_1um: float = 10.0, nf: int = 64, r: int = 4,
+                     refine_radius: float = 4.0) -> Model:
+    """The r^-2 shell on n^3 cubes with the cubes within ``refine_radius``
+    cube edges of the centre divided into r^3 sub-cubes -- finer sampling
+    near the dust evaporation zone, where the paper refines; sub-cube
+    densities from the profile voxelised at r times the resolution with the
+    same tau normalisation."""
+    coarse = r2_shell(n=n, tau_1um=tau_1um, nf=nf)
+    fine = r2_shell(n=n * r, tau_1um=tau_1um, nf=nf, sub=1)
+    c = np.arange(n) + 0.5 - n / 2
+    Z, Y, X = np.meshgrid(c, c, c, indexing="ij")
+    mask = np.sqrt(X * X + Y * Y + Z * Z) <= refine_radius
+    return refine_cubes(coarse, mask, r=r, fine_rho=fine.rho)
+
+
 def pah_emissivity(model: Model, n_classes: int = 4):
     """Synthetic PAH emissivity classes for the re-emission pass: eps_n(nu) =
     K_PAH(nu) * s_n(nu), s_n a log-normal band in wavelength whose peak moves
@@ -449,12 +512,15 @@ def pah_emissivity(model: Model, n_classes: int = 4):
     lam = wavelength_um(model.nu)
     peaks = np.geomspace(5.0, 40.0, n_classes)
     eps = np.stack([kabs * np.exp(-0.5 * (np.log(lam / p) / 0.6) ** 2) for p in peaks])
-    nz, ny, nx = model.rho.shape[1:]
+    nz, ny, nx = model.shape
     z, y, x = np.meshgrid(np.arange(nz) + 0.5 - nz / 2, np.arange(ny) + 0.5 - ny / 2,
                           np.arange(nx) + 0.5 - nx / 2, indexing="ij")
     r = np.sqrt(x * x + y * y + z * z) / (0.5 * math.sqrt(nx * nx + ny * ny + nz * nz))
-    cls = np.minimum((r * n_classes).astype(np.int32), n_classes - 1)
-    return eps, cls.reshape(-1)
+    cls = np.minimum((r * n_classes).astype(np.int32), n_classes - 1).reshape(-1)
+    if model.refine:                       # sub-cubes take their cube's class
+        per = np.where(model.refined.reshape(-1) > 0, model.refine ** 3, 1)
+        cls = np.repeat(cls, per)
+    return eps, cls
 
 
 def inclinations_deg():
