@@ -282,6 +282,53 @@ def form_mrw_disk(rt, ctx, flush, packets=1e7, npix=512):
     return res
 
 
+def form_refined_shell(rt, ctx, flush, packets=1e7, npix=256):
+    """r^-2 shell (tau(1 um) = 10, 64 frequencies) on 64^3 cubes, the cubes
+    within 6 cube edges of the star divided into 4^3 sub-cubes (one level of
+    refinement): B&W transport, Eq. 4 temperatures and images (5
+    inclinations x 12 frequencies), against the same shell on the uniform
+    64^3 grid."""
+    import math as _m
+    import torch
+    import workloads as W
+    mr = W.r2_shell_refined(n=64, tau_1um=10.0, nf=64, r=4, refine_radius=6.0)
+    mu = W.r2_shell(n=64, tau_1um=10.0, nf=64)
+    N = int(packets)
+    res = {}
+    for name, m in (("refined", mr), ("uniform", mu)):
+        grid, opac, srcs = ctx.grid(m), ctx.opacity(m), rt.Sources(m.sources)
+        out = rt.TransportOut(grid.ncell, 1, opac.nf, event_cap=6 * N)
+
+        def run(r):
+            out.zero_()
+            out.stats[13:].zero_()
+            rt.transport(ctx, grid, opac, srcs, N, out=out, record_events=True, seed=5 + max(r, 0))
+        ts = _timed(run, 3, 1, flush)
+        S = _stats_delta(out, torch.zeros_like(out.stats))
+        t = statistics.median(ts)
+        res[name] = {"transport": {"value": S["crossings"] / t, "unit": UNIT, "ms": 1e3 * t,
+                                   "crossings": S["crossings"], "cells": grid.ncell,
+                                   "roofline": _roof(_transport_bytes(S, 1), t)}}
+        T = rt.temperatures(ctx, grid, opac, out.E_abs)
+        fidx = W.nearest_freq_indices(m.nu, W.image_wavelengths_um())
+        cams = [W.Camera(_m.radians(th), 0.0, npix, 140 * W.PC) for th in W.inclinations_deg()]
+        steps = torch.zeros(1, dtype=torch.int64, device="cuda")
+
+        def ray(r):
+            steps.zero_()
+            rt.raytrace(ctx, grid, opac, T, out, out.xi, srcs, cams, fidx, steps=steps)
+        ts = _timed(ray, 3, 1, flush)
+        t = statistics.median(ts)
+        n = int(steps.item())
+        nfp = (len(fidx) + 3) // 4 * 4
+        res[name]["raytrace"] = {"value": n / t, "unit": "ray-cell steps/s", "ms": 1e3 * t,
+                                 "steps": n, "roofline": _roof(n * (4 + 4 * nfp), t)}
+    res["workload"] = (f"r^-2 shell tau1um=10, 64 freq, {N:.0e} packets, B&W, Lucy thin, events; "
+                       f"64^3 cubes, {int(mr.refined.sum())} cubes within 6 edges of the star divided "
+                       f"into 4^3 ({mr.ncell} cells); images 5 incl x 12 freq x {npix}^2")
+    return res
+
+
 def form_batched(rt, ctx, flush, per_model=1e6, n_models=64):
     """64 clumpy tori of uneven size (64^3 .. 192^3, silicate + carbon + PAH,
     100 frequencies) in one persistent launch replayed from a CUDA graph,
@@ -383,7 +430,8 @@ def run_forms(a):
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     forms = {}
     for name, fn in (("fp64_debug", form_fp64_debug), ("mrw_disk", form_mrw_disk),
-                     ("adjoint", form_adjoint), ("batched", form_batched)):
+                     ("adjoint", form_adjoint), ("batched", form_batched),
+                     ("refined_shell", form_refined_shell)):
         if a.forms != "all" and name not in a.forms.split(","):
             continue
         t0 = time.perf_counter()

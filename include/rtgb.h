@@ -80,6 +80,25 @@ RT_API void rt_ctx_destroy(rt_ctx* ctx);
 RT_API rt_status rt_grid_upload(rt_ctx* ctx, int nx, int ny, int nz, int n_species,
                          const double box_min[3], double cell_size, const float* rho,
                          rt_stream stream, rt_grid** out);
+/* A grid with one level of refinement (Sect. 2: each cube may be divided
+ * into sub-cubes of constant density).  nx x ny x nz cubes of edge
+ * cell_size; the cubes with refined[cube] != 0 (host [nz][ny][nx] bytes) are
+ * divided into r^3 sub-cubes (r = refine, 2..16).  Cells are numbered cube
+ * by cube in z, y, x order; a divided cube's r^3 sub-cubes take consecutive
+ * numbers, again in z, y, x order.  rho: [n_species][ncell] float32, host or
+ * device, ncell = (cubes not divided) + r^3 (cubes divided), at most 2e9.
+ * Every per-cell array of the other calls (E_abs, count, esq, T, the cell of
+ * events and PAH records) is indexed by this cell number.  Served by
+ * rt_transport, rt_pah_reemit, rt_temperatures, rt_temperature_guess and
+ * rt_raytrace; rt_raytrace_backward, the batched and no-alloc transports
+ * refuse refined grids (RT_ERR_INVALID_ARG).  Errors as rt_grid_upload,
+ * plus a bad refine factor. */
+RT_API rt_status rt_grid_upload_refined(rt_ctx* ctx, int nx, int ny, int nz, int n_species,
+                                        const double box_min[3], double cell_size, int refine,
+                                        const unsigned char* refined, const float* rho,
+                                        rt_stream stream, rt_grid** out);
+/* Cells of a grid (leaves of a refined one). */
+RT_API uint64_t rt_grid_ncell(const rt_grid* grid);
 RT_API void rt_grid_free(rt_grid* grid);
 
 /* Dust cross sections per unit mass (paper Sect. 2 "absorption kappa_abs and

@@ -89,6 +89,15 @@ void rt_ctx_destroy(rt_ctx* c)
 rt_status rt_grid_upload(rt_ctx* ctx, int nx, int ny, int nz, int ns, const double box_min[3],
                          double cell, const float* rho, rt_stream stream, rt_grid** out)
 {
+    return rt_grid_upload_refined(ctx, nx, ny, nz, ns, box_min, cell, 0, nullptr, rho, stream, out);
+}
+
+uint64_t rt_grid_ncell(const rt_grid* g) { return g ? (uint64_t)g->ncell() : 0; }
+
+rt_status rt_grid_upload_refined(rt_ctx* ctx, int nx, int ny, int nz, int ns, const double box_min[3],
+                                 double cell, int refine, const unsigned char* refined,
+                                 const float* rho, rt_stream stream, rt_grid** out)
+{
     if (!ctx || ctx->magic != kMagic) return fail(RT_ERR_STATE, "rt_grid_upload: bad context");
     if (!out || !rho || !box_min) return fail(RT_ERR_INVALID_ARG, "rt_grid_upload: NULL pointer");
     if (nx <= 0 || ny <= 0 || nz <= 0) return fail(RT_ERR_INVALID_ARG, "rt_grid_upload: sizes must be positive");
@@ -97,15 +106,58 @@ rt_status rt_grid_upload(rt_ctx* ctx, int nx, int ny, int nz, int ns, const doub
     if (!(cell > 0.0) || !isfin(cell)) return fail(RT_ERR_INVALID_ARG, "rt_grid_upload: bad cell size");
     for (int a = 0; a < 3; ++a)
         if (!isfin(box_min[a])) return fail(RT_ERR_INVALID_ARG, "rt_grid_upload: non-finite box_min");
+    if (refine != 0 && (refine < 2 || refine > 16 || !refined))
+        return fail(RT_ERR_INVALID_ARG, "rt_grid_upload_refined: refine must be 2..16 with a refined mask");
+    // one level of refinement: first cell of every cube, cube of every cell
+    const size_t ncube = (size_t)nx * ny * nz;
+    std::vector<int> cube, leaf_cube;
+    std::vector<unsigned char> leaf_fine;
+    size_t nleaf = ncube;
+    if (refine) {
+        const size_t r3 = (size_t)refine * refine * refine;
+        nleaf = 0;
+        for (size_t c = 0; c < ncube; ++c) nleaf += refined[c] ? r3 : 1;
+        if ((double)nleaf > 2.0e9 || nleaf >= (size_t)kCubeDivided)
+            return fail(RT_ERR_INVALID_ARG, "rt_grid_upload_refined: more than 2e9 cells");
+        cube.resize(ncube);
+        leaf_cube.resize(nleaf);
+        leaf_fine.resize(nleaf);
+        size_t b = 0;
+        for (size_t c = 0; c < ncube; ++c) {
+            const size_t m = refined[c] ? r3 : 1;
+            cube[c] = (int)b | (refined[c] ? kCubeDivided : 0);
+            for (size_t q = 0; q < m; ++q) {
+                leaf_cube[b + q] = (int)c;
+                leaf_fine[b + q] = refined[c] ? 1 : 0;
+            }
+            b += m;
+        }
+    }
     RT_CUDA(cudaSetDevice(ctx->device));
     rt_grid* g = new rt_grid();
     std::memset((void*)g, 0, sizeof(*g));
     g->ctx = ctx; g->nx = nx; g->ny = ny; g->nz = nz; g->ns = ns; g->cell = cell;
     for (int a = 0; a < 3; ++a) g->box_min[a] = box_min[a];
+    g->refine = refine;
+    g->nleaf = nleaf;
     const size_t n = g->ncell() * ns;
     cudaStream_t s = (cudaStream_t)stream;
     unsigned int* bad = nullptr;
-    cudaError_t e = cudaMalloc(&g->d_rho, n * sizeof(float));
+    cudaError_t e = cudaSuccess;
+    if (refine) {
+        e = cudaMalloc(&g->d_cube, ncube * sizeof(int));
+        if (e == cudaSuccess) e = cudaMalloc(&g->d_leaf_cube, nleaf * sizeof(int));
+        if (e == cudaSuccess) e = cudaMalloc(&g->d_leaf_fine, nleaf);
+        if (e == cudaSuccess) e = cudaMemcpy(g->d_cube, cube.data(), ncube * sizeof(int), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(g->d_leaf_cube, leaf_cube.data(), nleaf * sizeof(int), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(g->d_leaf_fine, leaf_fine.data(), nleaf, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaFree(g->d_cube); cudaFree(g->d_leaf_cube); cudaFree(g->d_leaf_fine);
+            delete g;
+            return cuda_fail(e, "rt_grid_upload_refined tables");
+        }
+    }
+    e = cudaMalloc(&g->d_rho, n * sizeof(float));
     if (e == cudaSuccess) e = cudaMemcpyAsync(g->d_rho, rho, n * sizeof(float), cudaMemcpyDefault, s);
     if (e == cudaSuccess) e = cudaMallocAsync(&bad, sizeof(unsigned int), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(bad, 0, sizeof(unsigned int), s);
@@ -119,12 +171,12 @@ rt_status rt_grid_upload(rt_ctx* ctx, int nx, int ny, int nz, int ns, const doub
     if (bad) cudaFreeAsync(bad, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
-        cudaFree(g->d_rho);
+        cudaFree(g->d_rho); cudaFree(g->d_cube); cudaFree(g->d_leaf_cube); cudaFree(g->d_leaf_fine);
         delete g;
         return cuda_fail(e, "rt_grid_upload");
     }
     if (hbad) {
-        cudaFree(g->d_rho);
+        cudaFree(g->d_rho); cudaFree(g->d_cube); cudaFree(g->d_leaf_cube); cudaFree(g->d_leaf_fine);
         delete g;
         return fail(RT_ERR_INVALID_ARG, "rt_grid_upload: density must be finite and >= 0");
     }
@@ -138,6 +190,9 @@ void rt_grid_free(rt_grid* g)
     cudaSetDevice(g->ctx->device);
     cudaFree(g->d_rho);
     cudaFree(g->d_packed);
+    cudaFree(g->d_cube);
+    cudaFree(g->d_leaf_cube);
+    cudaFree(g->d_leaf_fine);
     delete g;
 }
 
@@ -353,6 +408,9 @@ static rt_status make_model(const rt_grid* g, const rt_opacity* op, const rt_sou
     m.rho = g->d_packed;
     m.nx = g->nx; m.ny = g->ny; m.nz = g->nz;
     m.ncell = (int)g->ncell();
+    m.refine = g->refine;
+    m.cube = g->d_cube;
+    m.leaf_cube = g->d_leaf_cube;
     m.model_id = model_id;
     m.model_index = model_index;
     m.nsrc = nsrc;
@@ -624,6 +682,7 @@ static rt_status transport_one(rt_ctx* ctx, const rt_grid* grid, const rt_opacit
     TransportKP kp;
     fill_kp(kp, op, p, dm, 1);
     fill_pc(kp, grid, p, out);
+    kp.refined = grid->refine ? 1 : 0;
     st = single_model_options(kp, op, p, out, n_sources, hms[0].md);
     if (st != RT_OK) { cudaFreeAsync(dm.buf, s); if (acc) cudaFreeAsync(acc, s); return st; }
     // PAH pass: the emissivity classes' cumulative tables (Eq. 6), FP64 and
@@ -719,6 +778,8 @@ rt_status rt_batch_create(rt_ctx* ctx, const rt_opacity* op, int n_models, const
         const rt_model& M = models[m];
         if (!M.grid || M.grid->ctx != ctx || M.grid->ns != op->ns)
             return fail(RT_ERR_INVALID_ARG, "rt_batch_create: grid missing, foreign or with other species");
+        if (M.grid->refine)
+            return fail(RT_ERR_INVALID_ARG, "rt_batch_create: refined grids are served by rt_transport only");
         if (M.n_packets == 0) return fail(RT_ERR_INVALID_ARG, "rt_batch_create: n_packets must be > 0");
         if (p->mode == RT_MODE_FROZEN_T && !M.T_prev)
             return fail(RT_ERR_INVALID_ARG, "rt_batch_create: frozen-T mode needs T_prev for every model");
@@ -911,6 +972,7 @@ rt_status rt_raytrace_backward(rt_ctx* ctx, const rt_grid* grid, const rt_opacit
     rt_status st = check_rt_args(ctx, grid, op, T, ev, nev, src, nsrc, cams, ncam, fidx, nfi);
     if (st != RT_OK) return st;
     if (!drho || !dscale) return fail(RT_ERR_INVALID_ARG, "rt_raytrace_backward: NULL output");
+    if (grid->refine) return fail(RT_ERR_INVALID_ARG, "rt_raytrace_backward: refined grids are not served");
     RT_CUDA(cudaSetDevice(ctx->device));
     return raytrace_impl(ctx, grid, op, T, ev, nev, nev_dev, xi_ev, src, nsrc, cams, ncam, fidx, nfi,
                          nullptr, nullptr, dimg, dsed, drho, dscale, (unsigned long long*)ray_steps, true,
@@ -1012,6 +1074,8 @@ rt_status rt_transport_noalloc(rt_ctx* ctx, const rt_grid* grid, const rt_opacit
         return fail(RT_ERR_INVALID_ARG, "rt_transport_noalloc: need pid_begin <= pid_end <= n_packets");
     if (p->n_pc_cams != 0)
         return fail(RT_ERR_INVALID_ARG, "rt_transport_noalloc: photon-counting cameras are served by rt_transport only");
+    if (grid->refine)
+        return fail(RT_ERR_INVALID_ARG, "rt_transport_noalloc: refined grids are served by rt_transport only");
     if (p->mode == RT_MODE_FROZEN_T && !T_prev)
         return fail(RT_ERR_INVALID_ARG, "rt_transport_noalloc: frozen-T mode needs T_prev");
     // scratch layout: staging | kext | packed density | FP64 energy scratch

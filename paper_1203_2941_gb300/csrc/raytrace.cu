@@ -52,6 +52,8 @@ struct RayKP {
     const double* dsed;        // [ncam_total][nfi]
     float* grad;               // [ns][ncell]
     unsigned long long* steps; // ray-cell step counter or nullptr
+    const int* cube;           // refined grids: [ncube] first cell | kCubeDivided
+    int refine;                // r, or 0
 };
 
 // add a per-thread step count to the counter, one atomic per warp
@@ -169,6 +171,116 @@ __device__ __forceinline__ bool dda_step(Ray& r, float& tcur, float& seg, int nx
     r.tm[2] += r.td[2]; r.i[2] += r.d[2] > 0.0f ? 1 : -1; return (unsigned)r.i[2] < (unsigned)nz;
 }
 
+// Two-level traversal of a grid with one level of refinement (Sect. 2):
+// cube indices, sub-cube indices (8 bits per axis, -1 in an undivided cube),
+// cell number and per-axis next-face times along p + t d (cube units).  A
+// step inside a divided cube moves to the next sub-cube; leaving a cube
+// enters the next one at the crossing point (its sub-cube along the other
+// axes by position, ties as in the transport) and restarts the face times.
+template <typename T>
+struct RefWalk {
+    int i[3];
+    int sub, c;
+    T tm[3], td[3];
+};
+
+template <typename T>
+__device__ __forceinline__ void rw_times(RefWalk<T>& w, int r, const T* p, const T* d, T tcur)
+{
+    const T h = w.sub >= 0 ? T(1) / T(r) : T(1);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const T lo = T(w.i[a]) + (w.sub >= 0 ? T((w.sub >> (8 * a)) & 255) * h : T(0));
+        const T xa = p[a] + tcur * d[a];
+        T dist;
+        if (d[a] > T(0)) dist = lo + h - xa;
+        else if (d[a] < T(0)) dist = xa - lo;
+        else dist = T(INFINITY);
+        w.tm[a] = d[a] != T(0) ? tcur + fmax(dist, T(0)) * w.td[a] : T(INFINITY);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void rw_enter(RefWalk<T>& w, const int* cube, int nx, int ny, int r,
+                                         const T* p, const T* d, T tcur, int ea)
+{
+    const int info = cube[(w.i[2] * ny + w.i[1]) * nx + w.i[0]];
+    if (!(info & kCubeDivided)) {
+        w.sub = -1;
+        w.c = info;
+    } else {
+        int sb[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const T u = (p[a] + tcur * d[a] - T(w.i[a])) * T(r);
+            const T f = floor(u);
+            int sa = (int)f;
+            if (f == u && d[a] < T(0)) sa -= 1;
+            sa = min(max(sa, 0), r - 1);
+            if (a == ea) sa = d[a] > T(0) ? 0 : r - 1;
+            sb[a] = sa;
+        }
+        w.sub = sb[0] | (sb[1] << 8) | (sb[2] << 16);
+        w.c = (info & ~kCubeDivided) + (sb[2] * r + sb[1]) * r + sb[0];
+    }
+    rw_times(w, r, p, d, tcur);
+}
+
+// start at p: the cube by floor (a coordinate on a face goes to the lower
+// cube when d points to -axis), clamped into the grid when `clamp` (ray
+// entry points on the box surface); false when p is outside
+template <typename T>
+__device__ __forceinline__ bool rw_start(RefWalk<T>& w, const int* cube, int nx, int ny, int nz, int r,
+                                         const T* p, const T* d, bool clamp)
+{
+    const int n[3] = { nx, ny, nz };
+    bool in = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const T f = floor(p[a]);
+        int i = (int)f;
+        if (f == p[a] && d[a] < T(0)) i -= 1;
+        if (clamp) i = min(max(i, 0), n[a] - 1);
+        in = in && i >= 0 && i < n[a];
+        w.i[a] = i;
+        w.td[a] = d[a] != T(0) ? T(1) / fabs(d[a]) : T(INFINITY);
+    }
+    if (in) rw_enter(w, cube, nx, ny, r, p, d, T(0), -1);
+    return in;
+}
+
+// chord of the current cell (seg) and the step to the next; false when the
+// path leaves the grid
+template <typename T>
+__device__ __forceinline__ bool rw_step(RefWalk<T>& w, const int* cube, int nx, int ny, int nz, int r,
+                                        const T* p, const T* d, T& tcur, T& seg)
+{
+    const int a = (w.tm[0] <= w.tm[1] && w.tm[0] <= w.tm[2]) ? 0 : (w.tm[1] <= w.tm[2] ? 1 : 2);
+    const T tn = a == 0 ? w.tm[0] : (a == 1 ? w.tm[1] : w.tm[2]);
+    seg = tn - tcur;
+    tcur = tn;
+    const int sg = d[a] > T(0) ? 1 : -1;
+    if (w.sub >= 0) {
+        const int sa = ((w.sub >> (8 * a)) & 255) + sg;
+        if (sa >= 0 && sa < r) {
+            w.sub = (w.sub & ~(255 << (8 * a))) | (sa << (8 * a));
+            w.c += sg * (a == 0 ? 1 : (a == 1 ? r : r * r));
+            if (a == 0) w.tm[0] += w.td[0] / T(r);
+            else if (a == 1) w.tm[1] += w.td[1] / T(r);
+            else w.tm[2] += w.td[2] / T(r);
+            return true;
+        }
+    }
+    w.i[0] += a == 0 ? sg : 0;
+    w.i[1] += a == 1 ? sg : 0;
+    w.i[2] += a == 2 ? sg : 0;
+    const int ia = a == 0 ? w.i[0] : (a == 1 ? w.i[1] : w.i[2]);
+    const int n_a = a == 0 ? nx : (a == 1 ? ny : nz);
+    if (ia < 0 || ia >= n_a) return false;
+    rw_enter(w, cube, nx, ny, r, p, d, tcur, a);
+    return true;
+}
+
 template <int NS>
 __device__ __forceinline__ void load_rho(const RayKP& P, int c, float* rho)
 {
@@ -195,7 +307,7 @@ __device__ __forceinline__ void load_eta(const float* base, float* eta)
 // threads repeat the ray's DDA (the same arithmetic, so the same chords) and
 // share its density loads, which keeps the compensated sums of a thread in
 // few registers and the SMs well occupied.
-template <int NS, int NFP>
+template <int NS, int NFP, bool REF>
 __global__ void __launch_bounds__(128) ray_fwd_kernel(const __grid_constant__ RayKP P)
 {
     constexpr int G = NFP / 4;
@@ -217,18 +329,21 @@ __global__ void __launch_bounds__(128) ray_fwd_kernel(const __grid_constant__ Ra
     }
     Ray r = pixel_ray(cm, ix, iy, P.nx, P.ny, P.nz, false);
     unsigned nsteps = 0;
+    RefWalk<float> w;
+    if (REF && r.hit) rw_start(w, P.cube, P.nx, P.ny, P.nz, P.refine, r.p, r.d, true);
     if (r.hit) {
         const float* eta_cam = P.eta + (size_t)cam * P.ncell * P.nfp + 4 * g;
         float tcur = 0.f, seg;
-        const int maxstep = P.nx + P.ny + P.nz + 4;
+        const int maxstep = (P.nx + P.ny + P.nz) * (REF ? P.refine : 1) + 4;
         for (int st = 0; st < maxstep; ++st) {
             ++nsteps;
-            const int c = (r.i[2] * P.ny + r.i[1]) * P.nx + r.i[0];
+            const int c = REF ? w.c : (r.i[2] * P.ny + r.i[1]) * P.nx + r.i[0];
             float rho[NS];
             load_rho<NS>(P, c, rho);
             const float4 e4 = __ldg(reinterpret_cast<const float4*>(eta_cam + (size_t)c * NFP));
             const float eta[4] = { e4.x, e4.y, e4.z, e4.w };
-            const bool inside = dda_step(r, tcur, seg, P.nx, P.ny, P.nz);
+            const bool inside = REF ? rw_step(w, P.cube, P.nx, P.ny, P.nz, P.refine, r.p, r.d, tcur, seg)
+                                    : dda_step(r, tcur, seg, P.nx, P.ny, P.nz);
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 float chi = 0.f;
@@ -416,7 +531,14 @@ struct ScatKP {
     const int* f_of_nu;        // [nf] image-frequency slot or -1
     const float2* ag;          // [ns][nf] {xi cell / (V dnu) (1 - g^2) / (4 pi), g}
     int nf, ns;
+    const unsigned char* leaf_fine;   // refined grids: sub-cubes have V / r^3
+    float fine_scale;                 // r^3
 };
+
+__device__ __forceinline__ float vol_factor(const ScatKP& P, uint32_t cell)
+{
+    return (P.leaf_fine && P.leaf_fine[cell]) ? P.fine_scale : 1.0f;
+}
 
 // Henyey-Greenstein weight towards camera k, FP32: the denominator
 // 1 + g^2 - 2 g cos = (1 - g)^2 + 2 g (1 - cos) keeps its precision at
@@ -450,8 +572,9 @@ __global__ void eta_scatter_kernel(const rt_event* ev, uint64_t cap, const uint6
         const int f = P.f_of_nu[e.nu];
         if (f < 0 || (size_t)e.cell >= P.nc) continue;
         const float2 ag = P.ag[e.species * P.nf + e.nu];
+        const float vf = vol_factor(P, e.cell);
         for (int k = 0; k < P.ncam; ++k)
-            atomicAdd(&eta[((size_t)k * P.nc + e.cell) * P.nfp + f], hg_toward(e, P.kobs + 3 * k, ag));
+            atomicAdd(&eta[((size_t)k * P.nc + e.cell) * P.nfp + f], vf * hg_toward(e, P.kobs + 3 * k, ag));
     }
 }
 
@@ -469,8 +592,9 @@ __global__ void eta_scatter_dup_kernel(const rt_event* ev, uint64_t cap, const u
             const int f = dup[2 * q], j = dup[2 * q + 1];
             if ((int)e.nu != j) continue;
             const float2 ag = P.ag[e.species * P.nf + e.nu];
+            const float vf = vol_factor(P, e.cell);
             for (int k = 0; k < P.ncam; ++k)
-                atomicAdd(&eta[((size_t)k * P.nc + e.cell) * P.nfp + f], hg_toward(e, P.kobs + 3 * k, ag));
+                atomicAdd(&eta[((size_t)k * P.nc + e.cell) * P.nfp + f], vf * hg_toward(e, P.kobs + 3 * k, ag));
         }
     }
 }
@@ -519,6 +643,8 @@ struct StarKP {
     double* sed;               // forward: += L exp(-tau) / (4 pi D^2)
     const double* dsed;        // backward
     float* grad;
+    const int* cube;           // refined grids: [ncube] first cell | kCubeDivided
+    int refine;                // r, or 0
 };
 
 // Direct light of each source along k_obs (FP64).  One warp per (camera,
@@ -549,6 +675,33 @@ __global__ void __launch_bounds__(32) star_kernel(const __grid_constant__ StarKP
                 coef = -P.dsed[cam * P.nfi + fc] * F;
             }
             if (!__any_sync(0xffffffffu, coef != 0.0)) return;
+        }
+        if (P.refine) {
+            // the same walk on a refined grid
+            const double* p0 = P.pos_cell + 3 * si;
+            RefWalk<double> w;
+            bool in = rw_start(w, P.cube, P.nx, P.ny, P.nz, P.refine, p0, d, false);
+            double tcur = 0.0, seg;
+            const int maxstep = (P.nx + P.ny + P.nz) * P.refine + 4;
+            for (int steps = 0; in && steps < maxstep; ++steps) {
+                const size_t c = (size_t)w.c;
+                in = rw_step(w, P.cube, P.nx, P.ny, P.nz, P.refine, p0, d, tcur, seg);
+                const double l = seg * P.cell;
+                if (pass == 0) {
+                    double chi = 0.0;
+                    for (int s = 0; s < P.ns; ++s) chi += (double)__ldg(&P.rho[s * P.nc + c]) * ke[s];
+                    tau += chi * l;
+                } else {
+                    for (int s = 0; s < P.ns; ++s) {
+                        double g = coef * ke[s];
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
+                        g *= l;
+                        if (f == 0 && g != 0.0) atomicAdd(&P.grad[s * P.nc + c], (float)g);
+                    }
+                }
+            }
+            continue;
         }
         int i[3];
         double tm[3], td[3];
@@ -626,7 +779,8 @@ void launch_rays(const RayKP& kp, int npix, bool backward, cudaStream_t s)
     const long long nthreads = (long long)npix * npix * (backward ? 1 : NFP / 4);
     dim3 grid((unsigned)((nthreads + th - 1) / th), kp.ncam);
     if (backward) ray_bwd_kernel<NS, NFP><<<grid, th, 0, s>>>(kp);
-    else ray_fwd_kernel<NS, NFP><<<grid, th, 0, s>>>(kp);
+    else if (kp.refine) ray_fwd_kernel<NS, NFP, true><<<grid, th, 0, s>>>(kp);
+    else ray_fwd_kernel<NS, NFP, false><<<grid, th, 0, s>>>(kp);
     count_launches();
 }
 
@@ -794,6 +948,8 @@ rt_status raytrace_impl(rt_ctx* ctx, const rt_grid* g, const rt_opacity* op, con
         sk.kobs = (const float*)(dbuf + o_ko);
         sk.f_of_nu = (const int*)(dbuf + o_fn);
         sk.nf = op->nf; sk.ns = ns;
+        sk.leaf_fine = g->d_leaf_fine;
+        sk.fine_scale = (float)((double)g->refine * g->refine * g->refine);
         const unsigned blocks = (unsigned)std::min<uint64_t>((nev + 255) / 256, (uint64_t)ctx->num_sms * 8);
         eta_scatter_kernel<<<blocks, 256, 0, s>>>(ev, nev, nev_dev, sk, ctx->d_eta);
         count_launches();
@@ -822,6 +978,8 @@ rt_status raytrace_impl(rt_ctx* ctx, const rt_grid* g, const rt_opacity* op, con
     kp.eta = ctx->d_eta; kp.bk = bk;
     kp.img = images; kp.dimg = dimg; kp.dsed = dsed; kp.grad = gcall;
     kp.steps = ray_steps;
+    kp.cube = g->d_cube;
+    kp.refine = g->refine;
     const int npix = cams[0].npix;
     for (int c0 = 0; c0 < ncam; c0 += kCamChunk) {
         kp.cam0 = c0;
@@ -854,6 +1012,7 @@ rt_status raytrace_impl(rt_ctx* ctx, const rt_grid* g, const rt_opacity* op, con
         sp.inv4piD2 = (const double*)(dbuf + o_i4);
         sp.nsrc = nsrc; sp.ncam = ncam;
         sp.sed = sed; sp.dsed = dsed; sp.grad = gcall;
+        sp.cube = g->d_cube; sp.refine = g->refine;
         star_kernel<<<ncam * nsrc, 32, 0, s>>>(sp, backward ? 1 : 0);
         count_launches();
         RT_CUDA(cudaGetLastError());

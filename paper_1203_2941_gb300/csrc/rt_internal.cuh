@@ -94,8 +94,16 @@ struct rt_grid {
     int packed_lucy_mode;
     double packed_lucy_tau;
     int packed_prec;
-    size_t ncell() const { return (size_t)nx * ny * nz; }
+    // one level of refinement (refine = r >= 2; 0 = uniform grid)
+    int refine;
+    size_t nleaf;                          // cells of a refined grid
+    int* d_cube;                           // [ncube] first cell, kCubeDivided if divided
+    int* d_leaf_cube;                      // [ncell] cube of each cell
+    unsigned char* d_leaf_fine;            // [ncell] 1 = sub-cube
+    size_t ncube() const { return (size_t)nx * ny * nz; }
+    size_t ncell() const { return refine ? nleaf : ncube(); }
 };
+constexpr int kCubeDivided = 1 << 30;      // flag in rt_grid::d_cube
 
 // ----------------------------------------------------------------- kernel parameter blocks
 namespace rtgb {
@@ -103,7 +111,7 @@ namespace rtgb {
 struct ModelDev {
     const void* rho;           // packed cells (float, float2 or float4)
     int nx, ny, nz;
-    int ncell;                 // nx * ny * nz
+    int ncell;                 // cells (nx * ny * nz, or the leaves of a refined grid)
     uint32_t model_id;
     int model_index;
     int nsrc;
@@ -117,6 +125,9 @@ struct ModelDev {
     const double* src_cdf64;   // [nsrc][nf] cumulative L_nu dnu
     const float* src_cdf32;    // [nsrc][nf] cumulative, normalised to 1
     double* E_abs; uint32_t* count; double* esq;
+    const int* cube;           // refined grids: [ncube] first cell | kCubeDivided
+    const int* leaf_cube;      // refined grids: [ncell] cube of each cell
+    int refine;                // r, or 0
     double* accE;              // FP32 build: this call's deposits in units of xi; with
     int acc_q;                 // acc_q = 1 each cell holds {sum, sum of squares} (xi, xi^2)
     double* sed_esc; unsigned long long* sed_cnt;
@@ -181,6 +192,7 @@ struct TransportKP {
     const float* eps_cdf32;             // [n_eps][nf] cumulative, normalised to 1
     const int* eps_class;               // [ncell] or NULL (class 0)
     int n_eps;
+    int refined;                        // the model's grid has one level of refinement
     int n_pc;                           // photon-counting cameras (single-model calls)
     double* pc_img;
     double pc_ctr[3];                   // grid centre, cell units

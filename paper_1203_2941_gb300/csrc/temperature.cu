@@ -14,6 +14,8 @@ constexpr double kPi = 3.14159265358979323846;
 struct TempKP {
     const float* rho; const double* E; double* T;
     size_t nc; int ns; double vol;
+    const unsigned char* leaf_fine;     // refined grids: 1 = sub-cube (volume vol_fine)
+    double vol_fine;
     const double2* tz; const TwNode* tw; const float* zinv;
     float zinv_z0[kMaxSpecies], zinv_idz[kMaxSpecies];
     int tw_ok[kMaxSpecies];
@@ -87,7 +89,8 @@ __global__ void temperatures_kernel(const __grid_constant__ TempKP P)
     const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     if (i >= P.nc * P.ns) return;
     const int s = (int)(i / P.nc);
-    const double rv = (double)P.rho[i] * P.vol;
+    const double vol = (P.leaf_fine && P.leaf_fine[i - (size_t)s * P.nc]) ? P.vol_fine : P.vol;
+    const double rv = (double)P.rho[i] * vol;
     const double e = P.E[i];
     if (!(rv > 0.0) || !(e > 0.0)) { P.T[i] = 0.0; return; }
     if (P.tw_ok[s]) {
@@ -123,15 +126,24 @@ __global__ void temperatures_kernel(const __grid_constant__ TempKP P)
 }
 
 __global__ void guess_kernel(int nx, int ny, int nz, int ns, double bx, double by, double bz,
-                             double cell, const double* pos, const double* L, int nsrc, double* T)
+                             double cell, const double* pos, const double* L, int nsrc, double* T,
+                             size_t nc, int refine, const int* cube, const int* leaf_cube)
 {
-    const size_t nc = (size_t)nx * ny * nz;
     const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     if (i >= nc) return;
     const double h = 6.62607015e-27, kb = 1.380649e-16, c = 2.99792458e10;
     const double sigma = 2.0 * pow(kPi, 5) * pow(kb, 4) / (15.0 * h * h * h * c * c);
-    const int ix = (int)(i % nx), iy = (int)((i / nx) % ny), iz = (int)(i / ((size_t)nx * ny));
-    const double x = bx + (ix + 0.5) * cell, y = by + (iy + 0.5) * cell, z = bz + (iz + 0.5) * cell;
+    // centre of cell i: a cube, or a sub-cube of a divided cube (refined grids)
+    const size_t qc = refine ? (size_t)leaf_cube[i] : i;
+    const int ix = (int)(qc % nx), iy = (int)((qc / nx) % ny), iz = (int)(qc / ((size_t)nx * ny));
+    double fx = 0.5, fy = 0.5, fz = 0.5;
+    if (refine && (cube[qc] & kCubeDivided)) {
+        const int off = (int)i - (cube[qc] & ~kCubeDivided);
+        fx = ((off % refine) + 0.5) / refine;
+        fy = (((off / refine) % refine) + 0.5) / refine;
+        fz = ((off / (refine * refine)) + 0.5) / refine;
+    }
+    const double x = bx + (ix + fx) * cell, y = by + (iy + fy) * cell, z = bz + (iz + fz) * cell;
     double q = 0.0;
     for (int k = 0; k < nsrc; ++k) {
         const double dx = x - pos[3 * k], dy = y - pos[3 * k + 1], dz = z - pos[3 * k + 2];
@@ -163,6 +175,8 @@ rt_status launch_temperatures(rt_ctx* ctx, const rt_grid* g, const rt_opacity* o
     TempKP kp;
     kp.rho = g->d_rho; kp.E = E; kp.T = T;
     kp.nc = nc; kp.ns = g->ns; kp.vol = g->cell * g->cell * g->cell;
+    kp.leaf_fine = g->d_leaf_fine;
+    kp.vol_fine = g->refine ? kp.vol / ((double)g->refine * g->refine * g->refine) : kp.vol;
     kp.tz = op->d_tz; kp.tw = op->d_tw; kp.zinv = op->d_zinv;
     for (int q = 0; q < kMaxSpecies; ++q) {
         kp.zinv_z0[q] = q < g->ns ? op->zinv_z0[q] : 0.0f;
@@ -189,7 +203,7 @@ rt_status launch_temperature_guess(rt_ctx* ctx, const rt_grid* g, const double* 
     const size_t nc = g->ncell();
     guess_kernel<<<(unsigned)((nc + 255) / 256), 256, 0, s>>>(
         g->nx, g->ny, g->nz, g->ns, g->box_min[0], g->box_min[1], g->box_min[2], g->cell, buf,
-        buf + 3 * nsrc, nsrc, T);
+        buf + 3 * nsrc, nsrc, T, nc, g->refine, g->d_cube, g->d_leaf_cube);
     count_launches();
     RT_CUDA(cudaGetLastError());
     RT_CUDA(cudaFreeAsync(buf, s));

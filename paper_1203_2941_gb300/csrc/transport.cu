@@ -271,6 +271,8 @@ struct Lane {
     bool outn;                 // the next face is the grid boundary
     const void* grid;          // packed cells of the packet's model
     uint32_t ncross, nlucy;    // crossings and Lucy deposits of the current packet
+    int cc, sub;               // refined grids: cube of the cell; sub-cube indices
+                               // (8 bits per axis) or -1 for an undivided cube
 };
 
 // a[s] for a register array and a run-time index, without local memory
@@ -298,8 +300,9 @@ __device__ __forceinline__ unsigned char* smem_raw()
 // compiled in, 4 = model descriptors read from the launch parameters (constant
 // bank) instead of global memory, 8 = a single model (its index and grid
 // pointer are constants, not lane registers), 16 = the deferred-packet queue
-// compiled in, 32 = PAH re-emission sources compiled in; production launches
-// leave unused paths out of the hot code.
+// compiled in, 32 = PAH re-emission sources compiled in, 64 = one level of
+// sub-cube refinement (two-level traversal); production launches leave
+// unused paths out of the hot code.
 template <typename R, int NS, int FEAT>
 struct Kernel {
     using PT = typename PackedT<NS>::T;
@@ -310,6 +313,7 @@ struct Kernel {
     static constexpr bool SINGLE = (FEAT & 8) != 0;
     static constexpr bool HAS_DEFER = (FEAT & 16) != 0;
     static constexpr bool HAS_PAH = (FEAT & 32) != 0;
+    static constexpr bool HAS_REF = (FEAT & 64) != 0;
 
     const TransportKP& P;
     const ModelDev* md;        // model of the lane's current packet
@@ -513,12 +517,146 @@ struct Kernel {
             L.k[a] = (R)r.k[a];
         }
         L.c = (int)r.cell;
+        if constexpr (HAS_REF) set_from_cell(L, L.c);
         L.j = (int)r.j;
 #pragma unroll
         for (int s = 0; s < NS; ++s) L.rho[s] = R(0);
         load_freq(L);
         load_cell(L);
         L.st = ST_FLIGHT;
+    }
+
+    // ------------------------------------------------ refined grids (Sect. 2)
+    // Cells are numbered cube by cube; a divided cube's r^3 sub-cubes follow
+    // one another in z, y, x order.  Positions and path lengths stay in cube
+    // edges; a sub-cube's edge is 1/r.
+
+    // cube indices of cube number q
+    __device__ __forceinline__ void cube_idx(int q, int* id) const
+    {
+        const int nxy = md->nx * md->ny;
+        id[2] = q / nxy;
+        const int rr = q - id[2] * nxy;
+        id[1] = rr / md->nx;
+        id[0] = rr - id[1] * md->nx;
+    }
+
+    // cube and sub-cube of cell c
+    __device__ __forceinline__ void set_from_cell(Lane<R, NS>& L, int c) const
+    {
+        const int q = md->leaf_cube[c];
+        const int info = md->cube[q];
+        L.cc = q;
+        if (info & kCubeDivided) {
+            const int r = md->refine;
+            const int off = c - (info & ~kCubeDivided);
+            const int s0 = off % r, s1 = (off / r) % r, s2 = off / (r * r);
+            L.sub = s0 | (s1 << 8) | (s2 << 16);
+        } else {
+            L.sub = -1;
+        }
+    }
+
+    // Enter cube q at position xc (cube units): its cell, descending into
+    // the sub-cube that holds xc when the cube is divided (a coordinate on a
+    // sub-face belongs to the lower sub-cube when moving towards -axis).
+    // Axis `ea` (0..2, or -1) is the one the packet entered through.
+    __device__ __forceinline__ void enter_cube(Lane<R, NS>& L, int q, const int* id, const R* xc,
+                                               int ea) const
+    {
+        const int info = md->cube[q];
+        L.cc = q;
+        if (!(info & kCubeDivided)) {
+            L.sub = -1;
+            L.c = info;
+            return;
+        }
+        const int r = md->refine;
+        int sb[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const R u = (xc[a] - (R)id[a]) * (R)r;
+            const R f = floor(u);
+            int sa = (int)f;
+            if (f == u && L.k[a] < R(0)) sa -= 1;
+            sa = min(max(sa, 0), r - 1);
+            if (a == ea) sa = L.k[a] > R(0) ? 0 : r - 1;
+            sb[a] = sa;
+        }
+        L.sub = sb[0] | (sb[1] << 8) | (sb[2] << 16);
+        L.c = (info & ~kCubeDivided) + (sb[2] * r + sb[1]) * r + sb[0];
+    }
+
+    // lower corner (cube units) and edge of the lane's cell
+    __device__ __forceinline__ R cell_box(const Lane<R, NS>& L, R* lo) const
+    {
+        int id[3];
+        cube_idx(L.cc, id);
+        if (L.sub < 0) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) lo[a] = (R)id[a];
+            return R(1);
+        }
+        const R h = R(1) / (R)md->refine;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) lo[a] = (R)id[a] + (R)((L.sub >> (8 * a)) & 255) * h;
+        return h;
+    }
+
+    // Next-face times of every axis from the current point x + tcur k
+    // (td holds 1/|k| per axis).
+    __device__ __forceinline__ void face_times(Lane<R, NS>& L) const
+    {
+        R lo[3];
+        const R h = cell_box(L, lo);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const R xa = L.x[a] + L.tcur * L.k[a];
+            R d;
+            if (L.k[a] > R(0)) d = lo[a] + h - xa;
+            else if (L.k[a] < R(0)) d = xa - lo[a];
+            else d = R(INFINITY);
+            L.tm[a] = L.k[a] != R(0) ? L.tcur + fmax(d, R(0)) * L.td[a] : R(INFINITY);
+        }
+    }
+
+    // Crossing of a refined grid's traversal through the face on axis a:
+    // the next sub-cube of the cube, else the next cube (entering its
+    // sub-cube when it is divided); leaving the grid escapes.
+    __device__ __forceinline__ void step_ref(Lane<R, NS>& L, int a)
+    {
+        const int sg = L.k[a] > R(0) ? 1 : -1;
+        const int r = md->refine;
+        if (L.sub >= 0) {
+            const int sa = ((L.sub >> (8 * a)) & 255) + sg;
+            if (sa >= 0 && sa < r) {
+                L.sub = (L.sub & ~(255 << (8 * a))) | (sa << (8 * a));
+                L.c += sg * (a == 0 ? 1 : (a == 1 ? r : r * r));
+                // (branches, not a run-time index: the lane state stays in registers)
+                if (a == 0) L.tm[0] += L.td[0] / (R)r;
+                else if (a == 1) L.tm[1] += L.td[1] / (R)r;
+                else L.tm[2] += L.td[2] / (R)r;
+                load_cell(L);
+                return;
+            }
+        }
+        int id[3];
+        cube_idx(L.cc, id);
+        id[0] += a == 0 ? sg : 0;
+        id[1] += a == 1 ? sg : 0;
+        id[2] += a == 2 ? sg : 0;
+        const int ia = a == 0 ? id[0] : (a == 1 ? id[1] : id[2]);
+        const int n_a = a == 0 ? md->nx : (a == 1 ? md->ny : md->nz);
+        if (ia < 0 || ia >= n_a) {
+            L.st = ST_ESCAPE;              // c keeps the last cell inside
+            return;
+        }
+        R xc[3];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) xc[b] = L.x[b] + L.tcur * L.k[b];
+        enter_cube(L, (id[2] * md->ny + id[1]) * md->nx + id[0], id, xc, a);
+        face_times(L);
+        load_cell(L);
     }
 
     __device__ __forceinline__ void emit(Lane<R, NS>& L, uint64_t w)
@@ -597,6 +735,9 @@ struct Kernel {
             in = in && (i >= 0 && i < n[a]);
         }
         L.c = in ? (idx[2] * n[1] + idx[1]) * n[0] + idx[0] : 0;
+        if constexpr (HAS_REF) {
+            if (in) enter_cube(L, L.c, idx, L.x, -1);
+        }
         count(RT_STAT_EMITTED, 1);
         traj(L, RT_TRAJ_EMIT, L.x);
         if (!in) {
@@ -636,10 +777,19 @@ struct Kernel {
         } else {
             L.j = search_cdf(P.eps_cdf32 + (size_t)n * P.nf, P.nf, ub);
         }
-        const int ix = c % md->nx, iy = (c / md->nx) % md->ny, iz = c / (md->nx * md->ny);
-        L.x[0] = (R)ix + ux;
-        L.x[1] = (R)iy + uy;
-        L.x[2] = (R)iz + uz;
+        if constexpr (HAS_REF) {
+            set_from_cell(L, c);
+            R lo[3];
+            const R h = cell_box(L, lo);
+            L.x[0] = lo[0] + ux * h;
+            L.x[1] = lo[1] + uy * h;
+            L.x[2] = lo[2] + uz * h;
+        } else {
+            const int ix = c % md->nx, iy = (c / md->nx) % md->ny, iz = c / (md->nx * md->ny);
+            L.x[0] = (R)ix + ux;
+            L.x[1] = (R)iy + uy;
+            L.x[2] = (R)iz + uz;
+        }
         iso_dir(u1, u2, L.k);
         L.c = c;
         traj(L, RT_TRAJ_EMIT, L.x);
@@ -696,7 +846,10 @@ struct Kernel {
     // FP64 build
     __device__ __forceinline__ double temperature64(const Lane<R, NS>& L, int s, double E)
     {
-        const double rv = sel(L.rho, s) * md->vol;
+        double rv = sel(L.rho, s) * md->vol;
+        if constexpr (HAS_REF) {
+            if (L.sub >= 0) rv /= (double)md->refine * md->refine * md->refine;   // sub-cube volume
+        }
         return rv > 0.0 ? solve_T64(P, s, E / rv) : 0.0;
     }
 
@@ -708,7 +861,10 @@ struct Kernel {
         if (P.mode == RT_MODE_BW) {
             const float rs = sel(L.rho, s);
             if (!(E > 0.0) || !(rs > 0.0f)) return -INFINITY;
-            const float y = log2_d(E) - __log2f(rs) - (float)md->log2_4piV;
+            float y = log2_d(E) - __log2f(rs) - (float)md->log2_4piV;
+            if constexpr (HAS_REF) {
+                if (L.sub >= 0) y += 3.0f * __log2f((float)md->refine);       // sub-cube volume
+            }
             float f = (y - P.tinv_y0[s]) * P.tinv_inv_dy[s];
             f = fminf(fmaxf(f, 0.0f), (float)(kTinvN - 1));
             const int i = min((int)f, kTinvN - 2);
@@ -818,6 +974,10 @@ struct Kernel {
         if constexpr (HAS_DEFER) {
             if (P.defer_events && !P.resume && L.nev >= P.defer_events && defer(L)) return;
         }
+        if constexpr (HAS_REF) {
+            flight_ref(L);
+            return;
+        }
         const int nx = md->nx, ny = md->ny, nz = md->nz;
         const int iz = L.c / (nx * ny);
         const int r = L.c - iz * nx * ny;
@@ -865,6 +1025,60 @@ struct Kernel {
         L.tcur = R(0);
         prefetch_next(L);
         L.st = ST_MARCH;
+    }
+
+    // Flight of a refined grid's packet: the MRW sphere and threshold use the
+    // cell's own box (a sub-cube's in divided cubes), then the two-level
+    // traversal starts from the cell's faces.
+    __device__ __forceinline__ void flight_ref(Lane<R, NS>& L)
+    {
+        R lo[3];
+        const R h = cell_box(L, lo);
+        if constexpr (HAS_MRW) {
+            if (P.mrw && P.mode != RT_MODE_NOREEMIT && L.chi * h > (R)P.mrw_tau_cell) {
+                R R0 = R(1e30);
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const R d1 = L.x[a] - lo[a], d2 = lo[a] + h - L.x[a];
+                    R0 = fmin(R0, fmin(d1, d2));
+                }
+                R0 = fmax(R0, R(0));
+                if (R0 * L.chi >= (R)P.mrw_gamma) {
+                    mrw_step(L, R0);
+                    return;
+                }
+            }
+        }
+        L.tau = -r_log(U(L));
+#pragma unroll
+        for (int a = 0; a < 3; ++a) L.td[a] = L.k[a] != R(0) ? R(1) / fabs(L.k[a]) : R(INFINITY);
+        L.tcur = R(0);
+        face_times(L);
+        L.st = ST_MARCH;
+    }
+
+    // One crossing step of a refined grid's traversal (no prefetch: the next
+    // cell is known only after the crossing).
+    __device__ __forceinline__ void march_ref(Lane<R, NS>& L)
+    {
+        const int a = (L.tm[0] <= L.tm[1] && L.tm[0] <= L.tm[2]) ? 0 : (L.tm[1] <= L.tm[2] ? 1 : 2);
+        const R tn = a == 0 ? L.tm[0] : (a == 1 ? L.tm[1] : L.tm[2]);
+        const R seg = tn - L.tcur;
+        const R dtau = L.chi * seg;
+        if (dtau <= L.tau) {
+            if (L.lucy) deposit_lucy(L, seg);
+            L.tau -= dtau;
+            L.tcur = tn;
+            L.ncross++;
+            step_ref(L, a);
+        } else {
+            const R d = L.tau / L.chi;
+            if (L.lucy) deposit_lucy(L, d);
+            L.tcur += d;
+#pragma unroll
+            for (int a2 = 0; a2 < 3; ++a2) L.x[a2] += L.tcur * L.k[a2];
+            L.st = ST_INTERACT;
+        }
     }
 
     __device__ __forceinline__ void mrw_step(Lane<R, NS>& L, R R0)
@@ -922,6 +1136,10 @@ struct Kernel {
     // converged.
     __device__ __forceinline__ void march(Lane<R, NS>& L)
     {
+        if constexpr (HAS_REF) {
+            march_ref(L);
+            return;
+        }
         const int a = L.nax;
         const R tn = a == 0 ? L.tm[0] : (a == 1 ? L.tm[1] : L.tm[2]);
         const R seg = tn - L.tcur;
@@ -1268,11 +1486,14 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (NS == 4 ? 3 : RT_TR
 // ------------------------------------------------------------- grid packing
 template <typename PT, int NS>
 __global__ void pack_kernel(const float* rho, size_t nc, double kext_max, PT* out,
-                            int prec, double cell, int lucy_mode, double lucy_tau,
-                            const double* kext, int nf)
+                            int prec, double cube, const unsigned char* leaf_fine, double inv_r,
+                            int lucy_mode, double lucy_tau, const double* kext, int nf)
 {
     const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     if (i >= nc) return;
+    // the Lucy criterion is on the cell's own edge (a sub-cube's in refined
+    // cubes); the packed density stays rho * cube edge (paths in cube units)
+    const double cell = (leaf_fine && leaf_fine[i]) ? cube * inv_r : cube;
     float r[4] = { 0.f, 0.f, 0.f, 0.f };
     double dust = 0.0;
     for (int s = 0; s < NS; ++s) {
@@ -1300,7 +1521,7 @@ __global__ void pack_kernel(const float* rho, size_t nc, double kext_max, PT* ou
         }
     }
     float v[4];
-    for (int s = 0; s < 4; ++s) v[s] = prec == RT_PREC_FP32 ? (float)((double)r[s] * cell) : r[s];
+    for (int s = 0; s < 4; ++s) v[s] = prec == RT_PREC_FP32 ? (float)((double)r[s] * cube) : r[s];
     v[0] = lucy ? -fabsf(v[0]) : fabsf(v[0]);
     if constexpr (NS == 1) out[i] = v[0];
     else if constexpr (NS == 2) out[i] = make_float2(v[0], v[1]);
@@ -1371,6 +1592,11 @@ template <typename R, int NS>
 rt_status launch_feat(rt_ctx* ctx, const TransportKP& kp, int schedule, int threads,
                       int blocks_per_sm, cudaStream_t s)
 {
+    // refined grids: the generic variants with the two-level traversal
+    if (kp.refined) {
+        if (kp.pah_src) return launch_one<R, NS, 115>(ctx, kp, schedule, threads, blocks_per_sm, s);
+        return launch_one<R, NS, 83>(ctx, kp, schedule, threads, blocks_per_sm, s);
+    }
     if constexpr (sizeof(R) == 8) {
         if (kp.pah_src) return launch_one<R, NS, 51>(ctx, kp, schedule, threads, blocks_per_sm, s);
         return launch_one<R, NS, 19>(ctx, kp, schedule, threads, blocks_per_sm, s);
@@ -1439,16 +1665,20 @@ rt_status pack_grid(rt_grid* g, const rt_opacity* op, int lucy_mode, double lucy
     const unsigned blocks = (unsigned)((nc + th - 1) / th);
     if (vec == 1)
         pack_kernel<float, 1><<<blocks, th, 0, s>>>(g->d_rho, nc, kext_max(op), (float*)g->d_packed, prec,
-                                                     g->cell, lucy_mode, lucy_tau, kext, op->nf);
+                                                     g->cell, g->d_leaf_fine, g->refine ? 1.0 / g->refine : 1.0,
+                                                     lucy_mode, lucy_tau, kext, op->nf);
     else if (vec == 2)
         pack_kernel<float2, 2><<<blocks, th, 0, s>>>(g->d_rho, nc, kext_max(op), (float2*)g->d_packed,
-                                                      prec, g->cell, lucy_mode, lucy_tau, kext, op->nf);
+                                                      prec, g->cell, g->d_leaf_fine, g->refine ? 1.0 / g->refine : 1.0,
+                                                     lucy_mode, lucy_tau, kext, op->nf);
     else if (g->ns == 3)
         pack_kernel<float4, 3><<<blocks, th, 0, s>>>(g->d_rho, nc, kext_max(op), (float4*)g->d_packed,
-                                                      prec, g->cell, lucy_mode, lucy_tau, kext, op->nf);
+                                                      prec, g->cell, g->d_leaf_fine, g->refine ? 1.0 / g->refine : 1.0,
+                                                     lucy_mode, lucy_tau, kext, op->nf);
     else
         pack_kernel<float4, 4><<<blocks, th, 0, s>>>(g->d_rho, nc, kext_max(op), (float4*)g->d_packed,
-                                                      prec, g->cell, lucy_mode, lucy_tau, kext, op->nf);
+                                                      prec, g->cell, g->d_leaf_fine, g->refine ? 1.0 / g->refine : 1.0,
+                                                     lucy_mode, lucy_tau, kext, op->nf);
     RT_CUDA(cudaGetLastError());
     RT_CUDA(cudaFreeAsync(kext, s));
     g->packed_vec = vec;
@@ -1482,16 +1712,20 @@ rt_status pack_grid_into(const rt_grid* g, const rt_opacity* op, int lucy_mode, 
     const unsigned blocks = (unsigned)((nc + 255) / 256);
     if (vec == 1)
         pack_kernel<float, 1><<<blocks, 256, 0, s>>>(g->d_rho, nc, kext_max(op), (float*)dst, prec,
-                                                      g->cell, lucy_mode, lucy_tau, kext, op->nf);
+                                                      g->cell, g->d_leaf_fine, g->refine ? 1.0 / g->refine : 1.0,
+                                                     lucy_mode, lucy_tau, kext, op->nf);
     else if (vec == 2)
         pack_kernel<float2, 2><<<blocks, 256, 0, s>>>(g->d_rho, nc, kext_max(op), (float2*)dst, prec,
-                                                       g->cell, lucy_mode, lucy_tau, kext, op->nf);
+                                                       g->cell, g->d_leaf_fine, g->refine ? 1.0 / g->refine : 1.0,
+                                                     lucy_mode, lucy_tau, kext, op->nf);
     else if (g->ns == 3)
         pack_kernel<float4, 3><<<blocks, 256, 0, s>>>(g->d_rho, nc, kext_max(op), (float4*)dst, prec,
-                                                       g->cell, lucy_mode, lucy_tau, kext, op->nf);
+                                                       g->cell, g->d_leaf_fine, g->refine ? 1.0 / g->refine : 1.0,
+                                                     lucy_mode, lucy_tau, kext, op->nf);
     else
         pack_kernel<float4, 4><<<blocks, 256, 0, s>>>(g->d_rho, nc, kext_max(op), (float4*)dst, prec,
-                                                       g->cell, lucy_mode, lucy_tau, kext, op->nf);
+                                                       g->cell, g->d_leaf_fine, g->refine ? 1.0 / g->refine : 1.0,
+                                                     lucy_mode, lucy_tau, kext, op->nf);
     count_launches(2);
     RT_CUDA(cudaGetLastError());
     return RT_OK;

@@ -33,7 +33,7 @@ EXPORTS = ["rt_last_error", "rt_version", "rt_ctx_create", "rt_ctx_destroy", "rt
            "rt_transport", "rt_temperatures", "rt_temperature_guess", "rt_raytrace",
            "rt_raytrace_backward", "rt_batch_create", "rt_batch_run", "rt_batch_free",
            "rt_transport_batched", "rt_philox", "rt_kernel_launches", "rt_transport_noalloc", "rt_visibilities",
-           "rt_pah_reemit"]
+           "rt_pah_reemit", "rt_grid_upload_refined", "rt_grid_ncell"]
 
 
 class RtError(RuntimeError):
@@ -108,6 +108,9 @@ def load(path: str = LIB_PATH):
         "rt_ctx_create": (i32, [i32, C.POINTER(vp)]),
         "rt_ctx_destroy": (None, [vp]),
         "rt_grid_upload": (i32, [vp, i32, i32, i32, i32, C.POINTER(dbl), dbl, vp, vp, C.POINTER(vp)]),
+        "rt_grid_upload_refined": (i32, [vp, i32, i32, i32, i32, C.POINTER(dbl), dbl, i32, vp, vp, vp,
+                                         C.POINTER(vp)]),
+        "rt_grid_ncell": (u64, [vp]),
         "rt_grid_free": (None, [vp]),
         "rt_opacity_upload": (i32, [vp, i32, vp, vp, i32, vp, vp, vp, vp, C.POINTER(vp)]),
         "rt_opacity_free": (None, [vp]),
@@ -159,6 +162,20 @@ def rt_ctx_create(device: int = 0) -> int:
 
 def rt_ctx_destroy(ctx: int) -> None:
     load().rt_ctx_destroy(ctx)
+
+
+def rt_grid_upload_refined(ctx, nx, ny, nz, n_species, box_min, cell, refine, refined_ptr, rho_ptr,
+                           stream=0) -> int:
+    h = C.c_void_p()
+    bm = (C.c_double * 3)(*[float(v) for v in box_min])
+    _check(load().rt_grid_upload_refined(ctx, nx, ny, nz, n_species, bm, float(cell), int(refine),
+                                         refined_ptr, rho_ptr, stream, C.byref(h)),
+           "rt_grid_upload_refined")
+    return h.value
+
+
+def rt_grid_ncell(grid) -> int:
+    return int(load().rt_grid_ncell(grid))
 
 
 def rt_grid_upload(ctx, nx, ny, nz, n_species, box_min, cell, rho_ptr, stream=0) -> int:

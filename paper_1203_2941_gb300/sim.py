@@ -52,28 +52,48 @@ class Context:
             pass
 
     def grid(self, model, stream=None) -> "Grid":
-        return Grid(self, model.rho, model.box_min, model.cell, stream)
+        return Grid(self, model.rho, model.box_min, model.cell, stream,
+                    refine=getattr(model, "refine", 0), refined=getattr(model, "refined", None))
 
     def opacity(self, model) -> "Opacity":
         return Opacity(self, model.nu, model.dnu, model.kabs, model.ksca, model.g, model.is_pah)
 
 
 class Grid:
-    def __init__(self, ctx: Context, rho, box_min, cell, stream=None):
+    """Density grid on the device.  Uniform: rho [ns, nz, ny, nx].  One level
+    of refinement: ``refine`` = r and ``refined`` [nz, ny, nx] (nonzero =
+    divided cube) with rho [ns, ncell] in the library's cell numbering."""
+
+    def __init__(self, ctx: Context, rho, box_min, cell, stream=None, refine: int = 0,
+                 refined=None):
         self.ctx = ctx
         if isinstance(rho, torch.Tensor):
             t = rho.detach().to(dtype=torch.float32).contiguous()
         else:
             t = torch.from_numpy(np.ascontiguousarray(rho, dtype=np.float32))
-        ns, nz, ny, nx = t.shape
-        self.shape = (nx, ny, nz)
-        self.ns = ns
-        self.ncell = nx * ny * nz
         self.box_min = [float(v) for v in box_min]
         self.cell = float(cell)
+        self.refine = int(refine or 0)
         self._src = t           # keep alive until the copy finished (upload syncs)
-        self.h = R.rt_grid_upload(ctx.h, nx, ny, nz, ns, self.box_min, self.cell, t.data_ptr(),
-                                  _stream(stream) if t.is_cuda else _stream(stream))
+        if self.refine:
+            mask = np.ascontiguousarray(refined, dtype=np.uint8)
+            nz, ny, nx = mask.shape
+            ns = t.shape[0]
+            self.h = R.rt_grid_upload_refined(ctx.h, nx, ny, nz, ns, self.box_min, self.cell,
+                                              self.refine, mask.ctypes.data_as(C.c_void_p),
+                                              t.data_ptr(), _stream(stream))
+            self.ncell = R.rt_grid_ncell(self.h)
+            if t.shape != (ns, self.ncell):
+                R.rt_grid_free(self.h)
+                self.h = None
+                raise ValueError(f"refined grid needs rho of shape ({ns}, {self.ncell})")
+        else:
+            ns, nz, ny, nx = t.shape
+            self.h = R.rt_grid_upload(ctx.h, nx, ny, nz, ns, self.box_min, self.cell, t.data_ptr(),
+                                      _stream(stream))
+            self.ncell = nx * ny * nz
+        self.shape = (nx, ny, nz)
+        self.ns = ns
         self._src = None
 
     def __del__(self):
