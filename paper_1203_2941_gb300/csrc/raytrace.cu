@@ -259,7 +259,8 @@ __device__ __forceinline__ bool rw_step(RefWalk<T>& w, const int* cube, int nx, 
     const T tn = a == 0 ? w.tm[0] : (a == 1 ? w.tm[1] : w.tm[2]);
     seg = tn - tcur;
     tcur = tn;
-    const int sg = d[a] > T(0) ? 1 : -1;
+    const T da = a == 0 ? d[0] : (a == 1 ? d[1] : d[2]);
+    const int sg = da > T(0) ? 1 : -1;
     if (w.sub >= 0) {
         const int sa = ((w.sub >> (8 * a)) & 255) + sg;
         if (sa >= 0 && sa < r) {

@@ -625,7 +625,8 @@ struct Kernel {
     // sub-cube when it is divided); leaving the grid escapes.
     __device__ __forceinline__ void step_ref(Lane<R, NS>& L, int a)
     {
-        const int sg = L.k[a] > R(0) ? 1 : -1;
+        const R ka = a == 0 ? L.k[0] : (a == 1 ? L.k[1] : L.k[2]);
+        const int sg = ka > R(0) ? 1 : -1;
         const int r = md->refine;
         if (L.sub >= 0) {
             const int sa = ((L.sub >> (8 * a)) & 255) + sg;
@@ -1592,9 +1593,16 @@ template <typename R, int NS>
 rt_status launch_feat(rt_ctx* ctx, const TransportKP& kp, int schedule, int threads,
                       int blocks_per_sm, cudaStream_t s)
 {
-    // refined grids: the generic variants with the two-level traversal
+    // refined grids: single-model FP32 launches without trajectories or the
+    // deferred queue take the lean variants; everything else the generic ones
     if (kp.refined) {
         if (kp.pah_src) return launch_one<R, NS, 115>(ctx, kp, schedule, threads, blocks_per_sm, s);
+        if constexpr (sizeof(R) == 4) {
+            if (kp.single && kp.param_models && !kp.want_traj && !kp.defer_events) {
+                if (kp.mrw) return launch_one<R, NS, 77>(ctx, kp, schedule, threads, blocks_per_sm, s);
+                return launch_one<R, NS, 76>(ctx, kp, schedule, threads, blocks_per_sm, s);
+            }
+        }
         return launch_one<R, NS, 83>(ctx, kp, schedule, threads, blocks_per_sm, s);
     }
     if constexpr (sizeof(R) == 8) {
