@@ -86,7 +86,7 @@ RT_API rt_status rt_grid_upload(rt_ctx* ctx, int nx, int ny, int nz, int n_speci
  * divided into r^3 sub-cubes (r = refine, 2..16).  Cells are numbered cube
  * by cube in z, y, x order; a divided cube's r^3 sub-cubes take consecutive
  * numbers, again in z, y, x order.  rho: [n_species][ncell] float32, host or
- * device, ncell = (cubes not divided) + r^3 (cubes divided), at most 2e9.
+ * device, ncell = (cubes not divided) + r^3 (cubes divided) < 2^30.
  * Every per-cell array of the other calls (E_abs, count, esq, T, the cell of
  * events and PAH records) is indexed by this cell number.  Served by
  * rt_transport, rt_pah_reemit, rt_temperatures, rt_temperature_guess and

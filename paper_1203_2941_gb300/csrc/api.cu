@@ -118,7 +118,7 @@ rt_status rt_grid_upload_refined(rt_ctx* ctx, int nx, int ny, int nz, int ns, co
         nleaf = 0;
         for (size_t c = 0; c < ncube; ++c) nleaf += refined[c] ? r3 : 1;
         if ((double)nleaf > 2.0e9 || nleaf >= (size_t)kCubeDivided)
-            return fail(RT_ERR_INVALID_ARG, "rt_grid_upload_refined: more than 2e9 cells");
+            return fail(RT_ERR_INVALID_ARG, "rt_grid_upload_refined: 2^30 cells or more");
         cube.resize(ncube);
         leaf_cube.resize(nleaf);
         leaf_fine.resize(nleaf);
