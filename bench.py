@@ -31,9 +31,10 @@ METRIC = "photon-packet cell-crossings/s"
 UNIT = "crossings/s"
 # DRAM bytes (read + write) of one full-size transport launch of this
 # workload, from a single-pass ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum, profiles/transport_kernel_r2shell128.md); to be
-# re-measured (or set to None) whenever the transport kernel changes
-TRANSPORT_DRAM_BYTES = 31.75e6 + 30.30e6
+# dram__bytes_write.sum; the command is in the transport kernel's summary
+# under profiles/); to be re-measured (or set to None) whenever the transport
+# kernel changes
+TRANSPORT_DRAM_BYTES = 31.858e6 + 31.178e6
 
 
 def parse():

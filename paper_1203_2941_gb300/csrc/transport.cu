@@ -301,8 +301,8 @@ __device__ __forceinline__ unsigned char* smem_raw()
 // bank) instead of global memory, 8 = a single model (its index and grid
 // pointer are constants, not lane registers), 16 = the deferred-packet queue
 // compiled in, 32 = PAH re-emission sources compiled in, 64 = one level of
-// sub-cube refinement (two-level traversal); production launches leave
-// unused paths out of the hot code.
+// sub-cube refinement (two-level traversal), 128 = photon-counting cameras;
+// production launches leave unused paths out of the hot code.
 template <typename R, int NS, int FEAT>
 struct Kernel {
     using PT = typename PackedT<NS>::T;
@@ -314,6 +314,7 @@ struct Kernel {
     static constexpr bool HAS_DEFER = (FEAT & 16) != 0;
     static constexpr bool HAS_PAH = (FEAT & 32) != 0;
     static constexpr bool HAS_REF = (FEAT & 64) != 0;
+    static constexpr bool HAS_PC = (FEAT & 128) != 0;
 
     const TransportKP& P;
     const ModelDev* md;        // model of the lane's current packet
@@ -1308,7 +1309,9 @@ struct Kernel {
             atomicAdd(&md->sed_cnt[b * P.nf + L.j], 1ull);
         }
         count(RT_STAT_ESCAPED, 1);
-        if (P.n_pc) photon_count(L);
+        if constexpr (HAS_PC) {
+            if (P.n_pc) photon_count(L);
+        }
         if constexpr (HAS_TRAJ) {
             if (md->traj) {
                 R xe[3];
@@ -1588,34 +1591,37 @@ rt_status launch_one(rt_ctx* ctx, const TransportKP& kp, int schedule, int threa
     return RT_OK;
 }
 
-// FP32: instantiate only the feature set a launch needs; FP64 debug: all
+// FP32: instantiate only the feature set a launch needs; FP64 debug: all.
+// The generic variants (every optional path, photon counting included) are
+// FEAT 147 (uniform grid), 179 (+ PAH sources), 211 (+ refinement) and 243
+// (both); photon-counting cameras always run a generic variant.
 template <typename R, int NS>
 rt_status launch_feat(rt_ctx* ctx, const TransportKP& kp, int schedule, int threads,
                       int blocks_per_sm, cudaStream_t s)
 {
-    // refined grids: single-model FP32 launches without trajectories or the
-    // deferred queue take the lean variants; everything else the generic ones
+    // refined grids: single-model FP32 launches without trajectories, the
+    // deferred queue or cameras take the lean variants
     if (kp.refined) {
-        if (kp.pah_src) return launch_one<R, NS, 115>(ctx, kp, schedule, threads, blocks_per_sm, s);
+        if (kp.pah_src) return launch_one<R, NS, 243>(ctx, kp, schedule, threads, blocks_per_sm, s);
         if constexpr (sizeof(R) == 4) {
-            if (kp.single && kp.param_models && !kp.want_traj && !kp.defer_events) {
+            if (kp.single && kp.param_models && !kp.want_traj && !kp.defer_events && !kp.n_pc) {
                 if (kp.mrw) return launch_one<R, NS, 77>(ctx, kp, schedule, threads, blocks_per_sm, s);
                 return launch_one<R, NS, 76>(ctx, kp, schedule, threads, blocks_per_sm, s);
             }
         }
-        return launch_one<R, NS, 83>(ctx, kp, schedule, threads, blocks_per_sm, s);
+        return launch_one<R, NS, 211>(ctx, kp, schedule, threads, blocks_per_sm, s);
     }
     if constexpr (sizeof(R) == 8) {
-        if (kp.pah_src) return launch_one<R, NS, 51>(ctx, kp, schedule, threads, blocks_per_sm, s);
-        return launch_one<R, NS, 19>(ctx, kp, schedule, threads, blocks_per_sm, s);
+        if (kp.pah_src) return launch_one<R, NS, 179>(ctx, kp, schedule, threads, blocks_per_sm, s);
+        return launch_one<R, NS, 147>(ctx, kp, schedule, threads, blocks_per_sm, s);
     } else {
         // PAH re-emission pass: the single-model variant, or the generic one
-        // with every optional path compiled in
         if (kp.pah_src) {
-            if (!kp.mrw && !kp.want_traj && !kp.defer_events && kp.single)
+            if (!kp.mrw && !kp.want_traj && !kp.defer_events && kp.single && !kp.n_pc)
                 return launch_one<R, NS, 44>(ctx, kp, schedule, threads, blocks_per_sm, s);
-            return launch_one<R, NS, 51>(ctx, kp, schedule, threads, blocks_per_sm, s);
+            return launch_one<R, NS, 179>(ctx, kp, schedule, threads, blocks_per_sm, s);
         }
+        if (kp.n_pc) return launch_one<R, NS, 147>(ctx, kp, schedule, threads, blocks_per_sm, s);
         // trajectory logging runs the generic variants; otherwise descriptors
         // come from the parameters when they fit, and one model is constant
         const int feat = (kp.mrw ? 1 : 0) |
