@@ -582,10 +582,15 @@ def main():
     hbm = hbm or 6800.0
     achieved = bytes_alg / t_tr_s / 1e9
     default_work = (a.n == 128 and a.tau == 10.0 and int(a.packets) == 10**7)
+    # sector-granular view of the same launch: every gather, deposit pair,
+    # absorption tally, event record and escape tally touches a 32-byte sector
+    bytes_sec = (32 * S["crossings"] + 32 * S["lucy_deposits"] + 64 * S["absorptions"]
+                 + 32 * min(S["scatters"], K * ev_cap) + 32 * S["escaped"]) / K
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
             "traffic": TRANSPORT_DRAM_BYTES if default_work else None,
             "kernel": "transport_kernel<float,1,12>", "peak_source": peak_src,
-            "bytes_per_launch": bytes_alg, "launch_ms": t_tr_s * 1e3}
+            "bytes_per_launch": bytes_alg, "launch_ms": t_tr_s * 1e3,
+            "sector_bytes_per_launch": bytes_sec, "sector_achieved": bytes_sec / t_tr_s / 1e9}
 
     # end to end through the public API with host buffers
     e2e = None

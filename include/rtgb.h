@@ -89,8 +89,8 @@ RT_API rt_status rt_grid_upload(rt_ctx* ctx, int nx, int ny, int nz, int n_speci
  * device, ncell = (cubes not divided) + r^3 (cubes divided) < 2^30.
  * Every per-cell array of the other calls (E_abs, count, esq, T, the cell of
  * events and PAH records) is indexed by this cell number.  Served by
- * rt_transport, rt_pah_reemit, rt_temperatures, rt_temperature_guess and
- * rt_raytrace; rt_raytrace_backward, the batched and no-alloc transports
+ * rt_transport, rt_pah_reemit, rt_temperatures, rt_temperature_guess,
+ * rt_raytrace and rt_raytrace_backward; the batched and no-alloc transports
  * refuse refined grids (RT_ERR_INVALID_ARG).  Errors as rt_grid_upload,
  * plus a bad refine factor. */
 RT_API rt_status rt_grid_upload_refined(rt_ctx* ctx, int nx, int ny, int nz, int n_species,

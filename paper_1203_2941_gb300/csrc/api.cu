@@ -972,7 +972,6 @@ rt_status rt_raytrace_backward(rt_ctx* ctx, const rt_grid* grid, const rt_opacit
     rt_status st = check_rt_args(ctx, grid, op, T, ev, nev, src, nsrc, cams, ncam, fidx, nfi);
     if (st != RT_OK) return st;
     if (!drho || !dscale) return fail(RT_ERR_INVALID_ARG, "rt_raytrace_backward: NULL output");
-    if (grid->refine) return fail(RT_ERR_INVALID_ARG, "rt_raytrace_backward: refined grids are not served");
     RT_CUDA(cudaSetDevice(ctx->device));
     return raytrace_impl(ctx, grid, op, T, ev, nev, nev_dev, xi_ev, src, nsrc, cams, ncam, fidx, nfi,
                          nullptr, nullptr, dimg, dsed, drho, dscale, (unsigned long long*)ray_steps, true,

@@ -369,7 +369,7 @@ __global__ void __launch_bounds__(128) ray_fwd_kernel(const __grid_constant__ Ra
 // pass 2 walks back to front from the far face, where the attenuation of the
 // observer-side optical depth is exp(-(tau_total - tau_behind_incl)) and the
 // sum of contributions farther than the current cell accumulates directly.
-template <int NS, int NFP>
+template <int NS, int NFP, bool REF>
 __global__ void __launch_bounds__(128) ray_bwd_kernel(const __grid_constant__ RayKP P)
 {
     const int ci = blockIdx.y;
@@ -395,19 +395,22 @@ __global__ void __launch_bounds__(128) ray_bwd_kernel(const __grid_constant__ Ra
     Ray r = pixel_ray(cm, ix, iy, P.nx, P.ny, P.nz, false);
     if (!r.hit) return;
     const float* eta_cam = P.eta + (size_t)cam * P.ncell * P.nfp;
-    const int maxstep = P.nx + P.ny + P.nz + 4;
+    const int maxstep = (P.nx + P.ny + P.nz) * (REF ? P.refine : 1) + 4;
     float tot[NFP], totc[NFP];
     unsigned nsteps = 0;
 #pragma unroll
     for (int f = 0; f < NFP; ++f) { tot[f] = 0.f; totc[f] = 0.f; }
     {
+        RefWalk<float> w1;
+        if (REF) rw_start(w1, P.cube, P.nx, P.ny, P.nz, P.refine, r.p, r.d, true);
         float tcur = 0.f, seg;
         for (int st = 0; st < maxstep; ++st) {
             ++nsteps;
-            const int c = (r.i[2] * P.ny + r.i[1]) * P.nx + r.i[0];
+            const int c = REF ? w1.c : (r.i[2] * P.ny + r.i[1]) * P.nx + r.i[0];
             float rho[NS];
             load_rho<NS>(P, c, rho);
-            const bool inside = dda_step(r, tcur, seg, P.nx, P.ny, P.nz);
+            const bool inside = REF ? rw_step(w1, P.cube, P.nx, P.ny, P.nz, P.refine, r.p, r.d, tcur, seg)
+                                    : dda_step(r, tcur, seg, P.nx, P.ny, P.nz);
 #pragma unroll
             for (int f = 0; f < NFP; ++f) {
                 float chi = 0.f;
@@ -424,13 +427,16 @@ __global__ void __launch_bounds__(128) ray_bwd_kernel(const __grid_constant__ Ra
 #pragma unroll
     for (int f = 0; f < NFP; ++f) { tb[f] = 0.f; tbc[f] = 0.f; beh[f] = 0.f; behc[f] = 0.f; }
     float tcur = 0.f, seg;
+    RefWalk<float> w2;
+    if (REF) rw_start(w2, P.cube, P.nx, P.ny, P.nz, P.refine, q.p, q.d, true);
     for (int st = 0; st < maxstep; ++st) {
         ++nsteps;
-        const int c = (q.i[2] * P.ny + q.i[1]) * P.nx + q.i[0];
+        const int c = REF ? w2.c : (q.i[2] * P.ny + q.i[1]) * P.nx + q.i[0];
         float rho[NS], eta[NFP];
         load_rho<NS>(P, c, rho);
         load_eta<NFP>(eta_cam + (size_t)c * NFP, eta);
-        const bool inside = dda_step(q, tcur, seg, P.nx, P.ny, P.nz);
+        const bool inside = REF ? rw_step(w2, P.cube, P.nx, P.ny, P.nz, P.refine, q.p, q.d, tcur, seg)
+                                : dda_step(q, tcur, seg, P.nx, P.ny, P.nz);
         float g[NS];
 #pragma unroll
         for (int s = 0; s < NS; ++s) g[s] = 0.f;
@@ -779,7 +785,8 @@ void launch_rays(const RayKP& kp, int npix, bool backward, cudaStream_t s)
     const int th = 128;
     const long long nthreads = (long long)npix * npix * (backward ? 1 : NFP / 4);
     dim3 grid((unsigned)((nthreads + th - 1) / th), kp.ncam);
-    if (backward) ray_bwd_kernel<NS, NFP><<<grid, th, 0, s>>>(kp);
+    if (backward && kp.refine) ray_bwd_kernel<NS, NFP, true><<<grid, th, 0, s>>>(kp);
+    else if (backward) ray_bwd_kernel<NS, NFP, false><<<grid, th, 0, s>>>(kp);
     else if (kp.refine) ray_fwd_kernel<NS, NFP, true><<<grid, th, 0, s>>>(kp);
     else ray_fwd_kernel<NS, NFP, false><<<grid, th, 0, s>>>(kp);
     count_launches();

@@ -448,12 +448,14 @@ def raytrace_backward(ctx: Context, grid: Grid, opac: Opacity, T: torch.Tensor, 
 
 class RayTrace(torch.autograd.Function):
     """Differentiable ray tracer: (rho, scale) -> (images, sed) with the
-    density scale * rho; temperatures and scattering events held fixed."""
+    density scale * rho; temperatures and scattering events held fixed.
+    Refined grids: pass ``refine`` and ``refined`` after ``freq_idx``."""
 
     @staticmethod
-    def forward(fctx, rho, scale, ctx, box_min, cell, opac, T, events, xi_ev, sources, cams, freq_idx):
+    def forward(fctx, rho, scale, ctx, box_min, cell, opac, T, events, xi_ev, sources, cams, freq_idx,
+                refine=0, refined=None):
         dens = (rho * scale).detach().contiguous()
-        grid = Grid(ctx, dens, box_min, cell)
+        grid = Grid(ctx, dens, box_min, cell, refine=refine, refined=refined)
         img, sed = raytrace(ctx, grid, opac, T, events, xi_ev, sources, cams, freq_idx)
         fctx.save_for_backward(rho, scale)
         fctx.stuff = (ctx, grid, opac, T, events, xi_ev, sources, cams, freq_idx)
@@ -467,7 +469,7 @@ class RayTrace(torch.autograd.Function):
                                                  freq_idx, g_img, g_sed)
         drho = (drho_eff.view_as(rho) * scale).to(rho.dtype)
         dscale = (dscale_eff / scale.to(torch.float64)).to(scale.dtype).reshape(scale.shape)
-        return drho, dscale, None, None, None, None, None, None, None, None, None, None
+        return drho, dscale, None, None, None, None, None, None, None, None, None, None, None, None
 
 
 def philox(ctx: Context, ctr0, key, n: int, stream=None) -> np.ndarray:

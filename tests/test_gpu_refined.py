@@ -11,6 +11,8 @@ oracle (run on a GB300).
 * Temperatures (sub-cube volumes), the initial guess, the PAH pass and the
   ray tracer (emissivity tables per sub-cube, two-level ray and starlight
   walks, scattering events in sub-cubes) against the oracle.
+* The ray-tracer adjoint on a refined grid against the oracle's FP64
+  adjoint, directly and through the autograd wrapper.
 * Entry points that do not serve refined grids refuse them.
 """
 import numpy as np
@@ -201,11 +203,94 @@ def test_refined_grid_refusals(rt, ctx):
     grid, opac, srcs = ctx.grid(m), ctx.opacity(m), rt.Sources(m.sources)
     with pytest.raises(rt.RtError):
         rt.Batch(ctx, opac, [m], [1000])
-    T = torch.full((1, m.ncell), 100.0, dtype=torch.float64, device="cuda")
-    cams = [W.Camera(0.5, 0.5, 8, 1e17)]
-    with pytest.raises(rt.RtError):
-        rt.raytrace_backward(ctx, grid, opac, T, None, 1.0, None, cams, [0],
-                             torch.ones((1, 1, 8, 8), device="cuda"),
-                             torch.zeros((1, 1), dtype=torch.float64, device="cuda"))
     with pytest.raises(ValueError):
         rt.sim.Grid(ctx, m.rho[:, :-1], m.box_min, m.cell, refine=2, refined=m.refined)
+
+
+def test_refined_degenerate_grids(rt, ctx, O):
+    """No cube divided: the refined grid is the uniform one (same cell
+    numbers, identical FP64 trajectories and energies).  Every cube divided
+    with the cube's density: identical paths, cube sums of the energies."""
+    m = W.random_grid(n=(5, 4, 3), ns=2, seed=12, tau_scale=2.0, albedo=(0.3, 0.8))
+    T0 = np.random.default_rng(1).uniform(40, 600, size=(m.ns, m.ncell))
+    opac, srcs = ctx.opacity(m), rt.Sources(m.sources)
+    kw = dict(mode=rt.rtgb.RT_MODE_FROZEN_T, lucy_mode=rt.rtgb.RT_LUCY_ALL,
+              precision=rt.rtgb.RT_PREC_FP64, traj_cap=400 * 400, seed=3)
+    base = rt.transport(ctx, ctx.grid(m), opac, srcs, 400, T_prev=torch.tensor(T0, device="cuda"), **kw)
+    none = W.refine_cubes(m, np.zeros(m.shape, bool), r=2)
+    a = rt.transport(ctx, ctx.grid(none), opac, srcs, 400, T_prev=torch.tensor(T0, device="cuda"), **kw)
+    allm = W.refine_cubes(m, np.ones(m.shape, bool), r=2)
+    b = rt.transport(ctx, ctx.grid(allm), opac, srcs, 400,
+                     T_prev=torch.tensor(np.repeat(T0, 8, axis=1), device="cuda"), **kw)
+    torch.cuda.synchronize()
+    t0 = np.sort(base.traj_numpy(), order=["pid", "seq"])
+    ta = np.sort(a.traj_numpy(), order=["pid", "seq"])
+    tb = np.sort(b.traj_numpy(), order=["pid", "seq"])
+    for f in ("pid", "seq", "type", "cell", "nu"):
+        np.testing.assert_array_equal(ta[f], t0[f])
+    np.testing.assert_allclose(ta["x"], t0["x"], rtol=0, atol=1e-12 * m.cell * 5)
+    np.testing.assert_allclose(a.E_abs.cpu().numpy(), base.E_abs.cpu().numpy(), rtol=1e-12)
+    for f in ("pid", "seq", "type", "nu"):
+        np.testing.assert_array_equal(tb[f], t0[f])
+    np.testing.assert_allclose(tb["x"], t0["x"], rtol=0, atol=1e-9 * m.cell * 5)
+    Eb = b.E_abs.cpu().numpy().reshape(m.ns, m.ncell, 8).sum(axis=2)
+    E0 = base.E_abs.cpu().numpy()
+    np.testing.assert_allclose(Eb, E0, rtol=1e-9, atol=1e-12 * E0.max())
+
+
+def test_largest_refinement_factor(rt, ctx, O):
+    """r = 16 (the largest factor): 4096 sub-cubes per divided cube."""
+    m0 = W.uniform_cube(n=3, tau_cell=0.4, nf=8, albedo=0.5)
+    mask = np.zeros(m0.shape, bool)
+    mask[1, 1, 1] = mask[0, 2, 1] = True
+    m = W.refine_cubes(m0, mask, r=16, jitter=0.4, seed=2)
+    assert m.ncell == 25 + 2 * 4096
+    grid, opac, srcs = ctx.grid(m), ctx.opacity(m), rt.Sources(m.sources)
+    T0 = np.full((1, m.ncell), 200.0)
+    out = rt.transport(ctx, grid, opac, srcs, 300, mode=rt.rtgb.RT_MODE_FROZEN_T,
+                       precision=rt.rtgb.RT_PREC_FP64, T_prev=torch.tensor(T0, device="cuda"),
+                       traj_cap=300 * 400, seed=8)
+    torch.cuda.synchronize()
+    ref = O.transport(m, 300, seed=8, mode=O.MODE_FROZEN_T, T_prev=T0, traj_cap=300 * 400)
+    _traj_compare(out.traj_numpy(), ref["traj"], m.cell * 3)
+    o32 = rt.transport(ctx, grid, opac, srcs, 100_000, seed=9)
+    torch.cuda.synchronize()
+    assert o32.stats_dict()["escaped"] == 100_000
+    assert o32.sed_esc.sum().item() == pytest.approx(m.luminosity, rel=1e-9)
+
+
+def test_refined_raytrace_adjoint_matches_oracle(rt, ctx, O):
+    m = _refined(ns=2, r=2, seed=14, n=(6, 5, 4), tau_scale=1.2)
+    grid, opac, srcs = ctx.grid(m), ctx.opacity(m), rt.Sources(m.sources)
+    rng = np.random.default_rng(2)
+    T = rng.uniform(50, 900, size=(m.ns, m.ncell))
+    fidx = [2, 6]
+    ev = np.zeros(600, dtype=[("cell", "<u4"), ("nu", "<u4"), ("species", "<u4"), ("pad", "<u4"),
+                              ("k", "<f8", (3,))])
+    ev["cell"] = rng.integers(0, m.ncell, len(ev))
+    ev["nu"] = rng.choice(fidx, len(ev))
+    ev["species"] = rng.integers(0, m.ns, len(ev))
+    k = rng.normal(size=(len(ev), 3))
+    ev["k"] = (k / np.linalg.norm(k, axis=1, keepdims=True)).astype(np.float32)
+    cams = [W.Camera(0.6, 0.2, 12, 3e16), W.Camera(2.1, -1.3, 12, 3e16)]
+    wi = rng.normal(size=(2, 2, 12, 12))
+    ws = rng.normal(size=(2, 2)) * 1e32
+    xi = 1e28
+    Tt = torch.tensor(T, device="cuda")
+    drho, dscale = rt.raytrace_backward(ctx, grid, opac, Tt, ev, xi, srcs, cams, fidx,
+                                        torch.tensor(wi, device="cuda"), torch.tensor(ws, device="cuda"))
+    torch.cuda.synchronize()
+    gr, gsr = O.raytrace_backward(m, T, ev, xi, cams, fidx, wi, ws)
+    g = drho.cpu().numpy().astype(np.float64)
+    scale = np.abs(gr).max()
+    assert np.all(np.abs(g - gr) <= 1e-2 * np.abs(gr) + 1e-4 * scale)
+    assert dscale.item() == pytest.approx(gsr, rel=1e-3)
+    rho = torch.tensor(m.rho, device="cuda", requires_grad=True)
+    sc = torch.tensor(1.0, dtype=torch.float64, device="cuda", requires_grad=True)
+    img, sed = rt.RayTrace.apply(rho, sc, ctx, m.box_min, m.cell, opac, Tt, ev, xi, srcs, cams, fidx,
+                                 m.refine, m.refined)
+    L = (img * torch.tensor(wi, device="cuda", dtype=torch.float32)).sum() + \
+        (sed * torch.tensor(ws, device="cuda")).sum()
+    L.backward()
+    ga = rho.grad.cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(ga - gr) <= 1e-2 * np.abs(gr) + 1e-4 * scale)

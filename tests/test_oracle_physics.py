@@ -687,3 +687,46 @@ def test_pah_reemission_rejects_bad_inputs(O):
     rec["cell"][0] = 0
     with pytest.raises(ValueError):
         O.pah_reemit(m, rec, 1.0, eps, np.full(m.ncell, 1))            # class out of range
+
+
+def test_refined_adjoint_matches_central_differences(O):
+    """The adjoint on a grid with one level of refinement, against central
+    differences of the forward ray tracer, for cells in divided cubes
+    (sub-cubes) and undivided ones."""
+    m0 = W.random_grid(n=(4, 3, 3), ns=1, nf=6, seed=5, tau_scale=1.5, albedo=(0.2, 0.6))
+    mask = np.zeros(m0.rho.shape[1:], bool)
+    mask[1, 1, 1] = mask[2, 0, 2] = mask[0, 2, 0] = True
+    m = W.refine_cubes(m0, mask, r=2, jitter=0.5, seed=3)
+    rng = np.random.default_rng(4)
+    T = rng.uniform(50, 900, size=(1, m.ncell))
+    ev = np.zeros(30, dtype=O.EVENT_DTYPE)
+    ev["cell"] = rng.integers(0, m.ncell, 30)
+    ev["nu"] = rng.choice([1, 4], 30)
+    kk = rng.normal(size=(30, 3))
+    ev["k"] = kk / np.linalg.norm(kk, axis=1, keepdims=True)
+    cams = [W.Camera(0.7, 0.3, 6, 3e16), W.Camera(2.0, -1.1, 6, 3e16)]
+    fidx = [1, 4]
+    wi = rng.normal(size=(2, 2, 6, 6))
+    ws = rng.normal(size=(2, 2)) * 1e32
+    xi = 1e28
+    g, gs = O.raytrace_backward(m, T, ev, xi, cams, fidx, wi, ws)
+    base = m.rho.copy()
+    fine = np.nonzero(np.repeat(mask.reshape(-1), np.where(mask.reshape(-1), 8, 1)))[0]
+    picks = [int(fine[0]), int(fine[5]), int(fine[13]), int(fine[22]), 0, m.ncell - 1]
+    tested = 0
+    for c in picks:
+        if base[0, c] == 0 or g[0, c] == 0:
+            continue
+        rp, rm = base.copy(), base.copy()
+        rp[0, c] = np.float32(base[0, c] * (1 + 1e-3))
+        rm[0, c] = np.float32(base[0, c] * (1 - 1e-3))
+        m.rho = rp
+        Lp = _loss(O, m, T, ev, xi, cams, fidx, wi, ws)
+        m.rho = rm
+        Lm = _loss(O, m, T, ev, xi, cams, fidx, wi, ws)
+        m.rho = base
+        fd = (Lp - Lm) / (float(rp[0, c]) - float(rm[0, c]))
+        assert g[0, c] == pytest.approx(fd, rel=2e-5, abs=1e-9 * np.abs(g).max())
+        tested += 1
+    assert tested >= 3
+    assert gs == pytest.approx(float((base.astype(np.float64) * g).sum()), rel=1e-12)
