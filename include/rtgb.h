@@ -89,10 +89,8 @@ RT_API rt_status rt_grid_upload(rt_ctx* ctx, int nx, int ny, int nz, int n_speci
  * device, ncell = (cubes not divided) + r^3 (cubes divided) < 2^30.
  * Every per-cell array of the other calls (E_abs, count, esq, T, the cell of
  * events and PAH records) is indexed by this cell number.  Served by
- * rt_transport, rt_pah_reemit, rt_temperatures, rt_temperature_guess,
- * rt_raytrace and rt_raytrace_backward; the batched and no-alloc transports
- * refuse refined grids (RT_ERR_INVALID_ARG).  Errors as rt_grid_upload,
- * plus a bad refine factor. */
+ * every call that takes a grid (a batch may mix refined and uniform
+ * grids).  Errors as rt_grid_upload, plus a bad refine factor. */
 RT_API rt_status rt_grid_upload_refined(rt_ctx* ctx, int nx, int ny, int nz, int n_species,
                                         const double box_min[3], double cell_size, int refine,
                                         const unsigned char* refined, const float* rho,
@@ -449,7 +447,8 @@ typedef struct {
 /* Prepare a batch: packs every grid, uploads the model table and source
  * tables (host-synchronous).  The batch keeps pointers to the grids and the
  * output buffers; they must outlive it.  n_models in 1..4096; all grids share
- * `opac` and must have its species count; p->n_pc_cams must be 0. */
+ * `opac` and must have its species count (grids may be refined);
+ * p->n_pc_cams must be 0. */
 RT_API rt_status rt_batch_create(rt_ctx* ctx, const rt_opacity* opac, int n_models,
                           const rt_model* models, const rt_transport_params* p,
                           rt_batch** out);

@@ -778,8 +778,6 @@ rt_status rt_batch_create(rt_ctx* ctx, const rt_opacity* op, int n_models, const
         const rt_model& M = models[m];
         if (!M.grid || M.grid->ctx != ctx || M.grid->ns != op->ns)
             return fail(RT_ERR_INVALID_ARG, "rt_batch_create: grid missing, foreign or with other species");
-        if (M.grid->refine)
-            return fail(RT_ERR_INVALID_ARG, "rt_batch_create: refined grids are served by rt_transport only");
         if (M.n_packets == 0) return fail(RT_ERR_INVALID_ARG, "rt_batch_create: n_packets must be > 0");
         if (p->mode == RT_MODE_FROZEN_T && !M.T_prev)
             return fail(RT_ERR_INVALID_ARG, "rt_batch_create: frozen-T mode needs T_prev for every model");
@@ -822,6 +820,8 @@ rt_status rt_batch_create(rt_ctx* ctx, const rt_opacity* op, int n_models, const
     st = stage_models(hms, nwork, op->nf, false, 0, b->dm);
     if (st != RT_OK) { cudaFree(b->acc); delete b; return st; }
     fill_kp(b->kp, op, p, b->dm, n_models);
+    for (int m = 0; m < n_models; ++m)
+        if (models[m].grid->refine) b->kp.refined = 1;   // the two-level traversal for every model
     for (int m = 0; m < n_models; ++m)
         if (models[m].out.traj && models[m].out.traj_cap) b->kp.want_traj = 1;
     if (n_models <= kParamModels) {
@@ -1073,8 +1073,6 @@ rt_status rt_transport_noalloc(rt_ctx* ctx, const rt_grid* grid, const rt_opacit
         return fail(RT_ERR_INVALID_ARG, "rt_transport_noalloc: need pid_begin <= pid_end <= n_packets");
     if (p->n_pc_cams != 0)
         return fail(RT_ERR_INVALID_ARG, "rt_transport_noalloc: photon-counting cameras are served by rt_transport only");
-    if (grid->refine)
-        return fail(RT_ERR_INVALID_ARG, "rt_transport_noalloc: refined grids are served by rt_transport only");
     if (p->mode == RT_MODE_FROZEN_T && !T_prev)
         return fail(RT_ERR_INVALID_ARG, "rt_transport_noalloc: frozen-T mode needs T_prev");
     // scratch layout: staging | kext | packed density | FP64 energy scratch
@@ -1114,6 +1112,7 @@ rt_status rt_transport_noalloc(rt_ctx* ctx, const rt_grid* grid, const rt_opacit
     RT_CUDA(cudaMemsetAsync(dm.work, 0, sizeof(unsigned long long), s));
     TransportKP kp;
     fill_kp(kp, op, p, dm, 1);
+    kp.refined = grid->refine ? 1 : 0;
     st = single_model_options(kp, op, p, out, n_sources, hms[0].md);
     if (st != RT_OK) return st;
     const int threads = p->threads_per_block ? p->threads_per_block : 256;

@@ -542,11 +542,12 @@ struct Kernel {
         id[0] = rr - id[1] * md->nx;
     }
 
-    // cube and sub-cube of cell c
+    // cube and sub-cube of cell c (a uniform grid of a batch that holds
+    // refined grids has no tables: its cells are its cubes)
     __device__ __forceinline__ void set_from_cell(Lane<R, NS>& L, int c) const
     {
-        const int q = md->leaf_cube[c];
-        const int info = md->cube[q];
+        const int q = md->refine ? md->leaf_cube[c] : c;
+        const int info = md->refine ? md->cube[q] : q;
         L.cc = q;
         if (info & kCubeDivided) {
             const int r = md->refine;
@@ -565,7 +566,7 @@ struct Kernel {
     __device__ __forceinline__ void enter_cube(Lane<R, NS>& L, int q, const int* id, const R* xc,
                                                int ea) const
     {
-        const int info = md->cube[q];
+        const int info = md->refine ? md->cube[q] : q;
         L.cc = q;
         if (!(info & kCubeDivided)) {
             L.sub = -1;

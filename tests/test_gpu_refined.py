@@ -13,7 +13,8 @@ oracle (run on a GB300).
   walks, scattering events in sub-cubes) against the oracle.
 * The ray-tracer adjoint on a refined grid against the oracle's FP64
   adjoint, directly and through the autograd wrapper.
-* Entry points that do not serve refined grids refuse them.
+* The batched launch (refined and uniform grids mixed) and the no-alloc
+  entry serve refined grids; bad refinement factors are refused.
 """
 import numpy as np
 import pytest
@@ -198,13 +199,14 @@ def test_fp64_pah_pass_on_refined_grid(rt, ctx, O):
                                atol=1e-9 * ref["E_abs"].max())
 
 
-def test_refined_grid_refusals(rt, ctx):
+def test_refined_grid_bad_inputs(rt, ctx):
     m = _refined(ns=1, r=2, seed=30)
-    grid, opac, srcs = ctx.grid(m), ctx.opacity(m), rt.Sources(m.sources)
-    with pytest.raises(rt.RtError):
-        rt.Batch(ctx, opac, [m], [1000])
     with pytest.raises(ValueError):
         rt.sim.Grid(ctx, m.rho[:, :-1], m.box_min, m.cell, refine=2, refined=m.refined)
+    with pytest.raises(rt.RtError):
+        rt.sim.Grid(ctx, m.rho, m.box_min, m.cell, refine=17, refined=m.refined)
+    with pytest.raises(rt.RtError):
+        rt.sim.Grid(ctx, m.rho, m.box_min, m.cell, refine=1, refined=m.refined)
 
 
 def test_refined_degenerate_grids(rt, ctx, O):
@@ -294,3 +296,32 @@ def test_refined_raytrace_adjoint_matches_oracle(rt, ctx, O):
     L.backward()
     ga = rho.grad.cpu().numpy().astype(np.float64)
     assert np.all(np.abs(ga - gr) <= 1e-2 * np.abs(gr) + 1e-4 * scale)
+
+
+def test_refined_and_uniform_grids_in_one_batch(rt, ctx, O):
+    """A batch mixing refined and uniform grids: every model's FP64
+    frozen-T run equals the oracle's (Philox model id = base + index)."""
+    def torus(n, k, s):
+        return W.clumpy_torus(n=n, n_clump=k, seed=s, nf=24, with_pah=False)
+    m1 = torus(8, 20, 1)
+    c = np.arange(8) + 0.5 - 4
+    Z, Y, X = np.meshgrid(c, c, c, indexing="ij")
+    m1 = W.refine_cubes(m1, np.sqrt(X * X + Y * Y + Z * Z) < 3, r=2, jitter=0.3, seed=1)
+    m2 = torus(12, 35, 3)
+    m3 = W.refine_cubes(torus(10, 30, 2), np.random.default_rng(3).random((10, 10, 10)) < 0.3, r=3,
+                        jitter=0.3, seed=2)
+    models = [m1, m2, m3]
+    opac = ctx.opacity(m2)
+    N = [150, 200, 150]
+    T0 = [torch.full((2, m.ncell), 250.0, dtype=torch.float64, device="cuda") for m in models]
+    b = rt.Batch(ctx, opac, models, N, T_prev=T0, mode=rt.rtgb.RT_MODE_FROZEN_T,
+                 precision=rt.rtgb.RT_PREC_FP64, seed=9, model_id=100)
+    b.run()
+    torch.cuda.synchronize()
+    for i, m in enumerate(models):
+        ref = O.transport(m, N[i], seed=9, model_id=100 + i, mode=O.MODE_FROZEN_T,
+                          T_prev=T0[i].cpu().numpy(), n_threads=4)
+        g = b.outs[i].numpy()
+        np.testing.assert_array_equal(g["count"], ref["count"])
+        np.testing.assert_allclose(g["E_abs"], ref["E_abs"], rtol=1e-9, atol=1e-12 * ref["E_abs"].max())
+        assert g["stats"]["crossings"] == ref["stats"]["crossings"]

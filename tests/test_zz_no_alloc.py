@@ -70,3 +70,24 @@ def test_noalloc_matches_rt_transport_twice():
 def W_guess(m):
     # constant temperatures are enough for frozen-T transport
     return np.full((m.ns, m.ncell), 120.0)
+
+
+def test_noalloc_on_refined_grid():
+    """The allocation-free entry serves refined grids too (the cube tables
+    belong to the grid)."""
+    import __graft_entry__ as g
+    g.build()
+    import paper_1203_2941_gb300 as rt
+    from paper_1203_2941_gb300 import rtgb as R
+    lib = R.load()
+    ctx = rt.Context(0)
+    m = W.r2_shell_refined(n=16, tau_1um=10.0, nf=16, r=2, refine_radius=3.0)
+    grid, opac, srcs = ctx.grid(m), ctx.opacity(m), rt.Sources(m.sources)
+    T0 = torch.tensor(W_guess(m), device="cuda")
+    N = 20000
+    ref = _run(rt, lib.rt_transport, ctx, grid, opac, srcs, N, T0, seed=6)
+    got = _run(rt, lib.rt_transport_noalloc, ctx, grid, opac, srcs, N, T0, seed=6)
+    for k in ("crossings", "interactions", "absorptions", "escaped", "lucy_deposits"):
+        assert got["stats"][k] == ref["stats"][k], k
+    np.testing.assert_array_equal(got["count"], ref["count"])
+    np.testing.assert_allclose(got["E_abs"], ref["E_abs"], rtol=1e-9, atol=1e-12 * ref["E_abs"].max())
