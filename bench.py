@@ -436,7 +436,8 @@ def run_forms(a):
         if a.forms != "all" and name not in a.forms.split(","):
             continue
         t0 = time.perf_counter()
-        forms[name] = fn(rt, ctx, flush)
+        kw = {"packets": a.packets} if name in ("mrw_disk", "refined_shell") else {}
+        forms[name] = fn(rt, ctx, flush, **kw)
         forms[name]["wall_s"] = time.perf_counter() - t0
         print(json.dumps({"form": name, **forms[name]}), flush=True)
     return forms

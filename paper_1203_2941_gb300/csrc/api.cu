@@ -409,6 +409,7 @@ static rt_status make_model(const rt_grid* g, const rt_opacity* op, const rt_sou
     m.nx = g->nx; m.ny = g->ny; m.nz = g->nz;
     m.ncell = (int)g->ncell();
     m.refine = g->refine;
+    m.inv_refine = g->refine ? 1.0 / g->refine : 1.0;
     m.cube = g->d_cube;
     m.leaf_cube = g->d_leaf_cube;
     m.model_id = model_id;

@@ -182,12 +182,13 @@ struct RefWalk {
     int i[3];
     int sub, c;
     T tm[3], td[3];
+    T ir;                      // 1 / r
 };
 
 template <typename T>
 __device__ __forceinline__ void rw_times(RefWalk<T>& w, int r, const T* p, const T* d, T tcur)
 {
-    const T h = w.sub >= 0 ? T(1) / T(r) : T(1);
+    const T h = w.sub >= 0 ? w.ir : T(1);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         const T lo = T(w.i[a]) + (w.sub >= 0 ? T((w.sub >> (8 * a)) & 255) * h : T(0));
@@ -235,6 +236,7 @@ __device__ __forceinline__ bool rw_start(RefWalk<T>& w, const int* cube, int nx,
 {
     const int n[3] = { nx, ny, nz };
     bool in = true;
+    w.ir = T(1) / T(r);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         const T f = floor(p[a]);
@@ -266,9 +268,9 @@ __device__ __forceinline__ bool rw_step(RefWalk<T>& w, const int* cube, int nx, 
         if (sa >= 0 && sa < r) {
             w.sub = (w.sub & ~(255 << (8 * a))) | (sa << (8 * a));
             w.c += sg * (a == 0 ? 1 : (a == 1 ? r : r * r));
-            if (a == 0) w.tm[0] += w.td[0] / T(r);
-            else if (a == 1) w.tm[1] += w.td[1] / T(r);
-            else w.tm[2] += w.td[2] / T(r);
+            if (a == 0) w.tm[0] += w.td[0] * w.ir;
+            else if (a == 1) w.tm[1] += w.td[1] * w.ir;
+            else w.tm[2] += w.td[2] * w.ir;
             return true;
         }
     }

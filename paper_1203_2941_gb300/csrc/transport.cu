@@ -273,6 +273,7 @@ struct Lane {
     uint32_t ncross, nlucy;    // crossings and Lucy deposits of the current packet
     int cc, sub;               // refined grids: cube of the cell; sub-cube indices
                                // (8 bits per axis) or -1 for an undivided cube
+                               // (rem then holds the cube's indices)
 };
 
 // a[s] for a register array and a run-time index, without local memory
@@ -549,6 +550,7 @@ struct Kernel {
         const int q = md->refine ? md->leaf_cube[c] : c;
         const int info = md->refine ? md->cube[q] : q;
         L.cc = q;
+        cube_idx(q, L.rem);
         if (info & kCubeDivided) {
             const int r = md->refine;
             const int off = c - (info & ~kCubeDivided);
@@ -568,6 +570,8 @@ struct Kernel {
     {
         const int info = md->refine ? md->cube[q] : q;
         L.cc = q;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) L.rem[a] = id[a];
         if (!(info & kCubeDivided)) {
             L.sub = -1;
             L.c = info;
@@ -592,16 +596,14 @@ struct Kernel {
     // lower corner (cube units) and edge of the lane's cell
     __device__ __forceinline__ R cell_box(const Lane<R, NS>& L, R* lo) const
     {
-        int id[3];
-        cube_idx(L.cc, id);
         if (L.sub < 0) {
 #pragma unroll
-            for (int a = 0; a < 3; ++a) lo[a] = (R)id[a];
+            for (int a = 0; a < 3; ++a) lo[a] = (R)L.rem[a];
             return R(1);
         }
-        const R h = R(1) / (R)md->refine;
+        const R h = (R)md->inv_refine;
 #pragma unroll
-        for (int a = 0; a < 3; ++a) lo[a] = (R)id[a] + (R)((L.sub >> (8 * a)) & 255) * h;
+        for (int a = 0; a < 3; ++a) lo[a] = (R)L.rem[a] + (R)((L.sub >> (8 * a)) & 255) * h;
         return h;
     }
 
@@ -636,15 +638,16 @@ struct Kernel {
                 L.sub = (L.sub & ~(255 << (8 * a))) | (sa << (8 * a));
                 L.c += sg * (a == 0 ? 1 : (a == 1 ? r : r * r));
                 // (branches, not a run-time index: the lane state stays in registers)
-                if (a == 0) L.tm[0] += L.td[0] / (R)r;
-                else if (a == 1) L.tm[1] += L.td[1] / (R)r;
-                else L.tm[2] += L.td[2] / (R)r;
+                // face spacing of a sub-cube: td / r (a product: no division per step)
+                const R ir = (R)md->inv_refine;
+                if (a == 0) L.tm[0] += L.td[0] * ir;
+                else if (a == 1) L.tm[1] += L.td[1] * ir;
+                else L.tm[2] += L.td[2] * ir;
                 load_cell(L);
                 return;
             }
         }
-        int id[3];
-        cube_idx(L.cc, id);
+        int id[3] = { L.rem[0], L.rem[1], L.rem[2] };
         id[0] += a == 0 ? sg : 0;
         id[1] += a == 1 ? sg : 0;
         id[2] += a == 2 ? sg : 0;
@@ -657,8 +660,15 @@ struct Kernel {
         R xc[3];
 #pragma unroll
         for (int b = 0; b < 3; ++b) xc[b] = L.x[b] + L.tcur * L.k[b];
-        enter_cube(L, (id[2] * md->ny + id[1]) * md->nx + id[0], id, xc, a);
-        face_times(L);
+        const bool was_fine = L.sub >= 0;
+        enter_cube(L, L.cc + sg * (a == 0 ? 1 : (a == 1 ? md->nx : md->nx * md->ny)), id, xc, a);
+        if (was_fine || L.sub >= 0) {
+            face_times(L);             // the face spacing changed: restart from the point
+        } else {
+            if (a == 0) L.tm[0] += L.td[0];
+            else if (a == 1) L.tm[1] += L.td[1];
+            else L.tm[2] += L.td[2];
+        }
         load_cell(L);
     }
 
