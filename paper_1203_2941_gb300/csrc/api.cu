@@ -410,6 +410,7 @@ static rt_status make_model(const rt_grid* g, const rt_opacity* op, const rt_sou
     m.ncell = (int)g->ncell();
     m.refine = g->refine;
     m.inv_refine = g->refine ? 1.0 / g->refine : 1.0;
+    m.inv_refine32 = (float)m.inv_refine;
     m.cube = g->d_cube;
     m.leaf_cube = g->d_leaf_cube;
     m.model_id = model_id;

@@ -129,6 +129,7 @@ struct ModelDev {
     const int* leaf_cube;      // refined grids: [ncell] cube of each cell
     int refine;                // r, or 0
     double inv_refine;         // 1 / r (exact for the power-of-two factors)
+    float inv_refine32;        // the same in FP32 (no FP64 conversion in the FP32 walk)
     double* accE;              // FP32 build: this call's deposits in units of xi; with
     int acc_q;                 // acc_q = 1 each cell holds {sum, sum of squares} (xi, xi^2)
     double* sed_esc; unsigned long long* sed_cnt;

@@ -533,6 +533,13 @@ struct Kernel {
     // one another in z, y, x order.  Positions and path lengths stay in cube
     // edges; a sub-cube's edge is 1/r.
 
+    // 1 / r in the build's precision
+    __device__ __forceinline__ R inv_r() const
+    {
+        if constexpr (DBG) return md->inv_refine;
+        else return md->inv_refine32;
+    }
+
     // cube indices of cube number q
     __device__ __forceinline__ void cube_idx(int q, int* id) const
     {
@@ -601,7 +608,7 @@ struct Kernel {
             for (int a = 0; a < 3; ++a) lo[a] = (R)L.rem[a];
             return R(1);
         }
-        const R h = (R)md->inv_refine;
+        const R h = inv_r();
 #pragma unroll
         for (int a = 0; a < 3; ++a) lo[a] = (R)L.rem[a] + (R)((L.sub >> (8 * a)) & 255) * h;
         return h;
@@ -639,7 +646,7 @@ struct Kernel {
                 L.c += sg * (a == 0 ? 1 : (a == 1 ? r : r * r));
                 // (branches, not a run-time index: the lane state stays in registers)
                 // face spacing of a sub-cube: td / r (a product: no division per step)
-                const R ir = (R)md->inv_refine;
+                const R ir = inv_r();
                 if (a == 0) L.tm[0] += L.td[0] * ir;
                 else if (a == 1) L.tm[1] += L.td[1] * ir;
                 else L.tm[2] += L.td[2] * ir;
