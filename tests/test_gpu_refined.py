@@ -325,3 +325,31 @@ def test_refined_and_uniform_grids_in_one_batch(rt, ctx, O):
         np.testing.assert_array_equal(g["count"], ref["count"])
         np.testing.assert_allclose(g["E_abs"], ref["E_abs"], rtol=1e-9, atol=1e-12 * ref["E_abs"].max())
         assert g["stats"]["crossings"] == ref["stats"]["crossings"]
+
+
+def test_refined_shell_at_bench_size(rt, ctx, O):
+    """The refined-shell bench workload at its full size (64^3 cubes, 912
+    divided into 4^3, 1e7 packets, the bench's launch configuration):
+    exact conservation and counts, and FP64 trajectories of 300 packet ids
+    of the same emission against the oracle on the full refined grid."""
+    m = W.r2_shell_refined(n=64, tau_1um=10.0, nf=64, r=4, refine_radius=6.0)
+    grid, opac, srcs = ctx.grid(m), ctx.opacity(m), rt.Sources(m.sources)
+    N = 10 ** 7
+    out = rt.transport(ctx, grid, opac, srcs, N, event_cap=6 * N, record_events=True, seed=5)
+    torch.cuda.synchronize()
+    st = out.stats_dict()
+    assert st["emitted"] == N and st["escaped"] == N and st["stuck"] == 0
+    assert abs(out.sed_esc.sum().item() / m.luminosity - 1) < 1e-9
+    assert int(out.count.sum().item()) == st["absorptions"]
+    assert st["n_events"] == st["scatters"] and st["events_dropped"] == 0
+    T0 = O.temperature_guess(m)
+    b, e = 5_000_000, 5_000_300
+    g = rt.transport(ctx, grid, opac, srcs, N, mode=rt.rtgb.RT_MODE_FROZEN_T,
+                     precision=rt.rtgb.RT_PREC_FP64, T_prev=torch.tensor(T0, device="cuda"),
+                     pid_begin=b, pid_end=e, traj_cap=400000, seed=5)
+    torch.cuda.synchronize()
+    ref = O.transport(m, N, seed=5, mode=O.MODE_FROZEN_T, T_prev=T0, pid_begin=b, pid_end=e,
+                      traj_cap=400000, n_threads=4)
+    _traj_compare(g.traj_numpy(), ref["traj"], m.cell * 64)
+    for k in ("crossings", "interactions", "absorptions", "escaped", "lucy_deposits"):
+        assert g.stats_dict()[k] == ref["stats"][k], k
