@@ -103,8 +103,15 @@ def test_full_size_images_of_one_camera(rt, setup, O):
     torch.cuda.synchronize()
     ev = out.events_numpy()
     ir, sr = O.raytrace(m, T.cpu().numpy(), ev, out.xi, cam, fidx)
+    # FP32 rays through 128 cells per axis: a face time of order 200 cell
+    # edges carries an absolute error of about one FP32 ulp there (1.5e-5
+    # edges), so the optical depth in front of a cell, and its attenuation,
+    # carry relative errors of order 1e-5 on the thick lines of sight (one
+    # run of this test, with a 1e-5 bound, failed on one frequency)
     a = img.cpu().numpy().astype(np.float64)
     for f in range(len(fidx)):
         mx = np.abs(ir[0, f]).max()
-        assert np.all(np.abs(a[0, f] - ir[0, f]) <= 1e-5 * mx + 1e-37), f
+        err = np.abs(a[0, f] - ir[0, f])
+        worst = np.unravel_index(np.argmax(err), err.shape)
+        assert np.all(err <= 3e-5 * mx + 1e-37), (f, err.max() / mx, worst, a[0, f][worst], ir[0, f][worst])
     np.testing.assert_allclose(sed.cpu().numpy(), sr, rtol=1e-5)
