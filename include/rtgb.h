@@ -138,8 +138,8 @@ enum { RT_PREC_FP32 = 0,      /* production: FP32 transport, FP64 accumulators *
 enum { RT_SCHED_PERSISTENT = 0, /* all SMs, dynamic packet refill */
        RT_SCHED_SERIAL = 1 };   /* one GPU thread, packets in id order (debug) */
 
-/* A photon-counting camera (Sect. 4: photons escaping into a solid angle
- * are counted and converted into a flux): packets that leave the grid with
+/* A photon-counting camera (the Monte Carlo image of Sect. 4, which the
+ * paper sets against its ray tracer): packets that leave the grid with
  * k . k_obs >= cos_accept add their power xi to the pixel of their exit
  * point projected on the image plane.  Frame as in rt_raytrace: k_obs from
  * (theta, phi), image axes e_x' = (-sin phi, cos phi, 0), e_y' = (-cos theta
