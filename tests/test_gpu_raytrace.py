@@ -242,3 +242,18 @@ def test_batch_matches_single_model_runs(rt, ctx, O):
         g = b32.outs[i].numpy()
         assert g["stats"]["emitted"] == 2 * [4000, 8000, 6000][i]
         assert abs(g["sed_esc"].sum() / (2 * m.luminosity) - 1) < 1e-9
+
+
+def test_visibilities_ragged_image_and_single_uv(rt, ctx, O):
+    """An odd image size (7 x 7 pixels, explicit pixel size) and a single
+    (u, v) point, against the oracle's sum."""
+    m = W.random_grid(n=(5, 4, 6), ns=2, nf=8, seed=8, tau_scale=1.0)
+    grid, opac = ctx.grid(m), ctx.opacity(m)
+    T = torch.tensor(np.random.default_rng(1).uniform(40, 800, size=(m.ns, m.ncell)), device="cuda")
+    cams = [W.Camera(1.1, -0.6, 7, 2e17, 0.9 * m.cell)]
+    img, sed = rt.raytrace(ctx, grid, opac, T, None, 0.0, None, cams, [3])
+    uv = np.array([[1.3e3, -2.2e3]])
+    V = rt.visibilities(ctx, grid, cams, img, uv).cpu().numpy()
+    Vr = O.visibilities(m, img.cpu().numpy(), cams, uv)
+    assert V.shape == (1, 1, 1)
+    assert abs(V[0, 0, 0] - Vr[0, 0, 0]) <= 1e-6 * np.abs(img.cpu().numpy()).sum() * (0.9 * m.cell / 2e17) ** 2

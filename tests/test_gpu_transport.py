@@ -482,3 +482,32 @@ def test_pah_reemission_bad_inputs(rt, ctx):
     torch.cuda.synchronize()
     st = out.stats_dict()
     assert st["emitted"] == 8 and st["stuck"] == 2 + 5 and st["escaped"] + st["absorptions"] >= 1
+
+
+def test_photon_counting_edge_cases(rt, ctx):
+    """Acceptance cosine 1 counts nothing (no direction is exactly k_obs in
+    practice); one all-sky pixel holds every escaped packet."""
+    m = W.uniform_cube(n=5, tau_cell=0.3, albedo=0.5)
+    grid, opac, srcs = _setup(rt, ctx, m)
+    cams = [rt.PcCamera(0.3, 0.1, 4, 1.0), rt.PcCamera(0.0, 0.0, 1, -1.0)]
+    out = rt.transport(ctx, grid, opac, srcs, 50_000, pc_cams=cams, seed=4)
+    torch.cuda.synchronize()
+    none, one = [g.cpu().numpy() for g in out.pc_images()]
+    assert none.sum() == 0.0
+    assert one.shape == (m.nf, 1, 1)
+    assert one.sum() == pytest.approx(m.luminosity, rel=1e-9)
+
+
+def test_pah_reemission_without_records(rt, ctx):
+    """No stored records: the wrapper launches nothing, the C entry refuses
+    an empty pass."""
+    m = W.uniform_cube(n=3, tau_cell=0.1)
+    grid, opac, _ = _setup(rt, ctx, m)
+    out = rt.pah_reemit(ctx, grid, opac, np.zeros(0, rt.rtgb.PAH_DTYPE), 1.0, np.ones((1, m.nf)))
+    torch.cuda.synchronize()
+    assert out.stats_dict()["emitted"] == 0 and out.E_abs.abs().sum().item() == 0.0
+    p = rt.make_params(1)
+    with pytest.raises(rt.RtError):
+        rt.rtgb.rt_pah_reemit(ctx.h, grid.h, opac.h, None, 0, 1.0,
+                              np.ones(m.nf).ctypes.data_as(__import__("ctypes").c_void_p), 1, None, p,
+                              None, out.c_struct(), 0)
