@@ -95,6 +95,15 @@ RT_API rt_status rt_grid_upload_refined(rt_ctx* ctx, int nx, int ny, int nz, int
                                         const double box_min[3], double cell_size, int refine,
                                         const unsigned char* refined, const float* rho,
                                         rt_stream stream, rt_grid** out);
+/* New densities for an existing grid (same shape, species and refinement):
+ * rho as for the upload (host or device, [n_species][ncell] float32), copied
+ * on `stream` into the grid's own copy and checked there, synchronously
+ * (finite, >= 0); no device memory is allocated or freed after the first
+ * call.  The packed copy the kernels read is rebuilt by the next call that
+ * uses the grid.  Errors: RT_ERR_INVALID_ARG for NULL or a bad density --
+ * the grid then refuses every call (RT_ERR_STATE) until an update succeeds;
+ * RT_ERR_CUDA. */
+RT_API rt_status rt_grid_update(rt_grid* grid, const float* rho, rt_stream stream);
 /* Cells of a grid (leaves of a refined one). */
 RT_API uint64_t rt_grid_ncell(const rt_grid* grid);
 RT_API void rt_grid_free(rt_grid* grid);

@@ -184,6 +184,34 @@ rt_status rt_grid_upload_refined(rt_ctx* ctx, int nx, int ny, int nz, int ns, co
     return RT_OK;
 }
 
+rt_status rt_grid_update(rt_grid* g, const float* rho, rt_stream stream)
+{
+    if (!g || !rho) return fail(RT_ERR_INVALID_ARG, "rt_grid_update: NULL pointer");
+    rt_ctx* ctx = g->ctx;
+    if (!ctx || ctx->magic != kMagic) return fail(RT_ERR_STATE, "rt_grid_update: bad context");
+    RT_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t n = g->ncell() * g->ns;
+    if (!g->d_flag) RT_CUDA(cudaMalloc(&g->d_flag, sizeof(unsigned int)));
+    unsigned int* bad = g->d_flag;
+    g->rho_bad = 1;                          // until the new values are checked
+    g->packed_prec = -1;                     // the packed copy is stale: repacked on next use
+    cudaError_t e = cudaMemcpyAsync(g->d_rho, rho, n * sizeof(float), cudaMemcpyDefault, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(bad, 0, sizeof(unsigned int), s);
+    if (e == cudaSuccess) {
+        check_rho_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g->d_rho, n, bad);
+        count_launches();
+        e = cudaGetLastError();
+    }
+    unsigned int hbad = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, sizeof(unsigned int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "rt_grid_update");
+    if (hbad) return fail(RT_ERR_INVALID_ARG, "rt_grid_update: density must be finite and >= 0");
+    g->rho_bad = 0;
+    return RT_OK;
+}
+
 void rt_grid_free(rt_grid* g)
 {
     if (!g) return;
@@ -193,6 +221,7 @@ void rt_grid_free(rt_grid* g)
     cudaFree(g->d_cube);
     cudaFree(g->d_leaf_cube);
     cudaFree(g->d_leaf_fine);
+    cudaFree(g->d_flag);
     delete g;
 }
 
@@ -648,6 +677,7 @@ static rt_status transport_one(rt_ctx* ctx, const rt_grid* grid, const rt_opacit
     if (!grid || !op) return fail(RT_ERR_INVALID_ARG, "rt_transport: NULL grid or opacity");
     if (grid->ctx != ctx || op->ctx != ctx) return fail(RT_ERR_STATE, "rt_transport: handle from another context");
     if (grid->ns != op->ns) return fail(RT_ERR_INVALID_ARG, "rt_transport: grid and opacity species differ");
+    if (grid->rho_bad) return fail(RT_ERR_STATE, "rt_transport: the grid's last density update was refused");
     rt_status st = check_params(p);
     if (st != RT_OK) return st;
     st = check_out(out);
@@ -778,8 +808,8 @@ rt_status rt_batch_create(rt_ctx* ctx, const rt_opacity* op, int n_models, const
     std::vector<uint64_t> nwork(n_models);
     for (int m = 0; m < n_models; ++m) {
         const rt_model& M = models[m];
-        if (!M.grid || M.grid->ctx != ctx || M.grid->ns != op->ns)
-            return fail(RT_ERR_INVALID_ARG, "rt_batch_create: grid missing, foreign or with other species");
+        if (!M.grid || M.grid->ctx != ctx || M.grid->ns != op->ns || M.grid->rho_bad)
+            return fail(RT_ERR_INVALID_ARG, "rt_batch_create: grid missing, foreign, with other species or refused density");
         if (M.n_packets == 0) return fail(RT_ERR_INVALID_ARG, "rt_batch_create: n_packets must be > 0");
         if (p->mode == RT_MODE_FROZEN_T && !M.T_prev)
             return fail(RT_ERR_INVALID_ARG, "rt_batch_create: frozen-T mode needs T_prev for every model");
@@ -885,6 +915,7 @@ rt_status rt_temperatures(rt_ctx* ctx, const rt_grid* grid, const rt_opacity* op
     if (!grid || !op || !E_abs || !T) return fail(RT_ERR_INVALID_ARG, "rt_temperatures: NULL pointer");
     if (grid->ctx != ctx || op->ctx != ctx) return fail(RT_ERR_STATE, "rt_temperatures: handle from another context");
     if (grid->ns != op->ns) return fail(RT_ERR_INVALID_ARG, "rt_temperatures: grid and opacity species differ");
+    if (grid->rho_bad) return fail(RT_ERR_STATE, "rt_temperatures: the grid's last density update was refused");
     RT_CUDA(cudaSetDevice(ctx->device));
     return launch_temperatures(ctx, grid, op, E_abs, T, (cudaStream_t)stream);
 }
@@ -913,6 +944,7 @@ static rt_status check_rt_args(rt_ctx* ctx, const rt_grid* grid, const rt_opacit
     if (!grid || !op || !T || !cams || !fidx) return fail(RT_ERR_INVALID_ARG, "rt_raytrace: NULL pointer");
     if (grid->ctx != ctx || op->ctx != ctx) return fail(RT_ERR_STATE, "rt_raytrace: handle from another context");
     if (grid->ns != op->ns) return fail(RT_ERR_INVALID_ARG, "rt_raytrace: grid and opacity species differ");
+    if (grid->rho_bad) return fail(RT_ERR_STATE, "rt_raytrace: the grid's last density update was refused");
     if (nev > 0 && !ev) return fail(RT_ERR_INVALID_ARG, "rt_raytrace: events NULL with n_events > 0");
     if (nsrc < 0 || nsrc > 64 || (nsrc > 0 && !src)) return fail(RT_ERR_INVALID_ARG, "rt_raytrace: bad sources");
     if (ncam < 1 || ncam > 1024) return fail(RT_ERR_INVALID_ARG, "rt_raytrace: n_cams must be 1..1024");
@@ -1067,6 +1099,7 @@ rt_status rt_transport_noalloc(rt_ctx* ctx, const rt_grid* grid, const rt_opacit
     if (!grid || !op) return fail(RT_ERR_INVALID_ARG, "rt_transport_noalloc: NULL grid or opacity");
     if (grid->ctx != ctx || op->ctx != ctx) return fail(RT_ERR_STATE, "rt_transport_noalloc: handle from another context");
     if (grid->ns != op->ns) return fail(RT_ERR_INVALID_ARG, "rt_transport_noalloc: grid and opacity species differ");
+    if (grid->rho_bad) return fail(RT_ERR_STATE, "rt_transport_noalloc: the grid's last density update was refused");
     rt_status st = check_params(p);
     if (st != RT_OK) return st;
     st = check_out(out);

@@ -94,6 +94,8 @@ struct rt_grid {
     int packed_lucy_mode;
     double packed_lucy_tau;
     int packed_prec;
+    int rho_bad;                           // the last density update was refused
+    unsigned int* d_flag;                  // device word for the density check of updates
     // one level of refinement (refine = r >= 2; 0 = uniform grid)
     int refine;
     size_t nleaf;                          // cells of a refined grid

@@ -33,7 +33,7 @@ EXPORTS = ["rt_last_error", "rt_version", "rt_ctx_create", "rt_ctx_destroy", "rt
            "rt_transport", "rt_temperatures", "rt_temperature_guess", "rt_raytrace",
            "rt_raytrace_backward", "rt_batch_create", "rt_batch_run", "rt_batch_free",
            "rt_transport_batched", "rt_philox", "rt_kernel_launches", "rt_transport_noalloc", "rt_visibilities",
-           "rt_pah_reemit", "rt_grid_upload_refined", "rt_grid_ncell"]
+           "rt_pah_reemit", "rt_grid_upload_refined", "rt_grid_ncell", "rt_grid_update"]
 
 
 class RtError(RuntimeError):
@@ -111,6 +111,7 @@ def load(path: str = LIB_PATH):
         "rt_grid_upload_refined": (i32, [vp, i32, i32, i32, i32, C.POINTER(dbl), dbl, i32, vp, vp, vp,
                                          C.POINTER(vp)]),
         "rt_grid_ncell": (u64, [vp]),
+        "rt_grid_update": (i32, [vp, vp, vp]),
         "rt_grid_free": (None, [vp]),
         "rt_opacity_upload": (i32, [vp, i32, vp, vp, i32, vp, vp, vp, vp, C.POINTER(vp)]),
         "rt_opacity_free": (None, [vp]),
@@ -172,6 +173,10 @@ def rt_grid_upload_refined(ctx, nx, ny, nz, n_species, box_min, cell, refine, re
                                          refined_ptr, rho_ptr, stream, C.byref(h)),
            "rt_grid_upload_refined")
     return h.value
+
+
+def rt_grid_update(grid, rho_ptr, stream=0):
+    _check(load().rt_grid_update(grid, rho_ptr, stream), "rt_grid_update")
 
 
 def rt_grid_ncell(grid) -> int:

@@ -96,6 +96,18 @@ class Grid:
         self.ns = ns
         self._src = None
 
+    def update(self, rho, stream=None) -> "Grid":
+        """New densities of the same shape (host or device), copied into the
+        grid's own buffer (no allocation); checked synchronously."""
+        if isinstance(rho, torch.Tensor):
+            t = rho.detach().to(dtype=torch.float32).contiguous()
+        else:
+            t = torch.from_numpy(np.ascontiguousarray(rho, dtype=np.float32))
+        if t.numel() != self.ns * self.ncell:
+            raise ValueError(f"density needs {self.ns * self.ncell} values, got {t.numel()}")
+        R.rt_grid_update(self.h, t.data_ptr(), _stream(stream))
+        return self
+
     def __del__(self):
         try:
             if self.h:

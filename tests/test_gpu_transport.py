@@ -511,3 +511,30 @@ def test_pah_reemission_without_records(rt, ctx):
         rt.rtgb.rt_pah_reemit(ctx.h, grid.h, opac.h, None, 0, 1.0,
                               np.ones(m.nf).ctypes.data_as(__import__("ctypes").c_void_p), 1, None, p,
                               None, out.c_struct(), 0)
+
+
+def test_grid_update_reuses_the_grid(rt, ctx, O):
+    """New densities through rt_grid_update give the same FP64 transport as
+    a grid uploaded with them; a bad density is refused and the grid then
+    refuses to be used until a good update."""
+    m = W.random_grid(n=(6, 5, 4), ns=2, seed=31, tau_scale=1.5, albedo=(0.3, 0.8))
+    m2 = W.random_grid(n=(6, 5, 4), ns=2, seed=31, tau_scale=3.0, albedo=(0.3, 0.8))
+    grid, opac, srcs = _setup(rt, ctx, m)
+    T0 = torch.full((m.ns, m.ncell), 200.0, dtype=torch.float64, device="cuda")
+    kw = dict(mode=rt.rtgb.RT_MODE_FROZEN_T, precision=rt.rtgb.RT_PREC_FP64, T_prev=T0, seed=4)
+    rt.transport(ctx, grid, opac, srcs, 300, **kw)               # packs the first density
+    grid.update(m2.rho)
+    a = rt.transport(ctx, grid, opac, srcs, 300, **kw)
+    b = rt.transport(ctx, ctx.grid(m2), opac, srcs, 300, **kw)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(a.count.cpu().numpy(), b.count.cpu().numpy())
+    np.testing.assert_allclose(a.E_abs.cpu().numpy(), b.E_abs.cpu().numpy(), rtol=1e-12, atol=0)
+    bad = m2.rho.copy()
+    bad.reshape(-1)[7] = np.nan
+    with pytest.raises(rt.RtError):
+        grid.update(bad)
+    with pytest.raises(rt.RtError):
+        rt.transport(ctx, grid, opac, srcs, 10, **kw)
+    grid.update(m.rho)
+    rt.transport(ctx, grid, opac, srcs, 10, **kw)
+    torch.cuda.synchronize()
