@@ -237,6 +237,36 @@ def form_fp64_debug(rt, ctx, flush):
     return res
 
 
+def form_plain_fp32(rt, ctx, flush, packets=1e7):
+    """The benchmark's transport (128^3 r^-2 shell, tau(1 um) = 10, 1e7
+    packets, B&W, Lucy thin, events) in the production form (FP32 transport,
+    FP64 accumulators) and in the plain-FP32 form (FP32 accumulators), same
+    packets."""
+    import torch
+    import workloads as W
+    from paper_1203_2941_gb300 import rtgb as R
+    m = W.r2_shell(n=128, tau_1um=10.0, nf=64)
+    grid, opac, srcs = ctx.grid(m), ctx.opacity(m), rt.Sources(m.sources)
+    N = int(packets)
+    res = {}
+    for name, prec in (("fp32_fp64acc", R.RT_PREC_FP32), ("fp32_fp32acc", R.RT_PREC_FP32_ACC32)):
+        out = rt.TransportOut(grid.ncell, 1, opac.nf, event_cap=6 * N)
+
+        def run(r):
+            out.zero_()
+            out.stats[13:].zero_()
+            rt.transport(ctx, grid, opac, srcs, N, out=out, record_events=True, seed=7 + max(r, 0),
+                         precision=prec)
+        ts = _timed(run, 5, 2, flush)
+        S = _stats_delta(out, torch.zeros_like(out.stats))
+        t = statistics.median(ts)
+        res[name] = {"value": S["crossings"] / t, "unit": UNIT, "ms": 1e3 * t,
+                     "roofline": _roof(_transport_bytes(S, 1), t)}
+    res["ratio_fp32acc_over_fp64acc"] = res["fp32_fp32acc"]["value"] / res["fp32_fp64acc"]["value"]
+    res["workload"] = f"r^-2 shell 128^3 tau1um=10, 64 freq, {N:.0e} packets, B&W, Lucy thin, events"
+    return res
+
+
 def form_mrw_disk(rt, ctx, flush, packets=1e7, npix=512):
     """Flared disk 256^3 (midplane tau_V = 1e4, 100 frequencies) with the
     modified random walk in cells of tau > 10; then Eq. 4 temperatures and
@@ -430,13 +460,13 @@ def run_forms(a):
     ctx = rt.Context(0)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     forms = {}
-    for name, fn in (("fp64_debug", form_fp64_debug), ("mrw_disk", form_mrw_disk),
-                     ("adjoint", form_adjoint), ("batched", form_batched),
-                     ("refined_shell", form_refined_shell)):
+    for name, fn in (("fp64_debug", form_fp64_debug), ("plain_fp32", form_plain_fp32),
+                     ("mrw_disk", form_mrw_disk), ("adjoint", form_adjoint),
+                     ("batched", form_batched), ("refined_shell", form_refined_shell)):
         if a.forms != "all" and name not in a.forms.split(","):
             continue
         t0 = time.perf_counter()
-        kw = {"packets": a.packets} if name in ("mrw_disk", "refined_shell") else {}
+        kw = {"packets": a.packets} if name in ("mrw_disk", "refined_shell", "plain_fp32") else {}
         forms[name] = fn(rt, ctx, flush, **kw)
         forms[name]["wall_s"] = time.perf_counter() - t0
         print(json.dumps({"form": name, **forms[name]}), flush=True)

@@ -143,7 +143,12 @@ enum { RT_LUCY_OFF = 0, RT_LUCY_THIN = 1, RT_LUCY_ALL = 2 };   /* Sect. 3.1 cell
 enum { RT_LUCY_LINEAR = 0,    /* deposit xi kappa_abs rho l (unbiased path-length form) */
        RT_LUCY_EXPM1 = 1 };   /* deposit (1 - exp(-kappa_abs rho l)) xi (Eq. 9) */
 enum { RT_PREC_FP32 = 0,      /* production: FP32 transport, FP64 accumulators */
-       RT_PREC_FP64 = 1 };    /* debug: every quantity in FP64 (trajectory parity) */
+       RT_PREC_FP64 = 1,      /* debug: every quantity in FP64 (trajectory parity) */
+       RT_PREC_FP32_ACC32 = 2 };  /* plain FP32: FP32 transport and FP32 per-cell
+                                 accumulators (a comparison form: sums of many
+                                 deposits lose digits); rt_transport on uniform
+                                 grids without trajectories, deferred queue,
+                                 cameras or PAH sources only */
 enum { RT_SCHED_PERSISTENT = 0, /* all SMs, dynamic packet refill */
        RT_SCHED_SERIAL = 1 };   /* one GPU thread, packets in id order (debug) */
 

@@ -316,7 +316,8 @@ static rt_status check_params(const rt_transport_params* p)
     if (!(p->lucy_tau >= 0.0) || !isfin(p->lucy_tau)) return fail(RT_ERR_INVALID_ARG, "transport: bad lucy_tau");
     if (p->mrw && (!(p->mrw_tau_cell > 0.0) || !(p->mrw_gamma > 0.0)))
         return fail(RT_ERR_INVALID_ARG, "transport: MRW thresholds must be positive");
-    if (p->precision != RT_PREC_FP32 && p->precision != RT_PREC_FP64) return fail(RT_ERR_INVALID_ARG, "transport: bad precision");
+    if (p->precision != RT_PREC_FP32 && p->precision != RT_PREC_FP64 && p->precision != RT_PREC_FP32_ACC32)
+        return fail(RT_ERR_INVALID_ARG, "transport: bad precision");
     if (p->schedule != RT_SCHED_PERSISTENT && p->schedule != RT_SCHED_SERIAL) return fail(RT_ERR_INVALID_ARG, "transport: bad schedule");
     if (p->n_packets == 0) return fail(RT_ERR_INVALID_ARG, "transport: n_packets must be > 0");
     if (p->march_min_active < -1 || p->march_min_active > 31) return fail(RT_ERR_INVALID_ARG, "transport: march_min_active must be -1..31");
@@ -592,7 +593,7 @@ static rt_status single_model_options(TransportKP& kp, const rt_opacity* op,
     kp.rho0 = m0.rho;
     kp.param_models = 1;
     kp.mp[0] = m0;
-    const bool persistent = p->schedule == RT_SCHED_PERSISTENT && p->precision == RT_PREC_FP32;
+    const bool persistent = p->schedule == RT_SCHED_PERSISTENT && p->precision != RT_PREC_FP64;
     kp.smem_sed = persistent && op->nf <= 256 ? 1 : 0;
     kp.smem_cdf = persistent && n_sources * op->nf <= 4096 ? n_sources * op->nf : 0;
     return RT_OK;
@@ -694,14 +695,20 @@ static rt_status transport_one(rt_ctx* ctx, const rt_grid* grid, const rt_opacit
                     T_prev, out, hms[0], pp ? pp->xi : 0.0);
     if (st != RT_OK) return st;
     if (p->pid_end == p->pid_begin) return RT_OK;
-    st = pack_grid(const_cast<rt_grid*>(grid), op, p->lucy_mode, p->lucy_tau, p->precision, s);
+    const bool acc32 = p->precision == RT_PREC_FP32_ACC32;
+    if (acc32 && (grid->refine || pp || p->n_pc_cams || p->defer_events || (out->traj && out->traj_cap)))
+        return fail(RT_ERR_INVALID_ARG, "rt_transport: the plain-FP32 form serves uniform grids without "
+                                        "trajectories, deferred queue, cameras or PAH sources");
+    const int prec = acc32 ? RT_PREC_FP32 : p->precision;     // the transport's arithmetic
+    st = pack_grid(const_cast<rt_grid*>(grid), op, p->lucy_mode, p->lucy_tau, prec, s);
     if (st != RT_OK) return st;
     hms[0].md.rho = grid->d_packed;
     // FP32 build: this call's deposits go to FP64 scratch in units of xi
+    // (FP32 scratch in the plain-FP32 form)
     const size_t n_acc = (size_t)op->ns * grid->ncell();
     double* acc = nullptr;
-    if (p->precision == RT_PREC_FP32) {
-        const size_t bytes = sizeof(double) * n_acc * (out->esq ? 2 : 1);
+    if (prec == RT_PREC_FP32) {
+        const size_t bytes = (acc32 ? sizeof(float) : sizeof(double)) * n_acc * (out->esq ? 2 : 1);
         RT_CUDA(cudaMallocAsync((void**)&acc, bytes, s));
         RT_CUDA(cudaMemsetAsync(acc, 0, bytes, s));
         hms[0].md.accE = acc;
@@ -715,6 +722,7 @@ static rt_status transport_one(rt_ctx* ctx, const rt_grid* grid, const rt_opacit
     fill_kp(kp, op, p, dm, 1);
     fill_pc(kp, grid, p, out);
     kp.refined = grid->refine ? 1 : 0;
+    kp.acc32 = acc32 ? 1 : 0;
     st = single_model_options(kp, op, p, out, n_sources, hms[0].md);
     if (st != RT_OK) { cudaFreeAsync(dm.buf, s); if (acc) cudaFreeAsync(acc, s); return st; }
     // PAH pass: the emissivity classes' cumulative tables (Eq. 6), FP64 and
@@ -771,17 +779,19 @@ static rt_status transport_one(rt_ctx* ctx, const rt_grid* grid, const rt_opacit
         kp.defer_cap = cap;
     }
     const int threads = p->threads_per_block ? p->threads_per_block : 256;
-    st = launch_transport(ctx, op, kp, op->ns, p->precision, p->schedule, threads, p->blocks_per_sm, s);
+    st = launch_transport(ctx, op, kp, op->ns, prec, p->schedule, threads, p->blocks_per_sm, s);
     if (st == RT_OK && qbuf) {
         TransportKP kr = kp;
         kr.resume = 1;
         cudaError_t e = cudaMemsetAsync(dm.work, 0, sizeof(unsigned long long), s);
-        st = e == cudaSuccess ? launch_transport(ctx, op, kr, op->ns, p->precision, p->schedule, threads,
+        st = e == cudaSuccess ? launch_transport(ctx, op, kr, op->ns, prec, p->schedule, threads,
                                                  p->blocks_per_sm, s)
                               : cuda_fail(e, "rt_transport resume");
     }
     if (st == RT_OK && acc)
-        st = launch_finalize(acc, hms[0].md.acc_q, n_acc, hms[0].md.xi, out->E_abs, out->esq, s);
+        st = acc32 ? launch_finalize32(reinterpret_cast<const float*>(acc), hms[0].md.acc_q, n_acc,
+                                       hms[0].md.xi, out->E_abs, out->esq, s)
+                   : launch_finalize(acc, hms[0].md.acc_q, n_acc, hms[0].md.xi, out->E_abs, out->esq, s);
     cudaFreeAsync(dm.buf, s);
     if (acc) cudaFreeAsync(acc, s);
     if (ebuf) cudaFreeAsync(ebuf, s);
@@ -803,6 +813,8 @@ rt_status rt_batch_create(rt_ctx* ctx, const rt_opacity* op, int n_models, const
     if (st != RT_OK) return st;
     if (p->n_pc_cams != 0)
         return fail(RT_ERR_INVALID_ARG, "rt_batch_create: photon-counting cameras are served by rt_transport only");
+    if (p->precision == RT_PREC_FP32_ACC32)
+        return fail(RT_ERR_INVALID_ARG, "rt_batch_create: the plain-FP32 form is served by rt_transport only");
     RT_CUDA(cudaSetDevice(ctx->device));
     std::vector<HostModel> hms(n_models);
     std::vector<uint64_t> nwork(n_models);
@@ -1108,6 +1120,8 @@ rt_status rt_transport_noalloc(rt_ctx* ctx, const rt_grid* grid, const rt_opacit
         return fail(RT_ERR_INVALID_ARG, "rt_transport_noalloc: need pid_begin <= pid_end <= n_packets");
     if (p->n_pc_cams != 0)
         return fail(RT_ERR_INVALID_ARG, "rt_transport_noalloc: photon-counting cameras are served by rt_transport only");
+    if (p->precision == RT_PREC_FP32_ACC32)
+        return fail(RT_ERR_INVALID_ARG, "rt_transport_noalloc: the plain-FP32 form is served by rt_transport only");
     if (p->mode == RT_MODE_FROZEN_T && !T_prev)
         return fail(RT_ERR_INVALID_ARG, "rt_transport_noalloc: frozen-T mode needs T_prev");
     // scratch layout: staging | kext | packed density | FP64 energy scratch

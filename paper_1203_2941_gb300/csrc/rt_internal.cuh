@@ -132,7 +132,8 @@ struct ModelDev {
     int refine;                // r, or 0
     double inv_refine;         // 1 / r (exact for the power-of-two factors)
     float inv_refine32;        // the same in FP32 (no FP64 conversion in the FP32 walk)
-    double* accE;              // FP32 build: this call's deposits in units of xi; with
+    double* accE;              // FP32 build: this call's deposits in units of xi (float
+                               // sums in the plain-FP32 form); with
     int acc_q;                 // acc_q = 1 each cell holds {sum, sum of squares} (xi, xi^2)
     double* sed_esc; unsigned long long* sed_cnt;
     const double* T_prev;
@@ -197,6 +198,7 @@ struct TransportKP {
     const int* eps_class;               // [ncell] or NULL (class 0)
     int n_eps;
     int refined;                        // the model's grid has one level of refinement
+    int acc32;                          // FP32 per-cell accumulators (plain-FP32 form)
     int n_pc;                           // photon-counting cameras (single-model calls)
     double* pc_img;
     double pc_ctr[3];                   // grid centre, cell units
@@ -283,6 +285,8 @@ rt_status launch_transport(rt_ctx* ctx, const rt_opacity* op, const TransportKP&
                            cudaStream_t s);
 rt_status launch_finalize(const double* acc, int acc_q, size_t n, double xi, double* E_abs,
                           double* esq, cudaStream_t s);
+rt_status launch_finalize32(const float* acc, int acc_q, size_t n, double xi, double* E_abs,
+                            double* esq, cudaStream_t s);
 rt_status launch_temperatures(rt_ctx* ctx, const rt_grid* g, const rt_opacity* op,
                               const double* E, double* T, cudaStream_t s);
 rt_status launch_temperature_guess(rt_ctx* ctx, const rt_grid* g, const double* src_pos,

@@ -30,6 +30,7 @@
 
 #include <algorithm>
 
+#include <type_traits>
 #include "rt_internal.cuh"
 
 namespace rtgb {
@@ -302,8 +303,9 @@ __device__ __forceinline__ unsigned char* smem_raw()
 // bank) instead of global memory, 8 = a single model (its index and grid
 // pointer are constants, not lane registers), 16 = the deferred-packet queue
 // compiled in, 32 = PAH re-emission sources compiled in, 64 = one level of
-// sub-cube refinement (two-level traversal), 128 = photon-counting cameras;
-// production launches leave unused paths out of the hot code.
+// sub-cube refinement (two-level traversal), 128 = photon-counting cameras,
+// 256 = FP32 per-cell accumulators (the plain-FP32 form); production launches
+// leave unused paths out of the hot code.
 template <typename R, int NS, int FEAT>
 struct Kernel {
     using PT = typename PackedT<NS>::T;
@@ -316,6 +318,19 @@ struct Kernel {
     static constexpr bool HAS_PAH = (FEAT & 32) != 0;
     static constexpr bool HAS_REF = (FEAT & 64) != 0;
     static constexpr bool HAS_PC = (FEAT & 128) != 0;
+    static constexpr bool ACC32 = (FEAT & 256) != 0;
+    using Acc = typename std::conditional<ACC32, float, double>::type;
+
+    // the call's per-cell scratch: {sum, sum of squares} of deposits in units of xi
+    __device__ __forceinline__ Acc* acc_at(size_t idx) const
+    {
+        return reinterpret_cast<Acc*>(md->accE) + (idx << md->acc_q);
+    }
+    __device__ __forceinline__ Acc to_acc(float v) const
+    {
+        if constexpr (ACC32) return v;
+        else return f2d(v);
+    }
 
     const TransportKP& P;
     const ModelDev* md;        // model of the lane's current packet
@@ -839,9 +854,9 @@ struct Kernel {
                 }
             } else {
                 if (ta > 0.0f) {
-                    double* e = md->accE + (idx << md->acc_q);
-                    atomicAdd(e, f2d(ta));
-                    if (md->acc_q) atomicAdd(e + 1, f2d(ta * ta));
+                    Acc* e = acc_at(idx);
+                    atomicAdd(e, to_acc(ta));
+                    if (md->acc_q) atomicAdd(e + 1, to_acc(ta * ta));
                 }
             }
         }
@@ -857,7 +872,7 @@ struct Kernel {
         if constexpr (DBG) {
             return have_old ? old + md->xi : __ldcg(&md->E_abs[i]);
         } else {
-            const double acc = have_old ? old + 1.0 : __ldcg(&md->accE[i << md->acc_q]);
+            const double acc = have_old ? old + 1.0 : (double)__ldcg(acc_at(i));
             return __ldcg(&md->E_abs[i]) + acc * md->xi;
         }
     }
@@ -1132,9 +1147,9 @@ struct Kernel {
                     if (md->esq) atomicAdd(&md->esq[idx], e * e);
                 }
             } else if (ta > 0.0f) {
-                double* e = md->accE + (idx << md->acc_q);
-                atomicAdd(e, f2d(ta));
-                if (md->acc_q) atomicAdd(e + 1, f2d(ta * ta));
+                Acc* e = acc_at(idx);
+                atomicAdd(e, to_acc(ta));
+                if (md->acc_q) atomicAdd(e + 1, to_acc(ta * ta));
             }
         }
         count(RT_STAT_MRW, 1);
@@ -1265,11 +1280,11 @@ struct Kernel {
             const bool lead = (int)(threadIdx.x & 31) == leader;
             double old = 0.0;
             if (!L.lucy) {
-                double* e = md->accE + (idx << md->acc_q);
+                Acc* e = acc_at(idx);
                 if (lead) {
-                    if (P.mode == RT_MODE_BW) old = atomicAdd(e, (double)n);
-                    else atomicAdd(e, (double)n);
-                    if (md->acc_q) atomicAdd(e + 1, (double)n);
+                    if (P.mode == RT_MODE_BW) old = (double)atomicAdd(e, (Acc)n);
+                    else atomicAdd(e, (Acc)n);
+                    if (md->acc_q) atomicAdd(e + 1, (Acc)n);
                 }
                 if (P.mode == RT_MODE_BW) {
                     old = __shfl_sync(grp, old, leader) + (double)rank;
@@ -1552,15 +1567,16 @@ __global__ void pack_kernel(const float* rho, size_t nc, double kext_max, PT* ou
 
 // E_abs += acc * xi and esq += acc_sq * xi^2 for one model (FP32 build);
 // with acc_q = 1 the scratch interleaves the two sums per cell
-__global__ void finalize_kernel(const double* acc, int acc_q, size_t n, double xi, double* E_abs,
+template <typename A>
+__global__ void finalize_kernel(const A* acc, int acc_q, size_t n, double xi, double* E_abs,
                                 double* esq)
 {
     const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const double a = acc[i << acc_q];
+    const double a = (double)acc[i << acc_q];
     if (a != 0.0) {
         E_abs[i] += a * xi;
-        if (acc_q && esq) esq[i] += acc[2 * i + 1] * xi * xi;
+        if (acc_q && esq) esq[i] += (double)acc[2 * i + 1] * xi * xi;
     }
 }
 
@@ -1640,6 +1656,13 @@ rt_status launch_feat(rt_ctx* ctx, const TransportKP& kp, int schedule, int thre
             return launch_one<R, NS, 179>(ctx, kp, schedule, threads, blocks_per_sm, s);
         }
         if (kp.n_pc) return launch_one<R, NS, 147>(ctx, kp, schedule, threads, blocks_per_sm, s);
+        if (kp.acc32) {
+            // the plain-FP32 form: single-model uniform-grid launches only
+            if (!kp.single || !kp.param_models || kp.want_traj || kp.defer_events)
+                return fail(RT_ERR_STATE, "transport: no plain-FP32 variant for this feature set");
+            if (kp.mrw) return launch_one<R, NS, 269>(ctx, kp, schedule, threads, blocks_per_sm, s);
+            return launch_one<R, NS, 268>(ctx, kp, schedule, threads, blocks_per_sm, s);
+        }
         // trajectory logging runs the generic variants; otherwise descriptors
         // come from the parameters when they fit, and one model is constant
         const int feat = (kp.mrw ? 1 : 0) |
@@ -1725,7 +1748,17 @@ rt_status launch_finalize(const double* acc, int acc_q, size_t n, double xi, dou
                           double* esq, cudaStream_t s)
 {
     if (n == 0) return RT_OK;
-    finalize_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(acc, acc_q, n, xi, E_abs, esq);
+    finalize_kernel<double><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(acc, acc_q, n, xi, E_abs, esq);
+    count_launches();
+    RT_CUDA(cudaGetLastError());
+    return RT_OK;
+}
+
+rt_status launch_finalize32(const float* acc, int acc_q, size_t n, double xi, double* E_abs,
+                            double* esq, cudaStream_t s)
+{
+    if (n == 0) return RT_OK;
+    finalize_kernel<float><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(acc, acc_q, n, xi, E_abs, esq);
     count_launches();
     RT_CUDA(cudaGetLastError());
     return RT_OK;

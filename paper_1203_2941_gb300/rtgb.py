@@ -22,7 +22,7 @@ RT_OK, RT_ERR_INVALID_ARG, RT_ERR_CUDA, RT_ERR_OOM, RT_ERR_CAPACITY, RT_ERR_STUC
 RT_MODE_BW, RT_MODE_FROZEN_T, RT_MODE_NOREEMIT = 0, 1, 2
 RT_LUCY_OFF, RT_LUCY_THIN, RT_LUCY_ALL = 0, 1, 2
 RT_LUCY_LINEAR, RT_LUCY_EXPM1 = 0, 1
-RT_PREC_FP32, RT_PREC_FP64 = 0, 1
+RT_PREC_FP32, RT_PREC_FP64, RT_PREC_FP32_ACC32 = 0, 1, 2
 RT_SCHED_PERSISTENT, RT_SCHED_SERIAL = 0, 1
 STAT_NAMES = ["crossings", "interactions", "scatters", "absorptions", "mrw_steps", "escaped",
               "stuck", "pah", "events_dropped", "lucy_deposits", "emitted", "pah_dropped",

@@ -538,3 +538,28 @@ def test_grid_update_reuses_the_grid(rt, ctx, O):
     grid.update(m.rho)
     rt.transport(ctx, grid, opac, srcs, 10, **kw)
     torch.cuda.synchronize()
+
+
+def test_plain_fp32_form(rt, ctx):
+    """FP32 per-cell accumulators (the plain-FP32 comparison form): the
+    same packets as the production form (same Philox streams), energy
+    conservation exact in the FP64 escape tally, per-cell energies within
+    the Monte Carlo noise of the production run (the two differ only by the
+    accumulators' rounding and the order of B&W updates); refused where it
+    is not served."""
+    m = W.r2_shell(n=24, tau_1um=3.0, nf=24)
+    grid, opac, srcs = _setup(rt, ctx, m)
+    N = 400_000
+    a = rt.transport(ctx, grid, opac, srcs, N, seed=12)
+    b = rt.transport(ctx, grid, opac, srcs, N, seed=12, precision=rt.rtgb.RT_PREC_FP32_ACC32)
+    torch.cuda.synchronize()
+    sb = b.stats_dict()
+    assert sb["escaped"] == N and sb["stuck"] == 0
+    assert b.sed_esc.sum().item() == pytest.approx(m.luminosity, rel=1e-9)
+    Ea, Eb = a.E_abs.cpu().numpy()[0], b.E_abs.cpu().numpy()[0]
+    sig = np.sqrt(a.esq.cpu().numpy()[0] + b.esq.cpu().numpy()[0])
+    on = Ea > 0
+    assert np.all(np.abs(Eb[on] - Ea[on]) <= 5 * sig[on] + 2e-3 * Ea[on])
+    assert Eb.sum() == pytest.approx(Ea.sum(), rel=2e-3)
+    with pytest.raises(rt.RtError):
+        rt.transport(ctx, grid, opac, srcs, 100, precision=rt.rtgb.RT_PREC_FP32_ACC32, traj_cap=1000)
