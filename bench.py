@@ -34,7 +34,7 @@ UNIT = "crossings/s"
 # dram__bytes_write.sum; the command is in the transport kernel's summary
 # under profiles/); to be re-measured (or set to None) whenever the transport
 # kernel changes
-TRANSPORT_DRAM_BYTES = 32.111e6 + 31.670e6
+TRANSPORT_DRAM_BYTES = 32.065e6 + 31.657e6
 
 
 def parse():
