@@ -267,6 +267,77 @@ def form_plain_fp32(rt, ctx, flush, packets=1e7):
     return res
 
 
+def form_next_rows(rt, ctx, flush, packets=1e7):
+    """The later rows on their own workloads: the PAH re-emission pass
+    (128^3 clumpy torus with PAH, the records of a 1e7-packet B&W run), Eq. 1
+    equal-energy source bins against random bins on the benchmark's
+    transport, photon-counting cameras (5 cones) on the same transport, and
+    visibilities of the benchmark's images (5 x 12 images of 256^2 at 1024
+    (u, v) points)."""
+    import math as _m
+    import numpy as _np
+    import torch
+    import workloads as W
+    N = int(packets)
+    res = {}
+    # PAH pass
+    mt = W.clumpy_torus(n=128, n_clump=1000, seed=77, nf=100)
+    eps, cls = W.pah_emissivity(mt)
+    gt, ot, st_ = ctx.grid(mt), ctx.opacity(mt), rt.Sources(mt.sources)
+    o1 = rt.transport(ctx, gt, ot, st_, N, pah_cap=N, seed=3)
+    torch.cuda.synchronize()
+    n_rec = int(min(o1.stats[14].item(), N))
+    cls_t = torch.tensor(cls, device="cuda")
+    o2 = rt.TransportOut(gt.ncell, gt.ns, ot.nf, pah_cap=n_rec)
+
+    def pah(r):
+        o2.zero_()
+        o2.stats[13:].zero_()
+        rt.pah_reemit(ctx, gt, ot, o1, o1.xi, eps, cls_t, out=o2, pah_cap=n_rec, seed=4 + max(r, 0),
+                      model_id=1)
+    ts = _timed(pah, 3, 1, flush)
+    S = _stats_delta(o2, torch.zeros_like(o2.stats))
+    t = statistics.median(ts)
+    res["pah_pass"] = {"value": S["crossings"] / t, "unit": UNIT, "ms": 1e3 * t, "packets": n_rec,
+                       "roofline": _roof(_transport_bytes(S, 3), t),
+                       "workload": "128^3 clumpy torus (1000 clumps, 3 species), records of a "
+                                   f"{N:.0e}-packet B&W run, 4 emissivity classes"}
+    # Eq. 1 source bins and photon counting on the benchmark's transport
+    m = W.r2_shell(n=128, tau_1um=10.0, nf=64)
+    grid, opac, srcs = ctx.grid(m), ctx.opacity(m), rt.Sources(m.sources)
+    out = rt.TransportOut(grid.ncell, 1, opac.nf, event_cap=6 * N)
+    cams = [rt.PcCamera(_m.radians(th), 0.0, 256, _m.cos(_m.radians(5.0))) for th in W.inclinations_deg()]
+    for name, kw in (("random_bins", {}), ("source_bins_1000", {"source_bins": 1000}),
+                     ("photon_counting_5_cameras", {"pc_cams": cams})):
+        def run(r):
+            out.zero_()
+            out.stats[13:].zero_()
+            rt.transport(ctx, grid, opac, srcs, N, out=out, record_events=True, seed=7 + max(r, 0), **kw)
+        ts = _timed(run, 3, 1, flush)
+        S = _stats_delta(out, torch.zeros_like(out.stats))
+        t = statistics.median(ts)
+        res[name] = {"value": S["crossings"] / t, "unit": UNIT, "ms": 1e3 * t,
+                     "roofline": _roof(_transport_bytes(S, 1), t)}
+    # visibilities of the benchmark's images
+    T = rt.temperatures(ctx, grid, opac, out.E_abs)
+    fidx = W.nearest_freq_indices(m.nu, W.image_wavelengths_um())
+    rcams = [W.Camera(_m.radians(th), 0.0, 256, 140 * W.PC) for th in W.inclinations_deg()]
+    img, _ = rt.raytrace(ctx, grid, opac, T, out, out.xi, srcs, rcams, fidx)
+    uv = _np.random.default_rng(1).normal(size=(1024, 2)) * 1e5
+    vis = {}
+
+    def vrun(r):
+        vis["v"] = rt.visibilities(ctx, grid, rcams, img, uv)
+    ts = _timed(vrun, 3, 1, flush)
+    t = statistics.median(ts)
+    n_img = len(rcams) * len(fidx)
+    nbytes = n_img * len(uv) * 256 * 256 * 4
+    res["visibilities"] = {"value": n_img * len(uv) / t, "unit": "visibilities/s", "ms": 1e3 * t,
+                           "roofline": _roof(nbytes, t),
+                           "workload": f"{n_img} images of 256^2 at {len(uv)} (u, v) points"}
+    return res
+
+
 def form_mrw_disk(rt, ctx, flush, packets=1e7, npix=512):
     """Flared disk 256^3 (midplane tau_V = 1e4, 100 frequencies) with the
     modified random walk in cells of tau > 10; then Eq. 4 temperatures and
@@ -462,11 +533,12 @@ def run_forms(a):
     forms = {}
     for name, fn in (("fp64_debug", form_fp64_debug), ("plain_fp32", form_plain_fp32),
                      ("mrw_disk", form_mrw_disk), ("adjoint", form_adjoint),
-                     ("batched", form_batched), ("refined_shell", form_refined_shell)):
+                     ("batched", form_batched), ("refined_shell", form_refined_shell),
+                     ("next_rows", form_next_rows)):
         if a.forms != "all" and name not in a.forms.split(","):
             continue
         t0 = time.perf_counter()
-        kw = {"packets": a.packets} if name in ("mrw_disk", "refined_shell", "plain_fp32") else {}
+        kw = {"packets": a.packets} if name in ("mrw_disk", "refined_shell", "plain_fp32", "next_rows") else {}
         forms[name] = fn(rt, ctx, flush, **kw)
         forms[name]["wall_s"] = time.perf_counter() - t0
         print(json.dumps({"form": name, **forms[name]}), flush=True)
