@@ -1043,61 +1043,101 @@ rt_status raytrace_impl(rt_ctx* ctx, const rt_grid* g, const rt_opacity* op, con
 namespace rtgb {
 namespace {
 
-// Complex visibility of one image at one (u, v): one block per (image, uv).
-// exp(-2 pi i (u alpha + v beta)) separates into a column and a row factor,
-// tabulated in shared memory (phases reduced in FP64, then FP32 sine and
-// cosine of pi times a number in [-1, 1)); a warp takes a row at a time,
-// its lanes stride along the row (coalesced), the row sum (FP32) is reduced
-// by shuffles and multiplied by the row factor, rows accumulate in FP64.
+// Complex visibilities of one image at KT (u, v) points: one block per
+// (image, tile of KT points).  exp(-2 pi i (u alpha + v beta)) separates into
+// a column and a row factor per point, tabulated in shared memory (phases
+// reduced in FP64, then FP32 sine and cosine of pi times a number in
+// [-1, 1)).  A warp takes a row at a time, its lanes stride along the row
+// (coalesced) and keep KT complex row sums in FP32, so each pixel is read
+// once for the KT points; the row sums are reduced by shuffles, multiplied by
+// the row factors and accumulated in FP64.
+template <int KT>
 __global__ void visibility_kernel(const float* images, int npix, const double* alpha0,
                                   const double* dalpha, const double* scale, int nf, const double* uv,
                                   int nuv, double* vis)
 {
-    extern __shared__ float2 tab[];                    // [npix] columns, [npix] rows
-    const int img = blockIdx.y, k = blockIdx.x;
+    extern __shared__ float2 tab[];                    // [KT][npix] columns, [KT][npix] rows
+    const int img = blockIdx.y, k0 = blockIdx.x * KT;
     const int cam = img / nf;
-    const double u = uv[2 * k], v = uv[2 * k + 1];
     const double a0 = alpha0[cam], da = dalpha[cam];
-    for (int i = threadIdx.x; i < 2 * npix; i += blockDim.x) {
-        const int p = i < npix ? i : i - npix;
-        const double w = i < npix ? u : v;
+    for (int i = threadIdx.x; i < 2 * KT * npix; i += blockDim.x) {
+        const int rowf = i >= KT * npix;               // row factors follow the column ones
+        const int q = rowf ? i - KT * npix : i;
+        const int kk = q / npix, p = q - kk * npix;
+        const int k = min(k0 + kk, nuv - 1);           // a partial last tile repeats a point
+        const double w = uv[2 * k + rowf];
         double cyc = w * (a0 + da * (double)p);        // cycles
         cyc -= rint(cyc);                              // [-1/2, 1/2]
-        float s, c;
-        sincospif((float)(-2.0 * cyc), &s, &c);
-        tab[i] = make_float2(c, s);
+        float sn, cs;
+        sincospif((float)(-2.0 * cyc), &sn, &cs);
+        tab[i] = make_float2(cs, sn);
     }
     __syncthreads();
     const float* I = images + (size_t)img * npix * npix;
+    const float2* col = tab;
+    const float2* row = tab + KT * npix;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    double re = 0.0, im = 0.0;
+    double re[KT], im[KT];
+#pragma unroll
+    for (int kk = 0; kk < KT; ++kk) { re[kk] = 0.0; im[kk] = 0.0; }
     for (int y = warp; y < npix; y += nw) {
-        float sr = 0.f, si = 0.f;
+        float sr[KT], si[KT];
+#pragma unroll
+        for (int kk = 0; kk < KT; ++kk) { sr[kk] = 0.f; si[kk] = 0.f; }
         for (int x = lane; x < npix; x += 32) {
             const float q = I[(size_t)y * npix + x];
-            sr += q * tab[x].x;
-            si += q * tab[x].y;
+#pragma unroll
+            for (int kk = 0; kk < KT; ++kk) {
+                const float2 c = col[kk * npix + x];
+                sr[kk] += q * c.x;
+                si[kk] += q * c.y;
+            }
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            sr += __shfl_xor_sync(0xffffffffu, sr, o);
-            si += __shfl_xor_sync(0xffffffffu, si, o);
+        for (int kk = 0; kk < KT; ++kk) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                sr[kk] += __shfl_xor_sync(0xffffffffu, sr[kk], o);
+                si[kk] += __shfl_xor_sync(0xffffffffu, si[kk], o);
+            }
         }
         if (lane == 0) {
-            const float2 r = tab[npix + y];
-            re += (double)sr * r.x - (double)si * r.y;
-            im += (double)sr * r.y + (double)si * r.x;
+#pragma unroll
+            for (int kk = 0; kk < KT; ++kk) {
+                const float2 r = row[kk * npix + y];
+                re[kk] += (double)sr[kk] * r.x - (double)si[kk] * r.y;
+                im[kk] += (double)sr[kk] * r.y + (double)si[kk] * r.x;
+            }
         }
     }
-    __shared__ double red[2][32];
-    if (lane == 0) { red[0][warp] = re; red[1][warp] = im; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double R = 0.0, M = 0.0;
-        for (int w = 0; w < nw; ++w) { R += red[0][w]; M += red[1][w]; }
-        vis[2 * ((size_t)img * nuv + k)] = R * scale[cam];
-        vis[2 * ((size_t)img * nuv + k) + 1] = M * scale[cam];
+    __shared__ double red[2][KT][32];
+    if (lane == 0) {
+#pragma unroll
+        for (int kk = 0; kk < KT; ++kk) { red[0][kk][warp] = re[kk]; red[1][kk][warp] = im[kk]; }
     }
+    __syncthreads();
+    if (threadIdx.x < KT && k0 + (int)threadIdx.x < nuv) {
+        const int kk = threadIdx.x;
+        double R = 0.0, M = 0.0;
+        for (int w = 0; w < nw; ++w) { R += red[0][kk][w]; M += red[1][kk][w]; }
+        vis[2 * ((size_t)img * nuv + k0 + kk)] = R * scale[cam];
+        vis[2 * ((size_t)img * nuv + k0 + kk) + 1] = M * scale[cam];
+    }
+}
+
+template <int KT>
+rt_status launch_vis(const float* images, int npix, const double* d, int ncam, int nf, int nuv,
+                     double* vis, cudaStream_t s)
+{
+    const size_t smem = sizeof(float2) * 2 * KT * (size_t)npix;
+    if (smem > 48 * 1024)
+        RT_CUDA(cudaFuncSetAttribute(visibility_kernel<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid((unsigned)((nuv + KT - 1) / KT), (unsigned)(ncam * nf));
+    visibility_kernel<KT><<<grid, 256, smem, s>>>(images, npix, d, d + ncam, d + 2 * ncam, nf,
+                                                  d + 3 * ncam, nuv, vis);
+    count_launches();
+    RT_CUDA(cudaGetLastError());
+    return RT_OK;
 }
 
 }  // namespace
@@ -1121,16 +1161,15 @@ rt_status visibilities_impl(rt_ctx* ctx, const rt_grid* g, const rt_camera* cams
     double* d = nullptr;
     RT_CUDA(cudaMallocAsync((void**)&d, sizeof(double) * h.size(), s));
     RT_CUDA(cudaMemcpyAsync(d, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice, s));
-    const size_t smem = sizeof(float2) * 2 * npix;
-    if (smem > 48 * 1024)
-        RT_CUDA(cudaFuncSetAttribute(visibility_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    dim3 grid((unsigned)nuv, (unsigned)(ncam * nf));
-    visibility_kernel<<<grid, 256, smem, s>>>(images, npix, d, d + ncam, d + 2 * ncam, nf,
-                                               d + 3 * ncam, nuv, vis);
-    count_launches();
-    RT_CUDA(cudaGetLastError());
+    // (u, v) points per block: as many as keep the factor tables within
+    // 64 KiB of shared memory (one for the largest images)
+    rt_status st;
+    if (npix <= 512) st = launch_vis<8>(images, npix, d, ncam, nf, nuv, vis, s);
+    else if (npix <= 1024) st = launch_vis<4>(images, npix, d, ncam, nf, nuv, vis, s);
+    else if (npix <= 2048) st = launch_vis<2>(images, npix, d, ncam, nf, nuv, vis, s);
+    else st = launch_vis<1>(images, npix, d, ncam, nf, nuv, vis, s);
     RT_CUDA(cudaFreeAsync(d, s));
-    return RT_OK;
+    return st;
 }
 
 }  // namespace rtgb

@@ -1628,7 +1628,7 @@ rt_status launch_one(rt_ctx* ctx, const TransportKP& kp, int schedule, int threa
 // FP32: instantiate only the feature set a launch needs; FP64 debug: all.
 // The generic variants (every optional path, photon counting included) are
 // FEAT 147 (uniform grid), 179 (+ PAH sources), 211 (+ refinement) and 243
-// (both); photon-counting cameras always run a generic variant.
+// (both); single-model launches with cameras take 140/141.
 template <typename R, int NS>
 rt_status launch_feat(rt_ctx* ctx, const TransportKP& kp, int schedule, int threads,
                       int blocks_per_sm, cudaStream_t s)
@@ -1655,7 +1655,14 @@ rt_status launch_feat(rt_ctx* ctx, const TransportKP& kp, int schedule, int thre
                 return launch_one<R, NS, 44>(ctx, kp, schedule, threads, blocks_per_sm, s);
             return launch_one<R, NS, 179>(ctx, kp, schedule, threads, blocks_per_sm, s);
         }
-        if (kp.n_pc) return launch_one<R, NS, 147>(ctx, kp, schedule, threads, blocks_per_sm, s);
+        if (kp.n_pc) {
+            // cameras: the single-model variants with photon counting compiled in
+            if (kp.single && kp.param_models && !kp.want_traj && !kp.defer_events) {
+                if (kp.mrw) return launch_one<R, NS, 141>(ctx, kp, schedule, threads, blocks_per_sm, s);
+                return launch_one<R, NS, 140>(ctx, kp, schedule, threads, blocks_per_sm, s);
+            }
+            return launch_one<R, NS, 147>(ctx, kp, schedule, threads, blocks_per_sm, s);
+        }
         if (kp.acc32) {
             // the plain-FP32 form: single-model uniform-grid launches only
             if (!kp.single || !kp.param_models || kp.want_traj || kp.defer_events)
