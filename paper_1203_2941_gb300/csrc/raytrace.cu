@@ -1043,22 +1043,23 @@ rt_status raytrace_impl(rt_ctx* ctx, const rt_grid* g, const rt_opacity* op, con
 namespace rtgb {
 namespace {
 
-// Complex visibilities of one image at KT (u, v) points: one block per
-// (image, tile of KT points).  exp(-2 pi i (u alpha + v beta)) separates into
-// a column and a row factor per point, tabulated in shared memory (phases
-// reduced in FP64, then FP32 sine and cosine of pi times a number in
-// [-1, 1)).  A warp takes a row at a time, its lanes stride along the row
-// (coalesced) and keep KT complex row sums in FP32, so each pixel is read
-// once for the KT points; the row sums are reduced by shuffles, multiplied by
-// the row factors and accumulated in FP64.
+// Complex visibilities of one camera's images at KT (u, v) points: one block
+// per (camera, tile of KT points).  exp(-2 pi i (u alpha + v beta))
+// separates into a column and a row factor per point; the block tabulates
+// them once in shared memory (phases reduced in FP64, then FP32 sine and
+// cosine of pi times a number in [-1, 1)) and serves every image frequency
+// of the camera with them.  A warp takes a row at a time, its lanes stride
+// along the row (coalesced) and keep KT complex row sums in FP32, so each
+// pixel is read once per tile; the row sums are reduced by shuffles,
+// multiplied by the row factors and accumulated in FP64.
 template <int KT>
 __global__ void visibility_kernel(const float* images, int npix, const double* alpha0,
                                   const double* dalpha, const double* scale, int nf, const double* uv,
                                   int nuv, double* vis)
 {
     extern __shared__ float2 tab[];                    // [KT][npix] columns, [KT][npix] rows
-    const int img = blockIdx.y, k0 = blockIdx.x * KT;
-    const int cam = img / nf;
+    __shared__ double red[2][KT][32];
+    const int cam = blockIdx.y, k0 = blockIdx.x * KT;
     const double a0 = alpha0[cam], da = dalpha[cam];
     for (int i = threadIdx.x; i < 2 * KT * npix; i += blockDim.x) {
         const int rowf = i >= KT * npix;               // row factors follow the column ones
@@ -1073,55 +1074,58 @@ __global__ void visibility_kernel(const float* images, int npix, const double* a
         tab[i] = make_float2(cs, sn);
     }
     __syncthreads();
-    const float* I = images + (size_t)img * npix * npix;
     const float2* col = tab;
     const float2* row = tab + KT * npix;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    double re[KT], im[KT];
+    for (int f = 0; f < nf; ++f) {
+        const int img = cam * nf + f;
+        const float* I = images + (size_t)img * npix * npix;
+        double re[KT], im[KT];
 #pragma unroll
-    for (int kk = 0; kk < KT; ++kk) { re[kk] = 0.0; im[kk] = 0.0; }
-    for (int y = warp; y < npix; y += nw) {
-        float sr[KT], si[KT];
+        for (int kk = 0; kk < KT; ++kk) { re[kk] = 0.0; im[kk] = 0.0; }
+        for (int y = warp; y < npix; y += nw) {
+            float sr[KT], si[KT];
 #pragma unroll
-        for (int kk = 0; kk < KT; ++kk) { sr[kk] = 0.f; si[kk] = 0.f; }
-        for (int x = lane; x < npix; x += 32) {
-            const float q = I[(size_t)y * npix + x];
+            for (int kk = 0; kk < KT; ++kk) { sr[kk] = 0.f; si[kk] = 0.f; }
+            for (int x = lane; x < npix; x += 32) {
+                const float q = I[(size_t)y * npix + x];
+#pragma unroll
+                for (int kk = 0; kk < KT; ++kk) {
+                    const float2 c = col[kk * npix + x];
+                    sr[kk] += q * c.x;
+                    si[kk] += q * c.y;
+                }
+            }
 #pragma unroll
             for (int kk = 0; kk < KT; ++kk) {
-                const float2 c = col[kk * npix + x];
-                sr[kk] += q * c.x;
-                si[kk] += q * c.y;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    sr[kk] += __shfl_xor_sync(0xffffffffu, sr[kk], o);
+                    si[kk] += __shfl_xor_sync(0xffffffffu, si[kk], o);
+                }
             }
-        }
+            if (lane == 0) {
 #pragma unroll
-        for (int kk = 0; kk < KT; ++kk) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                sr[kk] += __shfl_xor_sync(0xffffffffu, sr[kk], o);
-                si[kk] += __shfl_xor_sync(0xffffffffu, si[kk], o);
+                for (int kk = 0; kk < KT; ++kk) {
+                    const float2 r = row[kk * npix + y];
+                    re[kk] += (double)sr[kk] * r.x - (double)si[kk] * r.y;
+                    im[kk] += (double)sr[kk] * r.y + (double)si[kk] * r.x;
+                }
             }
         }
         if (lane == 0) {
 #pragma unroll
-            for (int kk = 0; kk < KT; ++kk) {
-                const float2 r = row[kk * npix + y];
-                re[kk] += (double)sr[kk] * r.x - (double)si[kk] * r.y;
-                im[kk] += (double)sr[kk] * r.y + (double)si[kk] * r.x;
-            }
+            for (int kk = 0; kk < KT; ++kk) { red[0][kk][warp] = re[kk]; red[1][kk][warp] = im[kk]; }
         }
-    }
-    __shared__ double red[2][KT][32];
-    if (lane == 0) {
-#pragma unroll
-        for (int kk = 0; kk < KT; ++kk) { red[0][kk][warp] = re[kk]; red[1][kk][warp] = im[kk]; }
-    }
-    __syncthreads();
-    if (threadIdx.x < KT && k0 + (int)threadIdx.x < nuv) {
-        const int kk = threadIdx.x;
-        double R = 0.0, M = 0.0;
-        for (int w = 0; w < nw; ++w) { R += red[0][kk][w]; M += red[1][kk][w]; }
-        vis[2 * ((size_t)img * nuv + k0 + kk)] = R * scale[cam];
-        vis[2 * ((size_t)img * nuv + k0 + kk) + 1] = M * scale[cam];
+        __syncthreads();
+        if (threadIdx.x < KT && k0 + (int)threadIdx.x < nuv) {
+            const int kk = threadIdx.x;
+            double R = 0.0, M = 0.0;
+            for (int w = 0; w < nw; ++w) { R += red[0][kk][w]; M += red[1][kk][w]; }
+            vis[2 * ((size_t)img * nuv + k0 + kk)] = R * scale[cam];
+            vis[2 * ((size_t)img * nuv + k0 + kk) + 1] = M * scale[cam];
+        }
+        __syncthreads();                               // red is reused by the next image
     }
 }
 
@@ -1132,7 +1136,7 @@ rt_status launch_vis(const float* images, int npix, const double* d, int ncam, i
     const size_t smem = sizeof(float2) * 2 * KT * (size_t)npix;
     if (smem > 48 * 1024)
         RT_CUDA(cudaFuncSetAttribute(visibility_kernel<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    dim3 grid((unsigned)((nuv + KT - 1) / KT), (unsigned)(ncam * nf));
+    dim3 grid((unsigned)((nuv + KT - 1) / KT), (unsigned)ncam);
     visibility_kernel<KT><<<grid, 256, smem, s>>>(images, npix, d, d + ncam, d + 2 * ncam, nf,
                                                   d + 3 * ncam, nuv, vis);
     count_launches();
