@@ -1051,7 +1051,8 @@ namespace {
 // of the camera with them.  A warp takes a row at a time, its lanes stride
 // along the row (coalesced) and keep KT complex row sums in FP32, so each
 // pixel is read once per tile; the row sums are reduced by shuffles,
-// multiplied by the row factors and accumulated in FP64.
+// multiplied by the row factors and accumulated in FP64, lane k of the warp
+// serving point k.
 template <int KT>
 __global__ void visibility_kernel(const float* images, int npix, const double* alpha0,
                                   const double* dalpha, const double* scale, int nf, const double* uv,
@@ -1080,9 +1081,7 @@ __global__ void visibility_kernel(const float* images, int npix, const double* a
     for (int f = 0; f < nf; ++f) {
         const int img = cam * nf + f;
         const float* I = images + (size_t)img * npix * npix;
-        double re[KT], im[KT];
-#pragma unroll
-        for (int kk = 0; kk < KT; ++kk) { re[kk] = 0.0; im[kk] = 0.0; }
+        double re = 0.0, im = 0.0;                     // lane kk < KT: point kk of the tile
         for (int y = warp; y < npix; y += nw) {
             float sr[KT], si[KT];
 #pragma unroll
@@ -1104,19 +1103,20 @@ __global__ void visibility_kernel(const float* images, int npix, const double* a
                     si[kk] += __shfl_xor_sync(0xffffffffu, si[kk], o);
                 }
             }
-            if (lane == 0) {
+            // every lane holds every sum after the butterfly; lane kk takes
+            // point kk, so the FP64 row products of the KT points issue as
+            // one warp instruction each (GB300's FP64 pipe is narrow)
+            float mr = 0.f, mi = 0.f;
 #pragma unroll
-                for (int kk = 0; kk < KT; ++kk) {
-                    const float2 r = row[kk * npix + y];
-                    re[kk] += (double)sr[kk] * r.x - (double)si[kk] * r.y;
-                    im[kk] += (double)sr[kk] * r.y + (double)si[kk] * r.x;
-                }
+            for (int kk = 0; kk < KT; ++kk)
+                if (lane == kk) { mr = sr[kk]; mi = si[kk]; }
+            if (lane < KT) {
+                const float2 r = row[lane * npix + y];
+                re += (double)mr * r.x - (double)mi * r.y;
+                im += (double)mr * r.y + (double)mi * r.x;
             }
         }
-        if (lane == 0) {
-#pragma unroll
-            for (int kk = 0; kk < KT; ++kk) { red[0][kk][warp] = re[kk]; red[1][kk][warp] = im[kk]; }
-        }
+        if (lane < KT) { red[0][lane][warp] = re; red[1][lane][warp] = im; }
         __syncthreads();
         if (threadIdx.x < KT && k0 + (int)threadIdx.x < nuv) {
             const int kk = threadIdx.x;
