@@ -50,7 +50,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--forms", default="", help="measure other forms instead of the step: "
-                    "all or a comma list of fp64_debug, mrw_disk, adjoint, batched")
+                    "all or a comma list of fp64_debug, plain_fp32, mrw_disk, adjoint, batched, "
+                    "refined_shell, next_rows")
     return ap.parse_args()
 
 
@@ -557,6 +558,7 @@ def run_reference(a):
     O.transport(om, N, seed=7, pid_begin=0, pid_end=100, mode=O.MODE_BW)
     per = (time.perf_counter() - t0) / 100
     n = max(100, int(6.0 / max(per, 1e-6)))
+    n = max(1, min(n, N // max(1, a.warmup + a.steps)))     # the samples stay inside [0, N)
     cross, times = 0, []
     for i in range(a.warmup + a.steps):
         t0 = time.perf_counter()
