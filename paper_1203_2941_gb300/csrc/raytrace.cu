@@ -1046,13 +1046,14 @@ namespace {
 // Complex visibilities of one camera's images at KT (u, v) points: one block
 // per (camera, tile of KT points).  exp(-2 pi i (u alpha + v beta))
 // separates into a column and a row factor per point; the block tabulates
-// them once in shared memory (phases reduced in FP64, then FP32 sine and
-// cosine of pi times a number in [-1, 1)) and serves every image frequency
-// of the camera with them.  A warp takes a row at a time, its lanes stride
-// along the row (coalesced) and keep KT complex row sums in FP32, so each
-// pixel is read once per tile; the row sums are reduced by shuffles,
-// multiplied by the row factors and accumulated in FP64, lane k of the warp
-// serving point k.
+// them once in shared memory (phases as exact fixed-point fractions of a
+// cycle, then FP32 sine and cosine of pi times a number in [-1, 1)) and
+// serves every image frequency of the camera with them.  A warp takes a row
+// at a time, its lanes stride along the row (coalesced) and keep KT complex
+// row sums in FP32, so each pixel is read once per tile; the row sums are
+// reduced by shuffles, multiplied by the row factors and accumulated with
+// compensated FP32 sums, lane k of the warp serving point k; the warps'
+// partial sums are added in FP64.
 template <int KT>
 __global__ void visibility_kernel(const float* images, int npix, const double* alpha0,
                                   const double* dalpha, const double* scale, int nf, const double* uv,
@@ -1060,18 +1061,31 @@ __global__ void visibility_kernel(const float* images, int npix, const double* a
 {
     extern __shared__ float2 tab[];                    // [KT][npix] columns, [KT][npix] rows
     __shared__ double red[2][KT][32];
+    __shared__ unsigned long long ph0[2 * KT], dph[2 * KT];
     const int cam = blockIdx.y, k0 = blockIdx.x * KT;
-    const double a0 = alpha0[cam], da = dalpha[cam];
+    // Phase of pixel p along an axis, in cycles: w (a0 + da p) = w a0 + p (w da).
+    // Both terms are reduced mod 1 once per point in FP64 and kept as 64-bit
+    // fixed-point fractions, so the per-pixel phases are exact integer
+    // sums mod 1 (resolution 2^-64 cycle; 2^-32 after the cut to 32 bits)
+    // and need no FP64 work.
+    if (threadIdx.x < 2 * KT) {
+        const int rowf = threadIdx.x >= KT, kk = threadIdx.x - (rowf ? KT : 0);
+        const int k = min(k0 + kk, nuv - 1);           // a partial last tile repeats a point
+        const double w = uv[2 * k + rowf];
+        const double c0 = w * alpha0[cam], d = w * dalpha[cam];
+        ph0[threadIdx.x] = __double2ull_rn((c0 - floor(c0)) * 18446744073709551616.0);
+        dph[threadIdx.x] = __double2ull_rn((d - floor(d)) * 18446744073709551616.0);
+    }
+    __syncthreads();
     for (int i = threadIdx.x; i < 2 * KT * npix; i += blockDim.x) {
         const int rowf = i >= KT * npix;               // row factors follow the column ones
         const int q = rowf ? i - KT * npix : i;
         const int kk = q / npix, p = q - kk * npix;
-        const int k = min(k0 + kk, nuv - 1);           // a partial last tile repeats a point
-        const double w = uv[2 * k + rowf];
-        double cyc = w * (a0 + da * (double)p);        // cycles
-        cyc -= rint(cyc);                              // [-1/2, 1/2]
+        const int slot = rowf * KT + kk;
+        const unsigned long long cyc = ph0[slot] + (unsigned long long)p * dph[slot];   // mod 1
+        const float x = (float)(int)(unsigned)(cyc >> 32) * 2.3283064365386963e-10f;   // [-1/2, 1/2)
         float sn, cs;
-        sincospif((float)(-2.0 * cyc), &sn, &cs);
+        sincospif(-2.0f * x, &sn, &cs);
         tab[i] = make_float2(cs, sn);
     }
     __syncthreads();
@@ -1081,7 +1095,7 @@ __global__ void visibility_kernel(const float* images, int npix, const double* a
     for (int f = 0; f < nf; ++f) {
         const int img = cam * nf + f;
         const float* I = images + (size_t)img * npix * npix;
-        double re = 0.0, im = 0.0;                     // lane kk < KT: point kk of the tile
+        float re = 0.f, rec = 0.f, im = 0.f, imc = 0.f;   // lane kk < KT: point kk, compensated
         for (int y = warp; y < npix; y += nw) {
             float sr[KT], si[KT];
 #pragma unroll
@@ -1104,19 +1118,21 @@ __global__ void visibility_kernel(const float* images, int npix, const double* a
                 }
             }
             // every lane holds every sum after the butterfly; lane kk takes
-            // point kk, so the FP64 row products of the KT points issue as
-            // one warp instruction each (GB300's FP64 pipe is narrow)
+            // point kk and adds the row product with a compensated FP32 sum
             float mr = 0.f, mi = 0.f;
 #pragma unroll
             for (int kk = 0; kk < KT; ++kk)
                 if (lane == kk) { mr = sr[kk]; mi = si[kk]; }
             if (lane < KT) {
                 const float2 r = row[lane * npix + y];
-                re += (double)mr * r.x - (double)mi * r.y;
-                im += (double)mr * r.y + (double)mi * r.x;
+                kahan_add(re, rec, mr * r.x - mi * r.y);
+                kahan_add(im, imc, mr * r.y + mi * r.x);
             }
         }
-        if (lane < KT) { red[0][lane][warp] = re; red[1][lane][warp] = im; }
+        if (lane < KT) {
+            red[0][lane][warp] = (double)re - (double)rec;
+            red[1][lane][warp] = (double)im - (double)imc;
+        }
         __syncthreads();
         if (threadIdx.x < KT && k0 + (int)threadIdx.x < nuv) {
             const int kk = threadIdx.x;
