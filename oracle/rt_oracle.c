@@ -19,8 +19,9 @@
  * (Sect. 3.1, Eq. 9) and the modified random walk in very thick cells
  * (Sect. 3.2).  The ray tracer follows Sect. 4 (Eqs. 11-17).
  *
- * Parity status of each function is listed in the test suite; functions whose
- * only check is the CUDA path are marked "parity unpinned" below.
+ * Each function is pinned by the CPU tests against closed forms, brute
+ * force, invariants or the paper's printed values; none is marked "parity
+ * unpinned".
  */
 #include "rt_oracle.h"
 
@@ -971,7 +972,7 @@ void or_temperatures(const or_model* m, const double* E_abs, double* T)
 
 /* Initial guess of the iterative scheme: optically thin gray dust around
  * the sources, T^4 = sum L / (16 pi sigma r^2), capped at 2000 K; cells at the
- * source position take the cap.  Parity unpinned beyond its closed form. */
+ * source position take the cap. */
 void or_temperature_guess(const or_model* m, const or_source* src, int nsrc, double* T)
 {
     const double sigma = 2.0 * pow(OR_PI, 5) * pow(OR_K, 4) / (15.0 * pow(OR_H, 3) * OR_C * OR_C);

@@ -730,3 +730,38 @@ def test_refined_adjoint_matches_central_differences(O):
         tested += 1
     assert tested >= 3
     assert gs == pytest.approx(float((base.astype(np.float64) * g).sum()), rel=1e-12)
+
+
+def test_temperature_guess_closed_form(O):
+    """The optically thin starting guess: T^4 = sum_i L_i / (16 pi sigma r_i^2)
+    at each cell centre (sigma from CODATA, not from the oracle's Planck
+    constants), capped at 2000 K; on a refined grid at each sub-cube centre."""
+    m = W.uniform_cube(n=5, tau_cell=0.1, side_au=40.0, source_pos=(0.3 * W.AU, -0.2 * W.AU, 0.1 * W.AU))
+    m.sources.append(W.Source((-6.0 * W.AU, 5.0 * W.AU, 2.0 * W.AU), 3.0 * W.LSUN, 4000.0))
+    mask = np.zeros(m.shape, bool)
+    mask[2, 2, 2] = mask[0, 4, 1] = True
+    mr = W.refine_cubes(m, mask, r=3)
+    for mm in (m, mr):
+        T = O.temperature_guess(mm)
+        nz, ny, nx = mm.shape
+        centres = []
+        for cz in range(nz):
+            for cy in range(ny):
+                for cx in range(nx):
+                    lo = mm.box_min + mm.cell * np.array([cx, cy, cz])
+                    if mm.refine and mm.refined[cz, cy, cx]:
+                        h = mm.cell / mm.refine
+                        for sz in range(mm.refine):
+                            for sy in range(mm.refine):
+                                for sx in range(mm.refine):
+                                    centres.append(lo + h * (np.array([sx, sy, sz]) + 0.5))
+                    else:
+                        centres.append(lo + 0.5 * mm.cell)
+        centres = np.array(centres)
+        assert len(centres) == mm.ncell
+        q = np.zeros(mm.ncell)
+        for s in mm.sources:
+            r2 = ((centres - np.asarray(s.pos)) ** 2).sum(axis=1)
+            q += s.L / (16 * math.pi * SIGMA * r2)
+        expect = np.minimum(q ** 0.25, 2000.0)
+        np.testing.assert_allclose(T[0], expect, rtol=1e-9)
