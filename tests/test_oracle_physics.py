@@ -621,12 +621,17 @@ def test_pah_reemission_frequency_law_per_class(O):
         assert r["sed_esc"].sum() == pytest.approx(len(rec) * 1.0, rel=1e-12)
 
 
-def test_pah_reemission_positions_and_directions(O):
-    """Emission points lie in the record's cell, uniform per axis (mean 1/2,
-    variance 1/12 of the cell); directions isotropic (<k> = 0,
-    <k_a^2> = 1/3)."""
+@pytest.mark.parametrize("refined", [False, True])
+def test_pah_reemission_positions_and_directions(O, refined):
+    """Emission points lie in the record's cell (a sub-cube on a refined
+    grid), uniform per axis (mean 1/2, variance 1/12 of the cell edge);
+    directions isotropic (<k> = 0, <k_a^2> = 1/3)."""
     m = W.random_grid(n=(5, 4, 3), ns=1, seed=2)
     m.rho[:] = 0.0
+    if refined:
+        mask = np.zeros(m.rho.shape[1:], bool)
+        mask[1, 2, 3] = mask[2, 0, 0] = True
+        m = W.refine_cubes(m, mask, r=3)
     eps, _ = W.pah_emissivity(m, n_classes=1)
     rng = np.random.default_rng(1)
     rec = np.zeros(6000, O.PAH_DTYPE)
@@ -637,8 +642,24 @@ def test_pah_reemission_positions_and_directions(O):
     assert len(em) == len(rec)
     c = rec["cell"][em["pid"]].astype(np.int64)
     nz, ny, nx = m.shape
-    idx = np.stack([c % nx, (c // nx) % ny, c // (nx * ny)], axis=1)
-    f = (em["x"] - m.box_min[None, :]) / m.cell - idx
+    # lower corner and edge of every cell, from the model's cell numbering
+    lo_all, h_all = [], []
+    for q in range(nx * ny * nz):
+        cz, cy, cx = q // (nx * ny), (q // nx) % ny, q % nx
+        base = m.box_min + m.cell * np.array([cx, cy, cz])
+        if refined and m.refined[cz, cy, cx]:
+            h = m.cell / m.refine
+            for sz in range(m.refine):
+                for sy in range(m.refine):
+                    for sx in range(m.refine):
+                        lo_all.append(base + h * np.array([sx, sy, sz]))
+                        h_all.append(h)
+        else:
+            lo_all.append(base)
+            h_all.append(m.cell)
+    lo_all, h_all = np.array(lo_all), np.array(h_all)
+    assert len(h_all) == m.ncell
+    f = (em["x"] - lo_all[c]) / h_all[c][:, None]
     assert np.all((f >= 0) & (f <= 1))
     n = len(f)
     assert np.all(np.abs(f.mean(axis=0) - 0.5) <= 5 * math.sqrt(1 / 12 / n))
