@@ -352,3 +352,39 @@ def test_refined_images_equal_unrefined_for_inherited_fields(O):
     ib, sb = O.raytrace(mr, np.repeat(T, per, axis=1), ev, 1.0, cams, [1, 4, 6])
     np.testing.assert_allclose(ib, ia, rtol=1e-9, atol=1e-12 * np.abs(ia).max())
     np.testing.assert_allclose(sb, sa, rtol=1e-9)
+
+
+def test_refined_mrw_sphere_stays_in_the_sub_cube(O):
+    """Modified random walk on a refined grid (Sect. 3.2 with sub-cubes):
+    every MRW step ends inside the cell it started in -- the sphere is the
+    largest one inside the sub-cube, not inside its cube -- and the walk is
+    taken in thick sub-cubes."""
+    m0 = W.uniform_cube(n=4, tau_cell=60.0, nf=6, albedo=0.3)
+    mask = np.zeros(m0.shape, bool)
+    mask[1:3, 1:3, 1:3] = True
+    m = W.refine_cubes(m0, mask, r=2)
+    r = O.transport(m, 60, seed=3, mode=O.MODE_BW, mrw=True, mrw_tau_cell=3.0, mrw_gamma=1.0,
+                    traj_cap=2_000_000)
+    t = r["traj"]
+    assert r["stats"]["mrw_steps"] > 0 and r["stats"]["traj_dropped"] == 0
+    nz, ny, nx = m.shape
+    lo_all, h_all = [], []
+    for q in range(nx * ny * nz):
+        cz, cy, cx = q // (nx * ny), (q // nx) % ny, q % nx
+        base = m.box_min + m.cell * np.array([cx, cy, cz])
+        if m.refined[cz, cy, cx]:
+            h = m.cell / 2
+            for sz in range(2):
+                for sy in range(2):
+                    for sx in range(2):
+                        lo_all.append(base + h * np.array([sx, sy, sz]))
+                        h_all.append(h)
+        else:
+            lo_all.append(base)
+            h_all.append(m.cell)
+    lo_all, h_all = np.array(lo_all), np.array(h_all)
+    mrw = t[t["type"] == O.T_MRW]
+    fine = h_all[mrw["cell"]] < m.cell
+    assert fine.sum() > 0 and (~fine).sum() > 0
+    f = (mrw["x"] - lo_all[mrw["cell"]]) / h_all[mrw["cell"]][:, None]
+    assert np.all((f >= -1e-12) & (f <= 1 + 1e-12))
