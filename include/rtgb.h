@@ -203,6 +203,13 @@ typedef struct {
     const rt_pc_camera* pc_cams;  /* host [n_pc_cams] photon-counting cameras
                                  (rt_transport only; NULL with 0 = none) */
     int n_pc_cams;            /* 0..16 (rt_transport only) */
+    const uint32_t* record_nu_mask;  /* host bitmask over the frequency bins,
+                                 bit j = (mask[j / 32] >> (j % 32)) & 1: with
+                                 record_events, a scattering event is stored only
+                                 when the packet's bin j is set (the image
+                                 frequencies of the ray tracer, whose scattering
+                                 source, Eq. 16, uses events at those frequencies
+                                 alone); NULL = every bin.  (n_freq + 31) / 32 words */
 } rt_transport_params;
 
 /* Fill p with the defaults: B&W, Lucy THIN at 1e-2, linear form, MRW off
@@ -349,7 +356,9 @@ RT_API rt_status rt_pah_reemit(rt_ctx* ctx, const rt_grid* grid, const rt_opacit
  * share the one array: calls whose GPU work overlaps (different streams
  * without ordering, or several host threads) race and must not be issued;
  * calls ordered on one stream are safe (each clears what must start at zero).
- * Photon-counting cameras are not served here (n_pc_cams must be 0). */
+ * Photon-counting cameras, the deferred-packet queue and the plain-FP32 form
+ * are not served here: n_pc_cams and defer_events must be 0 and precision not
+ * RT_PREC_FP32_ACC32, else RT_ERR_INVALID_ARG. */
 RT_API rt_status rt_transport_noalloc(rt_ctx* ctx, const rt_grid* grid, const rt_opacity* opac,
                                       const rt_source* sources, int n_sources,
                                       const rt_transport_params* p, const double* T_prev,
@@ -489,6 +498,31 @@ RT_API uint64_t rt_kernel_launches(void);
  * keeps ctr0[0] + n below 2^32).  out: device uint32 [4n]. */
 RT_API rt_status rt_philox(rt_ctx* ctx, const uint32_t ctr0[4], const uint32_t key[2], uint64_t n,
                     uint32_t* out, rt_stream stream);
+
+/* The modified random walk's path-length law as the FP32 transport draws it
+ * (Sect. 3.2; Fleck & Canfield 1984): for i < n, y[i] is the dimensionless
+ * first-passage time the FP32 kernel takes for the uniform u[i] in (0, 1] --
+ * the y with S(y) = u, S(y) = 2 sum_{k>=1} (-1)^(k+1) exp(-k^2 pi^2 y) the
+ * probability that a walker started at the centre of a sphere has not yet
+ * reached its surface, interpolated in the opacity's FP32 table of S
+ * (2048 nodes on 0 <= y <= 2; beyond, the one-term tail ln(2/u)/pi^2); the
+ * path length of an MRW step is l = 3 chi R0^2 y.  u, y: device float [n].
+ * Test hook: lets the FP32 draws be checked against the series. */
+RT_API rt_status rt_mrw_sample(rt_ctx* ctx, const rt_opacity* opac, const float* u, uint64_t n,
+                               float* y, rt_stream stream);
+
+/* Memory-level probe (no counterpart in the paper): n_reads reads of one
+ * 4-byte word each, at pseudo-random 32-byte sectors of buf[0, bytes),
+ * spread over every SM (8 blocks of 256 threads each), the access pattern of
+ * the transport's per-crossing density gathers.  Timed by the caller (CUDA
+ * events on `stream`), n_reads * 32 bytes over the time is the sector
+ * bandwidth that the memory level holding the buffer serves to such gathers:
+ * the L2 for a buffer well inside it, HBM for one far larger.  buf: device,
+ * 32-byte aligned, bytes >= 32 (and below 128 GiB); sink: device uint64 or
+ * NULL, incremented only on an impossible checksum (keeps the reads live).
+ * Errors: RT_ERR_INVALID_ARG for a bad buffer. */
+RT_API rt_status rt_probe_gather(rt_ctx* ctx, const void* buf, size_t bytes, uint64_t n_reads,
+                                 uint32_t seed, unsigned long long* sink, rt_stream stream);
 
 #ifdef __cplusplus
 }

@@ -542,6 +542,15 @@ static void fill_kp(TransportKP& kp, const rt_opacity* op, const rt_transport_pa
     kp.lucy_form = p->lucy_form;
     kp.mrw = p->mrw;
     kp.record_events = p->record_events;
+    for (int w = 0; w < kMaxFreq / 32; ++w) {
+        uint32_t bits = 0u;
+        for (int b = 0; b < 32; ++b) {
+            const int j = 32 * w + b;
+            if (j < op->nf && (!p->record_nu_mask || ((p->record_nu_mask[j / 32] >> (j % 32)) & 1u)))
+                bits |= 1u << b;
+        }
+        kp.ev_mask[w] = bits;
+    }
     kp.pah_mask = 0;
     for (int s = 0; s < op->ns; ++s)
         if (op->is_pah[s]) kp.pah_mask |= 1 << s;
@@ -1122,6 +1131,8 @@ rt_status rt_transport_noalloc(rt_ctx* ctx, const rt_grid* grid, const rt_opacit
         return fail(RT_ERR_INVALID_ARG, "rt_transport_noalloc: photon-counting cameras are served by rt_transport only");
     if (p->precision == RT_PREC_FP32_ACC32)
         return fail(RT_ERR_INVALID_ARG, "rt_transport_noalloc: the plain-FP32 form is served by rt_transport only");
+    if (p->defer_events != 0)
+        return fail(RT_ERR_INVALID_ARG, "rt_transport_noalloc: the deferred-packet queue (defer_events) is served by rt_transport only");
     if (p->mode == RT_MODE_FROZEN_T && !T_prev)
         return fail(RT_ERR_INVALID_ARG, "rt_transport_noalloc: frozen-T mode needs T_prev");
     // scratch layout: staging | kext | packed density | FP64 energy scratch
@@ -1179,6 +1190,27 @@ rt_status rt_philox(rt_ctx* ctx, const uint32_t ctr0[4], const uint32_t key[2], 
     if ((uint64_t)ctr0[0] + n > 0x100000000ull) return fail(RT_ERR_INVALID_ARG, "rt_philox: counter word 0 would wrap");
     RT_CUDA(cudaSetDevice(ctx->device));
     return launch_philox(ctr0, key, n, out, (cudaStream_t)stream);
+}
+
+rt_status rt_probe_gather(rt_ctx* ctx, const void* buf, size_t bytes, uint64_t n_reads, uint32_t seed,
+                          unsigned long long* sink, rt_stream stream)
+{
+    if (!ctx || ctx->magic != kMagic) return fail(RT_ERR_STATE, "rt_probe_gather: bad context");
+    if (!buf || bytes < 32) return fail(RT_ERR_INVALID_ARG, "rt_probe_gather: need a buffer of at least 32 bytes");
+    if (reinterpret_cast<uintptr_t>(buf) % 32 != 0) return fail(RT_ERR_INVALID_ARG, "rt_probe_gather: buffer not 32-byte aligned");
+    if (bytes / 32 > 0xFFFFFFFFull) return fail(RT_ERR_INVALID_ARG, "rt_probe_gather: buffer above 128 GiB");
+    RT_CUDA(cudaSetDevice(ctx->device));
+    return launch_gather_probe(ctx->num_sms, buf, bytes, n_reads, seed, sink, (cudaStream_t)stream);
+}
+
+rt_status rt_mrw_sample(rt_ctx* ctx, const rt_opacity* op, const float* u, uint64_t n, float* y,
+                        rt_stream stream)
+{
+    if (!ctx || ctx->magic != kMagic) return fail(RT_ERR_STATE, "rt_mrw_sample: bad context");
+    if (!op || op->ctx != ctx) return fail(RT_ERR_STATE, "rt_mrw_sample: opacity from another context");
+    if (n > 0 && (!u || !y)) return fail(RT_ERR_INVALID_ARG, "rt_mrw_sample: NULL pointer");
+    RT_CUDA(cudaSetDevice(ctx->device));
+    return launch_mrw_sample(op->d_mrwS, u, n, y, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -27,10 +27,74 @@ namespace {
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kCamChunk = 16;
 
+// Pixel rays walk the grid in FP32 with double-float face times.  A face
+// time of axis a is affine in the face index, t_a(k) = t_a(0) + k/|d_a|, so
+// the walk keeps, per axis, the time of the next face as an unevaluated sum
+// hi + lo of two floats (about 48 significant bits) and advances it by the
+// double-float 1/|d_a| when the ray crosses that face; the chord of a cell is
+// the difference of two such times, rounded once to FP32.  Chords are then
+// exact to about 1e-12 cell edges however far the ray has marched, which
+// keeps even the short chords of rays clipping a cell's corner accurate: a
+// plain FP32 walk (one float per face time, or per distance to a face) lets
+// the rounding of the direction and of each step accumulate to about 1e-7
+// edges within a few dozen cells.  The entry point, cell and first face times
+// are computed in FP64 once per ray.
+struct DF {
+    float hi, lo;
+};
+
+__host__ __device__ __forceinline__ DF df_of(double v)
+{
+    DF r;
+    r.hi = (float)v;
+    r.lo = (float)(v - (double)r.hi);
+    return r;
+}
+
+// a + b (two-sum of the high parts, then the low parts; renormalised)
+__host__ __device__ __forceinline__ DF df_add(DF a, DF b)
+{
+    const float s = a.hi + b.hi;
+    const float bb = s - a.hi;
+    const float e = (a.hi - (s - bb)) + (b.hi - bb);
+    const float lo = e + (a.lo + b.lo);
+    DF r;
+    r.hi = s + lo;
+    r.lo = lo - (r.hi - s);
+    return r;
+}
+
+// a - m b for a small non-negative integer m (exact product error by fma)
+__host__ __device__ __forceinline__ DF df_sub_mul(DF a, float m, DF b)
+{
+    const float p = m * b.hi;
+    const float pe = fmaf(m, b.hi, -p) + m * b.lo;
+    DF nb;
+    nb.hi = -p;
+    nb.lo = -pe;
+    return df_add(a, nb);
+}
+
+// a - b rounded to FP32
+__host__ __device__ __forceinline__ float df_diff(DF a, DF b) { return (a.hi - b.hi) + (a.lo - b.lo); }
+
+// a <= b
+__host__ __device__ __forceinline__ bool df_le(DF a, DF b) { return a.hi < b.hi || (a.hi == b.hi && a.lo <= b.lo); }
+
+// Per-camera walk constants: 1/|d_a| and 1/(r |d_a|) (sub-cube face spacing)
+// as double-floats, |d_a| r in FP32, and the axes marched towards -axis.
+struct WalkCam {
+    DF td[3], tds[3];
+    float adr[3];              // r |d_a|: time to sub-edges along axis a
+};
+
 struct CamDev {
-    float kobs[3], ex[3], ey[3];
-    float pix_cell;      // pixel size in cells
-    double apix_d2;      // A_pix / D^2
+    double k[3], ex[3], ey[3]; // observer direction and image axes (FP64: ray set-up)
+    double ik[3];              // 1 / k_a (0 when k_a = 0)
+    double pix_cell;           // pixel size in cells
+    double apix_d2;            // A_pix / D^2
+    WalkCam wc;                // double-float face spacings of the FP32 walk
+    unsigned negf, negr;       // axes marched towards -axis: forward (along -k), reverse (along +k)
     int npix;
 };
 
@@ -90,85 +154,6 @@ __device__ __forceinline__ float dphi_f(float x)
 {
     if (x < 1e-2f) return -0.5f + x * (1.0f / 3.0f) - x * x * 0.125f;
     return (expf(-x) * (1.0f + x) - 1.0f) / (x * x);
-}
-
-// Ray set-up: origin of pixel (ix, iy) in cell units, box span along kobs.
-struct Ray {
-    float p[3], d[3];          // start point (cell units) and march direction (-kobs)
-    int i[3];
-    float tm[3], td[3];
-    bool hit;
-};
-
-__device__ __forceinline__ void setup_dda(Ray& r, int nx, int ny, int nz)
-{
-    const int n[3] = { nx, ny, nz };
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const float f = floorf(r.p[a]);
-        int i = (int)f;
-        if (f == r.p[a] && r.d[a] < 0.0f) i -= 1;
-        r.i[a] = min(max(i, 0), n[a] - 1);
-        if (r.d[a] > 0.0f) {
-            r.td[a] = 1.0f / r.d[a];
-            r.tm[a] = fmaxf(((float)(r.i[a] + 1) - r.p[a]) / r.d[a], 0.0f);
-        } else if (r.d[a] < 0.0f) {
-            r.td[a] = -1.0f / r.d[a];
-            r.tm[a] = fmaxf(((float)r.i[a] - r.p[a]) / r.d[a], 0.0f);
-        } else {
-            r.td[a] = INFINITY;
-            r.tm[a] = INFINITY;
-        }
-    }
-}
-
-// rays from the observer: start on the near face, march along -kobs;
-// reverse = true starts on the far face and marches along +kobs
-__device__ __forceinline__ Ray pixel_ray(const CamDev& cm, int ix, int iy, int nx, int ny, int nz,
-                                         bool reverse)
-{
-    Ray r;
-    const float xp = ((float)ix + 0.5f - 0.5f * cm.npix) * cm.pix_cell;
-    const float yp = ((float)iy + 0.5f - 0.5f * cm.npix) * cm.pix_cell;
-    const float n[3] = { (float)nx, (float)ny, (float)nz };
-    float o[3];
-    float lo = -INFINITY, hi = INFINITY;
-    bool hit = true;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        o[a] = 0.5f * n[a] + xp * cm.ex[a] + yp * cm.ey[a];
-        const float k = cm.kobs[a];
-        if (k != 0.0f) {
-            float s1 = (0.0f - o[a]) / k, s2 = (n[a] - o[a]) / k;
-            if (s1 > s2) { const float t = s1; s1 = s2; s2 = t; }
-            lo = fmaxf(lo, s1);
-            hi = fminf(hi, s2);
-        } else if (o[a] < 0.0f || o[a] > n[a]) {
-            hit = false;
-        }
-    }
-    r.hit = hit && (lo < hi);
-    const float s0 = reverse ? lo : hi;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        r.p[a] = o[a] + s0 * cm.kobs[a];
-        r.d[a] = reverse ? cm.kobs[a] : -cm.kobs[a];
-    }
-    if (r.hit) setup_dda(r, nx, ny, nz);
-    return r;
-}
-
-// advance to the next cell; returns false when the ray left the grid
-__device__ __forceinline__ bool dda_step(Ray& r, float& tcur, float& seg, int nx, int ny, int nz)
-{
-    const bool ax = (r.tm[0] <= r.tm[1]) && (r.tm[0] <= r.tm[2]);
-    const bool ay = !ax && (r.tm[1] <= r.tm[2]);
-    const float tn = ax ? r.tm[0] : (ay ? r.tm[1] : r.tm[2]);
-    seg = tn - tcur;
-    tcur = tn;
-    if (ax) { r.tm[0] += r.td[0]; r.i[0] += r.d[0] > 0.0f ? 1 : -1; return (unsigned)r.i[0] < (unsigned)nx; }
-    if (ay) { r.tm[1] += r.td[1]; r.i[1] += r.d[1] > 0.0f ? 1 : -1; return (unsigned)r.i[1] < (unsigned)ny; }
-    r.tm[2] += r.td[2]; r.i[2] += r.d[2] > 0.0f ? 1 : -1; return (unsigned)r.i[2] < (unsigned)nz;
 }
 
 // Two-level traversal of a grid with one level of refinement (Sect. 2):
@@ -284,6 +269,208 @@ __device__ __forceinline__ bool rw_step(RefWalk<T>& w, const int* cube, int nx, 
     return true;
 }
 
+struct DFWalk {
+    int i[3];                  // cube indices
+    int sub;                   // refined grids: sub-cube indices, 8 bits per axis, or -1
+    int c;                     // cell number
+    DF tm[3];                  // time of the current cube's exit face per axis; for an axis
+                               // with d_a = 0: {inf, cube-local coordinate} (refined grids)
+    DF t;                      // time at the current point
+};
+
+// Set up from the entry point p (cell units, FP64) and direction d: cube by
+// floor (a coordinate on a face goes to the lower cube when marching towards
+// -axis), clamped into the grid; on a refined grid the sub-cube by the same
+// rule inside the cube.
+__host__ __device__ __forceinline__ void dw_start(DFWalk& w, const double* p, const double* d, int nx,
+                                                  int ny, int nz, const int* cube, int r)
+{
+    const int n[3] = { nx, ny, nz };
+    double q[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const double f = floor(p[a]);
+        int i = (int)f;
+        if (f == p[a] && d[a] < 0.0) i -= 1;
+        i = i < 0 ? 0 : (i > n[a] - 1 ? n[a] - 1 : i);
+        w.i[a] = i;
+        double qa = p[a] - (double)i;
+        qa = qa < 0.0 ? 0.0 : (qa > 1.0 ? 1.0 : qa);
+        q[a] = qa;
+        if (d[a] > 0.0) w.tm[a] = df_of((1.0 - qa) / d[a]);
+        else if (d[a] < 0.0) w.tm[a] = df_of(qa / -d[a]);
+        else { w.tm[a].hi = INFINITY; w.tm[a].lo = (float)qa; }
+    }
+    w.t.hi = 0.0f;
+    w.t.lo = 0.0f;
+    const int q0 = (w.i[2] * ny + w.i[1]) * nx + w.i[0];
+    const int info = cube ? cube[q0] : q0;
+    if (!cube || !(info & kCubeDivided)) {
+        w.sub = -1;
+        w.c = info;
+        return;
+    }
+    int sb[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const double u = q[a] * r;
+        const double f = floor(u);
+        int s = (int)f;
+        if (f == u && d[a] < 0.0) s -= 1;
+        sb[a] = s < 0 ? 0 : (s > r - 1 ? r - 1 : s);
+    }
+    w.sub = sb[0] | (sb[1] << 8) | (sb[2] << 16);
+    w.c = (info & ~kCubeDivided) + (sb[2] * r + sb[1]) * r + sb[0];
+}
+
+// Uniform grid: chord of the current cell (seg) and the step to the next
+// (nearest face, ties to the lowest axis); false when the ray leaves the grid.
+// `neg` has bit a set when the ray marches towards -axis a.
+__host__ __device__ __forceinline__ bool dw_step(DFWalk& w, const WalkCam& wc, unsigned neg, int nx, int ny,
+                                                 int nz, float& seg)
+{
+    const bool a0 = df_le(w.tm[0], w.tm[1]) && df_le(w.tm[0], w.tm[2]);
+    const bool a1 = !a0 && df_le(w.tm[1], w.tm[2]);
+    const int a = a0 ? 0 : (a1 ? 1 : 2);
+    const DF tn = a == 0 ? w.tm[0] : (a == 1 ? w.tm[1] : w.tm[2]);
+    const DF step = a == 0 ? wc.td[0] : (a == 1 ? wc.td[1] : wc.td[2]);
+    seg = fmaxf(df_diff(tn, w.t), 0.0f);
+    w.t = tn;
+    const DF nt = df_add(tn, step);
+    w.tm[0] = a == 0 ? nt : w.tm[0];
+    w.tm[1] = a == 1 ? nt : w.tm[1];
+    w.tm[2] = a == 2 ? nt : w.tm[2];
+    const int sg = (neg >> a) & 1 ? -1 : 1;
+    if (a == 0) { w.i[0] += sg; return (unsigned)w.i[0] < (unsigned)nx; }
+    if (a == 1) { w.i[1] += sg; return (unsigned)w.i[1] < (unsigned)ny; }
+    w.i[2] += sg;
+    return (unsigned)w.i[2] < (unsigned)nz;
+}
+
+// Refined grid: the cube-level face times advance as on a uniform grid of
+// cubes; inside a divided cube the next sub-face along axis b lies m_b
+// sub-cube spacings before the cube's exit face (m_b = sub-faces still
+// ahead).  Leaving a cube enters the next one; when it is divided the
+// sub-cube along the entry axis is the first one met, along the other axes
+// the one holding the crossing point (from its distance to the cube's exit
+// face: a point on a sub-face belongs to the sub-cube ahead of it).
+__host__ __device__ __forceinline__ bool dw_step_ref(DFWalk& w, const WalkCam& wc, unsigned neg,
+                                                     const int* cube, int nx, int ny, int nz, int r,
+                                                     float& seg)
+{
+    DF tf[3];
+    if (w.sub < 0) {
+        tf[0] = w.tm[0]; tf[1] = w.tm[1]; tf[2] = w.tm[2];
+    } else {
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const int s = (w.sub >> (8 * b)) & 255;
+            const int m = ((neg >> b) & 1) ? s : r - 1 - s;
+            tf[b] = (m == 0 || w.tm[b].hi == INFINITY) ? w.tm[b] : df_sub_mul(w.tm[b], (float)m, wc.tds[b]);
+        }
+    }
+    const bool a0 = df_le(tf[0], tf[1]) && df_le(tf[0], tf[2]);
+    const bool a1 = !a0 && df_le(tf[1], tf[2]);
+    const int a = a0 ? 0 : (a1 ? 1 : 2);
+    const DF tn = a == 0 ? tf[0] : (a == 1 ? tf[1] : tf[2]);
+    seg = fmaxf(df_diff(tn, w.t), 0.0f);
+    w.t = tn;
+    const int sg = (neg >> a) & 1 ? -1 : 1;
+    if (w.sub >= 0) {
+        const int sa = ((w.sub >> (8 * a)) & 255) + sg;
+        if (sa >= 0 && sa < r) {
+            w.sub = (w.sub & ~(255 << (8 * a))) | (sa << (8 * a));
+            w.c += sg * (a == 0 ? 1 : (a == 1 ? r : r * r));
+            return true;
+        }
+    }
+    // leave the cube through its face on axis a (selects, not a run-time
+    // index: the walk state stays in registers)
+    const DF nt = df_add(tn, a == 0 ? wc.td[0] : (a == 1 ? wc.td[1] : wc.td[2]));
+    w.tm[0] = a == 0 ? nt : w.tm[0];
+    w.tm[1] = a == 1 ? nt : w.tm[1];
+    w.tm[2] = a == 2 ? nt : w.tm[2];
+    w.i[0] += a == 0 ? sg : 0;
+    w.i[1] += a == 1 ? sg : 0;
+    w.i[2] += a == 2 ? sg : 0;
+    const int ia = a == 0 ? w.i[0] : (a == 1 ? w.i[1] : w.i[2]);
+    const int n_a = a == 0 ? nx : (a == 1 ? ny : nz);
+    if (ia < 0 || ia >= n_a) return false;
+    const int info = cube[(w.i[2] * ny + w.i[1]) * nx + w.i[0]];
+    if (!(info & kCubeDivided)) {
+        w.sub = -1;
+        w.c = info;
+        return true;
+    }
+    int sb[3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        const bool nb = (neg >> b) & 1;
+        int s;
+        if (b == a) {
+            s = nb ? r - 1 : 0;
+        } else if (w.tm[b].hi == INFINITY) {
+            // no motion along b: the sub-cube of the constant coordinate
+            s = (int)floorf(w.tm[b].lo * (float)r);
+        } else {
+            // distance to the cube's exit face along b, in sub-cube edges
+            const float D = df_diff(w.tm[b], w.t) * wc.adr[b];
+            const int m = (int)ceilf(D) - 1;
+            s = nb ? m : r - 1 - m;
+        }
+        sb[b] = s < 0 ? 0 : (s > r - 1 ? r - 1 : s);
+    }
+    w.sub = sb[0] | (sb[1] << 8) | (sb[2] << 16);
+    w.c = (info & ~kCubeDivided) + (sb[2] * r + sb[1]) * r + sb[0];
+    return true;
+}
+
+// Entry point (cell units, FP64) and march direction of the ray of pixel
+// (ix, iy): on the box face nearest the observer, marching along -kobs, or
+// on the far face (reverse), marching along +kobs.  False when the pixel's
+// line misses the box.
+__device__ __forceinline__ bool ray_entry(const CamDev& cm, int ix, int iy, int nx, int ny, int nz,
+                                          bool reverse, double* p, double* d)
+{
+    const double xp = ((double)ix + 0.5 - 0.5 * cm.npix) * cm.pix_cell;
+    const double yp = ((double)iy + 0.5 - 0.5 * cm.npix) * cm.pix_cell;
+    const int n[3] = { nx, ny, nz };
+    double o[3];
+    double lo = -INFINITY, hi = INFINITY;
+    bool hit = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        o[a] = 0.5 * n[a] + xp * cm.ex[a] + yp * cm.ey[a];
+        if (cm.k[a] != 0.0) {
+            double s1 = -o[a] * cm.ik[a], s2 = ((double)n[a] - o[a]) * cm.ik[a];
+            if (s1 > s2) { const double t = s1; s1 = s2; s2 = t; }
+            lo = fmax(lo, s1);
+            hi = fmin(hi, s2);
+        } else if (o[a] < 0.0 || o[a] > (double)n[a]) {
+            hit = false;
+        }
+    }
+    if (!(hit && lo < hi)) return false;
+    const double s0 = reverse ? lo : hi;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        p[a] = o[a] + s0 * cm.k[a];
+        d[a] = reverse ? cm.k[a] : -cm.k[a];
+    }
+    return true;
+}
+
+// start the walk of pixel (ix, iy); false when its line misses the box
+template <bool REF>
+__device__ __forceinline__ bool pixel_walk(DFWalk& w, const CamDev& cm, int ix, int iy, int nx, int ny,
+                                           int nz, const int* cube, int r, bool reverse)
+{
+    double p[3], d[3];
+    if (!ray_entry(cm, ix, iy, nx, ny, nz, reverse, p, d)) return false;
+    dw_start(w, p, d, nx, ny, nz, REF ? cube : nullptr, r);
+    return true;
+}
+
 template <int NS>
 __device__ __forceinline__ void load_rho(const RayKP& P, int c, float* rho)
 {
@@ -307,7 +494,7 @@ __device__ __forceinline__ void load_eta(const float* base, float* eta)
 
 // Forward march.  A ray is served by NFP / 4 consecutive threads, each
 // carrying four image frequencies (one float4 of the emissivity row): the
-// threads repeat the ray's DDA (the same arithmetic, so the same chords) and
+// threads repeat the ray's walk (the same arithmetic, so the same chords) and
 // share its density loads, which keeps the compensated sums of a thread in
 // few registers and the SMs well occupied.
 template <int NS, int NFP, bool REF>
@@ -330,30 +517,28 @@ __global__ void __launch_bounds__(128) ray_fwd_kernel(const __grid_constant__ Ra
 #pragma unroll
         for (int s = 0; s < NS; ++s) ke[s][q] = P.kext[s][4 * g + q];
     }
-    Ray r = pixel_ray(cm, ix, iy, P.nx, P.ny, P.nz, false);
     unsigned nsteps = 0;
-    RefWalk<float> w;
-    if (REF && r.hit) rw_start(w, P.cube, P.nx, P.ny, P.nz, P.refine, r.p, r.d, true);
-    if (r.hit) {
+    DFWalk w;
+    if (pixel_walk<REF>(w, cm, ix, iy, P.nx, P.ny, P.nz, P.cube, P.refine, false)) {
         const float* eta_cam = P.eta + (size_t)cam * P.ncell * P.nfp + 4 * g;
-        float tcur = 0.f, seg;
         const int maxstep = (P.nx + P.ny + P.nz) * (REF ? P.refine : 1) + 4;
         for (int st = 0; st < maxstep; ++st) {
             ++nsteps;
-            const int c = REF ? w.c : (r.i[2] * P.ny + r.i[1]) * P.nx + r.i[0];
+            const int c = REF ? w.c : (w.i[2] * P.ny + w.i[1]) * P.nx + w.i[0];
             float rho[NS];
             load_rho<NS>(P, c, rho);
             const float4 e4 = __ldg(reinterpret_cast<const float4*>(eta_cam + (size_t)c * NFP));
             const float eta[4] = { e4.x, e4.y, e4.z, e4.w };
-            const bool inside = REF ? rw_step(w, P.cube, P.nx, P.ny, P.nz, P.refine, r.p, r.d, tcur, seg)
-                                    : dda_step(r, tcur, seg, P.nx, P.ny, P.nz);
+            float seg;
+            const bool inside = REF ? dw_step_ref(w, cm.wc, cm.negf, P.cube, P.nx, P.ny, P.nz, P.refine, seg)
+                                    : dw_step(w, cm.wc, cm.negf, P.nx, P.ny, P.nz, seg);
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 float chi = 0.f;
 #pragma unroll
                 for (int s = 0; s < NS; ++s) chi += rho[s] * ke[s][q];
                 const float dt = chi * seg;
-                const float contrib = eta[q] * seg * phi_f(dt) * __expf(-tau[q]);
+                const float contrib = eta[q] * seg * phi_f(dt) * expf(-tau[q]);
                 kahan_add(I[q], Ic[q], contrib);
                 kahan_add(tau[q], tc[q], dt);
             }
@@ -394,51 +579,48 @@ __global__ void __launch_bounds__(128) ray_bwd_kernel(const __grid_constant__ Ra
         any = any || v != 0.f;
     }
     if (!any) return;
-    Ray r = pixel_ray(cm, ix, iy, P.nx, P.ny, P.nz, false);
-    if (!r.hit) return;
+    DFWalk w1;
+    if (!pixel_walk<REF>(w1, cm, ix, iy, P.nx, P.ny, P.nz, P.cube, P.refine, false)) return;
     const float* eta_cam = P.eta + (size_t)cam * P.ncell * P.nfp;
     const int maxstep = (P.nx + P.ny + P.nz) * (REF ? P.refine : 1) + 4;
     float tot[NFP], totc[NFP];
     unsigned nsteps = 0;
 #pragma unroll
     for (int f = 0; f < NFP; ++f) { tot[f] = 0.f; totc[f] = 0.f; }
-    {
-        RefWalk<float> w1;
-        if (REF) rw_start(w1, P.cube, P.nx, P.ny, P.nz, P.refine, r.p, r.d, true);
-        float tcur = 0.f, seg;
-        for (int st = 0; st < maxstep; ++st) {
-            ++nsteps;
-            const int c = REF ? w1.c : (r.i[2] * P.ny + r.i[1]) * P.nx + r.i[0];
-            float rho[NS];
-            load_rho<NS>(P, c, rho);
-            const bool inside = REF ? rw_step(w1, P.cube, P.nx, P.ny, P.nz, P.refine, r.p, r.d, tcur, seg)
-                                    : dda_step(r, tcur, seg, P.nx, P.ny, P.nz);
+    for (int st = 0; st < maxstep; ++st) {
+        ++nsteps;
+        const int c = REF ? w1.c : (w1.i[2] * P.ny + w1.i[1]) * P.nx + w1.i[0];
+        float rho[NS];
+        load_rho<NS>(P, c, rho);
+        float seg;
+        const bool inside = REF ? dw_step_ref(w1, cm.wc, cm.negf, P.cube, P.nx, P.ny, P.nz, P.refine, seg)
+                                : dw_step(w1, cm.wc, cm.negf, P.nx, P.ny, P.nz, seg);
 #pragma unroll
-            for (int f = 0; f < NFP; ++f) {
-                float chi = 0.f;
+        for (int f = 0; f < NFP; ++f) {
+            float chi = 0.f;
 #pragma unroll
-                for (int s = 0; s < NS; ++s) chi += rho[s] * P.kext[s][f];
-                kahan_add(tot[f], totc[f], chi * seg);
-            }
-            if (!inside) break;
+            for (int s = 0; s < NS; ++s) chi += rho[s] * P.kext[s][f];
+            kahan_add(tot[f], totc[f], chi * seg);
         }
+        if (!inside) break;
     }
-    Ray q = pixel_ray(cm, ix, iy, P.nx, P.ny, P.nz, true);
-    if (!q.hit) { count_steps(P.steps, nsteps); return; }
+    DFWalk w2;
+    if (!pixel_walk<REF>(w2, cm, ix, iy, P.nx, P.ny, P.nz, P.cube, P.refine, true)) {
+        count_steps(P.steps, nsteps);
+        return;
+    }
     float tb[NFP], tbc[NFP], beh[NFP], behc[NFP];
 #pragma unroll
     for (int f = 0; f < NFP; ++f) { tb[f] = 0.f; tbc[f] = 0.f; beh[f] = 0.f; behc[f] = 0.f; }
-    float tcur = 0.f, seg;
-    RefWalk<float> w2;
-    if (REF) rw_start(w2, P.cube, P.nx, P.ny, P.nz, P.refine, q.p, q.d, true);
     for (int st = 0; st < maxstep; ++st) {
         ++nsteps;
-        const int c = REF ? w2.c : (q.i[2] * P.ny + q.i[1]) * P.nx + q.i[0];
+        const int c = REF ? w2.c : (w2.i[2] * P.ny + w2.i[1]) * P.nx + w2.i[0];
         float rho[NS], eta[NFP];
         load_rho<NS>(P, c, rho);
         load_eta<NFP>(eta_cam + (size_t)c * NFP, eta);
-        const bool inside = REF ? rw_step(w2, P.cube, P.nx, P.ny, P.nz, P.refine, q.p, q.d, tcur, seg)
-                                : dda_step(q, tcur, seg, P.nx, P.ny, P.nz);
+        float seg;
+        const bool inside = REF ? dw_step_ref(w2, cm.wc, cm.negr, P.cube, P.nx, P.ny, P.nz, P.refine, seg)
+                                : dw_step(w2, cm.wc, cm.negr, P.nx, P.ny, P.nz, seg);
         float g[NS];
 #pragma unroll
         for (int s = 0; s < NS; ++s) g[s] = 0.f;
@@ -450,7 +632,7 @@ __global__ void __launch_bounds__(128) ray_bwd_kernel(const __grid_constant__ Ra
             const float dt = chi * seg;
             kahan_add(tb[f], tbc[f], dt);
             const float front = fmaxf(tot[f] - tb[f], 0.0f);      // tau between cell and observer
-            const float att = __expf(-front);
+            const float att = expf(-front);
             const float ph = phi_f(dt);
             const float dph = dphi_f(dt);
             const float contrib = eta[f] * seg * ph * att;
@@ -869,14 +1051,23 @@ rt_status raytrace_impl(rt_ctx* ctx, const rt_grid* g, const rt_opacity* op, con
         const double ex[3] = { -sp, cp, 0.0 };
         const double ey[3] = { -ct * cp, -ct * sp, st_ };
         const double pix = cams[c].pixel > 0.0 ? cams[c].pixel : diag / cams[c].npix;
+        cd[c].negf = cd[c].negr = 0u;
         for (int a = 0; a < 3; ++a) {
             kobs[3 * c + a] = (float)ko[a];
             kobs_d[3 * c + a] = ko[a];
-            cd[c].kobs[a] = (float)ko[a];
-            cd[c].ex[a] = (float)ex[a];
-            cd[c].ey[a] = (float)ey[a];
+            cd[c].k[a] = ko[a];
+            cd[c].ex[a] = ex[a];
+            cd[c].ey[a] = ey[a];
+            cd[c].ik[a] = ko[a] != 0.0 ? 1.0 / ko[a] : 0.0;
+            const double ad = fabs(ko[a]);
+            const double rr = g->refine ? (double)g->refine : 1.0;
+            cd[c].wc.td[a] = ad > 0.0 ? df_of(1.0 / ad) : DF{ INFINITY, 0.0f };
+            cd[c].wc.tds[a] = ad > 0.0 ? df_of(1.0 / (ad * rr)) : DF{ INFINITY, 0.0f };
+            cd[c].wc.adr[a] = (float)(ad * rr);
+            if (ko[a] > 0.0) cd[c].negf |= 1u << a;
+            if (ko[a] < 0.0) cd[c].negr |= 1u << a;
         }
-        cd[c].pix_cell = (float)(pix / g->cell);
+        cd[c].pix_cell = pix / g->cell;
         cd[c].apix_d2 = pix * pix / (cams[c].D * cams[c].D);
         cd[c].npix = cams[c].npix;
         inv4piD2[c] = 1.0 / (4.0 * kPi * cams[c].D * cams[c].D);

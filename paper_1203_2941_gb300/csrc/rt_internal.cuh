@@ -172,6 +172,7 @@ struct TransportKP {
     int nf;
     int ns;                             // species of the opacity (<= the kernel's padded NS)
     int mode, lucy_form, mrw, record_events;
+    uint32_t ev_mask[kMaxFreq / 32];    // frequency bins whose scattering events are stored
     int pah_mask;
     int march_min_active;
     int want_traj;                      // some model logs trajectories
@@ -256,6 +257,23 @@ __device__ __forceinline__ double f2d(float f)
     return __hiloint2double((int)hi, (int)((b & 7u) << 29));
 }
 
+// MRW y from the survival table (FP32 path): S decreases on the uniform y
+// grid; below the table the tail S ~ 2 exp(-pi^2 y) is exact to 1e-7.
+__device__ __forceinline__ float mrw_y32(const float* S, float u)
+{
+    if (u >= 1.0f) return 0.0f;
+    const float s_last = S[kMrwN - 1];
+    if (u <= s_last) return logf(2.0f / u) * (float)(1.0 / (3.14159265358979323846 * 3.14159265358979323846));
+    int lo = 0, hi = kMrwN - 1;               // S[lo] >= u > S[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (S[mid] >= u) lo = mid; else hi = mid;
+    }
+    const float a = S[lo], b = S[hi];
+    const float w = (a - u) / fmaxf(a - b, 1e-30f);
+    return ((float)lo + w) * (float)(kMrwYmax / (kMrwN - 1));
+}
+
 // Hardware reciprocal estimate of a double (a Newton step needs no more)
 __device__ __forceinline__ double rcp_approx(double x)
 {
@@ -299,6 +317,9 @@ rt_status raytrace_impl(rt_ctx* ctx, const rt_grid* g, const rt_opacity* op, con
                         cudaStream_t s);
 rt_status launch_philox(const uint32_t ctr0[4], const uint32_t key[2], uint64_t n, uint32_t* out,
                         cudaStream_t s);
+rt_status launch_mrw_sample(const float* table, const float* u, uint64_t n, float* y, cudaStream_t s);
+rt_status launch_gather_probe(int num_sms, const void* buf, size_t bytes, uint64_t n_reads, uint32_t seed,
+                              unsigned long long* sink, cudaStream_t s);
 // launch accounting (rt_kernel_launches)
 void count_launches(unsigned n = 1);
 // host helpers

@@ -164,6 +164,13 @@ __global__ void philox_kernel(uint4 c0, uint2 key, uint64_t n, uint4* out)
     out[i] = philox4x32_10(c, key);
 }
 
+// the FP32 transport's MRW path-length draw for given uniforms (test hook)
+__global__ void mrw_sample_kernel(const float* S, const float* u, uint64_t n, float* y)
+{
+    const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (i < n) y[i] = mrw_y32(S, u[i]);
+}
+
 }  // namespace
 
 rt_status launch_temperatures(rt_ctx* ctx, const rt_grid* g, const rt_opacity* op, const double* E,
@@ -216,6 +223,15 @@ rt_status launch_philox(const uint32_t ctr0[4], const uint32_t key[2], uint64_t 
     if (n == 0) return RT_OK;
     philox_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
         make_uint4(ctr0[0], ctr0[1], ctr0[2], ctr0[3]), make_uint2(key[0], key[1]), n, (uint4*)out);
+    count_launches();
+    RT_CUDA(cudaGetLastError());
+    return RT_OK;
+}
+
+rt_status launch_mrw_sample(const float* table, const float* u, uint64_t n, float* y, cudaStream_t s)
+{
+    if (n == 0) return RT_OK;
+    mrw_sample_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(table, u, n, y);
     count_launches();
     RT_CUDA(cudaGetLastError());
     return RT_OK;

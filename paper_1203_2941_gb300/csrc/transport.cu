@@ -230,23 +230,6 @@ __device__ double mrw_y64(double u)
     return 0.5 * (lo + hi);
 }
 
-// MRW y from the survival table (FP32 path): S decreases on the uniform y
-// grid; below the table the tail S ~ 2 exp(-pi^2 y) is exact to 1e-7.
-__device__ __forceinline__ float mrw_y32(const float* S, float u)
-{
-    if (u >= 1.0f) return 0.0f;
-    const float s_last = S[kMrwN - 1];
-    if (u <= s_last) return logf(2.0f / u) * (float)(1.0 / (kPi * kPi));
-    int lo = 0, hi = kMrwN - 1;               // S[lo] >= u > S[hi]
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (S[mid] >= u) lo = mid; else hi = mid;
-    }
-    const float a = S[lo], b = S[hi];
-    const float w = (a - u) / fmaxf(a - b, 1e-30f);
-    return ((float)lo + w) * (float)(kMrwYmax / (kMrwN - 1));
-}
-
 // ------------------------------------------------------------- per-lane packet state
 // Registers decide occupancy for this latency-bound kernel, so the state is
 // kept lean: the cell is one linear index, and per flight each axis keeps its
@@ -1233,7 +1216,7 @@ struct Kernel {
             else g = s_op()[s * P.nf + L.j].w;
             const R mu = hg_mu(g, U(L));
             const R uphi = U(L);
-            if (P.record_events) {
+            if (P.record_events && ((P.ev_mask[L.j >> 5] >> (L.j & 31)) & 1u)) {
                 const unsigned long long slot = atomicAdd(&md->stats[RT_STAT_N_EVENTS], 1ull);
                 if (md->events && slot < md->event_cap) {
                     rt_event e;

@@ -32,7 +32,7 @@ EXPORTS = ["rt_last_error", "rt_version", "rt_ctx_create", "rt_ctx_destroy", "rt
            "rt_grid_free", "rt_opacity_upload", "rt_opacity_free", "rt_transport_params_default",
            "rt_transport", "rt_temperatures", "rt_temperature_guess", "rt_raytrace",
            "rt_raytrace_backward", "rt_batch_create", "rt_batch_run", "rt_batch_free",
-           "rt_transport_batched", "rt_philox", "rt_kernel_launches", "rt_transport_noalloc", "rt_visibilities",
+           "rt_transport_batched", "rt_philox", "rt_mrw_sample", "rt_probe_gather", "rt_kernel_launches", "rt_transport_noalloc", "rt_visibilities",
            "rt_pah_reemit", "rt_grid_upload_refined", "rt_grid_ncell", "rt_grid_update"]
 
 
@@ -55,7 +55,8 @@ class rt_transport_params(C.Structure):
                 ("max_events", C.c_uint64), ("record_events", C.c_int), ("precision", C.c_int),
                 ("schedule", C.c_int), ("threads_per_block", C.c_int), ("blocks_per_sm", C.c_int),
                 ("march_min_active", C.c_int), ("defer_events", C.c_uint64),
-                ("source_bins", C.c_uint32), ("pc_cams", C.c_void_p), ("n_pc_cams", C.c_int)]
+                ("source_bins", C.c_uint32), ("pc_cams", C.c_void_p), ("n_pc_cams", C.c_int),
+                ("record_nu_mask", C.c_void_p)]
 
 
 class rt_transport_out(C.Structure):
@@ -135,6 +136,8 @@ def load(path: str = LIB_PATH):
         "rt_batch_free": (None, [vp]),
         "rt_transport_batched": (i32, [vp, vp, i32, vp, C.POINTER(rt_transport_params), vp]),
         "rt_philox": (i32, [vp, vp, vp, u64, vp, vp]),
+        "rt_mrw_sample": (i32, [vp, vp, vp, u64, vp, vp]),
+        "rt_probe_gather": (i32, [vp, vp, C.c_size_t, u64, C.c_uint32, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -290,6 +293,14 @@ def rt_batch_free(batch):
 def rt_transport_batched(ctx, opac, n_models, models, params, stream=0):
     _check(load().rt_transport_batched(ctx, opac, n_models, models, C.byref(params), stream),
            "rt_transport_batched")
+
+
+def rt_probe_gather(ctx, buf_ptr, nbytes, n_reads, seed, sink_ptr, stream=0):
+    _check(load().rt_probe_gather(ctx, buf_ptr, nbytes, n_reads, seed, sink_ptr, stream), "rt_probe_gather")
+
+
+def rt_mrw_sample(ctx, opac, u_ptr, n, y_ptr, stream=0):
+    _check(load().rt_mrw_sample(ctx, opac, u_ptr, n, y_ptr, stream), "rt_mrw_sample")
 
 
 def rt_philox(ctx, ctr0, key, n, out_ptr, stream=0):

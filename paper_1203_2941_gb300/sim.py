@@ -245,7 +245,10 @@ def make_params(n_packets: int, mode=R.RT_MODE_BW, lucy_mode=R.RT_LUCY_THIN,
                 mrw_gamma=2.0, seed=1, model_id=0, pid_begin=0, pid_end=None,
                 max_events=10_000_000, record_events=False, precision=R.RT_PREC_FP32,
                 schedule=R.RT_SCHED_PERSISTENT, threads_per_block=0, blocks_per_sm=0,
-                march_min_active=-1, defer_events=0, source_bins=0) -> R.rt_transport_params:
+                march_min_active=-1, defer_events=0, source_bins=0,
+                record_nu=None) -> R.rt_transport_params:
+    """Transport parameters; ``record_nu`` lists the frequency bins whose
+    scattering events are stored (None: every bin)."""
     p = R.rt_transport_params_default()
     p.mode, p.lucy_mode, p.lucy_form, p.lucy_tau = mode, lucy_mode, lucy_form, lucy_tau
     p.mrw, p.mrw_tau_cell, p.mrw_gamma = int(bool(mrw)), mrw_tau_cell, mrw_gamma
@@ -260,6 +263,13 @@ def make_params(n_packets: int, mode=R.RT_MODE_BW, lucy_mode=R.RT_LUCY_THIN,
     p.march_min_active = march_min_active
     p.defer_events = int(defer_events)
     p.source_bins = int(source_bins)
+    if record_nu is not None:
+        idx = [int(j) for j in record_nu]
+        words = (C.c_uint32 * max(1, (max(idx, default=0) // 32) + 1))()
+        for j in idx:
+            words[j // 32] |= 1 << (j % 32)
+        p._record_nu_words = words            # kept alive with the struct
+        p.record_nu_mask = C.cast(words, C.c_void_p)
     return p
 
 
@@ -489,6 +499,15 @@ def philox(ctx: Context, ctr0, key, n: int, stream=None) -> np.ndarray:
     R.rt_philox(ctx.h, ctr0, key, n, _ptr(out), _stream(stream))
     torch.cuda.synchronize()
     return out.cpu().numpy().view(np.uint32)
+
+
+def mrw_sample(ctx: Context, opac, u, stream=None) -> np.ndarray:
+    """The FP32 transport's MRW first-passage times y for uniforms u in (0, 1]."""
+    ut = torch.as_tensor(np.ascontiguousarray(u, dtype=np.float32)).to("cuda")
+    y = torch.empty_like(ut)
+    R.rt_mrw_sample(ctx.h, opac.h, _ptr(ut), ut.numel(), _ptr(y), _stream(stream))
+    torch.cuda.synchronize()
+    return y.cpu().numpy()
 
 
 class Batch:

@@ -61,8 +61,8 @@ int main(void) {
          sizeof(rt_pah_event), sizeof(rt_traj));
   printf("%zu %zu %zu\n", offsetof(rt_transport_params, march_min_active),
          offsetof(rt_transport_out, stats), offsetof(rt_model, out));
-  printf("%zu %zu %zu\n", sizeof(rt_pc_camera), offsetof(rt_transport_params, pc_cams),
-         offsetof(rt_transport_out, pc_img));
+  printf("%zu %zu %zu %zu\n", sizeof(rt_pc_camera), offsetof(rt_transport_params, pc_cams),
+         offsetof(rt_transport_out, pc_img), offsetof(rt_transport_params, record_nu_mask));
   return 0;
 }
 '''
@@ -79,5 +79,5 @@ int main(void) {
             R.rt_transport_params.march_min_active.offset, R.rt_transport_out.stats.offset,
             R.rt_model.out.offset,
             ctypes.sizeof(R.rt_pc_camera), R.rt_transport_params.pc_cams.offset,
-            R.rt_transport_out.pc_img.offset]
+            R.rt_transport_out.pc_img.offset, R.rt_transport_params.record_nu_mask.offset]
     assert [int(v) for v in got] == want

@@ -2,8 +2,9 @@
 the FP64 CPU oracle (run on a GB300).
 
 * rt_temperatures (Eq. 4) on the same absorbed energies: 1e-10 relative.
-* rt_raytrace (Eqs. 11-17): images within 1e-5 of the pixel maximum and
-  relative on bright pixels, SEDs within 1e-5 relative, with thermal
+* rt_raytrace (Eqs. 11-17): images within 1e-5 relative on every pixel above
+  1e-3 of the image maximum (1e-5 of the maximum below), SEDs within 1e-5
+  relative, with thermal
   emission, stored scattering events and direct starlight, 1 and 3 species,
   several cameras, ragged image sizes.
 * rt_raytrace_backward: dL/drho within 1e-2 of the oracle's FP64 adjoint on
@@ -19,6 +20,7 @@ import pytest
 import torch
 
 import workloads as W
+from imgcheck import assert_images_close
 
 pytestmark = pytest.mark.gpu
 
@@ -81,15 +83,8 @@ def _events(m, n, seed, nus):
     return ev
 
 
-def _compare_images(img, ref, rtol=1e-5):
-    for c in range(ref.shape[0]):
-        for f in range(ref.shape[1]):
-            a, b = img[c, f], ref[c, f]
-            mx = np.abs(b).max()
-            assert np.all(np.abs(a - b) <= rtol * mx + 1e-37), (c, f, np.abs(a - b).max() / max(mx, 1e-300))
-            bright = np.abs(b) > 1e-2 * mx
-            if bright.any():
-                assert np.all(np.abs(a[bright] / b[bright] - 1) < 1e-4)
+def _compare_images(img, ref):
+    assert_images_close(img, ref, rtol=1e-5, floor=1e-3)
 
 
 @pytest.mark.parametrize("case", ["shell", "torus", "ragged"])

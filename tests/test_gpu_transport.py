@@ -7,8 +7,10 @@
   Wood transport in the one-lane serial schedule, 1-3 species, the Lucy
   variants and the modified random walk; accumulated energies agree to 1e-9.
 * FP32 production build: per-cell absorbed energy within
-  max(3 sigma, 1e-3 E), escaped SED within 3 sigma, temperatures within 0.5%
-  where the relative sigma of E is below 1%; exact energy conservation.
+  max(3 sigma, 1e-3 E) and escaped SED within 3 sigma, with the binomial
+  outlier allowance and chi-square bound of statcheck (false-alarm rate
+  1e-6 each); temperatures within 0.5% where the relative sigma of E is below
+  1%; exact energy conservation.
 * Edge cases: empty grid, source on a cell face, empty packet range, event
   and PAH buffer overflow, the per-packet event cap, ragged grid shapes.
 """
@@ -20,6 +22,7 @@ import pytest
 import torch
 
 import workloads as W
+from statcheck import assert_outliers, assert_same_energies, assert_same_sed
 
 pytestmark = pytest.mark.gpu
 
@@ -221,52 +224,51 @@ def test_fp64_pah_and_noreemit_match_oracle(rt, ctx, O):
     _traj_compare(out2.traj_numpy(), ref2["traj"], m2.cell * 5)
 
 
-def _stat_compare(g, ref, xi, E_rel=1e-3, nsig=3.0):
-    """Per-cell E_abs within max(nsig*sigma, E_rel*E) with sigma from both
-    runs' sums of squared deposits."""
-    sg = np.sqrt(g["esq"]) if g["esq"] is not None else xi * np.sqrt(g["count"])
-    sr = np.sqrt(ref["esq"])
-    sig = np.sqrt(sg ** 2 + sr ** 2)
-    tol = np.maximum(nsig * sig, E_rel * np.maximum(g["E_abs"], ref["E_abs"]))
-    d = np.abs(g["E_abs"] - ref["E_abs"])
-    return d <= tol + 1e-30, sig
-
-
 def test_fp32_bw_statistics_match_oracle_homogeneous_sphere(rt, ctx, O):
     """Homogeneous sphere (32^3 in the full-size configuration; 16^3 here so
-    the B&W oracle finishes in seconds), B&W, Lucy in thin cells."""
+    the B&W oracle finishes in seconds), B&W, Lucy in thin cells: per-cell
+    E_abs within max(3 sigma, 1e-3 E) with the binomial allowance of
+    statcheck, the chi-square of the per-cell differences, the escaped SED
+    per bin within 3 sigma, exact conservation, and temperatures within
+    3 sigma_T + 0.5 % where both runs sample the energy to 10 %."""
     m = W.homogeneous_sphere(n=16, tau_v=1.0)
     grid, opac, srcs = _setup(rt, ctx, m)
-    N = 40000
+    N = 400000
     out = rt.transport(ctx, grid, opac, srcs, N, seed=11)
     torch.cuda.synchronize()
     ref = O.transport(m, N, seed=12, mode=O.MODE_BW)
+    ref2 = O.transport(m, N, seed=13, mode=O.MODE_BW)
     g = out.numpy()
     xi = m.luminosity / N
     assert abs(g["sed_esc"].sum() / m.luminosity - 1) < 1e-12
     assert g["stats"]["escaped"] == N
-    ok, sig = _stat_compare(g, ref, xi, nsig=4.0)
-    # 4 sigma per cell over ~4000 cells: allow the expected Gaussian outliers
-    assert (~ok).sum() <= max(3, int(0.002 * ok.size)), (~ok).sum()
-    # total absorbed energy and escaped SED
-    tot_sig = math.sqrt((sig ** 2).sum())
-    assert abs(g["E_abs"].sum() - ref["E_abs"].sum()) < 4 * tot_sig + 1e-3 * ref["E_abs"].sum()
-    s_sig = xi * np.sqrt(g["sed_cnt"] + ref["sed_cnt"])
-    assert np.all(np.abs(g["sed_esc"] - ref["sed_esc"]) <= 4.5 * s_sig + 1e-12)
-    # temperatures where the energy is well sampled
+    phi, ncell = assert_same_energies(g, ref, ref2, xi)
+    assert ncell > 800
+    assert assert_same_sed(g, ref, xi) > 100
+    # total absorbed energy (cells of one packet are correlated: phi-scaled)
+    sig = np.sqrt(g["esq"] + ref["esq"])
+    tot_sig = math.sqrt(phi * (sig ** 2).sum())
+    assert abs(g["E_abs"].sum() - ref["E_abs"].sum()) < 3 * tot_sig + 1e-3 * ref["E_abs"].sum()
+    # temperatures (T ~ E^(1/4)) within 3 sigma_T + 0.5 % where both runs'
+    # energies are sampled to 10 % (the full-size test holds cells sampled to
+    # 1 %, where the stated 0.5 % applies on its own)
     Tg = O.temperatures(m, g["E_abs"])
     Tr = O.temperatures(m, ref["E_abs"])
-    rel = np.sqrt(g["esq"]) / np.maximum(g["E_abs"], 1e-300)
-    good = (rel < 0.01) & (g["E_abs"] > 0) & (ref["E_abs"] > 0)
-    if good.sum() > 0:
-        assert np.all(np.abs(Tg[good] / Tr[good] - 1) < 0.005)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        rg = np.sqrt(g["esq"]) / g["E_abs"]
+        rr = np.sqrt(ref["esq"]) / ref["E_abs"]
+    good = (g["E_abs"] > 0) & (ref["E_abs"] > 0) & (rg < 0.1) & (rr < 0.1)
+    assert good.sum() > 100
+    sT = 0.25 * np.sqrt(phi * (rg[good] ** 2 + rr[good] ** 2))
+    dT = np.abs(Tg[good] / Tr[good] - 1)
+    assert_outliers(int((dT > 3 * sT + 0.005).sum()), int(good.sum()), "temperatures")
 
 
 def test_fp32_frozen_statistics_and_packet_ranges(rt, ctx, O):
     m = W.r2_shell(n=16, tau_1um=10.0, nf=32)
     grid, opac, srcs = _setup(rt, ctx, m)
     T0 = O.temperature_guess(m)
-    N = 30000
+    N = 300000
     Tt = torch.tensor(T0, device="cuda")
     out = rt.transport(ctx, grid, opac, srcs, N, mode=rt.rtgb.RT_MODE_FROZEN_T, T_prev=Tt, seed=2)
     # the same emission split into two packet ranges accumulates identically
@@ -280,9 +282,95 @@ def test_fp32_frozen_statistics_and_packet_ranges(rt, ctx, O):
     assert g["stats"]["crossings"] == g2["stats"]["crossings"]
     np.testing.assert_allclose(g["E_abs"], g2["E_abs"], rtol=1e-9, atol=1e-9 * g["E_abs"].max())
     ref = O.transport(m, N, seed=3, mode=O.MODE_FROZEN_T, T_prev=T0, n_threads=8)
-    ok, _ = _stat_compare(g, ref, m.luminosity / N, nsig=4.0)
-    assert (~ok).sum() <= max(3, int(0.002 * ok.size))
+    ref2 = O.transport(m, N, seed=4, mode=O.MODE_FROZEN_T, T_prev=T0, n_threads=8)
+    xi = m.luminosity / N
+    assert assert_same_energies(g, ref, ref2, xi)[1] > 100
+    assert assert_same_sed(g, ref, xi) > 100
     assert abs(g["sed_esc"].sum() / m.luminosity - 1) < 1e-12
+
+
+def test_fp32_mrw_path_lengths_match_the_series(rt, ctx, O):
+    """The FP32 transport's MRW path-length draws (Sect. 3.2) against the
+    oracle's FP64 inversion of the survival series, for uniforms on the FP32
+    grid the kernel draws ((k + 1) 2^-24, k < 2^24), including both ends.
+    Pointwise: within 1e-5 in y where u <= 0.9 (|S'(y)| > 0.05 there, so the
+    table's FP32 rounding and linear interpolation stay far below that) and
+    within 2e-4 everywhere (towards u = 1 the slope of S vanishes and the
+    FP32 rounding of S, 6e-8, maps to up to ~1e-4 in y); <y> = 1/6 of the
+    series.  Distribution: a KS test of 1e6 draws against 1 - S(y)."""
+    from scipy import stats
+    m = W.uniform_cube(n=2, tau_cell=20.0, nf=4)
+    opac = ctx.opacity(m)
+    rng = np.random.default_rng(7)
+    k = rng.integers(0, 2 ** 24, 10 ** 6)
+    ends = np.array([0, 1, 2, 3, 2 ** 24 - 4, 2 ** 24 - 3, 2 ** 24 - 2, 2 ** 24 - 1])
+    k = np.concatenate([ends, k])
+    u = ((k + 1).astype(np.float64) * 2.0 ** -24).astype(np.float32)
+    y = rt.mrw_sample(ctx, opac, u).astype(np.float64)
+    assert np.all(np.isfinite(y)) and np.all(y >= 0)
+    assert y[ends.size - 1] == 0.0                         # u = 1: no path
+    npt = 30000
+    yr = np.array([O.mrw_sample_y(float(v)) for v in u[:npt]])
+    err = np.abs(y[:npt] - yr)
+    low = u[:npt] <= 0.9
+    assert err[low].max() <= 1e-5, err[low].max()
+    assert err.max() <= 2e-4, err.max()
+    body = y[ends.size:]
+    assert abs(body.mean() - 1.0 / 6.0) < 5 * math.sqrt(1.0 / 90.0 / body.size)
+    F = 1.0 - np.array([O.mrw_survival(float(v)) for v in body])
+    assert stats.kstest(F, "uniform").pvalue > 1e-6
+
+
+def _batches(run, N, nb):
+    """Per-cell energies, escaped SEDs and MRW step counts of N packets run as
+    nb packet-id batches; totals with standard errors from the batches'
+    spread (the batches are independent packet streams)."""
+    E, S, Cn, M = [], [], [], []
+    for b in range(nb):
+        r = run(b * N // nb, (b + 1) * N // nb)
+        E.append(np.asarray(r["E_abs"], dtype=np.float64).ravel())
+        S.append(np.asarray(r["sed_esc"], dtype=np.float64).sum(0))
+        M.append(float(r["stats"]["mrw_steps"]))
+    E, S, M = np.array(E), np.array(S), np.array(M)
+    k = math.sqrt(nb)
+    return dict(E=E.sum(0), sE=E.std(0, ddof=1) * k, S=S.sum(0), sS=S.std(0, ddof=1) * k,
+                M=M.sum(), sM=M.std(ddof=1) * k)
+
+
+def test_fp32_mrw_transport_matches_oracle(rt, ctx, O):
+    """The production FP32 transport with the modified random walk (Sect.
+    3.2) on a uniform cube of tau_cell = 20 against the FP64 oracle, frozen
+    temperatures (order-independent): absorbed energy per cell and in total,
+    the escaped SED per frequency and the number of MRW steps within 3 sigma
+    + 2 % (sigma from 20 independent packet batches of each run; per cell,
+    where that sigma has about 38 degrees of freedom, |z| < 5 and a mean z^2
+    below 2)."""
+    m = W.uniform_cube(n=4, tau_cell=20.0, nf=4, albedo=0.5)
+    grid, opac, srcs = _setup(rt, ctx, m)
+    T0 = np.full((1, m.ncell), 300.0)
+    Tt = torch.tensor(T0, device="cuda")
+    N, nb = 200000, 20
+
+    def gpu(b, e):
+        out = rt.transport(ctx, grid, opac, srcs, N, mode=rt.rtgb.RT_MODE_FROZEN_T, T_prev=Tt,
+                           mrw=True, seed=41, pid_begin=b, pid_end=e)
+        torch.cuda.synchronize()
+        return out.numpy()
+
+    def ref(b, e):
+        return O.transport(m, N, seed=42, mode=O.MODE_FROZEN_T, T_prev=T0, mrw=True, n_threads=8,
+                           pid_begin=b, pid_end=e)
+
+    g, r = _batches(gpu, N, nb), _batches(ref, N, nb)
+    assert g["M"] > N and r["M"] > N                       # many MRW steps per packet
+    assert abs(g["M"] - r["M"]) < 3 * math.hypot(g["sM"], r["sM"]) + 0.02 * r["M"]
+    assert abs(g["E"].sum() - r["E"].sum()) < 3 * math.hypot(
+        math.sqrt((g["sE"] ** 2).sum()), math.sqrt((r["sE"] ** 2).sum())) + 0.02 * r["E"].sum()
+    z = (g["E"] - r["E"]) / np.sqrt(g["sE"] ** 2 + r["sE"] ** 2 + (0.02 * r["E"]) ** 2)
+    assert np.all(np.abs(z) < 5.0) and (z ** 2).mean() < 2.0, (np.abs(z).max(), (z ** 2).mean())
+    lit = r["S"] > 0
+    assert np.all((np.abs(g["S"] - r["S"]) <= 3 * np.hypot(g["sS"], r["sS"]) + 0.02 * r["S"])[lit])
+    assert np.all(g["S"][~lit] == 0)
 
 
 def test_edge_cases(rt, ctx, O):

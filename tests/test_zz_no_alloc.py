@@ -11,7 +11,9 @@ Frozen-temperature transport is used so both entry points follow identical
 packet histories (no dependence on the order of atomic updates): counts and
 crossings agree exactly, energies and escaped SEDs to 1e-9.  This file is
 collected last so that a stop at the first failure has already run every
-other test.
+other test.  Around a warm call, the device's free memory and the default
+memory pool's usage high-water mark (the pool cudaMallocAsync draws on) must
+not move: the call allocates nothing, not even memory it frees again.
 """
 import ctypes as C
 
@@ -24,15 +26,67 @@ import workloads as W
 pytestmark = pytest.mark.gpu
 
 
-def _run(rt, fn, ctx, grid, opac, srcs, N, T_prev, seed):
+def _cudart():
+    """The CUDA runtime already loaded into this process (by the library or torch)."""
+    for name in ("libcudart.so.13", "libcudart.so"):
+        try:
+            return C.CDLL(name)
+        except OSError:
+            pass
+    with open("/proc/self/maps") as f:
+        for line in f:
+            if "libcudart.so" in line:
+                return C.CDLL(line.split()[-1])
+    pytest.fail("no CUDA runtime library loaded")
+
+
+class _AllocProbe:
+    """Device free memory and the default pool's used-memory high-water mark."""
+    RESERVED_HIGH, USED_CURRENT, USED_HIGH = 6, 7, 8      # cudaMemPoolAttr values
+
+    def __init__(self, device=0):
+        self.rt = _cudart()
+        self.pool = C.c_void_p()
+        assert self.rt.cudaDeviceGetDefaultMemPool(C.byref(self.pool), device) == 0
+
+    def _attr(self, a):
+        v = C.c_uint64()
+        assert self.rt.cudaMemPoolGetAttribute(self.pool, a, C.byref(v)) == 0
+        return v.value
+
+    def _free(self):
+        free, total = C.c_size_t(), C.c_size_t()
+        assert self.rt.cudaMemGetInfo(C.byref(free), C.byref(total)) == 0
+        return free.value
+
+    def start(self):
+        torch.cuda.synchronize()
+        zero = C.c_uint64(0)
+        for a in (self.RESERVED_HIGH, self.USED_HIGH):      # reset the marks to the current use
+            assert self.rt.cudaMemPoolSetAttribute(self.pool, a, C.byref(zero)) == 0
+        self.used0 = self._attr(self.USED_CURRENT)
+        self.free0 = self._free()
+
+    def check(self):
+        torch.cuda.synchronize()
+        assert self._attr(self.USED_HIGH) == self.used0, "the pool served an allocation during the call"
+        assert self._free() == self.free0, "device free memory changed during the call"
+
+
+def _run(rt, fn, ctx, grid, opac, srcs, N, T_prev, seed, probe=None):
     from paper_1203_2941_gb300 import rtgb as R
     out = rt.TransportOut(grid.ncell, grid.ns, opac.nf, event_cap=8 * N)
     p = rt.make_params(N, mode=R.RT_MODE_FROZEN_T, seed=seed, record_events=True)
     stream = int(torch.cuda.current_stream().cuda_stream)
+    cs = out.c_struct()
+    if probe:
+        probe.start()
     code = fn(ctx.h, grid.h, opac.h, srcs.arr, srcs.n, C.byref(p), int(T_prev.data_ptr()),
-              C.byref(out.c_struct()), stream)
+              C.byref(cs), stream)
     assert code == R.RT_OK, R.load().rt_last_error().decode()
     torch.cuda.synchronize()
+    if probe:
+        probe.check()
     return out.numpy()
 
 
@@ -48,8 +102,12 @@ def test_noalloc_matches_rt_transport_twice():
     T0 = torch.tensor(W_guess(m), device="cuda")
     N = 40000
     ref = _run(rt, lib.rt_transport, ctx, grid, opac, srcs, N, T0, seed=5)
-    for _ in range(2):
-        got = _run(rt, lib.rt_transport_noalloc, ctx, grid, opac, srcs, N, T0, seed=5)
+    probe = _AllocProbe(0)
+    for call in range(2):
+        # the first call on the device looks up the scratch array's address;
+        # the second, warm call is watched for allocations
+        got = _run(rt, lib.rt_transport_noalloc, ctx, grid, opac, srcs, N, T0, seed=5,
+                   probe=probe if call == 1 else None)
         for k in ("crossings", "interactions", "absorptions", "scatters", "escaped", "lucy_deposits"):
             assert got["stats"][k] == ref["stats"][k], k
         np.testing.assert_array_equal(got["count"], ref["count"])
@@ -65,6 +123,14 @@ def test_noalloc_matches_rt_transport_twice():
                                     C.byref(obig.c_struct()),
                                     int(torch.cuda.current_stream().cuda_stream))
     assert code == R.RT_ERR_CAPACITY
+    # the deferred-packet queue needs an allocation: refused, not ignored
+    p = rt.make_params(N, mode=R.RT_MODE_FROZEN_T, seed=5)
+    p.defer_events = 4
+    out = rt.TransportOut(grid.ncell, grid.ns, opac.nf)
+    code = lib.rt_transport_noalloc(ctx.h, grid.h, opac.h, srcs.arr, srcs.n, C.byref(p),
+                                    int(T0.data_ptr()), C.byref(out.c_struct()),
+                                    int(torch.cuda.current_stream().cuda_stream))
+    assert code == R.RT_ERR_INVALID_ARG
 
 
 def W_guess(m):
