@@ -150,7 +150,14 @@ enum { RT_PREC_FP32 = 0,      /* production: FP32 transport, FP64 accumulators *
                                  grids without trajectories, deferred queue,
                                  cameras or PAH sources only */
 enum { RT_SCHED_PERSISTENT = 0, /* all SMs, dynamic packet refill */
-       RT_SCHED_SERIAL = 1 };   /* one GPU thread, packets in id order (debug) */
+       RT_SCHED_SERIAL = 1,     /* one GPU thread, packets in id order (debug) */
+       RT_SCHED_COMPACT = 2 };  /* all SMs with per-warp packet compaction (Sect. 3.4
+                                   load balancing): each warp parks packets in a
+                                   shared-memory stash so that its lanes march
+                                   together and serve interactions together;
+                                   single-model FP32 launches on uniform grids
+                                   without trajectories, the deferred queue or
+                                   cameras (others run RT_SCHED_PERSISTENT) */
 
 /* A photon-counting camera (the Monte Carlo image of Sect. 4, which the
  * paper sets against its ray tracer): packets that leave the grid with
@@ -210,6 +217,9 @@ typedef struct {
                                  frequencies of the ray tracer, whose scattering
                                  source, Eq. 16, uses events at those frequencies
                                  alone); NULL = every bin.  (n_freq + 31) / 32 words */
+    int compact_swap;         /* RT_SCHED_COMPACT: when at most this many lanes of a
+                                 warp still march, its stopped lanes trade their
+                                 packets for parked marching ones (0..31; -1 = 24) */
 } rt_transport_params;
 
 /* Fill p with the defaults: B&W, Lucy THIN at 1e-2, linear form, MRW off
@@ -513,8 +523,9 @@ RT_API rt_status rt_mrw_sample(rt_ctx* ctx, const rt_opacity* opac, const float*
 
 /* Memory-level probe (no counterpart in the paper): n_reads reads of one
  * 4-byte word each, at pseudo-random 32-byte sectors of buf[0, bytes),
- * spread over every SM (8 blocks of 256 threads each), the access pattern of
- * the transport's per-crossing density gathers.  Timed by the caller (CUDA
+ * spread over every SM (8 blocks of 256 threads each, four independent reads
+ * in flight per thread), the access pattern of the transport's per-crossing
+ * density gathers.  Timed by the caller (CUDA
  * events on `stream`), n_reads * 32 bytes over the time is the sector
  * bandwidth that the memory level holding the buffer serves to such gathers:
  * the L2 for a buffer well inside it, HBM for one far larger.  buf: device,

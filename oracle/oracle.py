@@ -85,7 +85,7 @@ class _Out(C.Structure):
                 ("events", C.c_void_p), ("event_cap", C.c_uint64), ("n_events", C.c_uint64),
                 ("pah", C.c_void_p), ("pah_cap", C.c_uint64), ("n_pah", C.c_uint64),
                 ("traj", C.c_void_p), ("traj_cap", C.c_uint64), ("n_traj", C.c_uint64),
-                ("stats", C.c_uint64 * 16), ("pc_img", C.c_void_p)]
+                ("stats", C.c_uint64 * 16), ("pc_img", C.c_void_p), ("loop_seconds", C.c_double)]
 
 
 class _PahSrc(C.Structure):
@@ -268,7 +268,7 @@ def transport(model, n_packets, seed=1, model_id=0, mode=MODE_BW, lucy_mode=LUCY
     return dict(E_abs=E, count=cnt, esq=q, sed_esc=sed, sed_cnt=sc,
                 events=ev[:out.n_events], pah=pah[:out.n_pah], traj=tr[:out.n_traj],
                 stats=stats, xi=model_luminosity(om) / n_packets if _pah is None else _pah.xi,
-                pc_img=imgs)
+                pc_img=imgs, loop_seconds=float(out.loop_seconds))
 
 
 def pah_reemit(model, records, xi, eps, eps_class=None, **kw):

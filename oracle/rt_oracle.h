@@ -92,6 +92,8 @@ typedef struct {
     or_traj* traj; uint64_t traj_cap; uint64_t n_traj;
     uint64_t stats[OR_S_N];
     double* pc_img;              /* camera c at offset sum_{c'<c} nf npix_c'^2: [nf][npix][npix] */
+    double loop_seconds;         /* wall time of the packet loop alone (set-up excluded),
+                                    a timing record for the CPU baseline, not a result */
 } or_out;
 
 typedef struct { double theta, phi; int npix; double D; double pixel; } or_camera;

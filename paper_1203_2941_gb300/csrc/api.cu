@@ -301,6 +301,7 @@ void rt_transport_params_default(rt_transport_params* p)
     p->march_min_active = -1;
     p->defer_events = 0;
     p->source_bins = 0;
+    p->compact_swap = -1;
 }
 
 }  // extern "C"
@@ -318,7 +319,9 @@ static rt_status check_params(const rt_transport_params* p)
         return fail(RT_ERR_INVALID_ARG, "transport: MRW thresholds must be positive");
     if (p->precision != RT_PREC_FP32 && p->precision != RT_PREC_FP64 && p->precision != RT_PREC_FP32_ACC32)
         return fail(RT_ERR_INVALID_ARG, "transport: bad precision");
-    if (p->schedule != RT_SCHED_PERSISTENT && p->schedule != RT_SCHED_SERIAL) return fail(RT_ERR_INVALID_ARG, "transport: bad schedule");
+    if (p->schedule != RT_SCHED_PERSISTENT && p->schedule != RT_SCHED_SERIAL && p->schedule != RT_SCHED_COMPACT)
+        return fail(RT_ERR_INVALID_ARG, "transport: bad schedule");
+    if (p->compact_swap < -1 || p->compact_swap > 31) return fail(RT_ERR_INVALID_ARG, "transport: compact_swap must be -1..31");
     if (p->n_packets == 0) return fail(RT_ERR_INVALID_ARG, "transport: n_packets must be > 0");
     if (p->march_min_active < -1 || p->march_min_active > 31) return fail(RT_ERR_INVALID_ARG, "transport: march_min_active must be -1..31");
     if (p->threads_per_block != 0 && (p->threads_per_block % 32 != 0 || p->threads_per_block > 256 || p->threads_per_block < 32))
@@ -555,6 +558,7 @@ static void fill_kp(TransportKP& kp, const rt_opacity* op, const rt_transport_pa
     for (int s = 0; s < op->ns; ++s)
         if (op->is_pah[s]) kp.pah_mask |= 1 << s;
     kp.march_min_active = p->march_min_active < 0 ? 16 : p->march_min_active;
+    kp.compact_swap = p->compact_swap < 0 ? 24 : p->compact_swap;
     kp.want_traj = 0;
     kp.single = 0;
     kp.rho0 = nullptr;
@@ -602,7 +606,7 @@ static rt_status single_model_options(TransportKP& kp, const rt_opacity* op,
     kp.rho0 = m0.rho;
     kp.param_models = 1;
     kp.mp[0] = m0;
-    const bool persistent = p->schedule == RT_SCHED_PERSISTENT && p->precision != RT_PREC_FP64;
+    const bool persistent = p->schedule != RT_SCHED_SERIAL && p->precision != RT_PREC_FP64;
     kp.smem_sed = persistent && op->nf <= 256 ? 1 : 0;
     kp.smem_cdf = persistent && n_sources * op->nf <= 4096 ? n_sources * op->nf : 0;
     return RT_OK;

@@ -24,7 +24,20 @@ __global__ void __launch_bounds__(256) gather_probe_kernel(const unsigned* buf, 
     h *= 0x85EBCA6Bu;
     h ^= h >> 13;
     unsigned acc = 0u;
-    for (uint64_t k = 0; k < per_thread; ++k) {
+    // four reads per iteration, each at its own sector: independent loads in
+    // flight per thread (the transport has one per lane plus the prefetch)
+    uint64_t k = 0;
+    for (; k + 4 <= per_thread; k += 4) {
+        unsigned v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            h = h * 1664525u + 1013904223u;
+            const uint64_t sct = ((uint64_t)h * n_sectors) >> 32;
+            v[q] = __ldg(buf + 8 * sct + (h >> 29));
+        }
+        acc += (v[0] ^ v[1]) + (v[2] ^ v[3]);
+    }
+    for (; k < per_thread; ++k) {
         h = h * 1664525u + 1013904223u;
         const uint64_t sct = ((uint64_t)h * n_sectors) >> 32;
         acc += __ldg(buf + 8 * sct + (h >> 29));

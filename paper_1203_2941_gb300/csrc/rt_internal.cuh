@@ -183,7 +183,8 @@ struct TransportKP {
     int smem_sed;                       // single-model persistent launch: SED tallied per block
     int smem_cdf;                       // floats of model 0's source CDFs kept in shared memory
     // dynamic shared-memory layout (byte offsets, set by the launcher)
-    int so_sed, so_cnt, so_op, so_mrw, so_cdf, so_ctr, so_claim;
+    int so_sed, so_cnt, so_op, so_mrw, so_cdf, so_ctr, so_claim, so_stash;
+    int compact_swap;                   // compaction: swap stopped lanes at <= this many marching
     unsigned long long max_events;
     unsigned long long source_bins;     // 0: random source bins; m: Eq. 1 equal-energy bins
     unsigned long long defer_events;    // 0 = off

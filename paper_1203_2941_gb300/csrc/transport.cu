@@ -281,14 +281,22 @@ __device__ __forceinline__ unsigned char* smem_raw()
     return smem_bytes;
 }
 
+// position of the n-th (from 0) set bit of m (n below the number of set bits)
+__device__ __forceinline__ int nth_bit(unsigned m, unsigned n)
+{
+    for (unsigned i = 0; i < n; ++i) m &= m - 1u;
+    return __ffs(m) - 1;
+}
+
 // FEAT bits: 1 = modified random walk compiled in, 2 = trajectory logging
 // compiled in, 4 = model descriptors read from the launch parameters (constant
 // bank) instead of global memory, 8 = a single model (its index and grid
 // pointer are constants, not lane registers), 16 = the deferred-packet queue
 // compiled in, 32 = PAH re-emission sources compiled in, 64 = one level of
 // sub-cube refinement (two-level traversal), 128 = photon-counting cameras,
-// 256 = FP32 per-cell accumulators (the plain-FP32 form); production launches
-// leave unused paths out of the hot code.
+// 256 = FP32 per-cell accumulators (the plain-FP32 form), 512 = per-warp
+// packet compaction (RT_SCHED_COMPACT); production launches leave unused
+// paths out of the hot code.
 template <typename R, int NS, int FEAT>
 struct Kernel {
     using PT = typename PackedT<NS>::T;
@@ -302,6 +310,7 @@ struct Kernel {
     static constexpr bool HAS_REF = (FEAT & 64) != 0;
     static constexpr bool HAS_PC = (FEAT & 128) != 0;
     static constexpr bool ACC32 = (FEAT & 256) != 0;
+    static constexpr bool COMPACT = (FEAT & 512) != 0;
     using Acc = typename std::conditional<ACC32, float, double>::type;
 
     // the call's per-cell scratch: {sum, sum of squares} of deposits in units of xi
@@ -1339,6 +1348,81 @@ struct Kernel {
         end_packet(L);
     }
 
+    // ------------------------------------------------ per-warp compaction
+    // A packet parks in a stash record of six uint4 (96 bytes): Philox
+    // position, event count, cell, frequency bin, state, remaining optical
+    // depth, flight origin and time, direction, next-face times and spacings,
+    // steps left per axis.  Its crossing and Lucy counters go to the parking
+    // lane's tallies first.  Unparking restores the registers exactly (the
+    // rest -- densities of the cell, opacities of the bin, strides, the
+    // prefetched next cell -- is reloaded), so a packet's trajectory does not
+    // depend on the lanes it visits.
+    __device__ __forceinline__ void park(Lane<R, NS>& L, uint4* rec)
+    {
+        count(RT_STAT_CROSSINGS, L.ncross);
+        count(RT_STAT_LUCY, L.nlucy);
+        L.ncross = 0;
+        L.nlucy = 0;
+        rec[0] = make_uint4(L.rng.plo, L.rng.phi, L.rng.draw, L.rng.c_hi);
+        rec[1] = make_uint4(L.nev, (unsigned)L.c, (unsigned)L.j | ((unsigned)L.st << 24), __float_as_uint(L.tau));
+        rec[2] = make_uint4(__float_as_uint(L.x[0]), __float_as_uint(L.x[1]), __float_as_uint(L.x[2]),
+                            __float_as_uint(L.tcur));
+        rec[3] = make_uint4(__float_as_uint(L.k[0]), __float_as_uint(L.k[1]), __float_as_uint(L.k[2]),
+                            (unsigned)L.rem[0]);
+        rec[4] = make_uint4(__float_as_uint(L.tm[0]), __float_as_uint(L.tm[1]), __float_as_uint(L.tm[2]),
+                            (unsigned)L.rem[1]);
+        rec[5] = make_uint4(__float_as_uint(L.td[0]), __float_as_uint(L.td[1]), __float_as_uint(L.td[2]),
+                            (unsigned)L.rem[2]);
+    }
+
+    __device__ __forceinline__ void unpark(Lane<R, NS>& L, const uint4* rec)
+    {
+        L.rng.ky = (uint32_t)(P.seed >> 32) ^ md->model_id;
+        { const uint4 r = rec[0]; L.rng.plo = r.x; L.rng.phi = r.y; L.rng.draw = r.z; L.rng.c_hi = r.w; }
+        L.rng.c_lo = 0;
+        {
+            const uint4 r = rec[1];
+            L.nev = r.x;
+            L.c = (int)r.y;
+            L.j = (int)(r.z & 0xffffffu);
+            L.st = (int)(r.z >> 24);
+            L.tau = __uint_as_float(r.w);
+        }
+        {
+            const uint4 r = rec[2];
+            L.x[0] = __uint_as_float(r.x); L.x[1] = __uint_as_float(r.y); L.x[2] = __uint_as_float(r.z);
+            L.tcur = __uint_as_float(r.w);
+        }
+        {
+            const uint4 r = rec[3];
+            L.k[0] = __uint_as_float(r.x); L.k[1] = __uint_as_float(r.y); L.k[2] = __uint_as_float(r.z);
+            L.rem[0] = (int)r.w;
+        }
+        {
+            const uint4 r = rec[4];
+            L.tm[0] = __uint_as_float(r.x); L.tm[1] = __uint_as_float(r.y); L.tm[2] = __uint_as_float(r.z);
+            L.rem[1] = (int)r.w;
+        }
+        {
+            const uint4 r = rec[5];
+            L.td[0] = __uint_as_float(r.x); L.td[1] = __uint_as_float(r.y); L.td[2] = __uint_as_float(r.z);
+            L.rem[2] = (int)r.w;
+        }
+        L.m = 0;
+        L.seq = 0;
+        L.ncross = 0;
+        L.nlucy = 0;
+        load_freq(L);
+        load_cell(L);
+        if (L.st == ST_MARCH) {
+            const int stride[3] = { 1, md->nx, md->nx * md->ny };
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+                L.dc[a] = L.k[a] > R(0) ? stride[a] : (L.k[a] < R(0) ? -stride[a] : 0);
+            prefetch_next(L);
+        }
+    }
+
     // End of the persistent loop (all lanes converged): counters of warps
     // whose lanes share one model are summed with shuffles first.
     __device__ __forceinline__ void flush_warp(int m) const
@@ -1374,6 +1458,163 @@ struct Kernel {
         }
     }
 };
+
+// Packets claimed per warp in chunks from the global work counter (one
+// atomic per chunk; 256 down to 32 ids as the work runs out), the warp's
+// unclaimed range kept in shared memory: lanes in state NEED emit the next
+// ids; lanes that find none become DONE once every id has been claimed.
+template <typename R, int NS, int FEAT>
+__device__ __forceinline__ void refill(Kernel<R, NS, FEAT>& K, Lane<R, NS>& L, const TransportKP& P,
+                                       unsigned long long* claim, unsigned long long total_work, int lane)
+{
+    const unsigned need = __ballot_sync(FULL, L.st == ST_NEED);
+    if (!need) return;
+    unsigned long long w_next = claim[0], w_end = claim[1];
+    if (w_next == w_end && w_end < total_work) {
+        unsigned long long base = 0;
+        const unsigned long long n_warps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
+        unsigned long long chunk = (total_work - w_end) / (4ull * n_warps);
+        chunk = chunk < 32ull ? 32ull : (chunk > 256ull ? 256ull : chunk);
+        if (lane == 0) base = atomicAdd(P.work_ctr, chunk);
+        base = __shfl_sync(FULL, base, 0);
+        if (base >= total_work) {
+            w_next = w_end = total_work;
+        } else {
+            w_next = base;
+            w_end = base + chunk < total_work ? base + chunk : total_work;
+        }
+    }
+    const unsigned avail = (unsigned)(w_end - w_next);
+    const unsigned rank = __popc(need & ((1u << lane) - 1u));
+    if (L.st == ST_NEED) {
+        if (rank < avail) K.emit(L, w_next + rank);
+        else if (w_end >= total_work) L.st = ST_DONE;
+    }
+    w_next += __popc(need) < avail ? __popc(need) : avail;
+    __syncwarp();
+    if (lane == 0) { claim[0] = w_next; claim[1] = w_end; }
+    __syncwarp();
+}
+
+// Per-warp packet compaction (RT_SCHED_COMPACT; the load balancing of Sect.
+// 3.4 done inside a warp).  Each warp owns a stash of kStash packet records
+// in shared memory, besides the 32 packets its lanes hold, and alternates two
+// phases so that its lanes run the same code:
+//   event phase  lanes still marching park their packets and take pending
+//                ones (stopped at an interaction or escape, or between MRW
+//                steps); lanes without a packet take pending ones, then new
+//                packets; every lane serves its interaction, escape or
+//                emission and starts its next flight
+//   march phase  all lanes cross cells together; once at most compact_swap
+//                lanes still march, the stopped lanes park their packets and
+//                take parked marching ones (one batch per trade); the phase
+//                ends when no parked marching packet is left and at most
+//                march_min_active (at most kStash / 2) lanes still march.
+// A trade parks into a free slot before it reads the other packet, so no
+// lane holds two packets at once; the bound on the lanes left marching
+// keeps the stash within kStash records (at most kStash / 2 parked between
+// phases, plus those being traded).  The stash slots of parked marching and
+// pending packets are warp-uniform bit masks.
+constexpr int kStash = 16;
+
+template <typename R, int NS, int FEAT>
+__device__ __forceinline__ void compact_loop(Kernel<R, NS, FEAT>& K, Lane<R, NS>& L, const TransportKP& P,
+                                             unsigned char* sm, unsigned long long total_work, int lane)
+{
+    unsigned long long* claim = reinterpret_cast<unsigned long long*>(sm + P.so_claim) + 2 * (threadIdx.x >> 5);
+    if (lane == 0) { claim[0] = 0; claim[1] = 0; }
+    uint4* stash = reinterpret_cast<uint4*>(sm + P.so_stash) + (size_t)(threadIdx.x >> 5) * (kStash * 6);
+    __syncwarp();
+    const unsigned lt = (1u << lane) - 1u;
+    const unsigned all = (1u << kStash) - 1u;
+    const int t_end = P.march_min_active < kStash / 2 ? P.march_min_active : kStash / 2;
+    const int t_swap = P.compact_swap > t_end ? P.compact_swap : t_end;
+    unsigned mm = 0u, em = 0u;                  // slots of parked marching / pending packets
+    for (;;) {
+        // event phase: marching lanes park, then take pending packets
+        {
+            const unsigned mar = __ballot_sync(FULL, L.st == ST_MARCH);
+            if (mar) {
+                const unsigned fr = ~(mm | em) & all;
+                const unsigned ne = __popc(em);
+                int put = -1, get = -1;
+                if (L.st == ST_MARCH) {
+                    const unsigned r = __popc(mar & lt);
+                    put = nth_bit(fr, r);
+                    if (r < ne) get = nth_bit(em, r);
+                    K.park(L, stash + put * 6);
+                    if (get >= 0) K.unpark(L, stash + get * 6);
+                    else L.st = ST_NEED;
+                }
+                mm |= __reduce_or_sync(FULL, put >= 0 ? 1u << put : 0u);
+                em &= ~__reduce_or_sync(FULL, get >= 0 ? 1u << get : 0u);
+                __syncwarp();
+            }
+        }
+        // lanes without a packet take pending packets, then new ones
+        {
+            const unsigned fre = __ballot_sync(FULL, L.st == ST_NEED || L.st == ST_DONE);
+            if (fre && em) {
+                int get = -1;
+                if (L.st == ST_NEED || L.st == ST_DONE) {
+                    const unsigned r = __popc(fre & lt);
+                    if (r < (unsigned)__popc(em)) get = nth_bit(em, r);
+                }
+                if (get >= 0) K.unpark(L, stash + get * 6);
+                em &= ~__reduce_or_sync(FULL, get >= 0 ? 1u << get : 0u);
+                __syncwarp();
+            }
+        }
+        refill(K, L, P, claim, total_work, lane);
+        // no new packet left: lanes without one take parked marching packets
+        {
+            const unsigned dn = __ballot_sync(FULL, L.st == ST_DONE);
+            if (dn && mm) {
+                int get = -1;
+                if (L.st == ST_DONE) {
+                    const unsigned r = __popc(dn & lt);
+                    if (r < (unsigned)__popc(mm)) get = nth_bit(mm, r);
+                }
+                if (get >= 0) K.unpark(L, stash + get * 6);
+                mm &= ~__reduce_or_sync(FULL, get >= 0 ? 1u << get : 0u);
+                __syncwarp();
+            }
+        }
+        if (__all_sync(FULL, L.st == ST_DONE) && mm == 0u && em == 0u) break;
+        if (L.st == ST_INTERACT) K.interact(L);
+        else if (L.st == ST_ESCAPE) K.escape(L);
+        if (L.st == ST_FLIGHT) K.flight(L);
+        if (L.st == ST_FLIGHT) K.flight(L);     // a second modified-random-walk step
+        // march phase
+        for (;;) {
+            if (L.st == ST_MARCH) K.march(L);
+            const unsigned mar = __ballot_sync(FULL, L.st == ST_MARCH);
+            const int nm = __popc(mar);
+            if (nm > t_swap) continue;
+            if (mm) {
+                const unsigned fr = ~(mm | em) & all;
+                int put = -1, get = -1;
+                if (L.st != ST_MARCH) {
+                    const unsigned r = __popc(~mar & lt);
+                    if (r < (unsigned)__popc(mm)) {
+                        get = nth_bit(mm, r);
+                        if (L.st != ST_NEED && L.st != ST_DONE) {
+                            put = nth_bit(fr, r);
+                            K.park(L, stash + put * 6);
+                        }
+                        K.unpark(L, stash + get * 6);
+                    }
+                }
+                mm &= ~__reduce_or_sync(FULL, get >= 0 ? 1u << get : 0u);
+                em |= __reduce_or_sync(FULL, put >= 0 ? 1u << put : 0u);
+                __syncwarp();
+                continue;
+            }
+            if (nm > t_end) continue;
+            break;
+        }
+    }
+}
 
 // Occupancy target of the FP32 kernel: 4 blocks of 256 threads per SM (64
 // registers); four-species variants carry four-wide density and opacity
@@ -1438,6 +1679,15 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (NS == 4 ? 3 : RT_TR
     }
 
     const int min_active = P.march_min_active;
+    if constexpr ((FEAT & 512) != 0) {
+        compact_loop<R, NS, FEAT>(K, L, P, sm, total_work, lane);
+        K.flush_warp(0);
+        if (P.smem_sed) {
+            __syncthreads();
+            K.flush_sed(threadIdx.x, blockDim.x);
+        }
+        return;
+    }
     // Packet ids are claimed per warp in chunks (one global atomic per chunk);
     // the chunk shrinks from 256 to 32 ids as the work runs out, which keeps
     // the tail balanced.  The warp's unclaimed range [claim[0], claim[1]) is
@@ -1589,6 +1839,7 @@ rt_status launch_one(rt_ctx* ctx, const TransportKP& kp, int schedule, int threa
     k.so_cnt = place(sizeof(unsigned) * nsed, 16);
     k.so_mrw = place((FEAT & 1) && kp.mrw ? sizeof(float) * kMrwN : 0, 16);
     k.so_cdf = place(sizeof(float) * kp.smem_cdf, 16);
+    k.so_stash = place((FEAT & 512) ? sizeof(uint4) * 6 * kStash * (threads / 32) : 0, 16);
     const size_t smem = (off + 15) / 16 * 16;
     auto fn = transport_kernel<R, NS, FEAT>;
     RT_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -1658,6 +1909,10 @@ rt_status launch_feat(rt_ctx* ctx, const TransportKP& kp, int schedule, int thre
         const int feat = (kp.mrw ? 1 : 0) |
                          (kp.want_traj ? 2 : ((kp.param_models ? 4 : 0) | (kp.single ? 8 : 0))) |
                          (kp.defer_events ? 16 : 0);
+        if (schedule == RT_SCHED_COMPACT && (feat == 12 || feat == 13)) {
+            if (feat == 13) return launch_one<R, NS, 525>(ctx, kp, schedule, threads, blocks_per_sm, s);
+            return launch_one<R, NS, 524>(ctx, kp, schedule, threads, blocks_per_sm, s);
+        }
         switch (feat) {
         case 0: return launch_one<R, NS, 0>(ctx, kp, schedule, threads, blocks_per_sm, s);
         case 1: return launch_one<R, NS, 1>(ctx, kp, schedule, threads, blocks_per_sm, s);

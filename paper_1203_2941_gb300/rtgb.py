@@ -23,7 +23,7 @@ RT_MODE_BW, RT_MODE_FROZEN_T, RT_MODE_NOREEMIT = 0, 1, 2
 RT_LUCY_OFF, RT_LUCY_THIN, RT_LUCY_ALL = 0, 1, 2
 RT_LUCY_LINEAR, RT_LUCY_EXPM1 = 0, 1
 RT_PREC_FP32, RT_PREC_FP64, RT_PREC_FP32_ACC32 = 0, 1, 2
-RT_SCHED_PERSISTENT, RT_SCHED_SERIAL = 0, 1
+RT_SCHED_PERSISTENT, RT_SCHED_SERIAL, RT_SCHED_COMPACT = 0, 1, 2
 STAT_NAMES = ["crossings", "interactions", "scatters", "absorptions", "mrw_steps", "escaped",
               "stuck", "pah", "events_dropped", "lucy_deposits", "emitted", "pah_dropped",
               "traj_dropped", "n_events", "n_pah", "n_traj", "deferred"]
@@ -56,7 +56,7 @@ class rt_transport_params(C.Structure):
                 ("schedule", C.c_int), ("threads_per_block", C.c_int), ("blocks_per_sm", C.c_int),
                 ("march_min_active", C.c_int), ("defer_events", C.c_uint64),
                 ("source_bins", C.c_uint32), ("pc_cams", C.c_void_p), ("n_pc_cams", C.c_int),
-                ("record_nu_mask", C.c_void_p)]
+                ("record_nu_mask", C.c_void_p), ("compact_swap", C.c_int)]
 
 
 class rt_transport_out(C.Structure):

@@ -246,7 +246,7 @@ def make_params(n_packets: int, mode=R.RT_MODE_BW, lucy_mode=R.RT_LUCY_THIN,
                 max_events=10_000_000, record_events=False, precision=R.RT_PREC_FP32,
                 schedule=R.RT_SCHED_PERSISTENT, threads_per_block=0, blocks_per_sm=0,
                 march_min_active=-1, defer_events=0, source_bins=0,
-                record_nu=None) -> R.rt_transport_params:
+                record_nu=None, compact_swap=-1) -> R.rt_transport_params:
     """Transport parameters; ``record_nu`` lists the frequency bins whose
     scattering events are stored (None: every bin)."""
     p = R.rt_transport_params_default()
@@ -263,6 +263,7 @@ def make_params(n_packets: int, mode=R.RT_MODE_BW, lucy_mode=R.RT_LUCY_THIN,
     p.march_min_active = march_min_active
     p.defer_events = int(defer_events)
     p.source_bins = int(source_bins)
+    p.compact_swap = int(compact_swap)
     if record_nu is not None:
         idx = [int(j) for j in record_nu]
         words = (C.c_uint32 * max(1, (max(idx, default=0) // 32) + 1))()
@@ -403,6 +404,12 @@ def _events_tensor(events):
         return None, 0, None
     if isinstance(events, TransportOut):
         return events.events, events.event_cap, events.stats.data_ptr() + 8 * 13
+    if isinstance(events, torch.Tensor):
+        # device event records (uint8, 20 bytes each), e.g. gathered from several ranks
+        if events.dtype != torch.uint8 or events.numel() % 20 or not events.is_cuda:
+            raise TypeError("device events must be a CUDA uint8 tensor of 20-byte records")
+        n = events.numel() // 20
+        return (events.contiguous(), n, None) if n else (None, 0, None)
     if isinstance(events, np.ndarray):
         if events.dtype != R.EVENT_DTYPE:
             ev = np.zeros(len(events), R.EVENT_DTYPE)
@@ -413,7 +420,7 @@ def _events_tensor(events):
             return None, 0, None
         t = torch.from_numpy(np.ascontiguousarray(events).view(np.uint8).copy()).cuda()
         return t, len(events), None
-    raise TypeError("events must be a TransportOut or a numpy event array")
+    raise TypeError("events must be a TransportOut, a numpy event array or a device record tensor")
 
 
 def raytrace(ctx: Context, grid: Grid, opac: Opacity, T: torch.Tensor, events, xi_ev: float,

@@ -1,0 +1,162 @@
+"""The ray-tracer adjoint at the size of its benchmark configuration (run on
+a GB300): a 128^3 clumpy torus (1000 clumps, silicate + carbon + PAH-like
+species), temperatures held fixed, the loss of a density fit,
+
+    L = sum_f ((F_f - F_obs,f) / (0.1 F_obs,f))^2
+      + sum_views sum_pix ((I - I_obs) / (0.1 I_obs + 1e-3 max I_obs))^2,
+
+F the SED at 40 wavelengths (0.3-500 um) seen from the first view, I the
+256^2 images at 10 um from 8 views, the observation made by the same
+forward model from a perturbed density (30 %, smoothed) with 10 % Gaussian
+noise.
+
+* dL/drho_s of rt_raytrace_backward against central differences (h = 1 %)
+  of the same loss through rt_raytrace on 100 random dusty (species, cell)
+  pairs: 1e-2 relative plus 1e-3 of the largest sampled component.
+* rt_raytrace_backward against the FP64 oracle's adjoint on one view at
+  64^2 pixels (10 um and two SED wavelengths, seeded upstream gradients,
+  the oracle's optically thin temperatures and seeded scattering events):
+  1e-2 relative plus 1e-4 of the largest component; d/d(scale) 1e-3.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rt():
+    import __graft_entry__ as g
+    g.build()
+    import paper_1203_2941_gb300 as rt
+    return rt
+
+
+@pytest.fixture(scope="module")
+def setup(rt):
+    ctx = rt.Context(0)
+    m = W.clumpy_torus(n=128, n_clump=1000, seed=77, nf=100)
+    grid, opac, srcs = ctx.grid(m), ctx.opacity(m), rt.Sources(m.sources)
+    # temperatures and scattering events held fixed: from a prior transport
+    out = rt.transport(ctx, grid, opac, srcs, 2_000_000, event_cap=8_000_000, seed=31,
+                       record_events=True)
+    T = rt.temperatures(ctx, grid, opac, out.E_abs)
+    torch.cuda.synchronize()
+    return ctx, m, grid, opac, srcs, out, T
+
+
+class Fit:
+    """The loss above for one density field (forward through rt_raytrace)."""
+
+    def __init__(self, rt, ctx, m, opac, srcs, out, T, npix=256):
+        self.rt, self.ctx, self.m, self.opac, self.srcs, self.out, self.T = rt, ctx, m, opac, srcs, out, T
+        self.sed_f = W.nearest_freq_indices(m.nu, W.adjoint_sed_wavelengths_um())
+        self.img_f = W.nearest_freq_indices(m.nu, [10.0])
+        D = 14e6 * W.PC
+        self.views = [W.Camera(th, ph, npix, D) for th, ph in W.adjoint_view_angles()]
+        self.sed_cam = [self.views[0]]
+        self.obs = None
+
+    def _chunks(self):
+        return [self.sed_f[i:i + 16] for i in range(0, len(self.sed_f), 16)]
+
+    def forward(self, grid):
+        rt = self.rt
+        img, _ = rt.raytrace(self.ctx, grid, self.opac, self.T, self.out, self.out.xi, self.srcs,
+                             self.views, self.img_f)
+        seds = [rt.raytrace(self.ctx, grid, self.opac, self.T, self.out, self.out.xi, self.srcs,
+                            self.sed_cam, ch)[1] for ch in self._chunks()]
+        return img, torch.cat(seds, dim=1)
+
+    def observe(self, grid, seed=78):
+        img, sed = self.forward(grid)
+        g = torch.Generator(device="cuda").manual_seed(seed)
+        img = img.double()
+        self.I_obs = img * (1 + 0.1 * torch.randn(img.shape, device="cuda", dtype=torch.float64, generator=g))
+        self.F_obs = sed * (1 + 0.1 * torch.randn(sed.shape, device="cuda", dtype=torch.float64, generator=g))
+        self.sI = 0.1 * self.I_obs.abs() + 1e-3 * self.I_obs.abs().max()
+        self.sF = 0.1 * self.F_obs.abs()
+
+    def loss(self, grid):
+        img, sed = self.forward(grid)
+        return float((((sed - self.F_obs) / self.sF) ** 2).sum() + (((img.double() - self.I_obs) / self.sI) ** 2).sum())
+
+    def gradient(self, grid):
+        rt = self.rt
+        img, sed = self.forward(grid)
+        gi = (2 * (img.double() - self.I_obs) / self.sI ** 2).float()
+        gs = 2 * (sed - self.F_obs) / self.sF ** 2
+        drho, dscale = rt.raytrace_backward(self.ctx, grid, self.opac, self.T, self.out, self.out.xi,
+                                            self.srcs, self.views, self.img_f, dL_dimg=gi)
+        for k, ch in enumerate(self._chunks()):
+            o = sum(len(c) for c in self._chunks()[:k])
+            d2, s2 = rt.raytrace_backward(self.ctx, grid, self.opac, self.T, self.out, self.out.xi,
+                                          self.srcs, self.sed_cam, ch, dL_dsed=gs[:, o:o + len(ch)].contiguous())
+            drho += d2
+            dscale += s2
+        return drho, dscale
+
+
+def test_adjoint_matches_central_differences_at_full_size(rt, setup):
+    ctx, m, grid, opac, srcs, out, T = setup
+    fit = Fit(rt, ctx, m, opac, srcs, out, T)
+    g_true = rt.Grid(ctx, torch.tensor(W.perturbed_density(m), device="cuda"), m.box_min, m.cell)
+    fit.observe(g_true)
+    rho0 = torch.tensor(m.rho, device="cuda")
+    work = rt.Grid(ctx, rho0, m.box_min, m.cell)
+    drho, _ = fit.gradient(work)
+    g = drho.cpu().numpy().reshape(m.ns, -1)
+    rho = m.rho.reshape(m.ns, -1)
+    dusty = np.argwhere(rho > 0)
+    pick = dusty[np.random.default_rng(79).choice(len(dusty), size=100, replace=False)]
+    h = 1e-2
+    fd = np.zeros(len(pick))
+    flat = rho0.view(m.ns, -1)
+    for k, (s, c) in enumerate(pick):
+        v = float(rho[s, c])
+        ls = []
+        for sign in (1, -1):
+            pert = flat.clone()
+            pert[s, c] = v * (1 + sign * h)
+            work.update(pert.view_as(rho0))
+            ls.append(fit.loss(work))
+        fd[k] = (ls[0] - ls[1]) / (2 * h * v)
+    work.update(rho0)
+    ga = np.array([g[s, c] for s, c in pick])
+    scale = np.abs(ga).max()
+    assert scale > 0
+    bad = np.abs(ga - fd) > 1e-2 * np.abs(fd) + 1e-3 * scale
+    assert not bad.any(), (np.nonzero(bad)[0][:5], ga[bad][:5], fd[bad][:5])
+
+
+def test_adjoint_matches_oracle_on_one_view(rt, setup, O):
+    ctx, m, grid, opac, srcs, out, T = setup
+    Tg = O.temperature_guess(m)
+    rng = np.random.default_rng(80)
+    ev = np.zeros(20000, dtype=O.EVENT_DTYPE)
+    fidx = W.nearest_freq_indices(m.nu, [10.0, 2.2, 70.0])
+    ev["cell"] = rng.integers(0, m.ncell, len(ev))
+    ev["nu"] = rng.choice(fidx, len(ev))
+    ev["species"] = rng.integers(0, m.ns, len(ev))
+    k = rng.normal(size=(len(ev), 3))
+    ev["k"] = (k / np.linalg.norm(k, axis=1, keepdims=True)).astype(np.float32)
+    xi = m.luminosity / 1e6
+    th, ph = W.adjoint_view_angles()[2]
+    cams = [W.Camera(th, ph, 64, 14e6 * W.PC)]
+    wi = rng.normal(size=(1, len(fidx), 64, 64)).astype(np.float32)
+    ws = rng.normal(size=(1, len(fidx)))
+    drho, dscale = rt.raytrace_backward(ctx, grid, opac, torch.tensor(Tg, device="cuda"), ev, xi, srcs,
+                                        cams, fidx, dL_dimg=torch.tensor(wi, device="cuda"),
+                                        dL_dsed=torch.tensor(ws, device="cuda"))
+    torch.cuda.synchronize()
+    gr, gsr = O.raytrace_backward(m, Tg, ev, xi, cams, fidx, wi.astype(np.float64), ws)
+    g = drho.cpu().numpy()
+    scale = np.abs(gr).max()
+    bad = np.abs(g - gr) > 1e-2 * np.abs(gr) + 1e-4 * scale
+    assert not bad.any(), (int(bad.sum()), np.abs(g - gr).max() / scale)
+    assert abs(float(dscale.item()) / gsr - 1) < 1e-3

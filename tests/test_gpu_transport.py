@@ -373,6 +373,52 @@ def test_fp32_mrw_transport_matches_oracle(rt, ctx, O):
     assert np.all(g["S"][~lit] == 0)
 
 
+@pytest.mark.parametrize("mrw", [False, True])
+def test_compaction_keeps_every_packet_history(rt, ctx, O, mrw):
+    """Per-warp packet compaction (RT_SCHED_COMPACT) moves packets between
+    lanes and a shared-memory stash; each packet's registers are restored
+    exactly, so in the frozen-T mode (order-independent) the counts of every
+    kind, the per-cell absorption counts and the escaped-packet counts equal
+    those of the persistent schedule bit for bit, and the FP64 energies agree
+    to the order of the atomic additions.  B&W with compaction conserves
+    energy exactly."""
+    m = W.r2_shell(n=24, tau_1um=10.0, nf=32) if not mrw else W.uniform_cube(n=6, tau_cell=25.0, nf=8, albedo=0.4)
+    grid, opac, srcs = _setup(rt, ctx, m)
+    T0 = torch.tensor(O.temperature_guess(m) if not mrw else np.full((1, m.ncell), 300.0), device="cuda")
+    N = 200000
+    res, evs = {}, {}
+    for name, sched in (("persistent", rt.rtgb.RT_SCHED_PERSISTENT), ("compact", rt.rtgb.RT_SCHED_COMPACT)):
+        o = rt.transport(ctx, grid, opac, srcs, N, mode=rt.rtgb.RT_MODE_FROZEN_T, T_prev=T0, seed=13,
+                         schedule=sched, mrw=mrw, event_cap=40 * N, record_events=True)
+        torch.cuda.synchronize()
+        res[name] = o.numpy()
+        evs[name] = o.events_numpy()
+    a, b = res["persistent"], res["compact"]
+    for k in ("crossings", "interactions", "scatters", "absorptions", "mrw_steps", "escaped",
+              "lucy_deposits", "emitted", "stuck", "n_events"):
+        assert a["stats"][k] == b["stats"][k], k
+    assert b["stats"]["escaped"] + b["stats"]["stuck"] == N
+    np.testing.assert_array_equal(a["count"], b["count"])
+    np.testing.assert_array_equal(a["sed_cnt"], b["sed_cnt"])
+    np.testing.assert_allclose(b["E_abs"], a["E_abs"], rtol=1e-9, atol=1e-12 * a["E_abs"].max())
+    np.testing.assert_allclose(b["esq"], a["esq"], rtol=1e-9, atol=1e-12 * a["esq"].max())
+    np.testing.assert_allclose(b["sed_esc"], a["sed_esc"], rtol=1e-12, atol=0)
+    if mrw:
+        assert b["stats"]["mrw_steps"] > N
+    # the same event records (as a multiset: the order of appends differs)
+    ea = np.sort(evs["persistent"], order=["cell", "nu", "species"])
+    eb = np.sort(evs["compact"], order=["cell", "nu", "species"])
+    assert len(ea) == len(eb) > 0
+    for f in ("cell", "nu", "species"):
+        np.testing.assert_array_equal(ea[f], eb[f])
+    # B&W with compaction: every packet escapes, the escaped SED sums to L
+    o = rt.transport(ctx, grid, opac, srcs, N, seed=14, schedule=rt.rtgb.RT_SCHED_COMPACT, mrw=mrw)
+    torch.cuda.synchronize()
+    g = o.numpy()
+    assert g["stats"]["escaped"] + g["stats"]["stuck"] == N
+    assert abs(g["sed_esc"].sum() / (m.luminosity * g["stats"]["escaped"] / N) - 1) < 1e-9
+
+
 def test_edge_cases(rt, ctx, O):
     # empty grid: every packet escapes on its first flight, no interaction
     m = W.uniform_cube(n=5, tau_cell=0.5)

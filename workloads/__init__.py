@@ -534,3 +534,40 @@ def image_wavelengths_um():
 def nearest_freq_indices(nu, lam_um: Sequence[float]):
     lam = wavelength_um(nu)
     return [int(np.argmin(np.abs(np.log(lam / l)))) for l in lam_um]
+
+
+# --------------------------------------------------------------------------
+# Synthetic observation for the ray-tracer adjoint (a density fit): the
+# SED wavelengths, the eight viewing angles and the "true" density that the
+# synthetic observation is made from, all seeded.
+
+def adjoint_sed_wavelengths_um(n: int = 40) -> List[float]:
+    """n log-spaced SED wavelengths over 0.3-500 um, the one nearest 10 um
+    replaced by 10 um."""
+    lam = np.geomspace(0.3, 500.0, n)
+    lam[int(np.argmin(np.abs(np.log(lam / 10.0))))] = 10.0
+    return [float(v) for v in lam]
+
+
+def adjoint_view_angles():
+    """Eight viewing directions (theta, phi in radians) of the image part of
+    the fit: inclinations 10-150 degrees, azimuths 45 degrees apart."""
+    return [(math.radians(th), math.radians(45.0 * k))
+            for k, th in enumerate((10, 30, 50, 70, 90, 110, 130, 150))]
+
+
+def perturbed_density(model: Model, sigma: float = 0.3, seed: int = 78) -> np.ndarray:
+    """The density a synthetic observation is made from: rho (1 + sigma n),
+    n a standard normal field smoothed over 3^3 cells and rescaled to unit
+    variance, the factor clipped at 0.05 (same factor for every species)."""
+    rng = np.random.default_rng(seed)
+    shape = model.rho.shape[1:]
+    g = rng.normal(size=shape)
+    s = np.zeros_like(g)
+    for dz in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                s += np.roll(g, (dz, dy, dx), axis=(0, 1, 2))
+    s /= s.std()
+    f = np.clip(1.0 + sigma * s, 0.05, None)
+    return (model.rho * f[None]).astype(np.float32)
