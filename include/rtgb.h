@@ -217,6 +217,13 @@ typedef struct {
                                  frequencies of the ray tracer, whose scattering
                                  source, Eq. 16, uses events at those frequencies
                                  alone); NULL = every bin.  (n_freq + 31) / 32 words */
+    const int32_t* source_grid_nu;   /* with source_bins = m: host [m] model frequency bin
+                                 of each bin of the separate source grid of Eq. 1
+                                 (rt_source_grid); packet pid is emitted from source
+                                 grid_src[b] in bin grid_nu[b], b = floor(pid m / N).
+                                 NULL: bins on the model grid (see source_bins).
+                                 rt_transport only */
+    const int32_t* source_grid_src;  /* host [m] source index of each bin (with the above) */
     int compact_swap;         /* RT_SCHED_COMPACT: when at most this many lanes of a
                                  warp still march, its stopped lanes trade their
                                  packets for parked marching ones (0..31; -1 = 24) */
@@ -346,6 +353,24 @@ RT_API rt_status rt_pah_reemit(rt_ctx* ctx, const rt_grid* grid, const rt_opacit
                                const rt_transport_params* p, const double* T_prev,
                                const rt_transport_out* out, rt_stream stream);
 
+/* The separate source frequency grid of Eq. 1 (Sect. 2): the sources'
+ * combined luminosity L cut into m bins of equal energy L/m on each source's
+ * own continuous spectrum -- a blackbody of T_eff, or a tabulated L_nu taken
+ * constant over each model frequency bin -- between the outer edges of the
+ * model bins (edges at the geometric means of neighbouring frequencies, the
+ * outer ones mirrored in ln nu).  Bin b is monochromatic at nu_star[b], where
+ * the cumulative luminosity reaches (b + 1/2) L/m (the sources taken in
+ * order, by their luminosities); src_idx[b] is its source and nu_idx[b] the
+ * model bin holding nu_star[b] (the dust grid extends the source grid,
+ * Sect. 2).  Pass nu_idx and src_idx as rt_transport_params.source_grid_nu /
+ * source_grid_src with source_bins = m to emit N/m packets per bin.
+ * Host arrays [m]; nu_star may be NULL.  FP64 on the host (the blackbody's
+ * cumulative by Simpson's rule on 2^15 intervals in ln nu, targets solved by
+ * Newton steps).  Errors: RT_ERR_INVALID_ARG for m = 0, no source or NULL
+ * outputs. */
+RT_API rt_status rt_source_grid(const rt_opacity* opac, const rt_source* sources, int n_sources,
+                                uint32_t m, int32_t* nu_idx, int32_t* src_idx, double* nu_star);
+
 /* Allocation-free variant of rt_transport (no counterpart in the paper; it
  * exists for callers that must not allocate device memory).  Same arguments,
  * semantics, outputs and errors as rt_transport, but the call itself never
@@ -366,8 +391,9 @@ RT_API rt_status rt_pah_reemit(rt_ctx* ctx, const rt_grid* grid, const rt_opacit
  * share the one array: calls whose GPU work overlaps (different streams
  * without ordering, or several host threads) race and must not be issued;
  * calls ordered on one stream are safe (each clears what must start at zero).
- * Photon-counting cameras, the deferred-packet queue and the plain-FP32 form
- * are not served here: n_pc_cams and defer_events must be 0 and precision not
+ * Photon-counting cameras, the deferred-packet queue, the separate source
+ * grid and the plain-FP32 form are not served here: n_pc_cams and
+ * defer_events must be 0, source_grid_nu NULL and precision not
  * RT_PREC_FP32_ACC32, else RT_ERR_INVALID_ARG. */
 RT_API rt_status rt_transport_noalloc(rt_ctx* ctx, const rt_grid* grid, const rt_opacity* opac,
                                       const rt_source* sources, int n_sources,

@@ -64,7 +64,8 @@ class _Params(C.Structure):
                 ("mrw_gamma", C.c_double), ("seed", C.c_uint64), ("model_id", C.c_uint32),
                 ("n_packets", C.c_uint64), ("pid_begin", C.c_uint64), ("pid_end", C.c_uint64),
                 ("max_events", C.c_uint64), ("record_events", C.c_int),
-                ("source_bins", C.c_uint32), ("pc", C.c_void_p), ("n_pc", C.c_int)]
+                ("source_bins", C.c_uint32), ("pc", C.c_void_p), ("n_pc", C.c_int),
+                ("sg_nu", C.c_void_p), ("sg_src", C.c_void_p)]
 
 
 class _PcCamera(C.Structure):
@@ -137,6 +138,9 @@ def lib():
             L.or_transport.restype = C.c_int
             L.or_transport.argtypes = [C.POINTER(_Model), C.POINTER(_Source), C.c_int,
                                        C.POINTER(_Params), C.c_void_p, C.POINTER(_Out), C.c_int]
+            L.or_source_grid.restype = C.c_int
+            L.or_source_grid.argtypes = [C.POINTER(_Model), C.POINTER(_Source), C.c_int, C.c_uint32,
+                                         C.c_void_p, C.c_void_p, C.c_void_p]
             L.or_pah_reemit.restype = C.c_int
             L.or_pah_reemit.argtypes = [C.POINTER(_Model), C.POINTER(_PahSrc), C.POINTER(_Params),
                                         C.c_void_p, C.POINTER(_Out), C.c_int]
@@ -212,7 +216,7 @@ def transport(model, n_packets, seed=1, model_id=0, mode=MODE_BW, lucy_mode=LUCY
               lucy_form=LUCY_LINEAR, lucy_tau=1e-2, mrw=False, mrw_tau_cell=10.0, mrw_gamma=2.0,
               pid_begin=0, pid_end=None, max_events=10_000_000, record_events=False,
               event_cap=0, pah_cap=0, traj_cap=0, T_prev=None, n_threads=1, esq=True,
-              accumulate=None, source_bins=0, pc_cameras=(), _pah=None):
+              accumulate=None, source_bins=0, pc_cameras=(), source_grid=None, _pah=None):
     """Run packets [pid_begin, pid_end) of an N = n_packets emission and return
     a dict of numpy arrays (E_abs, count, esq, sed_esc, sed_cnt, events, pah,
     traj, stats, pc_img).  ``accumulate`` may hold a previous result dict whose
@@ -231,6 +235,11 @@ def transport(model, n_packets, seed=1, model_id=0, mode=MODE_BW, lucy_mode=LUCY
                                                          float(c[3]), float(c[4])) for c in pcs])
     if pcs:
         p.pc, p.n_pc = C.cast(pc_arr, C.c_void_p), len(pcs)
+    if source_grid is not None:
+        sg_nu = np.ascontiguousarray(source_grid[0], dtype=np.int32)
+        sg_src = np.ascontiguousarray(source_grid[1], dtype=np.int32)
+        assert len(sg_nu) == len(sg_src) == int(source_bins)
+        p.sg_nu, p.sg_src = _ptr(sg_nu), _ptr(sg_src)
     pc_img = np.zeros(sum(nf * int(c[2]) ** 2 for c in pcs))
     if accumulate is not None and pcs:
         pc_img = np.concatenate([a.reshape(-1) for a in accumulate["pc_img"]]).copy()
@@ -269,6 +278,19 @@ def transport(model, n_packets, seed=1, model_id=0, mode=MODE_BW, lucy_mode=LUCY
                 events=ev[:out.n_events], pah=pah[:out.n_pah], traj=tr[:out.n_traj],
                 stats=stats, xi=model_luminosity(om) / n_packets if _pah is None else _pah.xi,
                 pc_img=imgs, loop_seconds=float(out.loop_seconds))
+
+
+def source_grid(model, m_bins):
+    """The Eq. 1 source frequency grid: (model bin index, source index,
+    frequency in Hz) of each of the m_bins equal-energy source bins."""
+    om = _om(model)
+    nu = np.zeros(m_bins, np.int32)
+    src = np.zeros(m_bins, np.int32)
+    fr = np.zeros(m_bins)
+    rc = lib().or_source_grid(C.byref(om.c), om.srcs, om.nsrc, int(m_bins), _ptr(nu), _ptr(src), _ptr(fr))
+    if rc != 0:
+        raise ValueError("oracle source grid rejected its arguments")
+    return nu, src, fr
 
 
 def pah_reemit(model, records, xi, eps, eps_class=None, **kw):

@@ -158,6 +158,113 @@ void or_source_lnu(const or_model* m, const or_source* src, double* lnu)
 }
 
 /* ------------------------------------------------------------------------ */
+/* Source frequency grid of Eq. 1                                            */
+/* ------------------------------------------------------------------------ */
+/* G(x) = int_0^x t^3 / (e^t - 1) dt, the blackbody's cumulative in
+ * x = h nu / k T: for x >= 2 the exponential series
+ *   G(x) = pi^4 / 15 - sum_k e^{-k x} (x^3/k + 3 x^2/k^2 + 6 x/k^3 + 6/k^4),
+ * for x < 2 the power series from t / (e^t - 1) = sum_n B_n t^n / n!,
+ *   G(x) = sum_n B_n x^(n+3) / (n! (n + 3))   (converges for x < 2 pi). */
+static double bb_cumulative(double x)
+{
+    if (x <= 0.0) return 0.0;
+    if (x >= 2.0) {
+        double s = 0.0;
+        for (int k = 1; k < 200; ++k) {
+            const double e = exp(-k * x);
+            const double t = e * (x * x * x / k + 3.0 * x * x / ((double)k * k) +
+                                  6.0 * x / ((double)k * k * k) + 6.0 / ((double)k * k * k * k));
+            s += t;
+            if (t < 1e-18 * s) break;
+        }
+        return OR_PI * OR_PI * OR_PI * OR_PI / 15.0 - s;
+    }
+    /* Bernoulli numbers B_0, B_1, B_2, B_4, ..., B_30 (odd ones above 1 vanish) */
+    static const double Bn[17] = { 1.0, -0.5, 1.0 / 6.0, -1.0 / 30.0, 1.0 / 42.0, -1.0 / 30.0,
+                                   5.0 / 66.0, -691.0 / 2730.0, 7.0 / 6.0, -3617.0 / 510.0,
+                                   43867.0 / 798.0, -174611.0 / 330.0, 854513.0 / 138.0,
+                                   -236364091.0 / 2730.0, 8553103.0 / 6.0,
+                                   -23749461029.0 / 870.0, 8615841276005.0 / 14322.0 };
+    double s = x * x * x / 3.0 - 0.5 * x * x * x * x / 4.0;   /* n = 0, 1 */
+    double fact = 1.0;                                          /* n! */
+    double xp = x * x * x;                                      /* x^(n+3) at n = 0 */
+    int nprev = 0;
+    for (int i = 2; i < 17; ++i) {
+        const int n = 2 * (i - 1);
+        for (int q = nprev + 1; q <= n; ++q) { fact *= q; xp *= x; }
+        nprev = n;
+        s += Bn[i] * xp / (fact * (n + 3));
+    }
+    return s;
+}
+
+/* edges of the model frequency bins: geometric means of neighbouring
+ * frequencies, the outer edges mirrored in ln nu */
+static void model_edges(const or_model* m, double* e)
+{
+    for (int j = 1; j < m->nf; ++j) e[j] = sqrt(m->nu[j - 1] * m->nu[j]);
+    e[0] = m->nf > 1 ? m->nu[0] * m->nu[0] / e[1] : 0.5 * m->nu[0];
+    e[m->nf] = m->nf > 1 ? m->nu[m->nf - 1] * m->nu[m->nf - 1] / e[m->nf - 1] : 2.0 * m->nu[0];
+}
+
+/* cumulative luminosity of source s from the lower model edge to nu, in
+ * units of its total over the model range (continuous spectrum) */
+static double src_cumulative(const or_model* m, const or_source* s, const double* e, double nu)
+{
+    if (nu <= e[0]) return 0.0;
+    if (nu >= e[m->nf]) return 1.0;
+    if (s->L_nu) {
+        double tot = 0.0, below = 0.0;
+        for (int j = 0; j < m->nf; ++j) {
+            const double w = s->L_nu[j] * (e[j + 1] - e[j]);
+            if (nu >= e[j + 1]) below += w;
+            else if (nu > e[j]) below += s->L_nu[j] * (nu - e[j]);
+            tot += w;
+        }
+        return tot > 0.0 ? below / tot : 0.0;
+    }
+    const double a = OR_H / (OR_K * s->T_eff);
+    const double g0 = bb_cumulative(a * e[0]), g1 = bb_cumulative(a * e[m->nf]);
+    return (bb_cumulative(a * nu) - g0) / (g1 - g0);
+}
+
+int or_source_grid(const or_model* m, const or_source* src, int nsrc, uint32_t mbins,
+                   int32_t* nu_idx, int32_t* src_idx, double* nu_star)
+{
+    if (nsrc < 1 || mbins < 1 || m->nf < 1) return 1;
+    double* e = (double*)malloc(sizeof(double) * (m->nf + 1));
+    model_edges(m, e);
+    double Ltot = 0.0;
+    for (int i = 0; i < nsrc; ++i) Ltot += src[i].L;
+    for (uint32_t b = 0; b < mbins; ++b) {
+        /* the source where the running sum of the L_i first reaches the
+         * point, then the frequency within it */
+        const double target = ((double)b + 0.5) / (double)mbins * Ltot;
+        double below = 0.0;
+        int si = 0;
+        for (; si < nsrc - 1; ++si) {
+            if (below + src[si].L >= target) break;
+            below += src[si].L;
+        }
+        const double f = src[si].L > 0.0 ? (target - below) / src[si].L : 0.5;
+        /* bisection in ln nu on the continuous cumulative */
+        double lo = log(e[0]), hi = log(e[m->nf]);
+        for (int it = 0; it < 200 && hi - lo > 1e-15 * fabs(hi); ++it) {
+            const double mid = 0.5 * (lo + hi);
+            if (src_cumulative(m, &src[si], e, exp(mid)) < f) lo = mid; else hi = mid;
+        }
+        const double nus = exp(0.5 * (lo + hi));
+        int j = 0;
+        while (j < m->nf - 1 && nus >= e[j + 1]) ++j;
+        nu_idx[b] = j;
+        src_idx[b] = si;
+        if (nu_star) nu_star[b] = nus;
+    }
+    free(e);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Grid helpers                                                              */
 /* ------------------------------------------------------------------------ */
 static int64_t ncube_of(const or_model* m) { return (int64_t)m->nx * m->ny * m->nz; }
@@ -621,6 +728,12 @@ static void run_packet(const or_ctx* C, or_out* o, uint64_t pid)
              * frequency bin. */
             const uint64_t b = (pid * (uint64_t)p->source_bins) / p->n_packets;
             const double u = ((double)b + 0.5) / (double)p->source_bins;
+            if (p->sg_nu) {
+                /* the separate source grid of Eq. 1 (or_source_grid) */
+                si = p->sg_src[b];
+                j = p->sg_nu[b];
+                goto emitted;
+            }
             double tot = 0.0;
             for (int i = 0; i < C->nsrc; ++i) tot += C->src_L[i];
             const double target = u * tot;
@@ -633,6 +746,7 @@ static void run_packet(const or_ctx* C, or_out* o, uint64_t pid)
             const double uf = (target - below) / (upto - below);
             j = pick_cdf(C->src_w + (size_t)si * m->nf, m->nf, uf);
         }
+    emitted:
         { double u1 = rng_u(&r), u2 = rng_u(&r); iso_dir(u1, u2, k); }
         for (int a = 0; a < 3; ++a) x[a] = C->src[si].pos[a];
         locate(m, x, k, &idx);
@@ -811,6 +925,11 @@ static int transport_impl(const or_model* m, const or_source* src, int nsrc,
 {
     if (m->nf < 1 || m->ns < 1 || m->ns > 64 || p->n_packets == 0) return 1;
     if (p->pid_end < p->pid_begin || p->pid_end > p->n_packets) return 1;
+    if (p->sg_nu && p->source_bins > 0) {
+        if (!p->sg_src) return 1;
+        for (uint32_t b = 0; b < p->source_bins; ++b)
+            if (p->sg_nu[b] < 0 || p->sg_nu[b] >= m->nf || p->sg_src[b] < 0 || p->sg_src[b] >= nsrc) return 1;
+    }
     if (p->n_pc < 0 || (p->n_pc > 0 && !p->pc)) return 1;
     for (int c = 0; c < p->n_pc; ++c)
         if (p->pc[c].npix < 1) return 1;

@@ -68,6 +68,9 @@ typedef struct {
                                from bin floor(pid m / N) (see or_transport) */
     const or_pc_camera* pc;  /* [n_pc] photon-counting cameras (or NULL) */
     int n_pc;
+    const int32_t* sg_nu;    /* with source_bins = m: the source frequency grid of Eq. 1
+                                (or_source_grid), source bin b's model frequency bin and */
+    const int32_t* sg_src;   /* source ([m] each); NULL: bins on the model grid (reading 20) */
 } or_params;
 
 typedef struct { uint32_t cell, nu, species, pad; double k[3]; } or_event;
@@ -129,6 +132,17 @@ int or_dda_segments(const or_model* m, const double x[3], const double k[3], int
 /* the path */
 int or_transport(const or_model* m, const or_source* src, int nsrc, const or_params* p,
                  const double* T_prev, or_out* out, int n_threads);
+/* The source frequency grid of Eq. 1 (Sect. 2): the sources' combined
+ * luminosity cut into mbins bins of equal energy on each source's own
+ * continuous spectrum (a blackbody of T_eff; a tabulated L_nu is constant over
+ * each model frequency bin), between the outer edges of the model frequency
+ * bins (bin edges at the geometric means of neighbouring frequencies, the
+ * outer ones mirrored).  Bin b is monochromatic at nu_star[b], where the
+ * cumulative luminosity reaches (b + 1/2) L / mbins; src_idx[b] is its source
+ * and nu_idx[b] the model bin holding nu_star[b].  Returns 0, or 1 for bad
+ * arguments. */
+int or_source_grid(const or_model* m, const or_source* src, int nsrc, uint32_t mbins,
+                   int32_t* nu_idx, int32_t* src_idx, double* nu_star);
 /* Runs packets [pid_begin, pid_end) of the pass; p->n_packets must equal
  * ps->n_rec and p->source_bins must be 0.  Packet pid starts from rec[pid]. */
 int or_pah_reemit(const or_model* m, const or_pah_src* ps, const or_params* p,

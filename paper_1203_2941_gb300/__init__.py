@@ -11,9 +11,9 @@ from .builder import build
 from .rtgb import RtError, load, rt_version
 from .sim import (Batch, Context, Grid, Opacity, PcCamera, RayTrace, Sources, TransportOut,
                   cameras, make_params, mrw_sample, pah_reemit, philox, raytrace, raytrace_backward,
-                  temperature_guess, temperatures, transport, visibilities)
+                  source_grid, temperature_guess, temperatures, transport, visibilities)
 
 __all__ = ["rtgb", "autotune", "build", "load", "rt_version", "RtError", "Context", "Grid", "Opacity",
            "Sources", "TransportOut", "transport", "temperatures", "temperature_guess",
            "raytrace", "raytrace_backward", "RayTrace", "philox", "mrw_sample", "Batch", "cameras",
-           "make_params", "visibilities", "PcCamera", "pah_reemit"]
+           "make_params", "visibilities", "PcCamera", "pah_reemit", "source_grid"]

@@ -567,6 +567,8 @@ static void fill_kp(TransportKP& kp, const rt_opacity* op, const rt_transport_pa
     kp.smem_cdf = 0;
     kp.max_events = p->max_events;
     kp.source_bins = p->source_bins;
+    kp.sg_nu = nullptr;                // set by rt_transport for a separate source grid
+    kp.sg_src = nullptr;
     kp.defer_events = 0;               // set by rt_transport when it allocates a queue
     kp.defer = nullptr;
     kp.defer_n = nullptr;
@@ -702,6 +704,14 @@ static rt_status transport_one(rt_ctx* ctx, const rt_grid* grid, const rt_opacit
         return fail(RT_ERR_INVALID_ARG, "rt_transport: photon-counting cameras need out->pc_img");
     if (p->mode == RT_MODE_FROZEN_T && !T_prev)
         return fail(RT_ERR_INVALID_ARG, "rt_transport: frozen-T mode needs T_prev");
+    if (p->source_grid_nu || p->source_grid_src) {
+        if (!p->source_grid_nu || !p->source_grid_src || p->source_bins == 0 || pp)
+            return fail(RT_ERR_INVALID_ARG, "rt_transport: a source grid needs both tables and source_bins > 0");
+        for (uint32_t b = 0; b < p->source_bins; ++b)
+            if (p->source_grid_nu[b] < 0 || p->source_grid_nu[b] >= op->nf || p->source_grid_src[b] < 0 ||
+                p->source_grid_src[b] >= n_sources)
+                return fail(RT_ERR_INVALID_ARG, "rt_transport: source grid entry out of range");
+    }
     RT_CUDA(cudaSetDevice(ctx->device));
     std::vector<HostModel> hms(1);
     st = make_model(grid, op, sources, n_sources, p->n_packets, p->pid_begin, p->model_id, 0,
@@ -772,6 +782,25 @@ static rt_status transport_one(rt_ctx* ctx, const rt_grid* grid, const rt_opacit
         kp.n_eps = pp->n_eps;
         kp.smem_cdf = 0;
     }
+    // the separate source grid's tables (Eq. 1)
+    char* gbuf = nullptr;
+    if (p->source_grid_nu) {
+        const size_t n = p->source_bins;
+        cudaError_t e = cudaMallocAsync((void**)&gbuf, 2 * sizeof(int32_t) * n, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(gbuf, p->source_grid_nu, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(gbuf + sizeof(int32_t) * n, p->source_grid_src, sizeof(int32_t) * n,
+                                cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) {
+            cudaFreeAsync(dm.buf, s);
+            if (acc) cudaFreeAsync(acc, s);
+            if (ebuf) cudaFreeAsync(ebuf, s);
+            if (gbuf) cudaFreeAsync(gbuf, s);
+            return cuda_fail(e, "rt_transport source grid");
+        }
+        kp.sg_nu = (const int*)gbuf;
+        kp.sg_src = (const int*)(gbuf + sizeof(int32_t) * n);
+    }
     // deferred packets: a queue in device memory, drained by a second launch
     char* qbuf = nullptr;
     if (p->defer_events > 0) {
@@ -783,6 +812,7 @@ static rt_status transport_one(rt_ctx* ctx, const rt_grid* grid, const rt_opacit
             cudaFreeAsync(dm.buf, s);
             if (acc) cudaFreeAsync(acc, s);
             if (ebuf) cudaFreeAsync(ebuf, s);
+            if (gbuf) cudaFreeAsync(gbuf, s);
             if (qbuf) cudaFreeAsync(qbuf, s);
             return cuda_fail(e, "rt_transport defer queue");
         }
@@ -808,6 +838,7 @@ static rt_status transport_one(rt_ctx* ctx, const rt_grid* grid, const rt_opacit
     cudaFreeAsync(dm.buf, s);
     if (acc) cudaFreeAsync(acc, s);
     if (ebuf) cudaFreeAsync(ebuf, s);
+    if (gbuf) cudaFreeAsync(gbuf, s);
     if (qbuf) cudaFreeAsync(qbuf, s);
     return st;
 }
@@ -828,6 +859,8 @@ rt_status rt_batch_create(rt_ctx* ctx, const rt_opacity* op, int n_models, const
         return fail(RT_ERR_INVALID_ARG, "rt_batch_create: photon-counting cameras are served by rt_transport only");
     if (p->precision == RT_PREC_FP32_ACC32)
         return fail(RT_ERR_INVALID_ARG, "rt_batch_create: the plain-FP32 form is served by rt_transport only");
+    if (p->source_grid_nu || p->source_grid_src)
+        return fail(RT_ERR_INVALID_ARG, "rt_batch_create: the separate source grid is served by rt_transport only");
     RT_CUDA(cudaSetDevice(ctx->device));
     std::vector<HostModel> hms(n_models);
     std::vector<uint64_t> nwork(n_models);
@@ -1137,6 +1170,8 @@ rt_status rt_transport_noalloc(rt_ctx* ctx, const rt_grid* grid, const rt_opacit
         return fail(RT_ERR_INVALID_ARG, "rt_transport_noalloc: the plain-FP32 form is served by rt_transport only");
     if (p->defer_events != 0)
         return fail(RT_ERR_INVALID_ARG, "rt_transport_noalloc: the deferred-packet queue (defer_events) is served by rt_transport only");
+    if (p->source_grid_nu || p->source_grid_src)
+        return fail(RT_ERR_INVALID_ARG, "rt_transport_noalloc: the separate source grid is served by rt_transport only");
     if (p->mode == RT_MODE_FROZEN_T && !T_prev)
         return fail(RT_ERR_INVALID_ARG, "rt_transport_noalloc: frozen-T mode needs T_prev");
     // scratch layout: staging | kext | packed density | FP64 energy scratch
@@ -1194,6 +1229,18 @@ rt_status rt_philox(rt_ctx* ctx, const uint32_t ctr0[4], const uint32_t key[2], 
     if ((uint64_t)ctr0[0] + n > 0x100000000ull) return fail(RT_ERR_INVALID_ARG, "rt_philox: counter word 0 would wrap");
     RT_CUDA(cudaSetDevice(ctx->device));
     return launch_philox(ctr0, key, n, out, (cudaStream_t)stream);
+}
+
+rt_status rt_source_grid(const rt_opacity* op, const rt_source* sources, int n_sources, uint32_t m,
+                         int32_t* nu_idx, int32_t* src_idx, double* nu_star)
+{
+    if (!op) return fail(RT_ERR_INVALID_ARG, "rt_source_grid: NULL opacity");
+    if (!sources || n_sources < 1) return fail(RT_ERR_INVALID_ARG, "rt_source_grid: no source");
+    if (m == 0 || !nu_idx || !src_idx) return fail(RT_ERR_INVALID_ARG, "rt_source_grid: need m > 0 and output arrays");
+    for (int i = 0; i < n_sources; ++i)
+        if (!(sources[i].L >= 0.0) || (!sources[i].L_nu && !(sources[i].T_eff > 0.0)))
+            return fail(RT_ERR_INVALID_ARG, "rt_source_grid: a source needs L >= 0 and T_eff > 0 or L_nu");
+    return build_source_grid(op, sources, n_sources, m, nu_idx, src_idx, nu_star);
 }
 
 rt_status rt_probe_gather(rt_ctx* ctx, const void* buf, size_t bytes, uint64_t n_reads, uint32_t seed,

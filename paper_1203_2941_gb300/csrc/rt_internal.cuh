@@ -187,6 +187,8 @@ struct TransportKP {
     int compact_swap;                   // compaction: swap stopped lanes at <= this many marching
     unsigned long long max_events;
     unsigned long long source_bins;     // 0: random source bins; m: Eq. 1 equal-energy bins
+    const int* sg_nu;                   // with source_bins: the separate source grid's model bin
+    const int* sg_src;                  // and source of each source bin (device), or NULL
     unsigned long long defer_events;    // 0 = off
     DeferRec* defer;                    // queue (main pass appends, resume pass reads)
     unsigned long long* defer_n;        // queue cursor (device)
@@ -289,6 +291,8 @@ __device__ __forceinline__ double rcp_approx(double x)
 // ----------------------------------------------------------------- cross-TU host entry points
 namespace rtgb {
 rt_status build_opacity_tables(rt_opacity* op);
+rt_status build_source_grid(const rt_opacity* op, const rt_source* src, int nsrc, uint32_t m,
+                            int32_t* nu_idx, int32_t* src_idx, double* nu_star);
 rt_status pack_grid(rt_grid* g, const rt_opacity* op, int lucy_mode, double lucy_tau, int prec,
                     cudaStream_t s);
 rt_status pack_grid_into(const rt_grid* g, const rt_opacity* op, int lucy_mode, double lucy_tau,

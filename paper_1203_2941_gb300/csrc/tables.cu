@@ -39,6 +39,117 @@ void source_spectrum(const rt_opacity* op, const rt_source& src, std::vector<dou
     for (int j = 0; j < op->nf; ++j) lnu[j] = tot > 0.0 ? src.L * lnu[j] / tot : 0.0;
 }
 
+// ------------------------------------------------------------------------
+// Source frequency grid of Eq. 1 (Sect. 2): the sources' combined luminosity
+// cut into m bins of equal energy on each source's own continuous spectrum
+// (a blackbody of T_eff; a tabulated L_nu is constant over each model
+// frequency bin) between the outer edges of the model bins, whose edges are
+// the geometric means of neighbouring frequencies (outer edges mirrored in
+// ln nu).  Bin b is monochromatic at the frequency where the cumulative
+// luminosity reaches (b + 1/2) L/m -- its source first, by the running sum of
+// the sources' luminosities -- and belongs to the model bin holding it.
+//
+// The blackbody's cumulative is tabulated in ln nu on 2^15 intervals by
+// Simpson's rule (relative error ~1e-14); a target inside an interval is
+// solved by Newton steps on the single-panel Simpson integral from the
+// interval's start.
+namespace {
+
+struct SourceCum {
+    bool tab = false;
+    std::vector<double> F;        // cumulative at the nodes (blackbody) or bin ends (tabulated)
+    double t0 = 0.0, h = 0.0, a = 0.0;
+    const std::vector<double>* e = nullptr;
+    const double* lnu = nullptr;
+
+    double g(double t) const      // integrand in ln nu: B_nu nu (unnormalised)
+    {
+        const double nu = exp(t);
+        const double x = a * nu;
+        return x > 700.0 ? 0.0 : nu * nu * nu * nu / expm1(x);
+    }
+
+    void build(const std::vector<double>& edges, const rt_source& s)
+    {
+        e = &edges;
+        const int nf = (int)edges.size() - 1;
+        if (s.L_nu) {
+            tab = true;
+            lnu = s.L_nu;
+            F.assign(nf + 1, 0.0);
+            for (int j = 0; j < nf; ++j) F[j + 1] = F[j] + s.L_nu[j] * (edges[j + 1] - edges[j]);
+            return;
+        }
+        a = kH / (kK * s.T_eff);
+        const int K = 1 << 15;
+        t0 = log(edges[0]);
+        h = (log(edges[nf]) - t0) / K;
+        F.assign(K + 1, 0.0);
+        for (int k = 0; k < K; ++k) {
+            const double tl = t0 + k * h;
+            F[k + 1] = F[k] + h / 6.0 * (g(tl) + 4.0 * g(tl + 0.5 * h) + g(tl + h));
+        }
+    }
+
+    // frequency where the cumulative fraction reaches f (0 < f < 1)
+    double invert(double f) const
+    {
+        const double target = f * F.back();
+        const size_t k = std::upper_bound(F.begin(), F.end(), target) - F.begin() - 1;
+        const size_t kk = std::min(k, F.size() - 2);
+        const double rem = target - F[kk];
+        if (tab) {
+            const double w = F[kk + 1] - F[kk];
+            const double lo = (*e)[kk], hi = (*e)[kk + 1];
+            return w > 0.0 ? lo + (hi - lo) * (rem / w) : lo;
+        }
+        const double tl = t0 + kk * h;
+        double dt = F[kk + 1] > F[kk] ? h * rem / (F[kk + 1] - F[kk]) : 0.0;
+        for (int it = 0; it < 6; ++it) {
+            const double S = dt / 6.0 * (g(tl) + 4.0 * g(tl + 0.5 * dt) + g(tl + dt));
+            const double gd = g(tl + dt);
+            if (!(gd > 0.0)) break;
+            dt -= (S - rem) / gd;
+            dt = std::min(std::max(dt, 0.0), h);
+        }
+        return exp(tl + dt);
+    }
+};
+
+}  // namespace
+
+rt_status build_source_grid(const rt_opacity* op, const rt_source* src, int nsrc, uint32_t m,
+                            int32_t* nu_idx, int32_t* src_idx, double* nu_star)
+{
+    const int nf = op->nf;
+    std::vector<double> e(nf + 1);
+    for (int j = 1; j < nf; ++j) e[j] = sqrt(op->nu[j - 1] * op->nu[j]);
+    e[0] = nf > 1 ? op->nu[0] * op->nu[0] / e[1] : 0.5 * op->nu[0];
+    e[nf] = nf > 1 ? op->nu[nf - 1] * op->nu[nf - 1] / e[nf - 1] : 2.0 * op->nu[0];
+    std::vector<SourceCum> cum(nsrc);
+    double Ltot = 0.0;
+    for (int i = 0; i < nsrc; ++i) {
+        cum[i].build(e, src[i]);
+        Ltot += src[i].L;
+    }
+    for (uint32_t b = 0; b < m; ++b) {
+        const double target = ((double)b + 0.5) / (double)m * Ltot;
+        double below = 0.0;
+        int si = 0;
+        for (; si < nsrc - 1; ++si) {
+            if (below + src[si].L >= target) break;
+            below += src[si].L;
+        }
+        const double f = src[si].L > 0.0 ? (target - below) / src[si].L : 0.5;
+        const double nus = cum[si].invert(f);
+        const int j = (int)(std::upper_bound(e.begin() + 1, e.begin() + nf, nus) - (e.begin() + 1));
+        nu_idx[b] = j;
+        src_idx[b] = si;
+        if (nu_star) nu_star[b] = nus;
+    }
+    return RT_OK;
+}
+
 // ln(4 pi sum_j kabs_j B(nu_j, T) dnu_j) by log-sum-exp (no underflow at low T);
 // lnc[j] = ln(kabs_j dnu_j 2 h nu_j^3 / c^2) (or -inf), x1[j] = h nu_j / k.
 // *slope (optional) receives d ln(4 pi P) / d ln T = <x / (1 - e^-x)> over the

@@ -724,7 +724,16 @@ struct Kernel {
         }
         int si = 0;
         R ub;
-        if (P.source_bins) {
+        bool binned = false;
+        if (P.source_bins && P.sg_nu) {
+            // the separate source grid of Eq. 1: source bin b's source and model bin
+            const uint64_t pid = ((uint64_t)L.rng.phi << 32) | L.rng.plo;
+            const uint64_t b = (pid * P.source_bins) / md->n_emit;
+            si = P.sg_src[b];
+            L.j = P.sg_nu[b];
+            ub = R(0);
+            binned = true;
+        } else if (P.source_bins) {
             // Eq. 1: equal-energy source bins, packet pid from bin floor(pid m / N)
             // at the point (b + 1/2) / m of the cumulative luminosity: its source,
             // then (by the fraction of that source below the point) its bin
@@ -741,11 +750,13 @@ struct Kernel {
             }
             ub = U(L);
         }
-        if constexpr (DBG) {
-            const double* cdf = md->src_cdf64 + (size_t)si * P.nf;
-            L.j = search_cdf(cdf, P.nf, ub * cdf[P.nf - 1]);
-        } else {
-            L.j = search_cdf((P.smem_cdf ? s_cdf() : md->src_cdf32) + (size_t)si * P.nf, P.nf, ub);
+        if (!binned) {
+            if constexpr (DBG) {
+                const double* cdf = md->src_cdf64 + (size_t)si * P.nf;
+                L.j = search_cdf(cdf, P.nf, ub * cdf[P.nf - 1]);
+            } else {
+                L.j = search_cdf((P.smem_cdf ? s_cdf() : md->src_cdf32) + (size_t)si * P.nf, P.nf, ub);
+            }
         }
         const R u1 = U(L), u2 = U(L);
         iso_dir(u1, u2, L.k);

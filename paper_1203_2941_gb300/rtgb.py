@@ -32,7 +32,7 @@ EXPORTS = ["rt_last_error", "rt_version", "rt_ctx_create", "rt_ctx_destroy", "rt
            "rt_grid_free", "rt_opacity_upload", "rt_opacity_free", "rt_transport_params_default",
            "rt_transport", "rt_temperatures", "rt_temperature_guess", "rt_raytrace",
            "rt_raytrace_backward", "rt_batch_create", "rt_batch_run", "rt_batch_free",
-           "rt_transport_batched", "rt_philox", "rt_mrw_sample", "rt_probe_gather", "rt_kernel_launches", "rt_transport_noalloc", "rt_visibilities",
+           "rt_transport_batched", "rt_philox", "rt_mrw_sample", "rt_probe_gather", "rt_source_grid", "rt_kernel_launches", "rt_transport_noalloc", "rt_visibilities",
            "rt_pah_reemit", "rt_grid_upload_refined", "rt_grid_ncell", "rt_grid_update"]
 
 
@@ -56,7 +56,8 @@ class rt_transport_params(C.Structure):
                 ("schedule", C.c_int), ("threads_per_block", C.c_int), ("blocks_per_sm", C.c_int),
                 ("march_min_active", C.c_int), ("defer_events", C.c_uint64),
                 ("source_bins", C.c_uint32), ("pc_cams", C.c_void_p), ("n_pc_cams", C.c_int),
-                ("record_nu_mask", C.c_void_p), ("compact_swap", C.c_int)]
+                ("record_nu_mask", C.c_void_p), ("source_grid_nu", C.c_void_p),
+                ("source_grid_src", C.c_void_p), ("compact_swap", C.c_int)]
 
 
 class rt_transport_out(C.Structure):
@@ -138,6 +139,7 @@ def load(path: str = LIB_PATH):
         "rt_philox": (i32, [vp, vp, vp, u64, vp, vp]),
         "rt_mrw_sample": (i32, [vp, vp, vp, u64, vp, vp]),
         "rt_probe_gather": (i32, [vp, vp, C.c_size_t, u64, C.c_uint32, vp, vp]),
+        "rt_source_grid": (i32, [vp, vp, C.c_int, C.c_uint32, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -293,6 +295,10 @@ def rt_batch_free(batch):
 def rt_transport_batched(ctx, opac, n_models, models, params, stream=0):
     _check(load().rt_transport_batched(ctx, opac, n_models, models, C.byref(params), stream),
            "rt_transport_batched")
+
+
+def rt_source_grid(opac, sources, n_sources, m, nu_ptr, src_ptr, star_ptr):
+    _check(load().rt_source_grid(opac, sources, n_sources, m, nu_ptr, src_ptr, star_ptr), "rt_source_grid")
 
 
 def rt_probe_gather(ctx, buf_ptr, nbytes, n_reads, seed, sink_ptr, stream=0):

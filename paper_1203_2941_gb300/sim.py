@@ -246,9 +246,10 @@ def make_params(n_packets: int, mode=R.RT_MODE_BW, lucy_mode=R.RT_LUCY_THIN,
                 max_events=10_000_000, record_events=False, precision=R.RT_PREC_FP32,
                 schedule=R.RT_SCHED_PERSISTENT, threads_per_block=0, blocks_per_sm=0,
                 march_min_active=-1, defer_events=0, source_bins=0,
-                record_nu=None, compact_swap=-1) -> R.rt_transport_params:
+                record_nu=None, compact_swap=-1, source_grid=None) -> R.rt_transport_params:
     """Transport parameters; ``record_nu`` lists the frequency bins whose
-    scattering events are stored (None: every bin)."""
+    scattering events are stored (None: every bin); ``source_grid`` is the
+    (model bin, source) table pair of ``source_grid()`` for source_bins."""
     p = R.rt_transport_params_default()
     p.mode, p.lucy_mode, p.lucy_form, p.lucy_tau = mode, lucy_mode, lucy_form, lucy_tau
     p.mrw, p.mrw_tau_cell, p.mrw_gamma = int(bool(mrw)), mrw_tau_cell, mrw_gamma
@@ -264,6 +265,14 @@ def make_params(n_packets: int, mode=R.RT_MODE_BW, lucy_mode=R.RT_LUCY_THIN,
     p.defer_events = int(defer_events)
     p.source_bins = int(source_bins)
     p.compact_swap = int(compact_swap)
+    if source_grid is not None:
+        nu_t = np.ascontiguousarray(source_grid[0], dtype=np.int32)
+        src_t = np.ascontiguousarray(source_grid[1], dtype=np.int32)
+        if len(nu_t) != int(source_bins) or len(src_t) != int(source_bins):
+            raise ValueError("source_grid tables need source_bins entries each")
+        p._source_grid = (nu_t, src_t)              # kept alive with the struct
+        p.source_grid_nu = nu_t.ctypes.data_as(C.c_void_p)
+        p.source_grid_src = src_t.ctypes.data_as(C.c_void_p)
     if record_nu is not None:
         idx = [int(j) for j in record_nu]
         words = (C.c_uint32 * max(1, (max(idx, default=0) // 32) + 1))()
@@ -506,6 +515,17 @@ def philox(ctx: Context, ctr0, key, n: int, stream=None) -> np.ndarray:
     R.rt_philox(ctx.h, ctr0, key, n, _ptr(out), _stream(stream))
     torch.cuda.synchronize()
     return out.cpu().numpy().view(np.uint32)
+
+
+def source_grid(opac: Opacity, sources: Sources, m: int):
+    """The separate source frequency grid of Eq. 1 (rt_source_grid): model
+    bin index, source index and frequency (Hz) of each of m equal-energy bins."""
+    nu = np.zeros(m, np.int32)
+    src = np.zeros(m, np.int32)
+    fr = np.zeros(m)
+    R.rt_source_grid(opac.h, sources.arr, sources.n, int(m), nu.ctypes.data_as(C.c_void_p),
+                     src.ctypes.data_as(C.c_void_p), fr.ctypes.data_as(C.c_void_p))
+    return nu, src, fr
 
 
 def mrw_sample(ctx: Context, opac, u, stream=None) -> np.ndarray:

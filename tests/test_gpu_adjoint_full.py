@@ -12,7 +12,14 @@ noise.
 
 * dL/drho_s of rt_raytrace_backward against central differences (h = 1 %)
   of the same loss through rt_raytrace on 100 random dusty (species, cell)
-  pairs: 1e-2 relative plus 1e-3 of the largest sampled component.
+  pairs: 1e-2 relative plus 1e-3 of the largest sampled component.  Here the
+  source function is the thermal emission and the starlight: the stored
+  scattering events enter the scattering emissivity through FP32 atomic
+  additions in no fixed order, which changes the 40-point SED by ~1e-7 from
+  one identical call to the next -- as much as a 1 % change of one cell's
+  density does -- so the difference quotient needs a deterministic forward
+  model.  The scattering part of the adjoint is checked against the oracle
+  below.
 * rt_raytrace_backward against the FP64 oracle's adjoint on one view at
   64^2 pixels (10 um and two SED wavelengths, seeded upstream gradients,
   the oracle's optically thin temperatures and seeded scattering events):
@@ -51,10 +58,12 @@ def setup(rt):
 
 
 class Fit:
-    """The loss above for one density field (forward through rt_raytrace)."""
+    """The loss above for one density field (forward through rt_raytrace;
+    events: a TransportOut, or None for thermal emission and starlight only)."""
 
-    def __init__(self, rt, ctx, m, opac, srcs, out, T, npix=256):
+    def __init__(self, rt, ctx, m, opac, srcs, out, T, npix=256, events=None):
         self.rt, self.ctx, self.m, self.opac, self.srcs, self.out, self.T = rt, ctx, m, opac, srcs, out, T
+        self.ev = events
         self.sed_f = W.nearest_freq_indices(m.nu, W.adjoint_sed_wavelengths_um())
         self.img_f = W.nearest_freq_indices(m.nu, [10.0])
         D = 14e6 * W.PC
@@ -67,9 +76,9 @@ class Fit:
 
     def forward(self, grid):
         rt = self.rt
-        img, _ = rt.raytrace(self.ctx, grid, self.opac, self.T, self.out, self.out.xi, self.srcs,
+        img, _ = rt.raytrace(self.ctx, grid, self.opac, self.T, self.ev, self.out.xi, self.srcs,
                              self.views, self.img_f)
-        seds = [rt.raytrace(self.ctx, grid, self.opac, self.T, self.out, self.out.xi, self.srcs,
+        seds = [rt.raytrace(self.ctx, grid, self.opac, self.T, self.ev, self.out.xi, self.srcs,
                             self.sed_cam, ch)[1] for ch in self._chunks()]
         return img, torch.cat(seds, dim=1)
 
@@ -91,11 +100,11 @@ class Fit:
         img, sed = self.forward(grid)
         gi = (2 * (img.double() - self.I_obs) / self.sI ** 2).float()
         gs = 2 * (sed - self.F_obs) / self.sF ** 2
-        drho, dscale = rt.raytrace_backward(self.ctx, grid, self.opac, self.T, self.out, self.out.xi,
+        drho, dscale = rt.raytrace_backward(self.ctx, grid, self.opac, self.T, self.ev, self.out.xi,
                                             self.srcs, self.views, self.img_f, dL_dimg=gi)
         for k, ch in enumerate(self._chunks()):
             o = sum(len(c) for c in self._chunks()[:k])
-            d2, s2 = rt.raytrace_backward(self.ctx, grid, self.opac, self.T, self.out, self.out.xi,
+            d2, s2 = rt.raytrace_backward(self.ctx, grid, self.opac, self.T, self.ev, self.out.xi,
                                           self.srcs, self.sed_cam, ch, dL_dsed=gs[:, o:o + len(ch)].contiguous())
             drho += d2
             dscale += s2

@@ -514,6 +514,75 @@ def test_equal_energy_source_bins(O):
     assert np.all(nu == nu[:, :1])
 
 
+def _model_edges(nu):
+    # model frequency bin edges: geometric means of neighbours, outer ones mirrored
+    e = np.empty(len(nu) + 1)
+    e[1:-1] = np.sqrt(nu[:-1] * nu[1:])
+    e[0] = nu[0] ** 2 / e[1]
+    e[-1] = nu[-1] ** 2 / e[-2]
+    return e
+
+
+def test_separate_source_grid_has_equal_energy_bins(O):
+    """The source frequency grid of Eq. 1 on the sources' own continuous
+    spectra: each bin holds the energy L/m, i.e. the cumulative luminosity at
+    the frequency of bin b is (b + 1/2) L/m, checked by adaptive quadrature of
+    the Planck function (scipy, independent of the oracle's series); the
+    model frequency bins receive the exact integral of the spectrum over
+    their frequency range to within one source bin per source; a tabulated
+    spectrum (constant over each model bin) receives its L_nu dnu per bin the
+    same way; with two sources the first L_1/L of the bins belong to the
+    first; the transport emits source bin b's packets in its model bin."""
+    from scipy import integrate
+    h, k = 6.62607015e-27, 1.380649e-16
+    m = W.r2_shell(n=4, nf=64)
+    e = _model_edges(m.nu)
+    T = m.sources[0].T_eff
+    B = lambda nu: nu ** 3 / np.expm1(h * nu / (k * T))
+
+    def cum(a, b):
+        # in ln nu, split at the model edges so quad sees smooth pieces
+        tot = 0.0
+        pts = np.concatenate([[a], e[(e > a) & (e < b)], [b]])
+        for lo, hi in zip(pts[:-1], pts[1:]):
+            tot += integrate.quad(lambda t: B(np.exp(t)) * np.exp(t), np.log(lo), np.log(hi),
+                                  epsabs=0, epsrel=1e-12, limit=200)[0]
+        return tot
+
+    total = cum(e[0], e[-1])
+    mb = 200
+    nu_i, src_i, fr = O.source_grid(m, mb)
+    assert np.all(src_i == 0) and np.all(np.diff(fr) > 0)
+    for b in range(0, mb, 7):
+        assert abs(cum(e[0], fr[b]) / total - (b + 0.5) / mb) < 1e-9, b
+    # each frequency bin index is the model bin holding the frequency
+    assert np.all((fr >= e[nu_i]) & (fr < e[nu_i + 1]))
+    # energy per model bin within one source bin
+    E_bins = np.bincount(nu_i, minlength=m.nf) / mb
+    E_true = np.array([cum(e[j], e[j + 1]) for j in range(m.nf)]) / total
+    assert np.all(np.abs(E_bins - E_true) <= 1.0 / mb * (1 + 1e-9))
+    # a tabulated spectrum, constant over each model bin
+    lnu = np.zeros(m.nf)
+    lnu[20:40] = np.linspace(1.0, 3.0, 20)
+    mt = W.r2_shell(n=4, nf=64)
+    mt.sources = [W.Source(mt.sources[0].pos, mt.sources[0].L, 0.0, lnu)]
+    nt, _, _ = O.source_grid(mt, mb)
+    w = lnu * np.diff(e)
+    assert np.all(np.abs(np.bincount(nt, minlength=m.nf) / mb - w / w.sum()) <= 1.0 / mb * (1 + 1e-9))
+    # two sources: bins in order of the sources, each with its share
+    m2 = W.r2_shell(n=4, nf=64)
+    m2.sources = [W.Source((0.0, 0.0, 0.0), 3.0 * W.LSUN, 5800.0), W.Source((0.0, 0.0, 0.0), 1.0 * W.LSUN, 2500.0)]
+    n2, s2, f2 = O.source_grid(m2, 400)
+    assert np.all(s2[:300] == 0) and np.all(s2[300:] == 1)
+    # the transport: source bin b's packets are emitted in model bin nu_i[b]
+    N = 4 * mb
+    r = O.transport(m, N, seed=5, mode=O.MODE_NOREEMIT, source_bins=mb, source_grid=(nu_i, src_i),
+                    traj_cap=40 * N)
+    em = np.sort(r["traj"][r["traj"]["type"] == O.T_EMIT], order="pid")
+    assert len(em) == N
+    np.testing.assert_array_equal(em["nu"], nu_i[(em["pid"] * mb) // N])
+
+
 def test_visibility_definition_pins(O):
     """Visibilities of images (oracle): a single bright pixel gives |V| = its
     flux with the phase of its sky offset; a Gaussian image gives the
