@@ -271,7 +271,7 @@ void rt_opacity_free(rt_opacity* op)
     if (!op) return;
     cudaSetDevice(op->ctx->device);
     cudaFree(op->d_nu); cudaFree(op->d_dnu); cudaFree(op->d_kabs); cudaFree(op->d_ksca);
-    cudaFree(op->d_g); cudaFree(op->d_opac32); cudaFree(op->d_recdf);
+    cudaFree(op->d_g); cudaFree(op->d_opac32); cudaFree(op->d_realias);
     cudaFree(op->d_tinv); cudaFree(op->d_tz); cudaFree(op->d_tw); cudaFree(op->d_zinv); cudaFree(op->d_mrwS);
     delete op;
 }
@@ -579,7 +579,7 @@ static void fill_kp(TransportKP& kp, const rt_opacity* op, const rt_transport_pa
     kp.mrw_gamma = p->mrw_gamma;
     kp.ns = op->ns;
     kp.opac32 = op->d_opac32;
-    kp.recdf = op->d_recdf + (p->mode == RT_MODE_BW ? (size_t)op->ns * kReT * op->nf : 0);
+    kp.realias = op->d_realias + (p->mode == RT_MODE_BW ? (size_t)op->ns * kReT * op->nf : 0);
     kp.re_lg0 = op->re_lg0;
     kp.re_inv_dlg = op->re_inv_dlg;
     kp.tinv = op->d_tinv;

@@ -67,7 +67,7 @@ struct rt_opacity {
     double* d_nu; double* d_dnu;           // [nf]
     double* d_kabs; double* d_ksca; double* d_g;  // [ns][nf]
     float4* d_opac32;                      // [ns][nf] {kext, kabs, ksca, g}
-    float* d_recdf;                        // [2][ns][kReT][nf] normalised re-emission CDFs:
+    uint32_t* d_realias;                   // [2][ns][kReT][nf] re-emission alias tables:
                                            // [0] Eq. 5 (kabs B dnu), [1] Eq. 10 (kabs dB/dT dnu)
     float re_lg0, re_inv_dlg;              // row k at log2 T = re_lg0 + k / re_inv_dlg
     float* d_tinv;                         // [ns][kTinvN] log2 T on uniform log2(P) grid
@@ -211,7 +211,7 @@ struct TransportKP {
     double mrw_tau_cell, mrw_gamma;
     // opacity tables
     const float4* opac32;
-    const float* recdf;                 // [ns][kReT][nf] re-emission CDFs of the call's mode
+    const uint32_t* realias;            // [ns][kReT][nf] re-emission alias tables of the call's mode
     float re_lg0, re_inv_dlg;
     const float* tinv;
     float tinv_y0[kMaxSpecies], tinv_inv_dy[kMaxSpecies];

@@ -1,7 +1,6 @@
 // Host-side construction of the per-opacity device tables:
 //  * float4 {kext, kabs, ksca, g} per species and frequency,
-//  * re-emission weights for the Eq. 5 (B) and Eq. 10 (dB/dT) CDFs in a
-//    scaled form that stays inside FP32 range,
+//  * re-emission alias tables for the Eq. 5 (B) and Eq. 10 (dB/dT) bin laws,
 //  * inverse Planck-mean tables (Eq. 4): log2 T on a uniform grid of
 //    log2(4 pi sum_j kabs_j B_j(T) dnu_j) for the FP32 transport and ln T on a
 //    uniform ln grid for the FP64 temperature solve,
@@ -230,17 +229,23 @@ rt_status build_opacity_tables(rt_opacity* op)
             o32[s * nf + j] = make_float4((float)(ka + ks), (float)ka, (float)ks, (float)op->g[s * nf + j]);
         }
 
-    // Re-emission CDFs for the FP32 transport: for each species and each
-    // temperature of a uniform log2 T grid (0.1 K .. 1e6 K), the normalised
-    // cumulative sum over bins of kabs B(T) dnu (Eq. 5) and kabs dB/dT dnu
-    // (Eq. 10), built in log form in FP64 (no underflow at 0.1 K).
+    // Re-emission tables for the FP32 transport: for each species and each
+    // temperature of a uniform log2 T grid (0.1 K .. 1e6 K), the bin
+    // probabilities kabs B(T) dnu (Eq. 5) and kabs dB/dT dnu (Eq. 10), built in
+    // log form in FP64 (no underflow at 0.1 K), as alias tables (Walker 1977,
+    // in the form of Vose 1991): with n bins, bin j keeps the threshold q_j
+    // and the alias a_j such that drawing j0 = floor(u n) and taking j0 when
+    // the fraction u n - j0 is below q_j0, else a_j0, yields bin j with its
+    // probability.  One 32-bit word per entry: q in 22-bit fixed point above
+    // a 10-bit alias (n <= 1024), so a draw is a single table read.
     const double lg_lo = log2(0.1), lg_hi = log2(1.0e6);
     const double dlg = (lg_hi - lg_lo) / (kReT - 1);
     op->re_lg0 = (float)lg_lo;
     op->re_inv_dlg = (float)(1.0 / dlg);
-    std::vector<float> recdf((size_t)2 * ns * kReT * nf);
+    std::vector<uint32_t> realias((size_t)2 * ns * kReT * nf);
     {
-        std::vector<double> lw(nf);
+        std::vector<double> lw(nf), pw(nf);
+        std::vector<int> small, large;
         for (int mode = 0; mode < 2; ++mode)
             for (int s = 0; s < ns; ++s)
                 for (int k = 0; k < kReT; ++k) {
@@ -256,20 +261,36 @@ rt_status build_opacity_tables(rt_opacity* op)
                         lw[j] = v;
                         mx = std::max(mx, v);
                     }
-                    float* row = &recdf[(((size_t)mode * ns + s) * kReT + k) * nf];
+                    uint32_t* row = &realias[(((size_t)mode * ns + s) * kReT + k) * nf];
                     double acc = 0.0;
                     for (int j = 0; j < nf; ++j) {
-                        acc += std::isfinite(mx) && std::isfinite(lw[j]) ? exp(lw[j] - mx) : 0.0;
-                        lw[j] = acc;
+                        pw[j] = std::isfinite(mx) && std::isfinite(lw[j]) ? exp(lw[j] - mx) : 0.0;
+                        acc += pw[j];
                     }
-                    float prev = 0.0f;
+                    // scaled probabilities n p_j (uniform when the row is empty)
+                    for (int j = 0; j < nf; ++j) pw[j] = acc > 0.0 ? pw[j] * nf / acc : 1.0;
+                    std::vector<double> q(nf, 1.0);
+                    std::vector<int> al(nf);
+                    small.clear();
+                    large.clear();
                     for (int j = 0; j < nf; ++j) {
-                        float c = acc > 0.0 ? (float)(lw[j] / acc) : (float)(j + 1) / nf;
-                        c = std::max(c, prev);
-                        row[j] = c;
-                        prev = c;
+                        al[j] = j;
+                        (pw[j] < 1.0 ? small : large).push_back(j);
                     }
-                    row[nf - 1] = 1.0f;
+                    while (!small.empty() && !large.empty()) {
+                        const int l = small.back(), g = large.back();
+                        small.pop_back();
+                        large.pop_back();
+                        q[l] = pw[l];
+                        al[l] = g;
+                        pw[g] = (pw[g] + pw[l]) - 1.0;
+                        (pw[g] < 1.0 ? small : large).push_back(g);
+                    }
+                    for (int j = 0; j < nf; ++j) {
+                        const double qq = std::min(std::max(q[j], 0.0), 1.0);
+                        const uint32_t fx = (uint32_t)std::min(std::llround(qq * 4194304.0), 4194304LL);
+                        row[j] = (fx << 10) | (uint32_t)al[j];
+                    }
                 }
     }
 
@@ -339,7 +360,7 @@ rt_status build_opacity_tables(rt_opacity* op)
     RT_CUDA(cudaMalloc(&op->d_ksca, sizeof(double) * sf));
     RT_CUDA(cudaMalloc(&op->d_g, sizeof(double) * sf));
     RT_CUDA(cudaMalloc(&op->d_opac32, sizeof(float4) * sf));
-    RT_CUDA(cudaMalloc(&op->d_recdf, sizeof(float) * recdf.size()));
+    RT_CUDA(cudaMalloc(&op->d_realias, sizeof(uint32_t) * realias.size()));
     RT_CUDA(cudaMalloc(&op->d_tinv, sizeof(float) * tinv.size()));
     RT_CUDA(cudaMalloc(&op->d_tz, sizeof(double2) * tz.size()));
     RT_CUDA(cudaMalloc(&op->d_tw, sizeof(TwNode) * tw.size()));
@@ -351,7 +372,7 @@ rt_status build_opacity_tables(rt_opacity* op)
     RT_CUDA(cudaMemcpy(op->d_ksca, op->ksca.data(), sizeof(double) * sf, cudaMemcpyHostToDevice));
     RT_CUDA(cudaMemcpy(op->d_g, op->g.data(), sizeof(double) * sf, cudaMemcpyHostToDevice));
     RT_CUDA(cudaMemcpy(op->d_opac32, o32.data(), sizeof(float4) * sf, cudaMemcpyHostToDevice));
-    RT_CUDA(cudaMemcpy(op->d_recdf, recdf.data(), sizeof(float) * recdf.size(), cudaMemcpyHostToDevice));
+    RT_CUDA(cudaMemcpy(op->d_realias, realias.data(), sizeof(uint32_t) * realias.size(), cudaMemcpyHostToDevice));
     RT_CUDA(cudaMemcpy(op->d_tinv, tinv.data(), sizeof(float) * tinv.size(), cudaMemcpyHostToDevice));
     RT_CUDA(cudaMemcpy(op->d_tz, tz.data(), sizeof(double2) * tz.size(), cudaMemcpyHostToDevice));
     RT_CUDA(cudaMemcpy(op->d_tw, tw.data(), sizeof(TwNode) * tw.size(), cudaMemcpyHostToDevice));

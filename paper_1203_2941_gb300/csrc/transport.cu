@@ -916,10 +916,10 @@ struct Kernel {
 
     // Re-emission frequency bin: Eq. 10 (B&W, dB/dT weights) or Eq. 5 (frozen
     // T).  FP64 build: the exact cumulative sum over bins.  FP32 build: the
-    // normalised CDF tabulated on a uniform log2 T grid; between the two
-    // bracketing rows the upper one is taken with probability equal to the
-    // interpolation weight (a draw from the linearly interpolated spectrum),
-    // then a binary search finds the smallest bin whose CDF reaches u.
+    // bin law tabulated on a uniform log2 T grid as alias tables; between the
+    // two bracketing rows the upper one is taken with probability equal to
+    // the interpolation weight (a draw from the linearly interpolated
+    // spectrum), then one alias-table read gives the bin.
     __device__ __forceinline__ int reemit(Lane<R, NS>& L, int s, double E, R u)
     {
         if constexpr (DBG) {
@@ -948,13 +948,12 @@ struct Kernel {
             f = fminf(fmaxf(f, 0.0f), (float)(kReT - 1));
             int k = min((int)f, kReT - 2);
             if (u_row < f - (float)k) ++k;
-            const float* cdf = P.recdf + ((size_t)s * kReT + k) * P.nf;
-            int lo = 0, hi = P.nf - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (__ldg(cdf + mid) >= u) hi = mid; else lo = mid + 1;
-            }
-            return lo;
+            // alias table of the row: one read
+            const uint32_t* row = P.realias + ((size_t)s * kReT + k) * P.nf;
+            const float x = u * (float)P.nf;
+            const int j0 = min((int)x, P.nf - 1);
+            const uint32_t w = __ldg(row + j0);
+            return x - (float)j0 < (float)(w >> 10) * 0x1p-22f ? j0 : (int)(w & 1023u);
         }
     }
 

@@ -12,7 +12,9 @@ noise.
 
 * dL/drho_s of rt_raytrace_backward against central differences (h = 1 %)
   of the same loss through rt_raytrace on 100 random dusty (species, cell)
-  pairs: 1e-2 relative plus 1e-3 of the largest sampled component.  Here the
+  pairs: 1e-2 relative plus four times the difference quotient's rounding
+  noise (the loss's FP32 rounding noise, measured, over 2 h rho); at least
+  20 of the cells carry a gradient ten times above that noise.  Here the
   source function is the thermal emission and the starlight: the stored
   scattering events enter the scattering emissivity through FP32 atomic
   additions in no fixed order, which changes the 40-point SED by ~1e-7 from
@@ -122,25 +124,38 @@ def test_adjoint_matches_central_differences_at_full_size(rt, setup):
     g = drho.cpu().numpy().reshape(m.ns, -1)
     rho = m.rho.reshape(m.ns, -1)
     dusty = np.argwhere(rho > 0)
-    pick = dusty[np.random.default_rng(79).choice(len(dusty), size=100, replace=False)]
+    rng = np.random.default_rng(79)
+    pick = dusty[rng.choice(len(dusty), size=100, replace=False)]
+    flat = rho0.view(m.ns, -1)
+    L0 = fit.loss(work)
+
+    def loss_with(s, c, v):
+        pert = flat.clone()
+        pert[s, c] = v
+        work.update(pert.view_as(rho0))
+        return fit.loss(work)
+
+    # rounding noise of the loss: a change of one cell's density re-rounds the
+    # FP32 pixels its rays cross (each pixel one ulp, ~1e-6 of a chi^2 term);
+    # measured with 1e-6 relative perturbations, whose own effect is far
+    # smaller
+    probe = dusty[rng.choice(len(dusty), size=20, replace=False)]
+    eps = np.array([loss_with(s, c, float(rho[s, c]) * (1 + 1e-6)) - L0 for s, c in probe])
+    eps_L = max(float(np.sqrt((eps ** 2).mean())), 1e-300)
     h = 1e-2
     fd = np.zeros(len(pick))
-    flat = rho0.view(m.ns, -1)
+    floor = np.zeros(len(pick))
     for k, (s, c) in enumerate(pick):
         v = float(rho[s, c])
-        ls = []
-        for sign in (1, -1):
-            pert = flat.clone()
-            pert[s, c] = v * (1 + sign * h)
-            work.update(pert.view_as(rho0))
-            ls.append(fit.loss(work))
-        fd[k] = (ls[0] - ls[1]) / (2 * h * v)
+        fd[k] = (loss_with(s, c, v * (1 + h)) - loss_with(s, c, v * (1 - h))) / (2 * h * v)
+        floor[k] = 4 * np.sqrt(2) * eps_L / (2 * h * v)
     work.update(rho0)
     ga = np.array([g[s, c] for s, c in pick])
-    scale = np.abs(ga).max()
-    assert scale > 0
-    bad = np.abs(ga - fd) > 1e-2 * np.abs(fd) + 1e-3 * scale
-    assert not bad.any(), (np.nonzero(bad)[0][:5], ga[bad][:5], fd[bad][:5])
+    assert np.abs(ga).max() > 0
+    bad = np.abs(ga - fd) > 1e-2 * np.abs(fd) + floor
+    assert not bad.any(), (np.nonzero(bad)[0][:5], ga[bad][:5], fd[bad][:5], floor[bad][:5])
+    # enough of the sampled cells carry a gradient far above the noise floor
+    assert (np.abs(fd) > 10 * floor).sum() >= 20, (np.abs(fd) / floor)
 
 
 def test_adjoint_matches_oracle_on_one_view(rt, setup, O):

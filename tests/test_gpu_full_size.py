@@ -13,8 +13,8 @@ one or that hold at any size:
   against the oracle's own 1e7-packet frozen-T run on every host core:
   per-cell absorbed energies within max(3 sigma, 1e-3 E) (binomial outlier
   allowance and chi-square of statcheck), the escaped SED per bin within
-  3 sigma, and Eq. 4 temperatures within 0.5 % on cells whose energy both
-  runs sample to 1 %;
+  3 sigma, and Eq. 4 temperatures within max(0.5 %, 3 sigma_T) on cells whose
+  energy both runs sample to 1 % (binomial allowance for the 3-sigma part);
 * the ray-traced images of one full-size camera at two image frequencies,
   from the GPU's temperatures and stored events, against the oracle's.
 """
@@ -25,7 +25,7 @@ import pytest
 
 import workloads as W
 from imgcheck import assert_images_close
-from statcheck import assert_same_energies, assert_same_sed
+from statcheck import assert_outliers, assert_same_energies, assert_same_sed
 
 pytestmark = pytest.mark.gpu
 
@@ -146,7 +146,13 @@ def test_full_size_fp32_frozen_transport_matches_oracle(rt, setup, O):
     assert good.size >= 20
     pick = np.random.default_rng(3).choice(good, size=min(good.size, 1500), replace=False)
     V = m.cell ** 3
+    # within 0.5 %, or within 3 sigma_T where the sampling noise of both runs
+    # exceeds that (sigma_T / T = sqrt(rg^2 + rr^2) / 4 is up to 0.35 % at 1 %),
+    # with the binomial allowance for the 3-sigma part
+    n_bad = 0
     for c in pick:
         Tg = O.solve_temperature(m, 0, E[c] / (rho[c] * V))
         Tr = O.solve_temperature(m, 0, Er[c] / (rho[c] * V))
-        assert abs(Tg / Tr - 1) < 0.005, (c, Tg, Tr)
+        sT = 0.25 * math.sqrt(phi * (rg[c] ** 2 + rr[c] ** 2))
+        n_bad += abs(Tg / Tr - 1) > max(0.005, 3 * sT)
+    assert_outliers(n_bad, len(pick), "temperatures")
