@@ -11,8 +11,8 @@ One step = one pass of the hot path over one model:
   modified random walk in cells of tau > 10, Lucy deposits in thin cells and
   the scattering events at the image frequencies; the Eq. 4 temperatures;
   ray-traced images (5 inclinations x 12 frequencies x 512^2 pixels) and SEDs.
-  The same disk at midplane tau_V = 1e5 (one warm-up and one timed step: a
-  step takes over a minute) is the ``disk_tau1e5`` sub-object.
+  The same disk at midplane tau_V = 1e5 (a step takes over a minute) is the
+  opt-in form ``--forms disk_tau1e5``.
 * ``--workload shell``: the r^-2 shell on 128^3 cells (tau(1 um) = 10, 64
   frequencies, 2500 K star), 1e7 packets, images of 256^2; it also appears
   as the ``shell_128`` sub-object of the default line.
@@ -171,9 +171,9 @@ class ClockSampler:
 
 
 def _oracle_sample(O, om, N, budget_s, first, **kw):
-    """Consecutive packet-id ranges of the emission, doubling from `first`
-    packets, until the oracle's packet loops have taken budget_s (a heavy
-    tail of slow packets cannot overrun it by more than one range).  Returns
+    """Consecutive packet-id ranges of the emission, four times longer each
+    from `first` packets, until the oracle's packet loops have taken
+    budget_s (a heavy tail of slow packets overruns it by at most one range).  Returns
     (packets, crossings, loop seconds, grid set-up seconds of one call)."""
     done, cross, loop, n, setup = 0, 0, 0.0, first, None
     while loop < budget_s and done < N:
@@ -185,7 +185,7 @@ def _oracle_sample(O, om, N, budget_s, first, **kw):
         done += n
         cross += r["stats"]["crossings"]
         loop += r["loop_seconds"]
-        n *= 2
+        n *= 4
     return done, cross, loop, setup
 
 
@@ -201,7 +201,7 @@ def cpu_baseline(m, a, budget_s=10.0):
     n, cross, dt, setup = _oracle_sample(O, om, N, budget_s, 50, seed=99, mode=O.MODE_BW, mrw=a.mrw)
     out = {"value": cross / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
            "sample": f"{n} packets of the {N:.0e}-packet B&W emission (packet ids 0..{n - 1}, in "
-                     f"doubling ranges, each from empty accumulators), {cross} crossings in {dt:.1f} s of packet "
+                     f"growing ranges, each from empty accumulators), {cross} crossings in {dt:.1f} s of packet "
                      f"loops (grid set-up {setup:.1f} s per call, not counted)",
            "setup_s": setup}
     cores = os.cpu_count() or 1
@@ -597,6 +597,33 @@ def form_adjoint(rt, ctx, flush, npix=256):
     return res
 
 
+def form_disk_tau1e5(rt, ctx, flush, packets=1e8):
+    """The benchmark step on the 256^3 flared disk at midplane tau_V = 1e5
+    (1e8 packets, MRW, 5 x 12 x 512^2 images): one warm-up and one timed
+    step (a step takes over a minute)."""
+    import torch
+    a = argparse.Namespace(workload="disk", n=256, tau=1e5, nf=100, packets=packets, npix=512, mrw=True,
+                           schedule="persistent")
+    m = build_model(a)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    gp = gather_peaks(rt, ctx, m.rho[0].size * 12)
+    r = run_step_bench(a, rt, ctx, m, 1, 1, flush, 0, 0, 1, None, peaks, gp, 0)
+    S = r["S"]
+    r["roofline"]["kernel"] = "transport_kernel<float,1,13>"
+    return {"workload": workload_config(a)["workload"], "metric": METRIC,
+            "value": S["crossings"] / r["tot_s"], "unit": UNIT, "steps": 1, "warmup": 1,
+            "ms_per_step": r["t_step"][0],
+            "phases_ms": {"transport": r["t_tr"][0], "temperatures": r["t_T"][0], "raytrace": r["t_ray"][0]},
+            "stats_per_step": {k: v for k, v in S.items() if not k.startswith("n_")},
+            "raytrace": {"metric": "ray-cell steps/s", "value": r["rsteps"] / (r["t_ray"][0] / 1e3),
+                         "roofline": r["ray_roofline"]},
+            "roofline": r["roofline"]}
+
+
 def form_compaction(rt, ctx, flush, packets=1e7):
     """Per-warp packet compaction (RT_SCHED_COMPACT) against the persistent
     schedule on the same packets: the 128^3 r^-2 shell (1e7 packets, B&W,
@@ -647,8 +674,9 @@ def run_forms(a):
     for name, fn in (("fp64_debug", form_fp64_debug), ("plain_fp32", form_plain_fp32),
                      ("mrw_disk", form_mrw_disk), ("adjoint", form_adjoint),
                      ("batched", form_batched), ("refined_shell", form_refined_shell),
-                     ("next_rows", form_next_rows), ("compaction", form_compaction)):
-        if a.forms != "all" and name not in a.forms.split(","):
+                     ("next_rows", form_next_rows), ("compaction", form_compaction),
+                     ("disk_tau1e5", form_disk_tau1e5)):
+        if (a.forms != "all" or name == "disk_tau1e5") and name not in a.forms.split(","):
             continue
         t0 = time.perf_counter()
         kw = ({"packets": a.packets_given if a.packets_given is not None else 1e7}
@@ -1031,27 +1059,6 @@ def main():
                  "raytrace": {"metric": "ray-cell steps/s", "value": rs["rsteps"] / (sum(rs["t_ray"]) / 1e3),
                               "roofline": rs["ray_roofline"]},
                  "roofline": rs["roofline"], "gather_probe": gps}
-    # the disk at midplane tau_V = 1e5: one warm-up and one timed step
-    thick = None
-    if a.workload == "disk" and not a.no_shell and a.tau == WORKLOADS["disk"]["tau"]:
-        log("disk at tau_V = 1e5")
-        c = argparse.Namespace(**vars(a))
-        c.tau = 1e5
-        mt = build_model(c)
-        rt_ = run_step_bench(c, rt, ctx, mt, 1, 1, flush, local, rank, world, dist, peaks, gp, 0)
-        St = rt_["S"]
-        rt_["roofline"]["kernel"] = "transport_kernel<float,1,13>"
-        rt_["roofline"]["traffic"] = None
-        thick = {"workload": workload_config(c)["workload"], "metric": METRIC,
-                 "value": St["crossings"] / rt_["tot_s"], "unit": UNIT, "steps": 1, "warmup": 1,
-                 "ms_per_step": rt_["t_step"][0],
-                 "phases_ms": {"transport": rt_["t_tr"][0], "temperatures": rt_["t_T"][0],
-                               "raytrace": rt_["t_ray"][0]},
-                 "stats_per_step": {k: v for k, v in St.items() if not k.startswith("n_")},
-                 "raytrace": {"metric": "ray-cell steps/s", "value": rt_["rsteps"] / (rt_["t_ray"][0] / 1e3),
-                              "roofline": rt_["ray_roofline"]},
-                 "roofline": rt_["roofline"]}
-        del mt
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:
         log("oracle baseline")
@@ -1069,8 +1076,7 @@ def main():
                              "ray_cell_steps_per_step": r["rsteps"] // K, "roofline": r["ray_roofline"]},
                 "stats_per_step": {k: v // K for k, v in S.items() if not k.startswith("n_")},
                 "roofline": roof, "gather_probe": gp, "cpu_baseline": cpu, "e2e": r.get("e2e"),
-                "clocks": r["clocks"], "gpu_launches": r["launches"], "shell_128": shell,
-                "disk_tau1e5": thick}
+                "clocks": r["clocks"], "gpu_launches": r["launches"], "shell_128": shell}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -988,9 +988,23 @@ struct Kernel {
         return P.ns - 1;
     }
 
+    // A slot of a per-model append cursor for each calling lane: the lanes of
+    // a warp appending to the same model's list share one atomic (a hot
+    // address otherwise serialises in L2), each taking base + its rank.
+    __device__ __forceinline__ unsigned long long claim_slot(unsigned long long* cursor, unsigned key) const
+    {
+        const unsigned grp = __match_any_sync(__activemask(), key);
+        const int leader = __ffs(grp) - 1;
+        const unsigned lane = threadIdx.x & 31;
+        unsigned long long base = 0;
+        if ((int)lane == leader) base = atomicAdd(cursor, (unsigned long long)__popc(grp));
+        base = __shfl_sync(grp, base, leader);
+        return base + __popc(grp & ((1u << lane) - 1u));
+    }
+
     __device__ __forceinline__ void store_pah(Lane<R, NS>& L, const R* x)
     {
-        const unsigned long long slot = atomicAdd(&md->stats[RT_STAT_N_PAH], 1ull);
+        const unsigned long long slot = claim_slot(&md->stats[RT_STAT_N_PAH], (unsigned)L.m);
         if (md->pah && slot < md->pah_cap) {
             rt_pah_event e;
             e.cell = (uint32_t)L.c; e.nu = (uint16_t)L.j; e.model = (uint16_t)md->model_index;
@@ -1236,7 +1250,7 @@ struct Kernel {
             const R mu = hg_mu(g, U(L));
             const R uphi = U(L);
             if (P.record_events && ((P.ev_mask[L.j >> 5] >> (L.j & 31)) & 1u)) {
-                const unsigned long long slot = atomicAdd(&md->stats[RT_STAT_N_EVENTS], 1ull);
+                const unsigned long long slot = claim_slot(&md->stats[RT_STAT_N_EVENTS], (unsigned)L.m);
                 if (md->events && slot < md->event_cap) {
                     rt_event e;
                     e.cell = (uint32_t)L.c; e.nu = (uint16_t)L.j; e.species = (uint8_t)s;
@@ -1339,9 +1353,18 @@ struct Kernel {
         if (P.smem_sed && !DBG) {
             atomicAdd(&s_sed()[b * P.nf + L.j], md->xi);
             atomicAdd(&s_cnt()[b * P.nf + L.j], 1u);
-        } else {
+        } else if constexpr (DBG) {
             atomicAdd(&md->sed_esc[b * P.nf + L.j], md->xi);
             atomicAdd(&md->sed_cnt[b * P.nf + L.j], 1ull);
+        } else {
+            // the lanes of a warp escaping into the same model's bin add once
+            const unsigned key = ((unsigned)L.m << 16) | (unsigned)(b * P.nf + L.j);
+            const unsigned grp = __match_any_sync(__activemask(), key);
+            if ((int)(threadIdx.x & 31) == __ffs(grp) - 1) {
+                const unsigned n = __popc(grp);
+                atomicAdd(&md->sed_esc[b * P.nf + L.j], md->xi * (double)n);
+                atomicAdd(&md->sed_cnt[b * P.nf + L.j], (unsigned long long)n);
+            }
         }
         count(RT_STAT_ESCAPED, 1);
         if constexpr (HAS_PC) {

@@ -12,9 +12,11 @@ noise.
 
 * dL/drho_s of rt_raytrace_backward against central differences (h = 1 %)
   of the same loss through rt_raytrace on 100 random dusty (species, cell)
-  pairs: 1e-2 relative plus four times the difference quotient's rounding
-  noise (the loss's FP32 rounding noise, measured, over 2 h rho); at least
-  20 of the cells carry a gradient ten times above that noise.  Here the
+  pairs of the silicate and carbon species: 1e-2 relative plus four times
+  the difference quotient's rounding noise (the loss's FP32 rounding noise,
+  measured, over 2 h rho); at least 20 of the cells carry a gradient ten
+  times above that noise.  (The PAH-like species' gradients are ~1e-3 of
+  the others', under that noise.)  Here the
   source function is the thermal emission and the starlight: the stored
   scattering events enter the scattering emissivity through FP32 atomic
   additions in no fixed order, which changes the 40-point SED by ~1e-7 from
@@ -25,7 +27,8 @@ noise.
 * rt_raytrace_backward against the FP64 oracle's adjoint on one view at
   64^2 pixels (10 um and two SED wavelengths, seeded upstream gradients,
   the oracle's optically thin temperatures and seeded scattering events):
-  1e-2 relative plus 1e-4 of the largest component; d/d(scale) 1e-3.
+  1e-2 relative plus 1e-4 of each species' largest component, every species
+  on its own scale (the PAH-like species included); d/d(scale) 1e-3.
 """
 import math
 
@@ -123,7 +126,11 @@ def test_adjoint_matches_central_differences_at_full_size(rt, setup):
     drho, _ = fit.gradient(work)
     g = drho.cpu().numpy().reshape(m.ns, -1)
     rho = m.rho.reshape(m.ns, -1)
+    # the silicate and carbon species: the PAH-like species' gradients are
+    # ~1e-3 of theirs, below the FP32 rounding noise of a 1 % difference
+    # quotient; its adjoint is checked per species against the oracle below
     dusty = np.argwhere(rho > 0)
+    dusty = dusty[m.is_pah[dusty[:, 0]] == 0]
     rng = np.random.default_rng(79)
     pick = dusty[rng.choice(len(dusty), size=100, replace=False)]
     flat = rho0.view(m.ns, -1)
@@ -180,7 +187,9 @@ def test_adjoint_matches_oracle_on_one_view(rt, setup, O):
     torch.cuda.synchronize()
     gr, gsr = O.raytrace_backward(m, Tg, ev, xi, cams, fidx, wi.astype(np.float64), ws)
     g = drho.cpu().numpy()
-    scale = np.abs(gr).max()
-    bad = np.abs(g - gr) > 1e-2 * np.abs(gr) + 1e-4 * scale
-    assert not bad.any(), (int(bad.sum()), np.abs(g - gr).max() / scale)
+    for s_ in range(m.ns):                     # each species against its own scale
+        scale = np.abs(gr[s_]).max()
+        assert scale > 0
+        bad = np.abs(g[s_] - gr[s_]) > 1e-2 * np.abs(gr[s_]) + 1e-4 * scale
+        assert not bad.any(), (s_, int(bad.sum()), np.abs(g[s_] - gr[s_]).max() / scale)
     assert abs(float(dscale.item()) / gsr - 1) < 1e-3

@@ -183,7 +183,8 @@ def test_raytrace_adjoint_matches_oracle(rt, ctx, O, ns):
     torch.cuda.synchronize()
     gr, gsr = O.raytrace_backward(m, T, ev, xi, cams, fidx, wi, ws)
     g = drho.cpu().numpy().astype(np.float64)
-    scale = np.abs(gr).max()
+    scale = np.abs(gr).max(axis=1, keepdims=True)          # each species on its own scale
+    assert np.all(scale > 0)
     assert np.all(np.abs(g - gr) <= 1e-2 * np.abs(gr) + 1e-4 * scale)
     assert dscale.item() == pytest.approx(gsr, rel=1e-3)
     # autograd wrapper: d(sum w * img + sum ws * sed)/d(rho, scale)
