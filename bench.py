@@ -38,10 +38,12 @@ sys.path.insert(0, ROOT)
 METRIC = "photon-packet cell-crossings/s"
 UNIT = "crossings/s"
 L2_BYTES = 126.5 * 2 ** 20          # GB300 L2 (nominal 129 MB)
-# DRAM bytes (read + write) of one transport launch of each workload, from a
-# single-pass ncu capture of the build named beside it (see profiles/); set
-# to None when the transport kernel changes until it is captured again
-TRANSPORT_DRAM = {"disk": None, "shell": None}
+# DRAM bytes (read + write) of one transport launch of each workload at its
+# default packet count, from single-pass ncu captures (profiles/): the disk's
+# taken on 1e7 packets and scaled by 10 (its traffic grows with the packets),
+# the shell's on the full launch.  Kernel source of commit 24a59b4; set to
+# None when the transport kernel changes until it is captured again.
+TRANSPORT_DRAM = {"disk": (26.847464192e9 + 10.863199488e9) * 10, "shell": 31.899392e6 + 0.653056e6}
 
 WORKLOADS = {
     "disk": dict(n=256, tau=1e4, nf=100, packets=1e8, npix=512, mrw=True,
@@ -1037,7 +1039,10 @@ def main():
     value = crossings_all / tot_s
     roof = r["roofline"]
     roof["kernel"] = "transport_kernel<float,1,13>" if a.mrw else "transport_kernel<float,1,12>"
-    roof["traffic"] = TRANSPORT_DRAM.get(a.workload) if int(a.packets) == int(WORKLOADS[a.workload]["packets"]) else None
+    wd = WORKLOADS[a.workload]
+    captured = (a.schedule == "persistent" and int(a.packets) == int(wd["packets"]) and a.n == wd["n"]
+                and a.tau == wd["tau"] and a.nf == wd["nf"] and bool(a.mrw) == wd["mrw"])
+    roof["traffic"] = TRANSPORT_DRAM.get(a.workload) if captured else None
     # the 128^3 r^-2 shell, the other full-size configuration, as a sub-object
     shell = None
     if a.workload == "disk" and not a.no_shell:

@@ -221,6 +221,7 @@ void rt_grid_free(rt_grid* g)
     cudaFree(g->d_cube);
     cudaFree(g->d_leaf_cube);
     cudaFree(g->d_leaf_fine);
+    cudaFree(g->d_cube_packed);
     cudaFree(g->d_flag);
     delete g;
 }
@@ -446,6 +447,7 @@ static rt_status make_model(const rt_grid* g, const rt_opacity* op, const rt_sou
     m.inv_refine32 = (float)m.inv_refine;
     m.cube = g->d_cube;
     m.leaf_cube = g->d_leaf_cube;
+    m.cube_rho = g->d_cube_packed;
     m.model_id = model_id;
     m.model_index = model_index;
     m.nsrc = nsrc;
@@ -726,6 +728,7 @@ static rt_status transport_one(rt_ctx* ctx, const rt_grid* grid, const rt_opacit
     st = pack_grid(const_cast<rt_grid*>(grid), op, p->lucy_mode, p->lucy_tau, prec, s);
     if (st != RT_OK) return st;
     hms[0].md.rho = grid->d_packed;
+    hms[0].md.cube_rho = grid->d_cube_packed;
     // FP32 build: this call's deposits go to FP64 scratch in units of xi
     // (FP32 scratch in the plain-FP32 form)
     const size_t n_acc = (size_t)op->ns * grid->ncell();
@@ -879,6 +882,7 @@ rt_status rt_batch_create(rt_ctx* ctx, const rt_opacity* op, int n_models, const
                         M.T_prev, &M.out, hms[m]);
         if (st != RT_OK) return st;
         hms[m].md.rho = M.grid->d_packed;
+        hms[m].md.cube_rho = M.grid->d_cube_packed;
         nwork[m] = M.n_packets;
     }
     RT_CUDA(cudaDeviceSynchronize());
@@ -1174,10 +1178,12 @@ rt_status rt_transport_noalloc(rt_ctx* ctx, const rt_grid* grid, const rt_opacit
         return fail(RT_ERR_INVALID_ARG, "rt_transport_noalloc: the separate source grid is served by rt_transport only");
     if (p->mode == RT_MODE_FROZEN_T && !T_prev)
         return fail(RT_ERR_INVALID_ARG, "rt_transport_noalloc: frozen-T mode needs T_prev");
-    // scratch layout: staging | kext | packed density | FP64 energy scratch
+    // scratch layout: staging | kext | packed density | packed cube density
+    // (refined grids) | FP64 energy scratch
     const size_t nc = grid->ncell();
     const int vec = grid->ns == 1 ? 1 : (grid->ns == 2 ? 2 : 4);
-    const size_t packed_bytes = align_up(nc * sizeof(float) * vec, 256);
+    const size_t packed_bytes = align_up(nc * sizeof(float) * vec, 256) +
+                                (grid->refine ? align_up(grid->ncube() * sizeof(float) * vec, 256) : 0);
     const size_t n_acc = (size_t)op->ns * nc;
     const size_t acc_bytes = p->precision == RT_PREC_FP32 ? sizeof(double) * n_acc * (out->esq ? 2 : 1) : 0;
     const size_t need = kNoAllocStaging + kNoAllocKext + packed_bytes + acc_bytes;
@@ -1197,9 +1203,12 @@ rt_status rt_transport_noalloc(rt_ctx* ctx, const rt_grid* grid, const rt_opacit
     double* kext = (double*)(base + kNoAllocStaging);
     unsigned char* packed = base + kNoAllocStaging + kNoAllocKext;
     double* acc = acc_bytes ? (double*)(packed + packed_bytes) : nullptr;
-    st = pack_grid_into(grid, op, p->lucy_mode, p->lucy_tau, p->precision, kext, packed, s);
+    unsigned char* cube_packed = packed + align_up(nc * sizeof(float) * vec, 256);
+    st = pack_grid_into(grid, op, p->lucy_mode, p->lucy_tau, p->precision, kext, packed,
+                        grid->refine ? cube_packed : nullptr, s);
     if (st != RT_OK) return st;
     hms[0].md.rho = packed;
+    hms[0].md.cube_rho = grid->refine ? cube_packed : nullptr;
     if (acc) {
         RT_CUDA(cudaMemsetAsync(acc, 0, acc_bytes, s));     // the array keeps the last call's sums
         hms[0].md.accE = acc;

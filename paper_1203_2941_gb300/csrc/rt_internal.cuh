@@ -102,6 +102,9 @@ struct rt_grid {
     int* d_cube;                           // [ncube] first cell, kCubeDivided if divided
     int* d_leaf_cube;                      // [ncell] cube of each cell
     unsigned char* d_leaf_fine;            // [ncell] 1 = sub-cube
+    // refined grids: [ncube] packed density of each undivided cube (the
+    // packed layout; zero for divided cubes), rebuilt with every packing
+    void* d_cube_packed;
     size_t ncube() const { return (size_t)nx * ny * nz; }
     size_t ncell() const { return refine ? nleaf : ncube(); }
 };
@@ -129,6 +132,7 @@ struct ModelDev {
     double* E_abs; uint32_t* count; double* esq;
     const int* cube;           // refined grids: [ncube] first cell | kCubeDivided
     const int* leaf_cube;      // refined grids: [ncell] cube of each cell
+    const void* cube_rho;      // refined grids: [ncube] packed density of undivided cubes
     int refine;                // r, or 0
     double inv_refine;         // 1 / r (exact for the power-of-two factors)
     float inv_refine32;        // the same in FP32 (no FP64 conversion in the FP32 walk)
@@ -296,7 +300,7 @@ rt_status build_source_grid(const rt_opacity* op, const rt_source* src, int nsrc
 rt_status pack_grid(rt_grid* g, const rt_opacity* op, int lucy_mode, double lucy_tau, int prec,
                     cudaStream_t s);
 rt_status pack_grid_into(const rt_grid* g, const rt_opacity* op, int lucy_mode, double lucy_tau,
-                         int prec, double* kext, void* dst, cudaStream_t s);
+                         int prec, double* kext, void* dst, void* cube_dst, cudaStream_t s);
 rt_status visibilities_impl(rt_ctx* ctx, const rt_grid* g, const rt_camera* cams, int ncam,
                             const float* images, int nf, const double* uv, int nuv, double* vis,
                             cudaStream_t s);

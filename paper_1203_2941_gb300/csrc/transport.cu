@@ -255,9 +255,11 @@ struct Lane {
     bool outn;                 // the next face is the grid boundary
     const void* grid;          // packed cells of the packet's model
     uint32_t ncross, nlucy;    // crossings and Lucy deposits of the current packet
-    int cc, sub;               // refined grids: cube of the cell; sub-cube indices
-                               // (8 bits per axis) or -1 for an undivided cube
-                               // (rem then holds the cube's indices)
+    int sub;                   // refined grids: sub-cube indices (8 bits per axis)
+                               // or -1 for an undivided cube (rem then holds the
+                               // cube's indices)
+    int cinfo;                 // refined grids: the next cube's first cell | divided
+                               // flag when the next crossing leaves the cube, else -1
 };
 
 // a[s] for a register array and a run-time index, without local memory
@@ -563,7 +565,6 @@ struct Kernel {
     {
         const int q = md->refine ? md->leaf_cube[c] : c;
         const int info = md->refine ? md->cube[q] : q;
-        L.cc = q;
         cube_idx(q, L.rem);
         if (info & kCubeDivided) {
             const int r = md->refine;
@@ -583,7 +584,6 @@ struct Kernel {
                                                int ea) const
     {
         const int info = md->refine ? md->cube[q] : q;
-        L.cc = q;
 #pragma unroll
         for (int a = 0; a < 3; ++a) L.rem[a] = id[a];
         if (!(info & kCubeDivided)) {
@@ -591,11 +591,18 @@ struct Kernel {
             L.c = info;
             return;
         }
+        descend(L, info, xc, ea);
+    }
+
+    // The sub-cube of the divided cube L.rem (first cell | flag `info`) that
+    // holds xc, entered through axis ea (or -1), as in enter_cube
+    __device__ __forceinline__ void descend(Lane<R, NS>& L, int info, const R* xc, int ea) const
+    {
         const int r = md->refine;
         int sb[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            const R u = (xc[a] - (R)id[a]) * (R)r;
+            const R u = (xc[a] - (R)L.rem[a]) * (R)r;
             const R f = floor(u);
             int sa = (int)f;
             if (f == u && L.k[a] < R(0)) sa -= 1;
@@ -605,6 +612,12 @@ struct Kernel {
         }
         L.sub = sb[0] | (sb[1] << 8) | (sb[2] << 16);
         L.c = (info & ~kCubeDivided) + (sb[2] * r + sb[1]) * r + sb[0];
+    }
+
+    // packed densities of a refined grid's undivided cubes
+    __device__ __forceinline__ const PT* cube_cells() const
+    {
+        return reinterpret_cast<const PT*>(md->cube_rho);
     }
 
     // lower corner (cube units) and edge of the lane's cell
@@ -638,52 +651,85 @@ struct Kernel {
         }
     }
 
-    // Crossing of a refined grid's traversal through the face on axis a:
-    // the next sub-cube of the cube, else the next cube (entering its
-    // sub-cube when it is divided); leaving the grid escapes.
-    __device__ __forceinline__ void step_ref(Lane<R, NS>& L, int a)
+    // The next crossing of a refined grid's traversal, found one crossing
+    // ahead as on the uniform grid (nearest face, ties to the lowest axis):
+    // inside a divided cube, the next sub-cube, whose density is requested
+    // now (cinfo = -1); else the next cube, whose first cell (cinfo) and
+    // packed density (undivided) are requested now side by side, or
+    // cinfo = kLeaveGrid when the face is the grid's.  A uniform grid in a
+    // batch of refined ones has no cube tables: its cubes are its cells.
+    // Written with selects and one load of a selected address, so that
+    // lanes stepping inside a cube and between cubes stay converged.
+    static constexpr int kLeaveGrid = -2;
+
+    __device__ __forceinline__ void prefetch_ref(Lane<R, NS>& L)
     {
+        const int a = (L.tm[0] <= L.tm[1] && L.tm[0] <= L.tm[2]) ? 0 : (L.tm[1] <= L.tm[2] ? 1 : 2);
+        L.nax = a;
         const R ka = a == 0 ? L.k[0] : (a == 1 ? L.k[1] : L.k[2]);
         const int sg = ka > R(0) ? 1 : -1;
         const int r = md->refine;
-        if (L.sub >= 0) {
-            const int sa = ((L.sub >> (8 * a)) & 255) + sg;
-            if (sa >= 0 && sa < r) {
-                L.sub = (L.sub & ~(255 << (8 * a))) | (sa << (8 * a));
-                L.c += sg * (a == 0 ? 1 : (a == 1 ? r : r * r));
-                // (branches, not a run-time index: the lane state stays in registers)
-                // face spacing of a sub-cube: td / r (a product: no division per step)
-                const R ir = inv_r();
-                if (a == 0) L.tm[0] += L.td[0] * ir;
-                else if (a == 1) L.tm[1] += L.td[1] * ir;
-                else L.tm[2] += L.td[2] * ir;
-                load_cell(L);
-                return;
-            }
-        }
-        int id[3] = { L.rem[0], L.rem[1], L.rem[2] };
-        id[0] += a == 0 ? sg : 0;
-        id[1] += a == 1 ? sg : 0;
-        id[2] += a == 2 ? sg : 0;
-        const int ia = a == 0 ? id[0] : (a == 1 ? id[1] : id[2]);
+        const int sa = ((L.sub >> (8 * a)) & 255) + sg;
+        const bool inside = L.sub >= 0 && sa >= 0 && sa < r;
+        const int ia = (a == 0 ? L.rem[0] : (a == 1 ? L.rem[1] : L.rem[2])) + sg;
         const int n_a = a == 0 ? md->nx : (a == 1 ? md->ny : md->nz);
-        if (ia < 0 || ia >= n_a) {
+        const bool leave = !inside && (ia < 0 || ia >= n_a);
+        const int i0 = a == 0 ? ia : L.rem[0], i1 = a == 1 ? ia : L.rem[1], i2 = a == 2 ? ia : L.rem[2];
+        const int q = (i2 * md->ny + i1) * md->nx + i0;
+        const PT* src = inside ? cells(L) + (L.c + sg * (a == 0 ? 1 : (a == 1 ? r : r * r)))
+                               : (r ? cube_cells() : cells(L)) + q;
+        if (!leave) L.pf = __ldg(src);
+        int info = q;
+        if (r && !inside && !leave) info = __ldg(md->cube + q);
+        L.cinfo = inside ? -1 : (leave ? kLeaveGrid : info);
+    }
+
+    // Crossing of a refined grid's traversal through the face on axis a
+    // (the one prefetch_ref found).  A step at one level (to the next
+    // sub-cube of the cube, or from an undivided cube to the next undivided
+    // one) takes the prefetched cell and adds the face spacing (td, or td / r
+    // in sub-cubes: a product, no division per step); a change of level
+    // restarts the face times from the point, and the descent into a divided
+    // cube reads the density of the sub-cube that holds the entry point, the
+    // one load not issued a crossing ahead (a cube step from one divided
+    // cube into the next also restarts them).  Leaving the grid escapes.
+    __device__ __forceinline__ void step_ref(Lane<R, NS>& L, int a)
+    {
+        if (L.cinfo == kLeaveGrid) {
             L.st = ST_ESCAPE;              // c keeps the last cell inside
             return;
         }
-        R xc[3];
+        const R ka = a == 0 ? L.k[0] : (a == 1 ? L.k[1] : L.k[2]);
+        const int sg = ka > R(0) ? 1 : -1;
+        const int r = md->refine;
+        const bool inside = L.cinfo < 0;
+        const bool fine = L.sub >= 0;
+        const bool divided = !inside && (L.cinfo & kCubeDivided) != 0;
+        const R h = fine ? inv_r() : R(1);
+        // same-level update, for every lane (selects, not a run-time index)
+        L.tm[0] = a == 0 ? L.tm[0] + L.td[0] * h : L.tm[0];
+        L.tm[1] = a == 1 ? L.tm[1] + L.td[1] * h : L.tm[1];
+        L.tm[2] = a == 2 ? L.tm[2] + L.td[2] * h : L.tm[2];
+        const int dr = inside ? 0 : sg;
+        L.rem[0] += a == 0 ? dr : 0;
+        L.rem[1] += a == 1 ? dr : 0;
+        L.rem[2] += a == 2 ? dr : 0;
+        const int sa = ((L.sub >> (8 * a)) & 255) + sg;
+        L.sub = inside ? (L.sub & ~(255 << (8 * a))) | (sa << (8 * a)) : -1;
+        L.c = inside ? L.c + sg * (a == 0 ? 1 : (a == 1 ? r : r * r)) : L.cinfo;
+        use_cell(L, L.pf);
+        if (!inside && (fine || divided)) {
+            // a cube step out of or into a divided cube
+            if (divided) {
+                R xc[3];
 #pragma unroll
-        for (int b = 0; b < 3; ++b) xc[b] = L.x[b] + L.tcur * L.k[b];
-        const bool was_fine = L.sub >= 0;
-        enter_cube(L, L.cc + sg * (a == 0 ? 1 : (a == 1 ? md->nx : md->nx * md->ny)), id, xc, a);
-        if (was_fine || L.sub >= 0) {
-            face_times(L);             // the face spacing changed: restart from the point
-        } else {
-            if (a == 0) L.tm[0] += L.td[0];
-            else if (a == 1) L.tm[1] += L.td[1];
-            else L.tm[2] += L.td[2];
+                for (int b = 0; b < 3; ++b) xc[b] = L.x[b] + L.tcur * L.k[b];
+                descend(L, L.cinfo, xc, a);
+                load_cell(L);
+            }
+            face_times(L);
         }
-        load_cell(L);
+        prefetch_ref(L);
     }
 
     __device__ __forceinline__ void emit(Lane<R, NS>& L, uint64_t w)
@@ -1105,14 +1151,15 @@ struct Kernel {
         for (int a = 0; a < 3; ++a) L.td[a] = L.k[a] != R(0) ? R(1) / fabs(L.k[a]) : R(INFINITY);
         L.tcur = R(0);
         face_times(L);
+        prefetch_ref(L);
         L.st = ST_MARCH;
     }
 
-    // One crossing step of a refined grid's traversal (no prefetch: the next
-    // cell is known only after the crossing).
+    // One crossing step of a refined grid's traversal (exit face and next
+    // cell found one crossing earlier by prefetch_ref)
     __device__ __forceinline__ void march_ref(Lane<R, NS>& L)
     {
-        const int a = (L.tm[0] <= L.tm[1] && L.tm[0] <= L.tm[2]) ? 0 : (L.tm[1] <= L.tm[2] ? 1 : 2);
+        const int a = L.nax;
         const R tn = a == 0 ? L.tm[0] : (a == 1 ? L.tm[1] : L.tm[2]);
         const R seg = tn - L.tcur;
         const R dtau = L.chi * seg;
@@ -1831,6 +1878,19 @@ __global__ void pack_kernel(const float* rho, size_t nc, double kext_max, PT* ou
     else out[i] = make_float4(v[0], v[1], v[2], v[3]);
 }
 
+// Packed density of every undivided cube of a refined grid, copied from its
+// one cell after the packing (zero for divided cubes, whose sub-cubes are
+// read instead): the traversal reads a cube's first cell and density side by
+// side, one crossing ahead
+template <typename PT>
+__global__ void cube_pack_kernel(const int* cube, size_t ncube, const PT* packed, PT* out)
+{
+    const size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (q >= ncube) return;
+    const int info = cube[q];
+    out[q] = (info & kCubeDivided) ? PT{} : packed[info];
+}
+
 // E_abs += acc * xi and esq += acc_sq * xi^2 for one model (FP32 build);
 // with acc_q = 1 the scratch interleaves the two sums per cell
 template <typename A>
@@ -1980,6 +2040,23 @@ static double kext_max(const rt_opacity* op)
     return mx;
 }
 
+// cube_pack_kernel over a refined grid's cubes (packed: its packed cells)
+static rt_status pack_cubes(const rt_grid* g, const void* packed, void* dst, cudaStream_t s)
+{
+    const int vec = g->ns == 1 ? 1 : (g->ns == 2 ? 2 : 4);
+    const size_t nq = g->ncube();
+    const unsigned blocks = (unsigned)((nq + 255) / 256);
+    if (vec == 1)
+        cube_pack_kernel<float><<<blocks, 256, 0, s>>>(g->d_cube, nq, (const float*)packed, (float*)dst);
+    else if (vec == 2)
+        cube_pack_kernel<float2><<<blocks, 256, 0, s>>>(g->d_cube, nq, (const float2*)packed, (float2*)dst);
+    else
+        cube_pack_kernel<float4><<<blocks, 256, 0, s>>>(g->d_cube, nq, (const float4*)packed, (float4*)dst);
+    count_launches();
+    RT_CUDA(cudaGetLastError());
+    return RT_OK;
+}
+
 rt_status pack_grid(rt_grid* g, const rt_opacity* op, int lucy_mode, double lucy_tau, int prec,
                     cudaStream_t s)
 {
@@ -2014,6 +2091,11 @@ rt_status pack_grid(rt_grid* g, const rt_opacity* op, int lucy_mode, double lucy
                                                      lucy_mode, lucy_tau, kext, op->nf);
     RT_CUDA(cudaGetLastError());
     RT_CUDA(cudaFreeAsync(kext, s));
+    if (g->refine) {
+        if (!g->d_cube_packed) RT_CUDA(cudaMalloc(&g->d_cube_packed, g->ncube() * sizeof(float) * vec));
+        const rt_status st = pack_cubes(g, g->d_packed, g->d_cube_packed, s);
+        if (st != RT_OK) return st;
+    }
     g->packed_vec = vec;
     g->packed_opac_serial = op->serial;
     g->packed_lucy_mode = lucy_mode;
@@ -2043,10 +2125,11 @@ rt_status launch_finalize32(const float* acc, int acc_q, size_t n, double xi, do
 }
 
 // Pack the grid into `dst` (ncell cells of 1, 2 or 4 floats) with the Lucy
-// flags of (lucy_mode, lucy_tau); `kext` receives ns * nf doubles of work
-// space.  Allocates nothing.
+// flags of (lucy_mode, lucy_tau), and a refined grid's cube densities into
+// `cube_dst` (ncube entries of the same width); `kext` receives ns * nf
+// doubles of work space.  Allocates nothing.
 rt_status pack_grid_into(const rt_grid* g, const rt_opacity* op, int lucy_mode, double lucy_tau,
-                         int prec, double* kext, void* dst, cudaStream_t s)
+                         int prec, double* kext, void* dst, void* cube_dst, cudaStream_t s)
 {
     const int vec = g->ns == 1 ? 1 : (g->ns == 2 ? 2 : 4);
     const size_t nc = g->ncell();
@@ -2071,6 +2154,7 @@ rt_status pack_grid_into(const rt_grid* g, const rt_opacity* op, int lucy_mode, 
                                                      lucy_mode, lucy_tau, kext, op->nf);
     count_launches(2);
     RT_CUDA(cudaGetLastError());
+    if (g->refine) return pack_cubes(g, dst, cube_dst, s);
     return RT_OK;
 }
 

@@ -5,9 +5,10 @@ oracle (run on a GB300).
   densities: per-packet trajectories (cells are sub-cubes) equal to 1e-9,
   frozen T on all SMs and B&W in the serial schedule, with Lucy cells and
   the modified random walk in thick sub-cubes; energies, tallies equal.
-* FP32: energy conservation, and a grid whose sub-cubes inherit their cube's
-  density gives the unrefined grid's cube energies within the Monte Carlo
-  noise.
+* FP32: per-cell energies against the oracle within the Monte Carlo noise
+  (statcheck) on refined grids with and without the modified random walk;
+  energy conservation, and a grid whose sub-cubes inherit their cube's
+  density gives the unrefined grid's cube energies within the noise.
 * Temperatures (sub-cube volumes), the initial guess, the PAH pass and the
   ray tracer (emissivity tables per sub-cube, two-level ray and starlight
   walks, scattering events in sub-cubes) against the oracle.
@@ -22,6 +23,7 @@ import torch
 
 import workloads as W
 from imgcheck import assert_images_close
+from statcheck import assert_same_energies
 
 pytestmark = pytest.mark.gpu
 
@@ -98,6 +100,49 @@ def test_fp64_bw_serial_and_mrw_on_refined_grid(rt, ctx, O):
         assert st[k] == ref["stats"][k], k
     g = out.numpy()
     np.testing.assert_allclose(g["E_abs"], ref["E_abs"], rtol=1e-9, atol=1e-9 * ref["E_abs"].max())
+
+
+def _shell_refined(r, tau_1um=100.0):
+    m = W.r2_shell(n=16, tau_1um=tau_1um, nf=32)
+    c = np.arange(16) + 0.5 - 8
+    Z, Y, X = np.meshgrid(c, c, c, indexing="ij")
+    return W.refine_cubes(m, np.sqrt(X * X + Y * Y + Z * Z) < 5, r=r, jitter=0.5, seed=4)
+
+
+@pytest.mark.parametrize("case", ["random_ns2_r3", "shell_r4_mrw"])
+def test_fp32_refined_statistics_match_oracle(rt, ctx, O, case):
+    """The FP32 two-level traversal (the next sub-cube or cube and its density
+    fetched one crossing ahead) against the FP64 oracle, frozen T: per-cell
+    E_abs within max(3 sigma, 1e-3 E) with the binomial allowance and the
+    chi-square bound of statcheck, the dispersion calibrated by a second
+    oracle run; the same counts of escapes.  Cases: a random grid of two
+    species with half its cubes divided into 3^3 sub-cubes of their own
+    densities, and an r^-2 shell whose central cubes are divided into 4^3
+    with the modified random walk in its thick sub-cubes."""
+    if case == "random_ns2_r3":
+        m = _refined(ns=2, r=3, seed=31, tau_scale=6.0, frac=0.5, n=(8, 7, 6))
+        kw = dict(mrw=False)
+        N = 300_000
+    else:
+        m = _shell_refined(4)
+        kw = dict(mrw=True, mrw_tau_cell=2.0, mrw_gamma=1.0)
+        N = 600_000
+    grid, opac, srcs = ctx.grid(m), ctx.opacity(m), rt.Sources(m.sources)
+    T0 = O.temperature_guess(m)
+    out = rt.transport(ctx, grid, opac, srcs, N, mode=rt.rtgb.RT_MODE_FROZEN_T,
+                       T_prev=torch.tensor(T0, device="cuda"), seed=41, **kw)
+    torch.cuda.synchronize()
+    g = out.numpy()
+    st = out.stats_dict()
+    assert st["escaped"] == N and st["stuck"] == 0
+    if kw["mrw"]:
+        assert st["mrw_steps"] > 0
+    ref = O.transport(m, N, seed=42, mode=O.MODE_FROZEN_T, T_prev=T0, n_threads=8, **kw)
+    ref2 = O.transport(m, N, seed=43, mode=O.MODE_FROZEN_T, T_prev=T0, n_threads=8, **kw)
+    xi = m.luminosity / N
+    phi, ncell = assert_same_energies(g, ref, ref2, xi)
+    assert ncell > 500
+    assert g["E_abs"].sum() == pytest.approx(ref["E_abs"].sum(), rel=0.02)
 
 
 def test_fp32_refined_conservation_and_inherited_density(rt, ctx):
