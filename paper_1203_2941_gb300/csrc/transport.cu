@@ -685,14 +685,19 @@ struct Kernel {
     }
 
     // Crossing of a refined grid's traversal through the face on axis a
-    // (the one prefetch_ref found).  A step at one level (to the next
-    // sub-cube of the cube, or from an undivided cube to the next undivided
-    // one) takes the prefetched cell and adds the face spacing (td, or td / r
-    // in sub-cubes: a product, no division per step); a change of level
-    // restarts the face times from the point, and the descent into a divided
-    // cube reads the density of the sub-cube that holds the entry point, the
-    // one load not issued a crossing ahead (a cube step from one divided
-    // cube into the next also restarts them).  Leaving the grid escapes.
+    // (the one prefetch_ref found).  Steps that stay on one level take the
+    // face spacing (td, or td / r in sub-cubes: a product, no division per
+    // step) and the prefetched density: to the next sub-cube of the cube,
+    // from an undivided cube to the next undivided one, and (FP32 build)
+    // from a divided cube into the next divided one, whose sub-cubes continue
+    // the same fine grid (the sub-cube index along a wraps, the others carry
+    // over; its density is the one load not issued a crossing ahead).  A
+    // change of level restarts the face times from the point; the descent
+    // from an undivided into a divided cube takes the sub-cube that holds
+    // the entry point.  The FP64 build takes the oracle's order of
+    // operations, for trajectories equal to rounding: every cube step out of
+    // or into a divided cube descends at the point and restarts the face
+    // times.  Leaving the grid escapes.
     __device__ __forceinline__ void step_ref(Lane<R, NS>& L, int a)
     {
         if (L.cinfo == kLeaveGrid) {
@@ -700,13 +705,14 @@ struct Kernel {
             return;
         }
         const R ka = a == 0 ? L.k[0] : (a == 1 ? L.k[1] : L.k[2]);
-        const int sg = ka > R(0) ? 1 : -1;
+        const bool pos = ka > R(0);
+        const int sg = pos ? 1 : -1;
         const int r = md->refine;
         const bool inside = L.cinfo < 0;
         const bool fine = L.sub >= 0;
         const bool divided = !inside && (L.cinfo & kCubeDivided) != 0;
         const R h = fine ? inv_r() : R(1);
-        // same-level update, for every lane (selects, not a run-time index)
+        // one-level update, for every lane (selects, not a run-time index)
         L.tm[0] = a == 0 ? L.tm[0] + L.td[0] * h : L.tm[0];
         L.tm[1] = a == 1 ? L.tm[1] + L.td[1] * h : L.tm[1];
         L.tm[2] = a == 2 ? L.tm[2] + L.td[2] * h : L.tm[2];
@@ -714,12 +720,18 @@ struct Kernel {
         L.rem[0] += a == 0 ? dr : 0;
         L.rem[1] += a == 1 ? dr : 0;
         L.rem[2] += a == 2 ? dr : 0;
-        const int sa = ((L.sub >> (8 * a)) & 255) + sg;
-        L.sub = inside ? (L.sub & ~(255 << (8 * a))) | (sa << (8 * a)) : -1;
-        L.c = inside ? L.c + sg * (a == 0 ? 1 : (a == 1 ? r : r * r)) : L.cinfo;
-        use_cell(L, L.pf);
-        if (!inside && (fine || divided)) {
-            // a cube step out of or into a divided cube
+        const int sh = 8 * a;
+        const int sa = inside ? ((L.sub >> sh) & 255) + sg : (pos ? 0 : r - 1);
+        const int sub = (L.sub & ~(255 << sh)) | (sa << sh);
+        L.sub = (inside || divided) ? sub : -1;
+        const int off = (((sub >> 16) & 255) * r + ((sub >> 8) & 255)) * r + (sub & 255);
+        L.c = inside ? L.c + sg * (a == 0 ? 1 : (a == 1 ? r : r * r))
+                     : (divided ? (L.cinfo & ~kCubeDivided) + off : L.cinfo);
+        PT v = L.pf;
+        if (fine && divided) v = __ldg(cells(L) + L.c);
+        use_cell(L, v);
+        const bool restart = DBG ? (!inside && (fine || divided)) : (fine != (inside || divided));
+        if (restart) {
             if (divided) {
                 R xc[3];
 #pragma unroll
