@@ -81,6 +81,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-shell", action="store_true", help="skip the 128^3 shell sub-object")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="skip the schedule autotuner (library default march_min_active)")
     ap.add_argument("--schedule", default="persistent", choices=["persistent", "compact"],
                     help="transport schedule: dynamic refill per warp, or with per-warp packet compaction")
     ap.add_argument("--sharded", action="store_true",
@@ -824,6 +826,20 @@ def run_step_bench(a, rt, ctx, m, K, Wu, flush, local, rank, world, dist, peaks,
     seed_base = 1000 * rank
     tkw = dict(record_events=True, record_nu=sorted(set(fidx)), mrw=a.mrw,
                schedule=R.RT_SCHED_COMPACT if a.schedule == "compact" else R.RT_SCHED_PERSISTENT)
+    tuned = None
+    if a.schedule == "persistent" and not getattr(a, "no_tune", False):
+        # the schedule autotuner (lanes still marching below which a warp
+        # serves its interactions) on a bounded sample of the same emission,
+        # before and outside the timed steps; the e2e steps use it too
+        from paper_1203_2941_gb300.autotune import tune_transport
+        t0 = time.perf_counter()
+        n_tune = min(N, 10_000_000)
+        tr = tune_transport(ctx, grid, opac, srcs, N, sample=n_tune, event_cap=ev_cap * n_tune // N,
+                            grid_values={"threads_per_block": (256,)}, repeats=2, **tkw)
+        tkw.update(tr.params)
+        tuned = {"params": tr.params, "sample_packets": n_tune, "seconds": time.perf_counter() - t0,
+                 "candidates_ms": {str(c["march_min_active"]): round(1e3 * t, 3) for c, t in tr.table}}
+        log(f"schedule tuned: {tr.params} ({tuned['seconds']:.1f} s)")
 
     def step(i, ev=None):
         for t in (out.E_abs, out.count, out.esq, out.sed_esc, out.sed_cnt):
@@ -873,7 +889,8 @@ def run_step_bench(a, rt, ctx, m, K, Wu, flush, local, rank, world, dist, peaks,
            "t_tr": t_tr, "t_T": t_T, "t_ray": t_ray, "launches": launches, "clocks": clk.summary(),
            "roofline": transport_roofline(S, K, sum(t_tr) / K / 1e3, grid.ns, grid.ncell, gp, peaks),
            "ray_roofline": raytrace_roofline(rsteps, K, sum(t_ray) / K / 1e3, grid.ns, len(fidx),
-                                             grid.ncell, len(cams), gp, peaks)}
+                                             grid.ncell, len(cams), gp, peaks),
+           "tuned": tuned}
     log(f"timed {K} steps: {sum(t_step) / 1e3:.2f} s")
     # end to end through the public API with host buffers
     if e2e_steps:
@@ -1063,7 +1080,7 @@ def main():
                                "raytrace": sum(rs["t_ray"]) / rs["K"]},
                  "raytrace": {"metric": "ray-cell steps/s", "value": rs["rsteps"] / (sum(rs["t_ray"]) / 1e3),
                               "roofline": rs["ray_roofline"]},
-                 "roofline": rs["roofline"], "gather_probe": gps}
+                 "roofline": rs["roofline"], "gather_probe": gps, "schedule_tuning": rs["tuned"]}
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:
         log("oracle baseline")
@@ -1081,7 +1098,8 @@ def main():
                              "ray_cell_steps_per_step": r["rsteps"] // K, "roofline": r["ray_roofline"]},
                 "stats_per_step": {k: v // K for k, v in S.items() if not k.startswith("n_")},
                 "roofline": roof, "gather_probe": gp, "cpu_baseline": cpu, "e2e": r.get("e2e"),
-                "clocks": r["clocks"], "gpu_launches": r["launches"], "shell_128": shell}
+                "clocks": r["clocks"], "gpu_launches": r["launches"], "schedule_tuning": r["tuned"],
+                "shell_128": shell}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -22,7 +22,7 @@ from dataclasses import dataclass, field
 from typing import Callable, Dict, Iterable, List, Optional, Sequence, Tuple
 
 DEFAULT_GRID = {
-    "march_min_active": (8, 12, 16, 20, 24),
+    "march_min_active": (2, 4, 6, 8, 12, 16, 20, 24),
     "threads_per_block": (256, 128),
     "blocks_per_sm": (0,),
 }
@@ -77,17 +77,20 @@ def _cuda_timer(run):
 
 def tune_transport(ctx, grid, opac, sources, n_packets: int, sample: int = 2_000_000,
                    grid_values: Optional[Dict[str, Iterable[int]]] = None, repeats: int = 3,
-                   **kw) -> TuneResult:
+                   event_cap: int = 0, **kw) -> TuneResult:
     """Tune ``transport`` for one model on min(n_packets, sample) packets of
-    the same emission (same xi = L / n_packets, same packet ids)."""
+    the same emission (same xi = L / n_packets, same packet ids); with
+    record_events in ``kw``, ``event_cap`` sizes the sample's event buffer
+    (events beyond it are counted as dropped, as in any call)."""
     import torch
 
     from . import sim
     n = int(min(n_packets, sample))
-    out = sim.TransportOut(grid.ncell, grid.ns, opac.nf)
+    out = sim.TransportOut(grid.ncell, grid.ns, opac.nf, event_cap=int(event_cap))
 
     def run(c):
         out.zero_()
+        out.stats.zero_()
         sim.transport(ctx, grid, opac, sources, int(n_packets), out=out, pid_end=n, **kw, **c)
 
     cands = candidates(grid_values)
