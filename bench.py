@@ -83,6 +83,8 @@ def parse():
     ap.add_argument("--no-shell", action="store_true", help="skip the 128^3 shell sub-object")
     ap.add_argument("--no-tune", action="store_true",
                     help="skip the schedule autotuner (library default march_min_active)")
+    ap.add_argument("--march-min-active", type=int, default=None,
+                    help="fixed march_min_active instead of the autotuner's choice")
     ap.add_argument("--schedule", default="persistent", choices=["persistent", "compact"],
                     help="transport schedule: dynamic refill per warp, or with per-warp packet compaction")
     ap.add_argument("--sharded", action="store_true",
@@ -838,7 +840,10 @@ def run_step_bench(a, rt, ctx, m, K, Wu, flush, local, rank, world, dist, peaks,
     tkw = dict(record_events=True, record_nu=sorted(set(fidx)), mrw=a.mrw,
                schedule=R.RT_SCHED_COMPACT if a.schedule == "compact" else R.RT_SCHED_PERSISTENT)
     tuned = None
-    if a.schedule == "persistent" and not getattr(a, "no_tune", False):
+    if getattr(a, "march_min_active", None) is not None:
+        tkw["march_min_active"] = a.march_min_active
+        tuned = {"params": {"march_min_active": a.march_min_active}, "fixed": True}
+    elif a.schedule == "persistent" and not getattr(a, "no_tune", False):
         # the schedule autotuner (lanes still marching below which a warp
         # serves its interactions) on a bounded sample of the same emission,
         # before and outside the timed steps; the e2e steps use it too
@@ -1076,6 +1081,7 @@ def main():
     if a.workload == "disk" and not a.no_shell:
         b = argparse.Namespace(**vars(a))
         b.workload = "shell"
+        b.march_min_active = None              # tuned for its own workload
         for k in ("packets", "n", "tau", "npix", "nf", "mrw"):
             setattr(b, k, WORKLOADS["shell"][k])
         log("shell sub-object")
