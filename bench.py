@@ -41,9 +41,10 @@ L2_BYTES = 126.5 * 2 ** 20          # GB300 L2 (nominal 129 MB)
 # DRAM bytes (read + write) of one transport launch of each workload at its
 # default packet count, from single-pass ncu captures (profiles/): the disk's
 # taken on 1e7 packets and scaled by 10 (its traffic grows with the packets),
-# the shell's on the full launch.  Kernel source of commit 24a59b4; set to
-# None when the transport kernel changes until it is captured again.
-TRANSPORT_DRAM = {"disk": (26.847464192e9 + 10.863199488e9) * 10, "shell": 31.899392e6 + 0.653056e6}
+# the shell's on the full launch, each at the schedule the autotuner chose
+# (march_min_active 6 and 16), on the build of commit 87ec2d0; set to None
+# when the transport kernel changes until it is captured again.
+TRANSPORT_DRAM = {"disk": (26.856892928e9 + 10.885639168e9) * 10, "shell": 31.8656e6 + 0.653824e6}
 
 WORKLOADS = {
     "disk": dict(n=256, tau=1e4, nf=100, packets=1e8, npix=512, mrw=True,
