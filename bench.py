@@ -922,7 +922,11 @@ def run_step_bench(a, rt, ctx, m, K, Wu, flush, local, rank, world, dist, peaks,
         g2 = rt.Grid(ctx, rho_h, m.box_min, m.cell)               # the caller's grid handle
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for k in range(e2e_steps):
+        for k in range(-1, e2e_steps):                            # k = -1: untimed warm-up
+            if k == 0:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                cross_e2e = 0
             g2.update(rho_h)                                      # H2D of the step's density
             e2e_out.zero_()
             o = rt.transport(ctx, g2, opac, srcs, N, out=e2e_out, seed=50 + k, **tkw)
@@ -935,6 +939,7 @@ def run_step_bench(a, rt, ctx, m, K, Wu, flush, local, rank, world, dist, peaks,
             st_h.copy_(o.stats, non_blocking=True)
             torch.cuda.synchronize()
             cross_e2e += int(st_h[0])
+            log(f"e2e step {k}: {time.perf_counter() - t0:.2f} s since the timed start")
         dt = time.perf_counter() - t0
         del g2, e2e_out
         res["e2e"] = {"value": cross_e2e / dt, "unit": UNIT,
