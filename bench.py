@@ -922,14 +922,18 @@ def run_step_bench(a, rt, ctx, m, K, Wu, flush, local, rank, world, dist, peaks,
         g2 = rt.Grid(ctx, rho_h, m.box_min, m.cell)               # the caller's grid handle
         torch.cuda.synchronize()
         t0 = time.perf_counter()
+        clk_e2e = ClockSampler(local).__enter__()
         for k in range(-1, e2e_steps):                            # k = -1: untimed warm-up
             if k == 0:
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
                 cross_e2e = 0
+            ts0 = time.perf_counter()
             g2.update(rho_h)                                      # H2D of the step's density
             e2e_out.zero_()
             o = rt.transport(ctx, g2, opac, srcs, N, out=e2e_out, seed=50 + k, **tkw)
+            torch.cuda.synchronize()
+            ts1 = time.perf_counter()
             T = rt.temperatures(ctx, g2, opac, o.E_abs)
             img, sed = rt.raytrace(ctx, g2, opac, T, o, o.xi, srcs, cams, fidx)
             E_h.copy_(o.E_abs, non_blocking=True)
@@ -939,14 +943,16 @@ def run_step_bench(a, rt, ctx, m, K, Wu, flush, local, rank, world, dist, peaks,
             st_h.copy_(o.stats, non_blocking=True)
             torch.cuda.synchronize()
             cross_e2e += int(st_h[0])
-            log(f"e2e step {k}: {time.perf_counter() - t0:.2f} s since the timed start")
+            log(f"e2e step {k}: {time.perf_counter() - t0:.2f} s since the timed start "
+                f"(update + transport {ts1 - ts0:.3f} s, the rest {time.perf_counter() - ts1:.3f} s)")
         dt = time.perf_counter() - t0
+        clk_e2e.__exit__(None, None, None)
         del g2, e2e_out
         res["e2e"] = {"value": cross_e2e / dt, "unit": UNIT,
                       "h2d_bytes_per_step": int(rho_h.numel() * 4),
                       "d2h_bytes_per_step": int(E_h.numel() * 8 + T_h.numel() * 8 + img_h.numel() * 4
                                                 + sed_h.numel() * 8 + st_h.numel() * 8),
-                      "ms_per_step": 1e3 * dt / e2e_steps, "steps": e2e_steps}
+                      "ms_per_step": 1e3 * dt / e2e_steps, "steps": e2e_steps, "clocks": clk_e2e.summary()}
     del out
     torch.cuda.empty_cache()
     return res
