@@ -919,7 +919,8 @@ def run_step_bench(a, rt, ctx, m, K, Wu, flush, local, rank, world, dist, peaks,
         st_h = torch.empty(R.RT_STAT_COUNT, dtype=torch.int64).pin_memory()
         e2e_out = rt.TransportOut(grid.ncell, grid.ns, opac.nf, event_cap=ev_cap)
         cross_e2e = 0
-        g2 = rt.Grid(ctx, rho_h, m.box_min, m.cell)               # the caller's grid handle
+        g2 = grid                                                 # the caller's grid handle, refilled
+                                                                  # from host memory every step
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         clk_e2e = ClockSampler(local).__enter__()
