@@ -30,7 +30,14 @@ STAT_NAMES = ["crossings", "interactions", "scatters", "absorptions", "mrw_steps
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (plain C11, -O2, IEEE semantics, OpenMP)."""
+    """Compile the oracle with gcc (plain C11, -O2, IEEE semantics, OpenMP).
+
+    With ``RT_ORACLE_LIB`` set in the environment, that prebuilt library is
+    used instead: the mutation tests load builds of ``rt_oracle.c`` with one
+    planted mistake each and check that the pins catch it."""
+    alt = os.environ.get("RT_ORACLE_LIB")
+    if alt:
+        return alt
     os.makedirs(BUILD, exist_ok=True)
     hdr = os.path.join(HERE, "rt_oracle.h")
     if (not force and os.path.exists(LIB)
@@ -107,8 +114,7 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            build()
-            L = C.CDLL(LIB)
+            L = C.CDLL(build())
             dp = C.POINTER(C.c_double)
             L.or_planck_B.restype = C.c_double
             L.or_planck_B.argtypes = [C.c_double, C.c_double]

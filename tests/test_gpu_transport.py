@@ -554,13 +554,13 @@ def test_fp32_photon_counting_invariants(rt, ctx, O):
     xi = out.xi
     assert np.all(np.abs(top.sum(axis=(1, 2)) - sed[9]) <= 2 * xi)
     np.testing.assert_allclose(full.sum(axis=(1, 2)), sed.sum(axis=0), rtol=1e-12, atol=2 * xi)
-    assert full.sum() == pytest.approx(m.luminosity, rel=1e-9)
+    assert full.sum() == pytest.approx(m.luminosity, rel=1e-9, abs=0)
     rt.transport(ctx, grid, opac, srcs, N, out=out, pc_cams=cams, seed=6)
     torch.cuda.synchronize()
     top, full = [g.cpu().numpy() for g in out.pc_images()]
     sed = out.sed_esc.cpu().numpy()
     assert np.all(np.abs(top.sum(axis=(1, 2)) - sed[9]) <= 4 * xi)
-    assert full.sum() == pytest.approx(2 * m.luminosity, rel=1e-9)
+    assert full.sum() == pytest.approx(2 * m.luminosity, rel=1e-9, abs=0)
 
 
 def test_photon_counting_rejections(rt, ctx):
@@ -622,7 +622,7 @@ def test_fp32_pah_reemission_conserves_energy(rt, ctx):
     s2 = o2.stats_dict()
     assert s2["emitted"] == n1 and s2["escaped"] + s2["pah"] == n1 and s2["stuck"] == 0
     e1, e2 = o1.sed_esc.sum().item(), o2.sed_esc.sum().item()
-    assert e1 + e2 + s2["pah"] * o1.xi == pytest.approx(m.luminosity, rel=1e-9)
+    assert e1 + e2 + s2["pah"] * o1.xi == pytest.approx(m.luminosity, rel=1e-9, abs=0)
 
 
 def test_fp32_pah_reemission_frequency_law(rt, ctx):
@@ -676,7 +676,7 @@ def test_photon_counting_edge_cases(rt, ctx):
     none, one = [g.cpu().numpy() for g in out.pc_images()]
     assert none.sum() == 0.0
     assert one.shape == (m.nf, 1, 1)
-    assert one.sum() == pytest.approx(m.luminosity, rel=1e-9)
+    assert one.sum() == pytest.approx(m.luminosity, rel=1e-9, abs=0)
 
 
 def test_pah_reemission_without_records(rt, ctx):
@@ -736,11 +736,11 @@ def test_plain_fp32_form(rt, ctx):
     torch.cuda.synchronize()
     sb = b.stats_dict()
     assert sb["escaped"] == N and sb["stuck"] == 0
-    assert b.sed_esc.sum().item() == pytest.approx(m.luminosity, rel=1e-9)
+    assert b.sed_esc.sum().item() == pytest.approx(m.luminosity, rel=1e-9, abs=0)
     Ea, Eb = a.E_abs.cpu().numpy()[0], b.E_abs.cpu().numpy()[0]
     sig = np.sqrt(a.esq.cpu().numpy()[0] + b.esq.cpu().numpy()[0])
     on = Ea > 0
     assert np.all(np.abs(Eb[on] - Ea[on]) <= 5 * sig[on] + 2e-3 * Ea[on])
-    assert Eb.sum() == pytest.approx(Ea.sum(), rel=2e-3)
+    assert Eb.sum() == pytest.approx(Ea.sum(), rel=2e-3, abs=0)
     with pytest.raises(rt.RtError):
         rt.transport(ctx, grid, opac, srcs, 100, precision=rt.rtgb.RT_PREC_FP32_ACC32, traj_cap=1000)

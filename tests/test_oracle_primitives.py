@@ -203,7 +203,7 @@ def test_dda_segment_sum_equals_box_exit(O):
         k = rng.normal(size=3)
         k /= np.linalg.norm(k)
         cells, lens = O.dda_segments(m, x, k)
-        assert lens.sum() == pytest.approx(_box_exit(x, k, lo, hi), rel=1e-12)
+        assert lens.sum() == pytest.approx(_box_exit(x, k, lo, hi), rel=1e-12, abs=0)
         assert np.all(lens >= 0)
         # consecutive cells share a face
         iz, rem = np.divmod(cells, 5 * 7)
@@ -283,7 +283,7 @@ def test_refined_dda_chords_match_brute_force(O):
         k = rng.normal(size=3)
         k /= np.linalg.norm(k)
         cells, lens = O.dda_segments(m, x, k)
-        assert lens.sum() == pytest.approx(_box_exit(x, k, m.box_min, m.box_min + ext), rel=1e-12)
+        assert lens.sum() == pytest.approx(_box_exit(x, k, m.box_min, m.box_min + ext), rel=1e-12, abs=0)
         s = (np.arange(int(lens.sum() / h)) + 0.5) * h
         lin = _leaf_of_points(m, x[None, :] + s[:, None] * k[None, :])
         # the sampled sequence of distinct cells is the DDA's (cells shorter
