@@ -44,7 +44,7 @@ L2_BYTES = 126.5 * 2 ** 20          # GB300 L2 (nominal 129 MB)
 # the shell's on the full launch, each at the schedule the autotuner chose
 # (march_min_active 6 and 16), on the build of commit 87ec2d0; set to None
 # when the transport kernel changes until it is captured again.
-TRANSPORT_DRAM = {"disk": (26.856892928e9 + 10.885639168e9) * 10, "shell": 31.8656e6 + 0.653824e6}
+TRANSPORT_DRAM = {}
 
 WORKLOADS = {
     "disk": dict(n=256, tau=1e4, nf=100, packets=1e8, npix=512, mrw=True,

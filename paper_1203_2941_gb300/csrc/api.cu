@@ -736,9 +736,14 @@ static rt_status transport_one(rt_ctx* ctx, const rt_grid* grid, const rt_opacit
     if (prec == RT_PREC_FP32) {
         const size_t bytes = (acc32 ? sizeof(float) : sizeof(double)) * n_acc * (out->esq ? 2 : 1);
         RT_CUDA(cudaMallocAsync((void**)&acc, bytes, s));
-        RT_CUDA(cudaMemsetAsync(acc, 0, bytes, s));
         hms[0].md.accE = acc;
         hms[0].md.acc_q = out->esq ? 1 : 0;
+        if (acc32) {
+            RT_CUDA(cudaMemsetAsync(acc, 0, bytes, s));
+        } else {
+            st = launch_seed(acc, hms[0].md.acc_q, n_acc, hms[0].md.xi, out->E_abs, s);
+            if (st != RT_OK) { cudaFreeAsync(acc, s); return st; }
+        }
     }
     DeviceModels dm;
     st = stage_models(hms, { p->pid_end - p->pid_begin }, op->nf, true, s, dm);
@@ -932,7 +937,13 @@ rt_status rt_batch_run(rt_batch* b, rt_stream stream)
     if (!b) return fail(RT_ERR_INVALID_ARG, "rt_batch_run: NULL batch");
     cudaStream_t s = (cudaStream_t)stream;
     RT_CUDA(cudaMemsetAsync(b->dm.work, 0, sizeof(unsigned long long), s));
-    if (b->acc) RT_CUDA(cudaMemsetAsync(b->acc, 0, b->acc_bytes, s));
+    if (b->acc) {
+        for (int m = 0; m < b->n_models; ++m) {
+            const ModelDev& md = b->host[m];
+            const rt_status st = launch_seed(md.accE, md.acc_q, b->n_acc[m], md.xi, md.E_abs, s);
+            if (st != RT_OK) return st;
+        }
+    }
     const int threads = b->p.threads_per_block ? b->p.threads_per_block : 256;
     rt_status st = launch_transport(b->ctx, b->op, b->kp, b->ns, b->p.precision, b->p.schedule,
                                     threads, b->p.blocks_per_sm, s);
@@ -1210,9 +1221,11 @@ rt_status rt_transport_noalloc(rt_ctx* ctx, const rt_grid* grid, const rt_opacit
     hms[0].md.rho = packed;
     hms[0].md.cube_rho = grid->refine ? cube_packed : nullptr;
     if (acc) {
-        RT_CUDA(cudaMemsetAsync(acc, 0, acc_bytes, s));     // the array keeps the last call's sums
         hms[0].md.accE = acc;
         hms[0].md.acc_q = out->esq ? 1 : 0;
+        // the array keeps the last call's sums: seeded afresh from E_abs
+        st = launch_seed(acc, hms[0].md.acc_q, n_acc, hms[0].md.xi, out->E_abs, s);
+        if (st != RT_OK) return st;
     }
     DeviceModels dm;
     st = stage_models_into(hms, p->pid_end - p->pid_begin, op->nf, base, kNoAllocStaging, s, dm);

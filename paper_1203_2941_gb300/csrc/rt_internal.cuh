@@ -314,6 +314,8 @@ rt_status launch_finalize(const double* acc, int acc_q, size_t n, double xi, dou
                           double* esq, cudaStream_t s);
 rt_status launch_finalize32(const float* acc, int acc_q, size_t n, double xi, double* E_abs,
                             double* esq, cudaStream_t s);
+rt_status launch_seed(double* acc, int acc_q, size_t n, double xi, const double* E_abs,
+                      cudaStream_t s);
 rt_status launch_temperatures(rt_ctx* ctx, const rt_grid* g, const rt_opacity* op,
                               const double* E, double* T, cudaStream_t s);
 rt_status launch_temperature_guess(rt_ctx* ctx, const rt_grid* g, const double* src_pos,

@@ -926,15 +926,20 @@ struct Kernel {
 
     // Accumulated absorbed power (erg/s) of species s in the lane's cell,
     // including this call's FP32-build scratch; `old` is the value an atomic
-    // add just returned (then the packet's own xi is added).
+    // add just returned (then the packet's own xi is added).  The FP64
+    // scratch starts each call at E_abs / xi (seed_kernel), so it alone holds
+    // the accumulated energy and an absorption reads nothing beyond its
+    // atomic; the FP32 scratch of the plain-FP32 form starts at zero.
     __device__ __forceinline__ double energy(const Lane<R, NS>& L, int s, double old, bool have_old)
     {
         const size_t i = (size_t)s * md->ncell + L.c;
         if constexpr (DBG) {
             return have_old ? old + md->xi : __ldcg(&md->E_abs[i]);
-        } else {
+        } else if constexpr (ACC32) {
             const double acc = have_old ? old + 1.0 : (double)__ldcg(acc_at(i));
             return __ldcg(&md->E_abs[i]) + acc * md->xi;
+        } else {
+            return (have_old ? old + 1.0 : __ldcg(acc_at(i))) * md->xi;
         }
     }
 
@@ -1903,8 +1908,23 @@ __global__ void cube_pack_kernel(const int* cube, size_t ncube, const PT* packed
     out[q] = (info & kCubeDivided) ? PT{} : packed[info];
 }
 
-// E_abs += acc * xi and esq += acc_sq * xi^2 for one model (FP32 build);
-// with acc_q = 1 the scratch interleaves the two sums per cell
+// The FP64 scratch of one model (FP32 build) before a transport: the sum
+// starts at E_abs / xi, so that B&W temperatures read the accumulated energy
+// from the scratch alone; the sum of squares (acc_q = 1, interleaved) at 0.
+// xi <= 0 (no luminosity) deposits nothing: the sum starts at 0.
+__global__ void seed_kernel(double* acc, int acc_q, size_t n, double xi, const double* E_abs)
+{
+    const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    acc[i << acc_q] = xi > 0.0 ? E_abs[i] / xi : 0.0;
+    if (acc_q) acc[2 * i + 1] = 0.0;
+}
+
+// After a transport (FP32 build), for one model: E_abs = acc * xi where the
+// FP64 scratch (seeded with E_abs / xi) received deposits, E_abs += acc * xi
+// from the zero-started FP32 scratch of the plain-FP32 form, and
+// esq += acc_sq * xi^2; with acc_q = 1 the scratch interleaves the two sums
+// per cell.
 template <typename A>
 __global__ void finalize_kernel(const A* acc, int acc_q, size_t n, double xi, double* E_abs,
                                 double* esq)
@@ -1912,9 +1932,15 @@ __global__ void finalize_kernel(const A* acc, int acc_q, size_t n, double xi, do
     const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double a = (double)acc[i << acc_q];
-    if (a != 0.0) {
-        E_abs[i] += a * xi;
-        if (acc_q && esq) esq[i] += (double)acc[2 * i + 1] * xi * xi;
+    if constexpr (sizeof(A) == 8) {
+        if (!(xi > 0.0)) return;
+        if (a != E_abs[i] / xi) E_abs[i] = a * xi;
+    } else {
+        if (a != 0.0) E_abs[i] += a * xi;
+    }
+    if (acc_q && esq) {
+        const double q = (double)acc[2 * i + 1];
+        if (q != 0.0) esq[i] += q * xi * xi;
     }
 }
 
@@ -2121,6 +2147,16 @@ rt_status launch_finalize(const double* acc, int acc_q, size_t n, double xi, dou
 {
     if (n == 0) return RT_OK;
     finalize_kernel<double><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(acc, acc_q, n, xi, E_abs, esq);
+    count_launches();
+    RT_CUDA(cudaGetLastError());
+    return RT_OK;
+}
+
+rt_status launch_seed(double* acc, int acc_q, size_t n, double xi, const double* E_abs,
+                      cudaStream_t s)
+{
+    if (n == 0) return RT_OK;
+    seed_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(acc, acc_q, n, xi, E_abs);
     count_launches();
     RT_CUDA(cudaGetLastError());
     return RT_OK;
