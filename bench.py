@@ -42,9 +42,9 @@ L2_BYTES = 126.5 * 2 ** 20          # GB300 L2 (nominal 129 MB)
 # default packet count, from single-pass ncu captures (profiles/): the disk's
 # taken on 1e7 packets and scaled by 10 (its traffic grows with the packets),
 # the shell's on the full launch, each at the schedule the autotuner chose
-# (march_min_active 6 and 16), on the build of commit 87ec2d0; set to None
-# when the transport kernel changes until it is captured again.
-TRANSPORT_DRAM = {}
+# (march_min_active 6 and 16), on the build of commit 445f240; emptied when
+# the transport kernel changes until it is captured again.
+TRANSPORT_DRAM = {"disk": (25.136743680e9 + 10.662938112e9) * 10, "shell": 29.148672e6 + 0.595456e6}
 
 WORKLOADS = {
     "disk": dict(n=256, tau=1e4, nf=100, packets=1e8, npix=512, mrw=True,

@@ -390,7 +390,8 @@ RT_API rt_status rt_source_grid(const rt_opacity* opac, const rt_source* sources
  * that device current) and should come before any stream capture.  All calls
  * share the one array: calls whose GPU work overlaps (different streams
  * without ordering, or several host threads) race and must not be issued;
- * calls ordered on one stream are safe (each clears what must start at zero).
+ * calls ordered on one stream are safe (each rewrites what the previous call
+ * left: the counters start at zero, the energy scratch at E_abs / xi).
  * Photon-counting cameras, the deferred-packet queue, the separate source
  * grid and the plain-FP32 form are not served here: n_pc_cams and
  * defer_events must be 0, source_grid_nu NULL and precision not

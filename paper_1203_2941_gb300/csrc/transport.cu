@@ -1909,14 +1909,15 @@ __global__ void cube_pack_kernel(const int* cube, size_t ncube, const PT* packed
 }
 
 // The FP64 scratch of one model (FP32 build) before a transport: the sum
-// starts at E_abs / xi, so that B&W temperatures read the accumulated energy
-// from the scratch alone; the sum of squares (acc_q = 1, interleaved) at 0.
-// xi <= 0 (no luminosity) deposits nothing: the sum starts at 0.
-__global__ void seed_kernel(double* acc, int acc_q, size_t n, double xi, const double* E_abs)
+// starts at E_abs / xi (taken as E_abs * (1 / xi), the same product the
+// finalize compares with), so that B&W temperatures read the accumulated
+// energy from the scratch alone; the sum of squares (acc_q = 1, interleaved)
+// at 0.  xi <= 0 (no luminosity) deposits nothing: the sum starts at 0.
+__global__ void seed_kernel(double* acc, int acc_q, size_t n, double inv_xi, const double* E_abs)
 {
     const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    acc[i << acc_q] = xi > 0.0 ? E_abs[i] / xi : 0.0;
+    acc[i << acc_q] = inv_xi > 0.0 ? E_abs[i] * inv_xi : 0.0;
     if (acc_q) acc[2 * i + 1] = 0.0;
 }
 
@@ -1926,15 +1927,15 @@ __global__ void seed_kernel(double* acc, int acc_q, size_t n, double xi, const d
 // esq += acc_sq * xi^2; with acc_q = 1 the scratch interleaves the two sums
 // per cell.
 template <typename A>
-__global__ void finalize_kernel(const A* acc, int acc_q, size_t n, double xi, double* E_abs,
-                                double* esq)
+__global__ void finalize_kernel(const A* acc, int acc_q, size_t n, double xi, double inv_xi,
+                                double* E_abs, double* esq)
 {
     const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double a = (double)acc[i << acc_q];
     if constexpr (sizeof(A) == 8) {
-        if (!(xi > 0.0)) return;
-        if (a != E_abs[i] / xi) E_abs[i] = a * xi;
+        if (!(inv_xi > 0.0)) return;
+        if (a != E_abs[i] * inv_xi) E_abs[i] = a * xi;
     } else {
         if (a != 0.0) E_abs[i] += a * xi;
     }
@@ -2142,11 +2143,15 @@ rt_status pack_grid(rt_grid* g, const rt_opacity* op, int lucy_mode, double lucy
     return RT_OK;
 }
 
+// 1 / xi for the seed and finalize kernels (0 when xi <= 0: nothing deposited)
+static double inv_of(double xi) { return xi > 0.0 ? 1.0 / xi : 0.0; }
+
 rt_status launch_finalize(const double* acc, int acc_q, size_t n, double xi, double* E_abs,
                           double* esq, cudaStream_t s)
 {
     if (n == 0) return RT_OK;
-    finalize_kernel<double><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(acc, acc_q, n, xi, E_abs, esq);
+    finalize_kernel<double><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(acc, acc_q, n, xi, inv_of(xi),
+                                                                       E_abs, esq);
     count_launches();
     RT_CUDA(cudaGetLastError());
     return RT_OK;
@@ -2156,7 +2161,7 @@ rt_status launch_seed(double* acc, int acc_q, size_t n, double xi, const double*
                       cudaStream_t s)
 {
     if (n == 0) return RT_OK;
-    seed_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(acc, acc_q, n, xi, E_abs);
+    seed_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(acc, acc_q, n, inv_of(xi), E_abs);
     count_launches();
     RT_CUDA(cudaGetLastError());
     return RT_OK;
@@ -2166,7 +2171,8 @@ rt_status launch_finalize32(const float* acc, int acc_q, size_t n, double xi, do
                             double* esq, cudaStream_t s)
 {
     if (n == 0) return RT_OK;
-    finalize_kernel<float><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(acc, acc_q, n, xi, E_abs, esq);
+    finalize_kernel<float><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(acc, acc_q, n, xi, inv_of(xi),
+                                                                      E_abs, esq);
     count_launches();
     RT_CUDA(cudaGetLastError());
     return RT_OK;
