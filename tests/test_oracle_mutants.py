@@ -108,6 +108,22 @@ MUTANTS = {
     "escape_bin_wrong_axis": ("int b = (int)floor((k[2] + 1.0) * 5.0);",
                               "int b = (int)floor((k[0] + 1.0) * 5.0);",
                               [PHYS + "test_photon_counting_matches_escape_tallies"]),
+    "lucy_criterion_inverted": ("C.lucy[c] = mx < p->lucy_tau;", "C.lucy[c] = mx > p->lucy_tau;",
+                                [PHYS + "test_lucy_cells_are_those_below_the_face_to_face_threshold"]),
+    "lucy_criterion_cell_diagonal": ("double t = chi_ext(m, c, j) * C.h[c];",
+                                     "double t = chi_ext(m, c, j) * C.h[c] * sqrt(3.0);",
+                                     [PHYS + "test_lucy_cells_are_those_below_the_face_to_face_threshold"]),
+    "event_stores_outgoing_direction": (
+        "e->k[0] = k[0]; e->k[1] = k[1]; e->k[2] = k[2];",
+        "double kk[3] = { k[0], k[1], k[2] }; or_rotate(kk, mu, phi);"
+        " e->k[0] = kk[0]; e->k[1] = kk[1]; e->k[2] = kk[2];",
+        [PHYS + "test_stored_events_carry_the_incoming_direction"]),
+    "mrw_sphere_reaches_past_the_far_face": ("double d1 = x[a] - lo, d2 = lo + h - x[a];",
+                                             "double d1 = x[a] - lo, d2 = lo + 2.0 * h - x[a];",
+                                             [PRIM + "test_refined_mrw_sphere_stays_in_the_sub_cube"]),
+    "sub_cube_axes_swapped": ("p->s[0] = (int)(off % r);\n            p->s[1] = (int)((off / r) % r);",
+                              "p->s[1] = (int)(off % r);\n            p->s[0] = (int)((off / r) % r);",
+                              [PHYS + "test_pah_reemission_positions_and_directions"]),
     # re-emission (Eqs. 5, 10)
     "bw_samples_b_not_dbdt": ("? or_planck_dBdT(m->nu[l], T)", "? or_planck_B(m->nu[l], T)",
                               [PHYS + "test_bw_and_iterative_reach_the_same_temperatures"]),
