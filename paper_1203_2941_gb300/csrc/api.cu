@@ -729,8 +729,8 @@ static rt_status transport_one(rt_ctx* ctx, const rt_grid* grid, const rt_opacit
     if (st != RT_OK) return st;
     hms[0].md.rho = grid->d_packed;
     hms[0].md.cube_rho = grid->d_cube_packed;
-    // FP32 build: this call's deposits go to FP64 scratch in units of xi
-    // (FP32 scratch in the plain-FP32 form)
+    // FP32 build: this call's deposits go to FP64 scratch in units of xi,
+    // seeded with E_abs / xi (zero-started FP32 scratch in the plain-FP32 form)
     const size_t n_acc = (size_t)op->ns * grid->ncell();
     double* acc = nullptr;
     if (prec == RT_PREC_FP32) {
