@@ -124,6 +124,15 @@ MUTANTS = {
     "sub_cube_axes_swapped": ("p->s[0] = (int)(off % r);\n            p->s[1] = (int)((off / r) % r);",
                               "p->s[1] = (int)(off % r);\n            p->s[0] = (int)((off / r) % r);",
                               [PHYS + "test_pah_reemission_positions_and_directions"]),
+    "source_drawn_uniformly": ("if (C->nsrc > 1) si = pick_cdf(C->src_L, C->nsrc, rng_u(&r));",
+                               "if (C->nsrc > 1) si = (int)(rng_u(&r) * C->nsrc) % C->nsrc;",
+                               [PHYS + "test_sources_emit_in_proportion_to_their_luminosity"]),
+    "mrw_deposit_by_extinction": (
+        "double e = C->xi * m->kabs[s * m->nf + j] * rho_of(m, s, c) * l;",
+        "double e = C->xi * (m->kabs[s * m->nf + j] + m->ksca[s * m->nf + j]) * rho_of(m, s, c) * l;",
+        [PHYS + "test_mrw_on_and_off_agree"]),
+    "frozen_t_samples_dbdt": (": or_planck_B(m->nu[l], T);", ": or_planck_dBdT(m->nu[l], T);",
+                              [PHYS + "test_bw_and_iterative_reach_the_same_temperatures"]),
     # re-emission (Eqs. 5, 10)
     "bw_samples_b_not_dbdt": ("? or_planck_dBdT(m->nu[l], T)", "? or_planck_B(m->nu[l], T)",
                               [PHYS + "test_bw_and_iterative_reach_the_same_temperatures"]),

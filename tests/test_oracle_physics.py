@@ -172,6 +172,26 @@ def test_source_spectrum_is_the_normalised_blackbody(O):
     np.testing.assert_allclose(lnu, B * src.L / (B * m.dnu).sum(), rtol=1e-12)
 
 
+def test_sources_emit_in_proportion_to_their_luminosity(O):
+    """Packets of equal energy L/N (Sect. 2): with several sources and random
+    frequency bins, each packet's source is drawn with probability L_i / L,
+    so the packets leaving each source follow a binomial law with that mean
+    (within 4 sigma), and each source's packets follow its own spectrum."""
+    m = W.uniform_cube(n=3, tau_cell=0.5, nf=24, gray=False)
+    m.rho[:] = 0.0
+    m.sources = [W.Source((0.1 * m.cell, 0.2 * m.cell, 0.0), 2.0 * W.LSUN, 5800.0),
+                 W.Source((-0.3 * m.cell, 0.0, 0.1 * m.cell), 1.0 * W.LSUN, 3000.0)]
+    N = 30000
+    r = O.transport(m, N, seed=8, mode=O.MODE_NOREEMIT, traj_cap=3 * N)
+    em = r["traj"][r["traj"]["type"] == O.T_EMIT]
+    assert len(em) == N
+    first = np.abs(em["x"][:, 0] - m.sources[0].pos[0]) < 1e-3 * m.cell
+    p = 2.0 / 3.0
+    assert abs(first.sum() - N * p) < 4 * math.sqrt(N * p * (1 - p)), first.sum()
+    # the 3000 K source's packets sit at longer wavelengths than the 5800 K one's
+    assert em["nu"][~first].mean() < em["nu"][first].mean()
+
+
 def test_lucy_and_count_estimators_agree_per_species(O):
     """The path-length (Lucy) estimator and the absorption-count estimator of a
     cell's absorbed energy have the same expectation, because absorptions
