@@ -170,6 +170,31 @@ def test_deferred_packets_keep_their_trajectories(rt, ctx, O, schedule):
     assert abs(out.numpy()["sed_esc"].sum() / m.luminosity - 1) < 1e-9
 
 
+def test_fp64_several_sources_random_bins_match_oracle(rt, ctx, O):
+    """Several sources with random frequency bins (Sect. 2): each packet's
+    source is drawn by luminosity, then its bin from that source's own
+    spectrum.  FP64 trajectories of three blackbody sources of different
+    luminosity and temperature equal the oracle's to 1e-9."""
+    m = W.random_grid(n=(6, 5, 4), ns=2, seed=16, tau_scale=1.5, albedo=(0.3, 0.7))
+    p0 = np.asarray(m.sources[0].pos)
+    m.sources = [W.Source(tuple(p0), 2.0 * W.LSUN, 5800.0),
+                 W.Source(tuple(0.5 * p0), 1.0 * W.LSUN, 3500.0),
+                 W.Source(tuple(0.3 * p0), 0.5 * W.LSUN, 900.0)]
+    grid, opac, srcs = _setup(rt, ctx, m)
+    T0 = np.random.default_rng(5).uniform(50, 800, size=(m.ns, m.ncell))
+    N = 1500
+    out = rt.transport(ctx, grid, opac, srcs, N, mode=rt.rtgb.RT_MODE_FROZEN_T,
+                       precision=rt.rtgb.RT_PREC_FP64, T_prev=torch.tensor(T0, device="cuda"),
+                       traj_cap=600 * N, seed=23)
+    torch.cuda.synchronize()
+    ref = O.transport(m, N, seed=23, mode=O.MODE_FROZEN_T, T_prev=T0, traj_cap=600 * N)
+    tg = out.traj_numpy()
+    _traj_compare(tg, ref["traj"], m.cell * 7)
+    em = tg[tg["type"] == O.T_EMIT]
+    starts = {tuple(np.round(x / m.cell, 6)) for x in em["x"]}
+    assert len(starts) == 3                      # every source emitted
+
+
 def test_equal_energy_source_bins_match_oracle(rt, ctx, O):
     """Eq. 1 source grid (source_bins = m): FP64 trajectories equal the
     oracle's; in FP32 the emission histogram (empty grid, every packet escapes
