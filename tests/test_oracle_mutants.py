@@ -133,6 +133,23 @@ MUTANTS = {
         [PHYS + "test_mrw_on_and_off_agree"]),
     "frozen_t_samples_dbdt": (": or_planck_B(m->nu[l], T);", ": or_planck_dBdT(m->nu[l], T);",
                               [PHYS + "test_bw_and_iterative_reach_the_same_temperatures"]),
+    "eq4_bracket_not_widened": (
+        "while (4.0 * OR_PI * or_planck_mean(m, s, hi) < target && hi < 1e12) hi *= 2.0;",
+        "while (0) hi *= 2.0;",
+        [PHYS + "test_temperature_solve_inverts_planck_mean"]),
+    "guess_cap_raised": ("if (!(t < 2000.0)) t = 2000.0;", "if (!(t < 20000.0)) t = 20000.0;",
+                         [PHYS + "test_temperature_guess_closed_form"]),
+    "refined_cell_number_axes_reversed": ("return b + ((int64_t)p->s[2] * r + p->s[1]) * r + p->s[0];",
+                                          "return b + ((int64_t)p->s[0] * r + p->s[1]) * r + p->s[2];",
+                                          [PRIM + "test_refined_dda_chords_match_brute_force"]),
+    "sub_cube_edge_not_divided": ("return p->f ? m->cell / m->refine : m->cell;", "return m->cell;",
+                                  [PRIM + "test_refined_dda_chords_match_brute_force"]),
+    "pc_y_from_the_x_axis": ("double yp = rel[0] * ey[0] + rel[1] * ey[1] + rel[2] * ey[2];",
+                             "double yp = rel[0] * ex[0] + rel[1] * ex[1] + rel[2] * ex[2];",
+                             [PHYS + "test_photon_counting_geometry_closed_forms"]),
+    "camera_y_axis_flipped": ("ey[0] = -ct * cp; ey[1] = -ct * sp; ey[2] = st;",
+                              "ey[0] = ct * cp; ey[1] = ct * sp; ey[2] = -st;",
+                              [PHYS + "test_photon_counting_geometry_closed_forms"]),
     # re-emission (Eqs. 5, 10)
     "bw_samples_b_not_dbdt": ("? or_planck_dBdT(m->nu[l], T)", "? or_planck_B(m->nu[l], T)",
                               [PHYS + "test_bw_and_iterative_reach_the_same_temperatures"]),

@@ -59,7 +59,7 @@ def test_temperature_solve_gray_closed_form(O):
 
 def test_temperature_solve_inverts_planck_mean(O):
     m = W.r2_shell(n=8, nf=64)
-    for T0 in (3.0, 47.0, 812.0, 1.6e4):
+    for T0 in (3.0, 47.0, 812.0, 1.6e4, 3.0e5):
         target = 4 * math.pi * O.planck_mean(m, 0, T0)
         assert O.solve_temperature(m, 0, target) == pytest.approx(T0, rel=1e-10, abs=0)
 
@@ -1027,3 +1027,8 @@ def test_temperature_guess_closed_form(O):
             q += s.L / (16 * math.pi * SIGMA * r2)
         expect = np.minimum(q ** 0.25, 2000.0)
         np.testing.assert_allclose(T[0], expect, rtol=1e-9)
+    # the cap: a hot source close to a cell centre (unit cube of 0.05 AU)
+    h = W.uniform_cube(n=4, tau_cell=0.1, side_au=0.05, source_pos=(0.01 * W.AU, 0.0, 0.0))
+    h.sources[0] = W.Source(h.sources[0].pos, 1e4 * W.LSUN, 5800.0)
+    T = O.temperature_guess(h)[0]
+    assert T.max() == 2000.0 and (T == 2000.0).sum() >= 8
