@@ -150,6 +150,8 @@ MUTANTS = {
     "camera_y_axis_flipped": ("ey[0] = -ct * cp; ey[1] = -ct * sp; ey[2] = st;",
                               "ey[0] = ct * cp; ey[1] = ct * sp; ey[2] = -st;",
                               [PHYS + "test_photon_counting_geometry_closed_forms"]),
+    "pah_absorption_reemitted": ("\n        if (m->is_pah && m->is_pah[s]) {", "\n        if (0) {",
+                                 [PHYS + "test_pah_packets_are_stored_and_counted"]),
     # re-emission (Eqs. 5, 10)
     "bw_samples_b_not_dbdt": ("? or_planck_dBdT(m->nu[l], T)", "? or_planck_B(m->nu[l], T)",
                               [PHYS + "test_bw_and_iterative_reach_the_same_temperatures"]),
