@@ -748,7 +748,14 @@ static rt_status transport_one(rt_ctx* ctx, const rt_grid* grid, const rt_opacit
     DeviceModels dm;
     st = stage_models(hms, { p->pid_end - p->pid_begin }, op->nf, true, s, dm);
     if (st != RT_OK) { if (acc) cudaFreeAsync(acc, s); return st; }
-    RT_CUDA(cudaMemsetAsync(dm.work, 0, sizeof(unsigned long long), s));
+    {
+        const cudaError_t e = cudaMemsetAsync(dm.work, 0, sizeof(unsigned long long), s);
+        if (e != cudaSuccess) {
+            cudaFreeAsync(dm.buf, s);
+            if (acc) cudaFreeAsync(acc, s);
+            return cuda_fail(e, "rt_transport work counter");
+        }
+    }
     TransportKP kp;
     fill_kp(kp, op, p, dm, 1);
     fill_pc(kp, grid, p, out);
