@@ -739,7 +739,8 @@ static rt_status transport_one(rt_ctx* ctx, const rt_grid* grid, const rt_opacit
         hms[0].md.accE = acc;
         hms[0].md.acc_q = out->esq ? 1 : 0;
         if (acc32) {
-            RT_CUDA(cudaMemsetAsync(acc, 0, bytes, s));
+            const cudaError_t e = cudaMemsetAsync(acc, 0, bytes, s);
+            if (e != cudaSuccess) { cudaFreeAsync(acc, s); return cuda_fail(e, "rt_transport scratch"); }
         } else {
             st = launch_seed(acc, hms[0].md.acc_q, n_acc, hms[0].md.xi, out->E_abs, s);
             if (st != RT_OK) { cudaFreeAsync(acc, s); return st; }
