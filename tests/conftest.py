@@ -15,6 +15,15 @@ def pytest_configure(config):
 
 @pytest.fixture(scope="session")
 def O():
-    from oracle import oracle
+    alt = os.environ.get("RT_ORACLE_PY")
+    if alt:
+        # a copy of oracle/oracle.py with one planted mistake (the mutation
+        # tests of the oracle's pins)
+        import importlib.util
+        spec = importlib.util.spec_from_file_location("oracle_planted", alt)
+        oracle = importlib.util.module_from_spec(spec)
+        spec.loader.exec_module(oracle)
+    else:
+        from oracle import oracle
     oracle.build()
     return oracle

@@ -1,13 +1,14 @@
 """Planted-mistake (mutation) checks of the oracle's pins (CPU only).
 
-Each mutant below is a copy of ``oracle/rt_oracle.c`` with ONE plausible
-mistake planted in it -- a dropped factor or term, a wrong sign, a transposed
+Each mutant below is a copy of ``oracle/rt_oracle.c`` (or of the Python
+half, ``oracle/oracle.py``) with ONE plausible mistake planted in it -- a dropped factor or term, a wrong sign, a transposed
 operand or index, the wrong cross-section or Planck function -- and the pins
 named beside it must fail on that build.  A mutant that every named pin
 passes would be a mistake the oracle could carry unnoticed.  The unmodified
 source, compiled the same way, must pass the union of the named pins (the
 control).  The builds and pin runs go to subprocesses in parallel, each
-loading its library through ``RT_ORACLE_LIB``.
+loading its library through ``RT_ORACLE_LIB`` (and a planted oracle.py
+through ``RT_ORACLE_PY``).
 """
 from __future__ import annotations
 
@@ -228,6 +229,24 @@ MUTANTS = {
 }
 
 
+# Mistakes planted in the Python half of the oracle (oracle/oracle.py), run
+# with the unmodified C library: name -> (text, replacement, pins)
+PY = os.path.join(ORACLE, "oracle.py")
+PY_MUTANTS = {
+    "vis_pixel_corner_not_centre": ("a = (np.arange(npix) + 0.5 - 0.5 * npix) * pix / cam.D",
+                                    "a = (np.arange(npix) - 0.5 * npix) * pix / cam.D",
+                                    [PHYS + "test_visibility_definition_pins"]),
+    "vis_u_and_v_swapped": ("ph = np.exp(-2j * np.pi * (u * a[None, :] + v * a[:, None]))",
+                            "ph = np.exp(-2j * np.pi * (u * a[:, None] + v * a[None, :]))",
+                            [PHYS + "test_visibility_definition_pins"]),
+    "vis_phase_sign": ("ph = np.exp(-2j * np.pi * (u * a[None, :] + v * a[:, None]))",
+                       "ph = np.exp(2j * np.pi * (u * a[None, :] + v * a[:, None]))",
+                       [PHYS + "test_visibility_definition_pins"]),
+    "vis_flux_over_d_not_d2": ("* pix * pix / (cam.D * cam.D)", "* pix * pix / cam.D",
+                               [PHYS + "test_visibility_definition_pins"]),
+}
+
+
 def _compile(src_text: str, out: str) -> None:
     c = out[:-3] + ".c"
     with open(c, "w") as f:
@@ -236,8 +255,10 @@ def _compile(src_text: str, out: str) -> None:
                     "-I", ORACLE, "-o", out, c, "-lm"], check=True, capture_output=True)
 
 
-def _run_pins(lib: str, pins) -> subprocess.CompletedProcess:
+def _run_pins(lib: str, pins, py: str = "") -> subprocess.CompletedProcess:
     env = dict(os.environ, RT_ORACLE_LIB=lib, OMP_NUM_THREADS="2")
+    if py:
+        env["RT_ORACLE_PY"] = py
     return subprocess.run([sys.executable, "-m", "pytest", "-q", "-p", "no:cacheprovider",
                            "-m", "not gpu", *pins], cwd=ROOT, env=env, capture_output=True,
                           text=True, timeout=900)
@@ -255,24 +276,48 @@ def _one(name, text, workdir):
     return r.returncode, (r.stdout + r.stderr)[-3000:]
 
 
+def _one_py(name, lib, workdir):
+    """A planted mistake in oracle.py (or, for "_pycontrol", the unmodified
+    file run the same way), with the unmodified C library."""
+    text = open(PY).read()
+    if name == "_pycontrol":
+        pins = sorted({p for _, _, ps in PY_MUTANTS.values() for p in ps})
+    else:
+        old, new, pins = PY_MUTANTS[name]
+        text = text.replace(old, new)
+    py = os.path.join(workdir, f"{name}.py")
+    with open(py, "w") as f:
+        f.write(text)
+    r = _run_pins(lib, pins, py)
+    return r.returncode, (r.stdout + r.stderr)[-3000:]
+
+
 @pytest.fixture(scope="module")
 def results(tmp_path_factory):
     text = open(SRC).read()
     for name, (old, _, _) in MUTANTS.items():
         assert text.count(old) == 1, f"mutant {name}: its site is not unique in rt_oracle.c"
+    py_text = open(PY).read()
+    for name, (old, _, _) in PY_MUTANTS.items():
+        assert py_text.count(old) == 1, f"mutant {name}: its site is not unique in oracle.py"
     wd = str(tmp_path_factory.mktemp("oracle_mutants"))
+    base = os.path.join(wd, "_unmodified.so")
+    _compile(text, base)
     names = ["_control"] + list(MUTANTS)
     with cf.ThreadPoolExecutor(max_workers=os.cpu_count() or 2) as ex:
         futs = {n: ex.submit(_one, n, text, wd) for n in names}
+        futs.update({n: ex.submit(_one_py, n, base, wd) for n in ["_pycontrol"] + list(PY_MUTANTS)})
         return {n: f.result() for n, f in futs.items()}
 
 
 def test_unmodified_oracle_passes_every_named_pin(results):
     rc, log = results["_control"]
     assert rc == 0, log
+    rc, log = results["_pycontrol"]
+    assert rc == 0, log
 
 
-@pytest.mark.parametrize("name", list(MUTANTS))
+@pytest.mark.parametrize("name", list(MUTANTS) + list(PY_MUTANTS))
 def test_planted_mistake_fails_a_pin(results, name):
     rc, log = results[name]
     # pytest exits 1 when tests ran and some failed; a crash or a collection
