@@ -153,6 +153,16 @@ MUTANTS = {
                               [PHYS + "test_photon_counting_geometry_closed_forms"]),
     "pah_absorption_reemitted": ("\n        if (m->is_pah && m->is_pah[s]) {", "\n        if (0) {",
                                  [PHYS + "test_pah_packets_are_stored_and_counted"]),
+    "eq4_bisection_stops_early": ("while (hi - lo > 1e-12 * hi) {", "while (hi - lo > 1e-4 * hi) {",
+                                  [PHYS + "test_temperature_solve_inverts_planck_mean"]),
+    "cdf_pick_one_bin_late": ("        if (acc >= target) return j;",
+                              "        if (acc >= target) return j + (j < n - 1);",
+                              [PHYS + "test_empty_grid_emission_spectrum_and_isotropy"]),
+    "hg_isotropic_branch_half_range": ("        mu = 2.0 * z - 1.0;", "        mu = z;",
+                                       [PRIM + "test_hg_sampler_moments_and_ks"]),
+    "mrw_bisection_reversed": ("        if (or_mrw_survival(mid) > u) lo = mid; else hi = mid;",
+                               "        if (or_mrw_survival(mid) > u) hi = mid; else lo = mid;",
+                               [PRIM + "test_mrw_sampler_moments_and_ks"]),
     # re-emission (Eqs. 5, 10)
     "bw_samples_b_not_dbdt": ("? or_planck_dBdT(m->nu[l], T)", "? or_planck_B(m->nu[l], T)",
                               [PHYS + "test_bw_and_iterative_reach_the_same_temperatures"]),
